@@ -1,0 +1,187 @@
+/*
+ * ibm.h -- C ABI of the GB300 fractional-step immersed-boundary solver.
+ *
+ * One call of ibm_step advances incompressible Navier--Stokes on a uniform
+ * staggered (MAC) grid by the fractional-step method of Sec. II.B of
+ * "Direct numerical simulation of flapping flags in grid-induced turbulence"
+ * (Olivieri, Viola, Mazzino, Rosti): AB2 advection and Crank--Nicolson
+ * diffusion by approximate factorisation for the provisional velocity, then
+ * immersed-boundary direct forcing (regularised delta-kernel interpolation
+ * and spreading, the uniform-grid form of the moving-least-squares forcing)
+ * for the passive bar grid and the flexible flag, then the pressure Poisson
+ * equation (transforms in the periodic y, z directions and a tridiagonal
+ * solve along x) and the projection. The flag is a spring network (Sec. II.B,
+ * last paragraphs) hinged at its leading edge, advanced in FP64 with
+ * velocity-Verlet sub-steps. Boundary conditions follow Sec. II.A: uniform
+ * inflow (U, 0, 0) at x = 0, convective outflow at x = Lx, periodic y, z.
+ *
+ * Units: lengths in flag lengths (L = 1), velocities in inflow speeds
+ * (U = 1), fluid density 1, viscosity 1/Re.
+ *
+ * Layout of every field on the device and in host buffers: x slowest,
+ * z fastest, index (i * ny + j) * nz + k.
+ *   u, v, w : (nx + 1) * ny * nz values.
+ *     u[i] sits on the x-face i (i = 0 inflow, i = nx outflow);
+ *     v[i], w[i] sit at x = (i + 1/2) h for i < nx; plane i = nx holds the
+ *     ghost values just outside the outflow.
+ *   p       : nx * ny * nz values at cell centres.
+ *
+ * Status codes: every int-returning function returns IBM_OK (0) or a
+ * negative IBM_E* code; ibm_strerror names it. Errors leave the state as it
+ * was before the call unless stated otherwise. The library never aborts the
+ * process and never traps on the GPU.
+ *
+ * Threading: one ibm_state must not be used from two host threads at once.
+ * Streams: all device work of a state is ordered on the stream given at
+ * creation (or a stream the library creates). ibm_step is asynchronous with
+ * respect to the host; the query calls synchronise that stream.
+ */
+#ifndef IBM_H
+#define IBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define IBM_OK         0
+#define IBM_EINVAL    -1   /* an argument is out of range or inconsistent    */
+#define IBM_ENOMEM    -2   /* device workspace missing, too small or unallocatable */
+#define IBM_ECUDA     -3   /* a CUDA runtime call failed                      */
+#define IBM_EDIVERGED -4   /* non-finite velocity or CFL above the limit      */
+#define IBM_ETIMEOUT  -5   /* a bounded device-side wait ran out              */
+#define IBM_EIO       -6   /* checkpoint file could not be written or read    */
+
+/* arithmetic of the fluid fields */
+#define IBM_FP64  0        /* everything in FP64                               */
+#define IBM_FP32  1        /* fluid fields and kernels in FP32; flag, sums FP64 */
+
+/* field selectors for ibm_get_field / ibm_set_field */
+#define IBM_FIELD_U 0
+#define IBM_FIELD_V 1
+#define IBM_FIELD_W 2
+#define IBM_FIELD_P 3
+
+/* Cells per direction. The spacing h = lx/nx must equal ly/ny and lz/nz;
+ * ny and nz must be powers of two in [4, 1024]; nx >= 4. */
+typedef struct { int nx, ny, nz; } ibm_grid;
+
+/* Domain lengths (Sec. II.A: Lx x Ly x Lz box). */
+typedef struct { double lx, ly, lz; } ibm_domain;
+
+/* Immersed bodies (Sec. II.A geometry).
+ * Bar grid: square rods of side bar_width on a mesh bar_mesh in the plane
+ *   x = bar_x, rods along y centred at z = (r + 1/2) bar_mesh and rods along
+ *   z centred at y = (r + 1/2) bar_mesh; ly and lz must be whole multiples
+ *   of bar_mesh. The rods are filled with markers (ceil(width/h) + 1 across
+ *   each short side, ceil(length/h) along), crossings counted once.
+ * Flag: flag_len x flag_span sheet hinged along its leading edge at
+ *   x = flag_x_le, centred in y and z, pitched by pitch0 about the spanwise
+ *   axis, flag_ns x flag_nt vertices (streamwise x spanwise), mass ratio
+ *   rho = (rho_s / rho_f)(thickness / L), bending coefficient
+ *   beta = B / (rho_f U^2 L^3), stretching spring constant `stretch`. */
+typedef struct {
+  int    bars_on;
+  double bar_x, bar_mesh, bar_width;
+  int    flag_on;
+  double flag_x_le, flag_len, flag_span;
+  int    flag_ns, flag_nt;
+  double mass_ratio, bending, pitch0, stretch;
+} ibm_bodies;
+
+/* Options (pass NULL for the defaults given in brackets). */
+typedef struct {
+  int    precision;   /* IBM_FP64 or IBM_FP32 [IBM_FP64]                         */
+  double cfl;         /* Courant number used when ibm_step gets dt <= 0 [0.3]    */
+  double cfl_limit;   /* ibm_step reports IBM_EDIVERGED above this CFL [2.0]     */
+  void*  stream;      /* cudaStream_t to run on; NULL: the library creates one   */
+  /* Initial perturbations added to u = U, v = w = 0 before the initial
+   * projection: host arrays of (nx+1)*ny*nz doubles in the field layout, or
+   * NULL. The inflow and outflow faces of u and the ghost planes of v, w must
+   * hold zeros. Copied during ibm_create; the caller keeps ownership. */
+  const double* init_u;
+  const double* init_v;
+  const double* init_w;
+} ibm_options;
+
+/* Diagnostics read by ibm_stats (all FP64). */
+typedef struct {
+  long long step;        /* steps taken                                         */
+  double t;              /* simulated time                                      */
+  double dt;             /* last time step                                      */
+  double cfl;            /* dt * max_cells(|u|+|v|+|w|) / h at the last step    */
+  double max_div;        /* max |div u| over cells (after the last projection)  */
+  double q_in, q_out;    /* volume fluxes through the inflow / outflow faces    */
+  double ke;             /* kinetic energy 1/2 sum |u|^2 h^3 (face values)      */
+  double ib_slip;        /* max |U*_l - U_l| over markers before the last forcing */
+  double te_mid[3];      /* position of the flag's trailing-edge mid vertex     */
+  double force[3];       /* total fluid force on the flag, sum -F_l dV_l        */
+  double max_strain;     /* max |len/len0 - 1| over flag springs                */
+  int    n_sub;          /* structural sub-steps used by the last step          */
+  int    n_markers;      /* flag vertices + bar markers                         */
+} ibm_stats_t;
+
+typedef struct ibm_state ibm_state;   /* opaque; owns its device data */
+
+/* Bytes of device workspace ibm_create needs for this problem (all fields,
+ * marker data, flag data and scratch). Fails with IBM_EINVAL on the argument
+ * checks ibm_create makes. */
+int ibm_workspace_bytes(const ibm_grid* grid, const ibm_domain* domain,
+                        const ibm_bodies* bodies, const ibm_options* opts,
+                        size_t* bytes);
+
+/* Build a solver state: validate, generate the flag lattice and bar markers
+ * on the host, upload them, set u = U + init_u, v = init_v, w = init_w,
+ * p = 0, apply one projection, and capture one time step as a CUDA graph.
+ * workspace: a device pointer of at least ibm_workspace_bytes() bytes,
+ * 256-byte aligned, owned by the caller and kept alive until ibm_destroy;
+ * or NULL, in which case the library allocates (and later frees) its own.
+ * Re > 0 sets the viscosity nu = 1/Re. */
+int ibm_create(const ibm_grid* grid, const ibm_domain* domain, double re,
+               const ibm_bodies* bodies, const ibm_options* opts,
+               void* workspace, size_t workspace_bytes, ibm_state** out);
+
+/* Advance nsteps >= 0 time steps (Sec. II.B step order). dt > 0: fixed step;
+ * dt <= 0: each step uses dt = cfl * h / max_cells(|u|+|v|+|w|) computed on
+ * the device from the current velocity. Asynchronous: returns after the
+ * launches are queued. Divergence is checked once per call, after the last
+ * step, and reported as IBM_EDIVERGED (the fields then hold the diverged
+ * state). */
+int ibm_step(ibm_state* s, double dt, int nsteps);
+
+/* Wait for the state's stream. */
+int ibm_sync(ibm_state* s);
+
+/* Copy the flag's vertex positions X, velocities V and the fluid force on
+ * each vertex F (each 3 * n_vertices doubles, vertex (a, b) at index
+ * a * flag_nt + b, xyz interleaved) to host memory. V and F may be NULL.
+ * n_vertices must equal flag_ns * flag_nt. Synchronises. */
+int ibm_flag_state(ibm_state* s, double* X, double* V, double* F, size_t n_vertices);
+
+/* Compute and copy the diagnostics (launches small reduction kernels and
+ * synchronises). */
+int ibm_stats(ibm_state* s, ibm_stats_t* out);
+
+/* Copy one field to / from host memory as doubles (n must equal the field
+ * size in the layout above). ibm_set_field converts to the state's precision
+ * and does not project. Both synchronise. */
+int ibm_get_field(ibm_state* s, int which, double* host, size_t n);
+int ibm_set_field(ibm_state* s, int which, const double* host, size_t n);
+
+/* Number of markers (flag vertices first, then bar markers) and their
+ * positions at the start of the next step (3 doubles each). */
+int ibm_marker_count(const ibm_state* s, size_t* n);
+int ibm_get_markers(ibm_state* s, double* X, size_t n);
+
+/* Release the state (and the workspace if the library allocated it). */
+void ibm_destroy(ibm_state* s);
+
+const char* ibm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBM_H */

@@ -1,0 +1,268 @@
+"""ctypes binding of the solver's C ABI (include/ibm.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. PyTorch provides the device workspace (so the memory belongs to
+torch's caching allocator) and the CUDA stream. The library must have been
+built (``paper_2103_08246_gb300.build.build()``); loading fails loudly
+otherwise, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .inputs import Workload
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libibm_gb300.so")
+
+IBM_OK, IBM_EINVAL, IBM_ENOMEM, IBM_ECUDA, IBM_EDIVERGED, IBM_ETIMEOUT, IBM_EIO = 0, -1, -2, -3, -4, -5, -6
+IBM_FP64, IBM_FP32 = 0, 1
+IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P = 0, 1, 2, 3
+
+# every symbol include/ibm.h declares
+SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_flag_state",
+           "ibm_stats", "ibm_get_field", "ibm_set_field", "ibm_marker_count", "ibm_get_markers",
+           "ibm_destroy", "ibm_strerror")
+
+
+class ibm_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+class ibm_domain(ctypes.Structure):
+    _fields_ = [("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double)]
+
+
+class ibm_bodies(ctypes.Structure):
+    _fields_ = [("bars_on", ctypes.c_int), ("bar_x", ctypes.c_double),
+                ("bar_mesh", ctypes.c_double), ("bar_width", ctypes.c_double),
+                ("flag_on", ctypes.c_int), ("flag_x_le", ctypes.c_double),
+                ("flag_len", ctypes.c_double), ("flag_span", ctypes.c_double),
+                ("flag_ns", ctypes.c_int), ("flag_nt", ctypes.c_int),
+                ("mass_ratio", ctypes.c_double), ("bending", ctypes.c_double),
+                ("pitch0", ctypes.c_double), ("stretch", ctypes.c_double)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class ibm_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("cfl", ctypes.c_double),
+                ("cfl_limit", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("init_u", _dp), ("init_v", _dp), ("init_w", _dp)]
+
+
+class ibm_stats_t(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_longlong), ("t", ctypes.c_double), ("dt", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("max_div", ctypes.c_double),
+                ("q_in", ctypes.c_double), ("q_out", ctypes.c_double), ("ke", ctypes.c_double),
+                ("ib_slip", ctypes.c_double), ("te_mid", ctypes.c_double * 3),
+                ("force", ctypes.c_double * 3), ("max_strain", ctypes.c_double),
+                ("n_sub", ctypes.c_int), ("n_markers", ctypes.c_int)]
+
+    def as_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the shared library and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"solver library not built: {path} is missing "
+                           "(run paper_2103_08246_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    sz = ctypes.c_size_t
+    lib.ibm_workspace_bytes.argtypes = [ctypes.POINTER(ibm_grid), ctypes.POINTER(ibm_domain),
+                                        ctypes.POINTER(ibm_bodies), ctypes.POINTER(ibm_options),
+                                        ctypes.POINTER(sz)]
+    lib.ibm_create.argtypes = [ctypes.POINTER(ibm_grid), ctypes.POINTER(ibm_domain), ctypes.c_double,
+                               ctypes.POINTER(ibm_bodies), ctypes.POINTER(ibm_options), vp, sz,
+                               ctypes.POINTER(vp)]
+    lib.ibm_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    lib.ibm_sync.argtypes = [vp]
+    lib.ibm_flag_state.argtypes = [vp, _dp, _dp, _dp, sz]
+    lib.ibm_stats.argtypes = [vp, ctypes.POINTER(ibm_stats_t)]
+    lib.ibm_get_field.argtypes = [vp, ctypes.c_int, _dp, sz]
+    lib.ibm_set_field.argtypes = [vp, ctypes.c_int, _dp, sz]
+    lib.ibm_marker_count.argtypes = [vp, ctypes.POINTER(sz)]
+    lib.ibm_get_markers.argtypes = [vp, _dp, sz]
+    lib.ibm_destroy.argtypes = [vp]
+    lib.ibm_destroy.restype = None
+    lib.ibm_strerror.argtypes = [ctypes.c_int]
+    lib.ibm_strerror.restype = ctypes.c_char_p
+    for name in SYMBOLS:
+        if name not in ("ibm_destroy", "ibm_strerror"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class IBMError(RuntimeError):
+    def __init__(self, code, where):
+        msg = load().ibm_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def _check(code, where):
+    if code != IBM_OK:
+        raise IBMError(code, where)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+def structs_from_workload(wl: Workload):
+    grid = ibm_grid(wl.nx, wl.ny, wl.nz)
+    dom = ibm_domain(wl.lx, wl.ly, wl.lz)
+    bodies = ibm_bodies(int(wl.bars_on), wl.bar_x, wl.bar_mesh, wl.bar_width, int(wl.flag_on),
+                        wl.flag_x_le, wl.flag_len, wl.flag_span, wl.flag_ns, wl.flag_nt,
+                        wl.mass_ratio, wl.bending, wl.pitch0, wl.stretch)
+    return grid, dom, bodies
+
+
+# ----------------------------------------------------------------- C-ABI names
+def ibm_workspace_bytes(grid, dom, bodies, opts) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().ibm_workspace_bytes(ctypes.byref(grid), ctypes.byref(dom), ctypes.byref(bodies),
+                                      ctypes.byref(opts) if opts is not None else None,
+                                      ctypes.byref(n)), "ibm_workspace_bytes")
+    return n.value
+
+
+def ibm_create(grid, dom, re, bodies, opts, workspace_ptr=None, workspace_bytes=0):
+    h = ctypes.c_void_p()
+    _check(load().ibm_create(ctypes.byref(grid), ctypes.byref(dom), float(re), ctypes.byref(bodies),
+                             ctypes.byref(opts) if opts is not None else None,
+                             workspace_ptr, workspace_bytes, ctypes.byref(h)), "ibm_create")
+    return h
+
+
+def ibm_step(state, dt, nsteps):
+    return load().ibm_step(state, float(dt), int(nsteps))
+
+
+def ibm_sync(state):
+    _check(load().ibm_sync(state), "ibm_sync")
+
+
+def ibm_flag_state(state, X, V=None, F=None):
+    _check(load().ibm_flag_state(state, _ptr(X), _ptr(V), _ptr(F), X.size // 3), "ibm_flag_state")
+
+
+def ibm_stats(state) -> dict:
+    st = ibm_stats_t()
+    _check(load().ibm_stats(state, ctypes.byref(st)), "ibm_stats")
+    return st.as_dict()
+
+
+def ibm_get_field(state, which, out):
+    _check(load().ibm_get_field(state, which, _ptr(out), out.size), "ibm_get_field")
+
+
+def ibm_set_field(state, which, arr):
+    a = np.ascontiguousarray(arr, dtype=np.float64)
+    _check(load().ibm_set_field(state, which, _ptr(a), a.size), "ibm_set_field")
+
+
+def ibm_marker_count(state) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().ibm_marker_count(state, ctypes.byref(n)), "ibm_marker_count")
+    return n.value
+
+
+def ibm_get_markers(state, out):
+    _check(load().ibm_get_markers(state, _ptr(out), out.size // 3), "ibm_get_markers")
+
+
+def ibm_destroy(state):
+    load().ibm_destroy(state)
+
+
+# ----------------------------------------------------------------- convenience
+class Solver:
+    """One solver state on the current CUDA device.
+
+    The device workspace is a torch uint8 tensor (torch's caching allocator);
+    the stream is torch's current stream unless one is given.
+    """
+
+    def __init__(self, wl: Workload, precision: int = IBM_FP64, noise=None, stream=None,
+                 cfl: float | None = None, cfl_limit: float = 2.0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the solver needs a CUDA device")
+        load()
+        self.wl = wl
+        self.precision = precision
+        self.grid, self.dom, self.bodies = structs_from_workload(wl)
+        # a dedicated stream: CUDA graphs cannot be captured on the legacy default stream
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self._noise = [np.ascontiguousarray(a, dtype=np.float64) for a in noise] if noise else None
+        opts = ibm_options(precision, wl.cfl if cfl is None else cfl, cfl_limit,
+                           ctypes.c_void_p(self.stream.cuda_stream),
+                           *([_ptr(a) for a in self._noise] if self._noise else [None] * 3))
+        self.ws_bytes = ibm_workspace_bytes(self.grid, self.dom, self.bodies, opts)
+        self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self.state = ibm_create(self.grid, self.dom, wl.re, self.bodies, opts,
+                                ctypes.c_void_p(aligned), self.ws_bytes)
+        self.nf = wl.flag_ns * wl.flag_nt if wl.flag_on else 0
+
+    def step(self, nsteps=1, dt=None):
+        dt = self.wl.dt if dt is None else dt
+        rc = ibm_step(self.state, dt if dt is not None else -1.0, nsteps)
+        _check(rc, "ibm_step")
+
+    def field(self, which):
+        wl = self.wl
+        planes = wl.nx if which == IBM_FIELD_P else wl.nx + 1
+        out = np.empty((planes, wl.ny, wl.nz))
+        ibm_get_field(self.state, which, out)
+        return out
+
+    def fields(self):
+        return tuple(self.field(q) for q in (IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P))
+
+    def flag(self):
+        X = np.empty((self.nf, 3))
+        V = np.empty((self.nf, 3))
+        F = np.empty((self.nf, 3))
+        ibm_flag_state(self.state, X, V, F)
+        return X, V, F
+
+    def markers(self):
+        n = ibm_marker_count(self.state)
+        X = np.empty((n, 3))
+        ibm_get_markers(self.state, X)
+        return X
+
+    def stats(self):
+        return ibm_stats(self.state)
+
+    def close(self):
+        if getattr(self, "state", None) is not None:
+            ibm_destroy(self.state)
+            self.state = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,766 @@
+// C ABI of the solver (declared in include/ibm.h): argument checks, host-side
+// geometry of the immersed bodies (Sec. II.A), device workspace layout, the
+// initial projection, and one captured CUDA graph per velocity buffer parity
+// for the time step of Sec. II.B.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <tuple>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/ibm.h"
+#include "solver.h"
+
+using namespace ibm;
+
+namespace {
+
+bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// ------------------------------------------------------------------ geometry
+struct FlagGeom {
+  int ns = 0, nt = 0;
+  std::vector<double> X, inv_mass, dv;
+  std::vector<int> spring;
+  std::vector<double> l0;
+  std::vector<int> hinge;
+  std::vector<double> k_hinge;
+  std::vector<int> csr_off, csr_idx;
+  double omega_max = 0.0;
+};
+
+// Flag lattice (Sec. II.A): sheet of flag_len x flag_span, leading edge at
+// x = flag_x_le, centred in y and z, pitched by pitch0 about the z axis.
+// Springs on lattice edges and both diagonals; bending hinges on every edge
+// shared by two triangles of one of the two triangulations (cells split along
+// either diagonal), stiffness beta |e|^2 / A on lattice edges and
+// 2 beta A / |e|^2 on diagonals, each triangulation weighted 1/2.
+FlagGeom build_flag(const ibm_bodies& b, const ibm_domain& d, double h) {
+  FlagGeom g;
+  const int ns = b.flag_ns, nt = b.flag_nt;
+  g.ns = ns;
+  g.nt = nt;
+  const int nv = ns * nt;
+  const double ds = b.flag_len / (ns - 1), dtt = b.flag_span / (nt - 1);
+  const double yc = 0.5 * d.ly, zc = 0.5 * d.lz;
+  auto vid = [nt](int a, int c) { return a * nt + c; };
+  g.X.resize(3 * nv);
+  for (int a = 0; a < ns; ++a)
+    for (int c = 0; c < nt; ++c) {
+      const int v = vid(a, c);
+      g.X[3 * v] = b.flag_x_le + a * ds * std::cos(b.pitch0);
+      g.X[3 * v + 1] = yc + a * ds * std::sin(b.pitch0);
+      g.X[3 * v + 2] = zc - 0.5 * b.flag_span + c * dtt;
+    }
+  // lumped areas: a quarter of every adjacent cell
+  std::vector<double> area(nv, 0.0);
+  for (int a = 0; a + 1 < ns; ++a)
+    for (int c = 0; c + 1 < nt; ++c) {
+      const double q = 0.25 * ds * dtt;
+      area[vid(a, c)] += q;
+      area[vid(a + 1, c)] += q;
+      area[vid(a, c + 1)] += q;
+      area[vid(a + 1, c + 1)] += q;
+    }
+  g.inv_mass.resize(nv);
+  g.dv.resize(nv);
+  for (int v = 0; v < nv; ++v) {
+    const bool pinned = v < nt;  // a = 0: the hinged leading edge
+    g.inv_mass[v] = pinned ? 0.0 : 1.0 / (b.mass_ratio * area[v]);
+    g.dv[v] = area[v] * h;
+  }
+  // springs
+  auto add_spring = [&](int p, int q) {
+    g.spring.push_back(p);
+    g.spring.push_back(q);
+    double s = 0.0;
+    for (int e = 0; e < 3; ++e) {
+      const double dd = g.X[3 * q + e] - g.X[3 * p + e];
+      s += dd * dd;
+    }
+    g.l0.push_back(std::sqrt(s));
+  };
+  for (int a = 0; a < ns; ++a)
+    for (int c = 0; c < nt; ++c) {
+      if (a + 1 < ns) add_spring(vid(a, c), vid(a + 1, c));
+      if (c + 1 < nt) add_spring(vid(a, c), vid(a, c + 1));
+    }
+  for (int a = 0; a + 1 < ns; ++a)
+    for (int c = 0; c + 1 < nt; ++c) {
+      add_spring(vid(a, c), vid(a + 1, c + 1));
+      add_spring(vid(a + 1, c), vid(a, c + 1));
+    }
+  // two triangulations, triangles counter-clockwise in the (s, t) plane
+  std::vector<std::array<int, 3>> tris;
+  std::vector<int> kind;
+  for (int split = 0; split < 2; ++split)
+    for (int a = 0; a + 1 < ns; ++a)
+      for (int c = 0; c + 1 < nt; ++c) {
+        const int v00 = vid(a, c), v10 = vid(a + 1, c), v01 = vid(a, c + 1), v11 = vid(a + 1, c + 1);
+        if (split == 0) {
+          tris.push_back({v00, v10, v11});
+          tris.push_back({v00, v11, v01});
+        } else {
+          tris.push_back({v00, v10, v01});
+          tris.push_back({v10, v11, v01});
+        }
+        kind.push_back(split);
+        kind.push_back(split);
+      }
+  std::map<std::tuple<int, int, int>, std::vector<int>> edges;
+  for (int t = 0; t < (int)tris.size(); ++t)
+    for (int e = 0; e < 3; ++e) {
+      const int p = tris[t][e], q = tris[t][(e + 1) % 3];
+      edges[std::make_tuple(kind[t], std::min(p, q), std::max(p, q))].push_back(t);
+    }
+  const double cell = ds * dtt;
+  for (auto& kv : edges) {
+    if (kv.second.size() != 2) continue;
+    const int ta = kv.second[0], tb = kv.second[1];
+    for (int e = 0; e < 3; ++e) g.hinge.push_back(tris[ta][e]);
+    for (int e = 0; e < 3; ++e) g.hinge.push_back(tris[tb][e]);
+    const int p = std::get<1>(kv.first), q = std::get<2>(kv.first);
+    const int ap = p / nt, cp = p % nt, aq = q / nt, cq = q % nt;
+    const double es = (aq - ap) * ds, et = (cq - cp) * dtt;
+    const double e2 = es * es + et * et;
+    const bool diag = (aq != ap) && (cq != cp);
+    g.k_hinge.push_back(0.5 * (diag ? 2.0 * b.bending * cell / e2 : b.bending * e2 / cell));
+  }
+  // per-vertex slot lists (springs: 2 slots, hinges: 6 slots), fixed order
+  const int nsp = (int)g.l0.size(), nh = (int)g.k_hinge.size();
+  std::vector<std::vector<int>> lists(nv);
+  for (int q = 0; q < nsp; ++q) {
+    lists[g.spring[2 * q]].push_back(2 * q);
+    lists[g.spring[2 * q + 1]].push_back(2 * q + 1);
+  }
+  for (int q = 0; q < nh; ++q)
+    for (int e = 0; e < 6; ++e) lists[g.hinge[6 * q + e]].push_back(2 * nsp + 6 * q + e);
+  g.csr_off.assign(nv + 1, 0);
+  for (int v = 0; v < nv; ++v) {
+    g.csr_off[v + 1] = g.csr_off[v] + (int)lists[v].size();
+    for (int s : lists[v]) g.csr_idx.push_back(s);
+  }
+  // Gershgorin bound of the stiffness / mass spectrum (linearised, flat):
+  // (2 k_s n_springs(v) + 8 sum_hinges_at_v k_e / l_min^2) / m_v, free vertices
+  std::vector<double> nspr(nv, 0.0), khs(nv, 0.0);
+  for (int q = 0; q < nsp; ++q) {
+    nspr[g.spring[2 * q]] += 1.0;
+    nspr[g.spring[2 * q + 1]] += 1.0;
+  }
+  for (int q = 0; q < nh; ++q) {
+    int vs[6];
+    for (int e = 0; e < 6; ++e) vs[e] = g.hinge[6 * q + e];
+    std::sort(vs, vs + 6);
+    const int* end = std::unique(vs, vs + 6);
+    for (const int* p = vs; p != end; ++p) khs[*p] += g.k_hinge[q];
+  }
+  const double lmin = std::min(ds, dtt);
+  double w2 = 0.0;
+  for (int v = nt; v < nv; ++v) {
+    const double m = b.mass_ratio * area[v];
+    w2 = std::max(w2, (2.0 * b.stretch * nspr[v] + 8.0 * khs[v] / (lmin * lmin)) / m);
+  }
+  g.omega_max = std::sqrt(w2);
+  return g;
+}
+
+// Bar-grid markers (Sec. II.A passive grid): rods along y centred at
+// z = (r + 1/2) M and rods along z centred at y = (r + 1/2) M in the plane
+// x = bar_x, each filled with n_w = ceil(d / h) + 1 points across both short
+// sides and ceil(L / h) points along, at (m + 1/2) L / n. Points of rods along y
+// inside a rod along z are dropped (crossings counted once). Each marker
+// carries volume (union of the bars) / count.
+void build_bars(const ibm_bodies& b, const ibm_domain& d, double h, std::vector<double>& X,
+                double& dv) {
+  const double dw = b.bar_width, M = b.bar_mesh;
+  const int nry = (int)std::lround(d.ly / M), nrz = (int)std::lround(d.lz / M);
+  const int nw = (int)std::ceil(dw / h - 1e-12) + 1;
+  const int nay = (int)std::ceil(d.ly / h - 1e-12), naz = (int)std::ceil(d.lz / h - 1e-12);
+  std::vector<double> across(nw);
+  for (int q = 0; q < nw; ++q) across[q] = dw * ((double)q / (nw - 1) - 0.5);
+  X.clear();
+  for (int r = 0; r < nrz; ++r) {          // rods along y, centred in z
+    const double z0 = (r + 0.5) * M;
+    for (int qx = 0; qx < nw; ++qx)
+      for (int qz = 0; qz < nw; ++qz)
+        for (int m = 0; m < nay; ++m) {
+          const double y = (m + 0.5) * d.ly / nay;
+          bool inside = false;
+          for (int s = 0; s < nry; ++s) {
+            double dy = std::fabs(y - (s + 0.5) * M);
+            dy = std::min(dy, d.ly - dy);
+            if (dy <= 0.5 * dw + 1e-12) inside = true;
+          }
+          if (inside) continue;
+          X.push_back(b.bar_x + across[qx]);
+          X.push_back(y);
+          X.push_back(z0 + across[qz]);
+        }
+  }
+  for (int r = 0; r < nry; ++r) {          // rods along z, centred in y
+    const double y0 = (r + 0.5) * M;
+    for (int qx = 0; qx < nw; ++qx)
+      for (int qy = 0; qy < nw; ++qy)
+        for (int m = 0; m < naz; ++m) {
+          X.push_back(b.bar_x + across[qx]);
+          X.push_back(y0 + across[qy]);
+          X.push_back((m + 0.5) * d.lz / naz);
+        }
+  }
+  const double vol = dw * dw * (nry * d.lz + nrz * d.ly) - (double)nry * nrz * dw * dw * dw;
+  const size_t n = X.size() / 3;
+  dv = n ? vol / (double)n : 0.0;
+}
+
+// ------------------------------------------------------------------ workspace
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <class P>
+  P* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    P* p = base ? reinterpret_cast<P*>(base + off) : nullptr;
+    off += count * sizeof(P);
+    return p;
+  }
+};
+
+struct Layout {
+  int nf = 0, nb = 0, nsp = 0, nh = 0, nslot = 0, ncsr = 0;
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ state
+struct ibm_state {
+  int precision = IBM_FP64;
+  Consts c{};
+  ibm_grid grid{};
+  ibm_domain dom{};
+  ibm_bodies bodies{};
+  double cfl = 0.3, cfl_limit = 2.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  int cur = 0;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  Fields<double> fd{};
+  Fields<float> ff{};
+  Markers mk{};
+  Flag fl{};
+  Params* prm = nullptr;
+  double* dstat = nullptr;    // 16 doubles of device scratch for diagnostics
+  Params* hprm = nullptr;     // pinned copy
+  double last_dt_fixed = -2.0;
+};
+
+namespace {
+
+int check_args(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const ibm_options* o) {
+  if (!g || !d || !b) return IBM_EINVAL;
+  if (g->nx < 4 || !is_pow2(g->ny) || !is_pow2(g->nz) || g->ny < 4 || g->nz < 4 || g->ny > 1024 ||
+      g->nz > 1024 || g->nx > 65536)
+    return IBM_EINVAL;
+  if (!(d->lx > 0) || !(d->ly > 0) || !(d->lz > 0)) return IBM_EINVAL;
+  const double h = d->lx / g->nx;
+  if (std::fabs(d->ly / g->ny - h) > 1e-9 * h || std::fabs(d->lz / g->nz - h) > 1e-9 * h)
+    return IBM_EINVAL;
+  if (b->bars_on) {
+    if (!(b->bar_mesh > 0) || !(b->bar_width > 0) || b->bar_width >= b->bar_mesh) return IBM_EINVAL;
+    const double ry = d->ly / b->bar_mesh, rz = d->lz / b->bar_mesh;
+    if (std::fabs(ry - std::round(ry)) > 1e-9 || std::fabs(rz - std::round(rz)) > 1e-9) return IBM_EINVAL;
+    if (b->bar_x - 0.5 * b->bar_width < 2 * h || b->bar_x + 0.5 * b->bar_width > d->lx - 2 * h)
+      return IBM_EINVAL;
+  }
+  if (b->flag_on) {
+    if (b->flag_ns < 2 || b->flag_nt < 2 || b->flag_ns * b->flag_nt > (1 << 20)) return IBM_EINVAL;
+    if (!(b->flag_len > 0) || !(b->flag_span > 0) || !(b->mass_ratio > 0) || !(b->bending >= 0) ||
+        !(b->stretch > 0))
+      return IBM_EINVAL;
+    if (b->flag_x_le < 2 * h || b->flag_x_le + b->flag_len > d->lx - 2 * h) return IBM_EINVAL;
+  }
+  if (o) {
+    if (o->precision != IBM_FP64 && o->precision != IBM_FP32) return IBM_EINVAL;
+    if (o->cfl < 0 || o->cfl_limit < 0) return IBM_EINVAL;
+  }
+  return IBM_OK;
+}
+
+template <class T>
+size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
+  Carver cv(base);
+  const Consts& c = s->c;
+  const size_t NF = (size_t)(c.nx + 1) * c.ny * c.nz, NP = (size_t)c.nx * c.ny * c.nz;
+  const size_t P = (size_t)c.ny * c.nz;
+  for (int b = 0; b < 2; ++b) {
+    f.u[b] = cv.take<T>(NF);
+    f.v[b] = cv.take<T>(NF);
+    f.w[b] = cv.take<T>(NF);
+  }
+  for (int q = 0; q < 3; ++q) f.n[q] = cv.take<T>(NF);
+  for (int q = 0; q < 3; ++q) f.d[q] = cv.take<T>(NF);
+  f.p = cv.take<T>(NP);
+  f.phi = cv.take<T>(NP);
+  f.ptab = cv.take<T>(NP);
+  for (int q = 0; q < 3; ++q) f.dout[q] = cv.take<T>(P);
+  f.tw_y = cv.take<T>(c.ny);
+  f.tw_z = cv.take<T>(c.nz);
+  f.n_partial = partial_count(c);
+  f.partial = cv.take<double>(f.n_partial);
+  f.prm = cv.take<Params>(1);
+  s->dstat = cv.take<double>(16);
+  Markers& m = s->mk;
+  m.nf = L.nf;
+  m.nb = L.nb;
+  m.nm = L.nf + L.nb;
+  m.Xb = cv.take<double>(3 * (size_t)L.nb);
+  m.coef = cv.take<double>(3 * (size_t)m.nm);
+  Flag& fl = s->fl;
+  fl.nv = L.nf;
+  fl.X = cv.take<double>(3 * (size_t)L.nf);
+  fl.V = cv.take<double>(3 * (size_t)L.nf);
+  fl.A = cv.take<double>(3 * (size_t)L.nf);
+  fl.Ff = cv.take<double>(3 * (size_t)L.nf);
+  fl.inv_mass = cv.take<double>(L.nf);
+  fl.dv = cv.take<double>(L.nf);
+  fl.n_spring = L.nsp;
+  fl.spring = cv.take<int>(2 * (size_t)L.nsp);
+  fl.l0 = cv.take<double>(L.nsp);
+  fl.n_hinge = L.nh;
+  fl.hinge = cv.take<int>(6 * (size_t)L.nh);
+  fl.k_hinge = cv.take<double>(L.nh);
+  fl.slot = cv.take<double>(3 * (size_t)L.nslot);
+  fl.csr_off = cv.take<int>(L.nf + 1);
+  fl.csr_idx = cv.take<int>(L.ncsr);
+  s->prm = f.prm;
+  return cv.off + 256;
+}
+
+#define CK(x)                          \
+  do {                                 \
+    cudaError_t e_ = (x);              \
+    if (e_ != cudaSuccess) {           \
+      cudaGetLastError();              \
+      return IBM_ECUDA;                \
+    }                                  \
+  } while (0)
+
+template <class T>
+Fields<T>& fields(ibm_state* s);
+template <>
+Fields<double>& fields<double>(ibm_state* s) { return s->fd; }
+template <>
+Fields<float>& fields<float>(ibm_state* s) { return s->ff; }
+
+template <class T>
+int upload_field(cudaStream_t st, T* dst, const double* src, size_t n) {
+  if (std::is_same<T, double>::value) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    std::vector<T> tmp(n);
+    for (size_t i = 0; i < n; ++i) tmp[i] = (T)src[i];
+    CK(cudaMemcpyAsync(dst, tmp.data(), n * sizeof(T), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  return IBM_OK;
+}
+
+template <class T>
+int download_field(cudaStream_t st, double* dst, const T* src, size_t n) {
+  if (std::is_same<T, double>::value) {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  } else {
+    std::vector<T> tmp(n);
+    CK(cudaMemcpyAsync(tmp.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < n; ++i) dst[i] = (double)tmp[i];
+  }
+  return IBM_OK;
+}
+
+template <class T>
+void record_step(ibm_state* s, int cur) {
+  Fields<T>& f = fields<T>(s);
+  const Consts& c = s->c;
+  cudaStream_t st = s->stream;
+  launch_begin_step(c, f, st);
+  launch_rhs(c, f, cur, st);
+  launch_outflow(c, f, cur, st);
+  launch_af(c, f, cur, st);
+  launch_ib(c, f, s->mk, s->fl, cur, st);
+  launch_flag(c, f.prm, s->fl, st);
+  launch_mass_div(c, f, cur, false, st);
+  launch_poisson(c, f, st);
+  launch_project(c, f, cur, false, st);
+}
+
+template <class T>
+int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
+               const std::vector<double>& Xb, double bar_dv) {
+  Fields<T>& f = fields<T>(s);
+  const Consts& c = s->c;
+  cudaStream_t st = s->stream;
+  const size_t NF = (size_t)(c.nx + 1) * c.ny * c.nz, NP = (size_t)c.nx * c.ny * c.nz;
+  CK(cudaMemsetAsync(s->ws, 0, s->ws_bytes, st));
+  // velocity: u = U + init_u, v = init_v, w = init_w
+  {
+    std::vector<double> buf(NF);
+    for (int comp = 0; comp < 3; ++comp) {
+      const double* src = o ? (comp == 0 ? o->init_u : comp == 1 ? o->init_v : o->init_w) : nullptr;
+      for (size_t e = 0; e < NF; ++e) buf[e] = (comp == 0 ? c.u_in : 0.0) + (src ? src[e] : 0.0);
+      T* dst = comp == 0 ? f.u[0] : comp == 1 ? f.v[0] : f.w[0];
+      int rc = upload_field<T>(st, dst, buf.data(), NF);
+      if (rc) return rc;
+    }
+  }
+  // twiddles exp(-2 pi i t / N)
+  for (int dir = 0; dir < 2; ++dir) {
+    const int n = dir == 0 ? c.ny : c.nz;
+    std::vector<double> tw(n);
+    for (int t = 0; t < n / 2; ++t) {
+      tw[2 * t] = std::cos(2.0 * M_PI * t / n);
+      tw[2 * t + 1] = -std::sin(2.0 * M_PI * t / n);
+    }
+    int rc = upload_field<T>(st, dir == 0 ? f.tw_y : f.tw_z, tw.data(), n);
+    if (rc) return rc;
+  }
+  // markers and flag
+  Markers& m = s->mk;
+  m.bar_dv = bar_dv;
+  if (m.nb) CK(cudaMemcpyAsync(m.Xb, Xb.data(), Xb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  Flag& fl = s->fl;
+  if (fl.nv) {
+    fl.ns = fg.ns;
+    fl.nt = fg.nt;
+    fl.k_s = s->bodies.stretch;
+    auto up = [&](void* dst, const void* src, size_t bytes) {
+      return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    CK(up(fl.X, fg.X.data(), fg.X.size() * sizeof(double)));
+    CK(up(fl.inv_mass, fg.inv_mass.data(), fg.inv_mass.size() * sizeof(double)));
+    CK(up(fl.dv, fg.dv.data(), fg.dv.size() * sizeof(double)));
+    CK(up(fl.spring, fg.spring.data(), fg.spring.size() * sizeof(int)));
+    CK(up(fl.l0, fg.l0.data(), fg.l0.size() * sizeof(double)));
+    CK(up(fl.hinge, fg.hinge.data(), fg.hinge.size() * sizeof(int)));
+    CK(up(fl.k_hinge, fg.k_hinge.data(), fg.k_hinge.size() * sizeof(double)));
+    CK(up(fl.csr_off, fg.csr_off.data(), fg.csr_off.size() * sizeof(int)));
+    CK(up(fl.csr_idx, fg.csr_idx.data(), fg.csr_idx.size() * sizeof(int)));
+    // enough CTAs for the hinge work, within the cluster limit
+    const int want = std::min((fl.n_hinge + fl.n_spring + 4095) / 4096, flag_max_cluster());
+    fl.cluster = 1;
+    while (2 * fl.cluster <= want) fl.cluster *= 2;
+  }
+  // parameters
+  Params p{};
+  p.first = 1;
+  p.dt_fixed = -1.0;
+  p.cfl = s->cfl;
+  CK(cudaMemcpyAsync(f.prm, &p, sizeof(Params), cudaMemcpyHostToDevice, st));
+  poisson_set_attributes();
+  fluid_set_attributes();
+  launch_poisson_table(c, f, st);
+  // initial projection of u0 (dt absorbed in phi), velocity only
+  s->cur = 0;
+  launch_mass_div(c, f, 0, true, st);
+  launch_poisson(c, f, st);
+  launch_project(c, f, 0, true, st);
+  s->cur = 1;
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  (void)NP;
+  // capture one step per buffer parity
+  for (int par = 0; par < 2; ++par) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    record_step<T>(s, par);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return IBM_ECUDA;
+    }
+    e = cudaGraphInstantiate(&s->exec[par], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return IBM_ECUDA;
+    }
+  }
+  return IBM_OK;
+}
+
+int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const ibm_options* o,
+            ibm_state* s, FlagGeom& fg, std::vector<double>& Xb, double& bar_dv, Layout& L) {
+  int rc = check_args(g, d, b, o);
+  if (rc) return rc;
+  s->grid = *g;
+  s->dom = *d;
+  s->bodies = *b;
+  s->precision = o ? o->precision : IBM_FP64;
+  s->cfl = (o && o->cfl > 0) ? o->cfl : 0.3;
+  s->cfl_limit = (o && o->cfl_limit > 0) ? o->cfl_limit : 2.0;
+  Consts& c = s->c;
+  c.nx = g->nx;
+  c.ny = g->ny;
+  c.nz = g->nz;
+  c.h = d->lx / g->nx;
+  c.inv_h = 1.0 / c.h;
+  c.lx = d->lx;
+  c.ly = d->ly;
+  c.lz = d->lz;
+  c.u_in = 1.0;
+  bar_dv = 0.0;
+  if (b->flag_on) fg = build_flag(*b, *d, c.h);
+  if (b->bars_on) build_bars(*b, *d, c.h, Xb, bar_dv);
+  c.omega_max = fg.omega_max;
+  L.nf = b->flag_on ? b->flag_ns * b->flag_nt : 0;
+  L.nb = (int)(Xb.size() / 3);
+  L.nsp = (int)fg.l0.size();
+  L.nh = (int)fg.k_hinge.size();
+  L.nslot = 2 * L.nsp + 6 * L.nh;
+  L.ncsr = (int)fg.csr_idx.size();
+  return IBM_OK;
+}
+
+template <class T>
+int step_impl(ibm_state* s, double dt, int nsteps) {
+  Fields<T>& f = fields<T>(s);
+  cudaStream_t st = s->stream;
+  const double mode = dt > 0 ? dt : -1.0;
+  if (mode != s->last_dt_fixed) {
+    // dt_fixed and cfl are adjacent members of Params
+    double two[2] = {mode, s->cfl};
+    CK(cudaMemcpyAsync(&f.prm->dt_fixed, two, sizeof(two), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    s->last_dt_fixed = mode;
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    CK(cudaGraphLaunch(s->exec[s->cur], st));
+    s->cur ^= 1;
+  }
+  CK(cudaMemcpyAsync(s->hprm, f.prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const Params& p = *s->hprm;
+  if (p.error) return IBM_EDIVERGED;
+  if (nsteps > 0 && p.dt * p.speed_max / s->c.h > s->cfl_limit) return IBM_EDIVERGED;
+  return IBM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* ibm_strerror(int code) {
+  switch (code) {
+    case IBM_OK: return "ok";
+    case IBM_EINVAL: return "invalid argument";
+    case IBM_ENOMEM: return "device workspace missing, too small or not allocatable";
+    case IBM_ECUDA: return "CUDA runtime error";
+    case IBM_EDIVERGED: return "solution diverged (non-finite velocity or CFL above limit)";
+    case IBM_ETIMEOUT: return "bounded device wait ran out";
+    case IBM_EIO: return "checkpoint I/O error";
+    default: return "unknown status";
+  }
+}
+
+int ibm_workspace_bytes(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b,
+                        const ibm_options* o, size_t* bytes) {
+  if (!bytes) return IBM_EINVAL;
+  ibm_state tmp;
+  FlagGeom fg;
+  std::vector<double> Xb;
+  double bdv;
+  Layout L;
+  int rc = prepare(g, d, b, o, &tmp, fg, Xb, bdv, L);
+  if (rc) return rc;
+  *bytes = tmp.precision == IBM_FP64 ? carve<double>(&tmp, nullptr, L, tmp.fd)
+                                     : carve<float>(&tmp, nullptr, L, tmp.ff);
+  return IBM_OK;
+}
+
+int ibm_create(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodies* b,
+               const ibm_options* o, void* workspace, size_t workspace_bytes, ibm_state** out) {
+  if (!out || !(re > 0)) return IBM_EINVAL;
+  *out = nullptr;
+  std::unique_ptr<ibm_state> s(new (std::nothrow) ibm_state());
+  if (!s) return IBM_ENOMEM;
+  FlagGeom fg;
+  std::vector<double> Xb;
+  double bdv = 0;
+  Layout L;
+  int rc = prepare(g, d, b, o, s.get(), fg, Xb, bdv, L);
+  if (rc) return rc;
+  s->c.nu = 1.0 / re;
+  const size_t need = s->precision == IBM_FP64 ? carve<double>(s.get(), nullptr, L, s->fd)
+                                               : carve<float>(s.get(), nullptr, L, s->ff);
+  if (workspace) {
+    if (workspace_bytes < need || ((uintptr_t)workspace & 255)) return IBM_ENOMEM;
+    s->ws = workspace;
+    s->own_ws = false;
+  } else {
+    if (cudaMalloc(&s->ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return IBM_ENOMEM;
+    }
+    s->own_ws = true;
+  }
+  s->ws_bytes = need;
+  if (s->precision == IBM_FP64) carve<double>(s.get(), s->ws, L, s->fd);
+  else carve<float>(s.get(), s->ws, L, s->ff);
+  if (o && o->stream) {
+    s->stream = (cudaStream_t)o->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      if (s->own_ws) cudaFree(s->ws);
+      return IBM_ECUDA;
+    }
+    s->own_stream = true;
+  }
+  if (cudaMallocHost(&s->hprm, sizeof(Params)) != cudaSuccess) {
+    cudaGetLastError();
+    ibm_destroy(s.release());
+    return IBM_ECUDA;
+  }
+  rc = s->precision == IBM_FP64 ? init_state<double>(s.get(), o, fg, Xb, bdv)
+                                : init_state<float>(s.get(), o, fg, Xb, bdv);
+  if (rc) {
+    ibm_destroy(s.release());
+    return rc;
+  }
+  *out = s.release();
+  return IBM_OK;
+}
+
+int ibm_step(ibm_state* s, double dt, int nsteps) {
+  if (!s || nsteps < 0) return IBM_EINVAL;
+  return s->precision == IBM_FP64 ? step_impl<double>(s, dt, nsteps) : step_impl<float>(s, dt, nsteps);
+}
+
+int ibm_sync(ibm_state* s) {
+  if (!s) return IBM_EINVAL;
+  CK(cudaStreamSynchronize(s->stream));
+  return IBM_OK;
+}
+
+int ibm_flag_state(ibm_state* s, double* X, double* V, double* F, size_t n) {
+  if (!s || !X) return IBM_EINVAL;
+  if (n != (size_t)s->fl.nv || n == 0) return IBM_EINVAL;
+  cudaStream_t st = s->stream;
+  CK(cudaMemcpyAsync(X, s->fl.X, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (V) CK(cudaMemcpyAsync(V, s->fl.V, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (F) CK(cudaMemcpyAsync(F, s->fl.Ff, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return IBM_OK;
+}
+
+int ibm_stats(ibm_state* s, ibm_stats_t* out) {
+  if (!s || !out) return IBM_EINVAL;
+  cudaStream_t st = s->stream;
+  CK(cudaMemsetAsync(s->dstat, 0, 16 * sizeof(double), st));
+  if (s->precision == IBM_FP64) launch_stats<double>(s->c, s->fd, s->cur, s->dstat, st);
+  else launch_stats<float>(s->c, s->ff, s->cur, s->dstat, st);
+  launch_flag_stats(s->fl, s->dstat + 4, st);
+  CK(cudaGetLastError());
+  double h[16];
+  CK(cudaMemcpyAsync(h, s->dstat, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(s->hprm, s->prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const Params& p = *s->hprm;
+  std::memset(out, 0, sizeof(*out));
+  out->step = p.step;
+  out->t = p.t;
+  out->dt = p.dt;
+  out->cfl = p.dt * p.speed_max / s->c.h;
+  out->ke = h[0];
+  out->max_div = h[1];
+  out->q_in = p.q_in;
+  out->q_out = p.q_out;
+  out->ib_slip = p.slip_max;
+  if (s->fl.nv) {
+    for (int e = 0; e < 3; ++e) {
+      out->te_mid[e] = h[4 + e];
+      out->force[e] = h[7 + e];
+    }
+    out->max_strain = h[10];
+  }
+  out->n_sub = p.n_sub;
+  out->n_markers = s->mk.nm;
+  return IBM_OK;
+}
+
+static int field_ptr(ibm_state* s, int which, void** ptr, size_t* n) {
+  const Consts& c = s->c;
+  const size_t NF = (size_t)(c.nx + 1) * c.ny * c.nz, NP = (size_t)c.nx * c.ny * c.nz;
+  const bool d = s->precision == IBM_FP64;
+  switch (which) {
+    case IBM_FIELD_U: *ptr = d ? (void*)s->fd.u[s->cur] : (void*)s->ff.u[s->cur]; *n = NF; break;
+    case IBM_FIELD_V: *ptr = d ? (void*)s->fd.v[s->cur] : (void*)s->ff.v[s->cur]; *n = NF; break;
+    case IBM_FIELD_W: *ptr = d ? (void*)s->fd.w[s->cur] : (void*)s->ff.w[s->cur]; *n = NF; break;
+    case IBM_FIELD_P: *ptr = d ? (void*)s->fd.p : (void*)s->ff.p; *n = NP; break;
+    default: return IBM_EINVAL;
+  }
+  return IBM_OK;
+}
+
+int ibm_get_field(ibm_state* s, int which, double* host, size_t n) {
+  if (!s || !host) return IBM_EINVAL;
+  void* ptr;
+  size_t cnt;
+  if (field_ptr(s, which, &ptr, &cnt) || cnt != n) return IBM_EINVAL;
+  if (s->precision == IBM_FP64) return download_field<double>(s->stream, host, (double*)ptr, n);
+  return download_field<float>(s->stream, host, (float*)ptr, n);
+}
+
+int ibm_set_field(ibm_state* s, int which, const double* host, size_t n) {
+  if (!s || !host) return IBM_EINVAL;
+  void* ptr;
+  size_t cnt;
+  if (field_ptr(s, which, &ptr, &cnt) || cnt != n) return IBM_EINVAL;
+  if (s->precision == IBM_FP64) return upload_field<double>(s->stream, (double*)ptr, host, n);
+  return upload_field<float>(s->stream, (float*)ptr, host, n);
+}
+
+int ibm_marker_count(const ibm_state* s, size_t* n) {
+  if (!s || !n) return IBM_EINVAL;
+  *n = (size_t)s->mk.nm;
+  return IBM_OK;
+}
+
+int ibm_get_markers(ibm_state* s, double* X, size_t n) {
+  if (!s || !X || n != (size_t)s->mk.nm) return IBM_EINVAL;
+  cudaStream_t st = s->stream;
+  if (s->mk.nf) CK(cudaMemcpyAsync(X, s->fl.X, 3 * (size_t)s->mk.nf * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (s->mk.nb)
+    CK(cudaMemcpyAsync(X + 3 * (size_t)s->mk.nf, s->mk.Xb, 3 * (size_t)s->mk.nb * sizeof(double),
+                       cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return IBM_OK;
+}
+
+void ibm_destroy(ibm_state* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (int q = 0; q < 2; ++q)
+    if (s->exec[q]) cudaGraphExecDestroy(s->exec[q]);
+  if (s->own_ws && s->ws) cudaFree(s->ws);
+  if (s->hprm) cudaFreeHost(s->hprm);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  cudaGetLastError();
+  delete s;
+}
+
+}  // extern "C"

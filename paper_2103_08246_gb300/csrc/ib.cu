@@ -1,0 +1,169 @@
+// Immersed-boundary direct forcing (Sec. II.B): interpolation of the
+// provisional velocity at every marker (a gather over the 3 x 3 x 3 nodes of
+// each staggered lattice in the support of the three-point kernel of Roma,
+// Peskin and Berger), the direct-forcing amplitude
+//   coef_l = dV_l / h^3 (U_l - U*_l)   (= dt F_l dV_l / h^3),
+// the fluid force on each flag vertex -F_l dV_l, and spreading of coef_l
+// with the same weights (atomic scatter).
+//
+// Markers 0 .. nf-1 are the flag vertices (target velocity V_l, position X_l
+// from the structure), the rest the bar-grid markers (target 0). Nodes
+// outside the unknowns along x are skipped (u faces 0 and nx, the v/w ghost
+// plane); y and z wrap periodically. Non-finite positions are skipped, so a
+// diverged flag cannot produce an out-of-range access.
+#include <cmath>
+
+#include "solver.h"
+
+namespace ibm {
+
+template <class T>
+__device__ inline T roma_phi(T r) {
+  const T a = fabs(r);
+  if (a <= (T)0.5) return ((T)1 + sqrt((T)1 - (T)3 * a * a)) / (T)3;
+  if (a < (T)1.5) {
+    const T b = (T)1 - a;
+    return ((T)5 - (T)3 * a - sqrt(fmax((T)0, (T)1 - (T)3 * b * b))) / (T)6;
+  }
+  return (T)0;
+}
+
+struct Stencil {
+  int i0, j[3], k[3];
+  bool vi[3];
+};
+
+// 3-node stencil per direction of component `comp` for a marker at X
+template <class T>
+__device__ inline void stencil(const Consts& c, int comp, double X, double Y, double Z,
+                               Stencil& st, T wx[3], T wy[3], T wz[3]) {
+  const double ox = comp == 0 ? 0.0 : 0.5;
+  const double oy = comp == 1 ? 0.0 : 0.5;
+  const double oz = comp == 2 ? 0.0 : 0.5;
+  const double sx = X * c.inv_h - ox, sy = Y * c.inv_h - oy, sz = Z * c.inv_h - oz;
+  const int ix = (int)floor(sx - 0.5), iy = (int)floor(sy - 0.5), iz = (int)floor(sz - 0.5);
+  const int lo = comp == 0 ? 1 : 0, hi = c.nx - 1;
+  st.i0 = ix;
+  for (int t = 0; t < 3; ++t) {
+    wx[t] = roma_phi<T>((T)(ix + t - sx));
+    wy[t] = roma_phi<T>((T)(iy + t - sy));
+    wz[t] = roma_phi<T>((T)(iz + t - sz));
+    st.vi[t] = (ix + t >= lo) && (ix + t <= hi);
+    int jj = (iy + t) % c.ny;
+    if (jj < 0) jj += c.ny;
+    int kk = (iz + t) % c.nz;
+    if (kk < 0) kk += c.nz;
+    st.j[t] = jj;
+    st.k[t] = kk;
+  }
+}
+
+__device__ inline bool marker(const Markers& m, const Flag& fl, int l, double& X, double& Y,
+                              double& Z, double U[3], double& dv) {
+  if (l < m.nf) {
+    X = fl.X[3 * l];
+    Y = fl.X[3 * l + 1];
+    Z = fl.X[3 * l + 2];
+    U[0] = fl.V[3 * l];
+    U[1] = fl.V[3 * l + 1];
+    U[2] = fl.V[3 * l + 2];
+    dv = fl.dv[l];
+  } else {
+    const int b = l - m.nf;
+    X = m.Xb[3 * b];
+    Y = m.Xb[3 * b + 1];
+    Z = m.Xb[3 * b + 2];
+    U[0] = U[1] = U[2] = 0.0;
+    dv = m.bar_dv;
+  }
+  // finite and inside a generous box: otherwise skip
+  return isfinite(X) && isfinite(Y) && isfinite(Z) && fabs(X) < 1e6 && fabs(Y) < 1e6 &&
+         fabs(Z) < 1e6;
+}
+
+template <class T>
+__global__ void k_ib_interp(Consts c, Params* prm, Markers m, Flag fl, const T* __restrict__ u,
+                            const T* __restrict__ v, const T* __restrict__ w) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  double slip = 0.0;
+  if (l < m.nm) {
+    double X, Y, Z, U[3], dv;
+    const bool ok = marker(m, fl, l, X, Y, Z, U, dv);
+    double us[3] = {0.0, 0.0, 0.0};
+    if (ok) {
+      for (int comp = 0; comp < 3; ++comp) {
+        const T* q = comp == 0 ? u : (comp == 1 ? v : w);
+        Stencil st;
+        T wx[3], wy[3], wz[3];
+        stencil<T>(c, comp, X, Y, Z, st, wx, wy, wz);
+        T acc = 0;
+        for (int a = 0; a < 3; ++a) {
+          if (!st.vi[a]) continue;
+          const size_t pi = (size_t)(st.i0 + a) * c.ny;
+          for (int b = 0; b < 3; ++b) {
+            const size_t pj = (pi + st.j[b]) * c.nz;
+            const T wab = wx[a] * wy[b];
+            for (int e = 0; e < 3; ++e) acc += wab * wz[e] * q[pj + st.k[e]];
+          }
+        }
+        us[comp] = (double)acc;
+      }
+    }
+    const double vol = dv * c.inv_h * c.inv_h * c.inv_h;
+    const double dt = prm->dt;
+    for (int comp = 0; comp < 3; ++comp) {
+      const double du = ok ? (U[comp] - us[comp]) : 0.0;
+      m.coef[3 * l + comp] = vol * du;
+      if (l < m.nf) fl.Ff[3 * l + comp] = -du / dt * dv;
+      slip = fmax(slip, fabs(du));
+    }
+  }
+  slip = warp_max(slip);
+  if ((threadIdx.x & 31) == 0 && slip > 0.0) atomic_max_nonneg(&prm->slip_max, slip);
+}
+
+template <class T>
+__global__ void k_ib_spread(Consts c, Markers m, Flag fl, T* __restrict__ u, T* __restrict__ v,
+                            T* __restrict__ w) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= m.nm) return;
+  double X, Y, Z, U[3], dv;
+  if (!marker(m, fl, l, X, Y, Z, U, dv)) return;
+  for (int comp = 0; comp < 3; ++comp) {
+    const T cf = (T)m.coef[3 * l + comp];
+    if (cf == (T)0) continue;
+    T* q = comp == 0 ? u : (comp == 1 ? v : w);
+    Stencil st;
+    T wx[3], wy[3], wz[3];
+    stencil<T>(c, comp, X, Y, Z, st, wx, wy, wz);
+    for (int a = 0; a < 3; ++a) {
+      if (!st.vi[a] || wx[a] == (T)0) continue;
+      const size_t pi = (size_t)(st.i0 + a) * c.ny;
+      for (int b = 0; b < 3; ++b) {
+        const T wab = wx[a] * wy[b] * cf;
+        if (wab == (T)0) continue;
+        const size_t pj = (pi + st.j[b]) * c.nz;
+        for (int e = 0; e < 3; ++e) {
+          const T val = wab * wz[e];
+          if (val != (T)0) atomicAdd(&q[pj + st.k[e]], val);
+        }
+      }
+    }
+  }
+}
+
+template <class T>
+void launch_ib(const Consts& c, const Fields<T>& f, const Markers& m, const Flag& fl, int cur,
+               cudaStream_t s) {
+  if (m.nm == 0) return;
+  const int nb = (m.nm + 127) / 128;
+  k_ib_interp<T><<<nb, 128, 0, s>>>(c, f.prm, m, fl, f.u[cur], f.v[cur], f.w[cur]);
+  k_ib_spread<T><<<nb, 128, 0, s>>>(c, m, fl, f.u[cur], f.v[cur], f.w[cur]);
+}
+
+template void launch_ib<double>(const Consts&, const Fields<double>&, const Markers&, const Flag&,
+                                int, cudaStream_t);
+template void launch_ib<float>(const Consts&, const Fields<float>&, const Markers&, const Flag&,
+                               int, cudaStream_t);
+
+}  // namespace ibm

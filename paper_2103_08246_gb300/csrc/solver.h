@@ -1,0 +1,79 @@
+// Host-side view of the device data of one solver state, and the kernel
+// launchers each translation unit provides.
+#pragma once
+
+#include "common.cuh"
+
+namespace ibm {
+
+template <class T>
+struct Fields {
+  T* u[2]; T* v[2]; T* w[2];  // velocity, double-buffered across the projection
+  T* p;                       // pressure (nx * ny * nz)
+  T* n[3];                    // nonlinear term N^{n-1}, overwritten with N^n
+  T* d[3];                    // RHS, then the velocity increments
+  T* phi;                     // divergence -> transforms -> pressure correction
+  T* ptab;                    // Poisson Thomas inverse pivots per mode
+  T* dout[3];                 // outflow-plane increments (ny * nz each)
+  T* tw_y; T* tw_z;           // FFT twiddles exp(-2 pi i t / N), t < N/2 (re, im)
+  double* partial;            // per-block partial maxima of the CFL speed
+  int n_partial;
+  Params* prm;
+};
+
+struct Markers {
+  int nm = 0;                 // flag vertices + bar markers
+  int nf = 0;                 // flag vertices (markers 0 .. nf-1)
+  int nb = 0;                 // bar markers
+  double* Xb = nullptr;       // bar marker positions (3 per marker)
+  double bar_dv = 0.0;        // volume carried by each bar marker
+  double* coef = nullptr;     // 3 per marker: dV / h^3 * (U - U*)
+};
+
+struct Flag {
+  int ns = 0, nt = 0, nv = 0;
+  double* X = nullptr;        // positions (3 per vertex)
+  double* V = nullptr;        // velocities
+  double* A = nullptr;        // accelerations (velocity Verlet)
+  double* Ff = nullptr;       // fluid force on each vertex, -F_l dV_l
+  double* inv_mass = nullptr; // 1/m for free vertices, 0 for the hinged edge
+  double* dv = nullptr;       // marker volume of each vertex (area * h)
+  int n_spring = 0;
+  int* spring = nullptr;      // 2 vertex ids per spring
+  double* l0 = nullptr;       // rest lengths
+  double k_s = 0.0;
+  int n_hinge = 0;
+  int* hinge = nullptr;       // 6 vertex ids: triangle A (3), triangle B (3)
+  double* k_hinge = nullptr;
+  double* slot = nullptr;     // 3 doubles per force slot (2 per spring, 6 per hinge)
+  int* csr_off = nullptr;     // nv + 1 offsets into csr_idx
+  int* csr_idx = nullptr;     // slot ids contributing to each vertex
+  int cluster = 1;            // CTAs cooperating in the structure kernel
+};
+
+// ---- fluid.cu
+template <class T> void launch_begin_step(const Consts& c, const Fields<T>& f, cudaStream_t s);
+template <class T> void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> void launch_outflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> void launch_af(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
+template <class T> void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
+int partial_count(const Consts& c);
+void fluid_set_attributes();
+template <class T> void launch_stats(const Consts& c, const Fields<T>& f, int cur, double* out, cudaStream_t s);
+
+// ---- poisson.cu
+template <class T> void launch_poisson(const Consts& c, const Fields<T>& f, cudaStream_t s);
+template <class T> void launch_poisson_table(const Consts& c, const Fields<T>& f, cudaStream_t s);
+void poisson_set_attributes();
+
+// ---- ib.cu
+template <class T> void launch_ib(const Consts& c, const Fields<T>& f, const Markers& m,
+                                  const Flag& fl, int cur, cudaStream_t s);
+
+// ---- flag.cu
+void launch_flag(const Consts& c, Params* prm, const Flag& fl, cudaStream_t s);
+void launch_flag_stats(const Flag& fl, double* out, cudaStream_t s);
+int flag_max_cluster();
+
+}  // namespace ibm
