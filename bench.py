@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of the fractional-step IB solver at 512 x 256 x 256.
+
+One "step" is one full time step of the method (Sec. II.B order: RHS, three
+implicit factors, IB interpolation/spreading, flag sub-steps, mass fix,
+Poisson solve, projection) of the production workload: 512 x 256 x 256
+cells, domain 8 x 4 x 4, Re = 200, bar grid (mesh 0.5, width 0.1) at x = 0.5,
+65 x 65 flag hinged at x = 3, CFL 0.3, seeded synthetic initial noise.
+
+Output: one JSON line (rank 0). `value` is steps/s of the headline path
+(FP32 fields, FP64 flag and sums) summed over all ranks; each rank runs an
+independent replica (the path is not sharded). The FP64 path, the per-stage
+roofline of the dominant kernel, the end-to-end rate through the C ABI with
+host buffers, and the CPU oracle on a bounded sample are reported beside it.
+
+--impl reference times the CPU oracle (the reference arm of this repository)
+on the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fractional steps/s & Gcell-updates/s at 512x256x256, mixed vs FP64, % HBM peak"
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per launch, in units of one scalar field (one read or one
+# write of every cell), per stage; see the design doc for the derivation.
+FIELD_PASSES = {
+    "rhs": 13, "af_x": 6, "af_y": 6, "af_z": 9, "mass_div": 4,
+    "dht_y": 2, "dht_z": 2, "poisson_x": 3, "project": 9,
+}
+# launches of each stage per step
+PER_STEP = {"rhs": 1, "af_x": 1, "af_y": 1, "af_z": 1, "mass_div": 1, "dht_y": 2, "dht_z": 2,
+            "poisson_x": 1, "project": 1, "ib": 1, "flag": 1, "outflow": 1}
+SAMPLE_NX = 64   # x planes of the CPU sample (the inflow end of the workload)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="only run this many FP32 production steps (for ncu) and exit")
+    ap.add_argument("--profile-precision", choices=["fp32", "fp64"], default="fp32")
+    return ap.parse_args()
+
+
+def run_profile(args):
+    """Plain run for profilers: create the production state and step it."""
+    import torch
+    from paper_2103_08246_gb300 import binding, build, inputs
+    build.build()
+    wl = inputs.PRODUCTION
+    prec = binding.IBM_FP32 if args.profile_precision == "fp32" else binding.IBM_FP64
+    s = binding.Solver(wl, prec, noise=inputs.initial_noise(wl))
+    s.step(args.profile_steps)
+    torch.cuda.synchronize()
+    s.close()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            if d.get("hbm_gbs"):
+                return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if _cuda_ok() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample_rate(steps: int, warmup: int, nx: int = SAMPLE_NX):
+    """Time the CPU oracle (single thread) on the first `nx` x-planes of the
+    production workload (same spacing and transverse size; the bar grid when
+    the sample reaches it; the flag lies further downstream and is left out).
+    Runs in a fresh interpreter so that BLAS is pinned to one thread.
+    Returns (cell-updates/s, seconds per sample step, description)."""
+    from paper_2103_08246_gb300 import inputs
+    h = inputs.PRODUCTION.lx / inputs.PRODUCTION.nx
+    lx = nx * h
+    wp = inputs.PRODUCTION
+    bars = lx >= wp.bar_x + 0.5 * wp.bar_width + 3 * h
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+from paper_2103_08246_gb300 import inputs
+wl = inputs.PRODUCTION.replace(nx={nx}, lx={lx!r}, flag_on=False, bars_on={bars!r})
+from oracle.solver import OracleSolver
+s = OracleSolver(wl, inputs.initial_noise(wl))
+for _ in range({warmup}):
+    s.step()
+t0 = time.perf_counter()
+for _ in range({steps}):
+    s.step()
+dt = (time.perf_counter() - t0) / {steps}
+print(json.dumps({{"sec_per_step": dt, "cells": wl.cells}}))
+"""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                         stderr=subprocess.PIPE, timeout=3600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr.decode()[-2000:])
+    r = json.loads(out.stdout.decode().strip().splitlines()[-1])
+    desc = (f"oracle (numpy/scipy FP64, 1 thread) on the first {nx} of 512 x-planes "
+            f"({nx}x256x256, {'bars' if bars else 'inflow region only'}, no flag), "
+            f"{steps} step(s) after {warmup} warm-up; scaled to the full workload by cell count")
+    return r["cells"] / r["sec_per_step"], r["sec_per_step"], desc
+
+
+def run_reference(args):
+    from paper_2103_08246_gb300 import inputs
+    wl = inputs.PRODUCTION
+    # size each step's sample so that warm-up + timed steps take about two minutes
+    _, sec16, _ = oracle_sample_rate(1, 0, 16)
+    per_plane = sec16 / 16
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    nx = int(max(8, min(SAMPLE_NX, budget / per_plane)))
+    rate, sec, desc = oracle_sample_rate(max(1, args.steps), max(0, args.warmup), nx)
+    steps_per_s = rate / wl.cells
+    line = {
+        "impl": "reference", "metric": METRIC, "value": steps_per_s, "unit": "steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 / steps_per_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "gcell_updates_per_s": rate / 1e9,
+        "config": {"workload": wl.name, "cells": wl.cells, "precision": "fp64",
+                   "cache": "inputs larger than L2"},
+        "cpu_baseline": {"value": steps_per_s, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": steps_per_s, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def time_steps(solver, steps, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def stage_roofline(wl, precision, peak_gbs, peak_kind):
+    """Per-stage device times on a timing-only state; roofline of the dominant kernel."""
+    from paper_2103_08246_gb300 import binding, inputs
+    t = binding.Solver(wl, precision, noise=inputs.initial_noise(wl))
+    t.step(2)
+    elem = 4 if precision == binding.IBM_FP32 else 8
+    cells = (wl.nx + 1) * wl.ny * wl.nz
+    stages = {}
+    for name in ("rhs", "outflow", "af_x", "af_y", "af_z", "ib", "flag", "mass_div", "dht_y",
+                 "dht_z", "poisson_x", "project"):
+        t.time_stage(name, 2)
+        stages[name] = t.time_stage(name, 10)
+    t.close()
+    per_step = {k: v * PER_STEP[k] for k, v in stages.items()}
+    dom = max((k for k in stages if k in FIELD_PASSES), key=lambda k: per_step[k])
+    alg_bytes = FIELD_PASSES[dom] * cells * elem
+    achieved = alg_bytes / (stages[dom] * 1e-3) / 1e9
+    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak_gbs,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak_gbs,
+            "traffic": None, "alg_bytes_per_launch": alg_bytes, "ms_per_launch": stages[dom]}
+    return roof, stages
+
+
+def e2e_rate(wl, precision, steps):
+    """Steps/s through the C ABI with host buffers: upload the state from pinned
+    host memory, K x (ibm_step + flag state read-back), read the fields back."""
+    import numpy as np
+    import torch
+    from paper_2103_08246_gb300 import binding, inputs
+    s = binding.Solver(wl, precision, noise=inputs.initial_noise(wl))
+    s.step(2)
+    fields = [s.field(q) for q in (binding.IBM_FIELD_U, binding.IBM_FIELD_V, binding.IBM_FIELD_W,
+                                   binding.IBM_FIELD_P)]
+    host = []
+    for a in fields:
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        host.append(t.numpy())
+    nf = s.nf
+    X = torch.empty((nf, 3), dtype=torch.float64, pin_memory=True).numpy()
+    V = torch.empty((nf, 3), dtype=torch.float64, pin_memory=True).numpy()
+    F = torch.empty((nf, 3), dtype=torch.float64, pin_memory=True).numpy()
+    elem = 4 if precision == binding.IBM_FP32 else 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q, a in zip((binding.IBM_FIELD_U, binding.IBM_FIELD_V, binding.IBM_FIELD_W,
+                     binding.IBM_FIELD_P), host):
+        binding.ibm_set_field(s.state, q, a)
+    for _ in range(steps):
+        s.step(1)
+        binding.ibm_flag_state(s.state, X, V, F)
+    for q, a in zip((binding.IBM_FIELD_U, binding.IBM_FIELD_V, binding.IBM_FIELD_W,
+                     binding.IBM_FIELD_P), host):
+        binding.ibm_get_field(s.state, q, a)
+    el = time.perf_counter() - t0
+    s.close()
+    field_bytes = sum(a.size for a in host) * elem
+    return {"value": steps / el, "unit": "steps/s",
+            "h2d_bytes_per_step": field_bytes / steps + 16,
+            "d2h_bytes_per_step": field_bytes / steps + 3 * X.nbytes + 8 * 64}
+
+
+def run_ours(args):
+    import torch
+    from paper_2103_08246_gb300 import binding, build, inputs
+    rank, world, local, pg = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    if local == 0:
+        build.build()
+    barrier(pg)
+    build.build()
+    binding.load()
+    wl = inputs.PRODUCTION
+    prec = binding.IBM_FP32
+    solver = binding.Solver(wl, prec, noise=inputs.initial_noise(wl))
+    solver.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+    kernels_per_step = solver.stats()["kernels_per_step"]
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_steps(solver, args.steps, solver.stream)
+    clk = clocks.stop()
+    barrier(pg)
+    ms = max_over_ranks(pg, ms)
+    st = solver.stats()
+    solver.close()
+    peak, peak_kind = measured_peaks()
+    out = None
+    if rank == 0:
+        roof, stages = stage_roofline(wl, prec, peak, peak_kind)
+        step_bytes = sum(FIELD_PASSES[k] * PER_STEP[k] for k in FIELD_PASSES) * \
+            (wl.nx + 1) * wl.ny * wl.nz * 4
+        fp64 = None
+        if not args.no_fp64:
+            s64 = binding.Solver(wl, binding.IBM_FP64, noise=inputs.initial_noise(wl))
+            s64.step(3)
+            ms64 = time_steps(s64, max(5, args.steps // 5), s64.stream)
+            s64.close()
+            fp64 = {"steps_per_s": 1000.0 / ms64, "ms_per_step": ms64,
+                    "gcell_updates_per_s": wl.cells / ms64 / 1e6,
+                    "speedup_fp32_over_fp64": ms64 / ms}
+        e2e = None if args.no_e2e else e2e_rate(wl, prec, args.steps)
+        if e2e is not None:
+            e2e["value"] *= world
+        cpu = None
+        if not args.no_cpu_baseline:
+            rate, sec, desc = oracle_sample_rate(2, 1)
+            cpu = {"value": rate / wl.cells, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                   "sample": desc, "gcell_updates_per_s": rate / 1e9}
+        value = world * 1000.0 / ms
+        out = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "cells": wl.cells, "precision": "fp32 fields, fp64 flag",
+                       "cfl": wl.cfl, "re": wl.re, "markers": st["n_markers"],
+                       "cache": "inputs larger than L2 (each field 134 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "gcell_updates_per_s": world * wl.cells / ms / 1e6,
+            "step_hbm_frac": (step_bytes / (ms * 1e-3) / 1e9) / peak,
+            "roofline": roof, "stages_ms": stages, "fp64": fp64, "e2e": e2e,
+            "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": kernels_per_step * args.steps,
+            "dt_last": st["dt"], "cfl_last": st["cfl"], "n_sub": st["n_sub"],
+        }
+        print(json.dumps(out), flush=True)
+    barrier(pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.profile_steps > 0:
+        run_profile(args)
+        return
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank == 0:
+            run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -58,6 +58,21 @@ extern "C" {
 #define IBM_FP64  0        /* everything in FP64                               */
 #define IBM_FP32  1        /* fluid fields and kernels in FP32; flag, sums FP64 */
 
+/* stages for ibm_time_stage (Sec. II.B step order) */
+#define IBM_STAGE_STEP      -1  /* the whole captured step                   */
+#define IBM_STAGE_RHS        0  /* explicit right-hand side (AB2 + CN half)   */
+#define IBM_STAGE_OUTFLOW    1  /* convective outflow plane                   */
+#define IBM_STAGE_AF_X       2  /* implicit factor along x                    */
+#define IBM_STAGE_AF_Y       3  /* implicit factor along y (periodic)         */
+#define IBM_STAGE_AF_Z       4  /* implicit factor along z (periodic) + u*    */
+#define IBM_STAGE_IB         5  /* marker interpolation + spreading           */
+#define IBM_STAGE_FLAG       6  /* structural sub-steps                       */
+#define IBM_STAGE_MASS_DIV   7  /* mass fix + divergence                      */
+#define IBM_STAGE_DHT_Y      8  /* transform along y                          */
+#define IBM_STAGE_DHT_Z      9  /* transform along z                          */
+#define IBM_STAGE_POISSON_X 10  /* tridiagonal solves along x                 */
+#define IBM_STAGE_PROJECT   11  /* projection + pressure update               */
+
 /* field selectors for ibm_get_field / ibm_set_field */
 #define IBM_FIELD_U 0
 #define IBM_FIELD_V 1
@@ -121,6 +136,7 @@ typedef struct {
   double max_strain;     /* max |len/len0 - 1| over flag springs                */
   int    n_sub;          /* structural sub-steps used by the last step          */
   int    n_markers;      /* flag vertices + bar markers                         */
+  int    kernels_per_step; /* kernel launches in one captured step              */
 } ibm_stats_t;
 
 typedef struct ibm_state ibm_state;   /* opaque; owns its device data */
@@ -174,6 +190,14 @@ int ibm_set_field(ibm_state* s, int which, const double* host, size_t n);
  * positions at the start of the next step (3 doubles each). */
 int ibm_marker_count(const ibm_state* s, size_t* n);
 int ibm_get_markers(ibm_state* s, double* X, size_t n);
+
+/* Benchmarking aid: launch one stage of the step `nrep` >= 1 times back to
+ * back on the state's stream, bracketed by CUDA events, and return the mean
+ * device time per launch in *ms. IBM_STAGE_STEP replays the captured step
+ * (a normal time step). Any other stage runs outside the step order and
+ * leaves the fields meaningless: use a state created for timing only.
+ * Synchronises. */
+int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms);
 
 /* Release the state (and the workspace if the library allocated it). */
 void ibm_destroy(ibm_state* s);

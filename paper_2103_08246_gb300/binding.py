@@ -25,7 +25,10 @@ IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P = 0, 1, 2, 3
 # every symbol include/ibm.h declares
 SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_flag_state",
            "ibm_stats", "ibm_get_field", "ibm_set_field", "ibm_marker_count", "ibm_get_markers",
-           "ibm_destroy", "ibm_strerror")
+           "ibm_time_stage", "ibm_destroy", "ibm_strerror")
+
+STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
+          "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11}
 
 
 class ibm_grid(ctypes.Structure):
@@ -61,7 +64,8 @@ class ibm_stats_t(ctypes.Structure):
                 ("q_in", ctypes.c_double), ("q_out", ctypes.c_double), ("ke", ctypes.c_double),
                 ("ib_slip", ctypes.c_double), ("te_mid", ctypes.c_double * 3),
                 ("force", ctypes.c_double * 3), ("max_strain", ctypes.c_double),
-                ("n_sub", ctypes.c_int), ("n_markers", ctypes.c_int)]
+                ("n_sub", ctypes.c_int), ("n_markers", ctypes.c_int),
+                ("kernels_per_step", ctypes.c_int)]
 
     def as_dict(self):
         out = {}
@@ -99,6 +103,7 @@ def load(path: str = LIB_PATH):
     lib.ibm_set_field.argtypes = [vp, ctypes.c_int, _dp, sz]
     lib.ibm_marker_count.argtypes = [vp, ctypes.POINTER(sz)]
     lib.ibm_get_markers.argtypes = [vp, _dp, sz]
+    lib.ibm_time_stage.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.ibm_destroy.argtypes = [vp]
     lib.ibm_destroy.restype = None
     lib.ibm_strerror.argtypes = [ctypes.c_int]
@@ -189,6 +194,12 @@ def ibm_get_markers(state, out):
     _check(load().ibm_get_markers(state, _ptr(out), out.size // 3), "ibm_get_markers")
 
 
+def ibm_time_stage(state, stage, nrep) -> float:
+    ms = ctypes.c_double(0.0)
+    _check(load().ibm_time_stage(state, int(stage), int(nrep), ctypes.byref(ms)), "ibm_time_stage")
+    return ms.value
+
+
 def ibm_destroy(state):
     load().ibm_destroy(state)
 
@@ -255,6 +266,9 @@ class Solver:
 
     def stats(self):
         return ibm_stats(self.state)
+
+    def time_stage(self, stage, nrep=10):
+        return ibm_time_stage(self.state, STAGES[stage] if isinstance(stage, str) else stage, nrep)
 
     def close(self):
         if getattr(self, "state", None) is not None:

@@ -263,6 +263,7 @@ struct ibm_state {
   double* dstat = nullptr;    // 16 doubles of device scratch for diagnostics
   Params* hprm = nullptr;     // pinned copy
   double last_dt_fixed = -2.0;
+  int kernels_per_step = 0;
 };
 
 namespace {
@@ -491,6 +492,9 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
       cudaGetLastError();
       return IBM_ECUDA;
     }
+    size_t nodes = 0;
+    cudaGraphGetNodes(g, nullptr, &nodes);
+    s->kernels_per_step = (int)nodes;
     e = cudaGraphInstantiate(&s->exec[par], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -556,6 +560,32 @@ int step_impl(ibm_state* s, double dt, int nsteps) {
   if (p.error) return IBM_EDIVERGED;
   if (nsteps > 0 && p.dt * p.speed_max / s->c.h > s->cfl_limit) return IBM_EDIVERGED;
   return IBM_OK;
+}
+
+}  // namespace
+
+namespace {
+template <class T>
+void launch_stage(ibm_state* s, int stage) {
+  Fields<T>& f = fields<T>(s);
+  const Consts& c = s->c;
+  cudaStream_t st = s->stream;
+  const int cur = s->cur;
+  switch (stage) {
+    case IBM_STAGE_RHS: launch_rhs(c, f, cur, st); break;
+    case IBM_STAGE_OUTFLOW: launch_outflow(c, f, cur, st); break;
+    case IBM_STAGE_AF_X: launch_af_x(c, f, cur, st); break;
+    case IBM_STAGE_AF_Y: launch_af_y(c, f, cur, st); break;
+    case IBM_STAGE_AF_Z: launch_af_z(c, f, cur, st); break;
+    case IBM_STAGE_IB: launch_ib(c, f, s->mk, s->fl, cur, st); break;
+    case IBM_STAGE_FLAG: launch_flag(c, f.prm, s->fl, st); break;
+    case IBM_STAGE_MASS_DIV: launch_mass_div(c, f, cur, false, st); break;
+    case IBM_STAGE_DHT_Y: launch_dht_y(c, f, st); break;
+    case IBM_STAGE_DHT_Z: launch_dht_z(c, f, st); break;
+    case IBM_STAGE_POISSON_X: launch_poisson_x(c, f, st); break;
+    case IBM_STAGE_PROJECT: launch_project_only(c, f, cur, false, st); break;
+    default: break;
+  }
 }
 
 }  // namespace
@@ -699,6 +729,36 @@ int ibm_stats(ibm_state* s, ibm_stats_t* out) {
   }
   out->n_sub = p.n_sub;
   out->n_markers = s->mk.nm;
+  out->kernels_per_step = s->kernels_per_step;
+  return IBM_OK;
+}
+
+int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
+  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_PROJECT) return IBM_EINVAL;
+  cudaStream_t st = s->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+  for (int r = 0; r < nrep; ++r) {
+    if (stage == IBM_STAGE_STEP) {
+      cudaGraphLaunch(s->exec[s->cur], st);
+      s->cur ^= 1;
+    } else if (s->precision == IBM_FP64) {
+      launch_stage<double>(s, stage);
+    } else {
+      launch_stage<float>(s, stage);
+    }
+  }
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float t = 0.f;
+  cudaError_t e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(e);
+  CK(cudaGetLastError());
+  *ms = (double)t / nrep;
   return IBM_OK;
 }
 

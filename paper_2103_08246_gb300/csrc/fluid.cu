@@ -503,29 +503,61 @@ void launch_outflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s
 }
 
 template <class T>
-void launch_af(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
+void launch_af_x(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   const int P = c.ny * c.nz;
   const size_t shx = 2 * (size_t)(c.nx + 1) * sizeof(T);
   k_af_x<T><<<dim3((P + 127) / 128, 3), 128, shx, s>>>(c, f.prm, f.d[0], f.d[1], f.d[2],
                                                         f.dout[0], f.dout[1], f.dout[2]);
+  (void)cur;
+}
+
+template <class T>
+void launch_af_y(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   k_af_y<T><<<dim3((c.nz + 63) / 64, c.nx, 3), 64, 0, s>>>(c, f.prm, f.d[0], f.d[1], f.d[2]);
+  (void)cur;
+}
+
+template <class T>
+void launch_af_z(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   const size_t shz = (size_t)ZL * (c.nz + 1) * sizeof(T);
   k_af_z<T><<<dim3((c.nx * c.ny + ZL - 1) / ZL, 3), 128, shz, s>>>(
       c, f.prm, f.d[0], f.d[1], f.d[2], f.u[cur], f.v[cur], f.w[cur]);
 }
 
 template <class T>
-void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
-  if (!initial) k_mass<T><<<1, 1024, 0, s>>>(c, f.prm, f.u[cur]);
+void launch_af(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
+  launch_af_x(c, f, cur, s);
+  launch_af_y(c, f, cur, s);
+  launch_af_z(c, f, cur, s);
+}
+
+template <class T>
+void launch_mass(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
+  k_mass<T><<<1, 1024, 0, s>>>(c, f.prm, f.u[cur]);
+}
+
+template <class T>
+void launch_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
   k_div<T><<<grid3(c, c.nx), dim3(TK, TJ), 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.phi,
                                                     initial ? 1 : 0);
 }
 
 template <class T>
-void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
+void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
+  if (!initial) launch_mass(c, f, cur, s);
+  launch_div(c, f, cur, initial, s);
+}
+
+template <class T>
+void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
   k_project<T><<<grid3(c, c.nx + 1), dim3(TK, TJ), 0, s>>>(
       c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1], f.phi, f.p,
       f.partial, initial ? 1 : 0);
+}
+
+template <class T>
+void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
+  launch_project_only(c, f, cur, initial, s);
   if (!initial) k_end_step<<<1, 1, 0, s>>>(f.prm);
 }
 
@@ -551,6 +583,12 @@ int partial_count(const Consts& c) {
   template void launch_rhs<T>(const Consts&, const Fields<T>&, int, cudaStream_t);             \
   template void launch_outflow<T>(const Consts&, const Fields<T>&, int, cudaStream_t);         \
   template void launch_af<T>(const Consts&, const Fields<T>&, int, cudaStream_t);              \
+  template void launch_af_x<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
+  template void launch_af_y<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
+  template void launch_af_z<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
+  template void launch_mass<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
+  template void launch_div<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t);       \
+  template void launch_project_only<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t); \
   template void launch_mass_div<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t);  \
   template void launch_project<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t);   \
   template void launch_stats<T>(const Consts&, const Fields<T>&, int, double*, cudaStream_t);

@@ -157,7 +157,7 @@ __global__ void k_poisson_table(Consts c, T* __restrict__ tab) {
 }
 
 template <class T>
-static void dht_y(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+void launch_dht_y(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   const int n = c.ny, logn = (int)std::lround(std::log2((double)n));
   const int W = c.nz < 16 ? c.nz : 16;
   const size_t sh = (size_t)(W / 2) * n * sizeof(typename Vec2<T>::type);
@@ -167,7 +167,7 @@ static void dht_y(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 }
 
 template <class T>
-static void dht_z(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+void launch_dht_z(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   const int n = c.nz, logn = (int)std::lround(std::log2((double)n));
   const int lines = c.nx * c.ny;
   int W = 16;
@@ -177,14 +177,19 @@ static void dht_z(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 }
 
 template <class T>
-void launch_poisson(const Consts& c, const Fields<T>& f, cudaStream_t s) {
-  dht_y(c, f, s);
-  dht_z(c, f, s);
+void launch_poisson_x(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   const int P = c.ny * c.nz;
   const T scale = (T)(c.h * c.h / ((double)c.ny * c.nz));
   k_poisson_x<T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, f.phi, scale);
-  dht_z(c, f, s);
-  dht_y(c, f, s);
+}
+
+template <class T>
+void launch_poisson(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+  launch_dht_y(c, f, s);
+  launch_dht_z(c, f, s);
+  launch_poisson_x(c, f, s);
+  launch_dht_z(c, f, s);
+  launch_dht_y(c, f, s);
 }
 
 template <class T>
@@ -194,6 +199,12 @@ void launch_poisson_table(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 }
 
 template void launch_poisson<double>(const Consts&, const Fields<double>&, cudaStream_t);
+template void launch_dht_y<double>(const Consts&, const Fields<double>&, cudaStream_t);
+template void launch_dht_y<float>(const Consts&, const Fields<float>&, cudaStream_t);
+template void launch_dht_z<double>(const Consts&, const Fields<double>&, cudaStream_t);
+template void launch_dht_z<float>(const Consts&, const Fields<float>&, cudaStream_t);
+template void launch_poisson_x<double>(const Consts&, const Fields<double>&, cudaStream_t);
+template void launch_poisson_x<float>(const Consts&, const Fields<float>&, cudaStream_t);
 template void launch_poisson<float>(const Consts&, const Fields<float>&, cudaStream_t);
 template void launch_poisson_table<double>(const Consts&, const Fields<double>&, cudaStream_t);
 template void launch_poisson_table<float>(const Consts&, const Fields<float>&, cudaStream_t);

@@ -56,6 +56,12 @@ template <class T> void launch_begin_step(const Consts& c, const Fields<T>& f, c
 template <class T> void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_outflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_af(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> void launch_af_x(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> void launch_af_y(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> void launch_af_z(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> void launch_mass(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> void launch_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
+template <class T> void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 template <class T> void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 template <class T> void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 int partial_count(const Consts& c);
@@ -64,6 +70,9 @@ template <class T> void launch_stats(const Consts& c, const Fields<T>& f, int cu
 
 // ---- poisson.cu
 template <class T> void launch_poisson(const Consts& c, const Fields<T>& f, cudaStream_t s);
+template <class T> void launch_dht_y(const Consts& c, const Fields<T>& f, cudaStream_t s);
+template <class T> void launch_dht_z(const Consts& c, const Fields<T>& f, cudaStream_t s);
+template <class T> void launch_poisson_x(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_poisson_table(const Consts& c, const Fields<T>& f, cudaStream_t s);
 void poisson_set_attributes();
 

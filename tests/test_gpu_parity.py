@@ -7,10 +7,17 @@ order differs between the two (atomic spreading order, FFT vs plain DFT,
 closed-form vs recursive pivots), so 1e-9 leaves a wide margin over the
 ~1e-13 seen per step.
 
-FP32: the same workloads; the kernels round every field operation to
-2^-24 ~ 6e-8 relative, the Poisson solve amplifies by its condition
-(~(nx/pi)^2 for the lowest x mode) and errors grow over the steps; the bound
-used is 5e-4 relative after 10 steps, or 1e-3 at the tiny workload after 20.
+FP32: the same workloads, errors measured against the natural scales
+(velocity U = 1, pressure U^2 = 1, flag positions L = 1, flag velocity U)
+because the noise-driven pressure and flag velocity are themselves near
+zero. Derivation of the bound: each field operation rounds to
+eps = 2^-24 ~ 6e-8; the divergence of O(U) face values carries an error
+~eps U / h, so D = div / dt carries eps U / (h dt) and phi (~h^2 D / 6 for the
+high modes that white rounding noise excites) eps U h / (6 dt) per step,
+~1.3e-6 U^2 at h = 1/4, dt = 2e-3; p accumulates phi over the steps. Velocity
+errors stay near eps times the number of operations per step. Bounds used:
+2e-5 for velocities and flag quantities, 2e-4 for p, after 10-20 steps
+(about 10x above the measured values).
 """
 import numpy as np
 import pytest
@@ -33,20 +40,29 @@ def _rel(g, o):
     return np.abs(g - o).max() / max(np.abs(o).max(), 1e-300)
 
 
-def _compare(gpu, ora, tol, flag=True):
+def _compare(gpu, ora, tol, flag=True, floor=None):
+    """Max-norm error of each quantity divided by max(|oracle|, floor[q]).
+
+    tol: a number, or a dict per quantity. floor None: pure relative error."""
+    floor = floor or {}
     errs = {}
     for name, g, o in zip("uvwp", gpu.fields(), ora.fields()):
         if name == "p":
             g, o = g - g.mean(), o - o.mean()
-        errs[name] = _rel(g, o)
+        errs[name] = np.abs(g - o).max() / max(np.abs(o).max(), floor.get(name, 1e-300))
     if flag and ora.nf:
         X, V, F = gpu.flag()
-        errs["X"] = np.abs(X - ora.X).max() / np.abs(ora.X).max()
-        errs["V"] = np.abs(V - ora.V).max() / max(np.abs(ora.V).max(), 1e-30)
+        errs["X"] = np.abs(X - ora.X).max() / max(np.abs(ora.X).max(), floor.get("X", 1e-300))
+        errs["V"] = np.abs(V - ora.V).max() / max(np.abs(ora.V).max(), floor.get("V", 1e-30))
         errs["F"] = np.abs(F - ora.F_flag).max() / max(np.abs(ora.F_flag).max(), 1e-30)
-    bad = {k: v for k, v in errs.items() if not v <= tol}
-    assert not bad, (errs, tol)
+    tols = tol if isinstance(tol, dict) else {k: tol for k in errs}
+    bad = {k: v for k, v in errs.items() if not v <= tols[k]}
+    assert not bad, (errs, tols)
     return errs
+
+
+FP32_FLOOR = {"u": 1.0, "v": 1.0, "w": 1.0, "p": 1.0, "X": 1.0, "V": 1.0}
+FP32_TOL = {"u": 2e-5, "v": 2e-5, "w": 2e-5, "p": 2e-4, "X": 2e-5, "V": 2e-5, "F": 2e-4}
 
 
 def _run(wl, precision, nsteps, amp=0.05, dt=None):
@@ -119,15 +135,16 @@ def test_fp32_small_cases(lib, case):
     kw = {"plain": {}, "bars_flag": dict(bars_on=True, bar_x=1.0, **FLAG)}[case]
     wl = _small(**kw)
     gpu, ora = _run(wl, binding.IBM_FP32, 10)
-    _compare(gpu, ora, 5e-4)
+    errs = _compare(gpu, ora, FP32_TOL, floor=FP32_FLOOR)
     gpu.close()
+    print(case, "FP32 errors:", errs)
 
 
 def test_fp32_tiny_workload(lib):
     from paper_2103_08246_gb300 import binding, inputs
     wl = inputs.TINY
     gpu, ora = _run(wl, binding.IBM_FP32, 20, amp=wl.noise_amp)
-    errs = _compare(gpu, ora, 1e-3)
+    errs = _compare(gpu, ora, FP32_TOL, floor=FP32_FLOOR)
     gpu.close()
     print("tiny workload FP32 errors:", errs)
 
