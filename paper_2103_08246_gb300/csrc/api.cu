@@ -31,8 +31,9 @@ struct FlagGeom {
   std::vector<double> X, inv_mass, dv;
   std::vector<int> spring;
   std::vector<double> l0;
-  std::vector<int> hinge;
-  std::vector<double> k_hinge;
+  std::vector<int> tri, tri_nb;       // 3 per triangle
+  std::vector<double> tri_k;          // 3 per triangle
+  int n_hinge = 0;
   std::vector<int> csr_off, csr_idx;
   double omega_max = 0.0;
 };
@@ -121,32 +122,46 @@ FlagGeom build_flag(const ibm_bodies& b, const ibm_domain& d, double h) {
       const int p = tris[t][e], q = tris[t][(e + 1) % 3];
       edges[std::make_tuple(kind[t], std::min(p, q), std::max(p, q))].push_back(t);
     }
+  const int ntri = (int)tris.size();
+  g.tri.resize(3 * ntri);
+  for (int t = 0; t < ntri; ++t)
+    for (int e = 0; e < 3; ++e) g.tri[3 * t + e] = tris[t][e];
+  g.tri_nb.assign(3 * ntri, -1);
+  g.tri_k.assign(3 * ntri, 0.0);
+  std::vector<int> fill(ntri, 0);
+  std::vector<std::array<int, 2>> hinge_tris;
+  std::vector<double> hinge_k;
   const double cell = ds * dtt;
   for (auto& kv : edges) {
     if (kv.second.size() != 2) continue;
     const int ta = kv.second[0], tb = kv.second[1];
-    for (int e = 0; e < 3; ++e) g.hinge.push_back(tris[ta][e]);
-    for (int e = 0; e < 3; ++e) g.hinge.push_back(tris[tb][e]);
     const int p = std::get<1>(kv.first), q = std::get<2>(kv.first);
     const int ap = p / nt, cp = p % nt, aq = q / nt, cq = q % nt;
     const double es = (aq - ap) * ds, et = (cq - cp) * dtt;
     const double e2 = es * es + et * et;
     const bool diag = (aq != ap) && (cq != cp);
-    g.k_hinge.push_back(0.5 * (diag ? 2.0 * b.bending * cell / e2 : b.bending * e2 / cell));
+    const double k = 0.5 * (diag ? 2.0 * b.bending * cell / e2 : b.bending * e2 / cell);
+    g.tri_nb[3 * ta + fill[ta]] = tb;
+    g.tri_k[3 * ta + fill[ta]++] = k;
+    g.tri_nb[3 * tb + fill[tb]] = ta;
+    g.tri_k[3 * tb + fill[tb]++] = k;
+    hinge_tris.push_back({ta, tb});
+    hinge_k.push_back(k);
   }
-  // per-vertex slot lists (springs: 2 slots, hinges: 6 slots), fixed order
-  const int nsp = (int)g.l0.size(), nh = (int)g.k_hinge.size();
+  g.n_hinge = (int)hinge_k.size();
+  // per-vertex slot lists (triangles: 3 slots, springs: 2 slots), fixed order
+  const int nsp = (int)g.l0.size();
   std::vector<std::vector<int>> lists(nv);
+  for (int t = 0; t < ntri; ++t)
+    for (int e = 0; e < 3; ++e) lists[g.tri[3 * t + e]].push_back(3 * t + e);
   for (int q = 0; q < nsp; ++q) {
-    lists[g.spring[2 * q]].push_back(2 * q);
-    lists[g.spring[2 * q + 1]].push_back(2 * q + 1);
+    lists[g.spring[2 * q]].push_back(3 * ntri + 2 * q);
+    lists[g.spring[2 * q + 1]].push_back(3 * ntri + 2 * q + 1);
   }
-  for (int q = 0; q < nh; ++q)
-    for (int e = 0; e < 6; ++e) lists[g.hinge[6 * q + e]].push_back(2 * nsp + 6 * q + e);
   g.csr_off.assign(nv + 1, 0);
   for (int v = 0; v < nv; ++v) {
     g.csr_off[v + 1] = g.csr_off[v] + (int)lists[v].size();
-    for (int s : lists[v]) g.csr_idx.push_back(s);
+    for (int sidx : lists[v]) g.csr_idx.push_back(sidx);
   }
   // Gershgorin bound of the stiffness / mass spectrum (linearised, flat):
   // (2 k_s n_springs(v) + 8 sum_hinges_at_v k_e / l_min^2) / m_v, free vertices
@@ -155,12 +170,15 @@ FlagGeom build_flag(const ibm_bodies& b, const ibm_domain& d, double h) {
     nspr[g.spring[2 * q]] += 1.0;
     nspr[g.spring[2 * q + 1]] += 1.0;
   }
-  for (int q = 0; q < nh; ++q) {
+  for (int q = 0; q < g.n_hinge; ++q) {
     int vs[6];
-    for (int e = 0; e < 6; ++e) vs[e] = g.hinge[6 * q + e];
+    for (int e = 0; e < 3; ++e) {
+      vs[e] = tris[hinge_tris[q][0]][e];
+      vs[3 + e] = tris[hinge_tris[q][1]][e];
+    }
     std::sort(vs, vs + 6);
     const int* end = std::unique(vs, vs + 6);
-    for (const int* p = vs; p != end; ++p) khs[*p] += g.k_hinge[q];
+    for (const int* p = vs; p != end; ++p) khs[*p] += hinge_k[q];
   }
   const double lmin = std::min(ds, dtt);
   double w2 = 0.0;
@@ -235,7 +253,7 @@ struct Carver {
 };
 
 struct Layout {
-  int nf = 0, nb = 0, nsp = 0, nh = 0, nslot = 0, ncsr = 0;
+  int nf = 0, nb = 0, nsp = 0, ntri = 0, nslot = 0, ncsr = 0;
 };
 
 }  // namespace
@@ -264,6 +282,8 @@ struct ibm_state {
   Params* hprm = nullptr;     // pinned copy
   double last_dt_fixed = -2.0;
   int kernels_per_step = 0;
+  cudaStream_t side = nullptr;            // structural update, overlapped in the graph
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -311,6 +331,11 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   }
   for (int q = 0; q < 3; ++q) f.n[q] = cv.take<T>(NF);
   for (int q = 0; q < 3; ++q) f.d[q] = cv.take<T>(NF);
+  for (int q = 0; q < 3; ++q) f.e[q] = cv.take<T>(NF);
+  f.ipt = cv.take<double>(2 * (size_t)(c.nx + 2));
+  f.iptf = cv.take<float>(2 * (size_t)(c.nx + 2));
+  f.taps = cv.take<double>((size_t)c.ny + c.nz + 32);
+  f.tapsf = cv.take<float>((size_t)c.ny + c.nz + 32);
   f.p = cv.take<T>(NP);
   f.phi = cv.take<T>(NP);
   f.ptab = cv.take<T>(NP);
@@ -338,9 +363,12 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   fl.n_spring = L.nsp;
   fl.spring = cv.take<int>(2 * (size_t)L.nsp);
   fl.l0 = cv.take<double>(L.nsp);
-  fl.n_hinge = L.nh;
-  fl.hinge = cv.take<int>(6 * (size_t)L.nh);
-  fl.k_hinge = cv.take<double>(L.nh);
+  fl.n_tri = L.ntri;
+  fl.tri = cv.take<int>(3 * (size_t)L.ntri);
+  fl.tri_nb = cv.take<int>(3 * (size_t)L.ntri);
+  fl.tri_k = cv.take<double>(3 * (size_t)L.ntri);
+  fl.tri_n = cv.take<double>(3 * (size_t)L.ntri);
+  fl.tri_inv = cv.take<double>(L.ntri);
   fl.slot = cv.take<double>(3 * (size_t)L.nslot);
   fl.csr_off = cv.take<int>(L.nf + 1);
   fl.csr_idx = cv.take<int>(L.ncsr);
@@ -392,17 +420,28 @@ int download_field(cudaStream_t st, double* dst, const T* src, size_t n) {
   return IBM_OK;
 }
 
+// One time step. The structural update of the previous step (pending since
+// its forcing) runs on a side stream concurrently with this step's explicit
+// and implicit velocity stages, and joins before this step's forcing, which
+// reads the updated flag positions.
 template <class T>
 void record_step(ibm_state* s, int cur) {
   Fields<T>& f = fields<T>(s);
   const Consts& c = s->c;
   cudaStream_t st = s->stream;
+  const bool flag = s->fl.nv > 0;
+  if (flag) {
+    cudaEventRecord(s->ev_fork, st);
+    cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+    launch_flag(f.prm, s->fl, false, s->side);
+    cudaEventRecord(s->ev_join, s->side);
+  }
   launch_begin_step(c, f, st);
   launch_rhs(c, f, cur, st);
   launch_outflow(c, f, cur, st);
   launch_af(c, f, cur, st);
+  if (flag) cudaStreamWaitEvent(st, s->ev_join, 0);
   launch_ib(c, f, s->mk, s->fl, cur, st);
-  launch_flag(c, f.prm, s->fl, st);
   launch_mass_div(c, f, cur, false, st);
   launch_poisson(c, f, st);
   launch_project(c, f, cur, false, st);
@@ -455,12 +494,13 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
     CK(up(fl.dv, fg.dv.data(), fg.dv.size() * sizeof(double)));
     CK(up(fl.spring, fg.spring.data(), fg.spring.size() * sizeof(int)));
     CK(up(fl.l0, fg.l0.data(), fg.l0.size() * sizeof(double)));
-    CK(up(fl.hinge, fg.hinge.data(), fg.hinge.size() * sizeof(int)));
-    CK(up(fl.k_hinge, fg.k_hinge.data(), fg.k_hinge.size() * sizeof(double)));
+    CK(up(fl.tri, fg.tri.data(), fg.tri.size() * sizeof(int)));
+    CK(up(fl.tri_nb, fg.tri_nb.data(), fg.tri_nb.size() * sizeof(int)));
+    CK(up(fl.tri_k, fg.tri_k.data(), fg.tri_k.size() * sizeof(double)));
     CK(up(fl.csr_off, fg.csr_off.data(), fg.csr_off.size() * sizeof(int)));
     CK(up(fl.csr_idx, fg.csr_idx.data(), fg.csr_idx.size() * sizeof(int)));
     // enough CTAs for the hinge work, within the cluster limit
-    const int want = std::min((fl.n_hinge + fl.n_spring + 4095) / 4096, flag_max_cluster());
+    const int want = std::min((fl.n_tri + fl.n_spring + 1023) / 1024, flag_max_cluster());
     fl.cluster = 1;
     while (2 * fl.cluster <= want) fl.cluster *= 2;
   }
@@ -482,6 +522,9 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   (void)NP;
+  CK(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
   // capture one step per buffer parity
   for (int par = 0; par < 2; ++par) {
     cudaGraph_t g;
@@ -532,8 +575,8 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   L.nf = b->flag_on ? b->flag_ns * b->flag_nt : 0;
   L.nb = (int)(Xb.size() / 3);
   L.nsp = (int)fg.l0.size();
-  L.nh = (int)fg.k_hinge.size();
-  L.nslot = 2 * L.nsp + 6 * L.nh;
+  L.ntri = (int)(fg.tri.size() / 3);
+  L.nslot = 2 * L.nsp + 3 * L.ntri;
   L.ncsr = (int)fg.csr_idx.size();
   return IBM_OK;
 }
@@ -554,9 +597,13 @@ int step_impl(ibm_state* s, double dt, int nsteps) {
     CK(cudaGraphLaunch(s->exec[s->cur], st));
     s->cur ^= 1;
   }
+  // the last step's structural update is still pending: run it now, so that
+  // the state is complete when ibm_step returns
+  if (nsteps > 0) launch_flag(f.prm, s->fl, false, st);
   CK(cudaMemcpyAsync(s->hprm, f.prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const Params& p = *s->hprm;
+  if (p.error & ERR_AF_RANGE) return IBM_EINVAL;
   if (p.error) return IBM_EDIVERGED;
   if (nsteps > 0 && p.dt * p.speed_max / s->c.h > s->cfl_limit) return IBM_EDIVERGED;
   return IBM_OK;
@@ -578,7 +625,7 @@ void launch_stage(ibm_state* s, int stage) {
     case IBM_STAGE_AF_Y: launch_af_y(c, f, cur, st); break;
     case IBM_STAGE_AF_Z: launch_af_z(c, f, cur, st); break;
     case IBM_STAGE_IB: launch_ib(c, f, s->mk, s->fl, cur, st); break;
-    case IBM_STAGE_FLAG: launch_flag(c, f.prm, s->fl, st); break;
+    case IBM_STAGE_FLAG: launch_flag(f.prm, s->fl, true, st); break;
     case IBM_STAGE_MASS_DIV: launch_mass_div(c, f, cur, false, st); break;
     case IBM_STAGE_DHT_Y: launch_dht_y(c, f, st); break;
     case IBM_STAGE_DHT_Z: launch_dht_z(c, f, st); break;
@@ -819,6 +866,9 @@ void ibm_destroy(ibm_state* s) {
   if (s->own_ws && s->ws) cudaFree(s->ws);
   if (s->hprm) cudaFreeHost(s->hprm);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  if (s->side) cudaStreamDestroy(s->side);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
   cudaGetLastError();
   delete s;
 }

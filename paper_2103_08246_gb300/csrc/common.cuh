@@ -25,7 +25,11 @@ struct Params {
   int n_sub;          // structural sub-steps of the current step
   int first;          // 1 until the first step has run (Euler start)
   int error;          // bit mask of device-side errors
-  int pad;
+  int flag_nsub;      // sub-steps of the pending structural update
+  double flag_dt;     // fluid step of the pending structural update
+  int flag_pending;   // 1 after a forcing step until the flag has been advanced
+  int af_h;           // warm-up length of the segmented implicit line solves
+  double af_rho;      // exp(-theta) of the implicit factors
 };
 
 // Host-provided constants of a problem.

@@ -3,19 +3,22 @@
 // constant.
 //
 // Energies: stretching springs E = k_s/2 (|x_b - x_a| - l0)^2 on lattice edges
-// and both cell diagonals; bending hinges E = k_e (1 - n_A . n_B) between the
+// and both cell diagonals; bending hinges E = k_h (1 - n_A . n_B) between the
 // two triangles (of one of the two overlaid triangulations) sharing an edge.
-// Hinge force on the vertices of triangle (p0, p1, p2), N = (p1-p0) x (p2-p0):
-//   g = (n_B - (n_A . n_B) n_A) / |N_A|,
-//   f1 = k_e (p2 - p0) x g,  f2 = k_e g x (p1 - p0),  f0 = -(f1 + f2),
-// and symmetrically for triangle B (the gradient of k_e n_A . n_B).
 //
-// Each force term is written to its own slot; every vertex then sums its
-// slots in a fixed order (CSR list), so the result does not depend on thread
-// timing. The CTAs of one thread-block cluster share the work; the cluster
-// barrier separates the position update, the force evaluation and the
-// gather. Positions and slots written by other CTAs are read with L2-only
-// loads.
+// The bending force is assembled per triangle. For triangle T = (p0, p1, p2)
+// with N = (p1 - p0) x (p2 - p0) and n = N / |N|, every hinge h of T with
+// neighbour normal m_h contributes k_h dn/dx^T m_h, and
+// dn/dx^T m = dN/dx^T (m - (n . m) n) / |N| is linear in the bracket, so
+//   G_T = sum_h k_h (m_h - (n . m_h) n) / |N|,
+//   f1 = (p2 - p0) x G_T,  f2 = G_T x (p1 - p0),  f0 = -(f1 + f2)
+// gives the whole bending force of T on its vertices with two cross products.
+//
+// Each force term is written to its own slot and every vertex sums its slots
+// in a fixed order (CSR list), so the result does not depend on thread
+// timing. The CTAs of one thread-block cluster share the work and meet at the
+// cluster barrier (hardware) between phases. Data written by other CTAs is
+// read with L2-only loads.
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -36,100 +39,102 @@ __device__ inline double dot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * 
 __device__ inline D3 cross(D3 a, D3 b) {
   return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
-__device__ inline D3 ldX(const double* X, int v) {
-  return {__ldcg(X + 3 * v), __ldcg(X + 3 * v + 1), __ldcg(X + 3 * v + 2)};
+__device__ inline D3 ld3(const double* p, int v) {
+  return {__ldcg(p + 3 * v), __ldcg(p + 3 * v + 1), __ldcg(p + 3 * v + 2)};
 }
-__device__ inline void stslot(double* s, int q, D3 f) {
-  s[3 * q] = f.x;
-  s[3 * q + 1] = f.y;
-  s[3 * q + 2] = f.z;
+__device__ inline void st3(double* p, int q, D3 f) {
+  p[3 * q] = f.x;
+  p[3 * q + 1] = f.y;
+  p[3 * q + 2] = f.z;
 }
 
-__device__ void flag_forces(const Flag& fl, int gt, int G) {
+// unit normals of all triangles, stretching forces of all springs
+__device__ void phase_normals_springs(const Flag& fl, int gt, int G) {
+  for (int t = gt; t < fl.n_tri; t += G) {
+    const int* tv = fl.tri + 3 * t;
+    const D3 p0 = ld3(fl.X, tv[0]), p1 = ld3(fl.X, tv[1]), p2 = ld3(fl.X, tv[2]);
+    const D3 N = cross(p1 - p0, p2 - p0);
+    const double inv = rsqrt(dot(N, N));
+    st3(fl.tri_n, t, inv * N);
+    fl.tri_inv[t] = inv;
+  }
+  const int base = 3 * fl.n_tri;
   for (int q = gt; q < fl.n_spring; q += G) {
     const int a = fl.spring[2 * q], b = fl.spring[2 * q + 1];
-    const D3 d = ldX(fl.X, b) - ldX(fl.X, a);
+    const D3 d = ld3(fl.X, b) - ld3(fl.X, a);
     const double len2 = dot(d, d);
     const double il = rsqrt(len2);
-    const double len = len2 * il;
-    const D3 f = (fl.k_s * (len - fl.l0[q]) * il) * d;   // pulls a towards b when stretched
-    stslot(fl.slot, 2 * q, f);
-    stslot(fl.slot, 2 * q + 1, -1.0 * f);
+    const D3 f = (fl.k_s * (len2 * il - fl.l0[q]) * il) * d;   // pulls a towards b when stretched
+    st3(fl.slot, base + 2 * q, f);
+    st3(fl.slot, base + 2 * q + 1, -1.0 * f);
   }
-  const int base = 2 * fl.n_spring;
-  for (int q = gt; q < fl.n_hinge; q += G) {
-    const int* hv = fl.hinge + 6 * q;
-    const D3 a0 = ldX(fl.X, hv[0]), a1 = ldX(fl.X, hv[1]), a2 = ldX(fl.X, hv[2]);
-    const D3 b0 = ldX(fl.X, hv[3]), b1 = ldX(fl.X, hv[4]), b2 = ldX(fl.X, hv[5]);
-    const D3 ea1 = a1 - a0, ea2 = a2 - a0, eb1 = b1 - b0, eb2 = b2 - b0;
-    const D3 NA = cross(ea1, ea2), NB = cross(eb1, eb2);
-    const double ia = rsqrt(dot(NA, NA)), ib = rsqrt(dot(NB, NB));
-    const D3 nA = ia * NA, nB = ib * NB;
-    const double cs = dot(nA, nB);
-    const double k = fl.k_hinge[q];
-    const D3 gA = (k * ia) * (nB - cs * nA);
-    const D3 gB = (k * ib) * (nA - cs * nB);
-    const D3 fa1 = cross(ea2, gA), fa2 = cross(gA, ea1);
-    const D3 fb1 = cross(eb2, gB), fb2 = cross(gB, eb1);
-    const int s0 = base + 6 * q;
-    stslot(fl.slot, s0 + 0, -1.0 * (fa1 + fa2));
-    stslot(fl.slot, s0 + 1, fa1);
-    stslot(fl.slot, s0 + 2, fa2);
-    stslot(fl.slot, s0 + 3, -1.0 * (fb1 + fb2));
-    stslot(fl.slot, s0 + 4, fb1);
-    stslot(fl.slot, s0 + 5, fb2);
+}
+
+// bending forces of every triangle from its hinges
+__device__ void phase_bending(const Flag& fl, int gt, int G) {
+  for (int t = gt; t < fl.n_tri; t += G) {
+    const D3 n = ld3(fl.tri_n, t);
+    D3 g = {0.0, 0.0, 0.0};
+    for (int e = 0; e < 3; ++e) {
+      const int nb = fl.tri_nb[3 * t + e];
+      if (nb < 0) continue;
+      const D3 m = ld3(fl.tri_n, nb);
+      g = g + fl.tri_k[3 * t + e] * (m - dot(n, m) * n);
+    }
+    g = __ldcg(fl.tri_inv + t) * g;
+    const int* tv = fl.tri + 3 * t;
+    const D3 p0 = ld3(fl.X, tv[0]), p1 = ld3(fl.X, tv[1]), p2 = ld3(fl.X, tv[2]);
+    const D3 f1 = cross(p2 - p0, g), f2 = cross(g, p1 - p0);
+    st3(fl.slot, 3 * t, -1.0 * (f1 + f2));
+    st3(fl.slot, 3 * t + 1, f1);
+    st3(fl.slot, 3 * t + 2, f2);
   }
 }
 
 __device__ inline D3 gather_acc(const Flag& fl, int v) {
   D3 f = {fl.Ff[3 * v], fl.Ff[3 * v + 1], fl.Ff[3 * v + 2]};
-  for (int e = fl.csr_off[v]; e < fl.csr_off[v + 1]; ++e) {
-    const int q = fl.csr_idx[e];
-    f = f + D3{__ldcg(fl.slot + 3 * q), __ldcg(fl.slot + 3 * q + 1), __ldcg(fl.slot + 3 * q + 2)};
-  }
+  for (int e = fl.csr_off[v]; e < fl.csr_off[v + 1]; ++e) f = f + ld3(fl.slot, fl.csr_idx[e]);
   return fl.inv_mass[v] * f;
 }
 
-__global__ void __launch_bounds__(512) k_flag(const Params* __restrict__ prm, Flag fl) {
+__global__ void __launch_bounds__(512) k_flag(Params* __restrict__ prm, Flag fl, int force) {
   cg::cluster_group cl = cg::this_cluster();
+  if (!force && !prm->flag_pending) return;   // same value for every thread of the cluster
   const int gt = (int)cl.block_rank() * blockDim.x + threadIdx.x;
   const int G = (int)cl.num_blocks() * blockDim.x;
-  const double dt = prm->dt;
-  const int nsub = prm->n_sub;
+  const double dt = prm->flag_dt;
+  const int nsub = prm->flag_nsub;
   const double hs = dt / nsub;
-  flag_forces(fl, gt, G);
+  phase_normals_springs(fl, gt, G);
   cl.sync();
-  for (int v = gt; v < fl.nv; v += G) {
-    const D3 a = gather_acc(fl, v);
-    fl.A[3 * v] = a.x;
-    fl.A[3 * v + 1] = a.y;
-    fl.A[3 * v + 2] = a.z;
-  }
+  phase_bending(fl, gt, G);
+  cl.sync();
+  for (int v = gt; v < fl.nv; v += G) st3(fl.A, v, gather_acc(fl, v));
   for (int s = 0; s < nsub; ++s) {
     for (int v = gt; v < fl.nv; v += G) {
       D3 V = {fl.V[3 * v], fl.V[3 * v + 1], fl.V[3 * v + 2]};
       const D3 A = {fl.A[3 * v], fl.A[3 * v + 1], fl.A[3 * v + 2]};
       V = V + (0.5 * hs) * A;
-      fl.V[3 * v] = V.x;
-      fl.V[3 * v + 1] = V.y;
-      fl.V[3 * v + 2] = V.z;
+      st3(fl.V, v, V);
       fl.X[3 * v] += hs * V.x;
       fl.X[3 * v + 1] += hs * V.y;
       fl.X[3 * v + 2] += hs * V.z;
     }
     cl.sync();
-    flag_forces(fl, gt, G);
+    phase_normals_springs(fl, gt, G);
+    cl.sync();
+    phase_bending(fl, gt, G);
     cl.sync();
     for (int v = gt; v < fl.nv; v += G) {
       const D3 a = gather_acc(fl, v);
-      fl.A[3 * v] = a.x;
-      fl.A[3 * v + 1] = a.y;
-      fl.A[3 * v + 2] = a.z;
+      st3(fl.A, v, a);
       fl.V[3 * v] += 0.5 * hs * a.x;
       fl.V[3 * v + 1] += 0.5 * hs * a.y;
       fl.V[3 * v + 2] += 0.5 * hs * a.z;
     }
   }
+  cl.sync();
+  if (gt == 0) prm->flag_pending = 0;
 }
 
 // te_mid (3), force (3), max strain (1)
@@ -189,7 +194,7 @@ int flag_max_cluster() {
   return cached;
 }
 
-void launch_flag(const Consts&, Params* prm, const Flag& fl, cudaStream_t s) {
+void launch_flag(Params* prm, const Flag& fl, bool force, cudaStream_t s) {
   if (fl.nv == 0) return;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(fl.cluster);
@@ -203,7 +208,7 @@ void launch_flag(const Consts&, Params* prm, const Flag& fl, cudaStream_t s) {
   attr.val.clusterDim.z = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_flag, (const Params*)prm, fl);
+  cudaLaunchKernelEx(&cfg, k_flag, prm, fl, force ? 1 : 0);
 }
 
 void launch_flag_stats(const Flag& fl, double* out, cudaStream_t s) {

@@ -17,52 +17,112 @@ constexpr int TJ = 8;        // threads along y
 constexpr int XCHUNK = 8;    // x planes per block in 3-D kernels
 
 // ---------------------------------------------------------------- parameters
-// dt (fixed or CFL), AB2 weights, implicit diffusion number, sub-steps.
+// Warm-up of the segmented implicit line solves: the LU recursions of the
+// factors (1 - a L_d) forget their start like rho^k, rho = exp(-theta), so a
+// segment started H points early is exact to rho^H (below 1e-17 in FP64,
+// 1e-9 in FP32).
+constexpr int SEG = 32;      // outputs per thread in the implicit line solves
+constexpr int HMAX = 24;     // largest warm-up the segments carry
+
+__device__ inline double af_theta(double r) { return 2.0 * asinh(0.5 / sqrt(r)); }
+
+// dt (fixed or CFL), AB2 weights, implicit diffusion number, sub-steps, and the
+// LU inverse pivots of the x factors (closed form, one entry per thread):
+//   Dirichlet start (u):      1/p_k = rho (1 - rho^{2k})   / (1 - rho^{2k+2})
+//   reflection start (v, w):  1/p_k = rho (1 - rho^{2k-1}) / (1 - rho^{2k+1})
+// Each kernel writes only the fields it owns: the structural update runs
+// concurrently and owns flag_pending.
 __global__ void k_begin_step(Consts c, Params* prm, const double* __restrict__ partial,
-                             int n_partial) {
+                             int n_partial, double* __restrict__ ipt, float* __restrict__ iptf,
+                             double* __restrict__ taps, float* __restrict__ tapsf, double tol) {
   __shared__ double scratch[32];
+  __shared__ double sh_r;
   double m = 0.0;
   for (int b = threadIdx.x; b < n_partial; b += blockDim.x) m = fmax(m, partial[b]);
   m = block_max(m, scratch);
-  if (threadIdx.x != 0) return;
-  Params p = *prm;
-  p.speed_max = m;
-  p.slip_max = 0.0;
-  double dt = p.dt_fixed > 0.0 ? p.dt_fixed : p.cfl * c.h / m;
-  if (!isfinite(m) || !(dt > 0.0) || !isfinite(dt)) {
-    p.error |= ERR_NONFINITE;
-    dt = p.dt_fixed > 0.0 ? p.dt_fixed : 0.0;
+  if (threadIdx.x == 0) {
+    const double dt_fixed = prm->dt_fixed;
+    int err = 0;
+    double dt = dt_fixed > 0.0 ? dt_fixed : prm->cfl * c.h / m;
+    if (!isfinite(m) || !(dt > 0.0) || !isfinite(dt)) {
+      err |= ERR_NONFINITE;
+      dt = dt_fixed > 0.0 ? dt_fixed : 1e-300;
+    }
+    double alpha = 1.0, beta = 0.0;
+    if (!prm->first) {
+      alpha = 1.0 + dt / (2.0 * prm->dt_old);
+      beta = -dt / (2.0 * prm->dt_old);
+    }
+    double r = c.nu * dt / (2.0 * c.h * c.h);
+    if (!(r > 0.0) || !isfinite(r)) {
+      err |= ERR_AF_RANGE;
+      r = 1e-300;
+    }
+    const double th = af_theta(r);
+    const double rho = exp(-th);
+    int H = (int)ceil(log(tol) / log(rho));
+    if (!(H >= 1)) H = 1;
+    if (H > HMAX) {
+      err |= ERR_AF_RANGE;
+      H = HMAX;
+    }
+    const double ns = ceil(dt * c.omega_max);
+    prm->speed_max = m;
+    prm->slip_max = 0.0;
+    prm->dt = dt;
+    prm->alpha = alpha;
+    prm->beta = beta;
+    prm->r = r;
+    prm->af_rho = rho;
+    prm->af_h = H;
+    prm->n_sub = ns < 1.0 ? 1 : (ns > 1e6 ? 1000000 : (int)ns);
+    if (err) prm->error |= err;
+    sh_r = r;
   }
-  if (p.first) {
-    p.alpha = 1.0;
-    p.beta = 0.0;
-  } else {
-    p.alpha = 1.0 + dt / (2.0 * p.dt_old);
-    p.beta = -dt / (2.0 * p.dt_old);
+  __syncthreads();
+  const double th = af_theta(sh_r);
+  const double rho = exp(-th);
+  for (int k = 1 + threadIdx.x; k <= c.nx; k += blockDim.x) {
+    const double a = rho * expm1(-2.0 * k * th) / expm1(-(2.0 * k + 2.0) * th);
+    const double b = rho * expm1(-(2.0 * k - 1.0) * th) / expm1(-(2.0 * k + 1.0) * th);
+    ipt[k] = a;
+    ipt[c.nx + 2 + k] = b;
+    iptf[k] = (float)a;
+    iptf[c.nx + 2 + k] = (float)b;
   }
-  p.dt = dt;
-  p.r = c.nu * dt / (2.0 * c.h * c.h);
-  if (!(p.r > 0.0)) {
-    p.error |= ERR_AF_RANGE;
-    p.r = 1e-300;
+  // free-space taps for the reflected x solve: (1/r) rho^{m+1} / (1 - rho^2)
+  for (int m = threadIdx.x; m <= HMAX; m += blockDim.x) {
+    const double v = (1.0 / sh_r) * exp(-(double)(m + 1) * th) / (-expm1(-2.0 * th));
+    taps[c.ny + c.nz + m] = v;
+    tapsf[c.ny + c.nz + m] = (float)v;
   }
-  double ns = ceil(dt * c.omega_max);
-  p.n_sub = ns < 1.0 ? 1 : (ns > 1e6 ? 1000000 : (int)ns);
-  *prm = p;
+  // taps of the exact periodic inverse of r (q - S - S^{-1}) on n points:
+  //   t_m = (1/r) rho / (1 - rho^2) (rho^m + rho^{n-m}) / (1 - rho^n),  m = 0..n-1
+  const double pre = (1.0 / sh_r) * rho / (-expm1(-2.0 * th));
+  for (int dir = 0; dir < 2; ++dir) {
+    const int n = dir == 0 ? c.ny : c.nz;
+    const double den = -expm1(-(double)n * th);
+    double* t = taps + (dir == 0 ? 0 : c.ny);
+    float* tf = tapsf + (dir == 0 ? 0 : c.ny);
+    for (int m = threadIdx.x; m < n; m += blockDim.x) {
+      const double v = pre * (exp(-(double)m * th) + exp(-(double)(n - m) * th)) / den;
+      t[m] = v;
+      tf[m] = (float)v;
+    }
+  }
 }
 
 // after the projection: advance the clock
 __global__ void k_end_step(Params* prm) {
-  Params p = *prm;
-  p.t += p.dt;
-  p.dt_old = p.dt;
-  p.step += 1;
-  p.first = 0;
-  *prm = p;
+  prm->t += prm->dt;
+  prm->dt_old = prm->dt;
+  prm->step += 1;
+  prm->first = 0;
 }
 
 // ---------------------------------------------------------------- RHS (A2)
 // RHS = dt [ -(alpha N^n + beta N^{n-1}) - G p^n + nu L u^n ], N in flux form.
+// One thread per (y, z) column and XCHUNK x planes; neighbours through L1.
 template <class T>
 __global__ void __launch_bounds__(TK* TJ)
 k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
@@ -177,134 +237,143 @@ __global__ void k_outflow(Consts c, const Params* __restrict__ prm, T* __restric
 }
 
 // ---------------------------------------------------------------- implicit factors (A3)
-// Each factor (1 - a L_d) is (r / 1)(q x_k - x_{k-1} - x_{k+1}) with
-// q = 2 + 1/r = rho + 1/rho, rho = exp(-theta), theta = 2 asinh(1 / (2 sqrt r)).
-// x lines (Dirichlet start for u, inflow-reflection start for v, w) use the
-// closed-form LU pivots p_k; periodic y, z lines use the factorisation
-// q - S - S^{-1} = (1/rho)(1 - rho S^{-1})(1 - rho S) as two first-order
-// recursions with periodic starting values.
-__device__ inline double af_theta(double r) { return 2.0 * asinh(0.5 / sqrt(r)); }
-
+// Each factor (1 - a L_d), a = nu dt / 2, is r (q x_k - x_{k-1} - x_{k+1}) with
+// r = a / h^2, q = 2 + 1/r = rho + 1/rho, rho = exp(-theta),
+// theta = 2 asinh(1 / (2 sqrt r)).
+// x lines: LU (Thomas) recursions y_k = (e_k + y_{k-1}) / p_k,
+//   x_k = y_k + x_{k+1} / p_k with the closed-form pivots tabulated per step
+//   (u: Dirichlet rows 1..nx-1, the outflow-face increment moved to the RHS;
+//   v, w: rows 0..nx-1 with the inflow reflection ghost).
+// periodic y, z lines: q - S - S^{-1} = (1/rho)(1 - rho S^{-1})(1 - rho S),
+//   i.e. y_j = e_j + rho y_{j-1}, z_j = y_j + rho z_{j+1}, x = rho z.
+// Every thread solves SEG consecutive points of one line, starting both
+// recursions H = af_h points outside its segment (periodic lines wrap), so
+// the lines are solved by many threads without a serial sweep; segments read
+// each other's halos, so every solve writes to a different buffer.
 template <class T>
-__global__ void k_af_x(Consts c, const Params* __restrict__ prm, T* __restrict__ d0,
-                       T* __restrict__ d1, T* __restrict__ d2, const T* __restrict__ o0,
-                       const T* __restrict__ o1, const T* __restrict__ o2) {
-  extern __shared__ unsigned char smem_raw[];
-  T* ip_dir = reinterpret_cast<T*>(smem_raw);   // [1 .. nx-1]
-  T* ip_gh = ip_dir + (c.nx + 1);               // [1 .. nx]
-  const double r = prm->r;
-  const double th = af_theta(r);
-  const double rho = exp(-th);
-  for (int kk = 1 + threadIdx.x; kk <= c.nx; kk += blockDim.x) {
-    ip_dir[kk] = (T)(rho * expm1(-2.0 * kk * th) / expm1(-(2.0 * kk + 2.0) * th));
-    ip_gh[kk] = (T)(rho * expm1(-(2.0 * kk - 1.0) * th) / expm1(-(2.0 * kk + 1.0) * th));
-  }
-  __syncthreads();
+__global__ void __launch_bounds__(128)
+k_af_x(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
+       const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
+       T* __restrict__ e0, T* __restrict__ e1, T* __restrict__ e2, const T* __restrict__ o0,
+       const T* __restrict__ o1, const T* __restrict__ o2) {
   const int P = c.ny * c.nz;
   const int jk = blockIdx.x * blockDim.x + threadIdx.x;
-  const int comp = blockIdx.y;
   if (jk >= P) return;
-  const T ir = (T)(1.0 / r);
-  const int nx = c.nx;
-  if (comp == 0) {
-    T* d = d0 + jk;
-    T y = 0;
-    for (int i = 1; i <= nx - 1; ++i) {
-      T e = d[(size_t)i * P] * ir;
-      if (i == nx - 1) e += o0[jk];
-      y = (e + y) * ip_dir[i];
-      d[(size_t)i * P] = y;
+  const int comp = blockIdx.z;
+  const int m = comp == 0 ? c.nx - 1 : c.nx;   // unknowns k = 1..m
+  const int ioff = comp == 0 ? 0 : -1;         // plane i = k + ioff
+  const int k0 = 1 + blockIdx.y * SEG;
+  if (k0 > m) return;
+  const int k1 = min(k0 + SEG, m + 1);
+  const int H = prm->af_h;
+  const T* ip = ipt + (comp == 0 ? 0 : c.nx + 2);
+  const T ir = (T)(1.0 / prm->r);
+  const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + jk + (size_t)ioff * P;
+  T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + jk + (size_t)ioff * P;
+  const T ob = (comp == 0 ? o0 : comp == 1 ? o1 : o2)[jk];
+  const int ks = max(1, k0 - H);
+  const int ke = min(m, k1 - 1 + H);
+  T y = 0;
+  for (int k = ks; k < k0; ++k) {
+    T e = d[(size_t)k * P] * ir;
+    if (k == m) e += ob;
+    y = (e + y) * ip[k];
+  }
+  T yr[SEG + HMAX];
+#pragma unroll
+  for (int q = 0; q < SEG + HMAX; ++q) {
+    const int k = k0 + q;
+    if (k <= ke) {
+      T e = d[(size_t)k * P] * ir;
+      if (k == m) e += ob;
+      y = (e + y) * ip[k];
+      yr[q] = y;
     }
-    T x = 0;
-    for (int i = nx - 1; i >= 1; --i) {
-      x = d[(size_t)i * P] + x * ip_dir[i];
-      d[(size_t)i * P] = x;
-    }
-  } else {
-    T* d = (comp == 1 ? d1 : d2) + jk;
-    const T ob = (comp == 1 ? o1 : o2)[jk];
-    T y = 0;
-    for (int i = 0; i <= nx - 1; ++i) {
-      T e = d[(size_t)i * P] * ir;
-      if (i == nx - 1) e += ob;
-      y = (e + y) * ip_gh[i + 1];
-      d[(size_t)i * P] = y;
-    }
-    T x = 0;
-    for (int i = nx - 1; i >= 0; --i) {
-      x = d[(size_t)i * P] + x * ip_gh[i + 1];
-      d[(size_t)i * P] = x;
+  }
+  T x = 0;
+#pragma unroll
+  for (int q = SEG + HMAX - 1; q >= 0; --q) {
+    const int k = k0 + q;
+    if (k <= ke) {
+      x = yr[q] + x * ip[k];
+      if (k < k1) out[(size_t)k * P] = x;
     }
   }
 }
 
-// periodic line solve along a strided line of n values starting at `d`
-template <class T>
-__device__ inline void periodic_line(T* d, int n, size_t stride, double r) {
-  const double th = af_theta(r);
-  const T rho = (T)exp(-th);
-  const T inv1m = (T)(-1.0 / expm1(-(double)n * th));
-  const T ir = (T)(1.0 / r);
-  // y = (1 - rho S^{-1})^{-1} e, periodic: y_0 = sum_m rho^m e_{-m} / (1 - rho^n)
-  T acc = 0, pw = 1;
-  for (int m = 0; m < n; ++m) {
-    if (pw < (T)1e-30) break;
-    acc += pw * d[(size_t)((n - m) % n) * stride];
-    pw *= rho;
+// periodic segment solve; in(j), store(j, x) address the line
+template <class T, class In, class Out>
+__device__ inline void periodic_segment(int n, int j0, int j1, int H, T rho, T ir, In in, Out store) {
+  T y = 0;
+  int j = (j0 - H) % n;
+  if (j < 0) j += n;
+  for (int q = 0; q < H; ++q) {
+    y = in(j) * ir + rho * y;
+    if (++j == n) j = 0;
   }
-  T y = acc * ir * inv1m;
-  d[0] = y;
-  for (int jj = 1; jj < n; ++jj) {
-    y = d[(size_t)jj * stride] * ir + rho * y;
-    d[(size_t)jj * stride] = y;
+  // j == j0 here
+  const int len = j1 - j0 + H;   // stored forward values
+  T yr[SEG + HMAX];
+#pragma unroll
+  for (int q = 0; q < SEG + HMAX; ++q) {
+    if (q < len) {
+      y = in(j) * ir + rho * y;
+      yr[q] = y;
+      if (++j == n) j = 0;
+    }
   }
-  // z = (1 - rho S)^{-1} y, periodic: z_{n-1} = sum_m rho^m y_{n-1+m} / (1 - rho^n)
-  acc = 0;
-  pw = 1;
-  for (int m = 0; m < n; ++m) {
-    if (pw < (T)1e-30) break;
-    acc += pw * d[(size_t)((n - 1 + m) % n) * stride];
-    pw *= rho;
-  }
-  T z = acc * inv1m;
-  d[(size_t)(n - 1) * stride] = rho * z;
-  for (int jj = n - 2; jj >= 0; --jj) {
-    z = d[(size_t)jj * stride] + rho * z;
-    d[(size_t)jj * stride] = rho * z;
+  T z = 0;
+#pragma unroll
+  for (int q = SEG + HMAX - 1; q >= 0; --q) {
+    if (q < len) {
+      z = yr[q] + rho * z;
+      if (q < j1 - j0) store(j0 + q, rho * z);
+    }
   }
 }
 
-// y lines: one thread per (i, k), walking y with stride nz (coalesced in k)
+// y lines: threads over (k, segment), walking y with stride nz (coalesced in k)
 template <class T>
-__global__ void k_af_y(Consts c, const Params* __restrict__ prm, T* __restrict__ d0,
-                       T* __restrict__ d1, T* __restrict__ d2) {
+__global__ void __launch_bounds__(128)
+k_af_y(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
+       const T* __restrict__ e1, const T* __restrict__ e2, T* __restrict__ d0, T* __restrict__ d1,
+       T* __restrict__ d2) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
+  const int nseg = (c.ny + SEG - 1) / SEG;
+  const int i = blockIdx.y / nseg, seg = blockIdx.y - i * nseg;
   const int comp = blockIdx.z;
   if (k >= c.nz) return;
   if (comp == 0 ? (i < 1 || i > c.nx - 1) : (i > c.nx - 1)) return;
-  T* d = (comp == 0 ? d0 : (comp == 1 ? d1 : d2)) + (size_t)i * plane(c) + k;
-  periodic_line(d, c.ny, (size_t)c.nz, prm->r);
+  const size_t base = (size_t)i * plane(c) + k;
+  const T* in = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + base;
+  T* out = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + base;
+  const int j0 = seg * SEG, j1 = min(j0 + SEG, c.ny);
+  const size_t st = (size_t)c.nz;
+  periodic_segment<T>(c.ny, j0, j1, prm->af_h, (T)prm->af_rho, (T)(1.0 / prm->r),
+                      [&](int j) { return in[(size_t)j * st]; },
+                      [&](int j, T v) { out[(size_t)j * st] = v; });
 }
 
-// z lines are contiguous: a block stages ZL lines in shared memory, one
-// thread per line solves, then u* = u^n + du is written back.
-constexpr int ZL = 32;
+// z lines are contiguous: a block stages whole lines in shared memory, threads
+// solve segments, and u* = u^n + du is written back.
 template <class T>
-__global__ void __launch_bounds__(128)
-k_af_z(Consts c, const Params* __restrict__ prm, T* __restrict__ d0, T* __restrict__ d1,
-       T* __restrict__ d2, T* __restrict__ u, T* __restrict__ v, T* __restrict__ w) {
+__global__ void __launch_bounds__(256)
+k_af_z(Consts c, const Params* __restrict__ prm, const T* __restrict__ d0,
+       const T* __restrict__ d1, const T* __restrict__ d2, T* __restrict__ u, T* __restrict__ v,
+       T* __restrict__ w) {
   extern __shared__ unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   const int nz = c.nz, ny = c.ny;
   const int ld = nz + 1;
+  const int nseg = (nz + SEG - 1) / SEG;
+  const int zl = blockDim.x / nseg;                    // lines per block
   const int comp = blockIdx.y;
-  const int first = comp == 0 ? ny : 0;               // u: planes 1..nx-1
+  const int first = comp == 0 ? ny : 0;                // u: planes 1..nx-1
   const int last = c.nx * ny;                          // exclusive
-  const int L0 = first + blockIdx.x * ZL;
+  const int L0 = first + blockIdx.x * zl;
   if (L0 >= last) return;
-  const int nl = min(ZL, last - L0);
-  T* d = comp == 0 ? d0 : (comp == 1 ? d1 : d2);
+  const int nl = min(zl, last - L0);
+  const T* d = comp == 0 ? d0 : (comp == 1 ? d1 : d2);
   T* q = comp == 0 ? u : (comp == 1 ? v : w);
   const size_t base = (size_t)L0 * nz;
   for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
@@ -312,11 +381,148 @@ k_af_z(Consts c, const Params* __restrict__ prm, T* __restrict__ d0, T* __restri
     s[l * ld + kk] = d[base + e];
   }
   __syncthreads();
-  if (threadIdx.x < nl) periodic_line(s + threadIdx.x * ld, nz, 1, prm->r);
+  // consecutive threads take consecutive lines (row stride nz + 1: no bank conflicts)
+  const int seg = threadIdx.x / zl, l = threadIdx.x - seg * zl;
+  T xo[SEG];
+  const int j0 = seg * SEG, j1 = min(j0 + SEG, nz);
+  if (l < nl) {
+    const T* line = s + l * ld;
+    periodic_segment<T>(nz, j0, j1, prm->af_h, (T)prm->af_rho, (T)(1.0 / prm->r),
+                        [&](int j) { return line[j]; },
+                        [&](int j, T val) { xo[j - j0] = val; });
+  }
+  __syncthreads();
+  if (l < nl) {
+#pragma unroll
+    for (int t = 0; t < SEG; ++t)
+      if (j0 + t < j1) s[l * ld + j0 + t] = xo[t];
+  }
   __syncthreads();
   for (int e = threadIdx.x; e < nl * nz; e += blockDim.x) {
-    const int l = e / nz, kk = e - l * nz;
-    q[base + e] += s[l * ld + kk];
+    const int ll = e / nz, kk = e - ll * nz;
+    q[base + e] += s[ll * ld + kk];
+  }
+}
+
+// FP32 periodic z factor: whole lines (plus a periodic halo) staged in shared
+// memory and multiplied by the exact periodic inverse, x_j = sum_m t_|m| e_{j+m}
+// (taps t from k_begin_step), truncated to |m| <= H where rho^H is below the
+// FP32 rounding (all n taps when 2H + 1 >= n). No serial dependence.
+template <class T>
+__device__ inline void tap_range(int n, int H, int& lo, int& hi) {
+  if (2 * H + 1 < n) {
+    lo = H;
+    hi = H;
+  } else {
+    lo = (n - 1) / 2;
+    hi = n / 2;
+  }
+}
+
+// x factor in FP32: the Dirichlet rows (u: du_0 = 0; v, w: du_{-1} = -du_0;
+// the outflow increment moved into the last right-hand side so the far end is
+// homogeneous) are reproduced exactly by the odd reflection of the right-hand
+// side about the two ends (about face 0 for u, about x = -h/2 for v, w, and
+// about plane nx), so the solve is the free-space inverse of
+// r (q - S - S^{-1}), t_m = (1/r) rho^{|m|+1} / (1 - rho^2), applied to the
+// reflected data and truncated to |m| <= H. A block stages XC planes plus
+// the halo of 32 consecutive (y, z) columns.
+constexpr int XC = 64;
+template <class T>
+__global__ void __launch_bounds__(256)
+k_af_xc(Consts c, const Params* __restrict__ prm, const T* __restrict__ taps,
+        const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
+        T* __restrict__ e0, T* __restrict__ e1, T* __restrict__ e2, const T* __restrict__ o0,
+        const T* __restrict__ o1, const T* __restrict__ o2) {
+  extern __shared__ unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  const int P = c.ny * c.nz;
+  const int comp = blockIdx.z;
+  const int nx = c.nx;
+  // unknown planes: u 1..nx-1 (reflection about 0 and nx); v, w 0..nx-1
+  // (reflection about -1/2 and nx)
+  const int ilo = comp == 0 ? 1 : 0, ihi = nx - 1;
+  const int i0 = ilo + blockIdx.y * XC;
+  if (i0 > ihi) return;
+  const int ni = min(XC, ihi - i0 + 1);
+  const int H = prm->af_h;
+  const int col0 = blockIdx.x * 32;
+  const int ncol = min(32, P - col0);
+  const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + col0;
+  T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + col0;
+  const T* ob = (comp == 0 ? o0 : comp == 1 ? o1 : o2) + col0;
+  const T rr_ = (T)prm->r;
+  const int rows = ni + 2 * H;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int e = tid; e < rows * 32; e += 256) {
+    const int rr = e >> 5, q = e & 31;
+    if (q >= ncol) continue;
+    int i = i0 - H + rr;
+    T sg = 1;
+    // reflect into the unknowns (odd extension)
+    for (int it = 0; it < 4; ++it) {
+      if (comp == 0) {
+        if (i <= 0) { i = -i; sg = -sg; }
+        if (i >= nx) { i = 2 * nx - i; sg = -sg; }
+      } else {
+        if (i < 0) { i = -1 - i; sg = -sg; }
+        if (i >= nx) { i = 2 * nx - i; sg = -sg; }
+      }
+    }
+    T val = 0;
+    if (i >= ilo && i <= ihi) {
+      val = d[(size_t)i * P + q];
+      if (i == ihi) val += ob[q] * rr_;
+    }
+    s[e] = sg * val;
+  }
+  __syncthreads();
+  const int q = threadIdx.x;
+  if (q >= ncol) return;
+  for (int rr = threadIdx.y; rr < ni; rr += 8) {
+    const T* sc = s + (rr + H) * 32 + q;
+    T acc = taps[0] * sc[0];
+    for (int m = 1; m <= H; ++m) acc += taps[m] * (sc[m * 32] + sc[-m * 32]);
+    out[(size_t)(i0 + rr) * P + q] = acc;
+  }
+}
+
+// z factor: lines contiguous; u* = u^n + du written to the velocity
+constexpr int ZLC = 8;
+template <class T>
+__global__ void __launch_bounds__(256)
+k_af_zc(Consts c, const Params* __restrict__ prm, const T* __restrict__ taps,
+        const T* __restrict__ e0, const T* __restrict__ e1, const T* __restrict__ e2,
+        T* __restrict__ u, T* __restrict__ v, T* __restrict__ w) {
+  extern __shared__ unsigned char smem_raw[];
+  T* s = reinterpret_cast<T*>(smem_raw);
+  const int n = c.nz, ny = c.ny;
+  const int comp = blockIdx.y;
+  const int first = comp == 0 ? ny : 0;
+  const int last = c.nx * ny;
+  const int L0 = first + blockIdx.x * ZLC;
+  if (L0 >= last) return;
+  const int nl = min(ZLC, last - L0);
+  int lo, hi;
+  tap_range<T>(n, prm->af_h, lo, hi);
+  const int rl = n + lo + hi;
+  const T* d = comp == 0 ? e0 : (comp == 1 ? e1 : e2);
+  T* qv = comp == 0 ? u : (comp == 1 ? v : w);
+  const size_t base = (size_t)L0 * n;
+  for (int e = threadIdx.x; e < nl * rl; e += blockDim.x) {
+    const int l = e / rl, rr = e - l * rl;
+    int jj = (rr - lo) % n;
+    if (jj < 0) jj += n;
+    s[e] = d[base + (size_t)l * n + jj];
+  }
+  __syncthreads();
+  const int lg = __ffs(n) - 1;
+  for (int e = threadIdx.x; e < nl * n; e += blockDim.x) {
+    const int l = e >> lg, jj = e & (n - 1);
+    const T* sl = s + l * rl + jj + lo;
+    T acc = 0;
+    for (int m = -lo; m <= hi; ++m) acc += taps[m < 0 ? -m : m] * sl[m];
+    qv[base + e] += acc;
   }
 }
 
@@ -386,7 +592,7 @@ k_project(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
   const bool act = (k < c.nz && j < c.ny);
   const int ny = c.ny, nz = c.nz, nx = c.nx;
   const size_t P = plane(c);
-  double smax = 0.0;
+  T smaxT = 0;
   if (act) {
     const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
     const int km = k == 0 ? nz - 1 : k - 1, kp = k == nz - 1 ? 0 : k + 1;
@@ -424,22 +630,22 @@ k_project(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
       const T un1 = unew(i + 1);
       const T vn1 = va[at(i, jp, k)] - gdt * (phi[at(i, jp, k)] - ph);
       const T wn1 = wa[at(i, j, kp)] - gdt * (phi[at(i, j, kp)] - ph);
-      double sp = fabs(0.5 * ((double)un + (double)un1)) + fabs(0.5 * ((double)vn + (double)vn1)) +
-                  fabs(0.5 * ((double)wn + (double)wn1));
-      if (!isfinite(sp)) sp = INFINITY;
-      smax = fmax(smax, sp);
+      T sp = fabs((T)0.5 * (un + un1)) + fabs((T)0.5 * (vn + vn1)) + fabs((T)0.5 * (wn + wn1));
+      if (!isfinite(sp)) sp = (T)INFINITY;
+      smaxT = fmax(smaxT, sp);
     }
   }
-  // flatten the 2-D block for the reduction
+  // flatten the 2-D block for the reduction (in T: a max is exact)
   const int tid = threadIdx.y * TK + threadIdx.x;
-  double v = warp_max(smax);
-  __shared__ double wmax[TK * TJ / 32];
+  T v = smaxT;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __shared__ T wmax[TK * TJ / 32];
   if ((tid & 31) == 0) wmax[tid >> 5] = v;
   __syncthreads();
   if (tid == 0) {
-    double m = 0.0;
+    T m = 0;
     for (int q = 0; q < TK * TJ / 32; ++q) m = fmax(m, wmax[q]);
-    partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = m;
+    partial[(blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = (double)m;
   }
 }
 
@@ -485,7 +691,9 @@ static dim3 grid3(const Consts& c, int planes) {
 
 template <class T>
 void launch_begin_step(const Consts& c, const Fields<T>& f, cudaStream_t s) {
-  k_begin_step<<<1, 1024, 0, s>>>(c, f.prm, f.partial, f.n_partial);
+  const double tol = sizeof(T) == 8 ? 1e-17 : 1e-9;
+  k_begin_step<<<1, 1024, 0, s>>>(c, f.prm, f.partial, f.n_partial, f.ipt, f.iptf, f.taps,
+                                  f.tapsf, tol);
 }
 
 template <class T>
@@ -505,22 +713,45 @@ void launch_outflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s
 template <class T>
 void launch_af_x(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   const int P = c.ny * c.nz;
-  const size_t shx = 2 * (size_t)(c.nx + 1) * sizeof(T);
-  k_af_x<T><<<dim3((P + 127) / 128, 3), 128, shx, s>>>(c, f.prm, f.d[0], f.d[1], f.d[2],
-                                                        f.dout[0], f.dout[1], f.dout[2]);
+  if constexpr (sizeof(T) == 4) {
+    const size_t sh = (size_t)(XC + 2 * HMAX) * 32 * sizeof(T);
+    k_af_xc<T><<<dim3((P + 31) / 32, (c.nx + XC - 1) / XC, 3), dim3(32, 8), sh, s>>>(
+        c, f.prm, (const T*)f.tapsf + c.ny + c.nz, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2],
+        f.dout[0], f.dout[1], f.dout[2]);
+    (void)cur;
+    return;
+  }
+  const int nseg = (c.nx + SEG - 1) / SEG;
+  const T* tab;
+  if constexpr (sizeof(T) == 8) tab = (const T*)f.ipt; else tab = (const T*)f.iptf;
+  k_af_x<T><<<dim3((P + 127) / 128, nseg, 3), 128, 0, s>>>(c, f.prm, tab, f.d[0], f.d[1], f.d[2],
+                                                            f.e[0], f.e[1], f.e[2], f.dout[0],
+                                                            f.dout[1], f.dout[2]);
   (void)cur;
 }
 
 template <class T>
 void launch_af_y(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
-  k_af_y<T><<<dim3((c.nz + 63) / 64, c.nx, 3), 64, 0, s>>>(c, f.prm, f.d[0], f.d[1], f.d[2]);
+  const int nseg = (c.ny + SEG - 1) / SEG;
+  k_af_y<T><<<dim3((c.nz + 127) / 128, c.nx * nseg, 3), 128, 0, s>>>(c, f.prm, f.e[0], f.e[1],
+                                                                       f.e[2], f.d[0], f.d[1], f.d[2]);
   (void)cur;
 }
 
+static int af_z_lines(const Consts& c) { return 256 / ((c.nz + SEG - 1) / SEG); }
+
 template <class T>
 void launch_af_z(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
-  const size_t shz = (size_t)ZL * (c.nz + 1) * sizeof(T);
-  k_af_z<T><<<dim3((c.nx * c.ny + ZL - 1) / ZL, 3), 128, shz, s>>>(
+  if constexpr (sizeof(T) == 4) {
+    const int halo = HMAX < c.nz / 2 ? HMAX : c.nz / 2;
+    const size_t sh = (size_t)ZLC * (c.nz + 2 * halo) * sizeof(T);
+    k_af_zc<T><<<dim3((c.nx * c.ny + ZLC - 1) / ZLC, 3), 256, sh, s>>>(
+        c, f.prm, (const T*)f.tapsf + c.ny, f.d[0], f.d[1], f.d[2], f.u[cur], f.v[cur], f.w[cur]);
+    return;
+  }
+  const int zl = af_z_lines(c);
+  const size_t shz = (size_t)zl * (c.nz + 1) * sizeof(T);
+  k_af_z<T><<<dim3((c.nx * c.ny + zl - 1) / zl, 3), 256, shz, s>>>(
       c, f.prm, f.d[0], f.d[1], f.d[2], f.u[cur], f.v[cur], f.w[cur]);
 }
 
@@ -567,10 +798,10 @@ void launch_stats(const Consts& c, const Fields<T>& f, int cur, double* out, cud
 }
 
 void fluid_set_attributes() {
+  cudaFuncSetAttribute(k_af_xc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_af_zc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_z<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_z<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_af_x<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_af_x<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 int partial_count(const Consts& c) {

@@ -85,6 +85,11 @@ template <class T>
 __global__ void k_ib_interp(Consts c, Params* prm, Markers m, Flag fl, const T* __restrict__ u,
                             const T* __restrict__ v, const T* __restrict__ w) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l == 0 && m.nf > 0) {   // hand this step's dt to the pending structural update
+    prm->flag_dt = prm->dt;
+    prm->flag_nsub = prm->n_sub;
+    prm->flag_pending = 1;
+  }
   double slip = 0.0;
   if (l < m.nm) {
     double X, Y, Z, U[3], dv;

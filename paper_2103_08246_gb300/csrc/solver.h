@@ -12,6 +12,11 @@ struct Fields {
   T* p;                       // pressure (nx * ny * nz)
   T* n[3];                    // nonlinear term N^{n-1}, overwritten with N^n
   T* d[3];                    // RHS, then the velocity increments
+  T* e[3];                    // second buffer of the implicit line solves
+  double* ipt;                // x-factor LU inverse pivots (2 x (nx + 2)), per step
+  float* iptf;                // the same in FP32
+  double* taps;               // periodic inverse taps along y (ny), z (nz), then free-space x taps
+  float* tapsf;               // the same in FP32
   T* phi;                     // divergence -> transforms -> pressure correction
   T* ptab;                    // Poisson Thomas inverse pivots per mode
   T* dout[3];                 // outflow-plane increments (ny * nz each)
@@ -42,10 +47,13 @@ struct Flag {
   int* spring = nullptr;      // 2 vertex ids per spring
   double* l0 = nullptr;       // rest lengths
   double k_s = 0.0;
-  int n_hinge = 0;
-  int* hinge = nullptr;       // 6 vertex ids: triangle A (3), triangle B (3)
-  double* k_hinge = nullptr;
-  double* slot = nullptr;     // 3 doubles per force slot (2 per spring, 6 per hinge)
+  int n_tri = 0;
+  int* tri = nullptr;         // 3 vertex ids per triangle (both triangulations)
+  int* tri_nb = nullptr;      // 3 per triangle: triangle across each hinge, or -1
+  double* tri_k = nullptr;    // 3 per triangle: stiffness of that hinge
+  double* tri_n = nullptr;    // 3 per triangle: unit normal (scratch)
+  double* tri_inv = nullptr;  // 1 per triangle: 1 / |N| (scratch)
+  double* slot = nullptr;     // 3 doubles per force slot: 3 per triangle, then 2 per spring
   int* csr_off = nullptr;     // nv + 1 offsets into csr_idx
   int* csr_idx = nullptr;     // slot ids contributing to each vertex
   int cluster = 1;            // CTAs cooperating in the structure kernel
@@ -81,7 +89,7 @@ template <class T> void launch_ib(const Consts& c, const Fields<T>& f, const Mar
                                   const Flag& fl, int cur, cudaStream_t s);
 
 // ---- flag.cu
-void launch_flag(const Consts& c, Params* prm, const Flag& fl, cudaStream_t s);
+void launch_flag(Params* prm, const Flag& fl, bool force, cudaStream_t s);
 void launch_flag_stats(const Flag& fl, double* out, cudaStream_t s);
 int flag_max_cluster();
 
