@@ -603,6 +603,7 @@ int step_impl(ibm_state* s, double dt, int nsteps) {
   CK(cudaMemcpyAsync(s->hprm, f.prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const Params& p = *s->hprm;
+  if (p.error & ERR_TIMEOUT) return IBM_ETIMEOUT;
   if (p.error & ERR_AF_RANGE) return IBM_EINVAL;
   if (p.error) return IBM_EDIVERGED;
   if (nsteps > 0 && p.dt * p.speed_max / s->c.h > s->cfl_limit) return IBM_EDIVERGED;

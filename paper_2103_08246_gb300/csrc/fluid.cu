@@ -8,6 +8,7 @@
 // 0..nx; v, w: cells 0..nx-1 plus the outflow ghost plane nx), p and phi nx.
 #include <cmath>
 
+#include "async_copy.cuh"
 #include "solver.h"
 
 namespace ibm {
@@ -210,6 +211,193 @@ k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
         d2[id] = dt * (-(alpha * N + beta * Np) - Gp + nu * L);
       }
     }
+  }
+}
+
+// Pipelined RHS (same arithmetic as k_rhs): a block owns TJ whole z-rows
+// of y and marches XR x-planes. For every x plane one thread issues bulk
+// asynchronous copies (TMA engine) of the rows j0-1 .. j0+TJ of u, v, w and
+// j0-1 .. j0+TJ-1 of p into a STAGES-deep shared-memory ring, completing on
+// one mbarrier per slot; the block computes plane i from planes i-1, i, i+1
+// while the copies of the next planes are in flight. Whole rows make the
+// periodic z wrap an index mask and every copy 16-byte aligned.
+constexpr int RSTAGES = 4;
+template <class T, int TJR>
+struct RhsRing {
+  // rows of one stage: u, v, w with halo, p with low-side halo, N^{n-1} x 3
+  static constexpr int ROWS = 3 * (TJR + 2) + (TJR + 1) + 3 * TJR;
+};
+constexpr int RTHREADS = 512;
+
+template <class T, int TJR>
+__global__ void __launch_bounds__(RTHREADS, 1)
+k_rhs_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ u,
+           const T* __restrict__ v, const T* __restrict__ w, const T* __restrict__ p,
+           T* __restrict__ n0, T* __restrict__ n1, T* __restrict__ n2, T* __restrict__ d0,
+           T* __restrict__ d1, T* __restrict__ d2, int XR) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t full[RSTAGES];
+  const int nx = c.nx, ny = c.ny, nz = c.nz;
+  const int tid = threadIdx.x;
+  const int j0 = blockIdx.x * TJR;
+  const int ib = blockIdx.y * XR, ie = min(ib + XR, nx);
+  const size_t P = plane(c);
+  const size_t rowb = (size_t)nz * sizeof(T);
+  constexpr int RW = TJR + 2;          // rows of u, v, w in a stage
+  constexpr int ROWS = RhsRing<T, TJR>::ROWS;
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  auto stage_ptr = [&](int slot) { return ring + (size_t)slot * ROWS * nz; };
+  // stage t holds x plane q = ib - 1 + t (t = 0 .. ie - ib + 1)
+  const int nstage = ie - ib + 2;
+  auto issue = [&](int t) {
+    const int q = ib - 1 + t;
+    const int qs = q < 0 ? 0 : q;
+    const bool has_p = (q >= 0 && q <= nx - 1);
+    const int slot = t % RSTAGES;
+    T* st = stage_ptr(slot);
+    const uint32_t bytes = (uint32_t)((3 * RW + (has_p ? (TJR + 1) + 3 * TJR : 0)) * rowb);
+    mbar_arrive_expect_tx(&full[slot], bytes);
+    for (int r = 0; r < RW; ++r) {
+      int jj = j0 - 1 + r;
+      jj = jj < 0 ? jj + ny : (jj >= ny ? jj - ny : jj);
+      const size_t g = ((size_t)qs * ny + jj) * nz;
+      bulk_g2s(st + (size_t)r * nz, u + g, (uint32_t)rowb, &full[slot]);
+      bulk_g2s(st + (size_t)(RW + r) * nz, v + g, (uint32_t)rowb, &full[slot]);
+      bulk_g2s(st + (size_t)(2 * RW + r) * nz, w + g, (uint32_t)rowb, &full[slot]);
+    }
+    if (has_p) {
+      for (int r = 0; r < TJR + 1; ++r) {
+        int jj = j0 - 1 + r;
+        jj = jj < 0 ? jj + ny : jj;
+        bulk_g2s(st + (size_t)(3 * RW + r) * nz, p + ((size_t)q * ny + jj) * nz, (uint32_t)rowb,
+                 &full[slot]);
+      }
+      const int nb = 3 * RW + TJR + 1;
+      for (int r = 0; r < TJR; ++r) {
+        const size_t g = ((size_t)q * ny + j0 + r) * nz;
+        bulk_g2s(st + (size_t)(nb + r) * nz, n0 + g, (uint32_t)rowb, &full[slot]);
+        bulk_g2s(st + (size_t)(nb + TJR + r) * nz, n1 + g, (uint32_t)rowb, &full[slot]);
+        bulk_g2s(st + (size_t)(nb + 2 * TJR + r) * nz, n2 + g, (uint32_t)rowb, &full[slot]);
+      }
+    }
+  };
+  if (tid == 0) {
+    for (int sl = 0; sl < RSTAGES; ++sl) mbar_init(&full[sl], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int t = 0; t < RSTAGES && t < nstage; ++t) issue(t);
+  const T dt = (T)prm->dt, alpha = (T)prm->alpha, beta = (T)prm->beta;
+  const T nu = (T)c.nu, ih = (T)c.inv_h, ih2 = (T)(c.inv_h * c.inv_h), hf = (T)0.5;
+  const int mask = nz - 1;
+  const int ncell = TJR * nz;
+  const int lg = __ffs(nz) - 1;
+  // stage t is ready when its slot's barrier completed use number t / RSTAGES
+  auto wait_stage = [&](int t) {
+    return mbar_wait(&full[t % RSTAGES], (uint32_t)((t / RSTAGES) & 1));
+  };
+  bool ok = wait_stage(0) && wait_stage(1);
+  for (int i = ib; i < ie; ++i) {
+    const int ta = i - ib, tb = ta + 1, tc = ta + 2;
+    ok = ok && wait_stage(tc);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(&prm->error, ERR_TIMEOUT);
+        // let the copies already issued land before the block leaves
+        for (int t = tc; t < nstage && t < tc + RSTAGES; ++t) (void)wait_stage(t);
+      }
+      return;
+    }
+    const T* A = stage_ptr(ta % RSTAGES);
+    const T* B = stage_ptr(tb % RSTAGES);
+    const T* C = stage_ptr(tc % RSTAGES);
+    const T sgn = i - 1 < 0 ? (T)-1 : (T)1;   // inflow reflection ghost of v, w
+    for (int cidx = tid; cidx < ncell; cidx += blockDim.x) {
+      const int r = cidx >> lg, k = cidx & mask;
+      const int j = j0 + r;
+      if (j >= ny) continue;
+      const int kp = (k + 1) & mask, km = (k - 1) & mask;
+      const int R = (r + 1) * nz, Rm = r * nz, Rp = (r + 2) * nz;
+      // row pointers: U, V, W planes a (i-1), b (i), c (i+1); P planes a, b
+      const T* Ua = A;
+      const T* Ub = B;
+      const T* Uc = C;
+      const T* Va = A + RW * nz;
+      const T* Vb = B + RW * nz;
+      const T* Vc = C + RW * nz;
+      const T* Wa = A + 2 * RW * nz;
+      const T* Wb = B + 2 * RW * nz;
+      const T* Wc = C + 2 * RW * nz;
+      const T* Pa = A + 3 * RW * nz;
+      const T* Pb = B + 3 * RW * nz;
+      const T* Nb = B + (3 * RW + TJR + 1) * nz + r * nz + k;   // N^{n-1} of plane i
+      const size_t id = ((size_t)i * ny + j) * nz + k;
+      const T pc = Pb[R + k];
+      if (i >= 1) {
+        const T uc = Ub[R + k];
+        const T uxp = Uc[R + k], uxm = Ua[R + k];
+        const T uyp = Ub[Rp + k], uym = Ub[Rm + k];
+        const T uzp = Ub[R + kp], uzm = Ub[R + km];
+        T fxp = hf * (uc + uxp);
+        fxp *= fxp;
+        T fxm = hf * (uxm + uc);
+        fxm *= fxm;
+        const T fxy0 = hf * (uym + uc) * (hf * (sgn * Va[R + k] + Vb[R + k]));
+        const T fxy1 = hf * (uc + uyp) * (hf * (sgn * Va[Rp + k] + Vb[Rp + k]));
+        const T fxz0 = hf * (uzm + uc) * (hf * (sgn * Wa[R + k] + Wb[R + k]));
+        const T fxz1 = hf * (uc + uzp) * (hf * (sgn * Wa[R + kp] + Wb[R + kp]));
+        const T N = (fxp - fxm + fxy1 - fxy0 + fxz1 - fxz0) * ih;
+        const T L = (uxp + uxm + uyp + uym + uzp + uzm - (T)6 * uc) * ih2;
+        const T Gp = (pc - Pa[R + k]) * ih;
+        const T Np = Nb[0];
+        n0[id] = N;
+        d0[id] = dt * (-(alpha * N + beta * Np) - Gp + nu * L);
+      }
+      {
+        const T vc = Vb[R + k];
+        const T vxp = Vc[R + k], vxm = sgn * Va[R + k];
+        const T vyp = Vb[Rp + k], vym = Vb[Rm + k];
+        const T vzp = Vb[R + kp], vzm = Vb[R + km];
+        const T fxr = hf * (Uc[Rm + k] + Uc[R + k]) * (hf * (vc + vxp));
+        const T fxl = hf * (Ub[Rm + k] + Ub[R + k]) * (hf * (vxm + vc));
+        T fyp = hf * (vc + vyp);
+        fyp *= fyp;
+        T fym = hf * (vym + vc);
+        fym *= fym;
+        const T fz1 = hf * (vc + vzp) * (hf * (Wb[Rm + kp] + Wb[R + kp]));
+        const T fz0 = hf * (vzm + vc) * (hf * (Wb[Rm + k] + Wb[R + k]));
+        const T N = (fxr - fxl + fyp - fym + fz1 - fz0) * ih;
+        const T L = (vxp + vxm + vyp + vym + vzp + vzm - (T)6 * vc) * ih2;
+        const T Gp = (pc - Pb[Rm + k]) * ih;
+        const T Np = Nb[TJR * nz];
+        n1[id] = N;
+        d1[id] = dt * (-(alpha * N + beta * Np) - Gp + nu * L);
+      }
+      {
+        const T wc = Wb[R + k];
+        const T wxp = Wc[R + k], wxm = sgn * Wa[R + k];
+        const T wyp = Wb[Rp + k], wym = Wb[Rm + k];
+        const T wzp = Wb[R + kp], wzm = Wb[R + km];
+        const T fxr = hf * (Uc[R + km] + Uc[R + k]) * (hf * (wc + wxp));
+        const T fxl = hf * (Ub[R + km] + Ub[R + k]) * (hf * (wxm + wc));
+        const T fy1 = hf * (Vb[Rp + km] + Vb[Rp + k]) * (hf * (wc + wyp));
+        const T fy0 = hf * (Vb[R + km] + Vb[R + k]) * (hf * (wym + wc));
+        T fzp = hf * (wc + wzp);
+        fzp *= fzp;
+        T fzm = hf * (wzm + wc);
+        fzm *= fzm;
+        const T N = (fxr - fxl + fy1 - fy0 + fzp - fzm) * ih;
+        const T L = (wxp + wxm + wyp + wym + wzp + wzm - (T)6 * wc) * ih2;
+        const T Gp = (pc - Pb[R + km]) * ih;
+        const T Np = Nb[2 * TJR * nz];
+        n2[id] = N;
+        d2[id] = dt * (-(alpha * N + beta * Np) - Gp + nu * L);
+      }
+    }
+    __syncthreads();
+    // the slot of plane i-1 is free: refill it with the stage RSTAGES ahead
+    if (tid == 0 && ta + RSTAGES < nstage) issue(ta + RSTAGES);
   }
 }
 
@@ -697,7 +885,21 @@ void launch_begin_step(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 }
 
 template <class T>
+static size_t rhs_pipe_smem(const Consts& c, int tjr) {
+  return (size_t)RSTAGES * (3 * (tjr + 2) + (tjr + 1) + 3 * tjr) * c.nz * sizeof(T);
+}
+
+template <class T>
 void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
+  constexpr int TJR = sizeof(T) == 4 ? 4 : 2;
+  const size_t sh = rhs_pipe_smem<T>(c, TJR);
+  if (sh <= 210 * 1024 && c.ny % TJR == 0 && (c.nz * sizeof(T)) % 16 == 0) {
+    const int XR = 32;
+    k_rhs_pipe<T, TJR><<<dim3(c.ny / TJR, (c.nx + XR - 1) / XR), RTHREADS, sh, s>>>(
+        c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.p, f.n[0], f.n[1], f.n[2], f.d[0], f.d[1],
+        f.d[2], XR);
+    return;
+  }
   k_rhs<T><<<grid3(c, c.nx + 1), dim3(TK, TJ), 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
                                                         f.p, f.n[0], f.n[1], f.n[2], f.d[0],
                                                         f.d[1], f.d[2]);
@@ -798,6 +1000,8 @@ void launch_stats(const Consts& c, const Fields<T>& f, int cur, double* out, cud
 }
 
 void fluid_set_attributes() {
+  cudaFuncSetAttribute(k_rhs_pipe<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  cudaFuncSetAttribute(k_rhs_pipe<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   cudaFuncSetAttribute(k_af_xc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_zc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_z<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
