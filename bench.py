@@ -359,6 +359,18 @@ def run_ours(args):
             fp64 = {"steps_per_s": 1000.0 / ms64, "ms_per_step": ms64,
                     "gcell_updates_per_s": wl.cells / ms64 / 1e6,
                     "speedup_fp32_over_fp64": ms64 / ms}
+        mixed = None
+        if not args.no_fp64:
+            sm = binding.Solver(wl, binding.IBM_MIXED, noise=inputs.initial_noise(wl))
+            sm.step(3)
+            msm = time_steps(sm, max(5, args.steps // 5), sm.stream)
+            poisson_mixed = sm.time_stage("poisson", 3)
+            smx = sm.stats()
+            sm.close()
+            mixed = {"steps_per_s": 1000.0 / msm, "ms_per_step": msm,
+                     "gcell_updates_per_s": wl.cells / msm / 1e6,
+                     "speedup_over_fp64": (fp64["ms_per_step"] / msm) if fp64 else None,
+                     "poisson_ms": poisson_mixed, "max_div": smx["max_div"]}
         e2e = None if args.no_e2e else e2e_rate(wl, prec, args.steps)
         if e2e is not None:
             e2e["value"] *= world
@@ -379,7 +391,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "gcell_updates_per_s": world * wl.cells / ms / 1e6,
             "step_hbm_frac": (step_bytes / (ms * 1e-3) / 1e9) / peak,
-            "roofline": roof, "stages_ms": stages, "fp64": fp64, "e2e": e2e,
+            "roofline": roof, "stages_ms": stages, "fp64": fp64, "mixed": mixed, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": kernels_per_step * args.steps,
             "dt_last": st["dt"], "cfl_last": st["cfl"], "n_sub": st["n_sub"],

@@ -57,6 +57,8 @@ extern "C" {
 /* arithmetic of the fluid fields */
 #define IBM_FP64  0        /* everything in FP64                               */
 #define IBM_FP32  1        /* fluid fields and kernels in FP32; flag, sums FP64 */
+#define IBM_MIXED 2        /* FP32 fields; Poisson transforms as split-TF32 tensor-core
+                              GEMMs (FP32 accumulation) + FP64 residual refinement */
 
 /* stages for ibm_time_stage (Sec. II.B step order) */
 #define IBM_STAGE_STEP      -1  /* the whole captured step                   */
@@ -72,6 +74,7 @@ extern "C" {
 #define IBM_STAGE_DHT_Z      9  /* transform along z                          */
 #define IBM_STAGE_POISSON_X 10  /* tridiagonal solves along x                 */
 #define IBM_STAGE_PROJECT   11  /* projection + pressure update               */
+#define IBM_STAGE_POISSON   12  /* the whole pressure solve of the precision   */
 
 /* field selectors for ibm_get_field / ibm_set_field */
 #define IBM_FIELD_U 0
@@ -108,7 +111,7 @@ typedef struct {
 
 /* Options (pass NULL for the defaults given in brackets). */
 typedef struct {
-  int    precision;   /* IBM_FP64 or IBM_FP32 [IBM_FP64]                         */
+  int    precision;   /* IBM_FP64, IBM_FP32 or IBM_MIXED [IBM_FP64]              */
   double cfl;         /* Courant number used when ibm_step gets dt <= 0 [0.3]    */
   double cfl_limit;   /* ibm_step reports IBM_EDIVERGED above this CFL [2.0]     */
   void*  stream;      /* cudaStream_t to run on; NULL: the library creates one   */

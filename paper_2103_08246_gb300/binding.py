@@ -19,7 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libibm_gb300.so")
 
 IBM_OK, IBM_EINVAL, IBM_ENOMEM, IBM_ECUDA, IBM_EDIVERGED, IBM_ETIMEOUT, IBM_EIO = 0, -1, -2, -3, -4, -5, -6
-IBM_FP64, IBM_FP32 = 0, 1
+IBM_FP64, IBM_FP32, IBM_MIXED = 0, 1, 2
 IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P = 0, 1, 2, 3
 
 # every symbol include/ibm.h declares
@@ -28,7 +28,7 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_time_stage", "ibm_destroy", "ibm_strerror")
 
 STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
-          "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11}
+          "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11, "poisson": 12}
 
 
 class ibm_grid(ctypes.Structure):

@@ -282,6 +282,8 @@ struct ibm_state {
   Params* hprm = nullptr;     // pinned copy
   double last_dt_fixed = -2.0;
   int kernels_per_step = 0;
+  float* hy = nullptr;                    // Hartley matrices (mixed precision)
+  float* hz = nullptr;
   cudaStream_t side = nullptr;            // structural update, overlapped in the graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
@@ -312,7 +314,8 @@ int check_args(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, cons
     if (b->flag_x_le < 2 * h || b->flag_x_le + b->flag_len > d->lx - 2 * h) return IBM_EINVAL;
   }
   if (o) {
-    if (o->precision != IBM_FP64 && o->precision != IBM_FP32) return IBM_EINVAL;
+    if (o->precision != IBM_FP64 && o->precision != IBM_FP32 && o->precision != IBM_MIXED)
+      return IBM_EINVAL;
     if (o->cfl < 0 || o->cfl_limit < 0) return IBM_EINVAL;
   }
   return IBM_OK;
@@ -373,6 +376,10 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   fl.csr_off = cv.take<int>(L.nf + 1);
   fl.csr_idx = cv.take<int>(L.ncsr);
   s->prm = f.prm;
+  if (s->precision == IBM_MIXED) {
+    s->hy = cv.take<float>((size_t)c.ny * c.ny);
+    s->hz = cv.take<float>((size_t)c.nz * c.nz);
+  }
   return cv.off + 256;
 }
 
@@ -425,6 +432,18 @@ int download_field(cudaStream_t st, double* dst, const T* src, size_t n) {
 // and implicit velocity stages, and joins before this step's forcing, which
 // reads the updated flag positions.
 template <class T>
+void solve_poisson(ibm_state* s, cudaStream_t st) {
+  Fields<T>& f = fields<T>(s);
+  if constexpr (std::is_same<T, float>::value) {
+    if (s->precision == IBM_MIXED) {
+      launch_poisson_mixed(s->c, f, s->hy, s->hz, st);
+      return;
+    }
+  }
+  launch_poisson(s->c, f, st);
+}
+
+template <class T>
 void record_step(ibm_state* s, int cur) {
   Fields<T>& f = fields<T>(s);
   const Consts& c = s->c;
@@ -443,7 +462,7 @@ void record_step(ibm_state* s, int cur) {
   if (flag) cudaStreamWaitEvent(st, s->ev_join, 0);
   launch_ib(c, f, s->mk, s->fl, cur, st);
   launch_mass_div(c, f, cur, false, st);
-  launch_poisson(c, f, st);
+  solve_poisson<T>(s, st);
   launch_project(c, f, cur, false, st);
 }
 
@@ -512,11 +531,21 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
   CK(cudaMemcpyAsync(f.prm, &p, sizeof(Params), cudaMemcpyHostToDevice, st));
   poisson_set_attributes();
   fluid_set_attributes();
+  mixed_set_attributes();
+  if (s->precision == IBM_MIXED) {
+    std::vector<float> H((size_t)std::max(c.ny, c.nz) * std::max(c.ny, c.nz));
+    hartley_matrix(c.ny, H.data());
+    CK(cudaMemcpyAsync(s->hy, H.data(), (size_t)c.ny * c.ny * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    hartley_matrix(c.nz, H.data());
+    CK(cudaMemcpyAsync(s->hz, H.data(), (size_t)c.nz * c.nz * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
   launch_poisson_table(c, f, st);
   // initial projection of u0 (dt absorbed in phi), velocity only
   s->cur = 0;
   launch_mass_div(c, f, 0, true, st);
-  launch_poisson(c, f, st);
+  solve_poisson<T>(s, st);
   launch_project(c, f, 0, true, st);
   s->cur = 1;
   CK(cudaGetLastError());
@@ -632,6 +661,7 @@ void launch_stage(ibm_state* s, int stage) {
     case IBM_STAGE_DHT_Z: launch_dht_z(c, f, st); break;
     case IBM_STAGE_POISSON_X: launch_poisson_x(c, f, st); break;
     case IBM_STAGE_PROJECT: launch_project_only(c, f, cur, false, st); break;
+    case IBM_STAGE_POISSON: solve_poisson<T>(s, st); break;
     default: break;
   }
 }
@@ -782,7 +812,7 @@ int ibm_stats(ibm_state* s, ibm_stats_t* out) {
 }
 
 int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
-  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_PROJECT) return IBM_EINVAL;
+  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_POISSON) return IBM_EINVAL;
   cudaStream_t st = s->stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

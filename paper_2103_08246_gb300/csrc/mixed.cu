@@ -1,0 +1,266 @@
+// Mixed-precision pressure solve (FP32 fields): the transverse transforms of
+// the Poisson solve (Sec. II.B projection step) are dense contractions with
+// the Hartley matrices H_n[j][k] = cas(2 pi j k / n), run on tensor cores as
+// split-TF32 GEMMs with FP32 accumulation,
+//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,  a_hi = tf32(a), a_lo = tf32(a - a_hi),
+// followed by an FP64 evaluation of the residual r = D - L_h phi and one
+// refinement sweep (the same solve applied to r, phi += delta).
+//
+// 2-D transform of every x plane X (ny x nz, z contiguous): H_y X H_z, as
+// two GEMMs: rows (all planes at once) times H_z, then H_y times each plane.
+#include <cmath>
+#include <cstdint>
+
+#include "solver.h"
+
+namespace ibm {
+
+constexpr int GBM = 128, GBN = 128, GBK = 32;
+constexpr int AS_LD = GBK + 4;    // shared row strides: conflict-free fragment reads
+constexpr int BS_LD = GBN + 8;
+
+struct GemmArgs {
+  const float* A;
+  const float* B;
+  float* C;
+  int M, N, K;
+  int lda, ldb, ldc;
+  long long sA, sB, sC;   // batch strides (elements)
+};
+
+__device__ inline uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ inline void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C[b] = A[b] (M x K) * B[b] (K x N), row-major, batched over blockIdx.z.
+// 8 warps: 2 along M (64 rows each) x 4 along N (32 columns each).
+__global__ void __launch_bounds__(256) k_gemm_tf32x3(GemmArgs g) {
+  extern __shared__ __align__(16) float gsm[];
+  float* As = gsm;                         // [2][GBM][AS_LD]
+  float* Bs = gsm + 2 * GBM * AS_LD;       // [2][GBK][BS_LD]
+  const int bz = blockIdx.z;
+  const float* A = g.A + bz * g.sA;
+  const float* B = g.B + bz * g.sB;
+  float* C = g.C + bz * g.sC;
+  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+  const int gid = lane >> 2, tig = lane & 3;
+  const bool full = (m0 + GBM <= g.M) && (n0 + GBN <= g.N) && (g.K % GBK == 0) &&
+                    (g.lda % 4 == 0) && (g.ldb % 4 == 0);
+  float acc[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[a][b][q] = 0.f;
+
+  float4 ra[4], rb[4];
+  auto load_regs = [&](int k0) {
+    if (full) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = tid + t * 256;            // 1024 float4 of A (128 x 32)
+        const int r = e >> 3, c4 = (e & 7) * 4;
+        ra[t] = *reinterpret_cast<const float4*>(A + (size_t)(m0 + r) * g.lda + k0 + c4);
+        const int rr = e >> 5, cc = (e & 31) * 4;  // 1024 float4 of B (32 x 128)
+        rb[t] = *reinterpret_cast<const float4*>(B + (size_t)(k0 + rr) * g.ldb + n0 + cc);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = tid + t * 256;
+        const int r = e >> 3, c4 = (e & 7) * 4;
+        float v[4];
+        for (int q = 0; q < 4; ++q) {
+          const int m = m0 + r, k = k0 + c4 + q;
+          v[q] = (m < g.M && k < g.K) ? A[(size_t)m * g.lda + k] : 0.f;
+        }
+        ra[t] = make_float4(v[0], v[1], v[2], v[3]);
+        const int rr = e >> 5, cc = (e & 31) * 4;
+        for (int q = 0; q < 4; ++q) {
+          const int k = k0 + rr, n = n0 + cc + q;
+          v[q] = (k < g.K && n < g.N) ? B[(size_t)k * g.ldb + n] : 0.f;
+        }
+        rb[t] = make_float4(v[0], v[1], v[2], v[3]);
+      }
+    }
+  };
+  auto store_regs = [&](int buf) {
+    float* as = As + buf * GBM * AS_LD;
+    float* bs = Bs + buf * GBK * BS_LD;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = tid + t * 256;
+      const int r = e >> 3, c4 = (e & 7) * 4;
+      float* pa = as + r * AS_LD + c4;
+      pa[0] = ra[t].x;
+      pa[1] = ra[t].y;
+      pa[2] = ra[t].z;
+      pa[3] = ra[t].w;
+      const int rr = e >> 5, cc = (e & 31) * 4;
+      float* pb = bs + rr * BS_LD + cc;
+      pb[0] = rb[t].x;
+      pb[1] = rb[t].y;
+      pb[2] = rb[t].z;
+      pb[3] = rb[t].w;
+    }
+  };
+  const int nk = (g.K + GBK - 1) / GBK;
+  load_regs(0);
+  store_regs(0);
+  __syncthreads();
+  for (int kt = 0; kt < nk; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < nk) load_regs((kt + 1) * GBK);
+    const float* as = As + buf * GBM * AS_LD;
+    const float* bs = Bs + buf * GBK * BS_LD;
+#pragma unroll
+    for (int kk = 0; kk < GBK; kk += 8) {
+      uint32_t ahi[4][4], alo[4][4], bhi[4][2], blo[4][2];
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt) {
+        const float* p = as + (wm + mt * 16 + gid) * AS_LD + kk + tig;
+        const float x[4] = {p[0], p[8 * AS_LD], p[4], p[8 * AS_LD + 4]};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ahi[mt][q] = tf32_of(x[q]);
+          alo[mt][q] = tf32_of(x[q] - __uint_as_float(ahi[mt][q]));
+        }
+      }
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const float* p = bs + (kk + tig) * BS_LD + wn + nt * 8 + gid;
+        const float x[2] = {p[0], p[4 * BS_LD]};
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          bhi[nt][q] = tf32_of(x[q]);
+          blo[nt][q] = tf32_of(x[q] - __uint_as_float(bhi[nt][q]));
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+          mma_tf32(acc[mt][nt], alo[mt], bhi[nt]);
+          mma_tf32(acc[mt][nt], ahi[mt], blo[nt]);
+          mma_tf32(acc[mt][nt], ahi[mt], bhi[nt]);
+        }
+    }
+    if (kt + 1 < nk) {
+      __syncthreads();
+      store_regs(buf ^ 1);
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      const int r = m0 + wm + mt * 16 + gid;
+      const int cidx = n0 + wn + nt * 8 + 2 * tig;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rr = r + 8 * h;
+        if (rr >= g.M) continue;
+        if (cidx < g.N) C[(size_t)rr * g.ldc + cidx] = acc[mt][nt][2 * h];
+        if (cidx + 1 < g.N) C[(size_t)rr * g.ldc + cidx + 1] = acc[mt][nt][2 * h + 1];
+      }
+    }
+}
+
+// FP64 residual r = D - L_h phi (Neumann x ends, periodic y, z), stored in FP32
+__global__ void k_residual64(Consts c, const float* __restrict__ D, const float* __restrict__ phi,
+                             float* __restrict__ r) {
+  const size_t n = (size_t)c.nx * c.ny * c.nz;
+  const size_t P = (size_t)c.ny * c.nz;
+  const double ih2 = c.inv_h * c.inv_h;
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n;
+       id += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(id / P);
+    const int jk = (int)(id - (size_t)i * P);
+    const int j = jk / c.nz, k = jk - j * c.nz;
+    const double pc = phi[id];
+    const double pxm = i > 0 ? (double)phi[id - P] : pc;
+    const double pxp = i < c.nx - 1 ? (double)phi[id + P] : pc;
+    const int jm = j == 0 ? c.ny - 1 : j - 1, jp = j == c.ny - 1 ? 0 : j + 1;
+    const int km = k == 0 ? c.nz - 1 : k - 1, kp = k == c.nz - 1 ? 0 : k + 1;
+    const size_t b = (size_t)i * P;
+    const double lap = (pxm + pxp + (double)phi[b + (size_t)jm * c.nz + k] +
+                        (double)phi[b + (size_t)jp * c.nz + k] + (double)phi[b + (size_t)j * c.nz + km] +
+                        (double)phi[b + (size_t)j * c.nz + kp] - 6.0 * pc) *
+                       ih2;
+    r[id] = (float)((double)D[id] - lap);
+  }
+}
+
+__global__ void k_add(size_t n, const float* __restrict__ a, const float* __restrict__ b,
+                      float* __restrict__ out) {
+  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n;
+       id += (size_t)gridDim.x * blockDim.x)
+    out[id] = a[id] + b[id];
+}
+
+static void gemm(const GemmArgs& g, int batch, cudaStream_t s) {
+  const size_t sh = (size_t)(2 * GBM * AS_LD + 2 * GBK * BS_LD) * sizeof(float);
+  k_gemm_tf32x3<<<dim3((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, batch), 256, sh, s>>>(g);
+}
+
+// 2-D Hartley transform of every x plane: out = H_y in H_z (tmp: scratch)
+static void transform2d(const Consts& c, const float* Hy, const float* Hz, const float* in,
+                        float* tmp, float* out, cudaStream_t s) {
+  const long long P = (long long)c.ny * c.nz;
+  GemmArgs a{in, Hz, tmp, c.nx * c.ny, c.nz, c.nz, c.nz, c.nz, c.nz, 0, 0, 0};
+  gemm(a, 1, s);
+  GemmArgs b{Hy, tmp, out, c.ny, c.nz, c.ny, c.ny, c.nz, c.nz, 0, P, P};
+  gemm(b, c.nx, s);
+}
+
+// phi <- solution of L_h phi = D (D in f.phi on entry), mixed precision with
+// one FP64-residual refinement sweep. Scratch: e[0], e[1], e[2].
+void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* Hy,
+                          const float* Hz, cudaStream_t s) {
+  const size_t n = (size_t)c.nx * c.ny * c.nz;
+  float* D = f.phi;
+  float* t0 = f.e[0];
+  float* x0 = f.e[1];
+  float* t1 = f.e[2];
+  // first solve: x0 = L^-1 D
+  transform2d(c, Hy, Hz, D, t0, x0, s);
+  launch_poisson_x_on(c, f, x0, s);
+  transform2d(c, Hy, Hz, x0, t0, x0, s);
+  // FP64 residual and correction: t1 = L^-1 (D - L x0)
+  const int nb = 152 * 8;
+  k_residual64<<<nb, 256, 0, s>>>(c, D, x0, t1);
+  transform2d(c, Hy, Hz, t1, t0, t1, s);
+  launch_poisson_x_on(c, f, t1, s);
+  transform2d(c, Hy, Hz, t1, t0, t1, s);
+  k_add<<<nb, 256, 0, s>>>(n, x0, t1, f.phi);
+}
+
+void mixed_set_attributes() {
+  cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+// Hartley matrices in FP32 (entries from FP64 cos/sin of 2 pi j k / n, jk mod n)
+void hartley_matrix(int n, float* host) {
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) {
+      const long long jk = ((long long)j * k) % n;
+      const double a = 2.0 * M_PI * (double)jk / n;
+      host[(size_t)j * n + k] = (float)(std::cos(a) + std::sin(a));
+    }
+}
+
+}  // namespace ibm

@@ -177,10 +177,15 @@ void launch_dht_z(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 }
 
 template <class T>
-void launch_poisson_x(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+void launch_poisson_x_on(const Consts& c, const Fields<T>& f, T* buf, cudaStream_t s) {
   const int P = c.ny * c.nz;
   const T scale = (T)(c.h * c.h / ((double)c.ny * c.nz));
-  k_poisson_x<T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, f.phi, scale);
+  k_poisson_x<T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, buf, scale);
+}
+
+template <class T>
+void launch_poisson_x(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+  launch_poisson_x_on(c, f, f.phi, s);
 }
 
 template <class T>
@@ -204,6 +209,8 @@ template void launch_dht_y<float>(const Consts&, const Fields<float>&, cudaStrea
 template void launch_dht_z<double>(const Consts&, const Fields<double>&, cudaStream_t);
 template void launch_dht_z<float>(const Consts&, const Fields<float>&, cudaStream_t);
 template void launch_poisson_x<double>(const Consts&, const Fields<double>&, cudaStream_t);
+template void launch_poisson_x_on<float>(const Consts&, const Fields<float>&, float*, cudaStream_t);
+template void launch_poisson_x_on<double>(const Consts&, const Fields<double>&, double*, cudaStream_t);
 template void launch_poisson_x<float>(const Consts&, const Fields<float>&, cudaStream_t);
 template void launch_poisson<float>(const Consts&, const Fields<float>&, cudaStream_t);
 template void launch_poisson_table<double>(const Consts&, const Fields<double>&, cudaStream_t);

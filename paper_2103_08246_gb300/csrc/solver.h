@@ -81,8 +81,15 @@ template <class T> void launch_poisson(const Consts& c, const Fields<T>& f, cuda
 template <class T> void launch_dht_y(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_dht_z(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_poisson_x(const Consts& c, const Fields<T>& f, cudaStream_t s);
+template <class T> void launch_poisson_x_on(const Consts& c, const Fields<T>& f, T* buf, cudaStream_t s);
 template <class T> void launch_poisson_table(const Consts& c, const Fields<T>& f, cudaStream_t s);
 void poisson_set_attributes();
+
+// ---- mixed.cu
+void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* Hy,
+                          const float* Hz, cudaStream_t s);
+void mixed_set_attributes();
+void hartley_matrix(int n, float* host);
 
 // ---- ib.cu
 template <class T> void launch_ib(const Consts& c, const Fields<T>& f, const Markers& m,

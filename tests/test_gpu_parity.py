@@ -192,3 +192,32 @@ def test_production_size_properties_fp32(lib):
     X, V, F = gpu.flag()
     assert np.all(np.isfinite(X)) and np.all(np.isfinite(V))
     gpu.close()
+
+
+# ---------------------------------------------------------------- mixed precision
+# FP32 fields with the Poisson transforms as split-TF32 tensor-core GEMMs and
+# one FP64-residual refinement sweep: errors against the FP64 oracle are held
+# to the FP32 bounds above (the split products keep ~FP32 accuracy and the
+# refinement removes the amplification of the transform rounding by the
+# Poisson conditioning).
+@pytest.mark.parametrize("case", ["plain", "ragged", "bars_flag"])
+def test_mixed_small_cases(lib, case):
+    from paper_2103_08246_gb300 import binding
+    kw = {"plain": {}, "ragged": dict(shape=(20, 8, 16)),
+          "bars_flag": dict(bars_on=True, bar_x=1.0, **FLAG)}[case]
+    wl = _small(**kw)
+    gpu, ora = _run(wl, binding.IBM_MIXED, 10)
+    errs = _compare(gpu, ora, FP32_TOL, floor=FP32_FLOOR)
+    gpu.close()
+    print(case, "mixed errors:", errs)
+
+
+def test_mixed_tiny_workload(lib):
+    from paper_2103_08246_gb300 import binding, inputs
+    wl = inputs.TINY
+    gpu, ora = _run(wl, binding.IBM_MIXED, 20, amp=wl.noise_amp)
+    errs = _compare(gpu, ora, FP32_TOL, floor=FP32_FLOOR)
+    st = gpu.stats()
+    assert st["max_div"] * (wl.lx / wl.nx) < 1e-5
+    gpu.close()
+    print("tiny workload mixed errors:", errs, "max_div", st["max_div"])
