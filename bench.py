@@ -318,6 +318,38 @@ def e2e_rate(wl, precision, steps):
             "d2h_bytes_per_step": field_bytes / steps + 3 * X.nbytes + 8 * 64}
 
 
+def ensemble_rate(steps):
+    """The 16-case ensemble (uneven grids, mixed precision, tuned tiles):
+    aggregate cell updates per second stepped together and one by one."""
+    import torch
+    from paper_2103_08246_gb300 import binding, ensemble
+    solvers, ens = ensemble.build()
+    ens.step(3)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(ens.stream)
+    ens.step(steps)
+    e1.record(ens.stream)
+    e1.synchronize()
+    ms_together = e0.elapsed_time(e1) / steps
+    ens.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in solvers:
+        s.step(steps)
+    torch.cuda.synchronize()
+    ms_alone = (time.perf_counter() - t0) * 1e3 / steps
+    cells = sum(s.wl.cells for s in solvers)
+    shapes = [f"{s.wl.nx}x{s.wl.ny}x{s.wl.nz}" for s in solvers]
+    for s in solvers:
+        s.close()
+    return {"cases": len(shapes), "cells": cells, "ms_per_ensemble_step": ms_together,
+            "gcell_updates_per_s": cells / ms_together / 1e6,
+            "ms_per_step_one_by_one": ms_alone, "speedup_over_one_by_one": ms_alone / ms_together,
+            "precision": "mixed", "shapes": shapes}
+
+
 def run_ours(args):
     import torch
     from paper_2103_08246_gb300 import binding, build, inputs
@@ -371,6 +403,7 @@ def run_ours(args):
                      "gcell_updates_per_s": wl.cells / msm / 1e6,
                      "speedup_over_fp64": (fp64["ms_per_step"] / msm) if fp64 else None,
                      "poisson_ms": poisson_mixed, "max_div": smx["max_div"]}
+        ens = None if args.no_fp64 else ensemble_rate(max(5, args.steps // 5))
         e2e = None if args.no_e2e else e2e_rate(wl, prec, args.steps)
         if e2e is not None:
             e2e["value"] *= world
@@ -391,7 +424,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "gcell_updates_per_s": world * wl.cells / ms / 1e6,
             "step_hbm_frac": (step_bytes / (ms * 1e-3) / 1e9) / peak,
-            "roofline": roof, "stages_ms": stages, "fp64": fp64, "mixed": mixed, "e2e": e2e,
+            "roofline": roof, "stages_ms": stages, "fp64": fp64, "mixed": mixed,
+            "ensemble": ens, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": kernels_per_step * args.steps,
             "dt_last": st["dt"], "cfl_last": st["cfl"], "n_sub": st["n_sub"],

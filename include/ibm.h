@@ -122,6 +122,12 @@ typedef struct {
   const double* init_u;
   const double* init_v;
   const double* init_w;
+  /* Tile parameters (0: defaults). rhs_planes: x planes per block of the
+   * streamed explicit stage [32], in [2, 256]; afx_planes: x planes per block
+   * of the FP32 implicit x factor [64], in [8, 256]. Results do not depend
+   * on them; ibm_autotune-style searches pick them per problem shape. */
+  int rhs_planes;
+  int afx_planes;
 } ibm_options;
 
 /* Diagnostics read by ibm_stats (all FP64). */
@@ -201,6 +207,20 @@ int ibm_get_markers(ibm_state* s, double* X, size_t n);
  * leaves the fields meaningless: use a state created for timing only.
  * Synchronises. */
 int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms);
+
+/* Ensembles: several independent states stepped together. One CUDA graph
+ * launch per step runs the captured step of every member as concurrent
+ * branches, so that small cases of uneven size share the GPU. Members keep
+ * their own fields and parameters (grid, Re, bodies, precision); they must
+ * not be stepped on their own while they belong to an ensemble, and must
+ * outlive it. The ensemble runs on `stream` (cudaStream_t, NULL: a stream
+ * the library creates). */
+typedef struct ibm_ensemble ibm_ensemble;
+int ibm_ensemble_create(ibm_state* const* members, int n, void* stream, ibm_ensemble** out);
+/* Advance every member nsteps steps (dt as in ibm_step, for every member).
+ * Checks every member for divergence at the end; returns the first error. */
+int ibm_ensemble_step(ibm_ensemble* e, double dt, int nsteps);
+void ibm_ensemble_destroy(ibm_ensemble* e);
 
 /* Release the state (and the workspace if the library allocated it). */
 void ibm_destroy(ibm_state* s);

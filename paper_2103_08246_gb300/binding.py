@@ -25,7 +25,8 @@ IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P = 0, 1, 2, 3
 # every symbol include/ibm.h declares
 SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_flag_state",
            "ibm_stats", "ibm_get_field", "ibm_set_field", "ibm_marker_count", "ibm_get_markers",
-           "ibm_time_stage", "ibm_destroy", "ibm_strerror")
+           "ibm_time_stage", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
+           "ibm_destroy", "ibm_strerror")
 
 STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
           "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11, "poisson": 12}
@@ -55,7 +56,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class ibm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("cfl_limit", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("init_u", _dp), ("init_v", _dp), ("init_w", _dp)]
+                ("init_u", _dp), ("init_v", _dp), ("init_w", _dp),
+                ("rhs_planes", ctypes.c_int), ("afx_planes", ctypes.c_int)]
 
 
 class ibm_stats_t(ctypes.Structure):
@@ -104,12 +106,16 @@ def load(path: str = LIB_PATH):
     lib.ibm_marker_count.argtypes = [vp, ctypes.POINTER(sz)]
     lib.ibm_get_markers.argtypes = [vp, _dp, sz]
     lib.ibm_time_stage.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.ibm_ensemble_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.ibm_ensemble_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    lib.ibm_ensemble_destroy.argtypes = [vp]
+    lib.ibm_ensemble_destroy.restype = None
     lib.ibm_destroy.argtypes = [vp]
     lib.ibm_destroy.restype = None
     lib.ibm_strerror.argtypes = [ctypes.c_int]
     lib.ibm_strerror.restype = ctypes.c_char_p
     for name in SYMBOLS:
-        if name not in ("ibm_destroy", "ibm_strerror"):
+        if name not in ("ibm_destroy", "ibm_strerror", "ibm_ensemble_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -200,6 +206,23 @@ def ibm_time_stage(state, stage, nrep) -> float:
     return ms.value
 
 
+def ibm_ensemble_create(states, stream=None):
+    arr = (ctypes.c_void_p * len(states))(*[st.value if isinstance(st, ctypes.c_void_p) else st
+                                             for st in states])
+    h = ctypes.c_void_p()
+    _check(load().ibm_ensemble_create(arr, len(states), stream, ctypes.byref(h)),
+           "ibm_ensemble_create")
+    return h
+
+
+def ibm_ensemble_step(ens, dt, nsteps):
+    return load().ibm_ensemble_step(ens, float(dt), int(nsteps))
+
+
+def ibm_ensemble_destroy(ens):
+    load().ibm_ensemble_destroy(ens)
+
+
 def ibm_destroy(state):
     load().ibm_destroy(state)
 
@@ -213,7 +236,7 @@ class Solver:
     """
 
     def __init__(self, wl: Workload, precision: int = IBM_FP64, noise=None, stream=None,
-                 cfl: float | None = None, cfl_limit: float = 2.0):
+                 cfl: float | None = None, cfl_limit: float = 2.0, tiles=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the solver needs a CUDA device")
@@ -224,9 +247,11 @@ class Solver:
         # a dedicated stream: CUDA graphs cannot be captured on the legacy default stream
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self._noise = [np.ascontiguousarray(a, dtype=np.float64) for a in noise] if noise else None
+        tiles = tiles or {}
         opts = ibm_options(precision, wl.cfl if cfl is None else cfl, cfl_limit,
                            ctypes.c_void_p(self.stream.cuda_stream),
-                           *([_ptr(a) for a in self._noise] if self._noise else [None] * 3))
+                           *([_ptr(a) for a in self._noise] if self._noise else [None] * 3),
+                           int(tiles.get("rhs_planes", 0)), int(tiles.get("afx_planes", 0)))
         self.ws_bytes = ibm_workspace_bytes(self.grid, self.dom, self.bodies, opts)
         self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device="cuda")
         torch.cuda.synchronize()
@@ -274,6 +299,31 @@ class Solver:
         if getattr(self, "state", None) is not None:
             ibm_destroy(self.state)
             self.state = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ensemble:
+    """Several Solver members stepped together by one graph launch per step."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.solvers = list(solvers)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.handle = ibm_ensemble_create([s.state for s in self.solvers],
+                                          ctypes.c_void_p(self.stream.cuda_stream))
+
+    def step(self, nsteps=1, dt=-1.0):
+        _check(ibm_ensemble_step(self.handle, dt, nsteps), "ibm_ensemble_step")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            ibm_ensemble_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

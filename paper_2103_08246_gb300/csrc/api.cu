@@ -273,6 +273,7 @@ struct ibm_state {
   bool own_ws = false;
   int cur = 0;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraph_t graph[2] = {nullptr, nullptr};   // kept for ensembles
   Fields<double> fd{};
   Fields<float> ff{};
   Markers mk{};
@@ -314,6 +315,9 @@ int check_args(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, cons
     if (b->flag_x_le < 2 * h || b->flag_x_le + b->flag_len > d->lx - 2 * h) return IBM_EINVAL;
   }
   if (o) {
+    if (o->rhs_planes < 0 || o->rhs_planes > 256 || (o->rhs_planes > 0 && o->rhs_planes < 2) ||
+        o->afx_planes < 0 || o->afx_planes > 256 || (o->afx_planes > 0 && o->afx_planes < 8))
+      return IBM_EINVAL;
     if (o->precision != IBM_FP64 && o->precision != IBM_FP32 && o->precision != IBM_MIXED)
       return IBM_EINVAL;
     if (o->cfl < 0 || o->cfl_limit < 0) return IBM_EINVAL;
@@ -568,7 +572,7 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
     cudaGraphGetNodes(g, nullptr, &nodes);
     s->kernels_per_step = (int)nodes;
     e = cudaGraphInstantiate(&s->exec[par], g, 0);
-    cudaGraphDestroy(g);
+    s->graph[par] = g;
     if (e != cudaSuccess) {
       cudaGetLastError();
       return IBM_ECUDA;
@@ -597,6 +601,8 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   c.ly = d->ly;
   c.lz = d->lz;
   c.u_in = 1.0;
+  c.rhs_planes = (o && o->rhs_planes > 0) ? o->rhs_planes : 32;
+  c.afx_planes = (o && o->afx_planes > 0) ? o->afx_planes : 64;
   bar_dv = 0.0;
   if (b->flag_on) fg = build_flag(*b, *d, c.h);
   if (b->bars_on) build_bars(*b, *d, c.h, Xb, bar_dv);
@@ -892,8 +898,10 @@ int ibm_get_markers(ibm_state* s, double* X, size_t n) {
 void ibm_destroy(ibm_state* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < 2; ++q) {
     if (s->exec[q]) cudaGraphExecDestroy(s->exec[q]);
+    if (s->graph[q]) cudaGraphDestroy(s->graph[q]);
+  }
   if (s->own_ws && s->ws) cudaFree(s->ws);
   if (s->hprm) cudaFreeHost(s->hprm);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -902,6 +910,112 @@ void ibm_destroy(ibm_state* s) {
   if (s->ev_join) cudaEventDestroy(s->ev_join);
   cudaGetLastError();
   delete s;
+}
+
+// ------------------------------------------------------------------ ensembles
+struct ibm_ensemble {
+  std::vector<ibm_state*> members;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};   // members' parity as at creation, flipped
+  int par = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+};
+
+static int ensemble_set_dt(ibm_state* s, double dt, cudaStream_t st) {
+  const double mode = dt > 0 ? dt : -1.0;
+  if (mode != s->last_dt_fixed) {
+    double two[2] = {mode, s->cfl};
+    Params* prm = s->prm;
+    CK(cudaMemcpyAsync(&prm->dt_fixed, two, sizeof(two), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    s->last_dt_fixed = mode;
+  }
+  return IBM_OK;
+}
+
+int ibm_ensemble_create(ibm_state* const* members, int n, void* stream, ibm_ensemble** out) {
+  if (!members || n < 1 || !out) return IBM_EINVAL;
+  *out = nullptr;
+  std::unique_ptr<ibm_ensemble> e(new (std::nothrow) ibm_ensemble());
+  if (!e) return IBM_ENOMEM;
+  for (int q = 0; q < n; ++q) {
+    if (!members[q] || !members[q]->graph[0] || !members[q]->graph[1]) return IBM_EINVAL;
+    for (int r = 0; r < q; ++r)
+      if (members[r] == members[q]) return IBM_EINVAL;
+    e->members.push_back(members[q]);
+    CK(cudaStreamSynchronize(members[q]->stream));
+  }
+  if (stream) {
+    e->stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+    e->own_stream = true;
+  }
+  // one parent graph per parity offset: member q runs its step graph for
+  // buffer parity (cur_q + offset) & 1, all members as independent branches
+  for (int off = 0; off < 2; ++off) {
+    cudaGraph_t parent;
+    CK(cudaGraphCreate(&parent, 0));
+    for (ibm_state* m : e->members) {
+      cudaGraphNode_t node;
+      cudaError_t err = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, m->graph[(m->cur + off) & 1]);
+      if (err != cudaSuccess) {
+        cudaGraphDestroy(parent);
+        cudaGetLastError();
+        ibm_ensemble_destroy(e.release());
+        return IBM_ECUDA;
+      }
+    }
+    cudaError_t err = cudaGraphInstantiate(&e->exec[off], parent, 0);
+    cudaGraphDestroy(parent);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      ibm_ensemble_destroy(e.release());
+      return IBM_ECUDA;
+    }
+  }
+  *out = e.release();
+  return IBM_OK;
+}
+
+int ibm_ensemble_step(ibm_ensemble* e, double dt, int nsteps) {
+  if (!e || nsteps < 0) return IBM_EINVAL;
+  cudaStream_t st = e->stream;
+  for (ibm_state* m : e->members) {
+    int rc = ensemble_set_dt(m, dt, st);
+    if (rc) return rc;
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    CK(cudaGraphLaunch(e->exec[e->par], st));
+    e->par ^= 1;
+    for (ibm_state* m : e->members) m->cur ^= 1;
+  }
+  int result = IBM_OK;
+  for (ibm_state* m : e->members) {
+    if (nsteps > 0) launch_flag(m->prm, m->fl, false, st);
+    CK(cudaMemcpyAsync(m->hprm, m->prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  for (ibm_state* m : e->members) {
+    const Params& p = *m->hprm;
+    int rc = IBM_OK;
+    if (p.error & ERR_TIMEOUT) rc = IBM_ETIMEOUT;
+    else if (p.error & ERR_AF_RANGE) rc = IBM_EINVAL;
+    else if (p.error) rc = IBM_EDIVERGED;
+    else if (nsteps > 0 && p.dt * p.speed_max / m->c.h > m->cfl_limit) rc = IBM_EDIVERGED;
+    if (rc && result == IBM_OK) result = rc;
+  }
+  return result;
+}
+
+void ibm_ensemble_destroy(ibm_ensemble* e) {
+  if (!e) return;
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  for (int q = 0; q < 2; ++q)
+    if (e->exec[q]) cudaGraphExecDestroy(e->exec[q]);
+  if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+  cudaGetLastError();
+  delete e;
 }
 
 }  // extern "C"

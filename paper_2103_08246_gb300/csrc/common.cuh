@@ -38,6 +38,8 @@ struct Consts {
   double h, inv_h, nu, lx, ly, lz;
   double u_in;        // inflow speed U
   double omega_max;   // structural stiffness bound (sub-step count)
+  int rhs_planes;     // tile: x planes per block of the streamed RHS
+  int afx_planes;     // tile: x planes per block of the FP32 x factor
 };
 
 constexpr int ERR_AF_RANGE = 1;     // implicit diffusion number outside range

@@ -613,9 +613,8 @@ __device__ inline void tap_range(int n, int H, int& lo, int& hi) {
 // side about the two ends (about face 0 for u, about x = -h/2 for v, w, and
 // about plane nx), so the solve is the free-space inverse of
 // r (q - S - S^{-1}), t_m = (1/r) rho^{|m|+1} / (1 - rho^2), applied to the
-// reflected data and truncated to |m| <= H. A block stages XC planes plus
-// the halo of 32 consecutive (y, z) columns.
-constexpr int XC = 64;
+// reflected data and truncated to |m| <= H. A block stages XC planes (a tile
+// parameter) plus the halo of 32 consecutive (y, z) columns.
 template <class T>
 __global__ void __launch_bounds__(256)
 k_af_xc(Consts c, const Params* __restrict__ prm, const T* __restrict__ taps,
@@ -625,6 +624,7 @@ k_af_xc(Consts c, const Params* __restrict__ prm, const T* __restrict__ taps,
   extern __shared__ unsigned char smem_raw[];
   T* s = reinterpret_cast<T*>(smem_raw);
   const int P = c.ny * c.nz;
+  const int XC = c.afx_planes;
   const int comp = blockIdx.z;
   const int nx = c.nx;
   // unknown planes: u 1..nx-1 (reflection about 0 and nx); v, w 0..nx-1
@@ -894,7 +894,7 @@ void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   constexpr int TJR = sizeof(T) == 4 ? 4 : 2;
   const size_t sh = rhs_pipe_smem<T>(c, TJR);
   if (sh <= 210 * 1024 && c.ny % TJR == 0 && (c.nz * sizeof(T)) % 16 == 0) {
-    const int XR = 32;
+    const int XR = c.rhs_planes;
     k_rhs_pipe<T, TJR><<<dim3(c.ny / TJR, (c.nx + XR - 1) / XR), RTHREADS, sh, s>>>(
         c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.p, f.n[0], f.n[1], f.n[2], f.d[0], f.d[1],
         f.d[2], XR);
@@ -916,6 +916,7 @@ template <class T>
 void launch_af_x(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   const int P = c.ny * c.nz;
   if constexpr (sizeof(T) == 4) {
+    const int XC = c.afx_planes;
     const size_t sh = (size_t)(XC + 2 * HMAX) * 32 * sizeof(T);
     k_af_xc<T><<<dim3((P + 31) / 32, (c.nx + XC - 1) / XC, 3), dim3(32, 8), sh, s>>>(
         c, f.prm, (const T*)f.tapsf + c.ny + c.nz, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2],

@@ -110,3 +110,28 @@ def initial_noise(wl: Workload, seed: int | None = None, amp: float | None = Non
 def random_field(shape, seed: int, lo=-1.0, hi=1.0):
     """A plain seeded uniform field (used by operator-level tests)."""
     return np.random.default_rng(seed).uniform(lo, hi, size=shape)
+
+
+def ensemble_cases(n: int = 16, seed: int = 0):
+    """Independent flag cases of uneven size (the batched-ensemble workload).
+
+    Spacing h = 1/16 (17 x 17 flag vertices at the grid spacing); x from 64
+    to 256 cells, y = z from {32, 64, 128} cells (power-of-two transverse
+    sizes), domains scaled accordingly; bar grid (mesh 0.5, width 0.1) at
+    x = 0.5; flag leading edge 1 to 4 bar meshes behind the grid; bending
+    log-uniform in [1e-3, 1e-1]; Re uniform in [100, 400]; CFL 0.3.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(n):
+        nyz = int(rng.choice([32, 64, 128]))
+        nx = int(rng.integers(64, 257))
+        h = 1.0 / 16.0
+        dist = float(rng.uniform(1.0, 4.0))
+        out.append(Workload(
+            name=f"ensemble-{q}-{nx}x{nyz}x{nyz}", nx=nx, ny=nyz, nz=nyz,
+            lx=nx * h, ly=nyz * h, lz=nyz * h, re=float(rng.uniform(100.0, 400.0)),
+            flag_x_le=0.5 + 0.5 * dist, flag_ns=17, flag_nt=17,
+            bending=float(10.0 ** rng.uniform(-3.0, -1.0)), dt=-1.0, cfl=0.3,
+            steps=100, seed=seed + q))
+    return out
