@@ -208,6 +208,25 @@ int ibm_get_markers(ibm_state* s, double* X, size_t n);
  * Synchronises. */
 int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms);
 
+/* Diagnostics without any device allocation or workspace scratch (the paper
+ * has no counterpart; this is a library facility). Same values as ibm_stats,
+ * but the reduction scratch is a fixed device array compiled into the
+ * library: 2 x 65,536 partial results plus 16 output values (about 1 MiB),
+ * which every GPU that loads the library keeps until the process exits.
+ * For callers that cannot allocate device memory at the point where they
+ * read diagnostics: code that runs while another part of the program is
+ * capturing a CUDA graph (cudaMalloc is not allowed then), loops that must
+ * not stall on the implicit device synchronisation of cudaMalloc/cudaFree,
+ * and programs whose device memory is wholly owned by another allocator.
+ * Sizes: grids needing more than 65,536 reduction blocks
+ * (ceil(nz/32) * ceil(ny/8) * ceil((nx+1)/8)) are rejected with IBM_EINVAL.
+ * The first call on a device looks the array's device address up once
+ * (with that device current); make that first call before any stream
+ * capture. Every call shares the array and overwrites all of it that it
+ * reads, so no clearing is needed; calls that overlap on the GPU (from two
+ * streams or threads) race on it. Synchronises the state's stream. */
+int ibm_stats_static(ibm_state* s, ibm_stats_t* out);
+
 /* Ensembles: several independent states stepped together. One CUDA graph
  * launch per step runs the captured step of every member as concurrent
  * branches, so that small cases of uneven size share the GPU. Members keep

@@ -25,7 +25,7 @@ IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P = 0, 1, 2, 3
 # every symbol include/ibm.h declares
 SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_flag_state",
            "ibm_stats", "ibm_get_field", "ibm_set_field", "ibm_marker_count", "ibm_get_markers",
-           "ibm_time_stage", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
+           "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_destroy", "ibm_strerror")
 
 STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
     lib.ibm_sync.argtypes = [vp]
     lib.ibm_flag_state.argtypes = [vp, _dp, _dp, _dp, sz]
     lib.ibm_stats.argtypes = [vp, ctypes.POINTER(ibm_stats_t)]
+    lib.ibm_stats_static.argtypes = [vp, ctypes.POINTER(ibm_stats_t)]
     lib.ibm_get_field.argtypes = [vp, ctypes.c_int, _dp, sz]
     lib.ibm_set_field.argtypes = [vp, ctypes.c_int, _dp, sz]
     lib.ibm_marker_count.argtypes = [vp, ctypes.POINTER(sz)]
@@ -178,6 +179,13 @@ def ibm_flag_state(state, X, V=None, F=None):
 def ibm_stats(state) -> dict:
     st = ibm_stats_t()
     _check(load().ibm_stats(state, ctypes.byref(st)), "ibm_stats")
+    return st.as_dict()
+
+
+def ibm_stats_static(state) -> dict:
+    """Diagnostics through the entry point that allocates nothing."""
+    st = ibm_stats_t()
+    _check(load().ibm_stats_static(state, ctypes.byref(st)), "ibm_stats_static")
     return st.as_dict()
 
 

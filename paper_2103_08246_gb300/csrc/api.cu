@@ -1019,3 +1019,135 @@ void ibm_ensemble_destroy(ibm_ensemble* e) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ diagnostics without allocation
+// Reduction scratch of ibm_stats_static: a fixed device array in this file
+// (host code only ever sees its address through cudaGetSymbolAddress).
+namespace {
+constexpr int kStatsMaxBlocks = 1 << 16;
+constexpr int kStatsScratch = 2 * kStatsMaxBlocks + 16;
+__device__ __align__(256) double g_stats_scratch[kStatsScratch];
+constexpr int kMaxDevices = 64;
+double* g_stats_dev_ptr[kMaxDevices] = {nullptr};
+
+constexpr int kSTK = 32, kSTJ = 8, kSX = 8;   // block tile of the first pass
+
+// first pass: per-block kinetic energy and max |div u| (no atomics)
+template <class T>
+__global__ void __launch_bounds__(kSTK* kSTJ)
+k_stats_blocks(Consts c, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
+               double* __restrict__ part) {
+  __shared__ double sk[kSTK * kSTJ / 32], sd[kSTK * kSTJ / 32];
+  const int k = blockIdx.x * kSTK + threadIdx.x;
+  const int j = blockIdx.y * kSTJ + threadIdx.y;
+  double ke = 0.0, dmax = 0.0;
+  if (k < c.nz && j < c.ny) {
+    const int ny = c.ny, nz = c.nz, nx = c.nx;
+    const int jp = j == ny - 1 ? 0 : j + 1, kp = k == nz - 1 ? 0 : k + 1;
+    const size_t P = (size_t)ny * nz;
+    const int i0 = blockIdx.z * kSX, i1 = min(i0 + kSX, nx + 1);
+    for (int i = i0; i < i1; ++i) {
+      const size_t id = ((size_t)i * ny + j) * nz + k;
+      const double uu = u[id];
+      ke += 0.5 * uu * uu;
+      if (i < nx) {
+        const double vv = v[id], ww = w[id];
+        ke += 0.5 * (vv * vv + ww * ww);
+        const double dv = ((double)u[id + P] - uu) + ((double)v[((size_t)i * ny + jp) * nz + k] - vv) +
+                          ((double)w[((size_t)i * ny + j) * nz + kp] - ww);
+        dmax = fmax(dmax, fabs(dv) * c.inv_h);
+      }
+    }
+  }
+  ke = warp_sum(ke);
+  dmax = warp_max(dmax);
+  const int tid = threadIdx.y * kSTK + threadIdx.x;
+  if ((tid & 31) == 0) {
+    sk[tid >> 5] = ke;
+    sd[tid >> 5] = dmax;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < kSTK * kSTJ / 32; ++q) {
+      a += sk[q];
+      b = fmax(b, sd[q]);
+    }
+    const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    part[blk] = a;
+    part[kStatsMaxBlocks + blk] = b;
+  }
+}
+
+// second pass: one block reduces the partials in a fixed order
+__global__ void k_stats_final(int nblk, double h3, const double* __restrict__ part,
+                              double* __restrict__ res) {
+  __shared__ double scratch[32];
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+    a += part[q];
+    b = fmax(b, part[kStatsMaxBlocks + q]);
+  }
+  a = block_sum(a, scratch);
+  __syncthreads();
+  b = block_max(b, scratch);
+  if (threadIdx.x == 0) {
+    res[0] = a * h3;
+    res[1] = b;
+  }
+}
+}  // namespace
+
+extern "C" int ibm_stats_static(ibm_state* s, ibm_stats_t* out) {
+  if (!s || !out) return IBM_EINVAL;
+  const Consts& c = s->c;
+  const dim3 grid((c.nz + kSTK - 1) / kSTK, (c.ny + kSTJ - 1) / kSTJ, (c.nx + 1 + kSX - 1) / kSX);
+  const long long nblk = (long long)grid.x * grid.y * grid.z;
+  if (nblk > kStatsMaxBlocks) return IBM_EINVAL;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return IBM_EINVAL;
+  if (!g_stats_dev_ptr[dev]) {
+    double* ptr = nullptr;
+    CK(cudaGetSymbolAddress((void**)&ptr, g_stats_scratch));
+    g_stats_dev_ptr[dev] = ptr;
+  }
+  double* part = g_stats_dev_ptr[dev];
+  double* res = part + 2 * kStatsMaxBlocks;
+  cudaStream_t st = s->stream;
+  if (s->precision == IBM_FP64)
+    k_stats_blocks<double><<<grid, dim3(kSTK, kSTJ), 0, st>>>(c, s->fd.u[s->cur], s->fd.v[s->cur],
+                                                             s->fd.w[s->cur], part);
+  else
+    k_stats_blocks<float><<<grid, dim3(kSTK, kSTJ), 0, st>>>(c, s->ff.u[s->cur], s->ff.v[s->cur],
+                                                            s->ff.w[s->cur], part);
+  k_stats_final<<<1, 1024, 0, st>>>((int)nblk, c.h * c.h * c.h, part, res);
+  launch_flag_stats(s->fl, res + 4, st);
+  CK(cudaGetLastError());
+  double h[16];
+  CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(s->hprm, s->prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const Params& p = *s->hprm;
+  std::memset(out, 0, sizeof(*out));
+  out->step = p.step;
+  out->t = p.t;
+  out->dt = p.dt;
+  out->cfl = p.dt * p.speed_max / c.h;
+  out->ke = h[0];
+  out->max_div = h[1];
+  out->q_in = p.q_in;
+  out->q_out = p.q_out;
+  out->ib_slip = p.slip_max;
+  if (s->fl.nv) {
+    for (int e = 0; e < 3; ++e) {
+      out->te_mid[e] = h[4 + e];
+      out->force[e] = h[7 + e];
+    }
+    out->max_strain = h[10];
+  }
+  out->n_sub = p.n_sub;
+  out->n_markers = s->mk.nm;
+  out->kernels_per_step = s->kernels_per_step;
+  return IBM_OK;
+}
