@@ -714,6 +714,79 @@ k_af_zc(Consts c, const Params* __restrict__ prm, const T* __restrict__ taps,
   }
 }
 
+// Streamed FP32 z factor: every z-row is a whole periodic line, so blocks
+// stream contiguous row ranges of the RHS and of u^n through a bulk-copy
+// ring (ZSTAGES slots of ZROWS rows each, mbarrier completion) and write
+// u* = u^n + sum_m t_|m| e_{k+m} with the periodic wrap as an index mask.
+constexpr int ZSTAGES = 6, ZROWS = 4;
+template <class T>
+__global__ void __launch_bounds__(256, 2)
+k_af_z_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ taps,
+            const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
+            T* __restrict__ u, T* __restrict__ v, T* __restrict__ w, int rows_per_block) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t full[ZSTAGES];
+  __shared__ T tp[2 * HMAX + 2];
+  const int n = c.nz, ny = c.ny;
+  const int comp = blockIdx.y;
+  const int first = comp == 0 ? ny : 0;       // u: planes 1..nx-1
+  const int last = c.nx * ny;
+  const int r0 = first + blockIdx.x * rows_per_block;
+  if (r0 >= last) return;
+  const int r1 = min(r0 + rows_per_block, last);
+  const int nrows = r1 - r0;
+  const int nst = (nrows + ZROWS - 1) / ZROWS;
+  const T* d = comp == 0 ? d0 : (comp == 1 ? d1 : d2);
+  T* q = comp == 0 ? u : (comp == 1 ? v : w);
+  T* ring = reinterpret_cast<T*>(smem_raw);   // [ZSTAGES][2][ZROWS][n]
+  const size_t rowb = (size_t)n * sizeof(T);
+  auto slot_ptr = [&](int slot) { return ring + (size_t)slot * 2 * ZROWS * n; };
+  auto issue = [&](int t) {
+    const int slot = t % ZSTAGES;
+    const int ra = r0 + t * ZROWS;
+    const int cnt = min(ZROWS, r1 - ra);
+    T* st = slot_ptr(slot);
+    mbar_arrive_expect_tx(&full[slot], (uint32_t)(2 * cnt * rowb));
+    bulk_g2s(st, d + (size_t)ra * n, (uint32_t)(cnt * rowb), &full[slot]);
+    bulk_g2s(st + (size_t)ZROWS * n, q + (size_t)ra * n, (uint32_t)(cnt * rowb), &full[slot]);
+  };
+  int lo, hi;
+  tap_range<T>(n, prm->af_h, lo, hi);
+  if (threadIdx.x == 0) {
+    for (int sl = 0; sl < ZSTAGES; ++sl) mbar_init(&full[sl], 1);
+    fence_mbar_init();
+  }
+  for (int m = threadIdx.x; m <= max(lo, hi); m += blockDim.x) tp[m] = taps[m];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int t = 0; t < ZSTAGES && t < nst; ++t) issue(t);
+  const int mask = n - 1, lg = __ffs(n) - 1;
+  for (int t = 0; t < nst; ++t) {
+    const bool ok = mbar_wait(&full[t % ZSTAGES], (uint32_t)((t / ZSTAGES) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(&prm->error, ERR_TIMEOUT);
+        for (int tt = t; tt < nst && tt < t + ZSTAGES; ++tt)
+          (void)mbar_wait(&full[tt % ZSTAGES], (uint32_t)((tt / ZSTAGES) & 1));
+      }
+      return;
+    }
+    const T* st = slot_ptr(t % ZSTAGES);
+    const int ra = r0 + t * ZROWS;
+    const int cnt = min(ZROWS, r1 - ra);
+    for (int e = threadIdx.x; e < cnt * n; e += blockDim.x) {
+      const int l = e >> lg, k = e & mask;
+      const T* dl = st + (size_t)l * n;
+      T acc = tp[0] * dl[k];
+      for (int m = 1; m <= lo && m <= hi; ++m) acc += tp[m] * (dl[(k + m) & mask] + dl[(k - m) & mask]);
+      if (hi > lo) acc += tp[hi] * dl[(k + hi) & mask];
+      q[(size_t)ra * n + e] = st[(size_t)ZROWS * n + e] + acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && t + ZSTAGES < nst) issue(t + ZSTAGES);
+  }
+}
+
 // ---------------------------------------------------------------- mass fix + divergence (A7)
 // Q_in, Q_out over the inflow/outflow faces (FP64, fixed summation order);
 // the shift (Q_in - Q_out) / (Ly Lz) goes onto the outflow face.
@@ -946,6 +1019,14 @@ static int af_z_lines(const Consts& c) { return 256 / ((c.nz + SEG - 1) / SEG); 
 template <class T>
 void launch_af_z(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
+    if ((c.nz * sizeof(T)) % 16 == 0) {
+      const int rpb = 512;
+      const size_t sh = (size_t)ZSTAGES * 2 * ZROWS * c.nz * sizeof(T);
+      k_af_z_pipe<T><<<dim3((c.nx * c.ny + rpb - 1) / rpb, 3), 256, sh, s>>>(
+          c, f.prm, (const T*)f.tapsf + c.ny, f.d[0], f.d[1], f.d[2], f.u[cur], f.v[cur], f.w[cur],
+          rpb);
+      return;
+    }
     const int halo = HMAX < c.nz / 2 ? HMAX : c.nz / 2;
     const size_t sh = (size_t)ZLC * (c.nz + 2 * halo) * sizeof(T);
     k_af_zc<T><<<dim3((c.nx * c.ny + ZLC - 1) / ZLC, 3), 256, sh, s>>>(
@@ -1005,6 +1086,7 @@ void fluid_set_attributes() {
   cudaFuncSetAttribute(k_rhs_pipe<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   cudaFuncSetAttribute(k_af_xc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_zc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_af_z_pipe<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_z<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_z<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }

@@ -22,6 +22,7 @@
 // which sets mean(phi) = 0.
 #include <cmath>
 
+#include "async_copy.cuh"
 #include "solver.h"
 
 namespace ibm {
@@ -101,9 +102,171 @@ k_dht(T* __restrict__ data, int n, int logn, int W, int lines_per_group, size_t 
   }
 }
 
-// Thomas solve along x per mode; rhs scaled by h^2 / (ny nz) (Hartley normalisation).
+// ---- 256-point transforms held in the registers of one warp (n = 256)
+// Four-step FFT, N = 8 x 32: lane l holds z[l + 32 m], m = 0..7; an 8-point
+// DFT over m in registers, twiddles W_256^{l p}, then a 32-point decimation-
+// in-frequency DFT across the lanes with shuffles. Lane l ends up holding
+// Z[p + 8 brev5(l)] in register p. Two real lines a, b travel as z = a + i b;
+// the Hartley outputs need Z_k and Z_{N-k}, fetched with one more shuffle.
 template <class T>
-__global__ void k_poisson_x(Consts c, const T* __restrict__ tab, T* __restrict__ phi, T scale) {
+struct Cx {
+  T r, i;
+};
+template <class T>
+__device__ inline Cx<T> cmul(Cx<T> a, Cx<T> b) {
+  return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r};
+}
+
+// in-register 8-point DFT: out[p] = sum_m in[m] W8^{m p}
+template <class T>
+__device__ inline void dft8(Cx<T> (&x)[8]) {
+  const T s = (T)0.70710678118654752440;
+  // radix-2 DIF stages (distance 4, 2, 1), outputs bit-reversed, then reorder
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const Cx<T> a = x[m], b = x[m + 4];
+    x[m] = {a.r + b.r, a.i + b.i};
+    Cx<T> d = {a.r - b.r, a.i - b.i};
+    // twiddle W8^m
+    if (m == 1) d = {s * (d.r + d.i), s * (d.i - d.r)};
+    if (m == 2) d = {d.i, -d.r};
+    if (m == 3) d = {s * (d.i - d.r), -s * (d.r + d.i)};
+    x[m + 4] = d;
+  }
+#pragma unroll
+  for (int g = 0; g < 8; g += 4)
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const Cx<T> a = x[g + m], b = x[g + m + 2];
+      x[g + m] = {a.r + b.r, a.i + b.i};
+      Cx<T> d = {a.r - b.r, a.i - b.i};
+      if (m == 1) d = {d.i, -d.r};   // W4^1 = -i
+      x[g + m + 2] = d;
+    }
+#pragma unroll
+  for (int g = 0; g < 8; g += 2) {
+    const Cx<T> a = x[g], b = x[g + 1];
+    x[g] = {a.r + b.r, a.i + b.i};
+    x[g + 1] = {a.r - b.r, a.i - b.i};
+  }
+  // bit-reversed (3 bits) -> natural order
+  Cx<T> t = x[1];
+  x[1] = x[4];
+  x[4] = t;
+  t = x[3];
+  x[3] = x[6];
+  x[6] = t;
+}
+
+template <class T>
+__device__ inline T shfl(T v, int lane) { return __shfl_sync(0xffffffffu, v, lane); }
+template <class T>
+__device__ inline T shfl_x(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+
+// tw: W_256^t = (cos, -sin)(2 pi t / 256), t = 0..255, in shared memory
+template <class T>
+__device__ inline void warp_hartley256(Cx<T> (&x)[8], const Cx<T>* tw, T (&ha)[8], T (&hb)[8]) {
+  const int l = threadIdx.x & 31;
+  dft8(x);
+#pragma unroll
+  for (int p = 1; p < 8; ++p) x[p] = cmul(x[p], tw[(l * p) & 255]);
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const bool upper = (l & d) != 0;
+    const Cx<T> w = tw[((l & (d - 1)) * (128 / d)) & 255];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const Cx<T> o = {shfl_x(x[p].r, d), shfl_x(x[p].i, d)};
+      if (upper) x[p] = cmul({o.r - x[p].r, o.i - x[p].i}, w);
+      else x[p] = {x[p].r + o.r, x[p].i + o.i};
+    }
+  }
+  const int q = (int)(__brev((unsigned)l) >> 27);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    const int pp = p == 0 ? 0 : 8 - p;
+    const int qq = p == 0 ? ((32 - q) & 31) : 31 - q;
+    const int src = (int)(__brev((unsigned)qq) >> 27);
+    const T wr = shfl(x[pp].r, src), wi = shfl(x[pp].i, src);
+    ha[p] = (T)0.5 * (x[p].r - x[p].i + wr + wi);
+    hb[p] = (T)0.5 * (x[p].r + x[p].i - wr + wi);
+  }
+}
+
+template <class T>
+__device__ inline void load_twiddles(Cx<T>* tw, const T* g) {
+  for (int t = threadIdx.x; t < 128; t += blockDim.x) {
+    tw[t] = {g[2 * t], g[2 * t + 1]};
+    tw[t + 128] = {-g[2 * t], -g[2 * t + 1]};   // W^{t+128} = -W^t
+  }
+  __syncthreads();
+}
+
+// z lines (contiguous rows of 256): one warp per pair of rows, in place
+template <class T>
+__global__ void __launch_bounds__(256) k_dht_z256(T* __restrict__ data, int nrows, const T* __restrict__ twg) {
+  __shared__ Cx<T> tw[256];
+  load_twiddles(tw, twg);
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int l = threadIdx.x & 31;
+  if (2 * warp + 1 >= nrows + 1) return;
+  T* a = data + (size_t)(2 * warp) * 256;
+  T* b = a + 256;
+  Cx<T> x[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) x[m] = {a[l + 32 * m], b[l + 32 * m]};
+  T ha[8], hb[8];
+  warp_hartley256(x, tw, ha, hb);
+  const int q = (int)(__brev((unsigned)l) >> 27);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    a[p + 8 * q] = ha[p];
+    b[p + 8 * q] = hb[p];
+  }
+}
+
+// y lines (columns of a plane, ny = 256): a block stages a 256 x 32 tile
+// (coalesced rows), 16 warps transform two columns each, the tile is stored back
+template <class T>
+__global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, const T* __restrict__ twg) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Cx<T> tw[256];
+  T* s = reinterpret_cast<T*>(smem_raw);   // [256][33]
+  const int ct = nz / 32;
+  const int plane = blockIdx.x / ct, c0 = (blockIdx.x - plane * ct) * 32;
+  T* base = data + (size_t)plane * 256 * nz + c0;
+  for (int e = threadIdx.x; e < 256 * 32; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    s[r * 33 + c] = base[(size_t)r * nz + c];
+  }
+  load_twiddles(tw, twg);   // includes __syncthreads
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  Cx<T> x[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) x[m] = {s[(l + 32 * m) * 33 + 2 * w], s[(l + 32 * m) * 33 + 2 * w + 1]};
+  T ha[8], hb[8];
+  warp_hartley256(x, tw, ha, hb);
+  __syncthreads();
+  const int q = (int)(__brev((unsigned)l) >> 27);
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    s[(p + 8 * q) * 33 + 2 * w] = ha[p];
+    s[(p + 8 * q) * 33 + 2 * w + 1] = hb[p];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 256 * 32; e += blockDim.x) {
+    const int r = e >> 5, c = e & 31;
+    base[(size_t)r * nz + c] = s[r * 33 + c];
+  }
+}
+
+// Thomas solve along x per mode; rhs scaled by h^2 / (ny nz) (Hartley
+// normalisation). One thread per mode walks x (coalesced across modes); the
+// loads of the next PF planes are issued ahead of the recursion so that each
+// thread keeps 2 PF independent loads in flight.
+constexpr int PF = 8;
+template <class T>
+__global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict__ tab, T* __restrict__ phi, T scale) {
   const int P = c.ny * c.nz;
   const int jk = blockIdx.x * blockDim.x + threadIdx.x;
   if (jk >= P) return;
@@ -112,14 +275,44 @@ __global__ void k_poisson_x(Consts c, const T* __restrict__ tab, T* __restrict__
   const T* iv = tab + jk;
   const bool zero_mode = (jk == 0);
   T y = 0;
-  for (int i = 0; i < nx; ++i) {
+  int i = 0;
+  for (; i + PF <= nx; i += PF) {
+    T rd[PF], rt[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      rd[q] = d[(size_t)(i + q) * P];
+      rt[q] = iv[(size_t)(i + q) * P];
+    }
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const T rhs = (zero_mode && i + q == 0) ? (T)0 : rd[q] * scale;
+      y = (rhs - y) * rt[q];
+      d[(size_t)(i + q) * P] = y;
+    }
+  }
+  for (; i < nx; ++i) {
     const size_t o = (size_t)i * P;
-    T rhs = (zero_mode && i == 0) ? (T)0 : d[o] * scale;
+    const T rhs = (zero_mode && i == 0) ? (T)0 : d[o] * scale;
     y = (rhs - y) * iv[o];
     d[o] = y;
   }
   T x = y;  // x_{nx-1} = dp_{nx-1}
-  for (int i = nx - 2; i >= 0; --i) {
+  i = nx - 2;
+  for (; i - PF + 1 >= 0; i -= PF) {
+    T rd[PF], rt[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      rd[q] = d[(size_t)(i - q) * P];
+      rt[q] = iv[(size_t)(i - q) * P];
+    }
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const T cp = (zero_mode && i - q == 0) ? (T)0 : rt[q];
+      x = rd[q] - cp * x;
+      d[(size_t)(i - q) * P] = x;
+    }
+  }
+  for (; i >= 0; --i) {
     const size_t o = (size_t)i * P;
     const T cp = (zero_mode && i == 0) ? (T)0 : iv[o];
     x = d[o] - cp * x;
@@ -127,9 +320,9 @@ __global__ void k_poisson_x(Consts c, const T* __restrict__ tab, T* __restrict__
   }
   if (zero_mode) {
     double s = 0.0;
-    for (int i = 0; i < nx; ++i) s += (double)d[(size_t)i * P];
+    for (int q = 0; q < nx; ++q) s += (double)d[(size_t)q * P];
     const T mean = (T)(s / nx);
-    for (int i = 0; i < nx; ++i) d[(size_t)i * P] -= mean;
+    for (int q = 0; q < nx; ++q) d[(size_t)q * P] -= mean;
   }
 }
 
@@ -158,6 +351,11 @@ __global__ void k_poisson_table(Consts c, T* __restrict__ tab) {
 
 template <class T>
 void launch_dht_y(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+  if (c.ny == 256 && c.nz % 32 == 0) {
+    const size_t sh = (size_t)256 * 33 * sizeof(T);
+    k_dht_y256<T><<<c.nx * (c.nz / 32), 512, sh, s>>>(f.phi, c.nz, f.tw_y);
+    return;
+  }
   const int n = c.ny, logn = (int)std::lround(std::log2((double)n));
   const int W = c.nz < 16 ? c.nz : 16;
   const size_t sh = (size_t)(W / 2) * n * sizeof(typename Vec2<T>::type);
@@ -168,6 +366,11 @@ void launch_dht_y(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 
 template <class T>
 void launch_dht_z(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+  if (c.nz == 256) {
+    const int rows = c.nx * c.ny;   // even: ny is an even power of two
+    k_dht_z256<T><<<(rows / 2 + 7) / 8, 256, 0, s>>>(f.phi, rows, f.tw_z);
+    return;
+  }
   const int n = c.nz, logn = (int)std::lround(std::log2((double)n));
   const int lines = c.nx * c.ny;
   int W = 16;
@@ -180,6 +383,7 @@ template <class T>
 void launch_poisson_x_on(const Consts& c, const Fields<T>& f, T* buf, cudaStream_t s) {
   const int P = c.ny * c.nz;
   const T scale = (T)(c.h * c.h / ((double)c.ny * c.nz));
+
   k_poisson_x<T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, buf, scale);
 }
 
@@ -218,6 +422,8 @@ template void launch_poisson_table<float>(const Consts&, const Fields<float>&, c
 
 // opt in to large dynamic shared memory for the transform kernels
 void poisson_set_attributes() {
+  cudaFuncSetAttribute(k_dht_y256<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_dht_y256<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_dht<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_dht<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_dht<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -96,6 +96,21 @@ def test_fp64_small_cases(lib, case):
     gpu.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_wide_transverse_grid(lib, precision):
+    """256 x 256 transverse planes (the size the register-resident transforms
+    and the streamed kernels are specialised for), 16 x-planes, 3 steps."""
+    from paper_2103_08246_gb300 import binding
+    prec = binding.IBM_FP64 if precision == "fp64" else binding.IBM_FP32
+    wl = _small(shape=(16, 256, 256))
+    gpu, ora = _run(wl, prec, 3)
+    if prec == binding.IBM_FP64:
+        _compare(gpu, ora, 1e-9)
+    else:
+        _compare(gpu, ora, FP32_TOL, floor=FP32_FLOOR)
+    gpu.close()
+
+
 def test_fp64_single_step_each_stage(lib):
     from paper_2103_08246_gb300 import binding
     wl = _small(bars_on=True, bar_x=1.0, **FLAG)
