@@ -601,6 +601,8 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   c.ly = d->ly;
   c.lz = d->lz;
   c.u_in = 1.0;
+  c.f_inv_h = (float)c.inv_h;
+  c.f_inv_h2 = (float)(c.inv_h * c.inv_h);
   c.rhs_planes = (o && o->rhs_planes > 0) ? o->rhs_planes : 32;
   c.afx_planes = (o && o->afx_planes > 0) ? o->afx_planes : 64;
   bar_dv = 0.0;
@@ -718,6 +720,7 @@ int ibm_create(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodi
   int rc = prepare(g, d, b, o, s.get(), fg, Xb, bdv, L);
   if (rc) return rc;
   s->c.nu = 1.0 / re;
+  s->c.f_nu = (float)s->c.nu;
   const size_t need = s->precision == IBM_FP64 ? carve<double>(s.get(), nullptr, L, s->fd)
                                                : carve<float>(s.get(), nullptr, L, s->ff);
   if (workspace) {

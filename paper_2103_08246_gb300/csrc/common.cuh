@@ -30,6 +30,14 @@ struct Params {
   int flag_pending;   // 1 after a forcing step until the flag has been advanced
   int af_h;           // warm-up length of the segmented implicit line solves
   double af_rho;      // exp(-theta) of the implicit factors
+  // FP32 copies of the per-step scalars, written once per step, so that FP32
+  // kernels never convert from FP64 per thread (conversions run on the FP64
+  // pipe)
+  float f_dt, f_alpha, f_beta, f_r, f_ir, f_rho, f_mass_shift;
+  float f_gdt;        // dt / h
+  float f_hnu;        // nu dt / (2 h^2)
+  float f_cc;         // U dt / h
+  float f_sc_div;     // 1 / (h dt)
 };
 
 // Host-provided constants of a problem.
@@ -40,7 +48,15 @@ struct Consts {
   double omega_max;   // structural stiffness bound (sub-step count)
   int rhs_planes;     // tile: x planes per block of the streamed RHS
   int afx_planes;     // tile: x planes per block of the FP32 x factor
+  float f_inv_h, f_inv_h2, f_nu;   // FP32 copies
 };
+
+// the per-step scalar in the precision of the kernel
+template <class T>
+__device__ __forceinline__ T pick(double d, float f) {
+  if constexpr (sizeof(T) == 8) return (T)d;
+  else return (T)f;
+}
 
 constexpr int ERR_AF_RANGE = 1;     // implicit diffusion number outside range
 constexpr int ERR_NONFINITE = 2;    // non-finite CFL speed

@@ -77,6 +77,16 @@ __global__ void k_begin_step(Consts c, Params* prm, const double* __restrict__ p
     prm->af_rho = rho;
     prm->af_h = H;
     prm->n_sub = ns < 1.0 ? 1 : (ns > 1e6 ? 1000000 : (int)ns);
+    prm->f_dt = (float)dt;
+    prm->f_alpha = (float)alpha;
+    prm->f_beta = (float)beta;
+    prm->f_r = (float)r;
+    prm->f_ir = (float)(1.0 / r);
+    prm->f_rho = (float)rho;
+    prm->f_gdt = (float)(dt * c.inv_h);
+    prm->f_hnu = (float)(0.5 * c.nu * dt * c.inv_h * c.inv_h);
+    prm->f_cc = (float)(c.u_in * dt * c.inv_h);
+    prm->f_sc_div = (float)(c.inv_h / dt);
     if (err) prm->error |= err;
     sh_r = r;
   }
@@ -136,8 +146,10 @@ k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
   const int nx = c.nx, ny = c.ny, nz = c.nz;
   const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
   const int km = k == 0 ? nz - 1 : k - 1, kp = k == nz - 1 ? 0 : k + 1;
-  const T dt = (T)prm->dt, alpha = (T)prm->alpha, beta = (T)prm->beta;
-  const T nu = (T)c.nu, ih = (T)c.inv_h, ih2 = (T)(c.inv_h * c.inv_h), hf = (T)0.5;
+  const T dt = pick<T>(prm->dt, prm->f_dt), alpha = pick<T>(prm->alpha, prm->f_alpha);
+  const T beta = pick<T>(prm->beta, prm->f_beta);
+  const T nu = pick<T>(c.nu, c.f_nu), ih = pick<T>(c.inv_h, c.f_inv_h);
+  const T ih2 = pick<T>(c.inv_h * c.inv_h, c.f_inv_h2), hf = (T)0.5;
   const size_t P = plane(c);
   auto at = [&](int i, int jj, int kk) { return ((size_t)i * ny + jj) * nz + kk; };
   const int i0 = blockIdx.z * XCHUNK;
@@ -288,8 +300,10 @@ k_rhs_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ u,
   __syncthreads();
   if (tid == 0)
     for (int t = 0; t < RSTAGES && t < nstage; ++t) issue(t);
-  const T dt = (T)prm->dt, alpha = (T)prm->alpha, beta = (T)prm->beta;
-  const T nu = (T)c.nu, ih = (T)c.inv_h, ih2 = (T)(c.inv_h * c.inv_h), hf = (T)0.5;
+  const T dt = pick<T>(prm->dt, prm->f_dt), alpha = pick<T>(prm->alpha, prm->f_alpha);
+  const T beta = pick<T>(prm->beta, prm->f_beta);
+  const T nu = pick<T>(c.nu, c.f_nu), ih = pick<T>(c.inv_h, c.f_inv_h);
+  const T ih2 = pick<T>(c.inv_h * c.inv_h, c.f_inv_h2), hf = (T)0.5;
   const int mask = nz - 1;
   const int ncell = TJR * nz;
   const int lg = __ffs(nz) - 1;
@@ -411,7 +425,7 @@ __global__ void k_outflow(Consts c, const Params* __restrict__ prm, T* __restric
   const int jk = blockIdx.x * blockDim.x + threadIdx.x;
   const int P = c.ny * c.nz;
   if (jk >= P) return;
-  const T cc = (T)(c.u_in * prm->dt * c.inv_h);
+  const T cc = pick<T>(c.u_in * prm->dt * c.inv_h, prm->f_cc);
   const size_t last = (size_t)c.nx * P + jk, prev = last - P;
   T inc = -cc * (u[last] - u[prev]);
   u[last] += inc;
@@ -455,7 +469,7 @@ k_af_x(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
   const int k1 = min(k0 + SEG, m + 1);
   const int H = prm->af_h;
   const T* ip = ipt + (comp == 0 ? 0 : c.nx + 2);
-  const T ir = (T)(1.0 / prm->r);
+  const T ir = pick<T>(1.0 / prm->r, prm->f_ir);
   const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + jk + (size_t)ioff * P;
   T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + jk + (size_t)ioff * P;
   const T ob = (comp == 0 ? o0 : comp == 1 ? o1 : o2)[jk];
@@ -486,6 +500,53 @@ k_af_x(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
       x = yr[q] + x * ip[k];
       if (k < k1) out[(size_t)k * P] = x;
     }
+  }
+}
+
+// x factor by the LU recursions on shared-memory-staged planes: one warp per
+// 32 consecutive (y, z) columns and XS planes (+ warm-up halos); lanes walk
+// their columns (bank-conflict free), loads and stores are 128-byte rows.
+constexpr int XS = 64;
+template <class T>
+__global__ void __launch_bounds__(32)
+k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
+        const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
+        T* __restrict__ e0, T* __restrict__ e1, T* __restrict__ e2, const T* __restrict__ o0,
+        const T* __restrict__ o1, const T* __restrict__ o2) {
+  __shared__ T s[(XS + 2 * HMAX) * 32];
+  const int P = c.ny * c.nz;
+  const int lane = threadIdx.x;
+  const int col0 = blockIdx.x * 32;
+  const int comp = blockIdx.z;
+  const int m = comp == 0 ? c.nx - 1 : c.nx;   // unknowns k = 1..m
+  const int ioff = comp == 0 ? 0 : -1;         // plane i = k + ioff
+  const int k0 = 1 + blockIdx.y * XS;
+  if (k0 > m) return;
+  const int k1 = min(k0 + XS, m + 1);
+  const int H = prm->af_h;
+  const int ks = max(1, k0 - H), ke = min(m, k1 - 1 + H);
+  const T* ip = ipt + (comp == 0 ? 0 : c.nx + 2);
+  const T ir = pick<T>(1.0 / prm->r, prm->f_ir);
+  const int col = col0 + lane;
+  const bool act = col < P;
+  const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + (size_t)ioff * P + col;
+  T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + (size_t)ioff * P + col;
+  const T ob = act ? (comp == 0 ? o0 : comp == 1 ? o1 : o2)[col] : (T)0;
+  if (act)
+    for (int k = ks; k <= ke; ++k) s[(k - ks) * 32 + lane] = d[(size_t)k * P];
+  __syncwarp();
+  if (!act) return;
+  T y = 0;
+  for (int k = ks; k <= ke; ++k) {
+    T e = s[(k - ks) * 32 + lane] * ir;
+    if (k == m) e += ob;
+    y = (e + y) * ip[k];
+    s[(k - ks) * 32 + lane] = y;
+  }
+  T x = 0;
+  for (int k = ke; k >= k0; --k) {
+    x = s[(k - ks) * 32 + lane] + x * ip[k];
+    if (k < k1) out[(size_t)k * P] = x;
   }
 }
 
@@ -537,7 +598,8 @@ k_af_y(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
   T* out = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + base;
   const int j0 = seg * SEG, j1 = min(j0 + SEG, c.ny);
   const size_t st = (size_t)c.nz;
-  periodic_segment<T>(c.ny, j0, j1, prm->af_h, (T)prm->af_rho, (T)(1.0 / prm->r),
+  periodic_segment<T>(c.ny, j0, j1, prm->af_h, pick<T>(prm->af_rho, prm->f_rho),
+                      pick<T>(1.0 / prm->r, prm->f_ir),
                       [&](int j) { return in[(size_t)j * st]; },
                       [&](int j, T v) { out[(size_t)j * st] = v; });
 }
@@ -575,7 +637,8 @@ k_af_z(Consts c, const Params* __restrict__ prm, const T* __restrict__ d0,
   const int j0 = seg * SEG, j1 = min(j0 + SEG, nz);
   if (l < nl) {
     const T* line = s + l * ld;
-    periodic_segment<T>(nz, j0, j1, prm->af_h, (T)prm->af_rho, (T)(1.0 / prm->r),
+    periodic_segment<T>(nz, j0, j1, prm->af_h, pick<T>(prm->af_rho, prm->f_rho),
+                        pick<T>(1.0 / prm->r, prm->f_ir),
                         [&](int j) { return line[j]; },
                         [&](int j, T val) { xo[j - j0] = val; });
   }
@@ -639,7 +702,7 @@ k_af_xc(Consts c, const Params* __restrict__ prm, const T* __restrict__ taps,
   const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + col0;
   T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + col0;
   const T* ob = (comp == 0 ? o0 : comp == 1 ? o1 : o2) + col0;
-  const T rr_ = (T)prm->r;
+  const T rr_ = pick<T>(prm->r, prm->f_r);
   const int rows = ni + 2 * H;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   for (int e = tid; e < rows * 32; e += 256) {
@@ -809,6 +872,7 @@ __global__ void k_mass(Consts c, Params* prm, const T* __restrict__ u) {
     prm->q_in = qi * h2;
     prm->q_out = qo * h2;
     prm->mass_shift = (qi - qo) * h2 / (c.ly * c.lz);
+    prm->f_mass_shift = (float)prm->mass_shift;
   }
 }
 
@@ -822,8 +886,8 @@ k_div(Consts c, const Params* __restrict__ prm, T* __restrict__ u, const T* __re
   const int ny = c.ny, nz = c.nz, nx = c.nx;
   const int jp = j == ny - 1 ? 0 : j + 1, kp = k == nz - 1 ? 0 : k + 1;
   const size_t P = plane(c);
-  const T shift = initial ? (T)0 : (T)prm->mass_shift;
-  const T sc = (T)(c.inv_h / (initial ? 1.0 : prm->dt));
+  const T shift = initial ? (T)0 : pick<T>(prm->mass_shift, prm->f_mass_shift);
+  const T sc = initial ? pick<T>(c.inv_h, c.f_inv_h) : pick<T>(c.inv_h / prm->dt, prm->f_sc_div);
   const int i0 = blockIdx.z * XCHUNK, i1 = min(i0 + XCHUNK, nx);
   for (int i = i0; i < i1; ++i) {
     const size_t id = ((size_t)i * ny + j) * nz + k;
@@ -857,9 +921,8 @@ k_project(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
   if (act) {
     const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
     const int km = k == 0 ? nz - 1 : k - 1, kp = k == nz - 1 ? 0 : k + 1;
-    const T dt = initial ? (T)1 : (T)prm->dt;
-    const T gdt = dt * (T)c.inv_h;
-    const T hnu = initial ? (T)0 : (T)(0.5 * c.nu * prm->dt * c.inv_h * c.inv_h);
+    const T gdt = initial ? pick<T>(c.inv_h, c.f_inv_h) : pick<T>(prm->dt * c.inv_h, prm->f_gdt);
+    const T hnu = initial ? (T)0 : pick<T>(0.5 * c.nu * prm->dt * c.inv_h * c.inv_h, prm->f_hnu);
     auto at = [&](int i, int jj, int kk) { return ((size_t)i * ny + jj) * nz + kk; };
     auto unew = [&](int i) -> T {  // new u on face i at (j, k)
       const size_t id = at(i, j, k);
@@ -988,6 +1051,15 @@ void launch_outflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s
 template <class T>
 void launch_af_x(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   const int P = c.ny * c.nz;
+  {
+    const T* tab;
+    if constexpr (sizeof(T) == 8) tab = (const T*)f.ipt; else tab = (const T*)f.iptf;
+    k_af_xr<T><<<dim3((P + 31) / 32, (c.nx + XS - 1) / XS, 3), 32, 0, s>>>(
+        c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2], f.dout[0], f.dout[1],
+        f.dout[2]);
+    (void)cur;
+    return;
+  }
   if constexpr (sizeof(T) == 4) {
     const int XC = c.afx_planes;
     const size_t sh = (size_t)(XC + 2 * HMAX) * 32 * sizeof(T);

@@ -33,21 +33,41 @@ struct Stencil {
   bool vi[3];
 };
 
-// 3-node stencil per direction of component `comp` for a marker at X
+// Per marker and direction: base node index and fractional offset of the
+// two staggered lattices (node offset 0 and 1/2), computed once in FP64;
+// weights phi(t - 1/2 - f), t = 0, 1, 2, then follow in the field precision.
 template <class T>
-__device__ inline void stencil(const Consts& c, int comp, double X, double Y, double Z,
-                               Stencil& st, T wx[3], T wy[3], T wz[3]) {
-  const double ox = comp == 0 ? 0.0 : 0.5;
-  const double oy = comp == 1 ? 0.0 : 0.5;
-  const double oz = comp == 2 ? 0.0 : 0.5;
-  const double sx = X * c.inv_h - ox, sy = Y * c.inv_h - oy, sz = Z * c.inv_h - oz;
-  const int ix = (int)floor(sx - 0.5), iy = (int)floor(sy - 0.5), iz = (int)floor(sz - 0.5);
+struct Frac {
+  int i0[2];
+  T f[2];
+};
+template <class T>
+__device__ inline Frac<T> frac_of(double s) {   // s = X / h
+  Frac<T> r;
+#pragma unroll
+  for (int o = 0; o < 2; ++o) {
+    const double a = s - 0.5 * o - 0.5;
+    const double fl = floor(a);
+    r.i0[o] = (int)fl;
+    r.f[o] = (T)(a - fl);
+  }
+  return r;
+}
+
+// 3-node stencil per direction of component `comp`
+template <class T>
+__device__ inline void stencil(const Consts& c, int comp, const Frac<T>& fx, const Frac<T>& fy,
+                               const Frac<T>& fz, Stencil& st, T wx[3], T wy[3], T wz[3]) {
+  const int ox = comp == 0 ? 0 : 1, oy = comp == 1 ? 0 : 1, oz = comp == 2 ? 0 : 1;
+  const int ix = fx.i0[ox], iy = fy.i0[oy], iz = fz.i0[oz];
   const int lo = comp == 0 ? 1 : 0, hi = c.nx - 1;
   st.i0 = ix;
+#pragma unroll
   for (int t = 0; t < 3; ++t) {
-    wx[t] = roma_phi<T>((T)(ix + t - sx));
-    wy[t] = roma_phi<T>((T)(iy + t - sy));
-    wz[t] = roma_phi<T>((T)(iz + t - sz));
+    const T tt = (T)t - (T)0.5;
+    wx[t] = roma_phi<T>(tt - fx.f[ox]);
+    wy[t] = roma_phi<T>(tt - fy.f[oy]);
+    wz[t] = roma_phi<T>(tt - fz.f[oz]);
     st.vi[t] = (ix + t >= lo) && (ix + t <= hi);
     int jj = (iy + t) % c.ny;
     if (jj < 0) jj += c.ny;
@@ -96,11 +116,13 @@ __global__ void k_ib_interp(Consts c, Params* prm, Markers m, Flag fl, const T* 
     const bool ok = marker(m, fl, l, X, Y, Z, U, dv);
     double us[3] = {0.0, 0.0, 0.0};
     if (ok) {
+      const Frac<T> fx = frac_of<T>(X * c.inv_h), fy = frac_of<T>(Y * c.inv_h),
+                    fz = frac_of<T>(Z * c.inv_h);
       for (int comp = 0; comp < 3; ++comp) {
         const T* q = comp == 0 ? u : (comp == 1 ? v : w);
         Stencil st;
         T wx[3], wy[3], wz[3];
-        stencil<T>(c, comp, X, Y, Z, st, wx, wy, wz);
+        stencil<T>(c, comp, fx, fy, fz, st, wx, wy, wz);
         T acc = 0;
         for (int a = 0; a < 3; ++a) {
           if (!st.vi[a]) continue;
@@ -134,13 +156,15 @@ __global__ void k_ib_spread(Consts c, Markers m, Flag fl, T* __restrict__ u, T* 
   if (l >= m.nm) return;
   double X, Y, Z, U[3], dv;
   if (!marker(m, fl, l, X, Y, Z, U, dv)) return;
+  const Frac<T> fx = frac_of<T>(X * c.inv_h), fy = frac_of<T>(Y * c.inv_h),
+                fz = frac_of<T>(Z * c.inv_h);
   for (int comp = 0; comp < 3; ++comp) {
     const T cf = (T)m.coef[3 * l + comp];
     if (cf == (T)0) continue;
     T* q = comp == 0 ? u : (comp == 1 ? v : w);
     Stencil st;
     T wx[3], wy[3], wz[3];
-    stencil<T>(c, comp, X, Y, Z, st, wx, wy, wz);
+    stencil<T>(c, comp, fx, fy, fz, st, wx, wy, wz);
     for (int a = 0; a < 3; ++a) {
       if (!st.vi[a] || wx[a] == (T)0) continue;
       const size_t pi = (size_t)(st.i0 + a) * c.ny;
