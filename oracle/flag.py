@@ -31,8 +31,9 @@ differentiation of the energy (PyTorch CPU, FP64). LE vertices are held fixed
 (the hinge transmits no moment because no bending spring crosses the LE).
 
 Time integration: velocity Verlet with n_sub equal sub-steps per fluid step,
-n_sub = ceil(dt * omega_max), where omega_max^2 bounds the linearised
-stiffness-over-mass spectrum by Gershgorin's theorem:
+n_sub = ceil(dt * omega_max / 1.8): velocity Verlet is stable for
+dt_s * omega < 2, and omega_max bounds the linearised stiffness-over-mass
+spectrum from above by Gershgorin's theorem, so dt_s * omega <= 1.8:
     omega_max^2 = max_v (2 k_s n_springs(v) + 8 sum_{hinges at v} k_e / l_min^2) / m_v
 over free vertices. The fluid force is held constant over the sub-steps.
 """
@@ -146,7 +147,7 @@ class FlagMesh:
         return math.sqrt(float(np.max(w2[self.free])))
 
     def substeps(self, dt):
-        return max(1, int(math.ceil(dt * self.omega_max())))
+        return max(1, int(math.ceil(dt * self.omega_max() / 1.8)))
 
 
 def energy(X, mesh, l0):

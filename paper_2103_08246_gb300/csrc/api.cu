@@ -351,6 +351,7 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   f.tw_z = cv.take<T>(c.nz);
   f.n_partial = partial_count(c);
   f.partial = cv.take<double>(f.n_partial);
+  f.qpart = cv.take<double>(2 * (size_t)outflow_blocks(c));
   f.prm = cv.take<Params>(1);
   s->dstat = cv.take<double>(16);
   Markers& m = s->mk;

@@ -48,13 +48,22 @@ __device__ inline void st3(double* p, int q, D3 f) {
   p[3 * q + 2] = f.z;
 }
 
+// 1 / sqrt(x) in FP64 from the FP32 estimate and one Newton-Raphson step for
+// f(y) = 1/y^2 - x: y1 = y0 (3/2 - x y0^2 / 2). The FP32 estimate carries a
+// relative error below ~2^-22, one step squares it (~1e-13), well inside the
+// parity bound of the structural solve; FP64 work drops to a few multiplies.
+__device__ inline double rsqrt_nr(double x) {
+  const double y0 = (double)rsqrtf((float)x);
+  return y0 * (1.5 - 0.5 * x * y0 * y0);
+}
+
 // unit normals of all triangles, stretching forces of all springs
 __device__ void phase_normals_springs(const Flag& fl, int gt, int G) {
   for (int t = gt; t < fl.n_tri; t += G) {
     const int* tv = fl.tri + 3 * t;
     const D3 p0 = ld3(fl.X, tv[0]), p1 = ld3(fl.X, tv[1]), p2 = ld3(fl.X, tv[2]);
     const D3 N = cross(p1 - p0, p2 - p0);
-    const double inv = rsqrt(dot(N, N));
+    const double inv = rsqrt_nr(dot(N, N));
     st3(fl.tri_n, t, inv * N);
     fl.tri_inv[t] = inv;
   }
@@ -63,7 +72,7 @@ __device__ void phase_normals_springs(const Flag& fl, int gt, int G) {
     const int a = fl.spring[2 * q], b = fl.spring[2 * q + 1];
     const D3 d = ld3(fl.X, b) - ld3(fl.X, a);
     const double len2 = dot(d, d);
-    const double il = rsqrt(len2);
+    const double il = rsqrt_nr(len2);
     const D3 f = (fl.k_s * (len2 * il - fl.l0[q]) * il) * d;   // pulls a towards b when stretched
     st3(fl.slot, base + 2 * q, f);
     st3(fl.slot, base + 2 * q + 1, -1.0 * f);

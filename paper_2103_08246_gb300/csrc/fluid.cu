@@ -67,7 +67,9 @@ __global__ void k_begin_step(Consts c, Params* prm, const double* __restrict__ p
       err |= ERR_AF_RANGE;
       H = HMAX;
     }
-    const double ns = ceil(dt * c.omega_max);
+    // velocity Verlet is stable for dt_s omega < 2; omega_max is a Gershgorin
+    // upper bound, so dt_s = dt / n_sub <= 1.8 / omega_max keeps every mode stable
+    const double ns = ceil(dt * c.omega_max / 1.8);
     prm->speed_max = m;
     prm->slip_max = 0.0;
     prm->dt = dt;
@@ -417,25 +419,42 @@ k_rhs_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ u,
 
 // ---------------------------------------------------------------- outflow (A1)
 // Convective condition dq/dt + U dq/dx = 0 on the outflow plane, first-order
-// upwind; the increment is kept for the x line solve.
+// upwind; the increment is kept for the x line solve. The inflow and new
+// outflow face fluxes are summed per block in FP64 (fixed order) for the
+// mass fix; the IB forcing never touches these two planes.
+constexpr int OUT_THREADS = 256;
 template <class T>
-__global__ void k_outflow(Consts c, const Params* __restrict__ prm, T* __restrict__ u,
-                          T* __restrict__ v, T* __restrict__ w, T* __restrict__ o0,
-                          T* __restrict__ o1, T* __restrict__ o2) {
+__global__ void __launch_bounds__(OUT_THREADS)
+k_outflow(Consts c, const Params* __restrict__ prm, T* __restrict__ u,
+          T* __restrict__ v, T* __restrict__ w, T* __restrict__ o0, T* __restrict__ o1,
+          T* __restrict__ o2, double* __restrict__ qpart) {
+  __shared__ double scratch[32];
   const int jk = blockIdx.x * blockDim.x + threadIdx.x;
   const int P = c.ny * c.nz;
-  if (jk >= P) return;
-  const T cc = pick<T>(c.u_in * prm->dt * c.inv_h, prm->f_cc);
-  const size_t last = (size_t)c.nx * P + jk, prev = last - P;
-  T inc = -cc * (u[last] - u[prev]);
-  u[last] += inc;
-  o0[jk] = inc;
-  inc = -cc * (v[last] - v[prev]);
-  v[last] += inc;
-  o1[jk] = inc;
-  inc = -cc * (w[last] - w[prev]);
-  w[last] += inc;
-  o2[jk] = inc;
+  double qi = 0.0, qo = 0.0;
+  if (jk < P) {
+    const T cc = pick<T>(c.u_in * prm->dt * c.inv_h, prm->f_cc);
+    const size_t last = (size_t)c.nx * P + jk, prev = last - P;
+    T inc = -cc * (u[last] - u[prev]);
+    const T un = u[last] + inc;
+    u[last] = un;
+    o0[jk] = inc;
+    inc = -cc * (v[last] - v[prev]);
+    v[last] += inc;
+    o1[jk] = inc;
+    inc = -cc * (w[last] - w[prev]);
+    w[last] += inc;
+    o2[jk] = inc;
+    qi = (double)u[jk];
+    qo = (double)un;
+  }
+  qi = block_sum(qi, scratch);
+  __syncthreads();
+  qo = block_sum(qo, scratch);
+  if (threadIdx.x == 0) {
+    qpart[2 * blockIdx.x] = qi;
+    qpart[2 * blockIdx.x + 1] = qo;
+  }
 }
 
 // ---------------------------------------------------------------- implicit factors (A3)
@@ -853,16 +872,13 @@ k_af_z_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ taps,
 // ---------------------------------------------------------------- mass fix + divergence (A7)
 // Q_in, Q_out over the inflow/outflow faces (FP64, fixed summation order);
 // the shift (Q_in - Q_out) / (Ly Lz) goes onto the outflow face.
-template <class T>
-__global__ void k_mass(Consts c, Params* prm, const T* __restrict__ u) {
+// reduce the outflow kernel's per-block flux partials (fixed order)
+__global__ void k_mass(Consts c, Params* prm, const double* __restrict__ qpart, int nb) {
   __shared__ double scratch[32];
-  const int P = c.ny * c.nz;
   double qi = 0.0, qo = 0.0;
-  const T* u0 = u;
-  const T* un = u + (size_t)c.nx * P;
-  for (int e = threadIdx.x; e < P; e += blockDim.x) {
-    qi += (double)u0[e];
-    qo += (double)un[e];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    qi += qpart[2 * b];
+    qo += qpart[2 * b + 1];
   }
   qi = block_sum(qi, scratch);
   __syncthreads();
@@ -1041,11 +1057,12 @@ void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
                                                         f.d[1], f.d[2]);
 }
 
+int outflow_blocks(const Consts& c) { return (c.ny * c.nz + OUT_THREADS - 1) / OUT_THREADS; }
+
 template <class T>
 void launch_outflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
-  const int P = c.ny * c.nz;
-  k_outflow<T><<<(P + 255) / 256, 256, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.dout[0],
-                                                f.dout[1], f.dout[2]);
+  k_outflow<T><<<outflow_blocks(c), OUT_THREADS, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
+                                                         f.dout[0], f.dout[1], f.dout[2], f.qpart);
 }
 
 template <class T>
@@ -1120,7 +1137,8 @@ void launch_af(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
 
 template <class T>
 void launch_mass(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
-  k_mass<T><<<1, 1024, 0, s>>>(c, f.prm, f.u[cur]);
+  k_mass<<<1, 1024, 0, s>>>(c, f.prm, f.qpart, outflow_blocks(c));
+  (void)cur;
 }
 
 template <class T>

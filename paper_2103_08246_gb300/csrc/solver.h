@@ -22,6 +22,7 @@ struct Fields {
   T* dout[3];                 // outflow-plane increments (ny * nz each)
   T* tw_y; T* tw_z;           // FFT twiddles exp(-2 pi i t / N), t < N/2 (re, im)
   double* partial;            // per-block partial maxima of the CFL speed
+  double* qpart;              // per-block inflow/outflow flux partials
   int n_partial;
   Params* prm;
 };
@@ -73,6 +74,7 @@ template <class T> void launch_project_only(const Consts& c, const Fields<T>& f,
 template <class T> void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 template <class T> void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 int partial_count(const Consts& c);
+int outflow_blocks(const Consts& c);
 void fluid_set_attributes();
 template <class T> void launch_stats(const Consts& c, const Fields<T>& f, int cur, double* out, cudaStream_t s);
 

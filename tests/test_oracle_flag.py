@@ -157,3 +157,47 @@ def test_euler_bernoulli_first_mode_frequency():
     assert err17 < 0.02, (w17, w_th)
     w9, _ = _first_mode_frequency(9)
     assert abs(w9 - w_th) / w_th > err17      # converges with resolution
+
+
+def _hessian_omega(m, X0, l0):
+    """Largest eigenfrequency of M^-1 K on the free vertices (exact, by eigh)."""
+    Xt = torch.tensor(X0, dtype=torch.float64)
+    H = torch.autograd.functional.hessian(lambda x: flag.energy(x.reshape(-1, 3), m, l0),
+                                          Xt.reshape(-1)).numpy()
+    free = np.repeat(m.free, 3)
+    minv = 1.0 / np.sqrt(np.repeat(m.mass, 3)[free])
+    Hf = H[np.ix_(free, free)] * minv[:, None] * minv[None, :]
+    return math.sqrt(max(np.linalg.eigvalsh(Hf).max(), 0.0))
+
+
+def test_substeps_respect_the_verlet_stability_limit():
+    """Gershgorin bounds the true spectrum, so dt_s * omega_true <= 1.8 < 2;
+    energy stays bounded over many sub-steps there, while a step 15 % past
+    the stability limit 2 / omega_true blows up (the bound is not vacuous)."""
+    m = _mesh(5, 4, ks=400.0, kb=0.5)
+    X0 = _flat(m, 0.8)
+    l0 = m.rest_lengths(X0)
+    rng = np.random.default_rng(3)
+    Xp = X0 + np.where(m.free[:, None], 1e-3 * rng.standard_normal(X0.shape), 0.0)
+    w_true = _hessian_omega(m, Xp, l0)
+    w_bound = m.omega_max()
+    assert w_true <= w_bound
+
+    def total_energy(X, V):
+        Xt = torch.tensor(X, dtype=torch.float64)
+        return float(flag.energy(Xt, m, l0)) + 0.5 * float((m.mass[:, None] * V * V).sum())
+
+    dt = 0.05
+    n_sub = m.substeps(dt)
+    assert dt / n_sub * w_bound <= 1.8 + 1e-12
+    X, V = Xp.copy(), np.zeros_like(Xp)
+    e0 = total_energy(X, V)
+    for _ in range(40):
+        X, V = flag.advance(X, V, np.zeros_like(X), dt, m, l0)
+    assert total_energy(X, V) < 1.5 * e0
+
+    h_bad = 2.3 / w_true
+    X, V = Xp.copy(), np.zeros_like(Xp)
+    for _ in range(40):
+        X, V = flag.advance(X, V, np.zeros_like(X), h_bad, m, l0, n_sub=1)
+    assert not np.isfinite(total_energy(X, V)) or total_energy(X, V) > 1e3 * e0
