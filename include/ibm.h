@@ -65,8 +65,8 @@ extern "C" {
 #define IBM_STAGE_RHS        0  /* explicit right-hand side (AB2 + CN half)   */
 #define IBM_STAGE_OUTFLOW    1  /* convective outflow plane                   */
 #define IBM_STAGE_AF_X       2  /* implicit factor along x                    */
-#define IBM_STAGE_AF_Y       3  /* implicit factor along y (periodic)         */
-#define IBM_STAGE_AF_Z       4  /* implicit factor along z (periodic) + u*    */
+#define IBM_STAGE_AF_Y       3  /* implicit factor along y (periodic), separate */
+#define IBM_STAGE_AF_Z       4  /* implicit factor along z (periodic) + u*, separate */
 #define IBM_STAGE_IB         5  /* marker interpolation + spreading           */
 #define IBM_STAGE_FLAG       6  /* structural sub-steps                       */
 #define IBM_STAGE_MASS_DIV   7  /* mass fix + divergence                      */
@@ -75,6 +75,11 @@ extern "C" {
 #define IBM_STAGE_POISSON_X 10  /* tridiagonal solves along x                 */
 #define IBM_STAGE_PROJECT   11  /* projection + pressure update               */
 #define IBM_STAGE_POISSON   12  /* the whole pressure solve of the precision   */
+#define IBM_STAGE_AF_YZ     13  /* y and z factors + u* in one kernel (used by the
+                                   step when nz = 32, 64, 128 or 256 and ny is a
+                                   multiple of 32 (FP32) or 16 (FP64); otherwise
+                                   the step runs AF_Y and AF_Z and this stage
+                                   launches nothing)                          */
 
 /* field selectors for ibm_get_field / ibm_set_field */
 #define IBM_FIELD_U 0
@@ -124,10 +129,14 @@ typedef struct {
   const double* init_w;
   /* Tile parameters (0: defaults). rhs_planes: x planes per block of the
    * streamed explicit stage [32], in [2, 256]; afx_planes: x planes per block
-   * of the FP32 implicit x factor [64], in [8, 256]. Results do not depend
-   * on them; ibm_autotune-style searches pick them per problem shape. */
+   * of the FP32 implicit x factor [64], in [8, 256]; rhs_stages: depth of the
+   * explicit stage's shared-memory ring in x planes [as many as 210 KB
+   * holds, at most 8], in [4, 8] (fewer than asked if they do not fit).
+   * Results do not depend on them; the package's autotuner picks them per
+   * problem shape. */
   int rhs_planes;
   int afx_planes;
+  int rhs_stages;
 } ibm_options;
 
 /* Diagnostics read by ibm_stats (all FP64). */
@@ -199,6 +208,23 @@ int ibm_set_field(ibm_state* s, int which, const double* host, size_t n);
  * positions at the start of the next step (3 doubles each). */
 int ibm_marker_count(const ibm_state* s, size_t* n);
 int ibm_get_markers(ibm_state* s, double* X, size_t n);
+
+/* Checkpoint / restart. ibm_save writes everything the next step reads --
+ * the device parameter block (time, step count, previous dt, AB2 and
+ * time-step mode), u, v, w, p and the previous advection term N^{n-1} in the
+ * state's precision, the per-block CFL speed maxima that set the next dt,
+ * and the flag's X, V, F in FP64 -- to the file `path`
+ * (created or truncated), after synchronising the state's stream. ibm_load
+ * reads such a file into a state created with the same grid, domain,
+ * Reynolds number, bodies and precision, so that stepping on gives the same
+ * result as never having stopped (up to the order of the atomic additions of
+ * the forcing). Errors: IBM_EIO if the file cannot be opened, written or
+ * read completely, is not a checkpoint, or has trailing bytes; IBM_EINVAL if
+ * it belongs to a different problem or precision. On any error ibm_load
+ * leaves the state unchanged. The format is this library's own (native
+ * byte order, not meant for exchange between machines). */
+int ibm_save(ibm_state* s, const char* path);
+int ibm_load(ibm_state* s, const char* path);
 
 /* Benchmarking aid: launch one stage of the step `nrep` >= 1 times back to
  * back on the state's stream, bracketed by CUDA events, and return the mean

@@ -1,6 +1,7 @@
 """Tile-shape autotuner for the solver's streamed kernels.
 
-The explicit stage (rhs_planes: x planes per block of the bulk-copy pipeline)
+The explicit stage (rhs_planes: x planes per block of the bulk-copy pipeline;
+rhs_stages: depth of its shared-memory ring)
 and the FP32 implicit x factor (afx_planes: x planes per block) have tile
 parameters that change performance but not results. For a problem shape and
 precision the tuner times each candidate with the library's stage timer on a
@@ -16,9 +17,10 @@ from . import binding
 
 CANDIDATES = {
     "rhs_planes": (8, 16, 32, 64),
+    "rhs_stages": (4, 5, 6, 8),
     "afx_planes": (32, 64, 128),
 }
-STAGE_OF = {"rhs_planes": "rhs", "afx_planes": "af_x"}
+STAGE_OF = {"rhs_planes": "rhs", "rhs_stages": "rhs", "afx_planes": "af_x"}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tile_cache.json")
 
 

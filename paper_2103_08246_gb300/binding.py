@@ -25,11 +25,13 @@ IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P = 0, 1, 2, 3
 # every symbol include/ibm.h declares
 SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_flag_state",
            "ibm_stats", "ibm_get_field", "ibm_set_field", "ibm_marker_count", "ibm_get_markers",
+           "ibm_save", "ibm_load",
            "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_destroy", "ibm_strerror")
 
 STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
-          "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11, "poisson": 12}
+          "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11, "poisson": 12,
+          "af_yz": 13}
 
 
 class ibm_grid(ctypes.Structure):
@@ -57,7 +59,8 @@ class ibm_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("cfl_limit", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("init_u", _dp), ("init_v", _dp), ("init_w", _dp),
-                ("rhs_planes", ctypes.c_int), ("afx_planes", ctypes.c_int)]
+                ("rhs_planes", ctypes.c_int), ("afx_planes", ctypes.c_int),
+                ("rhs_stages", ctypes.c_int)]
 
 
 class ibm_stats_t(ctypes.Structure):
@@ -106,6 +109,8 @@ def load(path: str = LIB_PATH):
     lib.ibm_set_field.argtypes = [vp, ctypes.c_int, _dp, sz]
     lib.ibm_marker_count.argtypes = [vp, ctypes.POINTER(sz)]
     lib.ibm_get_markers.argtypes = [vp, _dp, sz]
+    lib.ibm_save.argtypes = [vp, ctypes.c_char_p]
+    lib.ibm_load.argtypes = [vp, ctypes.c_char_p]
     lib.ibm_time_stage.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.ibm_ensemble_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.ibm_ensemble_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
@@ -208,6 +213,14 @@ def ibm_get_markers(state, out):
     _check(load().ibm_get_markers(state, _ptr(out), out.size // 3), "ibm_get_markers")
 
 
+def ibm_save(state, path):
+    _check(load().ibm_save(state, os.fsencode(path)), "ibm_save")
+
+
+def ibm_load(state, path):
+    _check(load().ibm_load(state, os.fsencode(path)), "ibm_load")
+
+
 def ibm_time_stage(state, stage, nrep) -> float:
     ms = ctypes.c_double(0.0)
     _check(load().ibm_time_stage(state, int(stage), int(nrep), ctypes.byref(ms)), "ibm_time_stage")
@@ -259,7 +272,8 @@ class Solver:
         opts = ibm_options(precision, wl.cfl if cfl is None else cfl, cfl_limit,
                            ctypes.c_void_p(self.stream.cuda_stream),
                            *([_ptr(a) for a in self._noise] if self._noise else [None] * 3),
-                           int(tiles.get("rhs_planes", 0)), int(tiles.get("afx_planes", 0)))
+                           int(tiles.get("rhs_planes", 0)), int(tiles.get("afx_planes", 0)),
+                           int(tiles.get("rhs_stages", 0)))
         self.ws_bytes = ibm_workspace_bytes(self.grid, self.dom, self.bodies, opts)
         self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device="cuda")
         torch.cuda.synchronize()
@@ -299,6 +313,12 @@ class Solver:
 
     def stats(self):
         return ibm_stats(self.state)
+
+    def save(self, path):
+        ibm_save(self.state, path)
+
+    def load(self, path):
+        ibm_load(self.state, path)
 
     def time_stage(self, stage, nrep=10):
         return ibm_time_stage(self.state, STAGES[stage] if isinstance(stage, str) else stage, nrep)

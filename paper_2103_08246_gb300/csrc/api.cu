@@ -287,6 +287,8 @@ struct ibm_state {
   float* hz = nullptr;
   cudaStream_t side = nullptr;            // structural update, overlapped in the graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t side2 = nullptr;           // implicit-factor tables, overlapped with the RHS
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
 };
 
 namespace {
@@ -316,7 +318,8 @@ int check_args(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, cons
   }
   if (o) {
     if (o->rhs_planes < 0 || o->rhs_planes > 256 || (o->rhs_planes > 0 && o->rhs_planes < 2) ||
-        o->afx_planes < 0 || o->afx_planes > 256 || (o->afx_planes > 0 && o->afx_planes < 8))
+        o->afx_planes < 0 || o->afx_planes > 256 || (o->afx_planes > 0 && o->afx_planes < 8) ||
+        o->rhs_stages < 0 || o->rhs_stages > 8 || (o->rhs_stages > 0 && o->rhs_stages < 4))
       return IBM_EINVAL;
     if (o->precision != IBM_FP64 && o->precision != IBM_FP32 && o->precision != IBM_MIXED)
       return IBM_EINVAL;
@@ -461,8 +464,14 @@ void record_step(ibm_state* s, int cur) {
     cudaEventRecord(s->ev_join, s->side);
   }
   launch_begin_step(c, f, st);
+  // the implicit factors' tables for this step's r, concurrent with the RHS
+  cudaEventRecord(s->ev_fork2, st);
+  cudaStreamWaitEvent(s->side2, s->ev_fork2, 0);
+  launch_af_tables(c, f, s->side2);
+  cudaEventRecord(s->ev_join2, s->side2);
   launch_rhs(c, f, cur, st);
   launch_outflow(c, f, cur, st);
+  cudaStreamWaitEvent(st, s->ev_join2, 0);
   launch_af(c, f, cur, st);
   if (flag) cudaStreamWaitEvent(st, s->ev_join, 0);
   launch_ib(c, f, s->mk, s->fl, cur, st);
@@ -559,6 +568,9 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
   CK(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&s->side2, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s->ev_fork2, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->ev_join2, cudaEventDisableTiming));
   // capture one step per buffer parity
   for (int par = 0; par < 2; ++par) {
     cudaGraph_t g;
@@ -605,6 +617,7 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   c.f_inv_h = (float)c.inv_h;
   c.f_inv_h2 = (float)(c.inv_h * c.inv_h);
   c.rhs_planes = (o && o->rhs_planes > 0) ? o->rhs_planes : 32;
+  c.rhs_stages = (o && o->rhs_stages > 0) ? o->rhs_stages : 8;
   c.afx_planes = (o && o->afx_planes > 0) ? o->afx_planes : 64;
   bar_dv = 0.0;
   if (b->flag_on) fg = build_flag(*b, *d, c.h);
@@ -671,6 +684,7 @@ void launch_stage(ibm_state* s, int stage) {
     case IBM_STAGE_POISSON_X: launch_poisson_x(c, f, st); break;
     case IBM_STAGE_PROJECT: launch_project_only(c, f, cur, false, st); break;
     case IBM_STAGE_POISSON: solve_poisson<T>(s, st); break;
+    case IBM_STAGE_AF_YZ: (void)launch_af_yz(c, f, cur, st); break;
     default: break;
   }
 }
@@ -822,7 +836,7 @@ int ibm_stats(ibm_state* s, ibm_stats_t* out) {
 }
 
 int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
-  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_POISSON) return IBM_EINVAL;
+  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_AF_YZ) return IBM_EINVAL;
   cudaStream_t st = s->stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -899,6 +913,126 @@ int ibm_get_markers(ibm_state* s, double* X, size_t n) {
   return IBM_OK;
 }
 
+// ------------------------------------------------------------------ checkpoints
+// File: a fixed header (magic, version, precision, grid, domain, viscosity,
+// body parameters, marker counts, element size), the device Params block,
+// then u, v, w (current buffer), p, N^{n-1} (three components) in the
+// state's precision, the CFL partial maxima, then the flag X, V, F in FP64. Everything the next
+// step reads is in the file; scratch (transform buffers, implicit-factor
+// ping-pong buffers) and tables rebuilt at creation are not.
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int version, precision, nx, ny, nz, nf, nb, elem;
+  double lx, ly, lz, nu;
+  double body[12];
+  long long params_bytes;
+};
+
+void fill_header(const ibm_state* s, CkptHeader& h) {
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "IBMCKPT1", 8);
+  h.version = 1;
+  h.precision = s->precision;
+  h.nx = s->c.nx;
+  h.ny = s->c.ny;
+  h.nz = s->c.nz;
+  h.nf = s->mk.nf;
+  h.nb = s->mk.nb;
+  h.elem = s->precision == IBM_FP64 ? 8 : 4;
+  h.lx = s->c.lx;
+  h.ly = s->c.ly;
+  h.lz = s->c.lz;
+  h.nu = s->c.nu;
+  const ibm_bodies& b = s->bodies;
+  const double body[12] = {(double)b.bars_on, b.bar_x,   b.bar_mesh,  b.bar_width,
+                           (double)b.flag_on, b.flag_x_le, b.flag_len, b.flag_span,
+                           b.mass_ratio,      b.bending, b.pitch0,    b.stretch};
+  std::memcpy(h.body, body, sizeof(body));
+  h.params_bytes = (long long)sizeof(Params);
+}
+
+// device regions of a checkpoint, in file order: pointer and bytes
+std::vector<std::pair<void*, size_t>> ckpt_regions(ibm_state* s) {
+  const Consts& c = s->c;
+  const size_t NF = (size_t)(c.nx + 1) * c.ny * c.nz, NP = (size_t)c.nx * c.ny * c.nz;
+  std::vector<std::pair<void*, size_t>> r;
+  r.push_back({s->prm, sizeof(Params)});
+  auto add = [&](auto& f) {
+    const size_t e = sizeof(*f.p);
+    r.push_back({f.u[s->cur], NF * e});
+    r.push_back({f.v[s->cur], NF * e});
+    r.push_back({f.w[s->cur], NF * e});
+    r.push_back({f.p, NP * e});
+    for (int q = 0; q < 3; ++q) r.push_back({f.n[q], NF * e});
+    // per-block maxima of the CFL speed from the last projection: the next
+    // step's dt in CFL mode
+    r.push_back({f.partial, (size_t)f.n_partial * sizeof(double)});
+  };
+  if (s->precision == IBM_FP64) add(s->fd);
+  else add(s->ff);
+  if (s->fl.nv) {
+    const size_t b = 3 * (size_t)s->fl.nv * sizeof(double);
+    r.push_back({s->fl.X, b});
+    r.push_back({s->fl.V, b});
+    r.push_back({s->fl.Ff, b});
+  }
+  return r;
+}
+
+struct FileCloser {
+  void operator()(FILE* f) const {
+    if (f) std::fclose(f);
+  }
+};
+}  // namespace
+
+int ibm_save(ibm_state* s, const char* path) {
+  if (!s || !path) return IBM_EINVAL;
+  CK(cudaStreamSynchronize(s->stream));
+  CkptHeader h;
+  fill_header(s, h);
+  std::unique_ptr<FILE, FileCloser> f(std::fopen(path, "wb"));
+  if (!f) return IBM_EIO;
+  if (std::fwrite(&h, sizeof(h), 1, f.get()) != 1) return IBM_EIO;
+  std::vector<char> buf;
+  for (auto& reg : ckpt_regions(s)) {
+    buf.resize(reg.second);
+    CK(cudaMemcpyAsync(buf.data(), reg.first, reg.second, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (std::fwrite(buf.data(), 1, reg.second, f.get()) != reg.second) return IBM_EIO;
+  }
+  if (std::fflush(f.get()) != 0) return IBM_EIO;
+  return IBM_OK;
+}
+
+int ibm_load(ibm_state* s, const char* path) {
+  if (!s || !path) return IBM_EINVAL;
+  std::unique_ptr<FILE, FileCloser> f(std::fopen(path, "rb"));
+  if (!f) return IBM_EIO;
+  CkptHeader h, mine;
+  if (std::fread(&h, sizeof(h), 1, f.get()) != 1) return IBM_EIO;
+  fill_header(s, mine);
+  if (std::memcmp(h.magic, mine.magic, 8) != 0 || h.version != mine.version) return IBM_EIO;
+  // a checkpoint of a different problem: refuse before touching the state
+  if (std::memcmp(&h, &mine, sizeof(h)) != 0) return IBM_EINVAL;
+  const auto regs = ckpt_regions(s);
+  std::vector<std::vector<char>> bufs(regs.size());
+  for (size_t q = 0; q < regs.size(); ++q) {
+    bufs[q].resize(regs[q].second);
+    if (std::fread(bufs[q].data(), 1, regs[q].second, f.get()) != regs[q].second) return IBM_EIO;
+  }
+  char extra;
+  if (std::fread(&extra, 1, 1, f.get()) != 0) return IBM_EIO;   // trailing bytes
+  CK(cudaStreamSynchronize(s->stream));
+  for (size_t q = 0; q < regs.size(); ++q)
+    CK(cudaMemcpyAsync(regs[q].first, bufs[q].data(), regs[q].second, cudaMemcpyHostToDevice,
+                       s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->last_dt_fixed = -2.0;   // the time-step mode travels in Params; re-send on the next step
+  return IBM_OK;
+}
+
 void ibm_destroy(ibm_state* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
@@ -912,6 +1046,9 @@ void ibm_destroy(ibm_state* s) {
   if (s->side) cudaStreamDestroy(s->side);
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->side2) cudaStreamDestroy(s->side2);
+  if (s->ev_fork2) cudaEventDestroy(s->ev_fork2);
+  if (s->ev_join2) cudaEventDestroy(s->ev_join2);
   cudaGetLastError();
   delete s;
 }

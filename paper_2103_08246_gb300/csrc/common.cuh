@@ -47,6 +47,7 @@ struct Consts {
   double u_in;        // inflow speed U
   double omega_max;   // structural stiffness bound (sub-step count)
   int rhs_planes;     // tile: x planes per block of the streamed RHS
+  int rhs_stages;     // tile: most x planes in the streamed RHS's ring
   int afx_planes;     // tile: x planes per block of the FP32 x factor
   float f_inv_h, f_inv_h2, f_nu;   // FP32 copies
 };

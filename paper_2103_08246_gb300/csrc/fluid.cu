@@ -6,7 +6,9 @@
 //
 // Layout: x slowest, z fastest; u, v, w have nx + 1 planes (u: faces
 // 0..nx; v, w: cells 0..nx-1 plus the outflow ghost plane nx), p and phi nx.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "async_copy.cuh"
 #include "solver.h"
@@ -27,21 +29,23 @@ constexpr int HMAX = 24;     // largest warm-up the segments carry
 
 __device__ inline double af_theta(double r) { return 2.0 * asinh(0.5 / sqrt(r)); }
 
-// dt (fixed or CFL), AB2 weights, implicit diffusion number, sub-steps, and the
-// LU inverse pivots of the x factors (closed form, one entry per thread):
-//   Dirichlet start (u):      1/p_k = rho (1 - rho^{2k})   / (1 - rho^{2k+2})
-//   reflection start (v, w):  1/p_k = rho (1 - rho^{2k-1}) / (1 - rho^{2k+1})
-// Each kernel writes only the fields it owns: the structural update runs
-// concurrently and owns flag_pending.
+// dt (fixed or CFL), AB2 weights, implicit diffusion number and sub-steps.
+// The per-block speed maxima are non-negative doubles (or +inf), whose bit
+// patterns order like the values, so the maximum is taken on the integer
+// pipe. Each kernel writes only the fields it owns: the structural update
+// runs concurrently and owns flag_pending.
 __global__ void k_begin_step(Consts c, Params* prm, const double* __restrict__ partial,
-                             int n_partial, double* __restrict__ ipt, float* __restrict__ iptf,
-                             double* __restrict__ taps, float* __restrict__ tapsf, double tol) {
-  __shared__ double scratch[32];
-  __shared__ double sh_r;
-  double m = 0.0;
-  for (int b = threadIdx.x; b < n_partial; b += blockDim.x) m = fmax(m, partial[b]);
-  m = block_max(m, scratch);
+                             int n_partial, double tol) {
+  __shared__ unsigned long long wmax[32];
+  unsigned long long mb = 0ull;
+  for (int b = threadIdx.x; b < n_partial; b += blockDim.x)
+    mb = max(mb, (unsigned long long)__double_as_longlong(partial[b]));
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mb;
+  __syncthreads();
   if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mb = max(mb, wmax[q]);
+    const double m = __longlong_as_double((long long)mb);
     const double dt_fixed = prm->dt_fixed;
     int err = 0;
     double dt = dt_fixed > 0.0 ? dt_fixed : prm->cfl * c.h / m;
@@ -90,39 +94,55 @@ __global__ void k_begin_step(Consts c, Params* prm, const double* __restrict__ p
     prm->f_cc = (float)(c.u_in * dt * c.inv_h);
     prm->f_sc_div = (float)(c.inv_h / dt);
     if (err) prm->error |= err;
-    sh_r = r;
   }
-  __syncthreads();
-  const double th = af_theta(sh_r);
+}
+
+// Tables of the implicit factors for this step's r, one entry per thread
+// (FP64 transcendental functions: spread over many blocks, and off the
+// critical path, concurrent with the explicit stage):
+//   LU inverse pivots of the x factors (closed form)
+//     Dirichlet start (u):      1/p_k = rho (1 - rho^{2k})   / (1 - rho^{2k+2})
+//     reflection start (v, w):  1/p_k = rho (1 - rho^{2k-1}) / (1 - rho^{2k+1})
+//   free-space taps of the reflected x solve: (1/r) rho^{m+1} / (1 - rho^2)
+//   taps of the exact periodic inverse of r (q - S - S^{-1}) on n points:
+//     t_m = (1/r) rho / (1 - rho^2) (rho^m + rho^{n-m}) / (1 - rho^n)
+constexpr int TAB_THREADS = 64;
+int table_entries(const Consts& c) { return c.nx + (HMAX + 1) + c.ny + c.nz; }
+
+__global__ void __launch_bounds__(TAB_THREADS)
+k_af_tables(Consts c, const Params* __restrict__ prm, double* __restrict__ ipt,
+            float* __restrict__ iptf, double* __restrict__ taps, float* __restrict__ tapsf) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const double r = prm->r;
+  const double th = af_theta(r);
   const double rho = exp(-th);
-  for (int k = 1 + threadIdx.x; k <= c.nx; k += blockDim.x) {
+  if (q < c.nx) {
+    const int k = q + 1;
     const double a = rho * expm1(-2.0 * k * th) / expm1(-(2.0 * k + 2.0) * th);
     const double b = rho * expm1(-(2.0 * k - 1.0) * th) / expm1(-(2.0 * k + 1.0) * th);
     ipt[k] = a;
     ipt[c.nx + 2 + k] = b;
     iptf[k] = (float)a;
     iptf[c.nx + 2 + k] = (float)b;
+    return;
   }
-  // free-space taps for the reflected x solve: (1/r) rho^{m+1} / (1 - rho^2)
-  for (int m = threadIdx.x; m <= HMAX; m += blockDim.x) {
-    const double v = (1.0 / sh_r) * exp(-(double)(m + 1) * th) / (-expm1(-2.0 * th));
-    taps[c.ny + c.nz + m] = v;
-    tapsf[c.ny + c.nz + m] = (float)v;
+  q -= c.nx;
+  if (q <= HMAX) {
+    const double v = (1.0 / r) * exp(-(double)(q + 1) * th) / (-expm1(-2.0 * th));
+    taps[c.ny + c.nz + q] = v;
+    tapsf[c.ny + c.nz + q] = (float)v;
+    return;
   }
-  // taps of the exact periodic inverse of r (q - S - S^{-1}) on n points:
-  //   t_m = (1/r) rho / (1 - rho^2) (rho^m + rho^{n-m}) / (1 - rho^n),  m = 0..n-1
-  const double pre = (1.0 / sh_r) * rho / (-expm1(-2.0 * th));
-  for (int dir = 0; dir < 2; ++dir) {
-    const int n = dir == 0 ? c.ny : c.nz;
-    const double den = -expm1(-(double)n * th);
-    double* t = taps + (dir == 0 ? 0 : c.ny);
-    float* tf = tapsf + (dir == 0 ? 0 : c.ny);
-    for (int m = threadIdx.x; m < n; m += blockDim.x) {
-      const double v = pre * (exp(-(double)m * th) + exp(-(double)(n - m) * th)) / den;
-      t[m] = v;
-      tf[m] = (float)v;
-    }
-  }
+  q -= HMAX + 1;
+  const int dir = q < c.ny ? 0 : 1;
+  const int n = dir == 0 ? c.ny : c.nz;
+  const int m = dir == 0 ? q : q - c.ny;
+  if (m >= n) return;
+  const double pre = (1.0 / r) * rho / (-expm1(-2.0 * th));
+  const double den = -expm1(-(double)n * th);
+  const double v = pre * (exp(-(double)m * th) + exp(-(double)(n - m) * th)) / den;
+  taps[q] = v;    // y taps at [0, ny), z taps at [ny, ny + nz)
+  tapsf[q] = (float)v;
 }
 
 // after the projection: advance the clock
@@ -235,7 +255,7 @@ k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
 // one mbarrier per slot; the block computes plane i from planes i-1, i, i+1
 // while the copies of the next planes are in flight. Whole rows make the
 // periodic z wrap an index mask and every copy 16-byte aligned.
-constexpr int RSTAGES = 4;
+constexpr int RSTAGES_MAX = 8;   // ring slots: as many stages as 210 KB holds, 4..8
 template <class T, int TJR>
 struct RhsRing {
   // rows of one stage: u, v, w with halo, p with low-side halo, N^{n-1} x 3
@@ -248,9 +268,9 @@ __global__ void __launch_bounds__(RTHREADS, 1)
 k_rhs_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ u,
            const T* __restrict__ v, const T* __restrict__ w, const T* __restrict__ p,
            T* __restrict__ n0, T* __restrict__ n1, T* __restrict__ n2, T* __restrict__ d0,
-           T* __restrict__ d1, T* __restrict__ d2, int XR) {
+           T* __restrict__ d1, T* __restrict__ d2, int XR, int RSTAGES) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t full[RSTAGES];
+  __shared__ uint64_t full[RSTAGES_MAX];
   const int nx = c.nx, ny = c.ny, nz = c.nz;
   const int tid = threadIdx.x;
   const int j0 = blockIdx.x * TJR;
@@ -321,7 +341,8 @@ k_rhs_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ u,
       if (tid == 0) {
         atomicOr(&prm->error, ERR_TIMEOUT);
         // let the copies already issued land before the block leaves
-        for (int t = tc; t < nstage && t < tc + RSTAGES; ++t) (void)wait_stage(t);
+        // (issued so far: stages up to ta - 1 + RSTAGES)
+        for (int t = tc; t < nstage && t < ta + RSTAGES; ++t) (void)wait_stage(t);
       }
       return;
     }
@@ -621,6 +642,208 @@ k_af_y(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
                       pick<T>(1.0 / prm->r, prm->f_ir),
                       [&](int j) { return in[(size_t)j * st]; },
                       [&](int j, T v) { out[(size_t)j * st] = v; });
+}
+
+// Fused periodic factors of one (component, x plane, block of J y rows):
+// (1 - aL_y) then (1 - aL_z), then u* = u^n + du. With q = 2 + 1/r and
+// rho + 1/rho = q, r (q - S - S^{-1}) = (r / rho)(1 - rho S)(1 - rho S^{-1}),
+// so each periodic factor is a forward recursion y_k = b_k / r + rho y_{k-1},
+// a backward recursion z_k = y_k + rho z_{k+1}, and du = rho z.
+//  y: one thread per z column walks its J rows. The periodic past enters
+//     through a warm-up of H rows before the block (rho^H below the
+//     tolerance); the periodic future through its closed form
+//     z_{j0+J} = (rho y_{j0+J-1} + sum_{q<H} rho^q b_{j0+J+q}) / (1 - rho^2).
+//     Results go to shared memory, rows padded by one word per 32.
+//  z: one warp per row, E = nz / 32 consecutive points per lane. Each
+//     recursion is a local pass, a Kogge-Stone scan of the lane carries
+//     (factor rho^E per lane), and the exact periodic closure: the
+//     non-periodic end value divided by (1 - rho^nz) re-enters every point
+//     with weight rho^distance.
+// Replaces the separate y and z kernels: reads the x factor's output and u^n
+// once, writes u* once.
+constexpr int YZ_THREADS = 256;
+template <class T>
+struct YZRows {
+  static constexpr int J = sizeof(T) == 4 ? 32 : 16;
+};
+
+// E consecutive values, as 16-byte accesses when E values fill whole vectors
+// (the caller's address is then 16-byte aligned)
+template <class T, int E>
+__device__ inline void load_run(const T* p, T (&v)[E]) {
+  if constexpr (sizeof(T) == 4 && E % 4 == 0) {
+#pragma unroll
+    for (int t = 0; t < E; t += 4) {
+      const float4 q = *reinterpret_cast<const float4*>(p + t);
+      v[t] = q.x;
+      v[t + 1] = q.y;
+      v[t + 2] = q.z;
+      v[t + 3] = q.w;
+    }
+  } else if constexpr (sizeof(T) == 8 && E % 2 == 0) {
+#pragma unroll
+    for (int t = 0; t < E; t += 2) {
+      const double2 q = *reinterpret_cast<const double2*>(p + t);
+      v[t] = q.x;
+      v[t + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < E; ++t) v[t] = p[t];
+  }
+}
+template <class T, int E>
+__device__ inline void store_run(T* p, const T (&v)[E]) {
+  if constexpr (sizeof(T) == 4 && E % 4 == 0) {
+#pragma unroll
+    for (int t = 0; t < E; t += 4)
+      *reinterpret_cast<float4*>(p + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+  } else if constexpr (sizeof(T) == 8 && E % 2 == 0) {
+#pragma unroll
+    for (int t = 0; t < E; t += 2) *reinterpret_cast<double2*>(p + t) = make_double2(v[t], v[t + 1]);
+  } else {
+#pragma unroll
+    for (int t = 0; t < E; ++t) p[t] = v[t];
+  }
+}
+
+template <class T, int E>
+__global__ void __launch_bounds__(YZ_THREADS)
+k_af_yz(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
+        const T* __restrict__ e1, const T* __restrict__ e2, T* __restrict__ u,
+        T* __restrict__ v, T* __restrict__ w) {
+  constexpr int NZ = 32 * E;
+  constexpr int LDP = NZ + NZ / 32;
+  constexpr int J = YZRows<T>::J;
+  __shared__ T sdu[J * LDP];
+  const int ny = c.ny, ymask = c.ny - 1;   // ny is a power of two
+  const int j0 = blockIdx.x * J, i = blockIdx.y, comp = blockIdx.z;
+  if (comp == 0 && i < 1) return;   // u: interior faces 1 .. nx-1 only
+  const size_t pb = (size_t)i * ny * NZ;
+  const T* in = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + pb;
+  T* q = (comp == 0 ? u : comp == 1 ? v : w) + pb;
+  const T rho = pick<T>(prm->af_rho, prm->f_rho);
+  const T ir = pick<T>(1.0 / prm->r, prm->f_ir);
+  const int H = prm->af_h;
+  const T inv_1mr2 = (T)1 / ((T)1 - rho * rho);
+  // ---- y factor
+  for (int k = threadIdx.x; k < NZ; k += YZ_THREADS) {
+    const T* col = in + k;
+    T y = 0;
+    int jw = (j0 - H) & ymask;
+    for (int m0 = 0; m0 < H; m0 += 8) {
+      T buf[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) buf[t] = (m0 + t < H) ? col[(size_t)((jw + t) & ymask) * NZ] : (T)0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (m0 + t < H) y = buf[t] * ir + rho * y;
+      jw = (jw + 8) & ymask;
+    }
+    T yr[J];
+#pragma unroll
+    for (int m = 0; m < J; ++m) yr[m] = col[(size_t)(j0 + m) * NZ];
+#pragma unroll
+    for (int m = 0; m < J; ++m) {
+      y = yr[m] * ir + rho * y;
+      yr[m] = y;
+    }
+    T sf = 0, pw = 1;
+    jw = (j0 + J) & ymask;
+    for (int m0 = 0; m0 < H; m0 += 8) {
+      T buf[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) buf[t] = (m0 + t < H) ? col[(size_t)((jw + t) & ymask) * NZ] : (T)0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+        if (m0 + t < H) {
+          sf += pw * (buf[t] * ir);
+          pw *= rho;
+        }
+      jw = (jw + 8) & ymask;
+    }
+    T z = (rho * y + sf) * inv_1mr2;
+    const int kp = k + (k >> 5);
+#pragma unroll
+    for (int m = J - 1; m >= 0; --m) {
+      z = yr[m] + rho * z;
+      sdu[m * LDP + kp] = rho * z;
+    }
+  }
+  __syncthreads();
+  // ---- z factor, then u* = u^n + du
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T rp[E];                                   // rho^(q+1)
+  rp[0] = rho;
+#pragma unroll
+  for (int t = 1; t < E; ++t) rp[t] = rp[t - 1] * rho;
+  const T pE = rp[E - 1];                    // rho^E
+  T pl = 1, pr = 1;                          // rho^(E lane), rho^(E (31 - lane))
+  {
+    T b = pE;
+#pragma unroll
+    for (int bit = 0; bit < 5; ++bit) {
+      if ((lane >> bit) & 1) pl *= b;
+      if (((31 - lane) >> bit) & 1) pr *= b;
+      b *= b;
+    }
+  }
+  const T rn = pl * pr * pE;                 // rho^nz
+  const T inv_1mrn = (T)1 / ((T)1 - rn);
+  for (int r = warp; r < J; r += YZ_THREADS / 32) {
+    T* qrow = q + (size_t)(j0 + r) * NZ + lane * E;
+    T un[E];
+    load_run<T, E>(qrow, un);
+    T x[E];
+    const T* srow = sdu + r * LDP;
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+      const int k = lane * E + t;
+      x[t] = srow[k + (k >> 5)];
+    }
+    // forward: y_k = x_k / r + rho y_{k-1}
+    T acc = 0;
+#pragma unroll
+    for (int t = 0; t < E; ++t) {
+      acc = x[t] * ir + rho * acc;
+      x[t] = acc;
+    }
+    T Y = acc, pe = pE;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+      const T o = __shfl_up_sync(0xffffffffu, Y, s);
+      if (lane >= s) Y += pe * o;
+      pe *= pe;
+    }
+    const T P = __shfl_sync(0xffffffffu, Y, 31) * inv_1mrn;
+    T C = __shfl_up_sync(0xffffffffu, Y, 1);
+    if (lane == 0) C = 0;
+    C += pl * P;
+#pragma unroll
+    for (int t = 0; t < E; ++t) x[t] += rp[t] * C;
+    // backward: z_k = y_k + rho z_{k+1}
+    acc = 0;
+#pragma unroll
+    for (int t = E - 1; t >= 0; --t) {
+      acc = x[t] + rho * acc;
+      x[t] = acc;
+    }
+    T Z = acc;
+    pe = pE;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+      const T o = __shfl_down_sync(0xffffffffu, Z, s);
+      if (lane + s < 32) Z += pe * o;
+      pe *= pe;
+    }
+    const T Pz = __shfl_sync(0xffffffffu, Z, 0) * inv_1mrn;
+    T C2 = __shfl_down_sync(0xffffffffu, Z, 1);
+    if (lane == 31) C2 = 0;
+    C2 += pr * Pz;
+#pragma unroll
+    for (int t = 0; t < E; ++t) un[t] += rho * (x[t] + rp[E - 1 - t] * C2);
+    store_run<T, E>(qrow, un);
+  }
 }
 
 // z lines are contiguous: a block stages whole lines in shared memory, threads
@@ -1032,24 +1255,31 @@ static dim3 grid3(const Consts& c, int planes) {
 template <class T>
 void launch_begin_step(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   const double tol = sizeof(T) == 8 ? 1e-17 : 1e-9;
-  k_begin_step<<<1, 1024, 0, s>>>(c, f.prm, f.partial, f.n_partial, f.ipt, f.iptf, f.taps,
-                                  f.tapsf, tol);
+  k_begin_step<<<1, 1024, 0, s>>>(c, f.prm, f.partial, f.n_partial, tol);
 }
 
 template <class T>
-static size_t rhs_pipe_smem(const Consts& c, int tjr) {
-  return (size_t)RSTAGES * (3 * (tjr + 2) + (tjr + 1) + 3 * tjr) * c.nz * sizeof(T);
+void launch_af_tables(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+  const int n = table_entries(c);
+  k_af_tables<<<(n + TAB_THREADS - 1) / TAB_THREADS, TAB_THREADS, 0, s>>>(c, f.prm, f.ipt, f.iptf,
+                                                                          f.taps, f.tapsf);
+}
+
+template <class T>
+static size_t rhs_stage_bytes(const Consts& c, int tjr) {
+  return (size_t)(3 * (tjr + 2) + (tjr + 1) + 3 * tjr) * c.nz * sizeof(T);
 }
 
 template <class T>
 void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   constexpr int TJR = sizeof(T) == 4 ? 4 : 2;
-  const size_t sh = rhs_pipe_smem<T>(c, TJR);
-  if (sh <= 210 * 1024 && c.ny % TJR == 0 && (c.nz * sizeof(T)) % 16 == 0) {
+  const size_t stage = rhs_stage_bytes<T>(c, TJR);
+  const int rs = (int)std::min<size_t>(std::min(RSTAGES_MAX, c.rhs_stages), (size_t)(210 * 1024) / stage);
+  if (rs >= 4 && c.ny % TJR == 0 && (c.nz * sizeof(T)) % 16 == 0) {
     const int XR = c.rhs_planes;
-    k_rhs_pipe<T, TJR><<<dim3(c.ny / TJR, (c.nx + XR - 1) / XR), RTHREADS, sh, s>>>(
+    k_rhs_pipe<T, TJR><<<dim3(c.ny / TJR, (c.nx + XR - 1) / XR), RTHREADS, rs * stage, s>>>(
         c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.p, f.n[0], f.n[1], f.n[2], f.d[0], f.d[1],
-        f.d[2], XR);
+        f.d[2], XR, rs);
     return;
   }
   k_rhs<T><<<grid3(c, c.nx + 1), dim3(TK, TJ), 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
@@ -1128,9 +1358,32 @@ void launch_af_z(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
       c, f.prm, f.d[0], f.d[1], f.d[2], f.u[cur], f.v[cur], f.w[cur]);
 }
 
+// fused y-z factors for nz = 32 E with E in {1, 2, 4, 8} and ny a multiple of
+// the row block; false when the shape needs the separate kernels
+template <class T>
+bool launch_af_yz(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
+  constexpr int J = YZRows<T>::J;
+  if (c.ny % J != 0) return false;
+  const dim3 grid(c.ny / J, c.nx, 3);
+#define YZ_CASE(EE)                                                                               \
+  case 32 * EE:                                                                                   \
+    k_af_yz<T, EE><<<grid, YZ_THREADS, 0, s>>>(c, f.prm, f.e[0], f.e[1], f.e[2], f.u[cur],       \
+                                              f.v[cur], f.w[cur]);                               \
+    return true;
+  switch (c.nz) {
+    YZ_CASE(1)
+    YZ_CASE(2)
+    YZ_CASE(4)
+    YZ_CASE(8)
+    default: return false;
+  }
+#undef YZ_CASE
+}
+
 template <class T>
 void launch_af(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   launch_af_x(c, f, cur, s);
+  if (launch_af_yz(c, f, cur, s)) return;
   launch_af_y(c, f, cur, s);
   launch_af_z(c, f, cur, s);
 }
@@ -1189,11 +1442,13 @@ int partial_count(const Consts& c) {
 #define INST(T)                                                                                \
   template void launch_begin_step<T>(const Consts&, const Fields<T>&, cudaStream_t);           \
   template void launch_rhs<T>(const Consts&, const Fields<T>&, int, cudaStream_t);             \
+  template void launch_af_tables<T>(const Consts&, const Fields<T>&, cudaStream_t);             \
   template void launch_outflow<T>(const Consts&, const Fields<T>&, int, cudaStream_t);         \
   template void launch_af<T>(const Consts&, const Fields<T>&, int, cudaStream_t);              \
   template void launch_af_x<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
   template void launch_af_y<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
   template void launch_af_z<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
+  template bool launch_af_yz<T>(const Consts&, const Fields<T>&, int, cudaStream_t);           \
   template void launch_mass<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
   template void launch_div<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t);       \
   template void launch_project_only<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t); \
