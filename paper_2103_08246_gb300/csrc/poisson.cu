@@ -17,7 +17,10 @@
 // phi_nx = phi_{nx-1}):
 //   phi_{i-1} + (-2 + lambda h^2) phi_i + phi_{i+1} = h^2 D_i,
 // lambda h^2 = -4 sin^2(pi k_y / N_y) - 4 sin^2(pi k_z / N_z). The LU inverse
-// pivots of every mode are tabulated once (FP64 arithmetic) at creation.
+// pivots are tabulated once (FP64 arithmetic) at creation. lambda depends on
+// k_y and k_z only through min(k, N - k), so the table holds the
+// (N_y/2 + 1) x (N_z/2 + 1) distinct modes of every plane: a quarter of a
+// field, which mostly stays in L2 between the two sweeps.
 // Mode (0, 0) is singular: phi_0 = 0 is pinned, then the line mean removed,
 // which sets mean(phi) = 0.
 #include <cmath>
@@ -217,16 +220,33 @@ __global__ void __launch_bounds__(256) k_dht_z256(T* __restrict__ data, int nrow
   for (int m = 0; m < 8; ++m) x[m] = {a[l + 32 * m], b[l + 32 * m]};
   T ha[8], hb[8];
   warp_hartley256(x, tw, ha, hb);
+  // lane l holds outputs 8 q .. 8 q + 7: two (FP32) or four (FP64) 16-byte stores
   const int q = (int)(__brev((unsigned)l) >> 27);
+  if constexpr (sizeof(T) == 4) {
+    float4* pa = reinterpret_cast<float4*>(a + 8 * q);
+    float4* pb = reinterpret_cast<float4*>(b + 8 * q);
+    pa[0] = make_float4(ha[0], ha[1], ha[2], ha[3]);
+    pa[1] = make_float4(ha[4], ha[5], ha[6], ha[7]);
+    pb[0] = make_float4(hb[0], hb[1], hb[2], hb[3]);
+    pb[1] = make_float4(hb[4], hb[5], hb[6], hb[7]);
+  } else {
+    double2* pa = reinterpret_cast<double2*>(a + 8 * q);
+    double2* pb = reinterpret_cast<double2*>(b + 8 * q);
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    a[p + 8 * q] = ha[p];
-    b[p + 8 * q] = hb[p];
+    for (int t = 0; t < 4; ++t) {
+      pa[t] = make_double2(ha[2 * t], ha[2 * t + 1]);
+      pb[t] = make_double2(hb[2 * t], hb[2 * t + 1]);
+    }
   }
 }
 
 // y lines (columns of a plane, ny = 256): a block stages a 256 x 32 tile
-// (coalesced rows), 16 warps transform two columns each, the tile is stored back
+// (coalesced rows), 16 warps transform two columns each, the tile is stored back.
+// Tile element (r, c) sits at r * 33 + ((c + (r >> 5)) & 31): the row pad
+// spreads the column reads over the banks, and the rotation by r / 32 does
+// the same for the transform's output rows 8 q + p (q = 0..31 across lanes).
+__device__ inline int ytile(int r, int c) { return r * 33 + ((c + (r >> 5)) & 31); }
+
 template <class T>
 __global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, const T* __restrict__ twg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -237,26 +257,26 @@ __global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, 
   T* base = data + (size_t)plane * 256 * nz + c0;
   for (int e = threadIdx.x; e < 256 * 32; e += blockDim.x) {
     const int r = e >> 5, c = e & 31;
-    s[r * 33 + c] = base[(size_t)r * nz + c];
+    s[ytile(r, c)] = base[(size_t)r * nz + c];
   }
   load_twiddles(tw, twg);   // includes __syncthreads
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   Cx<T> x[8];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) x[m] = {s[(l + 32 * m) * 33 + 2 * w], s[(l + 32 * m) * 33 + 2 * w + 1]};
+  for (int m = 0; m < 8; ++m) x[m] = {s[ytile(l + 32 * m, 2 * w)], s[ytile(l + 32 * m, 2 * w + 1)]};
   T ha[8], hb[8];
   warp_hartley256(x, tw, ha, hb);
   __syncthreads();
   const int q = (int)(__brev((unsigned)l) >> 27);
 #pragma unroll
   for (int p = 0; p < 8; ++p) {
-    s[(p + 8 * q) * 33 + 2 * w] = ha[p];
-    s[(p + 8 * q) * 33 + 2 * w + 1] = hb[p];
+    s[ytile(p + 8 * q, 2 * w)] = ha[p];
+    s[ytile(p + 8 * q, 2 * w + 1)] = hb[p];
   }
   __syncthreads();
   for (int e = threadIdx.x; e < 256 * 32; e += blockDim.x) {
     const int r = e >> 5, c = e & 31;
-    base[(size_t)r * nz + c] = s[r * 33 + c];
+    base[(size_t)r * nz + c] = s[ytile(r, c)];
   }
 }
 
@@ -264,7 +284,16 @@ __global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, 
 // normalisation). One thread per mode walks x (coalesced across modes); the
 // loads of the next PF planes are issued ahead of the recursion so that each
 // thread keeps 2 PF independent loads in flight.
-constexpr int PF = 8;
+constexpr int PF = 16;
+__host__ __device__ inline size_t ptab_plane(const Consts& c) {
+  return (size_t)(c.ny / 2 + 1) * (c.nz / 2 + 1);
+}
+__device__ inline size_t ptab_index(const Consts& c, int jk) {
+  const int ky = jk / c.nz, kz = jk - ky * c.nz;
+  const int qy = ky <= c.ny / 2 ? ky : c.ny - ky, qz = kz <= c.nz / 2 ? kz : c.nz - kz;
+  return (size_t)qy * (c.nz / 2 + 1) + qz;
+}
+
 template <class T>
 __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict__ tab, T* __restrict__ phi, T scale) {
   const int P = c.ny * c.nz;
@@ -272,7 +301,8 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
   if (jk >= P) return;
   const int nx = c.nx;
   T* d = phi + jk;
-  const T* iv = tab + jk;
+  const T* iv = tab + ptab_index(c, jk);
+  const size_t PT = ptab_plane(c);
   const bool zero_mode = (jk == 0);
   T y = 0;
   int i = 0;
@@ -281,7 +311,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
 #pragma unroll
     for (int q = 0; q < PF; ++q) {
       rd[q] = d[(size_t)(i + q) * P];
-      rt[q] = iv[(size_t)(i + q) * P];
+      rt[q] = iv[(size_t)(i + q) * PT];
     }
 #pragma unroll
     for (int q = 0; q < PF; ++q) {
@@ -293,7 +323,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
   for (; i < nx; ++i) {
     const size_t o = (size_t)i * P;
     const T rhs = (zero_mode && i == 0) ? (T)0 : d[o] * scale;
-    y = (rhs - y) * iv[o];
+    y = (rhs - y) * iv[(size_t)i * PT];
     d[o] = y;
   }
   T x = y;  // x_{nx-1} = dp_{nx-1}
@@ -303,7 +333,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
 #pragma unroll
     for (int q = 0; q < PF; ++q) {
       rd[q] = d[(size_t)(i - q) * P];
-      rt[q] = iv[(size_t)(i - q) * P];
+      rt[q] = iv[(size_t)(i - q) * PT];
     }
 #pragma unroll
     for (int q = 0; q < PF; ++q) {
@@ -314,7 +344,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
   }
   for (; i >= 0; --i) {
     const size_t o = (size_t)i * P;
-    const T cp = (zero_mode && i == 0) ? (T)0 : iv[o];
+    const T cp = (zero_mode && i == 0) ? (T)0 : iv[(size_t)i * PT];
     x = d[o] - cp * x;
     d[o] = x;
   }
@@ -326,25 +356,27 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
   }
 }
 
-// inverse pivots 1 / (diag_i - c'_{i-1}) of every mode, FP64 arithmetic
+// inverse pivots 1 / (diag_i - c'_{i-1}) of every distinct mode, FP64 arithmetic
 template <class T>
 __global__ void k_poisson_table(Consts c, T* __restrict__ tab) {
-  const int P = c.ny * c.nz;
-  const int jk = blockIdx.x * blockDim.x + threadIdx.x;
-  if (jk >= P) return;
-  const int ky = jk / c.nz, kz = jk - ky * c.nz;
+  const int qz_n = c.nz / 2 + 1;
+  const int PT = (c.ny / 2 + 1) * qz_n;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= PT) return;
+  const int ky = m / qz_n, kz = m - ky * qz_n;
   const double sy = sin(M_PI * ky / c.ny), sz = sin(M_PI * kz / c.nz);
   const double lam = -4.0 * sy * sy - 4.0 * sz * sz;
+  const bool pinned = (m == 0);
   const int nx = c.nx;
   double cp = 0.0;
   for (int i = 0; i < nx; ++i) {
     double diag = (i == 0 || i == nx - 1) ? -1.0 + lam : -2.0 + lam;
     double lower = i == 0 ? 0.0 : 1.0;
-    if (jk == 0 && i == 0) diag = 1.0;              // pinned phi_0 = 0
-    const double prev_cp = (jk == 0 && i == 1) ? 0.0 : cp;
+    if (pinned && i == 0) diag = 1.0;              // pinned phi_0 = 0
+    const double prev_cp = (pinned && i == 1) ? 0.0 : cp;
     const double denom = diag - lower * prev_cp;
     const double inv = 1.0 / denom;
-    tab[(size_t)i * P + jk] = (T)inv;
+    tab[(size_t)i * PT + m] = (T)inv;
     cp = inv;  // upper = 1
   }
 }
@@ -401,10 +433,12 @@ void launch_poisson(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   launch_dht_y(c, f, s);
 }
 
+size_t poisson_table_size(const Consts& c) { return (size_t)c.nx * ptab_plane(c); }
+
 template <class T>
 void launch_poisson_table(const Consts& c, const Fields<T>& f, cudaStream_t s) {
-  const int P = c.ny * c.nz;
-  k_poisson_table<T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab);
+  const int PT = (int)ptab_plane(c);
+  k_poisson_table<T><<<(PT + 127) / 128, 128, 0, s>>>(c, f.ptab);
 }
 
 template void launch_poisson<double>(const Consts&, const Fields<double>&, cudaStream_t);

@@ -18,7 +18,7 @@ struct Fields {
   double* taps;               // periodic inverse taps along y (ny), z (nz), then free-space x taps
   float* tapsf;               // the same in FP32
   T* phi;                     // divergence -> transforms -> pressure correction
-  T* ptab;                    // Poisson Thomas inverse pivots per mode
+  T* ptab;                    // Poisson Thomas inverse pivots per distinct mode
   T* dout[3];                 // outflow-plane increments (ny * nz each)
   T* tw_y; T* tw_z;           // FFT twiddles exp(-2 pi i t / N), t < N/2 (re, im)
   double* partial;            // per-block partial maxima of the CFL speed
@@ -76,6 +76,7 @@ template <class T> void launch_project_only(const Consts& c, const Fields<T>& f,
 template <class T> void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 template <class T> void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 int partial_count(const Consts& c);
+size_t poisson_table_size(const Consts& c);
 int outflow_blocks(const Consts& c);
 void fluid_set_attributes();
 template <class T> void launch_stats(const Consts& c, const Fields<T>& f, int cur, double* out, cudaStream_t s);
