@@ -438,6 +438,263 @@ k_rhs_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ u,
   }
 }
 
+// Streamed explicit stage, vector form. Same arithmetic as above; each thread
+// owns a run of E = 16 / sizeof(T) consecutive z points of one row and reads
+// its stencil rows with 16-byte shared loads (plus single values at the run's
+// two z edges), so a cell costs about eight shared loads instead of ~34.
+// The ring stages u, v, w (rows j0-1 .. j0+TJ) and p (rows j0-1 .. j0+TJ-1)
+// of one x plane per slot; N^{n-1} is read straight from global memory into
+// registers (it has no neighbours in the stencil). A block is TJ rows of
+// runs (256 threads at nz = 256); FP32 fits two blocks per SM.
+template <class T>
+struct RhsVec {
+  static constexpr int E = 16 / sizeof(T);
+  static constexpr int TJ = sizeof(T) == 4 ? 4 : 2;
+  static constexpr int RW = TJ + 2;
+  static constexpr int ROWS = 3 * RW + TJ + 1;
+  static constexpr int STAGES = 4;
+};
+template <class T>
+struct V16;
+template <>
+struct V16<float> {
+  using type = float4;
+};
+template <>
+struct V16<double> {
+  using type = double2;
+};
+template <class T, int E>
+__device__ inline void lds_run(const T* p, T (&v)[E]) {
+  const typename V16<T>::type q = *reinterpret_cast<const typename V16<T>::type*>(p);
+  if constexpr (E == 4) {
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  } else {
+    v[0] = q.x;
+    v[1] = q.y;
+  }
+}
+template <class T, int E>
+__device__ inline void stg_run(T* p, const T (&v)[E]) {
+  using V = typename V16<T>::type;
+  if constexpr (E == 4) {
+    *reinterpret_cast<V*>(p) = V{v[0], v[1], v[2], v[3]};
+  } else {
+    *reinterpret_cast<V*>(p) = V{v[0], v[1]};
+  }
+}
+template <class T, int E>
+__device__ inline void ldg_run(const T* p, T (&v)[E]) {
+  lds_run<T, E>(p, v);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256, 2)
+k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* __restrict__ v,
+          const T* __restrict__ w, const T* __restrict__ p, T* __restrict__ n0,
+          T* __restrict__ n1, T* __restrict__ n2, T* __restrict__ d0, T* __restrict__ d1,
+          T* __restrict__ d2, int XR) {
+  using RV = RhsVec<T>;
+  constexpr int E = RV::E, TJ = RV::TJ, RW = RV::RW, ROWS = RV::ROWS, NS = RV::STAGES;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t full[NS];
+  const int nx = c.nx, ny = c.ny, nz = c.nz;
+  const int tid = threadIdx.x;
+  const int j0 = blockIdx.x * TJ;
+  const int ib = blockIdx.y * XR, ie = min(ib + XR, nx);
+  const size_t rowb = (size_t)nz * sizeof(T);
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  auto stage_ptr = [&](int slot) { return ring + (size_t)slot * ROWS * nz; };
+  const int nstage = ie - ib + 2;   // stage t holds x plane ib - 1 + t
+  auto issue = [&](int t) {
+    const int q = ib - 1 + t;
+    const int qs = q < 0 ? 0 : q;
+    const bool has_p = (q >= 0 && q <= nx - 1);
+    const int slot = t % NS;
+    T* st = stage_ptr(slot);
+    const uint32_t bytes = (uint32_t)((3 * RW + (has_p ? TJ + 1 : 0)) * rowb);
+    mbar_arrive_expect_tx(&full[slot], bytes);
+    for (int r = 0; r < RW; ++r) {
+      int jj = j0 - 1 + r;
+      jj = jj < 0 ? jj + ny : (jj >= ny ? jj - ny : jj);
+      const size_t g = ((size_t)qs * ny + jj) * nz;
+      bulk_g2s(st + (size_t)r * nz, u + g, (uint32_t)rowb, &full[slot]);
+      bulk_g2s(st + (size_t)(RW + r) * nz, v + g, (uint32_t)rowb, &full[slot]);
+      bulk_g2s(st + (size_t)(2 * RW + r) * nz, w + g, (uint32_t)rowb, &full[slot]);
+    }
+    if (has_p)
+      for (int r = 0; r < TJ + 1; ++r) {
+        int jj = j0 - 1 + r;
+        jj = jj < 0 ? jj + ny : jj;
+        bulk_g2s(st + (size_t)(3 * RW + r) * nz, p + ((size_t)q * ny + jj) * nz, (uint32_t)rowb,
+                 &full[slot]);
+      }
+  };
+  if (tid == 0) {
+    for (int sl = 0; sl < NS; ++sl) mbar_init(&full[sl], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int t = 0; t < NS && t < nstage; ++t) issue(t);
+  const T dt = pick<T>(prm->dt, prm->f_dt), alpha = pick<T>(prm->alpha, prm->f_alpha);
+  const T beta = pick<T>(prm->beta, prm->f_beta);
+  const T nu = pick<T>(c.nu, c.f_nu), ih = pick<T>(c.inv_h, c.f_inv_h);
+  const T ih2 = pick<T>(c.inv_h * c.inv_h, c.f_inv_h2), hf = (T)0.5;
+  const int mask = nz - 1;
+  const int runs = nz / E;                  // runs per row
+  const int r = tid / runs;                 // row of this thread in the tile
+  const int k0 = (tid - r * runs) * E;      // first z point of the run
+  const int km1 = (k0 - 1) & mask, kpE = (k0 + E) & mask;
+  const int j = j0 + r;
+  const int R = (r + 1) * nz, Rm = r * nz, Rp = (r + 2) * nz;   // rows in u, v, w, p blocks
+  auto wait_stage = [&](int t) {
+    return mbar_wait(&full[t % NS], (uint32_t)((t / NS) & 1));
+  };
+  bool ok = wait_stage(0) && wait_stage(1);
+  for (int i = ib; i < ie; ++i) {
+    const int ta = i - ib, tb = ta + 1, tc = ta + 2;
+    const size_t id = ((size_t)i * ny + j) * nz + k0;
+    T Np0[E], Np1[E], Np2[E];
+    ldg_run<T, E>(n0 + id, Np0);
+    ldg_run<T, E>(n1 + id, Np1);
+    ldg_run<T, E>(n2 + id, Np2);
+    ok = ok && wait_stage(tc);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(&prm->error, ERR_TIMEOUT);
+        // let the copies already issued (stages up to ta - 1 + NS) land first
+        for (int t = tc; t < nstage && t < ta + NS; ++t) (void)wait_stage(t);
+      }
+      return;
+    }
+    const T* A = stage_ptr(ta % NS);
+    const T* B = stage_ptr(tb % NS);
+    const T* C = stage_ptr(tc % NS);
+    const T* Ua = A;
+    const T* Ub = B;
+    const T* Uc = C;
+    const T* Va = A + RW * nz;
+    const T* Vb = B + RW * nz;
+    const T* Vc = C + RW * nz;
+    const T* Wa = A + 2 * RW * nz;
+    const T* Wb = B + 2 * RW * nz;
+    const T* Wc = C + 2 * RW * nz;
+    const T* Pa = A + 3 * RW * nz;
+    const T* Pb = B + 3 * RW * nz;
+    const T sgn = i - 1 < 0 ? (T)-1 : (T)1;   // inflow reflection ghost of v, w
+    // shared rows of the run (E values) and edge values
+    T ub[E], ubm[E], ubp[E], uc[E], ucm[E];
+    T vb[E], vbm[E], vbp[E], va[E], vap[E], vc[E];
+    T wb[E], wbm[E], wbp[E], wa[E], wc[E];
+    T pb[E], pbm[E];
+    lds_run<T, E>(Ub + R + k0, ub);
+    lds_run<T, E>(Ub + Rm + k0, ubm);
+    lds_run<T, E>(Ub + Rp + k0, ubp);
+    lds_run<T, E>(Uc + R + k0, uc);
+    lds_run<T, E>(Uc + Rm + k0, ucm);
+    lds_run<T, E>(Vb + R + k0, vb);
+    lds_run<T, E>(Vb + Rm + k0, vbm);
+    lds_run<T, E>(Vb + Rp + k0, vbp);
+    lds_run<T, E>(Va + R + k0, va);
+    lds_run<T, E>(Va + Rp + k0, vap);
+    lds_run<T, E>(Vc + R + k0, vc);
+    lds_run<T, E>(Wb + R + k0, wb);
+    lds_run<T, E>(Wb + Rm + k0, wbm);
+    lds_run<T, E>(Wb + Rp + k0, wbp);
+    lds_run<T, E>(Wa + R + k0, wa);
+    lds_run<T, E>(Wc + R + k0, wc);
+    lds_run<T, E>(Pb + R + k0, pb);
+    lds_run<T, E>(Pb + Rm + k0, pbm);
+    const T ub_l = Ub[R + km1], ub_r = Ub[R + kpE], uc_l = Uc[R + km1];
+    const T vb_l = Vb[R + km1], vb_r = Vb[R + kpE], vbp_l = Vb[Rp + km1];
+    const T wb_l = Wb[R + km1], wb_r = Wb[R + kpE], wa_r = Wa[R + kpE], wbm_r = Wb[Rm + kpE];
+    const T pb_l = Pb[R + km1];
+    T No[E], Do[E];
+    // u on face i (interior faces only)
+    if (i >= 1) {
+      T ua[E], pa[E];
+      lds_run<T, E>(Ua + R + k0, ua);
+      lds_run<T, E>(Pa + R + k0, pa);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const T c0 = ub[e];
+        const T uzp = e == E - 1 ? ub_r : ub[e + 1], uzm = e == 0 ? ub_l : ub[e - 1];
+        const T wap = e == E - 1 ? wa_r : wa[e + 1], wbp1 = e == E - 1 ? wb_r : wb[e + 1];
+        T fxp = hf * (c0 + uc[e]);
+        fxp *= fxp;
+        T fxm = hf * (ua[e] + c0);
+        fxm *= fxm;
+        const T fxy0 = hf * (ubm[e] + c0) * (hf * (sgn * va[e] + vb[e]));
+        const T fxy1 = hf * (c0 + ubp[e]) * (hf * (sgn * vap[e] + vbp[e]));
+        const T fxz0 = hf * (uzm + c0) * (hf * (sgn * wa[e] + wb[e]));
+        const T fxz1 = hf * (c0 + uzp) * (hf * (sgn * wap + wbp1));
+        const T N = (fxp - fxm + fxy1 - fxy0 + fxz1 - fxz0) * ih;
+        const T L = (uc[e] + ua[e] + ubp[e] + ubm[e] + uzp + uzm - (T)6 * c0) * ih2;
+        const T Gp = (pb[e] - pa[e]) * ih;
+        No[e] = N;
+        Do[e] = dt * (-(alpha * N + beta * Np0[e]) - Gp + nu * L);
+      }
+      stg_run<T, E>(n0 + id, No);
+      stg_run<T, E>(d0 + id, Do);
+    }
+    // v at (i + 1/2, j, k + 1/2)
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const T c0 = vb[e];
+      const T vxp = vc[e], vxm = sgn * va[e];
+      const T vzp = e == E - 1 ? vb_r : vb[e + 1], vzm = e == 0 ? vb_l : vb[e - 1];
+      const T wbp1 = e == E - 1 ? wb_r : wb[e + 1], wbmp1 = e == E - 1 ? wbm_r : wbm[e + 1];
+      const T fxr = hf * (ucm[e] + uc[e]) * (hf * (c0 + vxp));
+      const T fxl = hf * (ubm[e] + ub[e]) * (hf * (vxm + c0));
+      T fyp = hf * (c0 + vbp[e]);
+      fyp *= fyp;
+      T fym = hf * (vbm[e] + c0);
+      fym *= fym;
+      const T fz1 = hf * (c0 + vzp) * (hf * (wbmp1 + wbp1));
+      const T fz0 = hf * (vzm + c0) * (hf * (wbm[e] + wb[e]));
+      const T N = (fxr - fxl + fyp - fym + fz1 - fz0) * ih;
+      const T L = (vxp + vxm + vbp[e] + vbm[e] + vzp + vzm - (T)6 * c0) * ih2;
+      const T Gp = (pb[e] - pbm[e]) * ih;
+      No[e] = N;
+      Do[e] = dt * (-(alpha * N + beta * Np1[e]) - Gp + nu * L);
+    }
+    stg_run<T, E>(n1 + id, No);
+    stg_run<T, E>(d1 + id, Do);
+    // w at (i + 1/2, j + 1/2, k)
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const T c0 = wb[e];
+      const T wxp = wc[e], wxm = sgn * wa[e];
+      const T wzp = e == E - 1 ? wb_r : wb[e + 1], wzm = e == 0 ? wb_l : wb[e - 1];
+      const T ucl = e == 0 ? uc_l : uc[e - 1], ubl = e == 0 ? ub_l : ub[e - 1];
+      const T vbpl = e == 0 ? vbp_l : vbp[e - 1], vbl = e == 0 ? vb_l : vb[e - 1];
+      const T pbl = e == 0 ? pb_l : pb[e - 1];
+      const T fxr = hf * (ucl + uc[e]) * (hf * (c0 + wxp));
+      const T fxl = hf * (ubl + ub[e]) * (hf * (wxm + c0));
+      const T fy1 = hf * (vbpl + vbp[e]) * (hf * (c0 + wbp[e]));
+      const T fy0 = hf * (vbl + vb[e]) * (hf * (wbm[e] + c0));
+      T fzp = hf * (c0 + wzp);
+      fzp *= fzp;
+      T fzm = hf * (wzm + c0);
+      fzm *= fzm;
+      const T N = (fxr - fxl + fy1 - fy0 + fzp - fzm) * ih;
+      const T L = (wxp + wxm + wbp[e] + wbm[e] + wzp + wzm - (T)6 * c0) * ih2;
+      const T Gp = (pb[e] - pbl) * ih;
+      No[e] = N;
+      Do[e] = dt * (-(alpha * N + beta * Np2[e]) - Gp + nu * L);
+    }
+    stg_run<T, E>(n2 + id, No);
+    stg_run<T, E>(d2 + id, Do);
+    __syncthreads();
+    // the slot of plane i-1 is free: refill it with the stage NS ahead
+    if (tid == 0 && ta + NS < nstage) issue(ta + NS);
+  }
+}
+
 // ---------------------------------------------------------------- outflow (A1)
 // Convective condition dq/dt + U dq/dx = 0 on the outflow plane, first-order
 // upwind; the increment is kept for the x line solve. The inflow and new
@@ -1272,6 +1529,18 @@ static size_t rhs_stage_bytes(const Consts& c, int tjr) {
 
 template <class T>
 void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
+  {
+    using RV = RhsVec<T>;
+    const int threads = RV::TJ * (c.nz / RV::E);
+    const size_t sh = (size_t)RV::STAGES * RV::ROWS * c.nz * sizeof(T);
+    if (threads % 32 == 0 && threads <= 256 && c.ny % RV::TJ == 0 && sh <= 200 * 1024) {
+      const int XR = c.rhs_planes;
+      k_rhs_vec<T><<<dim3(c.ny / RV::TJ, (c.nx + XR - 1) / XR), threads, sh, s>>>(
+          c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.p, f.n[0], f.n[1], f.n[2], f.d[0], f.d[1],
+          f.d[2], XR);
+      return;
+    }
+  }
   constexpr int TJR = sizeof(T) == 4 ? 4 : 2;
   const size_t stage = rhs_stage_bytes<T>(c, TJR);
   const int rs = (int)std::min<size_t>(std::min(RSTAGES_MAX, c.rhs_stages), (size_t)(210 * 1024) / stage);
@@ -1426,6 +1695,8 @@ void launch_stats(const Consts& c, const Fields<T>& f, int cur, double* out, cud
 
 void fluid_set_attributes() {
   cudaFuncSetAttribute(k_rhs_pipe<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
+  cudaFuncSetAttribute(k_rhs_vec<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_rhs_vec<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_rhs_pipe<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
   cudaFuncSetAttribute(k_af_xc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_zc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
