@@ -259,6 +259,8 @@ struct Layout {
 }  // namespace
 
 // ------------------------------------------------------------------ state
+enum { GRAPH_HEAD = 0, GRAPH_MID = 1, GRAPH_TAIL = 2, GRAPH_KINDS = 3 };
+
 struct ibm_state {
   int precision = IBM_FP64;
   Consts c{};
@@ -272,8 +274,8 @@ struct ibm_state {
   size_t ws_bytes = 0;
   bool own_ws = false;
   int cur = 0;
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  cudaGraph_t graph[2] = {nullptr, nullptr};   // kept for ensembles
+  cudaGraphExec_t exec[GRAPH_KINDS][2] = {};
+  cudaGraph_t graph[GRAPH_KINDS][2] = {};      // kept for ensembles
   Fields<double> fd{};
   Fields<float> ff{};
   Markers mk{};
@@ -435,10 +437,6 @@ int download_field(cudaStream_t st, double* dst, const T* src, size_t n) {
   return IBM_OK;
 }
 
-// One time step. The structural update of the previous step (pending since
-// its forcing) runs on a side stream concurrently with this step's explicit
-// and implicit velocity stages, and joins before this step's forcing, which
-// reads the updated flag positions.
 template <class T>
 void solve_poisson(ibm_state* s, cudaStream_t st) {
   Fields<T>& f = fields<T>(s);
@@ -451,18 +449,19 @@ void solve_poisson(ibm_state* s, cudaStream_t st) {
   launch_poisson(s->c, f, st);
 }
 
+// A time step is split at the immersed-boundary forcing into a head (dt, RHS,
+// implicit factors) and a tail (forcing, structure, pressure, projection).
+// The structural update needs only the forcing's result and is needed only
+// by the next step's forcing, so it runs on a side stream from the forcing of
+// one step to the end of the next step's head. ibm_step(n) therefore replays
+//   head(n0), mid x (n - 1), tail,   mid = tail of one step + head of the next,
+// three captured graphs per velocity buffer parity; every replay ends with
+// all its work (the structural update included) joined.
 template <class T>
-void record_step(ibm_state* s, int cur) {
+void record_head(ibm_state* s, int cur) {
   Fields<T>& f = fields<T>(s);
   const Consts& c = s->c;
   cudaStream_t st = s->stream;
-  const bool flag = s->fl.nv > 0;
-  if (flag) {
-    cudaEventRecord(s->ev_fork, st);
-    cudaStreamWaitEvent(s->side, s->ev_fork, 0);
-    launch_flag(f.prm, s->fl, false, s->side);
-    cudaEventRecord(s->ev_join, s->side);
-  }
   launch_begin_step(c, f, st);
   // the implicit factors' tables for this step's r, concurrent with the RHS
   cudaEventRecord(s->ev_fork2, st);
@@ -473,11 +472,37 @@ void record_step(ibm_state* s, int cur) {
   launch_outflow(c, f, cur, st);
   cudaStreamWaitEvent(st, s->ev_join2, 0);
   launch_af(c, f, cur, st);
-  if (flag) cudaStreamWaitEvent(st, s->ev_join, 0);
+}
+
+// forcing, structural update forked; returns whether a join is owed
+template <class T>
+bool record_tail_body(ibm_state* s, int cur) {
+  Fields<T>& f = fields<T>(s);
+  const Consts& c = s->c;
+  cudaStream_t st = s->stream;
   launch_ib(c, f, s->mk, s->fl, cur, st);
+  const bool flag = s->fl.nv > 0;
+  if (flag) {
+    cudaEventRecord(s->ev_fork, st);
+    cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+    launch_flag(f.prm, s->fl, false, s->side);
+    cudaEventRecord(s->ev_join, s->side);
+  }
   launch_mass_div(c, f, cur, false, st);
   solve_poisson<T>(s, st);
   launch_project(c, f, cur, false, st);
+  return flag;
+}
+
+template <class T>
+void record_graph(ibm_state* s, int kind, int cur) {
+  if (kind == GRAPH_HEAD) {
+    record_head<T>(s, cur);
+    return;
+  }
+  const bool join = record_tail_body<T>(s, cur);
+  if (kind == GRAPH_MID) record_head<T>(s, cur ^ 1);
+  if (join) cudaStreamWaitEvent(s->stream, s->ev_join, 0);
 }
 
 template <class T>
@@ -571,26 +596,29 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
   CK(cudaStreamCreateWithFlags(&s->side2, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&s->ev_fork2, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->ev_join2, cudaEventDisableTiming));
-  // capture one step per buffer parity
-  for (int par = 0; par < 2; ++par) {
-    cudaGraph_t g;
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    record_step<T>(s, par);
-    cudaError_t e = cudaStreamEndCapture(st, &g);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return IBM_ECUDA;
+  // capture head, mid and tail per buffer parity
+  for (int kind = 0; kind < GRAPH_KINDS; ++kind)
+    for (int par = 0; par < 2; ++par) {
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      record_graph<T>(s, kind, par);
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return IBM_ECUDA;
+      }
+      if (kind == GRAPH_MID) {
+        size_t nodes = 0;
+        cudaGraphGetNodes(g, nullptr, &nodes);
+        s->kernels_per_step = (int)nodes;   // a steady-state step: tail + next head
+      }
+      e = cudaGraphInstantiate(&s->exec[kind][par], g, 0);
+      s->graph[kind][par] = g;
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return IBM_ECUDA;
+      }
     }
-    size_t nodes = 0;
-    cudaGraphGetNodes(g, nullptr, &nodes);
-    s->kernels_per_step = (int)nodes;
-    e = cudaGraphInstantiate(&s->exec[par], g, 0);
-    s->graph[par] = g;
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return IBM_ECUDA;
-    }
-  }
   return IBM_OK;
 }
 
@@ -644,13 +672,15 @@ int step_impl(ibm_state* s, double dt, int nsteps) {
     CK(cudaStreamSynchronize(st));
     s->last_dt_fixed = mode;
   }
-  for (int n = 0; n < nsteps; ++n) {
-    CK(cudaGraphLaunch(s->exec[s->cur], st));
+  if (nsteps > 0) {
+    CK(cudaGraphLaunch(s->exec[GRAPH_HEAD][s->cur], st));
+    for (int n = 1; n < nsteps; ++n) {
+      CK(cudaGraphLaunch(s->exec[GRAPH_MID][s->cur], st));
+      s->cur ^= 1;
+    }
+    CK(cudaGraphLaunch(s->exec[GRAPH_TAIL][s->cur], st));
     s->cur ^= 1;
   }
-  // the last step's structural update is still pending: run it now, so that
-  // the state is complete when ibm_step returns
-  if (nsteps > 0) launch_flag(f.prm, s->fl, false, st);
   CK(cudaMemcpyAsync(s->hprm, f.prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const Params& p = *s->hprm;
@@ -844,7 +874,8 @@ int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
   CK(cudaEventRecord(e0, st));
   for (int r = 0; r < nrep; ++r) {
     if (stage == IBM_STAGE_STEP) {
-      cudaGraphLaunch(s->exec[s->cur], st);
+      cudaGraphLaunch(s->exec[GRAPH_HEAD][s->cur], st);
+      cudaGraphLaunch(s->exec[GRAPH_TAIL][s->cur], st);
       s->cur ^= 1;
     } else if (s->precision == IBM_FP64) {
       launch_stage<double>(s, stage);
@@ -1036,10 +1067,11 @@ int ibm_load(ibm_state* s, const char* path) {
 void ibm_destroy(ibm_state* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
-  for (int q = 0; q < 2; ++q) {
-    if (s->exec[q]) cudaGraphExecDestroy(s->exec[q]);
-    if (s->graph[q]) cudaGraphDestroy(s->graph[q]);
-  }
+  for (int k = 0; k < GRAPH_KINDS; ++k)
+    for (int q = 0; q < 2; ++q) {
+      if (s->exec[k][q]) cudaGraphExecDestroy(s->exec[k][q]);
+      if (s->graph[k][q]) cudaGraphDestroy(s->graph[k][q]);
+    }
   if (s->own_ws && s->ws) cudaFree(s->ws);
   if (s->hprm) cudaFreeHost(s->hprm);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -1056,7 +1088,9 @@ void ibm_destroy(ibm_state* s) {
 // ------------------------------------------------------------------ ensembles
 struct ibm_ensemble {
   std::vector<ibm_state*> members;
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};   // members' parity as at creation, flipped
+  // [kind][offset]: every member runs its graph of that kind for buffer
+  // parity (its parity at creation + offset) & 1
+  cudaGraphExec_t exec[GRAPH_KINDS][2] = {};
   int par = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -1080,7 +1114,8 @@ int ibm_ensemble_create(ibm_state* const* members, int n, void* stream, ibm_ense
   std::unique_ptr<ibm_ensemble> e(new (std::nothrow) ibm_ensemble());
   if (!e) return IBM_ENOMEM;
   for (int q = 0; q < n; ++q) {
-    if (!members[q] || !members[q]->graph[0] || !members[q]->graph[1]) return IBM_EINVAL;
+    if (!members[q] || !members[q]->graph[GRAPH_MID][0] || !members[q]->graph[GRAPH_MID][1])
+      return IBM_EINVAL;
     for (int r = 0; r < q; ++r)
       if (members[r] == members[q]) return IBM_EINVAL;
     e->members.push_back(members[q]);
@@ -1092,29 +1127,32 @@ int ibm_ensemble_create(ibm_state* const* members, int n, void* stream, ibm_ense
     CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
     e->own_stream = true;
   }
-  // one parent graph per parity offset: member q runs its step graph for
-  // buffer parity (cur_q + offset) & 1, all members as independent branches
-  for (int off = 0; off < 2; ++off) {
-    cudaGraph_t parent;
-    CK(cudaGraphCreate(&parent, 0));
-    for (ibm_state* m : e->members) {
-      cudaGraphNode_t node;
-      cudaError_t err = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, m->graph[(m->cur + off) & 1]);
+  // one parent graph per graph kind and parity offset: member q runs its graph
+  // of that kind for buffer parity (cur_q + offset) & 1, all members as
+  // independent branches
+  for (int kind = 0; kind < GRAPH_KINDS; ++kind)
+    for (int off = 0; off < 2; ++off) {
+      cudaGraph_t parent;
+      CK(cudaGraphCreate(&parent, 0));
+      for (ibm_state* m : e->members) {
+        cudaGraphNode_t node;
+        cudaError_t err = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0,
+                                                     m->graph[kind][(m->cur + off) & 1]);
+        if (err != cudaSuccess) {
+          cudaGraphDestroy(parent);
+          cudaGetLastError();
+          ibm_ensemble_destroy(e.release());
+          return IBM_ECUDA;
+        }
+      }
+      cudaError_t err = cudaGraphInstantiate(&e->exec[kind][off], parent, 0);
+      cudaGraphDestroy(parent);
       if (err != cudaSuccess) {
-        cudaGraphDestroy(parent);
         cudaGetLastError();
         ibm_ensemble_destroy(e.release());
         return IBM_ECUDA;
       }
     }
-    cudaError_t err = cudaGraphInstantiate(&e->exec[off], parent, 0);
-    cudaGraphDestroy(parent);
-    if (err != cudaSuccess) {
-      cudaGetLastError();
-      ibm_ensemble_destroy(e.release());
-      return IBM_ECUDA;
-    }
-  }
   *out = e.release();
   return IBM_OK;
 }
@@ -1126,16 +1164,20 @@ int ibm_ensemble_step(ibm_ensemble* e, double dt, int nsteps) {
     int rc = ensemble_set_dt(m, dt, st);
     if (rc) return rc;
   }
-  for (int n = 0; n < nsteps; ++n) {
-    CK(cudaGraphLaunch(e->exec[e->par], st));
+  if (nsteps > 0) {
+    CK(cudaGraphLaunch(e->exec[GRAPH_HEAD][e->par], st));
+    for (int n = 1; n < nsteps; ++n) {
+      CK(cudaGraphLaunch(e->exec[GRAPH_MID][e->par], st));
+      e->par ^= 1;
+    }
+    CK(cudaGraphLaunch(e->exec[GRAPH_TAIL][e->par], st));
     e->par ^= 1;
-    for (ibm_state* m : e->members) m->cur ^= 1;
+    if (nsteps & 1)
+      for (ibm_state* m : e->members) m->cur ^= 1;
   }
   int result = IBM_OK;
-  for (ibm_state* m : e->members) {
-    if (nsteps > 0) launch_flag(m->prm, m->fl, false, st);
+  for (ibm_state* m : e->members)
     CK(cudaMemcpyAsync(m->hprm, m->prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
-  }
   CK(cudaStreamSynchronize(st));
   for (ibm_state* m : e->members) {
     const Params& p = *m->hprm;
@@ -1152,8 +1194,9 @@ int ibm_ensemble_step(ibm_ensemble* e, double dt, int nsteps) {
 void ibm_ensemble_destroy(ibm_ensemble* e) {
   if (!e) return;
   if (e->stream) cudaStreamSynchronize(e->stream);
-  for (int q = 0; q < 2; ++q)
-    if (e->exec[q]) cudaGraphExecDestroy(e->exec[q]);
+  for (int k = 0; k < GRAPH_KINDS; ++k)
+    for (int q = 0; q < 2; ++q)
+      if (e->exec[k][q]) cudaGraphExecDestroy(e->exec[k][q]);
   if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
   cudaGetLastError();
   delete e;
