@@ -354,7 +354,7 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   for (int q = 0; q < 3; ++q) f.dout[q] = cv.take<T>(P);
   f.tw_y = cv.take<T>(c.ny);
   f.tw_z = cv.take<T>(c.nz);
-  f.n_partial = partial_count(c);
+  f.n_partial = partial_count<T>(c);
   f.partial = cv.take<double>(f.n_partial);
   f.qpart = cv.take<double>(2 * (size_t)outflow_blocks(c));
   f.prm = cv.take<Params>(1);

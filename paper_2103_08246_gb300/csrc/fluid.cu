@@ -1469,6 +1469,174 @@ k_project(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
   }
 }
 
+// Vector forms of the divergence and the projection: a thread owns a run of
+// E = 16 / sizeof(T) consecutive z points of one row and walks x planes, so
+// every field access is a 16-byte load or store (single values at the run's
+// two z edges); the projection keeps phi of planes i-1, i, i+1 and the new u
+// of the next face in registers. Block: TJ rows x (nz / E) runs = 256 threads.
+template <class T>
+struct RunTile {
+  static constexpr int E = 16 / sizeof(T);
+  static constexpr int THREADS = 256;
+};
+// rows per block of the run kernels, 0 when the shape does not fit them
+template <class T>
+int run_rows(const Consts& c) {
+  const int runs = c.nz / RunTile<T>::E;
+  if (runs < 1 || runs > RunTile<T>::THREADS || RunTile<T>::THREADS % runs) return 0;
+  const int tj = RunTile<T>::THREADS / runs;
+  return c.ny % tj == 0 ? tj : 0;
+}
+constexpr int RUN_XCH = 16;   // x planes per block of the run kernels
+
+template <class T>
+__global__ void __launch_bounds__(256)
+k_div_vec(Consts c, const Params* __restrict__ prm, T* __restrict__ u, const T* __restrict__ v,
+          const T* __restrict__ w, T* __restrict__ phi, int initial) {
+  constexpr int E = RunTile<T>::E;
+  const int nx = c.nx, ny = c.ny, nz = c.nz;
+  const int runs = nz / E;
+  const int tj = RunTile<T>::THREADS / runs;
+  const int r = threadIdx.x / runs, k0 = (threadIdx.x - r * runs) * E;
+  const int j = blockIdx.x * tj + r;
+  const int jp = (j + 1) & (ny - 1), kpE = (k0 + E) & (nz - 1);
+  const size_t P = plane(c);
+  const T shift = initial ? (T)0 : pick<T>(prm->mass_shift, prm->f_mass_shift);
+  const T sc = initial ? pick<T>(c.inv_h, c.f_inv_h) : pick<T>(c.inv_h / prm->dt, prm->f_sc_div);
+  const int i0 = blockIdx.y * RUN_XCH, i1 = min(i0 + RUN_XCH, nx);
+  if (i0 >= i1) return;
+  T uw[E];
+  ldg_run<T, E>(u + ((size_t)i0 * ny + j) * nz + k0, uw);
+  for (int i = i0; i < i1; ++i) {
+    const size_t id = ((size_t)i * ny + j) * nz + k0;
+    T ue[E], vv[E], vn[E], ww[E], dv[E];
+    ldg_run<T, E>(u + id + P, ue);
+    ldg_run<T, E>(v + id, vv);
+    ldg_run<T, E>(v + ((size_t)i * ny + jp) * nz + k0, vn);
+    ldg_run<T, E>(w + id, ww);
+    const T w_r = w[((size_t)i * ny + j) * nz + kpE];
+    if (i == nx - 1) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) ue[e] += shift;
+      stg_run<T, E>(u + id + P, ue);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const T wp = e == E - 1 ? w_r : ww[e + 1];
+      dv[e] = ((ue[e] - uw[e]) + (vn[e] - vv[e]) + (wp - ww[e])) * sc;
+      uw[e] = ue[e];
+    }
+    stg_run<T, E>(phi + id, dv);
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256)
+k_project_vec(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
+              const T* __restrict__ va, const T* __restrict__ wa, T* __restrict__ ub,
+              T* __restrict__ vb, T* __restrict__ wb, const T* __restrict__ phi, T* __restrict__ p,
+              double* __restrict__ partial, int initial) {
+  constexpr int E = RunTile<T>::E;
+  const int nx = c.nx, ny = c.ny, nz = c.nz;
+  const int runs = nz / E;
+  const int tj = RunTile<T>::THREADS / runs;
+  const int tid = threadIdx.x;
+  const int r = tid / runs, k0 = (tid - r * runs) * E;
+  const int j = blockIdx.x * tj + r;
+  const int jm = (j - 1) & (ny - 1), jp = (j + 1) & (ny - 1);
+  const int km1 = (k0 - 1) & (nz - 1), kpE = (k0 + E) & (nz - 1);
+  auto at = [&](int i, int jj, int kk) { return ((size_t)i * ny + jj) * nz + kk; };
+  const T gdt = initial ? pick<T>(c.inv_h, c.f_inv_h) : pick<T>(prm->dt * c.inv_h, prm->f_gdt);
+  const T hnu = initial ? (T)0 : pick<T>(0.5 * c.nu * prm->dt * c.inv_h * c.inv_h, prm->f_hnu);
+  const int i0 = blockIdx.y * RUN_XCH, i1 = min(i0 + RUN_XCH, nx + 1);
+  T smax = 0;
+  T phm[E], ph[E], php[E], un[E], un1[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) phm[e] = ph[e] = (T)0;
+  if (i0 >= 1 && i0 - 1 <= nx - 1) ldg_run<T, E>(phi + at(i0 - 1, j, k0), phm);
+  if (i0 <= nx - 1) ldg_run<T, E>(phi + at(i0, j, k0), ph);
+  ldg_run<T, E>(ua + at(i0, j, k0), un);
+  if (i0 >= 1 && i0 <= nx - 1) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) un[e] -= gdt * (ph[e] - phm[e]);
+  }
+  for (int i = i0; i < i1; ++i) {
+    const size_t id = at(i, j, k0);
+    if (i == nx) {   // outflow face and the ghost planes of v, w: copies
+      T t[E];
+      stg_run<T, E>(ub + id, un);
+      ldg_run<T, E>(va + id, t);
+      stg_run<T, E>(vb + id, t);
+      ldg_run<T, E>(wa + id, t);
+      stg_run<T, E>(wb + id, t);
+      break;
+    }
+    // next plane: phi (Neumann image at the last plane) and the new u of face i+1
+    if (i + 1 <= nx - 1) {
+      ldg_run<T, E>(phi + id + plane(c), php);
+    } else {
+#pragma unroll
+      for (int e = 0; e < E; ++e) php[e] = ph[e];
+    }
+    ldg_run<T, E>(ua + id + plane(c), un1);
+    if (i + 1 <= nx - 1) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) un1[e] -= gdt * (php[e] - ph[e]);
+    }
+    T vv[E], vjp[E], ww[E], pjm[E], pjp[E], pp[E];
+    ldg_run<T, E>(va + id, vv);
+    ldg_run<T, E>(va + at(i, jp, k0), vjp);
+    ldg_run<T, E>(wa + id, ww);
+    ldg_run<T, E>(phi + at(i, jm, k0), pjm);
+    ldg_run<T, E>(phi + at(i, jp, k0), pjp);
+    const T w_r = wa[at(i, j, kpE)];
+    const T ph_l = phi[at(i, j, km1)], ph_r = phi[at(i, j, kpE)];
+    if (!initial) ldg_run<T, E>(p + id, pp);
+    stg_run<T, E>(ub + id, un);
+    T vo[E], wo[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const T pl = e == 0 ? ph_l : ph[e - 1], pr = e == E - 1 ? ph_r : ph[e + 1];
+      const T wr = e == E - 1 ? w_r : ww[e + 1];
+      const T vn = vv[e] - gdt * (ph[e] - pjm[e]);
+      const T wn = ww[e] - gdt * (ph[e] - pl);
+      vo[e] = vn;
+      wo[e] = wn;
+      const T vn1 = vjp[e] - gdt * (pjp[e] - ph[e]);
+      const T wn1 = wr - gdt * (pr - ph[e]);
+      if (!initial) {
+        const T pxm = i == 0 ? ph[e] : phm[e];
+        const T lap = pxm + php[e] + pjm[e] + pjp[e] + pl + pr - (T)6 * ph[e];
+        pp[e] += ph[e] - hnu * lap;
+      }
+      T sp = fabs((T)0.5 * (un[e] + un1[e])) + fabs((T)0.5 * (vn + vn1)) +
+             fabs((T)0.5 * (wn + wn1));
+      if (!isfinite(sp)) sp = (T)INFINITY;
+      smax = fmax(smax, sp);
+    }
+    stg_run<T, E>(vb + id, vo);
+    stg_run<T, E>(wb + id, wo);
+    if (!initial) stg_run<T, E>(p + id, pp);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      phm[e] = ph[e];
+      ph[e] = php[e];
+      un[e] = un1[e];
+    }
+  }
+  // block maximum (in T: a max is exact)
+  T vmax = smax;
+  for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  __shared__ T wmax[RunTile<T>::THREADS / 32];
+  if ((tid & 31) == 0) wmax[tid >> 5] = vmax;
+  __syncthreads();
+  if (tid == 0) {
+    T m = 0;
+    for (int q = 0; q < RunTile<T>::THREADS / 32; ++q) m = fmax(m, wmax[q]);
+    partial[blockIdx.y * gridDim.x + blockIdx.x] = (double)m;
+  }
+}
+
 // ---------------------------------------------------------------- diagnostics
 // out[0] += kinetic energy, out[1] = max |div u| (atomics; diagnostics only)
 template <class T>
@@ -1665,6 +1833,11 @@ void launch_mass(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
 
 template <class T>
 void launch_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
+  if (const int tj = run_rows<T>(c)) {
+    k_div_vec<T><<<dim3(c.ny / tj, (c.nx + RUN_XCH - 1) / RUN_XCH), RunTile<T>::THREADS, 0, s>>>(
+        c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.phi, initial ? 1 : 0);
+    return;
+  }
   k_div<T><<<grid3(c, c.nx), dim3(TK, TJ), 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.phi,
                                                     initial ? 1 : 0);
 }
@@ -1677,6 +1850,12 @@ void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial,
 
 template <class T>
 void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
+  if (const int tj = run_rows<T>(c)) {
+    k_project_vec<T><<<dim3(c.ny / tj, (c.nx + 1 + RUN_XCH - 1) / RUN_XCH), RunTile<T>::THREADS, 0,
+                       s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.u[cur ^ 1], f.v[cur ^ 1],
+                            f.w[cur ^ 1], f.phi, f.p, f.partial, initial ? 1 : 0);
+    return;
+  }
   k_project<T><<<grid3(c, c.nx + 1), dim3(TK, TJ), 0, s>>>(
       c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1], f.phi, f.p,
       f.partial, initial ? 1 : 0);
@@ -1705,10 +1884,15 @@ void fluid_set_attributes() {
   cudaFuncSetAttribute(k_af_z<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
+// blocks of the projection launch (one CFL partial each)
+template <class T>
 int partial_count(const Consts& c) {
+  if (const int tj = run_rows<T>(c)) return c.ny / tj * ((c.nx + 1 + RUN_XCH - 1) / RUN_XCH);
   const dim3 g = grid3(c, c.nx + 1);
   return (int)(g.x * g.y * g.z);
 }
+template int partial_count<float>(const Consts&);
+template int partial_count<double>(const Consts&);
 
 #define INST(T)                                                                                \
   template void launch_begin_step<T>(const Consts&, const Fields<T>&, cudaStream_t);           \

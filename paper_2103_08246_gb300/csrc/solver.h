@@ -75,6 +75,7 @@ template <class T> void launch_div(const Consts& c, const Fields<T>& f, int cur,
 template <class T> void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 template <class T> void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 template <class T> void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
+template <class T>
 int partial_count(const Consts& c);
 size_t poisson_table_size(const Consts& c);
 int outflow_blocks(const Consts& c);
