@@ -18,7 +18,7 @@ from . import binding
 CANDIDATES = {
     "rhs_planes": (8, 16, 32, 64),
     "rhs_stages": (4, 5, 6, 8),
-    "afx_planes": (32, 64, 128),
+    "afx_planes": (16, 32, 64),
 }
 STAGE_OF = {"rhs_planes": "rhs", "rhs_stages": "rhs", "afx_planes": "af_x"}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tile_cache.json")
@@ -51,8 +51,7 @@ def tune(wl, precision, cache_path=DEFAULT_CACHE, reps=5, use_cache=True):
     tiles = {k: v[len(v) // 2] for k, v in CANDIDATES.items()}
     timings = {}
     for name, values in CANDIDATES.items():
-        if name == "afx_planes" and precision == binding.IBM_FP64:
-            continue   # the FP64 x factor has no such tile
+
         best = None
         for val in values:
             trial = dict(tiles, **{name: val})

@@ -644,7 +644,7 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   c.u_in = 1.0;
   c.f_inv_h = (float)c.inv_h;
   c.f_inv_h2 = (float)(c.inv_h * c.inv_h);
-  c.rhs_planes = (o && o->rhs_planes > 0) ? o->rhs_planes : 32;
+  c.rhs_planes = (o && o->rhs_planes > 0) ? o->rhs_planes : 16;
   c.rhs_stages = (o && o->rhs_stages > 0) ? o->rhs_stages : 8;
   c.afx_planes = (o && o->afx_planes > 0) ? o->afx_planes : 64;
   bar_dv = 0.0;

@@ -847,6 +847,95 @@ k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
   }
 }
 
+// x factor in registers: one thread per (y, z) column and XV planes, warm-up
+// halos of H planes on both sides (the LU recursions forget their start
+// within rho^H). Inputs of the segment and of the trailing halo are held in
+// registers for the backward pass; 256 columns per block, every access a
+// coalesced row of the block's columns.
+template <class T, int XV>
+__global__ void __launch_bounds__(256)
+k_af_xv(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
+        const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
+        T* __restrict__ e0, T* __restrict__ e1, T* __restrict__ e2, const T* __restrict__ o0,
+        const T* __restrict__ o1, const T* __restrict__ o2) {
+  const int P = c.ny * c.nz;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  const int comp = blockIdx.z;
+  const int m = comp == 0 ? c.nx - 1 : c.nx;   // unknowns k = 1..m
+  const int ioff = comp == 0 ? 0 : -1;         // plane i = k + ioff
+  const int k0 = 1 + blockIdx.y * XV;
+  if (k0 > m || col >= P) return;
+  const int k1 = min(k0 + XV, m + 1);
+  const int H = prm->af_h;
+  const int ks = max(1, k0 - H), ke = min(m, k1 - 1 + H);
+  const T* ip = ipt + (comp == 0 ? 0 : c.nx + 2);
+  const T ir = pick<T>(1.0 / prm->r, prm->f_ir);
+  const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + (size_t)ioff * P + col;
+  T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + (size_t)ioff * P + col;
+  const T ob = (comp == 0 ? o0 : comp == 1 ? o1 : o2)[col];
+  // forward warm-up over ks .. k0-1 (values not kept)
+  T y = 0;
+  for (int kb = ks; kb < k0; kb += 8) {
+    T buf[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) buf[t] = (kb + t < k0) ? d[(size_t)(kb + t) * P] : (T)0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (kb + t < k0) y = (buf[t] * ir + y) * ip[kb + t];
+  }
+  // the segment
+  const int ns = k1 - k0;
+  T yr[XV];
+#pragma unroll
+  for (int q = 0; q < XV; ++q) yr[q] = q < ns ? d[(size_t)(k0 + q) * P] : (T)0;
+#pragma unroll
+  for (int q = 0; q < XV; ++q)
+    if (q < ns) {
+      const int k = k0 + q;
+      T e = yr[q] * ir;
+      if (k == m) e += ob;
+      y = (e + y) * ip[k];
+      yr[q] = y;
+    }
+  // trailing halo k1 .. ke, kept for the backward pass
+  const int nt = ke - k1 + 1;
+  T yt[HMAX];
+#pragma unroll
+  for (int m0 = 0; m0 < HMAX; m0 += 8) {
+    if (m0 < nt) {
+      T buf[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) buf[t] = (m0 + t < nt) ? d[(size_t)(k1 + m0 + t) * P] : (T)0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int k = k1 + m0 + t;
+        if (m0 + t < nt) {
+          T e = buf[t] * ir;
+          if (k == m) e += ob;
+          y = (e + y) * ip[k];
+        }
+        yt[m0 + t] = y;
+      }
+    }
+  }
+  T x = 0;
+#pragma unroll
+  for (int m0 = HMAX - 8; m0 >= 0; m0 -= 8) {
+    if (m0 < nt) {
+#pragma unroll
+      for (int t = 7; t >= 0; --t)
+        if (m0 + t < nt) x = yt[m0 + t] + x * ip[k1 + m0 + t];
+    }
+  }
+#pragma unroll
+  for (int q = XV - 1; q >= 0; --q)
+    if (q < ns) {
+      const int k = k0 + q;
+      x = yr[q] + x * ip[k];
+      out[(size_t)k * P] = x;
+    }
+}
+
 // periodic segment solve; in(j), store(j, x) address the line
 template <class T, class In, class Out>
 __device__ inline void periodic_segment(int n, int j0, int j1, int H, T rho, T ir, In in, Out store) {
@@ -1738,6 +1827,19 @@ void launch_af_x(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   {
     const T* tab;
     if constexpr (sizeof(T) == 8) tab = (const T*)f.ipt; else tab = (const T*)f.iptf;
+    // afx_planes selects the x segment: 16 or 32 planes per thread in registers,
+    // otherwise XS planes per warp staged in shared memory
+    if (c.afx_planes == 16 || c.afx_planes == 32) {
+      const int xv = c.afx_planes;
+      const dim3 grid((P + 255) / 256, (c.nx + xv - 1) / xv, 3);
+      if (xv == 16)
+        k_af_xv<T, 16><<<grid, 256, 0, s>>>(c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1],
+                                            f.e[2], f.dout[0], f.dout[1], f.dout[2]);
+      else
+        k_af_xv<T, 32><<<grid, 256, 0, s>>>(c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1],
+                                            f.e[2], f.dout[0], f.dout[1], f.dout[2]);
+      return;
+    }
     k_af_xr<T><<<dim3((P + 31) / 32, (c.nx + XS - 1) / XS, 3), 32, 0, s>>>(
         c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2], f.dout[0], f.dout[1],
         f.dout[2]);
