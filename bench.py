@@ -39,10 +39,10 @@ FALLBACK_HBM_GBS = 6800.0
 # and the outputs it must write, with perfect on-chip reuse inside the kernel.
 FIELD_PASSES = {
     "rhs": 13, "af_x": 6, "af_yz": 9, "mass_div": 4,
-    "dht_y": 2, "dht_z": 2, "poisson_x": 3, "project": 9,
+    "dht2d": 2, "poisson_x": 3, "project": 9,
 }
 # launches of each stage per step
-PER_STEP = {"rhs": 1, "af_x": 1, "af_yz": 1, "mass_div": 1, "dht_y": 2, "dht_z": 2,
+PER_STEP = {"rhs": 1, "af_x": 1, "af_yz": 1, "mass_div": 1, "dht2d": 2,
             "poisson_x": 1, "project": 1, "ib": 1, "flag": 1, "outflow": 1}
 # The method's unfused field passes per step (explicit stage 13, three
 # implicit factors 21, mass fix and divergence 4, pressure solve 10,
@@ -269,8 +269,8 @@ def stage_roofline(wl, precision, peak_gbs, peak_kind):
     elem = 4 if precision == binding.IBM_FP32 else 8
     cells = (wl.nx + 1) * wl.ny * wl.nz
     stages = {}
-    for name in ("rhs", "outflow", "af_x", "af_yz", "ib", "flag", "mass_div", "dht_y",
-                 "dht_z", "poisson_x", "project"):
+    for name in ("rhs", "outflow", "af_x", "af_yz", "ib", "flag", "mass_div", "dht2d",
+                 "poisson_x", "project"):
         t.time_stage(name, 2)
         stages[name] = t.time_stage(name, 10)
     t.close()

@@ -80,6 +80,10 @@ extern "C" {
                                    multiple of 32 (FP32) or 16 (FP64); otherwise
                                    the step runs AF_Y and AF_Z and this stage
                                    launches nothing)                          */
+#define IBM_STAGE_DHT_2D    14  /* both transforms of every x plane in one pass
+                                   (used by the pressure solve when ny = nz =
+                                   256; otherwise the solve runs DHT_Y and
+                                   DHT_Z and this stage launches nothing)     */
 
 /* field selectors for ibm_get_field / ibm_set_field */
 #define IBM_FIELD_U 0

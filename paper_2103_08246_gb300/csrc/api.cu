@@ -715,6 +715,7 @@ void launch_stage(ibm_state* s, int stage) {
     case IBM_STAGE_PROJECT: launch_project_only(c, f, cur, false, st); break;
     case IBM_STAGE_POISSON: solve_poisson<T>(s, st); break;
     case IBM_STAGE_AF_YZ: (void)launch_af_yz(c, f, cur, st); break;
+    case IBM_STAGE_DHT_2D: (void)launch_dht2d(c, f, st); break;
     default: break;
   }
 }
@@ -866,7 +867,7 @@ int ibm_stats(ibm_state* s, ibm_stats_t* out) {
 }
 
 int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
-  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_AF_YZ) return IBM_EINVAL;
+  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_DHT_2D) return IBM_EINVAL;
   cudaStream_t st = s->stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

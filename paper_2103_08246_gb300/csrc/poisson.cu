@@ -23,12 +23,16 @@
 // field, which mostly stays in L2 between the two sweeps.
 // Mode (0, 0) is singular: phi_0 = 0 is pinned, then the line mean removed,
 // which sets mean(phi) = 0.
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 #include "async_copy.cuh"
 #include "solver.h"
 
 namespace ibm {
+
+namespace cg = cooperative_groups;
 
 __device__ inline int bitrev(int x, int logn) { return (int)(__brev((unsigned)x) >> (32 - logn)); }
 
@@ -284,6 +288,90 @@ __global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, 
 // normalisation). One thread per mode walks x (coalesced across modes); the
 // loads of the next PF planes are issued ahead of the recursion so that each
 // thread keeps 2 PF independent loads in flight.
+// Both transforms of one 256 x 256 x-plane in a single pass: a cluster of 8
+// CTAs holds the plane as eight 256 x 32 column tiles (CTA q: columns
+// 32 q .. 32 q + 31). Each CTA transforms its 32 columns along y (two per
+// warp per round), the cluster synchronises, then CTA q transforms rows
+// 32 q .. 32 q + 31 along z (two per warp per round), gathering each row's
+// eight 32-value pieces from the eight tiles through distributed shared
+// memory and storing the finished rows straight to global memory. A last
+// cluster barrier keeps every tile alive until all its readers are done.
+// The plane is read and written once.
+constexpr int DHT2D_CLUSTER = 8;
+constexpr int DHT2D_THREADS = 256;
+template <class T>
+__global__ void __cluster_dims__(DHT2D_CLUSTER, 1, 1) __launch_bounds__(DHT2D_THREADS)
+k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Cx<T> tw[256];
+  T* s = reinterpret_cast<T*>(smem_raw);   // [256][33], element (r, c) at ytile(r, c)
+  cg::cluster_group cl = cg::this_cluster();
+  const int q = (int)cl.block_rank();
+  const int plane = blockIdx.x / DHT2D_CLUSTER;
+  T* pbase = data + (size_t)plane * 256 * 256;
+  {
+    const T* base = pbase + 32 * q;
+    constexpr int PER = 256 * 32 / DHT2D_THREADS;   // 32 values per thread
+    T buf[PER];
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = threadIdx.x + t * DHT2D_THREADS;
+      buf[t] = base[(size_t)(e >> 5) * 256 + (e & 31)];
+    }
+#pragma unroll
+    for (int t = 0; t < PER; ++t) {
+      const int e = threadIdx.x + t * DHT2D_THREADS;
+      s[ytile(e >> 5, e & 31)] = buf[t];
+    }
+  }
+  load_twiddles(tw, twy);   // includes __syncthreads
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int qb = (int)(__brev((unsigned)l) >> 27);
+  constexpr int NW = DHT2D_THREADS / 32;
+  // y: column pairs (2 cp, 2 cp + 1) of this tile
+  for (int cp = w; cp < 16; cp += NW) {
+    Cx<T> x[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = {s[ytile(l + 32 * m, 2 * cp)], s[ytile(l + 32 * m, 2 * cp + 1)]};
+    T ha[8], hb[8];
+    warp_hartley256(x, tw, ha, hb);
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      s[ytile(p + 8 * qb, 2 * cp)] = ha[p];
+      s[ytile(p + 8 * qb, 2 * cp + 1)] = hb[p];
+    }
+  }
+  cl.sync();   // every tile transformed along y (ny = nz: the same twiddles serve z)
+  // z: row pairs of this CTA; value (r, k) lives in tile k / 32 at column k % 32
+  for (int rp = w; rp < 16; rp += NW) {
+    const int r0 = 32 * q + 2 * rp;
+    Cx<T> x[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const T* t = cl.map_shared_rank(s, m);
+      x[m] = {t[ytile(r0, l)], t[ytile(r0 + 1, l)]};
+    }
+    T ha[8], hb[8];
+    warp_hartley256(x, tw, ha, hb);
+    // lane l holds outputs 8 qb .. 8 qb + 7 of both rows: 16-byte stores
+    T* a = pbase + (size_t)r0 * 256 + 8 * qb;
+    T* b = a + 256;
+    if constexpr (sizeof(T) == 4) {
+      reinterpret_cast<float4*>(a)[0] = make_float4(ha[0], ha[1], ha[2], ha[3]);
+      reinterpret_cast<float4*>(a)[1] = make_float4(ha[4], ha[5], ha[6], ha[7]);
+      reinterpret_cast<float4*>(b)[0] = make_float4(hb[0], hb[1], hb[2], hb[3]);
+      reinterpret_cast<float4*>(b)[1] = make_float4(hb[4], hb[5], hb[6], hb[7]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        reinterpret_cast<double2*>(a)[t] = make_double2(ha[2 * t], ha[2 * t + 1]);
+        reinterpret_cast<double2*>(b)[t] = make_double2(hb[2 * t], hb[2 * t + 1]);
+      }
+    }
+  }
+  cl.sync();   // no tile is released while another CTA may still read it
+}
+
 constexpr int PF = 16;
 __host__ __device__ inline size_t ptab_plane(const Consts& c) {
   return (size_t)(c.ny / 2 + 1) * (c.nz / 2 + 1);
@@ -425,7 +513,20 @@ void launch_poisson_x(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 }
 
 template <class T>
+bool launch_dht2d(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+  if (c.ny != 256 || c.nz != 256) return false;
+  const size_t sh = (size_t)256 * 33 * sizeof(T);
+  k_dht2d_256<T><<<c.nx * DHT2D_CLUSTER, DHT2D_THREADS, sh, s>>>(f.phi, f.tw_y);
+  return true;
+}
+
+template <class T>
 void launch_poisson(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+  if (launch_dht2d(c, f, s)) {
+    launch_poisson_x(c, f, s);
+    launch_dht2d(c, f, s);
+    return;
+  }
   launch_dht_y(c, f, s);
   launch_dht_z(c, f, s);
   launch_poisson_x(c, f, s);
@@ -442,6 +543,8 @@ void launch_poisson_table(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 }
 
 template void launch_poisson<double>(const Consts&, const Fields<double>&, cudaStream_t);
+template bool launch_dht2d<double>(const Consts&, const Fields<double>&, cudaStream_t);
+template bool launch_dht2d<float>(const Consts&, const Fields<float>&, cudaStream_t);
 template void launch_dht_y<double>(const Consts&, const Fields<double>&, cudaStream_t);
 template void launch_dht_y<float>(const Consts&, const Fields<float>&, cudaStream_t);
 template void launch_dht_z<double>(const Consts&, const Fields<double>&, cudaStream_t);
@@ -456,6 +559,8 @@ template void launch_poisson_table<float>(const Consts&, const Fields<float>&, c
 
 // opt in to large dynamic shared memory for the transform kernels
 void poisson_set_attributes() {
+  cudaFuncSetAttribute(k_dht2d_256<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_dht2d_256<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_dht_y256<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_dht_y256<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_dht<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

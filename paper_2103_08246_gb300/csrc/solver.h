@@ -70,6 +70,7 @@ template <class T> void launch_af_x(const Consts& c, const Fields<T>& f, int cur
 template <class T> void launch_af_y(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_af_z(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> bool launch_af_yz(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> bool launch_dht2d(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_mass(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 template <class T> void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
