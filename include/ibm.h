@@ -133,9 +133,10 @@ typedef struct {
   const double* init_w;
   /* Tile parameters (0: defaults). rhs_planes: x planes per block of the
    * streamed explicit stage [16], in [2, 256]; afx_planes: x planes per
-   * segment of the implicit x factor [64]: 16 or 32 hold a segment in each
-   * thread's registers, other values in [8, 256] select 64-plane segments
-   * staged in shared memory; rhs_stages: depth of the
+   * segment of the implicit x factor [64]: 16 or 24 hold a segment in each
+   * thread's registers; otherwise values up to 40 select 32-plane and larger
+   * values 64-plane segments staged in shared memory (range [8, 256]);
+   * rhs_stages: depth of the
    * explicit stage's shared-memory ring in x planes [as many as 210 KB
    * holds, at most 8], in [4, 8] (fewer than asked if they do not fit).
    * Results do not depend on them; the package's autotuner picks them per

@@ -18,7 +18,7 @@ from . import binding
 CANDIDATES = {
     "rhs_planes": (8, 16, 32, 64),
     "rhs_stages": (4, 5, 6, 8),
-    "afx_planes": (16, 32, 64),
+    "afx_planes": (16, 32, 64),   # 16: register segments; 32, 64: shared-memory segments
 }
 STAGE_OF = {"rhs_planes": "rhs", "rhs_stages": "rhs", "afx_planes": "af_x"}
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tile_cache.json")

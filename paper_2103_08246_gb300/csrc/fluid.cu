@@ -803,8 +803,7 @@ k_af_x(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
 // x factor by the LU recursions on shared-memory-staged planes: one warp per
 // 32 consecutive (y, z) columns and XS planes (+ warm-up halos); lanes walk
 // their columns (bank-conflict free), loads and stores are 128-byte rows.
-constexpr int XS = 64;
-template <class T>
+template <class T, int XS>
 __global__ void __launch_bounds__(32)
 k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
         const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
@@ -1827,22 +1826,28 @@ void launch_af_x(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   {
     const T* tab;
     if constexpr (sizeof(T) == 8) tab = (const T*)f.ipt; else tab = (const T*)f.iptf;
-    // afx_planes selects the x segment: 16 or 32 planes per thread in registers,
-    // otherwise XS planes per warp staged in shared memory
-    if (c.afx_planes == 16 || c.afx_planes == 32) {
+    // afx_planes selects the x segment: 16 or 24 planes per thread in registers,
+    if (c.afx_planes == 16 || c.afx_planes == 24) {
       const int xv = c.afx_planes;
       const dim3 grid((P + 255) / 256, (c.nx + xv - 1) / xv, 3);
       if (xv == 16)
         k_af_xv<T, 16><<<grid, 256, 0, s>>>(c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1],
                                             f.e[2], f.dout[0], f.dout[1], f.dout[2]);
       else
-        k_af_xv<T, 32><<<grid, 256, 0, s>>>(c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1],
+        k_af_xv<T, 24><<<grid, 256, 0, s>>>(c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1],
                                             f.e[2], f.dout[0], f.dout[1], f.dout[2]);
       return;
     }
-    k_af_xr<T><<<dim3((P + 31) / 32, (c.nx + XS - 1) / XS, 3), 32, 0, s>>>(
-        c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2], f.dout[0], f.dout[1],
-        f.dout[2]);
+    // otherwise segments of 32 or 64 planes staged in shared memory by warps
+    if (c.afx_planes <= 40) {
+      k_af_xr<T, 32><<<dim3((P + 31) / 32, (c.nx + 31) / 32, 3), 32, 0, s>>>(
+          c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2], f.dout[0], f.dout[1],
+          f.dout[2]);
+    } else {
+      k_af_xr<T, 64><<<dim3((P + 31) / 32, (c.nx + 63) / 64, 3), 32, 0, s>>>(
+          c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2], f.dout[0], f.dout[1],
+          f.dout[2]);
+    }
     (void)cur;
     return;
   }

@@ -284,10 +284,6 @@ __global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, 
   }
 }
 
-// Thomas solve along x per mode; rhs scaled by h^2 / (ny nz) (Hartley
-// normalisation). One thread per mode walks x (coalesced across modes); the
-// loads of the next PF planes are issued ahead of the recursion so that each
-// thread keeps 2 PF independent loads in flight.
 // Both transforms of one 256 x 256 x-plane in a single pass: a cluster of 8
 // CTAs holds the plane as eight 256 x 32 column tiles (CTA q: columns
 // 32 q .. 32 q + 31). Each CTA transforms its 32 columns along y (two per
@@ -372,6 +368,11 @@ k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
   cl.sync();   // no tile is released while another CTA may still read it
 }
 
+// Thomas solve along x per mode; rhs scaled by h^2 / (ny nz) (Hartley
+// normalisation). One thread per mode walks x (coalesced across modes) in
+// chunks of PF planes; the loads of the next chunk (right-hand side and
+// inverse pivots) are issued before the current chunk's recursion, so each
+// thread keeps up to 4 PF independent loads in flight.
 constexpr int PF = 16;
 __host__ __device__ inline size_t ptab_plane(const Consts& c) {
   return (size_t)(c.ny / 2 + 1) * (c.nz / 2 + 1);
@@ -392,49 +393,89 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
   const T* iv = tab + ptab_index(c, jk);
   const size_t PT = ptab_plane(c);
   const bool zero_mode = (jk == 0);
+  // forward elimination, PF planes per chunk; the next chunk's loads are
+  // issued before the current chunk's recursion (two chunks in flight)
   T y = 0;
-  int i = 0;
-  for (; i + PF <= nx; i += PF) {
+  const int nfull = nx / PF;
+  {
     T rd[PF], rt[PF];
+    if (nfull > 0) {
 #pragma unroll
-    for (int q = 0; q < PF; ++q) {
-      rd[q] = d[(size_t)(i + q) * P];
-      rt[q] = iv[(size_t)(i + q) * PT];
+      for (int q = 0; q < PF; ++q) {
+        rd[q] = d[(size_t)q * P];
+        rt[q] = iv[(size_t)q * PT];
+      }
     }
+    for (int ch = 0; ch < nfull; ++ch) {
+      const int i = ch * PF;
+      T nd[PF], nt[PF];
+      if (ch + 1 < nfull) {
 #pragma unroll
-    for (int q = 0; q < PF; ++q) {
-      const T rhs = (zero_mode && i + q == 0) ? (T)0 : rd[q] * scale;
-      y = (rhs - y) * rt[q];
-      d[(size_t)(i + q) * P] = y;
+        for (int q = 0; q < PF; ++q) {
+          nd[q] = d[(size_t)(i + PF + q) * P];
+          nt[q] = iv[(size_t)(i + PF + q) * PT];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        const T rhs = (zero_mode && i + q == 0) ? (T)0 : rd[q] * scale;
+        y = (rhs - y) * rt[q];
+        d[(size_t)(i + q) * P] = y;
+      }
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        rd[q] = nd[q];
+        rt[q] = nt[q];
+      }
     }
   }
-  for (; i < nx; ++i) {
+  for (int i = nfull * PF; i < nx; ++i) {
     const size_t o = (size_t)i * P;
     const T rhs = (zero_mode && i == 0) ? (T)0 : d[o] * scale;
     y = (rhs - y) * iv[(size_t)i * PT];
     d[o] = y;
   }
+  // back substitution from the top, the same chunking (the partial chunk first)
   T x = y;  // x_{nx-1} = dp_{nx-1}
-  i = nx - 2;
-  for (; i - PF + 1 >= 0; i -= PF) {
-    T rd[PF], rt[PF];
-#pragma unroll
-    for (int q = 0; q < PF; ++q) {
-      rd[q] = d[(size_t)(i - q) * P];
-      rt[q] = iv[(size_t)(i - q) * PT];
-    }
-#pragma unroll
-    for (int q = 0; q < PF; ++q) {
-      const T cp = (zero_mode && i - q == 0) ? (T)0 : rt[q];
-      x = rd[q] - cp * x;
-      d[(size_t)(i - q) * P] = x;
-    }
-  }
-  for (; i >= 0; --i) {
+  int i = nx - 2;
+  const int rem = (nx - 1) % PF;
+  for (; i > nx - 2 - rem; --i) {
     const size_t o = (size_t)i * P;
     const T cp = (zero_mode && i == 0) ? (T)0 : iv[(size_t)i * PT];
     x = d[o] - cp * x;
     d[o] = x;
+  }
+  {
+    const int nch = (i + 1) / PF;   // full chunks below: planes i, i-1, ..., 0
+    T rd[PF], rt[PF];
+    if (nch > 0) {
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        rd[q] = d[(size_t)(i - q) * P];
+        rt[q] = iv[(size_t)(i - q) * PT];
+      }
+    }
+    for (int ch = 0; ch < nch; ++ch, i -= PF) {
+      T nd[PF], nt[PF];
+      if (ch + 1 < nch) {
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+          nd[q] = d[(size_t)(i - PF - q) * P];
+          nt[q] = iv[(size_t)(i - PF - q) * PT];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        const T cp = (zero_mode && i - q == 0) ? (T)0 : rt[q];
+        x = rd[q] - cp * x;
+        d[(size_t)(i - q) * P] = x;
+      }
+#pragma unroll
+      for (int q = 0; q < PF; ++q) {
+        rd[q] = nd[q];
+        rt[q] = nt[q];
+      }
+    }
   }
   if (zero_mode) {
     double s = 0.0;
