@@ -217,9 +217,16 @@ static void gemm(const GemmArgs& g, int batch, cudaStream_t s) {
   k_gemm_tf32x3<<<dim3((g.N + GBN - 1) / GBN, (g.M + GBM - 1) / GBM, batch), 256, sh, s>>>(g);
 }
 
-// 2-D Hartley transform of every x plane: out = H_y in H_z (tmp: scratch)
+// 2-D Hartley transform of every x plane: out = H_y in H_z (tmp: scratch).
+// 256 x 256 planes run on the tcgen05 tensor cores as two passes
+// out = ((in H)^T H)^T; other shapes on the mma.sync kernel above.
 static void transform2d(const Consts& c, const float* Hy, const float* Hz, const float* in,
-                        float* tmp, float* out, cudaStream_t s) {
+                        float* tmp, float* out, int* error, cudaStream_t s) {
+  if (c.ny == 256 && c.nz == 256) {
+    tc_rows_times_h_t(in, Hz, tmp, c.nx, error, s);
+    tc_rows_times_h_t(tmp, Hy, out, c.nx, error, s);
+    return;
+  }
   const long long P = (long long)c.ny * c.nz;
   GemmArgs a{in, Hz, tmp, c.nx * c.ny, c.nz, c.nz, c.nz, c.nz, c.nz, 0, 0, 0};
   gemm(a, 1, s);
@@ -236,21 +243,23 @@ void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* 
   float* t0 = f.e[0];
   float* x0 = f.e[1];
   float* t1 = f.e[2];
+  int* err = &f.prm->error;
   // first solve: x0 = L^-1 D
-  transform2d(c, Hy, Hz, D, t0, x0, s);
+  transform2d(c, Hy, Hz, D, t0, x0, err, s);
   launch_poisson_x_on(c, f, x0, s);
-  transform2d(c, Hy, Hz, x0, t0, x0, s);
+  transform2d(c, Hy, Hz, x0, t0, x0, err, s);
   // FP64 residual and correction: t1 = L^-1 (D - L x0)
   const int nb = 152 * 8;
   k_residual64<<<nb, 256, 0, s>>>(c, D, x0, t1);
-  transform2d(c, Hy, Hz, t1, t0, t1, s);
+  transform2d(c, Hy, Hz, t1, t0, t1, err, s);
   launch_poisson_x_on(c, f, t1, s);
-  transform2d(c, Hy, Hz, t1, t0, t1, s);
+  transform2d(c, Hy, Hz, t1, t0, t1, err, s);
   k_add<<<nb, 256, 0, s>>>(n, x0, t1, f.phi);
 }
 
 void mixed_set_attributes() {
   cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  tc_gemm_set_attributes();
 }
 
 // Hartley matrices in FP32 (entries from FP64 cos/sin of 2 pi j k / n, jk mod n)

@@ -79,6 +79,10 @@ template <class T> void launch_project(const Consts& c, const Fields<T>& f, int 
 template <class T>
 int partial_count(const Consts& c);
 size_t poisson_table_size(const Consts& c);
+// tensor-core (tcgen05) split-TF32 transform pass: out = (X H)^T per 256 x 256 plane
+void tc_rows_times_h_t(const float* X, const float* H, float* out, int planes, int* error,
+                       cudaStream_t s);
+void tc_gemm_set_attributes();
 int outflow_blocks(const Consts& c);
 void fluid_set_attributes();
 template <class T> void launch_stats(const Consts& c, const Fields<T>& f, int cur, double* out, cudaStream_t s);

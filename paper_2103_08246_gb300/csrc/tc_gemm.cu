@@ -1,0 +1,268 @@
+// Split-TF32 GEMM on the fifth-generation tensor cores (tcgen05, sm_103a) for
+// the Hartley transforms of the mixed-precision pressure solve: for every
+// 256 x 256 plane X (rows of 256 contiguous values) it computes
+//   out = (X H)^T,   H = H^T the 256-point Hartley matrix,
+// with FP32 operands rounded as a ~ a_hi + a_lo, a_hi = tf32(a),
+// a_lo = tf32(a - a_hi), and a_hi b_hi + a_hi b_lo + a_lo b_hi accumulated in
+// FP32 in tensor memory. Applied twice, ((X H)^T H)^T = H X H: the 2-D
+// transform of the plane, with both GEMMs reading K-major rows.
+//
+// One CTA (4 warps) computes 128 rows x 256 columns of X H over K in blocks
+// of 32:
+//  * all threads load the next K block (A: 128 x 32, B: 256 x 32) from global
+//    memory into registers while the tensor core works on the current one,
+//    split it into hi / lo parts and store both into shared memory in the
+//    K-major "core matrix" layout (8 rows x 16 bytes per 128-byte core
+//    matrix; core matrices adjacent in K are 128 bytes apart, adjacent in
+//    M / N 1024 bytes apart);
+//  * one thread issues the 4 x 3 tcgen05.mma (M = 128, N = 256, K = 8 each)
+//    of the block and commits them to the stage's mbarrier, which the
+//    loaders wait on before they overwrite that stage (two stages);
+//  * the accumulator (128 lanes x 256 FP32 columns of tensor memory) is read
+//    back with tcgen05.ld, each warp its 32 lanes (rows), and stored
+//    transposed into the plane: for every column the warp's 32 rows are 32
+//    consecutive floats.
+// Every mbarrier wait is bounded; on expiry the kernel sets the error flag,
+// still waits (bounded) for its own tensor-core work, releases its tensor
+// memory and returns.
+#include <cstdint>
+
+#include "async_copy.cuh"
+#include "solver.h"
+
+namespace ibm {
+
+namespace {
+
+constexpr int TC_M = 128, TC_N = 256, TC_KB = 32;
+constexpr int TC_THREADS = 128;
+constexpr int TC_TMEM_COLS = 256;
+constexpr uint32_t A_TILE = TC_M * TC_KB * 4;   // bytes of one A part (hi or lo)
+constexpr uint32_t B_TILE = TC_N * TC_KB * 4;
+constexpr uint32_t STAGE = 2 * A_TILE + 2 * B_TILE;   // A_hi, A_lo, B_hi, B_lo
+constexpr int TC_STAGES = 2;
+
+// byte offset of element (row, k) of a K-major tile with TC_KB columns
+__device__ inline uint32_t kmajor_off(int row, int k) {
+  return (uint32_t)(((row >> 3) * (TC_KB / 4) + (k >> 2)) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ inline uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle
+__device__ inline uint64_t smem_desc(uint32_t saddr) {
+  constexpr uint64_t LBO = 128, SBO = 1024;
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version of this architecture
+  return d;                 // base offset 0, swizzle none
+}
+
+// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  return (1u << 4)                      // D format F32
+         | (2u << 7)                    // A format TF32
+         | (2u << 10)                   // B format TF32
+         | ((uint32_t)(TC_N >> 3) << 17)
+         | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ inline void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                              uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ inline void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ inline void tc_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+struct TcArgs {
+  const float* X;   // rows of 256 values (M rows, planes of 256 rows)
+  const float* H;   // 256 x 256, symmetric
+  float* out;       // per plane: out[n][r] = sum_k X[r][k] H[k][n]
+  int M;
+  int* error;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  __shared__ uint64_t done[TC_STAGES];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.x * TC_M;
+  const float* A = g.X;
+  const float* B = g.H;
+  constexpr int LD = 256;
+  const uint32_t sbase = smem_u32(tsm);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) mbar_init(&done[s], 1);
+    fence_mbar_init();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  // register staging of one K block: A 8 float4, B 16 float4 per thread.
+  // float4 number e holds row (e >> 6) * 8 + (e & 7), columns 4 ((e >> 3) & 7)
+  // .. + 3: the 8 lanes of a shared-store phase fill one 128-byte core matrix.
+  auto row_of = [](int e) { return (e >> 6) * 8 + (e & 7); };
+  auto col_of = [](int e) { return ((e >> 3) & 7) * 4; };
+  float4 ra[8], rb[16];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + t * TC_THREADS;   // 1024 float4 of A (128 rows x 32)
+      ra[t] = *reinterpret_cast<const float4*>(A + (size_t)(m0 + row_of(e)) * LD + k0 + col_of(e));
+    }
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const int e = tid + t * TC_THREADS;   // 2048 float4 of B (256 rows n x 32)
+      rb[t] = *reinterpret_cast<const float4*>(B + (size_t)row_of(e) * LD + k0 + col_of(e));
+    }
+  };
+  auto split_store = [&](unsigned char* hi_tile, unsigned char* lo_tile, int row, int c4,
+                         const float4& v) {
+    const float x[4] = {v.x, v.y, v.z, v.w};
+    uint4 hi, lo;
+    uint32_t* ph = &hi.x;
+    uint32_t* pl = &lo.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ph[q] = tf32_bits(x[q]);
+      pl[q] = tf32_bits(x[q] - __uint_as_float(ph[q]));
+    }
+    const uint32_t off = kmajor_off(row, c4);
+    *reinterpret_cast<uint4*>(hi_tile + off) = hi;
+    *reinterpret_cast<uint4*>(lo_tile + off) = lo;
+  };
+  auto put = [&](unsigned char* st) {
+    unsigned char* ah = st;
+    unsigned char* al = st + A_TILE;
+    unsigned char* bh = st + 2 * A_TILE;
+    unsigned char* bl = st + 2 * A_TILE + B_TILE;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = tid + t * TC_THREADS;
+      split_store(ah, al, row_of(e), col_of(e), ra[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const int e = tid + t * TC_THREADS;
+      split_store(bh, bl, row_of(e), col_of(e), rb[t]);
+    }
+    // make the generic-proxy stores visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  };
+  constexpr uint32_t idesc = tc_idesc();
+  auto issue = [&](int s, bool first) {
+    const uint32_t st = sbase + (uint32_t)s * STAGE;
+    const uint32_t ah = st, al = st + A_TILE, bh = st + 2 * A_TILE, bl = st + 2 * A_TILE + B_TILE;
+#pragma unroll
+    for (int kk = 0; kk < TC_KB / 8; ++kk) {
+      const uint32_t ko = (uint32_t)kk * 256;   // two core matrices (K = 8) per step
+      tc_mma(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, (first && kk == 0) ? 0u : 1u);
+      tc_mma(tmem, smem_desc(ah + ko), smem_desc(bl + ko), idesc, 1u);
+      tc_mma(tmem, smem_desc(al + ko), smem_desc(bh + ko), idesc, 1u);
+    }
+    tc_commit(&done[s]);
+  };
+
+  const int nk = 256 / TC_KB;
+  bool ok = true;
+  uint32_t uses[TC_STAGES] = {0, 0};   // commits made on each stage's barrier
+  load(0);
+  for (int kb = 0; kb < nk; ++kb) {
+    const int s = kb % TC_STAGES;
+    // the stage's previous MMAs (block kb - 2) must be done before it is overwritten
+    if (uses[s] > 0) ok = mbar_wait(&done[s], (uses[s] - 1) & 1) && ok;
+    put(tsm + (size_t)s * STAGE);
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      issue(s, kb == 0);
+    }
+    ++uses[s];
+    if (kb + 1 < nk) load((kb + 1) * TC_KB);
+  }
+  // all MMAs complete: the last commit of each used stage
+  for (int s = 0; s < TC_STAGES; ++s)
+    if (uses[s] > 0) ok = mbar_wait(&done[s], (uses[s] - 1) & 1) && ok;
+  // one decision for the whole CTA: the tensor-memory loads below are warp-collective
+  ok = __syncthreads_and(ok) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!ok && tid == 0) atomicOr(g.error, ERR_TIMEOUT);
+  if (ok) {
+    // warp w owns accumulator lanes (rows) 32 w .. 32 w + 31; row m = plane * 256 + r
+    const int m = m0 + warp * 32 + (tid & 31);
+    float* plane = g.out + (size_t)(m >> 8) * 65536 + (m & 255);
+#pragma unroll 1
+    for (int c0 = 0; c0 < TC_N; c0 += 32) {
+      float v[32];
+      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) plane[(size_t)(c0 + q) * 256] = v[q];
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                 : "memory");
+}
+
+}  // namespace
+
+constexpr size_t TC_SMEM = (size_t)TC_STAGES * STAGE;
+
+// out = (X H)^T for each of the `planes` 256 x 256 planes of X (rows of 256
+// contiguous values); X, H, out 16-byte aligned, out distinct from X.
+// error: device flag that receives ERR_TIMEOUT if a bounded wait runs out.
+void tc_rows_times_h_t(const float* X, const float* H, float* out, int planes, int* error,
+                       cudaStream_t s) {
+  TcArgs g{X, H, out, planes * 256, error};
+  k_gemm_tc_tf32x3<<<planes * 256 / TC_M, TC_THREADS, TC_SMEM, s>>>(g);
+}
+
+void tc_gemm_set_attributes() {
+  cudaFuncSetAttribute(k_gemm_tc_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+}
+
+}  // namespace ibm

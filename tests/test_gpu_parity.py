@@ -96,12 +96,13 @@ def test_fp64_small_cases(lib, case):
     gpu.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
 def test_wide_transverse_grid(lib, precision):
-    """256 x 256 transverse planes (the size the register-resident transforms
-    and the streamed kernels are specialised for), 16 x-planes, 3 steps."""
+    """256 x 256 transverse planes (the size the register-resident and
+    cluster transforms, the tensor-core (tcgen05) transform GEMMs and the
+    streamed kernels are specialised for), 16 x-planes, 3 steps."""
     from paper_2103_08246_gb300 import binding
-    prec = binding.IBM_FP64 if precision == "fp64" else binding.IBM_FP32
+    prec = {"fp64": binding.IBM_FP64, "fp32": binding.IBM_FP32, "mixed": binding.IBM_MIXED}[precision]
     wl = _small(shape=(16, 256, 256))
     gpu, ora = _run(wl, prec, 3)
     if prec == binding.IBM_FP64:
