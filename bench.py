@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run this many FP32 production steps (for ncu) and exit")
-    ap.add_argument("--profile-precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--profile-precision", choices=["fp32", "fp64", "mixed"], default="fp32")
     ap.add_argument("--profile-small", action="store_true",
                     help="profile the 256x256x256 half-length case (flag at x = 2)")
     return ap.parse_args()
@@ -76,7 +76,8 @@ def run_profile(args):
     wl = inputs.PRODUCTION
     if args.profile_small:
         wl = wl.replace(name="half-256x256x256", nx=256, lx=4.0, flag_x_le=2.0)
-    prec = binding.IBM_FP32 if args.profile_precision == "fp32" else binding.IBM_FP64
+    prec = {"fp32": binding.IBM_FP32, "fp64": binding.IBM_FP64,
+            "mixed": binding.IBM_MIXED}[args.profile_precision]
     s = binding.Solver(wl, prec, noise=inputs.initial_noise(wl))
     s.step(args.profile_steps)
     torch.cuda.synchronize()

@@ -170,22 +170,49 @@ __device__ inline T shfl(T v, int lane) { return __shfl_sync(0xffffffffu, v, lan
 template <class T>
 __device__ inline T shfl_x(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 
-// tw: W_256^t = (cos, -sin)(2 pi t / 256), t = 0..255, in shared memory
+// Twiddles a lane needs in every transform, read once from the shared table
+// tw (W_256^t = (cos, -sin)(2 pi t / 256), t = 0..255): W^{l p} after the
+// 8-point DFTs, and per cross-lane stage (distance d) a sign and a factor
+// that turn both halves of the butterfly into one expression,
+//   lower lane: x + o = (o + x) * 1,   upper lane: (o - x) * W.
 template <class T>
-__device__ inline void warp_hartley256(Cx<T> (&x)[8], const Cx<T>* tw, T (&ha)[8], T (&hb)[8]) {
+struct LaneTw {
+  Cx<T> tp[8];
+  Cx<T> ws[5];
+  T sg[5];
+};
+
+template <class T>
+__device__ inline LaneTw<T> lane_twiddles(const Cx<T>* tw) {
+  LaneTw<T> lt;
+  const int l = threadIdx.x & 31;
+#pragma unroll
+  for (int p = 0; p < 8; ++p) lt.tp[p] = tw[(l * p) & 255];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int d = 16 >> s;
+    const bool upper = (l & d) != 0;
+    lt.ws[s] = upper ? tw[((l & (d - 1)) * (128 / d)) & 255] : Cx<T>{(T)1, (T)0};
+    lt.sg[s] = upper ? (T)-1 : (T)1;
+  }
+  return lt;
+}
+
+template <class T>
+__device__ inline void warp_hartley256(Cx<T> (&x)[8], const LaneTw<T>& lt, T (&ha)[8], T (&hb)[8]) {
   const int l = threadIdx.x & 31;
   dft8(x);
 #pragma unroll
-  for (int p = 1; p < 8; ++p) x[p] = cmul(x[p], tw[(l * p) & 255]);
+  for (int p = 1; p < 8; ++p) x[p] = cmul(x[p], lt.tp[p]);
 #pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) {
-    const bool upper = (l & d) != 0;
-    const Cx<T> w = tw[((l & (d - 1)) * (128 / d)) & 255];
+  for (int s = 0; s < 5; ++s) {
+    const int d = 16 >> s;
+    const T sg = lt.sg[s];
+    const Cx<T> w = lt.ws[s];
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
       const Cx<T> o = {shfl_x(x[p].r, d), shfl_x(x[p].i, d)};
-      if (upper) x[p] = cmul({o.r - x[p].r, o.i - x[p].i}, w);
-      else x[p] = {x[p].r + o.r, x[p].i + o.i};
+      x[p] = cmul({o.r + sg * x[p].r, o.i + sg * x[p].i}, w);
     }
   }
   const int q = (int)(__brev((unsigned)l) >> 27);
@@ -214,6 +241,7 @@ template <class T>
 __global__ void __launch_bounds__(256) k_dht_z256(T* __restrict__ data, int nrows, const T* __restrict__ twg) {
   __shared__ Cx<T> tw[256];
   load_twiddles(tw, twg);
+  const LaneTw<T> lt = lane_twiddles(tw);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int l = threadIdx.x & 31;
   if (2 * warp + 1 >= nrows + 1) return;
@@ -223,7 +251,7 @@ __global__ void __launch_bounds__(256) k_dht_z256(T* __restrict__ data, int nrow
 #pragma unroll
   for (int m = 0; m < 8; ++m) x[m] = {a[l + 32 * m], b[l + 32 * m]};
   T ha[8], hb[8];
-  warp_hartley256(x, tw, ha, hb);
+  warp_hartley256(x, lt, ha, hb);
   // lane l holds outputs 8 q .. 8 q + 7: two (FP32) or four (FP64) 16-byte stores
   const int q = (int)(__brev((unsigned)l) >> 27);
   if constexpr (sizeof(T) == 4) {
@@ -264,12 +292,13 @@ __global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, 
     s[ytile(r, c)] = base[(size_t)r * nz + c];
   }
   load_twiddles(tw, twg);   // includes __syncthreads
+  const LaneTw<T> lt = lane_twiddles(tw);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   Cx<T> x[8];
 #pragma unroll
   for (int m = 0; m < 8; ++m) x[m] = {s[ytile(l + 32 * m, 2 * w)], s[ytile(l + 32 * m, 2 * w + 1)]};
   T ha[8], hb[8];
-  warp_hartley256(x, tw, ha, hb);
+  warp_hartley256(x, lt, ha, hb);
   __syncthreads();
   const int q = (int)(__brev((unsigned)l) >> 27);
 #pragma unroll
@@ -321,6 +350,7 @@ k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
     }
   }
   load_twiddles(tw, twy);   // includes __syncthreads
+  const LaneTw<T> lt = lane_twiddles(tw);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int qb = (int)(__brev((unsigned)l) >> 27);
   constexpr int NW = DHT2D_THREADS / 32;
@@ -330,7 +360,7 @@ k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) x[m] = {s[ytile(l + 32 * m, 2 * cp)], s[ytile(l + 32 * m, 2 * cp + 1)]};
     T ha[8], hb[8];
-    warp_hartley256(x, tw, ha, hb);
+    warp_hartley256(x, lt, ha, hb);
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
       s[ytile(p + 8 * qb, 2 * cp)] = ha[p];
@@ -348,7 +378,7 @@ k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
       x[m] = {t[ytile(r0, l)], t[ytile(r0 + 1, l)]};
     }
     T ha[8], hb[8];
-    warp_hartley256(x, tw, ha, hb);
+    warp_hartley256(x, lt, ha, hb);
     // lane l holds outputs 8 qb .. 8 qb + 7 of both rows: 16-byte stores
     T* a = pbase + (size_t)r0 * 256 + 8 * qb;
     T* b = a + 256;
