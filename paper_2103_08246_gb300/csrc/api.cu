@@ -409,6 +409,43 @@ Fields<double>& fields<double>(ibm_state* s) { return s->fd; }
 template <>
 Fields<float>& fields<float>(ibm_state* s) { return s->ff; }
 
+// FP64 host values <-> FP32 device field, converted on the device: the
+// doubles travel through a device staging buffer in chunks
+__global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+       q += (size_t)gridDim.x * blockDim.x)
+    b[q] = (float)a[q];
+}
+__global__ void k_f32_to_f64(const float* __restrict__ a, double* __restrict__ b, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+       q += (size_t)gridDim.x * blockDim.x)
+    b[q] = (double)a[q];
+}
+
+int upload_f32_staged(cudaStream_t st, float* dst, const double* src, size_t n, double* stage,
+                      size_t cap) {
+  for (size_t o = 0; o < n; o += cap) {
+    const size_t m = std::min(cap, n - o);
+    CK(cudaMemcpyAsync(stage, src + o, m * sizeof(double), cudaMemcpyHostToDevice, st));
+    k_f64_to_f32<<<1024, 256, 0, st>>>(stage, dst + o, m);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return IBM_OK;
+}
+
+int download_f32_staged(cudaStream_t st, double* dst, const float* src, size_t n, double* stage,
+                        size_t cap) {
+  for (size_t o = 0; o < n; o += cap) {
+    const size_t m = std::min(cap, n - o);
+    k_f32_to_f64<<<1024, 256, 0, st>>>(src + o, stage, m);
+    CK(cudaMemcpyAsync(dst + o, stage, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return IBM_OK;
+}
+
 template <class T>
 int upload_field(cudaStream_t st, T* dst, const double* src, size_t n) {
   if (std::is_same<T, double>::value) {
@@ -896,6 +933,12 @@ int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
   return IBM_OK;
 }
 
+// doubles that fit in the FP32 scratch buffer e[0] (one field of floats)
+static size_t stage_capacity(const ibm_state* s) {
+  const Consts& c = s->c;
+  return (size_t)(c.nx + 1) * c.ny * c.nz / 2;
+}
+
 static int field_ptr(ibm_state* s, int which, void** ptr, size_t* n) {
   const Consts& c = s->c;
   const size_t NF = (size_t)(c.nx + 1) * c.ny * c.nz, NP = (size_t)c.nx * c.ny * c.nz;
@@ -916,7 +959,9 @@ int ibm_get_field(ibm_state* s, int which, double* host, size_t n) {
   size_t cnt;
   if (field_ptr(s, which, &ptr, &cnt) || cnt != n) return IBM_EINVAL;
   if (s->precision == IBM_FP64) return download_field<double>(s->stream, host, (double*)ptr, n);
-  return download_field<float>(s->stream, host, (float*)ptr, n);
+  // staging: the implicit-factor scratch e[0..2] (contiguous, idle between steps)
+  return download_f32_staged(s->stream, host, (const float*)ptr, n, (double*)s->ff.e[0],
+                             stage_capacity(s));
 }
 
 int ibm_set_field(ibm_state* s, int which, const double* host, size_t n) {
@@ -925,7 +970,7 @@ int ibm_set_field(ibm_state* s, int which, const double* host, size_t n) {
   size_t cnt;
   if (field_ptr(s, which, &ptr, &cnt) || cnt != n) return IBM_EINVAL;
   if (s->precision == IBM_FP64) return upload_field<double>(s->stream, (double*)ptr, host, n);
-  return upload_field<float>(s->stream, (float*)ptr, host, n);
+  return upload_f32_staged(s->stream, (float*)ptr, host, n, (double*)s->ff.e[0], stage_capacity(s));
 }
 
 int ibm_marker_count(const ibm_state* s, size_t* n) {
