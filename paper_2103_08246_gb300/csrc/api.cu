@@ -357,6 +357,7 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   f.n_partial = partial_count<T>(c);
   f.partial = cv.take<double>(f.n_partial);
   f.qpart = cv.take<double>(2 * (size_t)outflow_blocks(c));
+  f.mean00 = cv.take<double>(1);
   f.prm = cv.take<Params>(1);
   s->dstat = cv.take<double>(16);
   Markers& m = s->mk;

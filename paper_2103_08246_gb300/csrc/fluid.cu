@@ -1619,7 +1619,7 @@ k_div_vec(Consts c, const Params* __restrict__ prm, T* __restrict__ u, const T* 
 }
 
 template <class T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_project_vec(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
               const T* __restrict__ va, const T* __restrict__ wa, T* __restrict__ ub,
               T* __restrict__ vb, T* __restrict__ wb, const T* __restrict__ phi, T* __restrict__ p,

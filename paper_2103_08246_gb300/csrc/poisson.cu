@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, 
 constexpr int DHT2D_CLUSTER = 8;
 constexpr int DHT2D_THREADS = 256;
 template <class T>
-__global__ void __cluster_dims__(DHT2D_CLUSTER, 1, 1) __launch_bounds__(DHT2D_THREADS)
+__global__ void __cluster_dims__(DHT2D_CLUSTER, 1, 1) __launch_bounds__(DHT2D_THREADS, sizeof(T) == 4 ? 4 : 2)
 k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Cx<T> tw[256];
@@ -414,7 +414,8 @@ __device__ inline size_t ptab_index(const Consts& c, int jk) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict__ tab, T* __restrict__ phi, T scale) {
+__global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict__ tab, T* __restrict__ phi, T scale,
+                                                   double* __restrict__ mean00) {
   const int P = c.ny * c.nz;
   const int jk = blockIdx.x * blockDim.x + threadIdx.x;
   if (jk >= P) return;
@@ -465,8 +466,11 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
     y = (rhs - y) * iv[(size_t)i * PT];
     d[o] = y;
   }
-  // back substitution from the top, the same chunking (the partial chunk first)
+  // back substitution from the top, the same chunking (the partial chunk first);
+  // the line sum of mode (0, 0) is gathered on the way (in T: an FP64
+  // conversion per plane and mode would load the narrow FP64 pipe)
   T x = y;  // x_{nx-1} = dp_{nx-1}
+  T lsum = x;
   int i = nx - 2;
   const int rem = (nx - 1) % PF;
   for (; i > nx - 2 - rem; --i) {
@@ -474,6 +478,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
     const T cp = (zero_mode && i == 0) ? (T)0 : iv[(size_t)i * PT];
     x = d[o] - cp * x;
     d[o] = x;
+    lsum += x;
   }
   {
     const int nch = (i + 1) / PF;   // full chunks below: planes i, i-1, ..., 0
@@ -499,6 +504,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
         const T cp = (zero_mode && i - q == 0) ? (T)0 : rt[q];
         x = rd[q] - cp * x;
         d[(size_t)(i - q) * P] = x;
+        lsum += x;
       }
 #pragma unroll
       for (int q = 0; q < PF; ++q) {
@@ -507,12 +513,15 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
       }
     }
   }
-  if (zero_mode) {
-    double s = 0.0;
-    for (int q = 0; q < nx; ++q) s += (double)d[(size_t)q * P];
-    const T mean = (T)(s / nx);
-    for (int q = 0; q < nx; ++q) d[(size_t)q * P] -= mean;
-  }
+  // the mean is removed by k_mode00_sub, in parallel over the planes
+  if (zero_mode) *mean00 = (double)lsum / nx;
+}
+
+// gauge mean(phi) = 0: subtract the line mean of mode (0, 0) in every plane
+template <class T>
+__global__ void k_mode00_sub(Consts c, T* __restrict__ phi, const double* __restrict__ mean00) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < c.nx) phi[(size_t)i * c.ny * c.nz] -= (T)*mean00;
 }
 
 // inverse pivots 1 / (diag_i - c'_{i-1}) of every distinct mode, FP64 arithmetic
@@ -575,7 +584,8 @@ void launch_poisson_x_on(const Consts& c, const Fields<T>& f, T* buf, cudaStream
   const int P = c.ny * c.nz;
   const T scale = (T)(c.h * c.h / ((double)c.ny * c.nz));
 
-  k_poisson_x<T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, buf, scale);
+  k_poisson_x<T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, buf, scale, f.mean00);
+  k_mode00_sub<T><<<(c.nx + 255) / 256, 256, 0, s>>>(c, buf, f.mean00);
 }
 
 template <class T>

@@ -23,6 +23,7 @@ struct Fields {
   T* tw_y; T* tw_z;           // FFT twiddles exp(-2 pi i t / N), t < N/2 (re, im)
   double* partial;            // per-block partial maxima of the CFL speed
   double* qpart;              // per-block inflow/outflow flux partials
+  double* mean00;             // line mean of the Poisson mode (0, 0)
   int n_partial;
   Params* prm;
 };
