@@ -533,6 +533,7 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
                  &full[slot]);
       }
   };
+  const int lane = tid & 31;
   if (tid == 0) {
     for (int sl = 0; sl < NS; ++sl) mbar_init(&full[sl], 1);
     fence_mbar_init();
@@ -555,6 +556,18 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
     return mbar_wait(&full[t % NS], (uint32_t)((t / NS) & 1));
   };
   bool ok = wait_stage(0) && wait_stage(1);
+  // z neighbours across the runs of one row: from the adjacent lane, or read
+  // from shared memory at the row's ends and at warp edges
+  auto left = [&](T last, const T* row) {
+    T v = __shfl_up_sync(0xffffffffu, last, 1);
+    if (lane == 0 || k0 == 0) v = row[km1];
+    return v;
+  };
+  auto right = [&](T first, const T* row) {
+    T v = __shfl_down_sync(0xffffffffu, first, 1);
+    if (lane == 31 || k0 + E >= nz) v = row[kpE];
+    return v;
+  };
   for (int i = ib; i < ie; ++i) {
     const int ta = i - ib, tb = ta + 1, tc = ta + 2;
     const size_t id = ((size_t)i * ny + j) * nz + k0;
@@ -609,10 +622,13 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
     lds_run<T, E>(Wc + R + k0, wc);
     lds_run<T, E>(Pb + R + k0, pb);
     lds_run<T, E>(Pb + Rm + k0, pbm);
-    const T ub_l = Ub[R + km1], ub_r = Ub[R + kpE], uc_l = Uc[R + km1];
-    const T vb_l = Vb[R + km1], vb_r = Vb[R + kpE], vbp_l = Vb[Rp + km1];
-    const T wb_l = Wb[R + km1], wb_r = Wb[R + kpE], wa_r = Wa[R + kpE], wbm_r = Wb[Rm + kpE];
-    const T pb_l = Pb[R + km1];
+    const T ub_l = left(ub[E - 1], Ub + R), ub_r = right(ub[0], Ub + R);
+    const T uc_l = left(uc[E - 1], Uc + R);
+    const T vb_l = left(vb[E - 1], Vb + R), vb_r = right(vb[0], Vb + R);
+    const T vbp_l = left(vbp[E - 1], Vb + Rp);
+    const T wb_l = left(wb[E - 1], Wb + R), wb_r = right(wb[0], Wb + R);
+    const T wa_r = right(wa[0], Wa + R), wbm_r = right(wbm[0], Wb + Rm);
+    const T pb_l = left(pb[E - 1], Pb + R);
     T No[E], Do[E];
     // u on face i (interior faces only)
     if (i >= 1) {
