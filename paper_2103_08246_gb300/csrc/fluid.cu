@@ -844,9 +844,33 @@ k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
   const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + (size_t)ioff * P + col;
   T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + (size_t)ioff * P + col;
   const T ob = act ? (comp == 0 ? o0 : comp == 1 ? o1 : o2)[col] : (T)0;
-  if (act)
-    for (int k = ks; k <= ke; ++k) s[(k - ks) * 32 + lane] = d[(size_t)k * P];
-  __syncwarp();
+  if (P % 32 == 0) {
+    // every plane's 32-column row is one 16-byte-aligned bulk copy; all of
+    // them are in flight at once on one mbarrier (bounded wait)
+    __shared__ uint64_t bar;
+    if (lane == 0) {
+      mbar_init(&bar, 1);
+      fence_mbar_init();
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const T* rows = d - lane;   // column col0 of plane k + ioff at rows + k P
+      mbar_arrive_expect_tx(&bar, (uint32_t)((ke - ks + 1) * 32 * sizeof(T)));
+      for (int k = ks; k <= ke; ++k)
+        bulk_g2s(s + (k - ks) * 32, rows + (size_t)k * P, 32 * sizeof(T), &bar);
+    }
+    if (!mbar_wait(&bar, 0)) {
+      if (lane == 0) {
+        atomicOr(&const_cast<Params*>(prm)->error, ERR_TIMEOUT);
+        (void)mbar_wait(&bar, 0);   // let the copies land before leaving
+      }
+      return;
+    }
+  } else {
+    if (act)
+      for (int k = ks; k <= ke; ++k) s[(k - ks) * 32 + lane] = d[(size_t)k * P];
+    __syncwarp();
+  }
   if (!act) return;
   T y = 0;
   for (int k = ks; k <= ke; ++k) {
