@@ -144,6 +144,13 @@ typedef struct {
   int rhs_planes;
   int afx_planes;
   int rhs_stages;
+  /* Nonzero: order-independent (bitwise reproducible) forcing. The scatter
+   * of the IB forcing accumulates in 64-bit fixed point (resolution 2^-40,
+   * partial sums below 2^23 in magnitude) and every touched node receives its
+   * sum in a single addition, so results do not depend on the order of the
+   * atomic operations. Costs 24 bytes per cell of workspace and one more pass
+   * over the markers. [0: floating-point atomic scatter] */
+  int deterministic;
 } ibm_options;
 
 /* Diagnostics read by ibm_stats (all FP64). */

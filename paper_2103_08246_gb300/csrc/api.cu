@@ -263,6 +263,7 @@ enum { GRAPH_HEAD = 0, GRAPH_MID = 1, GRAPH_TAIL = 2, GRAPH_KINDS = 3 };
 
 struct ibm_state {
   int precision = IBM_FP64;
+  bool deterministic = false;
   Consts c{};
   ibm_grid grid{};
   ibm_domain dom{};
@@ -366,6 +367,8 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   m.nm = L.nf + L.nb;
   m.Xb = cv.take<double>(3 * (size_t)L.nb);
   m.coef = cv.take<double>(3 * (size_t)m.nm);
+  m.nfield = NF;
+  m.acc = s->deterministic ? cv.take<unsigned long long>(3 * NF) : nullptr;
   Flag& fl = s->fl;
   fl.nv = L.nf;
   fl.X = cv.take<double>(3 * (size_t)L.nf);
@@ -668,6 +671,7 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   s->dom = *d;
   s->bodies = *b;
   s->precision = o ? o->precision : IBM_FP64;
+  s->deterministic = o && o->deterministic;
   s->cfl = (o && o->cfl > 0) ? o->cfl : 0.3;
   s->cfl_limit = (o && o->cfl_limit > 0) ? o->cfl_limit : 2.0;
   Consts& c = s->c;

@@ -28,6 +28,20 @@ __device__ inline T roma_phi(T r) {
   return (T)0;
 }
 
+// 64-bit fixed point of the deterministic scatter: value * 2^40, two's
+// complement in an unsigned word (integer addition wraps identically)
+constexpr double FIX_SCALE = 1099511627776.0;   // 2^40
+__device__ inline unsigned long long to_fixed(double x) {
+  return (unsigned long long)__double2ll_rn(x * FIX_SCALE);
+}
+__device__ inline unsigned long long to_fixed(float x) {
+  return (unsigned long long)__float2ll_rn(x * (float)FIX_SCALE);
+}
+template <class T>
+__device__ inline T from_fixed(unsigned long long s) {
+  return (T)((double)(long long)s * (1.0 / FIX_SCALE));
+}
+
 struct Stencil {
   int i0, j[3], k[3];
   bool vi[3];
@@ -174,7 +188,43 @@ __global__ void k_ib_spread(Consts c, Markers m, Flag fl, T* __restrict__ u, T* 
         const size_t pj = (pi + st.j[b]) * c.nz;
         for (int e = 0; e < 3; ++e) {
           const T val = wab * wz[e];
-          if (val != (T)0) atomicAdd(&q[pj + st.k[e]], val);
+          if (val == (T)0) continue;
+          if (m.acc)
+            atomicAdd(&m.acc[comp * m.nfield + pj + st.k[e]], to_fixed(val));
+          else
+            atomicAdd(&q[pj + st.k[e]], val);
+        }
+      }
+    }
+  }
+}
+
+// Deterministic mode, second pass: every node a marker touched takes its
+// fixed-point sum out of the accumulator (exchange with zero); the first
+// visitor adds it to the field, later visitors find zero. One nonzero
+// addition per node: the result does not depend on thread order.
+template <class T>
+__global__ void k_ib_flush(Consts c, Markers m, Flag fl, T* __restrict__ u, T* __restrict__ v,
+                           T* __restrict__ w) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= m.nm) return;
+  double X, Y, Z, U[3], dv;
+  if (!marker(m, fl, l, X, Y, Z, U, dv)) return;
+  const Frac<T> fx = frac_of<T>(X * c.inv_h), fy = frac_of<T>(Y * c.inv_h),
+                fz = frac_of<T>(Z * c.inv_h);
+  for (int comp = 0; comp < 3; ++comp) {
+    T* q = comp == 0 ? u : (comp == 1 ? v : w);
+    Stencil st;
+    T wx[3], wy[3], wz[3];
+    stencil<T>(c, comp, fx, fy, fz, st, wx, wy, wz);
+    for (int a = 0; a < 3; ++a) {
+      if (!st.vi[a]) continue;
+      const size_t pi = (size_t)(st.i0 + a) * c.ny;
+      for (int b = 0; b < 3; ++b) {
+        const size_t pj = (pi + st.j[b]) * c.nz;
+        for (int e = 0; e < 3; ++e) {
+          const unsigned long long sum = atomicExch(&m.acc[comp * m.nfield + pj + st.k[e]], 0ull);
+          if (sum != 0ull) atomicAdd(&q[pj + st.k[e]], from_fixed<T>(sum));
         }
       }
     }
@@ -188,6 +238,7 @@ void launch_ib(const Consts& c, const Fields<T>& f, const Markers& m, const Flag
   const int nb = (m.nm + 127) / 128;
   k_ib_interp<T><<<nb, 128, 0, s>>>(c, f.prm, m, fl, f.u[cur], f.v[cur], f.w[cur]);
   k_ib_spread<T><<<nb, 128, 0, s>>>(c, m, fl, f.u[cur], f.v[cur], f.w[cur]);
+  if (m.acc) k_ib_flush<T><<<nb, 128, 0, s>>>(c, m, fl, f.u[cur], f.v[cur], f.w[cur]);
 }
 
 template void launch_ib<double>(const Consts&, const Fields<double>&, const Markers&, const Flag&,

@@ -35,6 +35,8 @@ struct Markers {
   double* Xb = nullptr;       // bar marker positions (3 per marker)
   double bar_dv = 0.0;        // volume carried by each bar marker
   double* coef = nullptr;     // 3 per marker: dV / h^3 * (U - U*)
+  unsigned long long* acc = nullptr;   // deterministic mode: fixed-point sums, 3 fields
+  size_t nfield = 0;                   // cells of one velocity field (accumulator stride)
 };
 
 struct Flag {
