@@ -42,24 +42,27 @@ def _zm(a):
     return np.roll(a, 1, axis=2)
 
 
-def with_x_ghosts(q):
+def with_x_ghosts(q, q_in=None):
     """v or w with the inflow ghost prepended: index m holds q_{m-1}, m = 0..nx+1.
 
-    The inflow ghost is q_{-1} = -q_0 so that the linear interpolant vanishes
-    on the inflow plane (uniform inflow (U, 0, 0), Sec. II.A).
+    The inflow ghost is q_{-1} = 2 q_in - q_0, so that the linear interpolant
+    equals the prescribed inflow value q_in on the inflow plane x = 0; with
+    the uniform inflow (U, 0, 0) of Sec. II.A, q_in = 0 and q_{-1} = -q_0.
     """
-    return np.concatenate([-q[:1], q], axis=0)
+    ghost = -q[:1] if q_in is None else 2.0 * q_in[None] - q[:1]
+    return np.concatenate([ghost, q], axis=0)
 
 
-def advection(u, v, w, h):
+def advection(u, v, w, h, v_in=None, w_in=None):
     """Nonlinear term N = div(u u) in flux form on the MAC grid (Sec. II.B).
 
     Returns (Nu, Nv, Nw) with the shapes of (u, v, w); entries that are not
-    unknowns (u faces 0 and nx, the v/w ghost plane nx) are zero.
+    unknowns (u faces 0 and nx, the v/w ghost plane nx) are zero. v_in, w_in:
+    prescribed transverse inflow planes (None: zero).
     """
     nx = u.shape[0] - 1
-    vg = with_x_ghosts(v)          # vg[i+1] = v_i for i = -1..nx
-    wg = with_x_ghosts(w)
+    vg = with_x_ghosts(v, v_in)    # vg[i+1] = v_i for i = -1..nx
+    wg = with_x_ghosts(w, w_in)
 
     # normal fluxes at cell centres
     uc = 0.5 * (u[1:] + u[:-1])                    # (i+1/2): shape (nx, ny, nz)
@@ -92,8 +95,9 @@ def advection(u, v, w, h):
     return nu, nv, nw
 
 
-def laplacian(u, v, w, h):
-    """7-point Laplacian of each velocity component on its own lattice."""
+def laplacian(u, v, w, h, v_in=None, w_in=None):
+    """7-point Laplacian of each velocity component on its own lattice
+    (v_in, w_in: prescribed transverse inflow planes, None: zero)."""
     nx = u.shape[0] - 1
     inv = 1.0 / (h * h)
     lu = np.zeros_like(u)
@@ -101,8 +105,8 @@ def laplacian(u, v, w, h):
                 + _yp(u)[1:nx] - 2.0 * u[1:nx] + _ym(u)[1:nx]
                 + _zp(u)[1:nx] - 2.0 * u[1:nx] + _zm(u)[1:nx]) * inv
     out = [lu]
-    for q in (v, w):
-        g = with_x_ghosts(q)
+    for q, q_in in ((v, v_in), (w, w_in)):
+        g = with_x_ghosts(q, q_in)
         lq = np.zeros_like(q)
         c = q[:nx]
         lq[:nx] = (g[2:] - 2.0 * c + g[:nx]

@@ -25,6 +25,14 @@ compatibility, preserved uniform flow), not against a closed form.
 Readings (the paper does not state them): nu = 1 / Re with U = L = 1;
 fluid density 1; the initial state is u = U plus the given perturbation,
 made divergence-free by one projection at t = 0 with p = 0.
+
+Prescribed (time-dependent) inflow, optional: ``set_inflow`` gives the inflow
+planes (u_in, v_in, w_in) of the next step's new time level. The step uses
+the current planes for the explicit terms (v, w ghosts q_{-1} = 2 q_in - q_0),
+shifts u_in by a constant so that its mean is U (Q_in = U Ly Lz exactly), and
+carries the boundary increments (u_in^{n+1} - u_0^n, v_in^{n+1} - v_in^n, ...)
+into the x factor of A3; the new u_in becomes face 0 of u^{n+1}. Without a
+call the inflow stays uniform (U, 0, 0).
 """
 from __future__ import annotations
 
@@ -55,6 +63,9 @@ class OracleSolver:
             self.v += noise[1]
             self.w += noise[2]
         self.p = np.zeros((nx, ny, nz))
+        self.v_in = np.zeros((ny, nz))     # current transverse inflow planes
+        self.w_in = np.zeros((ny, nz))
+        self.pending_inflow = None
         self.n_prev = None
         self.dt_old = None
         self.t = 0.0
@@ -98,6 +109,10 @@ class OracleSolver:
             return np.concatenate([self.X, self.Xb], axis=0)
         return self.Xb
 
+    def set_inflow(self, u_in, v_in, w_in):
+        """Inflow planes (ny, nz) for the new time level of the following steps."""
+        self.pending_inflow = tuple(np.array(a, dtype=np.float64) for a in (u_in, v_in, w_in))
+
     def next_dt(self):
         if self.wl.dt > 0:
             return self.wl.dt
@@ -118,8 +133,8 @@ class OracleSolver:
         un, vn, wn = mac.outflow_convective(u, v, w, dt, h, self.U_IN)  # A1
         du_out, dv_out, dw_out = un - u[nx], vn - v[nx], wn - w[nx]
 
-        N = mac.advection(u, v, w, h)                                    # A2
-        L = mac.laplacian(u, v, w, h)
+        N = mac.advection(u, v, w, h, self.v_in, self.w_in)              # A2
+        L = mac.laplacian(u, v, w, h, self.v_in, self.w_in)
         G = mac.pressure_gradient(self.p, h)
         rhs = []
         for c in range(3):
@@ -129,11 +144,20 @@ class OracleSolver:
             rhs.append(dt * (-nl - G[c] + nu * L[c]))
 
         r = nu * dt / (2.0 * h * h)                                      # A3
-        du, dv, dw = af.af_solve(rhs[0], rhs[1], rhs[2], r, du_out, dv_out, dw_out)
+        du_in = dv_in = dw_in = None
+        if self.pending_inflow is not None:
+            pu, pv, pw = self.pending_inflow
+            u_new = pu - pu.mean() + self.U_IN          # Q_in = U Ly Lz
+            du_in, dv_in, dw_in = u_new - u[0], pv - self.v_in, pw - self.w_in
+        du, dv, dw = af.af_solve(rhs[0], rhs[1], rhs[2], r, du_out, dv_out, dw_out,
+                                 du_in, dv_in, dw_in)
         us = u + du
         vs = v + dv
         ws = w + dw
         us[nx], vs[nx], ws[nx] = un, vn, wn
+        if self.pending_inflow is not None:
+            us[0] = u_new
+            self.v_in, self.w_in = self.pending_inflow[1].copy(), self.pending_inflow[2].copy()
 
         Xm = self.markers()                                              # A4
         if Xm.shape[0]:

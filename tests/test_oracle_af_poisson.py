@@ -4,7 +4,8 @@ pressure Poisson solve (Sec. II.B).
 * AF: separable trigonometric modes that satisfy each line's boundary rows are
   eigenvectors of every factor, so (1 - aL_x)(1 - aL_y)(1 - aL_z) du = RHS has
   the closed-form solution RHS / prod_d (1 + r mu_d), mu = 2 - 2 cos(theta).
-  The outflow-increment row is pinned by the closed-form sinh profile.
+  The outflow- and inflow-increment rows are pinned by closed-form sinh
+  profiles.
 * Poisson: the DFT + Thomas solution equals a dense direct solve of the
   assembled operator (Neumann in x, periodic in y, z, mean-zero gauge),
   on grids with unequal sides so that a transposed axis fails.
@@ -58,6 +59,26 @@ def test_af_outflow_increment_profile():
     iv = np.arange(nx)
     expect_v = c * np.sinh(theta * (iv + 0.5)) / math.sinh(theta * (nx + 0.5))
     np.testing.assert_allclose(dv[:nx, 0, 0], expect_v, rtol=1e-12)
+
+
+def test_af_inflow_increment_profile():
+    # zero RHS and outflow increments, inflow increment c: u (Dirichlet face
+    # value c at i = 0, zero at i = nx) follows c sinh(theta (nx - i)) / sinh(theta nx);
+    # v, w (ghost 2c - q_0, so the inflow-plane value (q_-1 + q_0) / 2 is c):
+    # A sinh(theta (nx - i)) with A (sinh(theta (nx + 1)) + sinh(theta nx)) / 2 = c
+    nx, ny, nz, r, c = 9, 4, 4, 0.8, 0.25
+    rhs = np.zeros((nx + 1, ny, nz))
+    zero = np.zeros((ny, nz))
+    inc = np.full((ny, nz), c)
+    du, dv, dw = af.af_solve(rhs, rhs, rhs, r, zero, zero, zero, inc, inc, inc)
+    theta = math.acosh((1 + 2 * r) / (2 * r))
+    i = np.arange(1, nx)
+    np.testing.assert_allclose(du[1:nx, 0, 0], c * np.sinh(theta * (nx - i)) / math.sinh(theta * nx),
+                               rtol=1e-12)
+    iv = np.arange(nx)
+    A = 2 * c / (math.sinh(theta * (nx + 1)) + math.sinh(theta * nx))
+    np.testing.assert_allclose(dv[:nx, 1, 2], A * np.sinh(theta * (nx - iv)), rtol=1e-12)
+    np.testing.assert_allclose(dw[:nx, 3, 0], A * np.sinh(theta * (nx - iv)), rtol=1e-12)
 
 
 def _assembled_operator(nx, ny, nz, h):
