@@ -151,6 +151,10 @@ typedef struct {
    * atomic operations. Costs 24 bytes per cell of workspace and one more pass
    * over the markers. [0: floating-point atomic scatter] */
   int deterministic;
+  /* Nonzero: the inflow plane x = 0 is prescribed by the caller
+   * (ibm_set_inflow / ibm_inflow_planes) instead of the uniform (U, 0, 0).
+   * Costs 8 planes of workspace and two small kernels per step. [0] */
+  int inflow;
 } ibm_options;
 
 /* Diagnostics read by ibm_stats (all FP64). */
@@ -217,6 +221,25 @@ int ibm_stats(ibm_state* s, ibm_stats_t* out);
  * and does not project. Both synchronise. */
 int ibm_get_field(ibm_state* s, int which, double* host, size_t n);
 int ibm_set_field(ibm_state* s, int which, const double* host, size_t n);
+
+/* Prescribed, time-dependent inflow (states created with opts->inflow != 0;
+ * IBM_EINVAL otherwise). The step that follows uses the pending planes as the
+ * inflow of its new time level (the Dirichlet condition of Sec. II.A made
+ * time-dependent): u on the inflow face becomes the pending u shifted by a
+ * constant so that its mean is U (inflow flux U * ly * lz exactly, as the
+ * pressure solve requires); v and w take the pending values on the inflow
+ * plane through the ghost q_-1 = 2 q_in - q_0; the changes against the
+ * previous level enter the implicit x factor. The explicit terms of a step
+ * use the previous level. Planes are ny * nz values, index j * nz + k; the
+ * pending planes keep their values until changed (a constant inflow after
+ * the first step), and start as u = U, v = w = 0.
+ * ibm_set_inflow copies three host planes of doubles (converted to the
+ * state's precision) and synchronises. ibm_inflow_planes returns the device
+ * addresses of the three pending planes in the state's precision, for
+ * callers that generate the inflow on the GPU: write them on the state's
+ * stream (or synchronise with it) before ibm_step. */
+int ibm_set_inflow(ibm_state* s, const double* u, const double* v, const double* w);
+int ibm_inflow_planes(ibm_state* s, void** u, void** v, void** w);
 
 /* Number of markers (flag vertices first, then bar markers) and their
  * positions at the start of the next step (3 doubles each). */

@@ -25,7 +25,7 @@ IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P = 0, 1, 2, 3
 # every symbol include/ibm.h declares
 SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_flag_state",
            "ibm_stats", "ibm_get_field", "ibm_set_field", "ibm_marker_count", "ibm_get_markers",
-           "ibm_save", "ibm_load",
+           "ibm_save", "ibm_load", "ibm_set_inflow", "ibm_inflow_planes",
            "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_destroy", "ibm_strerror")
 
@@ -60,7 +60,8 @@ class ibm_options(ctypes.Structure):
                 ("cfl_limit", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("init_u", _dp), ("init_v", _dp), ("init_w", _dp),
                 ("rhs_planes", ctypes.c_int), ("afx_planes", ctypes.c_int),
-                ("rhs_stages", ctypes.c_int), ("deterministic", ctypes.c_int)]
+                ("rhs_stages", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("inflow", ctypes.c_int)]
 
 
 class ibm_stats_t(ctypes.Structure):
@@ -109,6 +110,8 @@ def load(path: str = LIB_PATH):
     lib.ibm_set_field.argtypes = [vp, ctypes.c_int, _dp, sz]
     lib.ibm_marker_count.argtypes = [vp, ctypes.POINTER(sz)]
     lib.ibm_get_markers.argtypes = [vp, _dp, sz]
+    lib.ibm_set_inflow.argtypes = [vp, _dp, _dp, _dp]
+    lib.ibm_inflow_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
     lib.ibm_save.argtypes = [vp, ctypes.c_char_p]
     lib.ibm_load.argtypes = [vp, ctypes.c_char_p]
     lib.ibm_time_stage.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
@@ -213,6 +216,18 @@ def ibm_get_markers(state, out):
     _check(load().ibm_get_markers(state, _ptr(out), out.size // 3), "ibm_get_markers")
 
 
+def ibm_set_inflow(state, u, v, w):
+    a = [np.ascontiguousarray(q, dtype=np.float64) for q in (u, v, w)]
+    _check(load().ibm_set_inflow(state, *[_ptr(q) for q in a]), "ibm_set_inflow")
+
+
+def ibm_inflow_planes(state):
+    """Device addresses of the pending inflow planes (u, v, w)."""
+    ptrs = [ctypes.c_void_p() for _ in range(3)]
+    _check(load().ibm_inflow_planes(state, *[ctypes.byref(q) for q in ptrs]), "ibm_inflow_planes")
+    return tuple(q.value for q in ptrs)
+
+
 def ibm_save(state, path):
     _check(load().ibm_save(state, os.fsencode(path)), "ibm_save")
 
@@ -258,7 +273,7 @@ class Solver:
 
     def __init__(self, wl: Workload, precision: int = IBM_FP64, noise=None, stream=None,
                  cfl: float | None = None, cfl_limit: float = 2.0, tiles=None,
-                 deterministic: bool = False):
+                 deterministic: bool = False, inflow: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the solver needs a CUDA device")
@@ -274,7 +289,8 @@ class Solver:
                            ctypes.c_void_p(self.stream.cuda_stream),
                            *([_ptr(a) for a in self._noise] if self._noise else [None] * 3),
                            int(tiles.get("rhs_planes", 0)), int(tiles.get("afx_planes", 0)),
-                           int(tiles.get("rhs_stages", 0)), 1 if deterministic else 0)
+                           int(tiles.get("rhs_stages", 0)), 1 if deterministic else 0,
+                           1 if inflow else 0)
         self.ws_bytes = ibm_workspace_bytes(self.grid, self.dom, self.bodies, opts)
         self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device="cuda")
         torch.cuda.synchronize()
@@ -314,6 +330,9 @@ class Solver:
 
     def stats(self):
         return ibm_stats(self.state)
+
+    def set_inflow(self, u, v, w):
+        ibm_set_inflow(self.state, u, v, w)
 
     def save(self, path):
         ibm_save(self.state, path)

@@ -264,6 +264,7 @@ enum { GRAPH_HEAD = 0, GRAPH_MID = 1, GRAPH_TAIL = 2, GRAPH_KINDS = 3 };
 struct ibm_state {
   int precision = IBM_FP64;
   bool deterministic = false;
+  bool inflow = false;
   Consts c{};
   ibm_grid grid{};
   ibm_domain dom{};
@@ -359,6 +360,8 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   f.partial = cv.take<double>(f.n_partial);
   f.qpart = cv.take<double>(2 * (size_t)outflow_blocks(c));
   f.mean00 = cv.take<double>(1);
+  f.inflow = s->inflow ? cv.take<T>(8 * P) : nullptr;
+  f.inflow_mean = s->inflow ? cv.take<double>(1) : nullptr;
   f.prm = cv.take<Params>(1);
   s->dstat = cv.take<double>(16);
   Markers& m = s->mk;
@@ -510,6 +513,7 @@ void record_head(ibm_state* s, int cur) {
   launch_af_tables(c, f, s->side2);
   cudaEventRecord(s->ev_join2, s->side2);
   launch_rhs(c, f, cur, st);
+  launch_inflow(c, f, cur, st);   // new inflow time level (prescribed inflow only)
   launch_outflow(c, f, cur, st);
   cudaStreamWaitEvent(st, s->ev_join2, 0);
   launch_af(c, f, cur, st);
@@ -564,6 +568,12 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
       int rc = upload_field<T>(st, dst, buf.data(), NF);
       if (rc) return rc;
     }
+  }
+  // prescribed inflow: pending u = U, everything else zero (uniform (U, 0, 0))
+  if (f.inflow) {
+    std::vector<double> ones((size_t)c.ny * c.nz, c.u_in);
+    int rc = upload_field<T>(st, f.inflow, ones.data(), ones.size());
+    if (rc) return rc;
   }
   // twiddles exp(-2 pi i t / N)
   for (int dir = 0; dir < 2; ++dir) {
@@ -672,6 +682,7 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   s->bodies = *b;
   s->precision = o ? o->precision : IBM_FP64;
   s->deterministic = o && o->deterministic;
+  s->inflow = o && o->inflow;
   s->cfl = (o && o->cfl > 0) ? o->cfl : 0.3;
   s->cfl_limit = (o && o->cfl_limit > 0) ? o->cfl_limit : 2.0;
   Consts& c = s->c;
@@ -978,6 +989,30 @@ int ibm_set_field(ibm_state* s, int which, const double* host, size_t n) {
   return upload_f32_staged(s->stream, (float*)ptr, host, n, (double*)s->ff.e[0], stage_capacity(s));
 }
 
+int ibm_inflow_planes(ibm_state* s, void** u, void** v, void** w) {
+  if (!s || !u || !v || !w || !s->inflow) return IBM_EINVAL;
+  const size_t P = (size_t)s->c.ny * s->c.nz;
+  char* base = s->precision == IBM_FP64 ? (char*)s->fd.inflow : (char*)s->ff.inflow;
+  const size_t e = s->precision == IBM_FP64 ? 8 : 4;
+  *u = base;
+  *v = base + P * e;
+  *w = base + 2 * P * e;
+  return IBM_OK;
+}
+
+int ibm_set_inflow(ibm_state* s, const double* u, const double* v, const double* w) {
+  if (!s || !u || !v || !w || !s->inflow) return IBM_EINVAL;
+  const size_t P = (size_t)s->c.ny * s->c.nz;
+  const double* src[3] = {u, v, w};
+  for (int q = 0; q < 3; ++q) {
+    int rc = s->precision == IBM_FP64
+                 ? upload_field<double>(s->stream, s->fd.inflow + q * P, src[q], P)
+                 : upload_field<float>(s->stream, s->ff.inflow + q * P, src[q], P);
+    if (rc) return rc;
+  }
+  return IBM_OK;
+}
+
 int ibm_marker_count(const ibm_state* s, size_t* n) {
   if (!s || !n) return IBM_EINVAL;
   *n = (size_t)s->mk.nm;
@@ -1005,7 +1040,7 @@ int ibm_get_markers(ibm_state* s, double* X, size_t n) {
 namespace {
 struct CkptHeader {
   char magic[8];
-  int version, precision, nx, ny, nz, nf, nb, elem;
+  int version, precision, nx, ny, nz, nf, nb, elem, inflow;
   double lx, ly, lz, nu;
   double body[12];
   long long params_bytes;
@@ -1022,6 +1057,7 @@ void fill_header(const ibm_state* s, CkptHeader& h) {
   h.nf = s->mk.nf;
   h.nb = s->mk.nb;
   h.elem = s->precision == IBM_FP64 ? 8 : 4;
+  h.inflow = s->inflow ? 1 : 0;
   h.lx = s->c.lx;
   h.ly = s->c.ly;
   h.lz = s->c.lz;
@@ -1050,6 +1086,8 @@ std::vector<std::pair<void*, size_t>> ckpt_regions(ibm_state* s) {
     // per-block maxima of the CFL speed from the last projection: the next
     // step's dt in CFL mode
     r.push_back({f.partial, (size_t)f.n_partial * sizeof(double)});
+    // prescribed inflow planes (pending and current levels)
+    if (f.inflow) r.push_back({f.inflow, 8 * (size_t)c.ny * c.nz * e});
   };
   if (s->precision == IBM_FP64) add(s->fd);
   else add(s->ff);

@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(TK* TJ)
 k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
       const T* __restrict__ v, const T* __restrict__ w, const T* __restrict__ p,
       T* __restrict__ n0, T* __restrict__ n1, T* __restrict__ n2, T* __restrict__ d0,
-      T* __restrict__ d1, T* __restrict__ d2) {
+      T* __restrict__ d1, T* __restrict__ d2, const T* __restrict__ vin,
+      const T* __restrict__ win) {
   const int k = blockIdx.x * TK + threadIdx.x;
   const int j = blockIdx.y * TJ + threadIdx.y;
   if (k >= c.nz || j >= c.ny) return;
@@ -204,7 +205,7 @@ k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
       {
         const T vc = v[id];
         const T vxp = v[id + P];
-        const T vxm = i == 0 ? -vc : v[id - P];
+        const T vxm = i == 0 ? (vin ? (T)2 * vin[(size_t)j * nz + k] : (T)0) - vc : v[id - P];
         const T vyp = v[at(i, jp, k)], vym = v[at(i, jm, k)];
         const T vzp = v[at(i, j, kp)], vzm = v[at(i, j, km)];
         const T fxr = hf * (u[at(i + 1, jm, k)] + u[at(i + 1, j, k)]) * (hf * (vc + vxp));
@@ -226,7 +227,7 @@ k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
       {
         const T wc = w[id];
         const T wxp = w[id + P];
-        const T wxm = i == 0 ? -wc : w[id - P];
+        const T wxm = i == 0 ? (win ? (T)2 * win[(size_t)j * nz + k] : (T)0) - wc : w[id - P];
         const T wyp = w[at(i, jp, k)], wym = w[at(i, jm, k)];
         const T wzp = w[at(i, j, kp)], wzm = w[at(i, j, km)];
         const T fxr = hf * (u[at(i + 1, j, km)] + u[at(i + 1, j, k)]) * (hf * (wc + wxp));
@@ -268,7 +269,8 @@ __global__ void __launch_bounds__(RTHREADS, 1)
 k_rhs_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ u,
            const T* __restrict__ v, const T* __restrict__ w, const T* __restrict__ p,
            T* __restrict__ n0, T* __restrict__ n1, T* __restrict__ n2, T* __restrict__ d0,
-           T* __restrict__ d1, T* __restrict__ d2, int XR, int RSTAGES) {
+           T* __restrict__ d1, T* __restrict__ d2, int XR, int RSTAGES, const T* __restrict__ vin,
+           const T* __restrict__ win) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t full[RSTAGES_MAX];
   const int nx = c.nx, ny = c.ny, nz = c.nz;
@@ -393,7 +395,8 @@ k_rhs_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ u,
       }
       {
         const T vc = Vb[R + k];
-        const T vxp = Vc[R + k], vxm = sgn * Va[R + k];
+        const T vxp = Vc[R + k];
+        const T vxm = sgn * Va[R + k] + ((i == 0 && vin) ? (T)2 * vin[(size_t)j * nz + k] : (T)0);
         const T vyp = Vb[Rp + k], vym = Vb[Rm + k];
         const T vzp = Vb[R + kp], vzm = Vb[R + km];
         const T fxr = hf * (Uc[Rm + k] + Uc[R + k]) * (hf * (vc + vxp));
@@ -413,7 +416,8 @@ k_rhs_pipe(Consts c, Params* __restrict__ prm, const T* __restrict__ u,
       }
       {
         const T wc = Wb[R + k];
-        const T wxp = Wc[R + k], wxm = sgn * Wa[R + k];
+        const T wxp = Wc[R + k];
+        const T wxm = sgn * Wa[R + k] + ((i == 0 && win) ? (T)2 * win[(size_t)j * nz + k] : (T)0);
         const T wyp = Wb[Rp + k], wym = Wb[Rm + k];
         const T wzp = Wb[R + kp], wzm = Wb[R + km];
         const T fxr = hf * (Uc[R + km] + Uc[R + k]) * (hf * (wc + wxp));
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(256, 2)
 k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* __restrict__ v,
           const T* __restrict__ w, const T* __restrict__ p, T* __restrict__ n0,
           T* __restrict__ n1, T* __restrict__ n2, T* __restrict__ d0, T* __restrict__ d1,
-          T* __restrict__ d2, int XR) {
+          T* __restrict__ d2, int XR, const T* __restrict__ vin, const T* __restrict__ win) {
   using RV = RhsVec<T>;
   constexpr int E = RV::E, TJ = RV::TJ, RW = RV::RW, ROWS = RV::ROWS, NS = RV::STAGES;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -598,7 +602,19 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
     const T* Wc = C + 2 * RW * nz;
     const T* Pa = A + 3 * RW * nz;
     const T* Pb = B + 3 * RW * nz;
-    const T sgn = i - 1 < 0 ? (T)-1 : (T)1;   // inflow reflection ghost of v, w
+    const T sgn = i - 1 < 0 ? (T)-1 : (T)1;   // inflow ghost of v, w: 2 q_in - q_0
+    T gv[E], gw[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) gv[e] = gw[e] = (T)0;
+    if (i == 0 && vin) {
+      ldg_run<T, E>(vin + (size_t)j * nz + k0, gv);
+      ldg_run<T, E>(win + (size_t)j * nz + k0, gw);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        gv[e] *= (T)2;
+        gw[e] *= (T)2;
+      }
+    }
     // shared rows of the run (E values) and edge values
     T ub[E], ubm[E], ubp[E], uc[E], ucm[E];
     T vb[E], vbm[E], vbp[E], va[E], vap[E], vc[E];
@@ -661,7 +677,7 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const T c0 = vb[e];
-      const T vxp = vc[e], vxm = sgn * va[e];
+      const T vxp = vc[e], vxm = sgn * va[e] + gv[e];
       const T vzp = e == E - 1 ? vb_r : vb[e + 1], vzm = e == 0 ? vb_l : vb[e - 1];
       const T wbp1 = e == E - 1 ? wb_r : wb[e + 1], wbmp1 = e == E - 1 ? wbm_r : wbm[e + 1];
       const T fxr = hf * (ucm[e] + uc[e]) * (hf * (c0 + vxp));
@@ -684,7 +700,7 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const T c0 = wb[e];
-      const T wxp = wc[e], wxm = sgn * wa[e];
+      const T wxp = wc[e], wxm = sgn * wa[e] + gw[e];
       const T wzp = e == E - 1 ? wb_r : wb[e + 1], wzm = e == 0 ? wb_l : wb[e - 1];
       const T ucl = e == 0 ? uc_l : uc[e - 1], ubl = e == 0 ? ub_l : ub[e - 1];
       const T vbpl = e == 0 ? vbp_l : vbp[e - 1], vbl = e == 0 ? vb_l : vb[e - 1];
@@ -751,71 +767,6 @@ k_outflow(Consts c, const Params* __restrict__ prm, T* __restrict__ u,
   }
 }
 
-// ---------------------------------------------------------------- implicit factors (A3)
-// Each factor (1 - a L_d), a = nu dt / 2, is r (q x_k - x_{k-1} - x_{k+1}) with
-// r = a / h^2, q = 2 + 1/r = rho + 1/rho, rho = exp(-theta),
-// theta = 2 asinh(1 / (2 sqrt r)).
-// x lines: LU (Thomas) recursions y_k = (e_k + y_{k-1}) / p_k,
-//   x_k = y_k + x_{k+1} / p_k with the closed-form pivots tabulated per step
-//   (u: Dirichlet rows 1..nx-1, the outflow-face increment moved to the RHS;
-//   v, w: rows 0..nx-1 with the inflow reflection ghost).
-// periodic y, z lines: q - S - S^{-1} = (1/rho)(1 - rho S^{-1})(1 - rho S),
-//   i.e. y_j = e_j + rho y_{j-1}, z_j = y_j + rho z_{j+1}, x = rho z.
-// Every thread solves SEG consecutive points of one line, starting both
-// recursions H = af_h points outside its segment (periodic lines wrap), so
-// the lines are solved by many threads without a serial sweep; segments read
-// each other's halos, so every solve writes to a different buffer.
-template <class T>
-__global__ void __launch_bounds__(128)
-k_af_x(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
-       const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
-       T* __restrict__ e0, T* __restrict__ e1, T* __restrict__ e2, const T* __restrict__ o0,
-       const T* __restrict__ o1, const T* __restrict__ o2) {
-  const int P = c.ny * c.nz;
-  const int jk = blockIdx.x * blockDim.x + threadIdx.x;
-  if (jk >= P) return;
-  const int comp = blockIdx.z;
-  const int m = comp == 0 ? c.nx - 1 : c.nx;   // unknowns k = 1..m
-  const int ioff = comp == 0 ? 0 : -1;         // plane i = k + ioff
-  const int k0 = 1 + blockIdx.y * SEG;
-  if (k0 > m) return;
-  const int k1 = min(k0 + SEG, m + 1);
-  const int H = prm->af_h;
-  const T* ip = ipt + (comp == 0 ? 0 : c.nx + 2);
-  const T ir = pick<T>(1.0 / prm->r, prm->f_ir);
-  const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + jk + (size_t)ioff * P;
-  T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + jk + (size_t)ioff * P;
-  const T ob = (comp == 0 ? o0 : comp == 1 ? o1 : o2)[jk];
-  const int ks = max(1, k0 - H);
-  const int ke = min(m, k1 - 1 + H);
-  T y = 0;
-  for (int k = ks; k < k0; ++k) {
-    T e = d[(size_t)k * P] * ir;
-    if (k == m) e += ob;
-    y = (e + y) * ip[k];
-  }
-  T yr[SEG + HMAX];
-#pragma unroll
-  for (int q = 0; q < SEG + HMAX; ++q) {
-    const int k = k0 + q;
-    if (k <= ke) {
-      T e = d[(size_t)k * P] * ir;
-      if (k == m) e += ob;
-      y = (e + y) * ip[k];
-      yr[q] = y;
-    }
-  }
-  T x = 0;
-#pragma unroll
-  for (int q = SEG + HMAX - 1; q >= 0; --q) {
-    const int k = k0 + q;
-    if (k <= ke) {
-      x = yr[q] + x * ip[k];
-      if (k < k1) out[(size_t)k * P] = x;
-    }
-  }
-}
-
 // x factor by the LU recursions on shared-memory-staged planes: one warp per
 // 32 consecutive (y, z) columns and XS planes (+ warm-up halos); lanes walk
 // their columns (bank-conflict free), loads and stores are 128-byte rows.
@@ -824,7 +775,7 @@ __global__ void __launch_bounds__(32)
 k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
         const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
         T* __restrict__ e0, T* __restrict__ e1, T* __restrict__ e2, const T* __restrict__ o0,
-        const T* __restrict__ o1, const T* __restrict__ o2) {
+        const T* __restrict__ o1, const T* __restrict__ o2, const T* __restrict__ inc) {
   __shared__ T s[(XS + 2 * HMAX) * 32];
   const int P = c.ny * c.nz;
   const int lane = threadIdx.x;
@@ -844,6 +795,8 @@ k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
   const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + (size_t)ioff * P + col;
   T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + (size_t)ioff * P + col;
   const T ob = act ? (comp == 0 ? o0 : comp == 1 ? o1 : o2)[col] : (T)0;
+  // inflow-face increment (u) or twice the inflow-value increment (v, w ghost)
+  const T ib = (act && inc) ? (comp == 0 ? (T)1 : (T)2) * inc[(size_t)comp * P + col] : (T)0;
   if (P % 32 == 0) {
     // every plane's 32-column row is one 16-byte-aligned bulk copy; all of
     // them are in flight at once on one mbarrier (bounded wait)
@@ -876,6 +829,7 @@ k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
   for (int k = ks; k <= ke; ++k) {
     T e = s[(k - ks) * 32 + lane] * ir;
     if (k == m) e += ob;
+    if (k == 1) e += ib;
     y = (e + y) * ip[k];
     s[(k - ks) * 32 + lane] = y;
   }
@@ -896,7 +850,7 @@ __global__ void __launch_bounds__(256)
 k_af_xv(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
         const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
         T* __restrict__ e0, T* __restrict__ e1, T* __restrict__ e2, const T* __restrict__ o0,
-        const T* __restrict__ o1, const T* __restrict__ o2) {
+        const T* __restrict__ o1, const T* __restrict__ o2, const T* __restrict__ inc) {
   const int P = c.ny * c.nz;
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   const int comp = blockIdx.z;
@@ -912,6 +866,7 @@ k_af_xv(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
   const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + (size_t)ioff * P + col;
   T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + (size_t)ioff * P + col;
   const T ob = (comp == 0 ? o0 : comp == 1 ? o1 : o2)[col];
+  const T ib = inc ? (comp == 0 ? (T)1 : (T)2) * inc[(size_t)comp * P + col] : (T)0;
   // forward warm-up over ks .. k0-1 (values not kept)
   T y = 0;
   for (int kb = ks; kb < k0; kb += 8) {
@@ -920,7 +875,7 @@ k_af_xv(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
     for (int t = 0; t < 8; ++t) buf[t] = (kb + t < k0) ? d[(size_t)(kb + t) * P] : (T)0;
 #pragma unroll
     for (int t = 0; t < 8; ++t)
-      if (kb + t < k0) y = (buf[t] * ir + y) * ip[kb + t];
+      if (kb + t < k0) y = (buf[t] * ir + (kb + t == 1 ? ib : (T)0) + y) * ip[kb + t];
   }
   // the segment
   const int ns = k1 - k0;
@@ -933,6 +888,7 @@ k_af_xv(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
       const int k = k0 + q;
       T e = yr[q] * ir;
       if (k == m) e += ob;
+      if (k == 1) e += ib;
       y = (e + y) * ip[k];
       yr[q] = y;
     }
@@ -951,6 +907,7 @@ k_af_xv(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
         if (m0 + t < nt) {
           T e = buf[t] * ir;
           if (k == m) e += ob;
+          if (k == 1) e += ib;
           y = (e + y) * ip[k];
         }
         yt[m0 + t] = y;
@@ -1294,74 +1251,6 @@ __device__ inline void tap_range(int n, int H, int& lo, int& hi) {
   } else {
     lo = (n - 1) / 2;
     hi = n / 2;
-  }
-}
-
-// x factor in FP32: the Dirichlet rows (u: du_0 = 0; v, w: du_{-1} = -du_0;
-// the outflow increment moved into the last right-hand side so the far end is
-// homogeneous) are reproduced exactly by the odd reflection of the right-hand
-// side about the two ends (about face 0 for u, about x = -h/2 for v, w, and
-// about plane nx), so the solve is the free-space inverse of
-// r (q - S - S^{-1}), t_m = (1/r) rho^{|m|+1} / (1 - rho^2), applied to the
-// reflected data and truncated to |m| <= H. A block stages XC planes (a tile
-// parameter) plus the halo of 32 consecutive (y, z) columns.
-template <class T>
-__global__ void __launch_bounds__(256)
-k_af_xc(Consts c, const Params* __restrict__ prm, const T* __restrict__ taps,
-        const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
-        T* __restrict__ e0, T* __restrict__ e1, T* __restrict__ e2, const T* __restrict__ o0,
-        const T* __restrict__ o1, const T* __restrict__ o2) {
-  extern __shared__ unsigned char smem_raw[];
-  T* s = reinterpret_cast<T*>(smem_raw);
-  const int P = c.ny * c.nz;
-  const int XC = c.afx_planes;
-  const int comp = blockIdx.z;
-  const int nx = c.nx;
-  // unknown planes: u 1..nx-1 (reflection about 0 and nx); v, w 0..nx-1
-  // (reflection about -1/2 and nx)
-  const int ilo = comp == 0 ? 1 : 0, ihi = nx - 1;
-  const int i0 = ilo + blockIdx.y * XC;
-  if (i0 > ihi) return;
-  const int ni = min(XC, ihi - i0 + 1);
-  const int H = prm->af_h;
-  const int col0 = blockIdx.x * 32;
-  const int ncol = min(32, P - col0);
-  const T* d = (comp == 0 ? d0 : comp == 1 ? d1 : d2) + col0;
-  T* out = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + col0;
-  const T* ob = (comp == 0 ? o0 : comp == 1 ? o1 : o2) + col0;
-  const T rr_ = pick<T>(prm->r, prm->f_r);
-  const int rows = ni + 2 * H;
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  for (int e = tid; e < rows * 32; e += 256) {
-    const int rr = e >> 5, q = e & 31;
-    if (q >= ncol) continue;
-    int i = i0 - H + rr;
-    T sg = 1;
-    // reflect into the unknowns (odd extension)
-    for (int it = 0; it < 4; ++it) {
-      if (comp == 0) {
-        if (i <= 0) { i = -i; sg = -sg; }
-        if (i >= nx) { i = 2 * nx - i; sg = -sg; }
-      } else {
-        if (i < 0) { i = -1 - i; sg = -sg; }
-        if (i >= nx) { i = 2 * nx - i; sg = -sg; }
-      }
-    }
-    T val = 0;
-    if (i >= ilo && i <= ihi) {
-      val = d[(size_t)i * P + q];
-      if (i == ihi) val += ob[q] * rr_;
-    }
-    s[e] = sg * val;
-  }
-  __syncthreads();
-  const int q = threadIdx.x;
-  if (q >= ncol) return;
-  for (int rr = threadIdx.y; rr < ni; rr += 8) {
-    const T* sc = s + (rr + H) * 32 + q;
-    T acc = taps[0] * sc[0];
-    for (int m = 1; m <= H; ++m) acc += taps[m] * (sc[m * 32] + sc[-m * 32]);
-    out[(size_t)(i0 + rr) * P + q] = acc;
   }
 }
 
@@ -1805,6 +1694,65 @@ static dim3 grid3(const Consts& c, int planes) {
   return dim3((c.nz + TK - 1) / TK, (c.ny + TJ - 1) / TJ, (planes + XCHUNK - 1) / XCHUNK);
 }
 
+// ---------------------------------------------------------------- prescribed inflow
+// plane q of the inflow block: 0..2 pending u, v, w; 3, 4 current v, w;
+// 5..7 increments u, v, w
+template <class T>
+static T* inflow_plane(const Consts& c, const Fields<T>& f, int q) {
+  return f.inflow ? f.inflow + (size_t)q * c.ny * c.nz : nullptr;
+}
+template <class T>
+static const T* inflow_cur_v(const Consts& c, const Fields<T>& f) { return inflow_plane(c, f, 3); }
+template <class T>
+static const T* inflow_cur_w(const Consts& c, const Fields<T>& f) { return inflow_plane(c, f, 4); }
+template <class T>
+static const T* inflow_inc(const Consts& c, const Fields<T>& f) { return inflow_plane(c, f, 5); }
+
+// mean of the pending u plane, FP64, fixed order (one block)
+template <class T>
+__global__ void k_inflow_mean(Consts c, const T* __restrict__ pu, double* __restrict__ mean) {
+  __shared__ double scratch[32];
+  const int P = c.ny * c.nz;
+  double s = 0.0;
+  for (int q = threadIdx.x; q < P; q += blockDim.x) s += (double)pu[q];
+  s = block_sum(s, scratch);
+  if (threadIdx.x == 0) *mean = s / P;
+}
+
+// the new inflow time level: u_in = pending u - mean + U on face 0, the
+// boundary increments for the x factor, and the current v, w planes
+template <class T>
+__global__ void k_inflow_advance(Consts c, T* __restrict__ blk, const double* __restrict__ mean,
+                                 T* __restrict__ u) {
+  const int P = c.ny * c.nz;
+  const int jk = blockIdx.x * blockDim.x + threadIdx.x;
+  if (jk >= P) return;
+  T* pu = blk;
+  T* pv = blk + P;
+  T* pw = blk + 2 * (size_t)P;
+  T* cv = blk + 3 * (size_t)P;
+  T* cw = blk + 4 * (size_t)P;
+  T* iu = blk + 5 * (size_t)P;
+  T* iv = blk + 6 * (size_t)P;
+  T* iw = blk + 7 * (size_t)P;
+  const T un = (T)((double)pu[jk] - *mean + c.u_in);
+  iu[jk] = un - u[jk];
+  u[jk] = un;
+  const T vn = pv[jk], wn = pw[jk];
+  iv[jk] = vn - cv[jk];
+  iw[jk] = wn - cw[jk];
+  cv[jk] = vn;
+  cw[jk] = wn;
+}
+
+template <class T>
+void launch_inflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
+  if (!f.inflow) return;
+  const int P = c.ny * c.nz;
+  k_inflow_mean<T><<<1, 1024, 0, s>>>(c, f.inflow, f.inflow_mean);
+  k_inflow_advance<T><<<(P + 255) / 256, 256, 0, s>>>(c, f.inflow, f.inflow_mean, f.u[cur]);
+}
+
 template <class T>
 void launch_begin_step(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   const double tol = sizeof(T) == 8 ? 1e-17 : 1e-9;
@@ -1833,7 +1781,7 @@ void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
       const int XR = c.rhs_planes;
       k_rhs_vec<T><<<dim3(c.ny / RV::TJ, (c.nx + XR - 1) / XR), threads, sh, s>>>(
           c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.p, f.n[0], f.n[1], f.n[2], f.d[0], f.d[1],
-          f.d[2], XR);
+          f.d[2], XR, inflow_cur_v(c, f), inflow_cur_w(c, f));
       return;
     }
   }
@@ -1844,12 +1792,13 @@ void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
     const int XR = c.rhs_planes;
     k_rhs_pipe<T, TJR><<<dim3(c.ny / TJR, (c.nx + XR - 1) / XR), RTHREADS, rs * stage, s>>>(
         c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.p, f.n[0], f.n[1], f.n[2], f.d[0], f.d[1],
-        f.d[2], XR, rs);
+        f.d[2], XR, rs, inflow_cur_v(c, f), inflow_cur_w(c, f));
     return;
   }
   k_rhs<T><<<grid3(c, c.nx + 1), dim3(TK, TJ), 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
                                                         f.p, f.n[0], f.n[1], f.n[2], f.d[0],
-                                                        f.d[1], f.d[2]);
+                                                        f.d[1], f.d[2], inflow_cur_v(c, f),
+                                                        inflow_cur_w(c, f));
 }
 
 int outflow_blocks(const Consts& c) { return (c.ny * c.nz + OUT_THREADS - 1) / OUT_THREADS; }
@@ -1872,41 +1821,26 @@ void launch_af_x(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
       const dim3 grid((P + 255) / 256, (c.nx + xv - 1) / xv, 3);
       if (xv == 16)
         k_af_xv<T, 16><<<grid, 256, 0, s>>>(c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1],
-                                            f.e[2], f.dout[0], f.dout[1], f.dout[2]);
+                                            f.e[2], f.dout[0], f.dout[1], f.dout[2],
+                                            inflow_inc(c, f));
       else
         k_af_xv<T, 24><<<grid, 256, 0, s>>>(c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1],
-                                            f.e[2], f.dout[0], f.dout[1], f.dout[2]);
+                                            f.e[2], f.dout[0], f.dout[1], f.dout[2],
+                                            inflow_inc(c, f));
       return;
     }
     // otherwise segments of 32 or 64 planes staged in shared memory by warps
     if (c.afx_planes <= 40) {
       k_af_xr<T, 32><<<dim3((P + 31) / 32, (c.nx + 31) / 32, 3), 32, 0, s>>>(
           c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2], f.dout[0], f.dout[1],
-          f.dout[2]);
+          f.dout[2], inflow_inc(c, f));
     } else {
       k_af_xr<T, 64><<<dim3((P + 31) / 32, (c.nx + 63) / 64, 3), 32, 0, s>>>(
           c, f.prm, tab, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2], f.dout[0], f.dout[1],
-          f.dout[2]);
+          f.dout[2], inflow_inc(c, f));
     }
     (void)cur;
-    return;
   }
-  if constexpr (sizeof(T) == 4) {
-    const int XC = c.afx_planes;
-    const size_t sh = (size_t)(XC + 2 * HMAX) * 32 * sizeof(T);
-    k_af_xc<T><<<dim3((P + 31) / 32, (c.nx + XC - 1) / XC, 3), dim3(32, 8), sh, s>>>(
-        c, f.prm, (const T*)f.tapsf + c.ny + c.nz, f.d[0], f.d[1], f.d[2], f.e[0], f.e[1], f.e[2],
-        f.dout[0], f.dout[1], f.dout[2]);
-    (void)cur;
-    return;
-  }
-  const int nseg = (c.nx + SEG - 1) / SEG;
-  const T* tab;
-  if constexpr (sizeof(T) == 8) tab = (const T*)f.ipt; else tab = (const T*)f.iptf;
-  k_af_x<T><<<dim3((P + 127) / 128, nseg, 3), 128, 0, s>>>(c, f.prm, tab, f.d[0], f.d[1], f.d[2],
-                                                            f.e[0], f.e[1], f.e[2], f.dout[0],
-                                                            f.dout[1], f.dout[2]);
-  (void)cur;
 }
 
 template <class T>
@@ -2024,7 +1958,6 @@ void fluid_set_attributes() {
   cudaFuncSetAttribute(k_rhs_vec<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_rhs_vec<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_rhs_pipe<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024);
-  cudaFuncSetAttribute(k_af_xc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_zc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_z_pipe<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_af_z<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -2045,6 +1978,7 @@ template int partial_count<double>(const Consts&);
   template void launch_begin_step<T>(const Consts&, const Fields<T>&, cudaStream_t);           \
   template void launch_rhs<T>(const Consts&, const Fields<T>&, int, cudaStream_t);             \
   template void launch_af_tables<T>(const Consts&, const Fields<T>&, cudaStream_t);             \
+  template void launch_inflow<T>(const Consts&, const Fields<T>&, int, cudaStream_t);           \
   template void launch_outflow<T>(const Consts&, const Fields<T>&, int, cudaStream_t);         \
   template void launch_af<T>(const Consts&, const Fields<T>&, int, cudaStream_t);              \
   template void launch_af_x<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \

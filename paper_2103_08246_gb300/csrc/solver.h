@@ -24,6 +24,11 @@ struct Fields {
   double* partial;            // per-block partial maxima of the CFL speed
   double* qpart;              // per-block inflow/outflow flux partials
   double* mean00;             // line mean of the Poisson mode (0, 0)
+  // prescribed inflow (null when disabled): 8 planes of ny * nz values:
+  // pending u, v, w (next time level, written by the caller), current v, w
+  // (ghosts of the explicit stage), increments u, v, w (x factor's first row)
+  T* inflow;
+  double* inflow_mean;        // mean of the pending u plane
   int n_partial;
   Params* prm;
 };
@@ -66,6 +71,7 @@ struct Flag {
 // ---- fluid.cu
 template <class T> void launch_begin_step(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_af_tables(const Consts& c, const Fields<T>& f, cudaStream_t s);
+template <class T> void launch_inflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_outflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_af(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
