@@ -241,6 +241,15 @@ int ibm_set_field(ibm_state* s, int which, const double* host, size_t n);
 int ibm_set_inflow(ibm_state* s, const double* u, const double* v, const double* w);
 int ibm_inflow_planes(ibm_state* s, void** u, void** v, void** w);
 
+/* One x-plane of the velocity (precursor dumps, probes): u on face i and
+ * v, w at x = (i + 1/2) h (i = nx: the outflow ghosts), 0 <= i <= nx, ny * nz
+ * values each, index j * nz + k. ibm_get_plane copies them to host doubles
+ * and synchronises; ibm_plane_device returns their device addresses in the
+ * state's precision, valid until the next ibm_step (the velocity buffers
+ * alternate between steps). */
+int ibm_get_plane(ibm_state* s, int i, double* u, double* v, double* w);
+int ibm_plane_device(ibm_state* s, int i, void** u, void** v, void** w);
+
 /* Number of markers (flag vertices first, then bar markers) and their
  * positions at the start of the next step (3 doubles each). */
 int ibm_marker_count(const ibm_state* s, size_t* n);

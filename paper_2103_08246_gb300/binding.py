@@ -25,7 +25,8 @@ IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P = 0, 1, 2, 3
 # every symbol include/ibm.h declares
 SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_flag_state",
            "ibm_stats", "ibm_get_field", "ibm_set_field", "ibm_marker_count", "ibm_get_markers",
-           "ibm_save", "ibm_load", "ibm_set_inflow", "ibm_inflow_planes",
+           "ibm_save", "ibm_load", "ibm_set_inflow", "ibm_inflow_planes", "ibm_get_plane",
+           "ibm_plane_device",
            "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_destroy", "ibm_strerror")
 
@@ -111,6 +112,9 @@ def load(path: str = LIB_PATH):
     lib.ibm_marker_count.argtypes = [vp, ctypes.POINTER(sz)]
     lib.ibm_get_markers.argtypes = [vp, _dp, sz]
     lib.ibm_set_inflow.argtypes = [vp, _dp, _dp, _dp]
+    lib.ibm_get_plane.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp]
+    lib.ibm_plane_device.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(vp)]
     lib.ibm_inflow_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
     lib.ibm_save.argtypes = [vp, ctypes.c_char_p]
     lib.ibm_load.argtypes = [vp, ctypes.c_char_p]
@@ -219,6 +223,18 @@ def ibm_get_markers(state, out):
 def ibm_set_inflow(state, u, v, w):
     a = [np.ascontiguousarray(q, dtype=np.float64) for q in (u, v, w)]
     _check(load().ibm_set_inflow(state, *[_ptr(q) for q in a]), "ibm_set_inflow")
+
+
+def ibm_get_plane(state, i, u, v, w):
+    _check(load().ibm_get_plane(state, int(i), _ptr(u), _ptr(v), _ptr(w)), "ibm_get_plane")
+
+
+def ibm_plane_device(state, i):
+    """Device addresses of x-plane i of u, v, w (valid until the next step)."""
+    ptrs = [ctypes.c_void_p() for _ in range(3)]
+    _check(load().ibm_plane_device(state, int(i), *[ctypes.byref(q) for q in ptrs]),
+           "ibm_plane_device")
+    return tuple(q.value for q in ptrs)
 
 
 def ibm_inflow_planes(state):
@@ -333,6 +349,12 @@ class Solver:
 
     def set_inflow(self, u, v, w):
         ibm_set_inflow(self.state, u, v, w)
+
+    def plane(self, i):
+        wl = self.wl
+        out = [np.empty((wl.ny, wl.nz)) for _ in range(3)]
+        ibm_get_plane(self.state, i, *out)
+        return tuple(out)
 
     def save(self, path):
         ibm_save(self.state, path)

@@ -989,6 +989,36 @@ int ibm_set_field(ibm_state* s, int which, const double* host, size_t n) {
   return upload_f32_staged(s->stream, (float*)ptr, host, n, (double*)s->ff.e[0], stage_capacity(s));
 }
 
+int ibm_plane_device(ibm_state* s, int i, void** u, void** v, void** w) {
+  if (!s || !u || !v || !w || i < 0 || i > s->c.nx) return IBM_EINVAL;
+  const size_t off = (size_t)i * s->c.ny * s->c.nz;
+  if (s->precision == IBM_FP64) {
+    *u = s->fd.u[s->cur] + off;
+    *v = s->fd.v[s->cur] + off;
+    *w = s->fd.w[s->cur] + off;
+  } else {
+    *u = s->ff.u[s->cur] + off;
+    *v = s->ff.v[s->cur] + off;
+    *w = s->ff.w[s->cur] + off;
+  }
+  return IBM_OK;
+}
+
+int ibm_get_plane(ibm_state* s, int i, double* u, double* v, double* w) {
+  if (!s || !u || !v || !w || i < 0 || i > s->c.nx) return IBM_EINVAL;
+  void* p[3];
+  int rc = ibm_plane_device(s, i, &p[0], &p[1], &p[2]);
+  if (rc) return rc;
+  const size_t P = (size_t)s->c.ny * s->c.nz;
+  double* out[3] = {u, v, w};
+  for (int q = 0; q < 3; ++q) {
+    rc = s->precision == IBM_FP64 ? download_field<double>(s->stream, out[q], (double*)p[q], P)
+                                  : download_field<float>(s->stream, out[q], (float*)p[q], P);
+    if (rc) return rc;
+  }
+  return IBM_OK;
+}
+
 int ibm_inflow_planes(ibm_state* s, void** u, void** v, void** w) {
   if (!s || !u || !v || !w || !s->inflow) return IBM_EINVAL;
   const size_t P = (size_t)s->c.ny * s->c.nz;

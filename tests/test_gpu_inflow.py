@@ -7,7 +7,9 @@
   flux is U ly lz exactly and the mass fix balances the outflow;
 * writing the pending planes in device memory (ibm_inflow_planes) gives the
   same result as passing host planes (ibm_set_inflow);
-* the inflow planes travel in checkpoints.
+* the inflow planes travel in checkpoints;
+* plane access (ibm_get_plane, ibm_plane_device) returns the x-planes of the
+  current velocity, so a run can feed its own planes back as inflow.
 """
 import numpy as np
 import pytest
@@ -114,3 +116,23 @@ def test_device_planes_equal_host_planes(lib, tmp_path):
         plain.set_inflow(*_planes(wl, 1))
     for s in (a, b, c, plain):
         s.close()
+
+
+def test_plane_access_and_feedback(lib):
+    from paper_2103_08246_gb300 import binding, inputs
+    wl = _case((20, 32, 32))
+    s = binding.Solver(wl, binding.IBM_FP64, noise=inputs.initial_noise(wl, amp=0.05), inflow=True)
+    s.step(2)
+    u, v, w, _ = s.fields()
+    for i in (0, 7, wl.nx):
+        pu, pv, pw = s.plane(i)
+        assert np.array_equal(pu, u[i]) and np.array_equal(pv, v[i]) and np.array_equal(pw, w[i])
+    ptrs = binding.ibm_plane_device(s.state, 7)
+    dev = torch.as_tensor(_DeviceArray(ptrs[1], (wl.ny, wl.nz), "<f8"), device="cuda")
+    assert np.array_equal(dev.cpu().numpy(), v[7])
+    # recycle plane 7 as the next inflow (a precursor-style feedback)
+    s.set_inflow(*s.plane(7))
+    s.step(1)
+    pu = u[7]
+    assert np.abs(s.field(binding.IBM_FIELD_U)[0] - (pu - pu.mean() + 1.0)).max() < 1e-14
+    s.close()
