@@ -40,7 +40,7 @@ constexpr int TC_TMEM_COLS = 256;
 constexpr uint32_t A_TILE = TC_M * TC_KB * 4;   // bytes of one A part (hi or lo)
 constexpr uint32_t B_TILE = TC_N * TC_KB * 4;
 constexpr uint32_t STAGE = 2 * A_TILE + 2 * B_TILE;   // A_hi, A_lo, B_hi, B_lo
-constexpr int TC_STAGES = 2;
+constexpr int TC_STAGES = 1;   // one operand stage: 96 KB, two CTAs per SM overlap each other
 
 // byte offset of element (row, k) of a K-major tile with TC_KB columns
 __device__ inline uint32_t kmajor_off(int row, int k) {
@@ -113,7 +113,7 @@ struct TcArgs {
   int* error;
 };
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g) {
+__global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc_tf32x3(TcArgs g) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   __shared__ uint64_t done[TC_STAGES];
   __shared__ uint32_t tmem_base;
@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g) {
 
   const int nk = 256 / TC_KB;
   bool ok = true;
-  uint32_t uses[TC_STAGES] = {0, 0};   // commits made on each stage's barrier
+  uint32_t uses[TC_STAGES] = {};   // commits made on each stage's barrier
   load(0);
   for (int kb = 0; kb < nk; ++kb) {
     const int s = kb % TC_STAGES;
