@@ -48,6 +48,12 @@ PER_STEP = {"rhs": 1, "af_x": 1, "af_yz": 1, "mass_div": 1, "dht2d": 2,
 # implicit factors 21, mass fix and divergence 4, pressure solve 10,
 # projection 9): the step's roofline counts these bytes whatever the fusion.
 METHOD_PASSES = 57
+# FP64 path: the explicit stage's FP64 instructions per cell (DFMA + DMUL +
+# DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of
+# GB300 (2 per clock per SM): the FP64 step is bound by that pipe.
+FP64_RHS_INST_PER_CELL = 113.4
+FP64_INST_PER_CLK_SM = 2
+N_SMS = 152
 SAMPLE_NX = 64   # x planes of the CPU sample (the inflow end of the workload)
 
 
@@ -393,10 +399,19 @@ def run_ours(args):
             s64 = binding.Solver(wl, binding.IBM_FP64, noise=inputs.initial_noise(wl))
             s64.step(3)
             ms64 = time_steps(s64, max(5, args.steps // 5), s64.stream)
+            s64.time_stage("rhs", 1)
+            rhs64 = s64.time_stage("rhs", 3)
             s64.close()
+            mhz = clk.get("sm_mhz") or 2070.0
+            peak_inst = FP64_INST_PER_CLK_SM * N_SMS * mhz * 1e6 / 1e9
+            ach_inst = FP64_RHS_INST_PER_CELL * (wl.nx + 1) * wl.ny * wl.nz / (rhs64 * 1e-3) / 1e9
             fp64 = {"steps_per_s": 1000.0 / ms64, "ms_per_step": ms64,
                     "gcell_updates_per_s": wl.cells / ms64 / 1e6,
-                    "speedup_fp32_over_fp64": ms64 / ms}
+                    "speedup_fp32_over_fp64": ms64 / ms,
+                    "roofline": {"kernel": "rhs", "bound": "alu", "unit": "G FP64 inst/s",
+                                 "achieved": ach_inst, "peak": peak_inst,
+                                 "peak_kind": "derived: 2 FP64 inst/clk/SM x 152 SMs x sampled clock",
+                                 "frac": ach_inst / peak_inst, "ms_per_launch": rhs64}}
         mixed = None
         if not args.no_fp64:
             sm = binding.Solver(wl, binding.IBM_MIXED, noise=inputs.initial_noise(wl))

@@ -548,7 +548,9 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
   const T dt = pick<T>(prm->dt, prm->f_dt), alpha = pick<T>(prm->alpha, prm->f_alpha);
   const T beta = pick<T>(prm->beta, prm->f_beta);
   const T nu = pick<T>(c.nu, c.f_nu), ih = pick<T>(c.inv_h, c.f_inv_h);
-  const T ih2 = pick<T>(c.inv_h * c.inv_h, c.f_inv_h2), hf = (T)0.5;
+  const T ih2 = pick<T>(c.inv_h * c.inv_h, c.f_inv_h2);
+  const T qh = (T)0.25 * ih, cdn = dt * nu * ih2, cdg = dt * ih;
+  const T mda = -dt * alpha, mdb = -dt * beta;
   const int mask = nz - 1;
   const int runs = nz / E;                  // runs per row
   const int r = tid / runs;                 // row of this thread in the tile
@@ -646,7 +648,11 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
     const T wa_r = right(wa[0], Wa + R), wbm_r = right(wbm[0], Wb + Rm);
     const T pb_l = left(pb[E - 1], Pb + R);
     T No[E], Do[E];
-    // u on face i (interior faces only)
+    // Flux differences with the halves folded into qh = ih / 4:
+    // (a+b)/2 (c+d)/2 products become (a+b)(c+d), and each face pair is one
+    // product and one fused multiply-add. RHS = -dt alpha N - dt beta N^{n-1}
+    // + dt nu ih^2 Lraw - dt ih (p_c - p_w), every term one FMA.
+    // u on face i (interior faces only; no inflow ghost enters it)
     if (i >= 1) {
       T ua[E], pa[E];
       lds_run<T, E>(Ua + R + k0, ua);
@@ -656,19 +662,14 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
         const T c0 = ub[e];
         const T uzp = e == E - 1 ? ub_r : ub[e + 1], uzm = e == 0 ? ub_l : ub[e - 1];
         const T wap = e == E - 1 ? wa_r : wa[e + 1], wbp1 = e == E - 1 ? wb_r : wb[e + 1];
-        T fxp = hf * (c0 + uc[e]);
-        fxp *= fxp;
-        T fxm = hf * (ua[e] + c0);
-        fxm *= fxm;
-        const T fxy0 = hf * (ubm[e] + c0) * (hf * (sgn * va[e] + vb[e]));
-        const T fxy1 = hf * (c0 + ubp[e]) * (hf * (sgn * vap[e] + vbp[e]));
-        const T fxz0 = hf * (uzm + c0) * (hf * (sgn * wa[e] + wb[e]));
-        const T fxz1 = hf * (c0 + uzp) * (hf * (sgn * wap + wbp1));
-        const T N = (fxp - fxm + fxy1 - fxy0 + fxz1 - fxz0) * ih;
-        const T L = (uc[e] + ua[e] + ubp[e] + ubm[e] + uzp + uzm - (T)6 * c0) * ih2;
-        const T Gp = (pb[e] - pa[e]) * ih;
+        const T sp = c0 + uc[e], sm = ua[e] + c0;
+        const T fx = sp * sp - sm * sm;
+        const T fy = (c0 + ubp[e]) * (vap[e] + vbp[e]) - (ubm[e] + c0) * (va[e] + vb[e]);
+        const T fz = (c0 + uzp) * (wap + wbp1) - (uzm + c0) * (wa[e] + wb[e]);
+        const T N = qh * (fx + fy + fz);
+        const T L = uc[e] + ua[e] + ubp[e] + ubm[e] + uzp + uzm - (T)6 * c0;
         No[e] = N;
-        Do[e] = dt * (-(alpha * N + beta * Np0[e]) - Gp + nu * L);
+        Do[e] = mda * N + (mdb * Np0[e] + (cdn * L - cdg * (pb[e] - pa[e])));
       }
       stg_run<T, E>(n0 + id, No);
       stg_run<T, E>(d0 + id, Do);
@@ -680,19 +681,14 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
       const T vxp = vc[e], vxm = sgn * va[e] + gv[e];
       const T vzp = e == E - 1 ? vb_r : vb[e + 1], vzm = e == 0 ? vb_l : vb[e - 1];
       const T wbp1 = e == E - 1 ? wb_r : wb[e + 1], wbmp1 = e == E - 1 ? wbm_r : wbm[e + 1];
-      const T fxr = hf * (ucm[e] + uc[e]) * (hf * (c0 + vxp));
-      const T fxl = hf * (ubm[e] + ub[e]) * (hf * (vxm + c0));
-      T fyp = hf * (c0 + vbp[e]);
-      fyp *= fyp;
-      T fym = hf * (vbm[e] + c0);
-      fym *= fym;
-      const T fz1 = hf * (c0 + vzp) * (hf * (wbmp1 + wbp1));
-      const T fz0 = hf * (vzm + c0) * (hf * (wbm[e] + wb[e]));
-      const T N = (fxr - fxl + fyp - fym + fz1 - fz0) * ih;
-      const T L = (vxp + vxm + vbp[e] + vbm[e] + vzp + vzm - (T)6 * c0) * ih2;
-      const T Gp = (pb[e] - pbm[e]) * ih;
+      const T fx = (ucm[e] + uc[e]) * (c0 + vxp) - (ubm[e] + ub[e]) * (vxm + c0);
+      const T sp = c0 + vbp[e], sm = vbm[e] + c0;
+      const T fy = sp * sp - sm * sm;
+      const T fz = (c0 + vzp) * (wbmp1 + wbp1) - (vzm + c0) * (wbm[e] + wb[e]);
+      const T N = qh * (fx + fy + fz);
+      const T L = vxp + vxm + vbp[e] + vbm[e] + vzp + vzm - (T)6 * c0;
       No[e] = N;
-      Do[e] = dt * (-(alpha * N + beta * Np1[e]) - Gp + nu * L);
+      Do[e] = mda * N + (mdb * Np1[e] + (cdn * L - cdg * (pb[e] - pbm[e])));
     }
     stg_run<T, E>(n1 + id, No);
     stg_run<T, E>(d1 + id, Do);
@@ -705,19 +701,14 @@ k_rhs_vec(Consts c, Params* __restrict__ prm, const T* __restrict__ u, const T* 
       const T ucl = e == 0 ? uc_l : uc[e - 1], ubl = e == 0 ? ub_l : ub[e - 1];
       const T vbpl = e == 0 ? vbp_l : vbp[e - 1], vbl = e == 0 ? vb_l : vb[e - 1];
       const T pbl = e == 0 ? pb_l : pb[e - 1];
-      const T fxr = hf * (ucl + uc[e]) * (hf * (c0 + wxp));
-      const T fxl = hf * (ubl + ub[e]) * (hf * (wxm + c0));
-      const T fy1 = hf * (vbpl + vbp[e]) * (hf * (c0 + wbp[e]));
-      const T fy0 = hf * (vbl + vb[e]) * (hf * (wbm[e] + c0));
-      T fzp = hf * (c0 + wzp);
-      fzp *= fzp;
-      T fzm = hf * (wzm + c0);
-      fzm *= fzm;
-      const T N = (fxr - fxl + fy1 - fy0 + fzp - fzm) * ih;
-      const T L = (wxp + wxm + wbp[e] + wbm[e] + wzp + wzm - (T)6 * c0) * ih2;
-      const T Gp = (pb[e] - pbl) * ih;
+      const T fx = (ucl + uc[e]) * (c0 + wxp) - (ubl + ub[e]) * (wxm + c0);
+      const T fy = (vbpl + vbp[e]) * (c0 + wbp[e]) - (vbl + vb[e]) * (wbm[e] + c0);
+      const T sp = c0 + wzp, sm = wzm + c0;
+      const T fz = sp * sp - sm * sm;
+      const T N = qh * (fx + fy + fz);
+      const T L = wxp + wxm + wbp[e] + wbm[e] + wzp + wzm - (T)6 * c0;
       No[e] = N;
-      Do[e] = dt * (-(alpha * N + beta * Np2[e]) - Gp + nu * L);
+      Do[e] = mda * N + (mdb * Np2[e] + (cdn * L - cdg * (pb[e] - pbl)));
     }
     stg_run<T, E>(n2 + id, No);
     stg_run<T, E>(d2 + id, Do);
