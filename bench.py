@@ -51,7 +51,7 @@ METHOD_PASSES = 57
 # FP64 path: the explicit stage's FP64 instructions per cell (DFMA + DMUL +
 # DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of
 # GB300 (2 per clock per SM): the FP64 step is bound by that pipe.
-FP64_RHS_INST_PER_CELL = 113.4
+FP64_RHS_INST_PER_CELL = 86.2
 FP64_INST_PER_CLK_SM = 2
 N_SMS = 152
 SAMPLE_NX = 64   # x planes of the CPU sample (the inflow end of the workload)
