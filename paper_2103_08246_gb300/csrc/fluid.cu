@@ -982,7 +982,8 @@ k_af_y(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
 // rho + 1/rho = q, r (q - S - S^{-1}) = (r / rho)(1 - rho S)(1 - rho S^{-1}),
 // so each periodic factor is a forward recursion y_k = b_k / r + rho y_{k-1},
 // a backward recursion z_k = y_k + rho z_{k+1}, and du = rho z.
-//  y: one thread per z column walks its J rows. The periodic past enters
+//  y: one thread per z column walks its J rows (values scaled by r, so the
+//     1/r of the forcing becomes one final factor). The periodic past enters
 //     through a warm-up of H rows before the block (rho^H below the
 //     tolerance); the periodic future through its closed form
 //     z_{j0+J} = (rho y_{j0+J-1} + sum_{q<H} rho^q b_{j0+J+q}) / (1 - rho^2).
@@ -1055,8 +1056,10 @@ k_af_yz(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
   const size_t pb = (size_t)i * ny * NZ;
   const T* in = (comp == 0 ? e0 : comp == 1 ? e1 : e2) + pb;
   T* q = (comp == 0 ? u : comp == 1 ? v : w) + pb;
+  // The recursions run on r-scaled values (y' = r y, z' = r z): the 1/r of
+  // the forcing moves into one final factor rho / r per output.
   const T rho = pick<T>(prm->af_rho, prm->f_rho);
-  const T ir = pick<T>(1.0 / prm->r, prm->f_ir);
+  const T rho_ir = rho * pick<T>(1.0 / prm->r, prm->f_ir);
   const int H = prm->af_h;
   const T inv_1mr2 = (T)1 / ((T)1 - rho * rho);
   // ---- y factor
@@ -1070,7 +1073,7 @@ k_af_yz(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
       for (int t = 0; t < 8; ++t) buf[t] = (m0 + t < H) ? col[(size_t)((jw + t) & ymask) * NZ] : (T)0;
 #pragma unroll
       for (int t = 0; t < 8; ++t)
-        if (m0 + t < H) y = buf[t] * ir + rho * y;
+        if (m0 + t < H) y = buf[t] + rho * y;
       jw = (jw + 8) & ymask;
     }
     T yr[J];
@@ -1078,7 +1081,7 @@ k_af_yz(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
     for (int m = 0; m < J; ++m) yr[m] = col[(size_t)(j0 + m) * NZ];
 #pragma unroll
     for (int m = 0; m < J; ++m) {
-      y = yr[m] * ir + rho * y;
+      y = yr[m] + rho * y;
       yr[m] = y;
     }
     T sf = 0, pw = 1;
@@ -1090,7 +1093,7 @@ k_af_yz(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
 #pragma unroll
       for (int t = 0; t < 8; ++t)
         if (m0 + t < H) {
-          sf += pw * (buf[t] * ir);
+          sf += pw * buf[t];
           pw *= rho;
         }
       jw = (jw + 8) & ymask;
@@ -1100,7 +1103,7 @@ k_af_yz(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
 #pragma unroll
     for (int m = J - 1; m >= 0; --m) {
       z = yr[m] + rho * z;
-      sdu[m * LDP + kp] = rho * z;
+      sdu[m * LDP + kp] = rho_ir * z;
     }
   }
   __syncthreads();
@@ -1134,11 +1137,11 @@ k_af_yz(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
       const int k = lane * E + t;
       x[t] = srow[k + (k >> 5)];
     }
-    // forward: y_k = x_k / r + rho y_{k-1}
+    // forward (r-scaled): y'_k = x_k + rho y'_{k-1}
     T acc = 0;
 #pragma unroll
     for (int t = 0; t < E; ++t) {
-      acc = x[t] * ir + rho * acc;
+      acc = x[t] + rho * acc;
       x[t] = acc;
     }
     T Y = acc, pe = pE;
@@ -1174,7 +1177,7 @@ k_af_yz(Consts c, const Params* __restrict__ prm, const T* __restrict__ e0,
     if (lane == 31) C2 = 0;
     C2 += pr * Pz;
 #pragma unroll
-    for (int t = 0; t < E; ++t) un[t] += rho * (x[t] + rp[E - 1 - t] * C2);
+    for (int t = 0; t < E; ++t) un[t] += rho_ir * (x[t] + rp[E - 1 - t] * C2);
     store_run<T, E>(qrow, un);
   }
 }
