@@ -48,6 +48,12 @@ PER_STEP = {"rhs": 1, "af_x": 1, "af_yz": 1, "mass_div": 1, "dht2d": 2,
 # implicit factors 21, mass fix and divergence 4, pressure solve 10,
 # projection 9): the step's roofline counts these bytes whatever the fusion.
 METHOD_PASSES = 57
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# production FP32 kernels, from one single-pass ncu capture at full size
+# (profiles/dram_traffic_production_fp32.md); valid for the kernels of that
+# capture and to be refreshed whenever one of them changes.
+TRAFFIC_BYTES = {"rhs": 1743.7e6, "project": 1199.9e6, "af_yz": 1156.7e6, "af_x": 755.0e6,
+                 "mass_div": 520.9e6, "poisson_x": 408.2e6, "dht2d": 213.4e6}
 # FP64 path: the explicit stage's FP64 instructions per cell (DFMA + DMUL +
 # DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of
 # GB300 (2 per clock per SM): the FP64 step is bound by that pipe.
@@ -287,7 +293,8 @@ def stage_roofline(wl, precision, peak_gbs, peak_kind):
     achieved = alg_bytes / (stages[dom] * 1e-3) / 1e9
     roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak_gbs,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak_gbs,
-            "traffic": None, "alg_bytes_per_launch": alg_bytes, "ms_per_launch": stages[dom]}
+            "traffic": (TRAFFIC_BYTES.get(dom) if precision == binding.IBM_FP32 else None),
+            "alg_bytes_per_launch": alg_bytes, "ms_per_launch": stages[dom]}
     return roof, stages
 
 
