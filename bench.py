@@ -53,7 +53,7 @@ METHOD_PASSES = 57
 # (profiles/dram_traffic_production_fp32.md); valid for the kernels of that
 # capture and to be refreshed whenever one of them changes.
 TRAFFIC_BYTES = {"rhs": 1743.7e6, "project": 1199.9e6, "af_yz": 1156.7e6, "af_x": 755.0e6,
-                 "mass_div": 520.9e6, "poisson_x": 408.2e6, "dht2d": 213.4e6}
+                 "mass_div": 520.9e6, "poisson_x": 408.2e6}
 # FP64 path: the explicit stage's FP64 instructions per cell (DFMA + DMUL +
 # DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of
 # GB300 (2 per clock per SM): the FP64 step is bound by that pipe.

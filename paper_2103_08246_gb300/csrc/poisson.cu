@@ -109,12 +109,18 @@ k_dht(T* __restrict__ data, int n, int logn, int W, int lines_per_group, size_t 
   }
 }
 
-// ---- 256-point transforms held in the registers of one warp (n = 256)
-// Four-step FFT, N = 8 x 32: lane l holds z[l + 32 m], m = 0..7; an 8-point
-// DFT over m in registers, twiddles W_256^{l p}, then a 32-point decimation-
-// in-frequency DFT across the lanes with shuffles. Lane l ends up holding
-// Z[p + 8 brev5(l)] in register p. Two real lines a, b travel as z = a + i b;
-// the Hartley outputs need Z_k and Z_{N-k}, fetched with one more shuffle.
+// ---- 256-point transforms of one warp (n = 256)
+// Four-step FFT, N = 8 x 32 with n = l + 32 m, k = p + 8 q: lane l holds
+// z[l + 32 m], m = 0..7; an 8-point DFT over m in registers and the twiddles
+// W_256^{l p} leave, for every p, a 32-point DFT over the lanes l. Those are
+// split again as 32 = 8 x 4 (l = a + 4 b, q = e + 8 f): a transpose through
+// the warp's shared buffer gives lane 4 p + a the values b = 0..7, an
+// in-register 8-point DFT over b, twiddles W_32^{a e}, and a 4-point DFT
+// across the lane quad (two shuffle stages, factors +-1 and -i only); lane
+// 4 p + a then holds Z[p + 8 e + 64 f] in register e, f = brev2(a). Two real
+// lines a, b travel as z = a + i b; the Hartley outputs need Z_k and Z_{N-k},
+// which every lane reads back from the shared buffer for k = l + 32 t, so
+// the outputs come out in the input's distribution (lane l: l + 32 t).
 template <class T>
 struct Cx {
   T r, i;
@@ -175,11 +181,11 @@ __device__ inline T shfl_x(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, 
 // 8-point DFTs, and per cross-lane stage (distance d) a sign and a factor
 // that turn both halves of the butterfly into one expression,
 //   lower lane: x + o = (o + x) * 1,   upper lane: (o - x) * W.
+// Twiddles W^{l p} of the first pass, read once from the shared table tw
+// (W_256^t = (cos, -sin)(2 pi t / 256), t = 0..255).
 template <class T>
 struct LaneTw {
   Cx<T> tp[8];
-  Cx<T> ws[5];
-  T sg[5];
 };
 
 template <class T>
@@ -188,43 +194,62 @@ __device__ inline LaneTw<T> lane_twiddles(const Cx<T>* tw) {
   const int l = threadIdx.x & 31;
 #pragma unroll
   for (int p = 0; p < 8; ++p) lt.tp[p] = tw[(l * p) & 255];
-#pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int d = 16 >> s;
-    const bool upper = (l & d) != 0;
-    lt.ws[s] = upper ? tw[((l & (d - 1)) * (128 / d)) & 255] : Cx<T>{(T)1, (T)0};
-    lt.sg[s] = upper ? (T)-1 : (T)1;
-  }
   return lt;
 }
 
+// per-warp shared scratch: the transpose [8][36] and then Z at k + 4 (k / 64)
+constexpr int WFFT_BUF = 8 * 36;
+__device__ inline int zslot(int k) { return k + 4 * (k >> 6); }
+
 template <class T>
-__device__ inline void warp_hartley256(Cx<T> (&x)[8], const LaneTw<T>& lt, T (&ha)[8], T (&hb)[8]) {
+__device__ inline void warp_hartley256(Cx<T> (&x)[8], const LaneTw<T>& lt, const Cx<T>* tw,
+                                       Cx<T>* wb, T (&ha)[8], T (&hb)[8]) {
   const int l = threadIdx.x & 31;
   dft8(x);
 #pragma unroll
   for (int p = 1; p < 8; ++p) x[p] = cmul(x[p], lt.tp[p]);
+  // transpose: lane 4 pp + a takes Y_{a + 4 b}[pp], b = 0..7
 #pragma unroll
-  for (int s = 0; s < 5; ++s) {
-    const int d = 16 >> s;
-    const T sg = lt.sg[s];
-    const Cx<T> w = lt.ws[s];
+  for (int p = 0; p < 8; ++p) wb[p * 36 + l] = x[p];
+  __syncwarp();
+  const int pp = l >> 2, a = l & 3;
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      const Cx<T> o = {shfl_x(x[p].r, d), shfl_x(x[p].i, d)};
-      x[p] = cmul({o.r + sg * x[p].r, o.i + sg * x[p].i}, w);
+  for (int b = 0; b < 8; ++b) x[b] = wb[pp * 36 + a + 4 * b];
+  dft8(x);
+#pragma unroll
+  for (int e = 1; e < 8; ++e) x[e] = cmul(x[e], tw[(8 * a * e) & 255]);   // W_32^{a e}
+  // 4-point DFT across the quad, decimation in frequency
+  {
+    const bool up = (a & 2) != 0, rot = (a & 3) == 3;
+    const T sg = up ? (T)-1 : (T)1;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const Cx<T> o = {shfl_x(x[e].r, 2), shfl_x(x[e].i, 2)};
+      const Cx<T> t = {o.r + sg * x[e].r, o.i + sg * x[e].i};
+      x[e] = rot ? Cx<T>{t.i, -t.r} : t;   // W_4^1 = -i on the odd upper lane
     }
   }
-  const int q = (int)(__brev((unsigned)l) >> 27);
+  {
+    const T sg = (a & 1) ? (T)-1 : (T)1;
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    const int pp = p == 0 ? 0 : 8 - p;
-    const int qq = p == 0 ? ((32 - q) & 31) : 31 - q;
-    const int src = (int)(__brev((unsigned)qq) >> 27);
-    const T wr = shfl(x[pp].r, src), wi = shfl(x[pp].i, src);
-    ha[p] = (T)0.5 * (x[p].r - x[p].i + wr + wi);
-    hb[p] = (T)0.5 * (x[p].r + x[p].i - wr + wi);
+    for (int e = 0; e < 8; ++e) {
+      const Cx<T> o = {shfl_x(x[e].r, 1), shfl_x(x[e].i, 1)};
+      x[e] = {o.r + sg * x[e].r, o.i + sg * x[e].i};
+    }
   }
+  __syncwarp();   // the transpose has been read by every lane
+  const int f = ((a & 1) << 1) | (a >> 1);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) wb[zslot(pp + 8 * e + 64 * f)] = x[e];
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int k = l + 32 * t;
+    const Cx<T> zk = wb[zslot(k)], zr = wb[zslot((256 - k) & 255)];
+    ha[t] = (T)0.5 * (zk.r - zk.i + zr.r + zr.i);
+    hb[t] = (T)0.5 * (zk.r + zk.i - zr.r + zr.i);
+  }
+  __syncwarp();   // the buffer is free for the warp's next transform
 }
 
 template <class T>
@@ -240,6 +265,7 @@ __device__ inline void load_twiddles(Cx<T>* tw, const T* g) {
 template <class T>
 __global__ void __launch_bounds__(256) k_dht_z256(T* __restrict__ data, int nrows, const T* __restrict__ twg) {
   __shared__ Cx<T> tw[256];
+  __shared__ Cx<T> wbuf[8][WFFT_BUF];
   load_twiddles(tw, twg);
   const LaneTw<T> lt = lane_twiddles(tw);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -251,32 +277,20 @@ __global__ void __launch_bounds__(256) k_dht_z256(T* __restrict__ data, int nrow
 #pragma unroll
   for (int m = 0; m < 8; ++m) x[m] = {a[l + 32 * m], b[l + 32 * m]};
   T ha[8], hb[8];
-  warp_hartley256(x, lt, ha, hb);
-  // lane l holds outputs 8 q .. 8 q + 7: two (FP32) or four (FP64) 16-byte stores
-  const int q = (int)(__brev((unsigned)l) >> 27);
-  if constexpr (sizeof(T) == 4) {
-    float4* pa = reinterpret_cast<float4*>(a + 8 * q);
-    float4* pb = reinterpret_cast<float4*>(b + 8 * q);
-    pa[0] = make_float4(ha[0], ha[1], ha[2], ha[3]);
-    pa[1] = make_float4(ha[4], ha[5], ha[6], ha[7]);
-    pb[0] = make_float4(hb[0], hb[1], hb[2], hb[3]);
-    pb[1] = make_float4(hb[4], hb[5], hb[6], hb[7]);
-  } else {
-    double2* pa = reinterpret_cast<double2*>(a + 8 * q);
-    double2* pb = reinterpret_cast<double2*>(b + 8 * q);
+  warp_hartley256(x, lt, tw, wbuf[threadIdx.x >> 5], ha, hb);
+  // lane l holds outputs l + 32 t: coalesced rows
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      pa[t] = make_double2(ha[2 * t], ha[2 * t + 1]);
-      pb[t] = make_double2(hb[2 * t], hb[2 * t + 1]);
-    }
+  for (int t = 0; t < 8; ++t) {
+    a[l + 32 * t] = ha[t];
+    b[l + 32 * t] = hb[t];
   }
 }
 
 // y lines (columns of a plane, ny = 256): a block stages a 256 x 32 tile
 // (coalesced rows), 16 warps transform two columns each, the tile is stored back.
 // Tile element (r, c) sits at r * 33 + ((c + (r >> 5)) & 31): the row pad
-// spreads the column reads over the banks, and the rotation by r / 32 does
-// the same for the transform's output rows 8 q + p (q = 0..31 across lanes).
+// spreads the column reads and writes (rows l + 32 t across the lanes) over
+// the banks. Each warp's FFT scratch follows the tile in shared memory.
 __device__ inline int ytile(int r, int c) { return r * 33 + ((c + (r >> 5)) & 31); }
 
 template <class T>
@@ -284,6 +298,7 @@ __global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Cx<T> tw[256];
   T* s = reinterpret_cast<T*>(smem_raw);   // [256][33]
+  Cx<T>* wbuf = reinterpret_cast<Cx<T>*>(s + 256 * 33) + (threadIdx.x >> 5) * WFFT_BUF;
   const int ct = nz / 32;
   const int plane = blockIdx.x / ct, c0 = (blockIdx.x - plane * ct) * 32;
   T* base = data + (size_t)plane * 256 * nz + c0;
@@ -298,13 +313,12 @@ __global__ void __launch_bounds__(512) k_dht_y256(T* __restrict__ data, int nz, 
 #pragma unroll
   for (int m = 0; m < 8; ++m) x[m] = {s[ytile(l + 32 * m, 2 * w)], s[ytile(l + 32 * m, 2 * w + 1)]};
   T ha[8], hb[8];
-  warp_hartley256(x, lt, ha, hb);
+  warp_hartley256(x, lt, tw, wbuf, ha, hb);
   __syncthreads();
-  const int q = (int)(__brev((unsigned)l) >> 27);
 #pragma unroll
-  for (int p = 0; p < 8; ++p) {
-    s[ytile(p + 8 * q, 2 * w)] = ha[p];
-    s[ytile(p + 8 * q, 2 * w + 1)] = hb[p];
+  for (int t = 0; t < 8; ++t) {
+    s[ytile(l + 32 * t, 2 * w)] = ha[t];
+    s[ytile(l + 32 * t, 2 * w + 1)] = hb[t];
   }
   __syncthreads();
   for (int e = threadIdx.x; e < 256 * 32; e += blockDim.x) {
@@ -330,6 +344,7 @@ k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Cx<T> tw[256];
   T* s = reinterpret_cast<T*>(smem_raw);   // [256][33], element (r, c) at ytile(r, c)
+  Cx<T>* wbuf = reinterpret_cast<Cx<T>*>(s + 256 * 33) + (threadIdx.x >> 5) * WFFT_BUF;
   cg::cluster_group cl = cg::this_cluster();
   const int q = (int)cl.block_rank();
   const int plane = blockIdx.x / DHT2D_CLUSTER;
@@ -352,7 +367,6 @@ k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
   load_twiddles(tw, twy);   // includes __syncthreads
   const LaneTw<T> lt = lane_twiddles(tw);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  const int qb = (int)(__brev((unsigned)l) >> 27);
   constexpr int NW = DHT2D_THREADS / 32;
   // y: column pairs (2 cp, 2 cp + 1) of this tile
   for (int cp = w; cp < 16; cp += NW) {
@@ -360,11 +374,11 @@ k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) x[m] = {s[ytile(l + 32 * m, 2 * cp)], s[ytile(l + 32 * m, 2 * cp + 1)]};
     T ha[8], hb[8];
-    warp_hartley256(x, lt, ha, hb);
+    warp_hartley256(x, lt, tw, wbuf, ha, hb);
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-      s[ytile(p + 8 * qb, 2 * cp)] = ha[p];
-      s[ytile(p + 8 * qb, 2 * cp + 1)] = hb[p];
+    for (int t = 0; t < 8; ++t) {
+      s[ytile(l + 32 * t, 2 * cp)] = ha[t];
+      s[ytile(l + 32 * t, 2 * cp + 1)] = hb[t];
     }
   }
   cl.sync();   // every tile transformed along y (ny = nz: the same twiddles serve z)
@@ -378,21 +392,14 @@ k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
       x[m] = {t[ytile(r0, l)], t[ytile(r0 + 1, l)]};
     }
     T ha[8], hb[8];
-    warp_hartley256(x, lt, ha, hb);
-    // lane l holds outputs 8 qb .. 8 qb + 7 of both rows: 16-byte stores
-    T* a = pbase + (size_t)r0 * 256 + 8 * qb;
+    warp_hartley256(x, lt, tw, wbuf, ha, hb);
+    // lane l holds outputs l + 32 t of both rows: coalesced rows
+    T* a = pbase + (size_t)r0 * 256;
     T* b = a + 256;
-    if constexpr (sizeof(T) == 4) {
-      reinterpret_cast<float4*>(a)[0] = make_float4(ha[0], ha[1], ha[2], ha[3]);
-      reinterpret_cast<float4*>(a)[1] = make_float4(ha[4], ha[5], ha[6], ha[7]);
-      reinterpret_cast<float4*>(b)[0] = make_float4(hb[0], hb[1], hb[2], hb[3]);
-      reinterpret_cast<float4*>(b)[1] = make_float4(hb[4], hb[5], hb[6], hb[7]);
-    } else {
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        reinterpret_cast<double2*>(a)[t] = make_double2(ha[2 * t], ha[2 * t + 1]);
-        reinterpret_cast<double2*>(b)[t] = make_double2(hb[2 * t], hb[2 * t + 1]);
-      }
+    for (int t = 0; t < 8; ++t) {
+      a[l + 32 * t] = ha[t];
+      b[l + 32 * t] = hb[t];
     }
   }
   cl.sync();   // no tile is released while another CTA may still read it
@@ -552,7 +559,7 @@ __global__ void k_poisson_table(Consts c, T* __restrict__ tab) {
 template <class T>
 void launch_dht_y(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   if (c.ny == 256 && c.nz % 32 == 0) {
-    const size_t sh = (size_t)256 * 33 * sizeof(T);
+    const size_t sh = (size_t)256 * 33 * sizeof(T) + 16 * WFFT_BUF * sizeof(Cx<T>);
     k_dht_y256<T><<<c.nx * (c.nz / 32), 512, sh, s>>>(f.phi, c.nz, f.tw_y);
     return;
   }
@@ -596,7 +603,7 @@ void launch_poisson_x(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 template <class T>
 bool launch_dht2d(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   if (c.ny != 256 || c.nz != 256) return false;
-  const size_t sh = (size_t)256 * 33 * sizeof(T);
+  const size_t sh = (size_t)256 * 33 * sizeof(T) + (DHT2D_THREADS / 32) * WFFT_BUF * sizeof(Cx<T>);
   k_dht2d_256<T><<<c.nx * DHT2D_CLUSTER, DHT2D_THREADS, sh, s>>>(f.phi, f.tw_y);
   return true;
 }
