@@ -22,6 +22,10 @@ to check by eye rather than for speed:
                forces by automatic differentiation of the energy, velocity
                Verlet sub-steps (Sec. II.B, last paragraphs).
 * ``solver``   one full time step in the paper's order.
+* ``generator`` the learned inflow generator (a stated reading of the
+               synthetic-inflow perspective of Sec. V): periodic 3x3
+               convolutions, residual network, its gradients, Adam, and the
+               rollout renormalisation.
 
 Every function states the passage it follows. Parity of each function is
 pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``, with one

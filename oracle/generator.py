@@ -1,0 +1,198 @@
+"""Learned inflow generator: plain FP64 oracle of the network, its gradients
+and its optimiser.
+
+TEST INFRASTRUCTURE ONLY (see the package header): nothing on the product
+path imports this module.
+
+The paper closes (Sec. V) by proposing that the costly grid-resolved inflow
+turbulence be replaced by a generated one. The generator here is a stated
+reading of that proposal: an autoregressive convolutional network that
+predicts the next inflow plane of velocity fluctuations from the two
+previous ones, on the periodic y-z plane of the domain (Sec. II.A: periodic
+in y and z).
+
+Feature maps are channels-last arrays [ny, nz, C]. Definitions:
+
+* periodic 3x3 cross-correlation
+      conv(W, X)[y, z, o] = sum_{dy, dz in {-1, 0, 1}} sum_c
+                            W[dy + 1, dz + 1, o, c] X[(y + dy) mod ny, (z + dz) mod nz, c]
+* activation  phi(s) = s (s > 0), s / 8 (s <= 0);  phi'(s) = 1 (s > 0), 1 / 8 (s <= 0)
+* network (L residual blocks of width C, input x with C0 channels):
+      h_1     = conv(W_in, x) + b_in
+      h_{l+1} = h_l + conv(W_l, phi(h_l)) + b_l        l = 1 .. L
+      delta   = conv(W_out, phi(h_{L+1})) + b_out      (3 channels)
+* loss  = mean over batch, pixels and the 3 channels of (delta - target)^2
+* Adam (Kingma & Ba): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+  w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+
+The input x holds the normalised planes q_t (channels 0-2) and q_{t-1}
+(channels 3-5); the remaining input channels are zero.
+
+``bf16=True`` rounds every convolution operand (weights, activations,
+back-propagated gradients) to bfloat16 (round to nearest, ties to even)
+before the FP64 arithmetic: the operand precision of the GPU path, for
+comparisons whose rounding decisions must match. The default is plain FP64.
+
+Parameters are kept in a dict of arrays:
+  W_in [3, 3, C, C0], b_in [C], W[l] [3, 3, C, C], b[l] [C], W_out [3, 3, 3, C], b_out [3].
+The flat order used by the C interface is: W_in, b_in, then for each block
+W_l, b_l, then W_out, b_out, every W in [dy][dz][o][c] order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def bf16_round(a):
+    """Round FP64 values to the nearest bfloat16 (ties to even), returned as FP64."""
+    f = np.asarray(a, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def phi(s):
+    return np.where(s > 0, s, s / 8.0)
+
+
+def dphi(s):
+    return np.where(s > 0, 1.0, 1.0 / 8.0)
+
+
+def conv(W, X):
+    """Periodic 3x3 cross-correlation, W [3, 3, O, C], X [ny, nz, C] -> [ny, nz, O]."""
+    out = np.zeros(X.shape[:2] + (W.shape[2],))
+    for dy in (-1, 0, 1):
+        for dz in (-1, 0, 1):
+            # shifted[y, z] = X[(y + dy) mod ny, (z + dz) mod nz]
+            shifted = np.roll(X, shift=(-dy, -dz), axis=(0, 1))
+            out += np.einsum("yzc,oc->yzo", shifted, W[dy + 1, dz + 1])
+    return out
+
+
+def conv_transpose(W, G):
+    """Adjoint of ``conv`` in its input: [ny, nz, O] -> [ny, nz, C],
+    out[p, c] = sum_tap sum_o W[tap, o, c] G[p - tap, o]."""
+    out = np.zeros(G.shape[:2] + (W.shape[3],))
+    for dy in (-1, 0, 1):
+        for dz in (-1, 0, 1):
+            shifted = np.roll(G, shift=(dy, dz), axis=(0, 1))   # G[p - tap]
+            out += np.einsum("yzo,oc->yzc", shifted, W[dy + 1, dz + 1])
+    return out
+
+
+def conv_weight_grad(G, X):
+    """Gradient of sum(G * conv(W, X)) in W: [3, 3, O, C],
+    dW[tap, o, c] = sum_p G[p, o] X[p + tap, c]."""
+    dW = np.zeros((3, 3, G.shape[2], X.shape[2]))
+    for dy in (-1, 0, 1):
+        for dz in (-1, 0, 1):
+            shifted = np.roll(X, shift=(-dy, -dz), axis=(0, 1))
+            dW[dy + 1, dz + 1] = np.einsum("yzo,yzc->oc", G, shifted)
+    return dW
+
+
+def init_params(rng, width, blocks, in_channels, block_scale=0.1):
+    """He-style initial weights; residual blocks scaled down by ``block_scale``
+    so that the untrained network is close to h -> h; zero biases; the output
+    layer starts small as well."""
+    def he(o, c, scale=1.0):
+        return rng.standard_normal((3, 3, o, c)) * scale * np.sqrt(2.0 / (9 * c))
+    p = {"W_in": he(width, in_channels), "b_in": np.zeros(width),
+         "W": [he(width, width, block_scale) for _ in range(blocks)],
+         "b": [np.zeros(width) for _ in range(blocks)],
+         "W_out": he(3, width, 0.1), "b_out": np.zeros(3)}
+    return p
+
+
+def flatten(p):
+    parts = [p["W_in"].ravel(), p["b_in"]]
+    for W, b in zip(p["W"], p["b"]):
+        parts += [W.ravel(), b]
+    parts += [p["W_out"].ravel(), p["b_out"]]
+    return np.concatenate(parts)
+
+
+def unflatten(v, width, blocks, in_channels):
+    v = np.asarray(v, dtype=np.float64)
+    o = 0
+
+    def take(shape):
+        nonlocal o
+        n = int(np.prod(shape))
+        a = v[o:o + n].reshape(shape)
+        o += n
+        return a.copy()
+    p = {"W_in": take((3, 3, width, in_channels)), "b_in": take((width,)), "W": [], "b": []}
+    for _ in range(blocks):
+        p["W"].append(take((3, 3, width, width)))
+        p["b"].append(take((width,)))
+    p["W_out"] = take((3, 3, 3, width))
+    p["b_out"] = take((3,))
+    assert o == v.size
+    return p
+
+
+def forward(p, x, bf16=False):
+    """Network output delta [ny, nz, 3] and the residual stream h_1 .. h_{L+1}."""
+    r = bf16_round if bf16 else (lambda a: a)
+    hs = [conv(r(p["W_in"]), r(x)) + p["b_in"]]
+    for W, b in zip(p["W"], p["b"]):
+        hs.append(hs[-1] + conv(r(W), r(phi(hs[-1]))) + b)
+    delta = conv(r(p["W_out"]), r(phi(hs[-1]))) + p["b_out"]
+    return delta, hs
+
+
+def loss_and_grads(p, xs, targets, bf16=False):
+    """Mean-square loss over a batch (lists of x and target) and its gradient
+    in every parameter, by the chain rule through the definitions above."""
+    r = bf16_round if bf16 else (lambda a: a)
+    count = sum(t.size for t in targets)
+    g = {"W_in": 0.0, "b_in": 0.0, "W": [0.0] * len(p["W"]), "b": [0.0] * len(p["b"]),
+         "W_out": 0.0, "b_out": 0.0}
+    loss = 0.0
+    for x, t in zip(xs, targets):
+        delta, hs = forward(p, x, bf16)
+        err = delta - t
+        loss += float(np.sum(err * err))
+        gd = 2.0 * err / count
+        top = hs[-1]
+        g["W_out"] = g["W_out"] + conv_weight_grad(r(gd), r(phi(top)))
+        g["b_out"] = g["b_out"] + gd.sum(axis=(0, 1))
+        gh = dphi(top) * conv_transpose(r(p["W_out"]), r(gd))
+        for l in range(len(p["W"]) - 1, -1, -1):
+            h = hs[l]
+            g["W"][l] = g["W"][l] + conv_weight_grad(r(gh), r(phi(h)))
+            g["b"][l] = g["b"][l] + gh.sum(axis=(0, 1))
+            gh = gh + dphi(h) * conv_transpose(r(p["W"][l]), r(gh))
+        g["W_in"] = g["W_in"] + conv_weight_grad(r(gh), r(x))
+        g["b_in"] = g["b_in"] + gh.sum(axis=(0, 1))
+    return loss / count, g
+
+
+def adam_step(w, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update of flat FP64 arrays (t counts from 1); returns new (w, m, v)."""
+    m = b1 * m + (1.0 - b1) * grad
+    v = b2 * v + (1.0 - b2) * grad * grad
+    mh = m / (1.0 - b1 ** t)
+    vh = v / (1.0 - b2 ** t)
+    return w - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def make_input(q_t, q_prev, in_channels):
+    """x = [q_t, q_{t-1}, 0 ...]: planes [ny, nz, 3] -> [ny, nz, in_channels]."""
+    x = np.zeros(q_t.shape[:2] + (in_channels,))
+    x[..., 0:3] = q_t
+    x[..., 3:6] = q_prev
+    return x
+
+
+def renormalise(q, rms_target):
+    """Rollout closure (a stated reading): each component of a generated plane
+    has its plane mean removed and is rescaled to the target rms, so that the
+    emitted inflow keeps the flux (mean) and the turbulence intensity of the
+    training data."""
+    out = q - q.mean(axis=(0, 1))
+    rms = np.sqrt((out * out).mean(axis=(0, 1)))
+    return out * (np.asarray(rms_target) / np.where(rms > 0, rms, 1.0))
