@@ -313,6 +313,76 @@ int ibm_ensemble_create(ibm_state* const* members, int n, void* stream, ibm_ense
 int ibm_ensemble_step(ibm_ensemble* e, double dt, int nsteps);
 void ibm_ensemble_destroy(ibm_ensemble* e);
 
+/* ---- Learned inflow generator ------------------------------------------
+ * The synthetic-inflow alternative that Sec. V of the paper leaves open: an
+ * autoregressive convolutional network that maps the two latest inflow
+ * planes of velocity fluctuations (q_t, q_{t-1}, each 3 components on the
+ * periodic ny x nz plane) to the next one, trained on planes recorded from
+ * a grid-resolved (precursor) run, then rolled out as the prescribed inflow
+ * of a state created with opts->inflow.
+ *
+ * Network (periodic 3 x 3 cross-correlations, phi(s) = s for s > 0, s / 8
+ * otherwise, width 128, `blocks` residual blocks):
+ *   h_1 = conv(W_in, x) + b_in,  x = (q_t, q_{t-1})[:in_channels]
+ *   h_{l+1} = h_l + conv(W_l, phi(h_l)) + b_l
+ *   delta = conv(W_out, phi(h_{L+1})) + b_out,   q_{t+1} = q_t + delta
+ * Convolution operands are bfloat16 (tensor cores), accumulation, residual
+ * streams and the Adam master weights FP32. Loss: mean of (delta - target)^2
+ * over samples, pixels and the 3 components.
+ * Parameters, flat (doubles at the interface): W_in, b_in, then W_l, b_l per
+ * block, then W_out, b_out; every W in [dy + 1][dz + 1][out][in] order, where
+ * out[y][z] += W[dy + 1][dz + 1][o][c] in[(y + dy) mod ny][(z + dz) mod nz][c].
+ * Planes q are normalised: q = (plane - mean) / std per component.
+ * All pointers below are DEVICE pointers unless stated otherwise; the
+ * generator owns its workspace; calls are ordered on `stream` and the ones
+ * that return values synchronise it. Errors: IBM_EINVAL (arguments),
+ * IBM_ENOMEM, IBM_ECUDA, IBM_ETIMEOUT (a bounded device wait ran out). */
+typedef struct ibm_gen ibm_gen;
+typedef struct {
+  int ny, nz;         /* plane: ny >= 1, nz a multiple of 128, ny * nz <= 2^24 */
+  int width;          /* 128 */
+  int blocks;         /* residual blocks, 0 .. 64 */
+  int in_channels;    /* input components used, 1 .. 6 (6: q_t and q_{t-1}) */
+  int batch;          /* most samples per training step, 1 .. 64 */
+  double lr, beta1, beta2, eps;   /* Adam (<= 0: 1e-3, 0.9, 0.999, 1e-8) */
+  void* stream;       /* cudaStream_t (NULL: the default stream) */
+} ibm_gen_config;
+int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out);
+size_t ibm_gen_param_count(const ibm_gen* g);
+/* host arrays of ibm_gen_param_count doubles; set_params also resets Adam */
+int ibm_gen_set_params(ibm_gen* g, const double* w, size_t n);
+int ibm_gen_get_params(ibm_gen* g, double* w, size_t n);
+/* gradients of the last ibm_gen_grad / ibm_gen_train_step */
+int ibm_gen_get_grads(ibm_gen* g, double* d, size_t n);
+/* host arrays of 3: data mean and std of each component (normalisation) and
+ * the rms of normalised q that rollouts keep */
+int ibm_gen_set_norm(ibm_gen* g, const double* mean, const double* std, const double* rms);
+/* q_t, q_prev: [batch][ny][nz][3] normalised; delta out: same layout */
+int ibm_gen_forward(ibm_gen* g, const float* q_t, const float* q_prev, float* delta, int batch);
+/* loss (host double, nullable) and its gradients for targets [batch][ny][nz][3] */
+int ibm_gen_grad(ibm_gen* g, const float* q_t, const float* q_prev, const float* target, int batch,
+                 double* loss);
+/* one Adam step with the stored gradients */
+int ibm_gen_adam_step(ibm_gen* g);
+/* one training step on raw planes [n_planes][3][ny][nz] (FP32, e.g. a
+ * precursor record): sample b predicts plane t_idx[b] + 1 from t_idx[b] and
+ * t_idx[b] - 1 (host ints, 1 <= t < n_planes - 1); gradients, then Adam.
+ * loss (host, nullable): the batch loss before the step. */
+int ibm_gen_train_step(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch,
+                       double* loss);
+/* rollout: start from two raw planes [3][ny][nz] (FP32) */
+int ibm_gen_rollout_init(ibm_gen* g, const float* plane_prev, const float* plane_cur);
+/* generate the next plane: q = q_t + delta, each component's plane mean
+ * removed and its rms set to the `rms` of ibm_gen_set_norm; writes
+ * mean + std * q into u, v, w ([ny][nz], doubles for IBM_FP64, floats
+ * otherwise; any may be NULL), e.g. the pending planes of
+ * ibm_inflow_planes. Asynchronous. */
+int ibm_gen_rollout(ibm_gen* g, void* u, void* v, void* w, int precision);
+/* copy the rollout history (normalised q_t, q_{t-1}, [ny][nz][3]) */
+int ibm_gen_history(ibm_gen* g, float* q_t, float* q_prev);
+int ibm_gen_sync(ibm_gen* g);
+void ibm_gen_destroy(ibm_gen* g);
+
 /* Release the state (and the workspace if the library allocated it). */
 void ibm_destroy(ibm_state* s);
 

@@ -93,19 +93,6 @@ def conv_weight_grad(G, X):
     return dW
 
 
-def init_params(rng, width, blocks, in_channels, block_scale=0.1):
-    """He-style initial weights; residual blocks scaled down by ``block_scale``
-    so that the untrained network is close to h -> h; zero biases; the output
-    layer starts small as well."""
-    def he(o, c, scale=1.0):
-        return rng.standard_normal((3, 3, o, c)) * scale * np.sqrt(2.0 / (9 * c))
-    p = {"W_in": he(width, in_channels), "b_in": np.zeros(width),
-         "W": [he(width, width, block_scale) for _ in range(blocks)],
-         "b": [np.zeros(width) for _ in range(blocks)],
-         "W_out": he(3, width, 0.1), "b_out": np.zeros(3)}
-    return p
-
-
 def flatten(p):
     parts = [p["W_in"].ravel(), p["b_in"]]
     for W, b in zip(p["W"], p["b"]):
@@ -181,10 +168,12 @@ def adam_step(w, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def make_input(q_t, q_prev, in_channels):
-    """x = [q_t, q_{t-1}, 0 ...]: planes [ny, nz, 3] -> [ny, nz, in_channels]."""
+    """x = the first in_channels of [q_t, q_{t-1}], then zeros: planes
+    [ny, nz, 3] -> [ny, nz, in_channels]."""
+    full = np.concatenate([q_t, q_prev], axis=-1)
     x = np.zeros(q_t.shape[:2] + (in_channels,))
-    x[..., 0:3] = q_t
-    x[..., 3:6] = q_prev
+    k = min(6, in_channels)
+    x[..., :k] = full[..., :k]
     return x
 
 

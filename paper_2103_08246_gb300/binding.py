@@ -28,7 +28,11 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_save", "ibm_load", "ibm_set_inflow", "ibm_inflow_planes", "ibm_get_plane",
            "ibm_plane_device",
            "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
-           "ibm_destroy", "ibm_strerror")
+           "ibm_gen_create", "ibm_gen_param_count", "ibm_gen_set_params", "ibm_gen_get_params",
+           "ibm_gen_get_grads", "ibm_gen_set_norm", "ibm_gen_forward", "ibm_gen_grad", "ibm_gen_adam_step",
+           "ibm_gen_train_step", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_history", "ibm_gen_sync",
+           "ibm_gen_destroy", "ibm_destroy", "ibm_strerror")
+_VOID = ("ibm_destroy", "ibm_ensemble_destroy", "ibm_gen_destroy")
 
 STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
           "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11, "poisson": 12,
@@ -63,6 +67,13 @@ class ibm_options(ctypes.Structure):
                 ("rhs_planes", ctypes.c_int), ("afx_planes", ctypes.c_int),
                 ("rhs_stages", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("inflow", ctypes.c_int)]
+
+
+class ibm_gen_config(ctypes.Structure):
+    _fields_ = [("ny", ctypes.c_int), ("nz", ctypes.c_int), ("width", ctypes.c_int),
+                ("blocks", ctypes.c_int), ("in_channels", ctypes.c_int), ("batch", ctypes.c_int),
+                ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class ibm_stats_t(ctypes.Structure):
@@ -122,14 +133,31 @@ def load(path: str = LIB_PATH):
     lib.ibm_ensemble_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.ibm_ensemble_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.ibm_ensemble_destroy.argtypes = [vp]
-    lib.ibm_ensemble_destroy.restype = None
     lib.ibm_destroy.argtypes = [vp]
-    lib.ibm_destroy.restype = None
     lib.ibm_strerror.argtypes = [ctypes.c_int]
     lib.ibm_strerror.restype = ctypes.c_char_p
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.ibm_gen_create.argtypes = [ctypes.POINTER(ibm_gen_config), ctypes.POINTER(vp)]
+    lib.ibm_gen_param_count.argtypes = [vp]
+    lib.ibm_gen_set_params.argtypes = [vp, _dp, sz]
+    lib.ibm_gen_get_params.argtypes = [vp, _dp, sz]
+    lib.ibm_gen_get_grads.argtypes = [vp, _dp, sz]
+    lib.ibm_gen_set_norm.argtypes = [vp, _dp, _dp, _dp]
+    lib.ibm_gen_forward.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    lib.ibm_gen_grad.argtypes = [vp, vp, vp, vp, ctypes.c_int, _dp]
+    lib.ibm_gen_adam_step.argtypes = [vp]
+    lib.ibm_gen_train_step.argtypes = [vp, vp, ctypes.c_int, ip, ctypes.c_int, _dp]
+    lib.ibm_gen_rollout_init.argtypes = [vp, vp, vp]
+    lib.ibm_gen_rollout.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    lib.ibm_gen_history.argtypes = [vp, vp, vp]
+    lib.ibm_gen_sync.argtypes = [vp]
+    lib.ibm_gen_destroy.argtypes = [vp]
     for name in SYMBOLS:
-        if name not in ("ibm_destroy", "ibm_strerror", "ibm_ensemble_destroy"):
+        if name in _VOID:
+            getattr(lib, name).restype = None
+        elif name != "ibm_strerror":
             getattr(lib, name).restype = ctypes.c_int
+    lib.ibm_gen_param_count.restype = sz
     _lib = lib
     return lib
 
@@ -279,6 +307,77 @@ def ibm_destroy(state):
     load().ibm_destroy(state)
 
 
+def ibm_gen_create(cfg):
+    h = ctypes.c_void_p()
+    _check(load().ibm_gen_create(ctypes.byref(cfg), ctypes.byref(h)), "ibm_gen_create")
+    return h
+
+
+def ibm_gen_param_count(gen) -> int:
+    return int(load().ibm_gen_param_count(gen))
+
+
+def ibm_gen_set_params(gen, w):
+    a = np.ascontiguousarray(w, dtype=np.float64)
+    _check(load().ibm_gen_set_params(gen, _ptr(a), a.size), "ibm_gen_set_params")
+
+
+def ibm_gen_get_params(gen, out):
+    _check(load().ibm_gen_get_params(gen, _ptr(out), out.size), "ibm_gen_get_params")
+
+
+def ibm_gen_get_grads(gen, out):
+    _check(load().ibm_gen_get_grads(gen, _ptr(out), out.size), "ibm_gen_get_grads")
+
+
+def ibm_gen_set_norm(gen, mean, std, rms):
+    a = [np.ascontiguousarray(q, dtype=np.float64) for q in (mean, std, rms)]
+    _check(load().ibm_gen_set_norm(gen, *[_ptr(q) for q in a]), "ibm_gen_set_norm")
+
+
+def ibm_gen_forward(gen, q_t, q_prev, delta, batch):
+    _check(load().ibm_gen_forward(gen, q_t, q_prev, delta, int(batch)), "ibm_gen_forward")
+
+
+def ibm_gen_grad(gen, q_t, q_prev, target, batch) -> float:
+    loss = ctypes.c_double(0.0)
+    _check(load().ibm_gen_grad(gen, q_t, q_prev, target, int(batch), ctypes.byref(loss)), "ibm_gen_grad")
+    return loss.value
+
+
+def ibm_gen_adam_step(gen):
+    _check(load().ibm_gen_adam_step(gen), "ibm_gen_adam_step")
+
+
+def ibm_gen_train_step(gen, planes, n_planes, t_idx, with_loss=True):
+    idx = np.ascontiguousarray(t_idx, dtype=np.int32)
+    loss = ctypes.c_double(0.0)
+    _check(load().ibm_gen_train_step(gen, planes, int(n_planes),
+                                     idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), idx.size,
+                                     ctypes.byref(loss) if with_loss else None), "ibm_gen_train_step")
+    return loss.value if with_loss else None
+
+
+def ibm_gen_rollout_init(gen, plane_prev, plane_cur):
+    _check(load().ibm_gen_rollout_init(gen, plane_prev, plane_cur), "ibm_gen_rollout_init")
+
+
+def ibm_gen_rollout(gen, u, v, w, precision):
+    _check(load().ibm_gen_rollout(gen, u, v, w, int(precision)), "ibm_gen_rollout")
+
+
+def ibm_gen_history(gen, q_t, q_prev):
+    _check(load().ibm_gen_history(gen, q_t, q_prev), "ibm_gen_history")
+
+
+def ibm_gen_sync(gen):
+    _check(load().ibm_gen_sync(gen), "ibm_gen_sync")
+
+
+def ibm_gen_destroy(gen):
+    load().ibm_gen_destroy(gen)
+
+
 # ----------------------------------------------------------------- convenience
 class Solver:
     """One solver state on the current CUDA device.
@@ -393,6 +492,93 @@ class Ensemble:
     def close(self):
         if getattr(self, "handle", None) is not None:
             ibm_ensemble_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Generator:
+    """Learned inflow generator (ibm_gen_*): device buffers are torch tensors
+    on the current CUDA device, the stream is torch's unless one is given."""
+
+    def __init__(self, ny, nz, blocks=13, in_channels=6, batch=8, lr=1e-3, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the generator needs a CUDA device")
+        load()
+        self.ny, self.nz, self.blocks, self.in_channels, self.batch = ny, nz, blocks, in_channels, batch
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        cfg = ibm_gen_config(ny, nz, 128, blocks, in_channels, batch, lr, 0.0, 0.0, 0.0,
+                             ctypes.c_void_p(self.stream.cuda_stream))
+        torch.cuda.synchronize()
+        self.handle = ibm_gen_create(cfg)
+        self.n_params = ibm_gen_param_count(self.handle)
+
+    def _dev(self, a):
+        import torch
+        t = torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+        torch.cuda.synchronize()
+        return t
+
+    def set_params(self, w):
+        ibm_gen_set_params(self.handle, w)
+
+    def params(self):
+        out = np.empty(self.n_params)
+        ibm_gen_get_params(self.handle, out)
+        return out
+
+    def grads(self):
+        out = np.empty(self.n_params)
+        ibm_gen_get_grads(self.handle, out)
+        return out
+
+    def set_norm(self, mean, std, rms):
+        ibm_gen_set_norm(self.handle, mean, std, rms)
+
+    def forward(self, q_t, q_prev):
+        """q's [batch, ny, nz, 3] (host arrays or CUDA tensors) -> delta (host)."""
+        import torch
+        qt, qp = self._dev(q_t), self._dev(q_prev)
+        out = torch.empty_like(qt)
+        ibm_gen_forward(self.handle, qt.data_ptr(), qp.data_ptr(), out.data_ptr(), qt.shape[0])
+        return out.cpu().numpy().astype(np.float64)
+
+    def grad(self, q_t, q_prev, target):
+        qt, qp, tg = self._dev(q_t), self._dev(q_prev), self._dev(target)
+        return ibm_gen_grad(self.handle, qt.data_ptr(), qp.data_ptr(), tg.data_ptr(), qt.shape[0])
+
+    def adam_step(self):
+        ibm_gen_adam_step(self.handle)
+
+    def train_step(self, planes, t_idx, with_loss=True):
+        """planes: CUDA float32 tensor [n, 3, ny, nz]."""
+        return ibm_gen_train_step(self.handle, planes.data_ptr(), planes.shape[0], t_idx, with_loss)
+
+    def rollout_init(self, plane_prev, plane_cur):
+        self._init = (self._dev(plane_prev), self._dev(plane_cur))
+        ibm_gen_rollout_init(self.handle, self._init[0].data_ptr(), self._init[1].data_ptr())
+
+    def rollout(self, u, v, w, precision=IBM_FP32):
+        ibm_gen_rollout(self.handle, u, v, w, precision)
+
+    def history(self):
+        import torch
+        qt = torch.empty((self.ny, self.nz, 3), dtype=torch.float32, device="cuda")
+        qp = torch.empty_like(qt)
+        ibm_gen_history(self.handle, qt.data_ptr(), qp.data_ptr())
+        return qt.cpu().numpy().astype(np.float64), qp.cpu().numpy().astype(np.float64)
+
+    def sync(self):
+        ibm_gen_sync(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            ibm_gen_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

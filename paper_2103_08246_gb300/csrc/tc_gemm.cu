@@ -27,8 +27,8 @@
 // memory and returns.
 #include <cstdint>
 
-#include "async_copy.cuh"
 #include "solver.h"
+#include "tcgen05.cuh"
 
 namespace ibm {
 
@@ -53,17 +53,6 @@ __device__ inline uint32_t tf32_bits(float x) {
   return r;
 }
 
-// shared-memory matrix descriptor: K-major, no swizzle
-__device__ inline uint64_t smem_desc(uint32_t saddr) {
-  constexpr uint64_t LBO = 128, SBO = 1024;
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;   // descriptor version of this architecture
-  return d;                 // base offset 0, swizzle none
-}
-
 // instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major
 __host__ __device__ constexpr uint32_t tc_idesc() {
   return (1u << 4)                      // D format F32
@@ -73,6 +62,9 @@ __host__ __device__ constexpr uint32_t tc_idesc() {
          | ((uint32_t)(TC_M >> 4) << 24);
 }
 
+// K-major operand tiles: K-groups 128 bytes apart, 8-row groups 1024 bytes apart
+__device__ inline uint64_t kdesc(uint32_t saddr) { return tc_desc(saddr, 128, 1024); }
+
 __device__ inline void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                               uint32_t accumulate) {
   asm volatile(
@@ -80,29 +72,6 @@ __device__ inline void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, u
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
-}
-
-__device__ inline void tc_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                   smem_u32(bar))
-               : "memory");
-}
-
-__device__ inline void tc_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 struct TcArgs {
@@ -125,11 +94,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc_tf32x3(TcArgs g) {
   const uint32_t sbase = smem_u32(tsm);
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_base)),
-                 "r"(TC_TMEM_COLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_alloc(&tmem_base, TC_TMEM_COLS);
   }
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; ++s) mbar_init(&done[s], 1);
@@ -198,11 +163,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc_tf32x3(TcArgs g) {
 #pragma unroll
     for (int kk = 0; kk < TC_KB / 8; ++kk) {
       const uint32_t ko = (uint32_t)kk * 256;   // two core matrices (K = 8) per step
-      tc_mma(tmem, smem_desc(ah + ko), smem_desc(bh + ko), idesc, (first && kk == 0) ? 0u : 1u);
-      tc_mma(tmem, smem_desc(ah + ko), smem_desc(bl + ko), idesc, 1u);
-      tc_mma(tmem, smem_desc(al + ko), smem_desc(bh + ko), idesc, 1u);
+      tc_mma(tmem, kdesc(ah + ko), kdesc(bh + ko), idesc, (first && kk == 0) ? 0u : 1u);
+      tc_mma(tmem, kdesc(ah + ko), kdesc(bl + ko), idesc, 1u);
+      tc_mma(tmem, kdesc(al + ko), kdesc(bh + ko), idesc, 1u);
     }
-    tc_commit(&done[s]);
+    tc_commit_to(&done[s]);
   };
 
   const int nk = 256 / TC_KB;
@@ -236,7 +201,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc_tf32x3(TcArgs g) {
 #pragma unroll 1
     for (int c0 = 0; c0 < TC_N; c0 += 32) {
       float v[32];
-      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tc_ld_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
       for (int q = 0; q < 32; ++q) plane[(size_t)(c0 + q) * 256] = v[q];
     }
@@ -244,8 +209,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_gemm_tc_tf32x3(TcArgs g) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
-                 : "memory");
+    tc_dealloc(tmem, TC_TMEM_COLS);
 }
 
 }  // namespace

@@ -13,6 +13,9 @@ of the inflow speed U = 1; Sec. II.A of the paper defines the geometry):
                   17x17 vertices, mass ratio 1, bending 0.01, dt = 2e-3.
 * ``production``  512x256x256 cells, domain 8x4x4, Re = 200, same bar grid,
                   flag at x = 3 with 65x65 vertices, bending 0.005, CFL 0.3.
+
+It also draws the inflow generator's initial weights (random numbers the
+training consumes) and synthetic plane sequences for its tests.
 """
 from __future__ import annotations
 
@@ -134,4 +137,61 @@ def ensemble_cases(n: int = 16, seed: int = 0):
             flag_x_le=0.5 + 0.5 * dist, flag_ns=17, flag_nt=17,
             bending=float(10.0 ** rng.uniform(-3.0, -1.0)), dt=-1.0, cfl=0.3,
             steps=100, seed=seed + q))
+    return out
+
+
+def generator_param_count(width: int = 128, blocks: int = 13, in_channels: int = 6) -> int:
+    """Parameters of the inflow generator: W_in, b_in, blocks x (W, b), W_out, b_out."""
+    return 9 * width * in_channels + width + blocks * (9 * width * width + width) + 9 * 3 * width + 3
+
+
+def generator_params(seed: int = 0, width: int = 128, blocks: int = 13, in_channels: int = 6,
+                     block_scale: float = 0.1, out_scale: float = 0.1, bias_std: float = 0.0):
+    """Seeded initial weights of the inflow generator, flat in the interface
+    order (W_in, b_in, then W_l, b_l per block, then W_out, b_out; every W in
+    [dy + 1][dz + 1][out][in] order). Weights are normal with standard
+    deviation sqrt(2 / (9 in)) (He), scaled by ``block_scale`` in the residual
+    blocks (an untrained network is close to h -> h) and by ``out_scale`` in
+    the output layer; biases normal with ``bias_std`` (zero by default)."""
+    rng = np.random.default_rng(seed)
+
+    def he(o, c, scale):
+        return (rng.standard_normal((3, 3, o, c)) * scale * np.sqrt(2.0 / (9 * c))).ravel()
+
+    def bias(n):
+        return rng.standard_normal(n) * bias_std if bias_std > 0 else np.zeros(n)
+    parts = [he(width, in_channels, 1.0), bias(width)]
+    for _ in range(blocks):
+        parts += [he(width, width, block_scale), bias(width)]
+    parts += [he(3, width, out_scale), bias(3)]
+    out = np.concatenate(parts)
+    assert out.size == generator_param_count(width, blocks, in_channels)
+    return out
+
+
+def advected_planes(n: int, ny: int, nz: int, seed: int = 0, shift: int = 1, modes: int = 3,
+                    mean=(1.0, 0.0, 0.0), amp=(0.1, 0.05, 0.05)):
+    """n planes [n, 3, ny, nz] of a smooth periodic random field carried
+    ``shift`` cells in z per plane (frozen turbulence passing a fixed plane):
+    plane t is f(y, z - shift t). f is a sum of random Fourier modes with
+    wavenumbers below ``modes``, scaled per component to rms ``amp`` around
+    ``mean``."""
+    rng = np.random.default_rng(seed)
+    y = np.arange(ny)[:, None]
+    out = np.empty((n, 3, ny, nz))
+    for c in range(3):
+        coef = []
+        for ky in range(-modes + 1, modes):
+            for kz in range(0, modes):
+                if ky == 0 and kz == 0:
+                    continue
+                coef.append((ky, kz, rng.standard_normal(), rng.uniform(0, 2 * np.pi)))
+        for t in range(n):
+            z = (np.arange(nz)[None, :] - shift * t)
+            f = np.zeros((ny, nz))
+            for ky, kz, a, ph in coef:
+                f += a * np.cos(2 * np.pi * (ky * y / ny + kz * z / nz) + ph)
+            out[t, c] = f
+        rms = np.sqrt((out[:, c] ** 2).mean())
+        out[:, c] = mean[c] + amp[c] * out[:, c] / rms
     return out

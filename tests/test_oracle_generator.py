@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 from oracle import generator as gen
+from paper_2103_08246_gb300 import inputs
 
 
 def _brute_conv(W, X):
@@ -51,10 +52,8 @@ def test_adjoints():
 def test_gradient_matches_finite_differences():
     rng = np.random.default_rng(3)
     width, blocks, c0 = 4, 2, 8
-    p = gen.init_params(rng, width, blocks, c0, block_scale=0.5)
-    for b in p["b"] + [p["b_in"], p["b_out"]]:
-        b += 0.1 * rng.standard_normal(b.shape)
-    p["W_out"] *= 10.0
+    p = gen.unflatten(inputs.generator_params(3, width, blocks, c0, block_scale=0.5, out_scale=1.0,
+                                              bias_std=0.1), width, blocks, c0)
     xs = [rng.standard_normal((5, 6, c0)) for _ in range(2)]
     ts = [rng.standard_normal((5, 6, 3)) for _ in range(2)]
     _, g = gen.loss_and_grads(p, xs, ts)
@@ -74,11 +73,18 @@ def test_gradient_matches_finite_differences():
 
 
 def test_flat_order_round_trips():
-    rng = np.random.default_rng(4)
-    p = gen.init_params(rng, 4, 3, 8)
-    v = gen.flatten(p)
+    v = inputs.generator_params(4, 4, 3, 8)
     assert v.size == 9 * 4 * 8 + 4 + 3 * (9 * 16 + 4) + 9 * 3 * 4 + 3
-    assert np.array_equal(gen.flatten(gen.unflatten(v, 4, 3, 8)), v)
+    assert v.size == inputs.generator_param_count(4, 3, 8)
+    p = gen.unflatten(v, 4, 3, 8)
+    assert p["W_in"].shape == (3, 3, 4, 8) and p["W_out"].shape == (3, 3, 3, 4)
+    assert np.array_equal(gen.flatten(p), v)
+
+
+def test_advected_planes_are_shifted_copies():
+    pl = inputs.advected_planes(4, 6, 16, seed=1, shift=1)
+    assert np.allclose(pl[1], np.roll(pl[0], 1, axis=-1), atol=1e-12)
+    assert np.allclose(pl[3], np.roll(pl[0], 3, axis=-1), atol=1e-12)
 
 
 def test_bf16_rounding():
