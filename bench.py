@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 
 METRIC = "fractional steps/s & Gcell-updates/s at 512x256x256, mixed vs FP64, % HBM peak"
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 
 # Algorithmic bytes per launch of each kernel of the step, in units of one
 # scalar field (one read or one write of every cell): the inputs it must read
@@ -106,6 +107,19 @@ def measured_peaks():
         except Exception:
             pass
     return FALLBACK_HBM_GBS, "fallback"
+
+
+def measured_bf16_peak():
+    """Dense bf16 TFLOP/s: the measured burst figure (a kernel timed alone)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            if d.get("bf16_tflops"):
+                return float(d["bf16_tflops"]), "measured bf16 burst"
+        except Exception:
+            pass
+    return FALLBACK_BF16_TFLOPS, "fallback"
 
 
 # ------------------------------------------------------------------ clocks
@@ -369,6 +383,53 @@ def ensemble_rate(steps):
             "precision": "mixed", "shapes": shapes}
 
 
+def generator_flops(P, blocks, cin=6, width=128, cout=3):
+    """Algorithmic FLOPs of the inflow generator per sample: forward, input
+    gradients (every layer but the first) and weight gradients; 2 per
+    multiply-add of each 3 x 3 periodic convolution over P pixels."""
+    conv = lambda ci, co: 2.0 * P * 9 * ci * co
+    fwd = conv(cin, width) + blocks * conv(width, width) + conv(width, cout)
+    dgrad = blocks * conv(width, width) + conv(cout, width)
+    return fwd, fwd + dgrad + fwd
+
+
+def generator_rate(bf16_peak, peak_kind, nrep=10):
+    """The learned inflow generator at the production plane (256 x 256,
+    13 residual blocks of width 128, batch 8): training step, rollout and
+    its dominant kernel (the residual-block convolution) on the tensor
+    cores."""
+    from paper_2103_08246_gb300 import binding, inputs
+    ny = nz = 256
+    blocks, batch = 13, 8
+    gen = binding.Generator(ny, nz, blocks=blocks, in_channels=6, batch=batch)
+    gen.set_params(inputs.generator_params(0, 128, blocks, 6))
+    fwd, train = generator_flops(ny * nz, blocks)
+    ms_train = gen.time("train_step", nrep)
+    ms_fwd = gen.time("forward", nrep)
+    ms_conv = gen.time("conv_fwd", 3 * nrep)
+    ms_dgrad = gen.time("conv_dgrad", 3 * nrep)
+    ms_wgrad = gen.time("conv_wgrad", 3 * nrep)
+    gen.close()
+    g1 = binding.Generator(ny, nz, blocks=blocks, in_channels=6, batch=1)
+    g1.set_params(inputs.generator_params(0, 128, blocks, 6))
+    ms_roll = g1.time("forward", nrep)
+    g1.close()
+    conv_flops = 2.0 * batch * ny * nz * 9 * 128 * 128
+    tf = lambda fl, ms: fl / (ms * 1e-3) / 1e12
+    return {"plane": f"{ny}x{nz}", "blocks": blocks, "width": 128, "batch": batch,
+            "params": inputs.generator_param_count(128, blocks, 6),
+            "train_step_ms": ms_train, "train_samples_per_s": batch / ms_train * 1e3,
+            "train_tflops": tf(batch * train, ms_train),
+            "forward_ms": ms_fwd, "forward_tflops": tf(batch * fwd, ms_fwd),
+            "rollout_forward_ms": ms_roll,
+            "conv_ms": {"fwd": ms_conv, "dgrad": ms_dgrad, "wgrad": ms_wgrad},
+            "roofline": {"kernel": "k_conv<128,128> (residual block, forward)", "bound": "tensor",
+                         "achieved": tf(conv_flops, ms_conv), "peak": bf16_peak, "peak_kind": peak_kind,
+                         "unit": "TFLOP/s", "frac": tf(conv_flops, ms_conv) / bf16_peak,
+                         "traffic": None, "flops_per_launch": conv_flops, "ms_per_launch": ms_conv},
+            "wgrad_tflops": tf(conv_flops, ms_wgrad), "dgrad_tflops": tf(conv_flops, ms_dgrad)}
+
+
 def run_ours(args):
     import torch
     from paper_2103_08246_gb300 import binding, build, inputs
@@ -432,6 +493,9 @@ def run_ours(args):
                      "speedup_over_fp64": (fp64["ms_per_step"] / msm) if fp64 else None,
                      "poisson_ms": poisson_mixed, "max_div": smx["max_div"]}
         ens = None if args.no_fp64 else ensemble_rate(max(5, args.steps // 5))
+        gen = None
+        if not args.no_fp64:
+            gen = generator_rate(*measured_bf16_peak())
         e2e = None if args.no_e2e else e2e_rate(wl, prec, args.steps)
         if e2e is not None:
             e2e["value"] *= world
@@ -453,7 +517,7 @@ def run_ours(args):
             "gcell_updates_per_s": world * wl.cells / ms / 1e6,
             "step_hbm_frac": (step_bytes / (ms * 1e-3) / 1e9) / peak,
             "roofline": roof, "stages_ms": stages, "fp64": fp64, "mixed": mixed,
-            "ensemble": ens, "e2e": e2e,
+            "ensemble": ens, "inflow_generator": gen, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": kernels_per_step * args.steps,
             "dt_last": st["dt"], "cfl_last": st["cfl"], "n_sub": st["n_sub"],

@@ -370,6 +370,26 @@ int ibm_gen_adam_step(ibm_gen* g);
  * loss (host, nullable): the batch loss before the step. */
 int ibm_gen_train_step(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch,
                        double* loss);
+/* loss (host double) of a batch of raw planes as in ibm_gen_train_step,
+ * without gradients or update (validation) */
+int ibm_gen_eval(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch,
+                 double* loss);
+/* training-input noise: ibm_gen_train_step adds std * N(0, 1) to every
+ * normalised input value (q_t and q_{t-1}) and takes the target from the
+ * noisy q_t, so that the network learns to pull perturbed planes back to
+ * the data (a stable rollout). N(0, 1) is Box-Muller of SplitMix64 (Steele,
+ * Lea and Flood 2014) with key seed + (Adam steps done) and counter
+ * (b * ny * nz + pixel) * 6 + input channel. std = 0 (the default) disables it. */
+int ibm_gen_set_noise(ibm_gen* g, double std, unsigned long long seed);
+/* learning rate of the following Adam steps (> 0) */
+int ibm_gen_set_lr(ibm_gen* g, double lr);
+/* mean device time (ms, CUDA events on the generator's stream) over nrep
+ * repetitions after one warm-up, on the data in place: what = 0 training
+ * step (gradients and Adam) of a full batch, 1 forward pass of a full
+ * batch, 2 / 3 / 4 the forward convolution, input-gradient convolution and
+ * weight gradient of the first residual block (blocks >= 1). Changes the
+ * parameters when what = 0. */
+int ibm_gen_time(ibm_gen* g, int what, int nrep, double* ms);
 /* rollout: start from two raw planes [3][ny][nz] (FP32) */
 int ibm_gen_rollout_init(ibm_gen* g, const float* plane_prev, const float* plane_cur);
 /* generate the next plane: q = q_t + delta, each component's plane mean

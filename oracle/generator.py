@@ -177,6 +177,38 @@ def make_input(q_t, q_prev, in_channels):
     return x
 
 
+def splitmix64(key, counter):
+    """SplitMix64 (Steele, Lea and Flood, 2014): the state key + (counter + 1)
+    times the golden gamma 0x9E3779B97F4A7C15, then the finaliser
+    z ^= z >> 30; z *= 0xBF58476D1CE4E5B9; z ^= z >> 27; z *= 0x94D049BB133111EB;
+    z ^= z >> 31 (arithmetic modulo 2^64). Arrays of counters."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(key) + (np.asarray(counter, dtype=np.uint64) + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def normal_from(r):
+    """Box-Muller of the two 32-bit halves: u1 = (hi + 1) / 2^32 in (0, 1],
+    u2 = lo / 2^32, N = sqrt(-2 ln u1) cos(2 pi u2)."""
+    hi = (r >> np.uint64(32)).astype(np.float64)
+    lo = (r & np.uint64(0xFFFFFFFF)).astype(np.float64)
+    u1 = (hi + 1.0) / 2.0 ** 32
+    u2 = lo / 2.0 ** 32
+    return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+
+
+def noisy_inputs(q_t, q_prev, b, noise_std, key):
+    """Training-input noise of sample b: q_t + std N, q_{t-1} + std N with the
+    counters (b P + p) 6 + channel (channels 0-2 for q_t, 3-5 for q_{t-1})."""
+    P = q_t.shape[0] * q_t.shape[1]
+    base = (np.uint64(b) * np.uint64(P) + np.arange(P, dtype=np.uint64)) * np.uint64(6)
+    eps = np.stack([normal_from(splitmix64(key, base + np.uint64(c))) for c in range(6)], axis=-1)
+    eps = eps.reshape(q_t.shape[:2] + (6,))
+    return q_t + noise_std * eps[..., :3], q_prev + noise_std * eps[..., 3:]
+
+
 def renormalise(q, rms_target):
     """Rollout closure (a stated reading): each component of a generated plane
     has its plane mean removed and is rescaled to the target rms, so that the

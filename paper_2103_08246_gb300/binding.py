@@ -30,7 +30,7 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_gen_create", "ibm_gen_param_count", "ibm_gen_set_params", "ibm_gen_get_params",
            "ibm_gen_get_grads", "ibm_gen_set_norm", "ibm_gen_forward", "ibm_gen_grad", "ibm_gen_adam_step",
-           "ibm_gen_train_step", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_history", "ibm_gen_sync",
+           "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_history", "ibm_gen_sync",
            "ibm_gen_destroy", "ibm_destroy", "ibm_strerror")
 _VOID = ("ibm_destroy", "ibm_ensemble_destroy", "ibm_gen_destroy")
 
@@ -147,6 +147,10 @@ def load(path: str = LIB_PATH):
     lib.ibm_gen_grad.argtypes = [vp, vp, vp, vp, ctypes.c_int, _dp]
     lib.ibm_gen_adam_step.argtypes = [vp]
     lib.ibm_gen_train_step.argtypes = [vp, vp, ctypes.c_int, ip, ctypes.c_int, _dp]
+    lib.ibm_gen_eval.argtypes = [vp, vp, ctypes.c_int, ip, ctypes.c_int, _dp]
+    lib.ibm_gen_set_lr.argtypes = [vp, ctypes.c_double]
+    lib.ibm_gen_set_noise.argtypes = [vp, ctypes.c_double, ctypes.c_ulonglong]
+    lib.ibm_gen_time.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp]
     lib.ibm_gen_rollout_init.argtypes = [vp, vp, vp]
     lib.ibm_gen_rollout.argtypes = [vp, vp, vp, vp, ctypes.c_int]
     lib.ibm_gen_history.argtypes = [vp, vp, vp]
@@ -358,6 +362,31 @@ def ibm_gen_train_step(gen, planes, n_planes, t_idx, with_loss=True):
     return loss.value if with_loss else None
 
 
+def ibm_gen_eval(gen, planes, n_planes, t_idx) -> float:
+    idx = np.ascontiguousarray(t_idx, dtype=np.int32)
+    loss = ctypes.c_double(0.0)
+    _check(load().ibm_gen_eval(gen, planes, int(n_planes), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                               idx.size, ctypes.byref(loss)), "ibm_gen_eval")
+    return loss.value
+
+
+def ibm_gen_set_noise(gen, std, seed=0):
+    _check(load().ibm_gen_set_noise(gen, float(std), int(seed)), "ibm_gen_set_noise")
+
+
+def ibm_gen_set_lr(gen, lr):
+    _check(load().ibm_gen_set_lr(gen, float(lr)), "ibm_gen_set_lr")
+
+
+GEN_TIMINGS = {"train_step": 0, "forward": 1, "conv_fwd": 2, "conv_dgrad": 3, "conv_wgrad": 4}
+
+
+def ibm_gen_time(gen, what, nrep) -> float:
+    ms = ctypes.c_double(0.0)
+    _check(load().ibm_gen_time(gen, int(what), int(nrep), ctypes.byref(ms)), "ibm_gen_time")
+    return ms.value
+
+
 def ibm_gen_rollout_init(gen, plane_prev, plane_cur):
     _check(load().ibm_gen_rollout_init(gen, plane_prev, plane_cur), "ibm_gen_rollout_init")
 
@@ -558,6 +587,18 @@ class Generator:
     def train_step(self, planes, t_idx, with_loss=True):
         """planes: CUDA float32 tensor [n, 3, ny, nz]."""
         return ibm_gen_train_step(self.handle, planes.data_ptr(), planes.shape[0], t_idx, with_loss)
+
+    def eval(self, planes, t_idx):
+        return ibm_gen_eval(self.handle, planes.data_ptr(), planes.shape[0], t_idx)
+
+    def set_lr(self, lr):
+        ibm_gen_set_lr(self.handle, lr)
+
+    def set_noise(self, std, seed=0):
+        ibm_gen_set_noise(self.handle, std, seed)
+
+    def time(self, what, nrep=10):
+        return ibm_gen_time(self.handle, GEN_TIMINGS[what] if isinstance(what, str) else what, nrep)
 
     def rollout_init(self, plane_prev, plane_cur):
         self._init = (self._dev(plane_prev), self._dev(plane_cur))

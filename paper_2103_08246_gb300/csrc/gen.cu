@@ -15,24 +15,29 @@
 // gradients) is bfloat16, the residual streams of h and of the gradient FP32.
 //
 // Kernels:
-//  * k_conv: implicit-GEMM convolution, one CTA per 128 pixels of one image
-//    row (nz a multiple of 128) and all N output channels. Per K block (one
-//    tap row dy, 32 input channels) the CTA stages the 130-pixel row segment
-//    (the z halo included) and the three taps' weights with 16-byte cp.async
-//    copies into K-major core-matrix tiles whose pixel dimension is linear in
-//    16-byte rows, so the three z taps are three start addresses of one tile;
-//    one thread issues 3 x 2 MMAs (M = 128, N, K = 16) per block into a
-//    tensor-memory accumulator, three shared-memory stages in flight. The
-//    epilogue (bias, residual, activation, or the activation derivative for
-//    the backward pass) runs on tcgen05.ld rows, one pixel per thread.
+//  * k_conv: implicit-GEMM convolution on tiles of 256 (or 128) pixels of
+//    one image row (nz a multiple of 128) and all N output channels,
+//    persistent (one CTA per SM) and warp-specialised. Per K block (one tap
+//    row dy, 32 input channels) four copy warps stage the haloed row segment
+//    and the three taps' weights with 16-byte cp.async copies into K-major
+//    core-matrix tiles whose pixel dimension is linear in 16-byte rows, so
+//    the three z taps (and the two 128-pixel halves) are start addresses of
+//    one tile; one thread issues 3 x 2 x 2 MMAs (M = 128, N, K = 16) per
+//    block into the tile's two tensor-memory accumulators. Four stages, two
+//    blocks of copies in flight ahead of the MMAs, hand-offs by mbarriers
+//    only. Four epilogue warps (bias, residual, activation, or the
+//    activation derivative of the backward pass; tcgen05.ld rows, one pixel
+//    per thread) drain one tile's accumulators while the MMAs fill the
+//    other buffer.
 //    Forward and input-gradient passes are the same kernel: the input
 //    gradient is a convolution with the flipped, transposed weights.
 //  * k_wgrad: weight gradients dW[tap][o][c] = sum_p G[p][o] X[p + tap][c],
 //    K = pixels: MN-major operand tiles straight from the channels-last maps
 //    (a pixel's channels are one core-matrix row), the three z taps again as
 //    start-address shifts of the haloed tile, three accumulators (one per
-//    tap) in tensor memory; CTAs split the pixels, their partials are summed
-//    in a fixed order (deterministic training).
+//    tap) in tensor memory; blocks of 128 pixels filled by bulk copies from
+//    two threads (one per operand), three stages; CTAs split the pixels,
+//    their partials are summed in a fixed order (deterministic training).
 //  * small kernels: input assembly, loss and its gradient, bias gradients,
 //    Adam, weight packing, rollout statistics and emission.
 // Every mbarrier wait is bounded; on expiry the kernel sets the error flag,
@@ -41,6 +46,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -57,198 +63,292 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int CV_THREADS = 128;
-constexpr int CV_M = 128;                   // pixels per tile
-constexpr int CV_AROWS = CV_M + 2;          // with the z halo
-constexpr uint32_t CV_ALBO = 138 * 16;      // K-group strip of the A tile (= 32 mod 128: no bank conflicts)
-constexpr int CV_STAGES = 3;
+constexpr int CV_THREADS = 256;
+constexpr int CV_STAGES = 4;
 
-template <int N, int KC>
+template <int N, int KC, int TM>
 struct ConvCfg {
   static constexpr int KB = KC < 32 ? KC : 32;     // input channels per K block
   static constexpr int KG = KB / 8;                // 16-byte K groups per block
   static constexpr int CB = KC / KB;               // channel blocks
   static constexpr int NK = 3 * CB;                // K blocks: tap rows x channel blocks
-  static constexpr uint32_t A_BYTES = KG * CV_ALBO;
+  static constexpr int AROWS = TM + 2;             // pixels with the z halo
+  // K-group strip of the A tile: the haloed rows, rounded to = 32 mod 128 bytes
+  // (the 8 threads of a shared-store phase then hit 8 distinct bank groups)
+  static constexpr uint32_t ALBO = ((AROWS * 16 + 127 - 32) / 128) * 128 + 32;
+  static constexpr uint32_t A_BYTES = KG * ALBO;
   static constexpr uint32_t B_LBO = N * 16 + 32;   // K-group strip of one tap's weights
   static constexpr uint32_t B_TAP = KG * B_LBO;
   static constexpr uint32_t STAGE = ((A_BYTES + 3 * B_TAP + 127) / 128) * 128;
-  static constexpr uint32_t SMEM = CV_STAGES * STAGE;
-  static constexpr uint32_t TMEM_COLS = N < 32 ? 32 : N;
+  // a CTA holding all 512 tensor-memory columns asks for enough shared
+  // memory that no second CTA fits on its SM
+  static constexpr uint32_t SMEM =
+      (2 * (TM / 128) * N >= 512 && CV_STAGES * STAGE < 120 * 1024) ? 120 * 1024 : CV_STAGES * STAGE;
 };
 
 __device__ inline float phi(float s) { return s > 0.f ? s : 0.125f * s; }
 
+// bfloat16 maps are stored in 16-byte granules of 8 channels, pixel-fastest
+// within a channel group: granule (row, group, z) at ((row C/8 + group) nz + z),
+// so that one channel group of a run of pixels is contiguous (one bulk copy)
+__host__ __device__ inline size_t granule(size_t row, int group, int z, int C, int nz) {
+  return (row * (size_t)(C / 8) + group) * nz + z;
+}
+
+// byte offset of weight (tap, row n, input channel k) in the shared-memory
+// image of a convolution's B operand: per K block (tap row, channel block)
+// the three taps' K-group strips of N rows x 16 bytes (+ 32 bytes of pad),
+// exactly as a stage holds them, so that one bulk copy fills a stage
+__host__ __device__ inline size_t wimg_off(int tap, int n, int k, int N, int KC) {
+  const int KB = KC < 32 ? KC : 32, KG = KB / 8, CB = KC / KB;
+  const size_t lbo = (size_t)N * 16 + 32;
+  const int dyi = tap / 3, t = tap % 3, cb = k / KB, kg = (k % KB) / 8, e = k % 8;
+  return ((((size_t)(dyi * CB + cb) * 3 + t) * KG + kg) * lbo) + (size_t)n * 16 + (size_t)e * 2;
+}
+__host__ __device__ inline size_t wimg_bytes(int N, int KC) { return (size_t)9 * (KC / 8) * ((size_t)N * 16 + 32); }
+
+// 1-D bulk copy of `bytes` to a shared address, completing on `bar`
+__device__ inline void bulk_g2s_u32(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst), "l"(src),
+      "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// granules z = zs .. zs + n - 1 (periodic in nz, n <= nz + 2) of one channel
+// group of one image row, contiguous at dst: one to three bulk copies
+__device__ inline void copy_strip(uint32_t dst, const bf16* map, size_t first_granule, int nz, int zs, int n,
+                                  uint64_t* bar) {
+  const char* base = reinterpret_cast<const char*>(map) + first_granule * 16;
+  int done = 0, z = zs;
+  if (z < 0) {
+    bulk_g2s_u32(dst, base + (size_t)(nz + z) * 16, (uint32_t)(-z) * 16, bar);
+    done = -z;
+    z = 0;
+  }
+  const int m = min(n - done, nz - z);
+  bulk_g2s_u32(dst + (uint32_t)done * 16, base + (size_t)z * 16, (uint32_t)m * 16, bar);
+  done += m;
+  if (done < n) bulk_g2s_u32(dst + (uint32_t)done * 16, base, (uint32_t)(n - done) * 16, bar);
+}
+
 struct ConvArgs {
-  const bf16* in;      // [pixels][KC]
-  const bf16* w;       // [9 taps][N][KC]
+  const bf16* in;      // KC-channel map, granule layout
+  const unsigned char* w;   // B-operand image (wimg_off)
   int ny, nz, rows;    // rows = samples * ny
   // epilogue: val = acc * (dact ? phi'(dact) : 1) + bias + res
-  const bf16* dact;    // [pixels][N] or null
+  const bf16* dact;    // N-channel map (granule layout) or null
   const float* bias;   // [nbias] or null
   int nbias;
   const float* res;    // [pixels][N] or null
   float* out32;        // [pixels][ld32], channels < n32 (null: none)
   int ld32, n32;
-  bf16* out16;         // [pixels][N] (null: none)
+  bf16* out16;         // N-channel map, granule layout (null: none)
   int out16_phi;       // out16 = phi(val) instead of val
   int* error;
 };
 
-template <int N, int KC>
-__global__ void __launch_bounds__(CV_THREADS, 2) k_conv(ConvArgs g) {
-  using C = ConvCfg<N, KC>;
+// epilogue of CW accumulator columns c0 .. c0 + CW - 1 of pixel p = (row, z)
+// (16-byte accesses, the loads of a chunk issued before the arithmetic; the
+// bfloat16 granules of consecutive lanes are consecutive)
+template <int N, int CW>
+__device__ inline void conv_epilogue(const ConvArgs& g, size_t row, int z, int c0, float (&v)[CW]) {
+  const size_t p = row * g.nz + z;
+  if (g.dact) {
+    uint4 raw[CW / 8];
+#pragma unroll
+    for (int q = 0; q < CW / 8; ++q)
+      raw[q] = *reinterpret_cast<const uint4*>(g.dact + granule(row, c0 / 8 + q, z, N, g.nz) * 8);
+#pragma unroll
+    for (int q = 0; q < CW / 8; ++q) {
+      const bf16* e = reinterpret_cast<const bf16*>(&raw[q]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[8 * q + j] *= (__bfloat162float(e[j]) > 0.f) ? 1.f : 0.125f;
+    }
+  }
+  if (g.bias) {
+#pragma unroll
+    for (int q = 0; q < CW; ++q) v[q] += (c0 + q < g.nbias) ? g.bias[c0 + q] : 0.f;
+  }
+  if (g.res) {
+    float4 t[CW / 4];
+    const float* rr = g.res + p * N + c0;
+#pragma unroll
+    for (int q = 0; q < CW / 4; ++q) t[q] = *reinterpret_cast<const float4*>(rr + 4 * q);
+#pragma unroll
+    for (int q = 0; q < CW / 4; ++q) {
+      v[4 * q] += t[q].x; v[4 * q + 1] += t[q].y; v[4 * q + 2] += t[q].z; v[4 * q + 3] += t[q].w;
+    }
+  }
+  if (g.out32) {
+    float* o = g.out32 + p * g.ld32 + c0;
+    if (g.ld32 == N) {
+#pragma unroll
+      for (int q = 0; q < CW; q += 4)
+        *reinterpret_cast<float4*>(o + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < CW; ++q)
+        if (c0 + q < g.n32) o[q] = v[q];
+    }
+  }
+  if (g.out16) {
+#pragma unroll
+    for (int q = 0; q < CW / 8; ++q) {
+      uint4 raw;
+      bf16* e = reinterpret_cast<bf16*>(&raw);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float x = v[8 * q + j];
+        e[j] = __float2bfloat16_rn(g.out16_phi ? phi(x) : x);
+      }
+      *reinterpret_cast<uint4*>(g.out16 + granule(row, c0 / 8 + q, z, N, g.nz) * 8) = raw;
+    }
+  }
+}
+
+// Persistent, warp-specialised: CTA c takes tiles c, c + gridDim.x, ... (a
+// tile is TM consecutive pixels of one image row, all N output channels).
+//  * warp 0 (one thread) copies: for each K block j of the CTA's tiles (one
+//    sequence over its tiles) it waits for the stage to be free (the tensor
+//    core's commit of block j - STAGES), announces the stage's bytes on its
+//    `full` barrier and issues bulk copies: per K group the haloed run of
+//    pixels (one to three copies), and the three taps' weights (one copy of
+//    the pre-packed image);
+//  * warp 1 (one thread) waits for `full`, issues the block's MMAs into the
+//    tile's tensor-memory buffer (two buffers, alternating by tile) and
+//    commits them to the stage's `empty` barrier, after the tile's last
+//    block also to the buffer's `tfull` barrier;
+//  * warps 4-7 run the epilogue of tile i from its buffer while the MMAs of
+//    tile i + 1 fill the other one, then arrive on the buffer's `tempty`.
+template <int N, int KC, int TM>
+__global__ void __launch_bounds__(CV_THREADS, 1) k_conv(ConvArgs g) {
+  using C = ConvCfg<N, KC, TM>;
+  constexpr int BUF_COLS = (TM / 128) * N;                       // one tile's accumulators
+  constexpr uint32_t COLS = 2 * BUF_COLS < 32 ? 32 : 2 * BUF_COLS;
+  constexpr uint32_t A_TX = (uint32_t)C::KG * C::AROWS * 16;
+  constexpr uint32_t B_TX = 3 * C::B_TAP;
   extern __shared__ __align__(1024) unsigned char csm[];
-  __shared__ uint64_t done[CV_STAGES];
+  __shared__ uint64_t full[CV_STAGES], empty[CV_STAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tiles_per_row = g.nz / CV_M;
-  const int row = blockIdx.x / tiles_per_row;            // sample * ny + y
-  const int z0 = (blockIdx.x - row * tiles_per_row) * CV_M;
-  const int b = row / g.ny, y = row - b * g.ny;
+  const int tiles_per_row = g.nz / TM;
+  const int ntiles = g.rows * tiles_per_row;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int total = my_tiles * C::NK;
   const uint32_t sbase = smem_u32(csm);
 
-  if (warp == 0) tc_alloc(&tmem_slot, C::TMEM_COLS);
+  if (warp == 0) tc_alloc(&tmem_slot, COLS);
   if (tid == 0) {
-    for (int s = 0; s < CV_STAGES; ++s) mbar_init(&done[s], 1);
+    for (int s = 0; s < CV_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
     fence_mbar_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-
-  auto load = [&](int kb, int s) {
-    const int dyi = kb / C::CB, cb = kb - dyi * C::CB;
-    int yy = y + dyi - 1;
-    yy += (yy < 0) ? g.ny : 0;
-    yy -= (yy >= g.ny) ? g.ny : 0;
-    const size_t rbase = (size_t)(b * g.ny + yy) * g.nz;
-    const uint32_t sa = sbase + (uint32_t)s * C::STAGE;
-    for (int e = tid; e < CV_AROWS * C::KG; e += CV_THREADS) {
-      const int r = e / C::KG, kg = e - r * C::KG;
-      int z = z0 - 1 + r;
-      z += (z < 0) ? g.nz : 0;
-      z -= (z >= g.nz) ? g.nz : 0;
-      cp_async16(sa + (uint32_t)kg * CV_ALBO + (uint32_t)r * 16,
-                 g.in + (rbase + z) * KC + cb * C::KB + kg * 8);
-    }
-    const uint32_t sb = sa + C::A_BYTES;
-    for (int e = tid; e < 3 * N * C::KG; e += CV_THREADS) {
-      const int kg = e % C::KG, n = (e / C::KG) % N, t = e / (C::KG * N);
-      cp_async16(sb + (uint32_t)t * C::B_TAP + (uint32_t)kg * C::B_LBO + (uint32_t)n * 16,
-                 g.w + ((size_t)((dyi * 3 + t) * N + n)) * KC + cb * C::KB + kg * 8);
-    }
-  };
-  constexpr uint32_t idesc = tc_idesc_bf16(CV_M, N, false, false);
-  auto issue = [&](int kb, int s) {
-    const uint32_t sa = sbase + (uint32_t)s * C::STAGE;
-    const uint32_t sb = sa + C::A_BYTES;
-#pragma unroll
-    for (int t = 0; t < 3; ++t)
-#pragma unroll
-      for (int kk = 0; kk < C::KB / 16; ++kk) {
-        const uint64_t ad = tc_desc(sa + (uint32_t)t * 16 + (uint32_t)kk * 2 * CV_ALBO, CV_ALBO, 128);
-        const uint64_t bd = tc_desc(sb + (uint32_t)t * C::B_TAP + (uint32_t)kk * 2 * C::B_LBO, C::B_LBO, 128);
-        tc_mma_bf16(tmem, ad, bd, idesc, (kb == 0 && t == 0 && kk == 0) ? 0u : 1u);
-      }
-    tc_commit_to(&done[s]);
-  };
-
   bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int j = 0; j < total; ++j) {
+        const int s = j % CV_STAGES;
+        if (j >= CV_STAGES) ok = mbar_wait(&empty[s], (uint32_t)((j - CV_STAGES) / CV_STAGES) & 1u) && ok;
+        const int tile = blockIdx.x + (j / C::NK) * gridDim.x;
+        const int kb = j % C::NK;
+        const int row = tile / tiles_per_row, z0 = (tile - row * tiles_per_row) * TM;
+        const int b = row / g.ny, y = row - b * g.ny;
+        const int dyi = kb / C::CB, cb = kb - dyi * C::CB;
+        int yy = y + dyi - 1;
+        yy += (yy < 0) ? g.ny : 0;
+        yy -= (yy >= g.ny) ? g.ny : 0;
+        const size_t rr = (size_t)(b * g.ny + yy);
+        const uint32_t sa = sbase + (uint32_t)s * C::STAGE;
+        mbar_arrive_expect_tx(&full[s], A_TX + B_TX);
 #pragma unroll
-  for (int i = 0; i < CV_STAGES - 1; ++i) {
-    if (i < C::NK) load(i, i);
-    cp_async_commit();
-  }
-  for (int kb = 0; kb < C::NK; ++kb) {
-    const int s = kb % CV_STAGES;
-    const int kn = kb + CV_STAGES - 1;
-    if (kn < C::NK) {
-      const int sn = kn % CV_STAGES;
-      // the stage's previous MMAs (block kn - STAGES) must be done before it is overwritten
-      if (kn >= CV_STAGES) ok = mbar_wait(&done[sn], (uint32_t)((kn - CV_STAGES) / CV_STAGES) & 1u) && ok;
-      load(kn, sn);
+        for (int kg = 0; kg < C::KG; ++kg)
+          copy_strip(sa + (uint32_t)kg * C::ALBO, g.in, granule(rr, cb * C::KG + kg, 0, KC, g.nz), g.nz, z0 - 1,
+                     C::AROWS, &full[s]);
+        bulk_g2s_u32(sa + C::A_BYTES, g.w + (size_t)(dyi * C::CB + cb) * B_TX, B_TX, &full[s]);
+      }
     }
-    cp_async_commit();
-    cp_async_wait<CV_STAGES - 1>();   // this thread's copies of block kb have landed
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      issue(kb, s);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc_bf16(128, N, false, false);
+      for (int j = 0; j < total; ++j) {
+        const int s = j % CV_STAGES;
+        const int lt = j / C::NK, kb = j % C::NK;
+        // the buffer's previous tile (lt - 2) must have been read out
+        if (kb == 0 && lt >= 2) ok = mbar_wait(&tempty[lt & 1], (uint32_t)((lt - 2) / 2) & 1u) && ok;
+        ok = mbar_wait(&full[s], (uint32_t)(j / CV_STAGES) & 1u) && ok;
+        tc_fence_after();
+        const uint32_t dbase = tmem + (uint32_t)((lt & 1) * BUF_COLS);
+        const uint32_t sa = sbase + (uint32_t)s * C::STAGE;
+        const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+#pragma unroll
+          for (int kk = 0; kk < C::KB / 16; ++kk) {
+            const uint64_t bd =
+                tc_desc(sb + (uint32_t)t * C::B_TAP + (uint32_t)kk * 2 * C::B_LBO, C::B_LBO, 128);
+#pragma unroll
+            for (int h = 0; h < TM / 128; ++h) {   // 128-pixel halves: rows h * 128 .. of the tile
+              const uint64_t ad =
+                  tc_desc(sa + (uint32_t)(t + h * 128) * 16 + (uint32_t)kk * 2 * C::ALBO, C::ALBO, 128);
+              tc_mma_bf16(dbase + (uint32_t)(h * N), ad, bd, idesc, (kb == 0 && t == 0 && kk == 0) ? 0u : 1u);
+            }
+          }
+        tc_commit_to(&empty[s]);
+        if (kb == C::NK - 1) tc_commit_to(&tfull[lt & 1]);
+      }
     }
-  }
-  ok = mbar_wait(&done[(C::NK - 1) % CV_STAGES], (uint32_t)((C::NK - 1) / CV_STAGES) & 1u) && ok;
-  ok = __syncthreads_and(ok) != 0;
-  tc_fence_after();
-  if (!ok && tid == 0) atomicOr(g.error, ERR_TIMEOUT);
-  if (ok) {
-    const size_t p = (size_t)row * g.nz + z0 + warp * 32 + lane;
+  } else if (warp >= 4) {
+    // epilogue warps: lane quarter warp - 4, all columns, both halves
+    const int quarter = warp - 4;
     constexpr int CW = N < 32 ? N : 32;
+    for (int lt = 0; lt < my_tiles; ++lt) {
+      const int tile = blockIdx.x + lt * gridDim.x;
+      const int row = tile / tiles_per_row, z0 = (tile - row * tiles_per_row) * TM;
+      ok = mbar_wait(&tfull[lt & 1], (uint32_t)(lt / 2) & 1u) && ok;
+      tc_fence_after();
+      const uint32_t dbase = tmem + (uint32_t)((lt & 1) * BUF_COLS);
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += CW) {
-      float v[CW];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      if constexpr (CW == 32) tc_ld_x32(ta, v); else tc_ld_x16(ta, v);
-      if (g.dact) {
-        const bf16* da = g.dact + p * N + c0;
-#pragma unroll
-        for (int q = 0; q < CW; q += 8) {
-          const uint4 raw = *reinterpret_cast<const uint4*>(da + q);
-          const bf16* e = reinterpret_cast<const bf16*>(&raw);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) v[q + j] *= (__bfloat162float(e[j]) > 0.f) ? 1.f : 0.125f;
+      for (int h = 0; h < TM / 128; ++h) {
+        const int z = z0 + h * 128 + quarter * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < N; c0 += CW) {
+          float v[CW];
+          const uint32_t ta = dbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(h * N + c0);
+          if constexpr (CW == 32) tc_ld_x32(ta, v); else tc_ld_x16(ta, v);
+          conv_epilogue<N, CW>(g, (size_t)row, z, c0, v);
         }
       }
-      if (g.bias) {
-#pragma unroll
-        for (int q = 0; q < CW; ++q) v[q] += (c0 + q < g.nbias) ? g.bias[c0 + q] : 0.f;
-      }
-      if (g.res) {
-        const float* rr = g.res + p * N + c0;
-#pragma unroll
-        for (int q = 0; q < CW; q += 4) {
-          const float4 t = *reinterpret_cast<const float4*>(rr + q);
-          v[q] += t.x; v[q + 1] += t.y; v[q + 2] += t.z; v[q + 3] += t.w;
-        }
-      }
-      if (g.out32) {
-        float* o = g.out32 + p * g.ld32 + c0;
-        if (g.ld32 == N) {
-#pragma unroll
-          for (int q = 0; q < CW; q += 4)
-            *reinterpret_cast<float4*>(o + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-        } else {
-#pragma unroll
-          for (int q = 0; q < CW; ++q)
-            if (c0 + q < g.n32) o[q] = v[q];
-        }
-      }
-      if (g.out16) {
-        bf16* o = g.out16 + p * N + c0;
-#pragma unroll
-        for (int q = 0; q < CW; q += 8) {
-          uint4 raw;
-          bf16* e = reinterpret_cast<bf16*>(&raw);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) e[j] = __float2bfloat16_rn(g.out16_phi ? phi(v[q + j]) : v[q + j]);
-          *reinterpret_cast<uint4*>(o + q) = raw;
-        }
-      }
+      tc_fence_before();
+      mbar_arrive(&tempty[lt & 1]);
     }
   }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tc_dealloc(tmem, C::TMEM_COLS);
+  // every MMA has completed once the last tile's buffer was committed
+  if (tid == 32 && my_tiles > 0)
+    ok = mbar_wait(&tfull[(my_tiles - 1) & 1], (uint32_t)((my_tiles - 1) / 2) & 1u) && ok;
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok && tid == 0) atomicOr(g.error, ERR_TIMEOUT);
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tmem, COLS);
 }
 
 // ---- weight gradients
-constexpr int WG_THREADS = 128;
-constexpr int WG_KP = 64;                  // pixels per K block
-constexpr uint32_t WG_SBO_H = 67 * 16;     // 8-channel strip, 66 haloed rows (odd x 16: no bank conflicts)
-constexpr uint32_t WG_SBO_P = 65 * 16;     // 8-channel strip, 64 rows
-constexpr int WG_STAGES = 4;
+constexpr int WG_THREADS = 256;
+constexpr int WG_KP = 128;                 // pixels per K block
+constexpr uint32_t WG_SBO_H = 131 * 16;    // 8-channel strip, 130 haloed rows (odd x 16: no bank conflicts)
+constexpr uint32_t WG_SBO_P = 129 * 16;    // 8-channel strip, 128 rows
+constexpr int WG_STAGES = 3;
 
 template <int NB>
 struct WgCfg {
@@ -258,8 +358,8 @@ struct WgCfg {
 };
 
 struct WgArgs {
-  const bf16* a;      // [pixels][128]: the M operand
-  const bf16* b;      // [pixels][NB]:  the N operand
+  const bf16* a;      // 128-channel map (granule layout): the M operand
+  const bf16* b;      // NB-channel map (granule layout): the N operand
   int shift_a;        // the tap shift p + tap applies to a (else to b)
   int ny, nz, rows;   // rows = samples * ny
   int chunks;         // CTAs per tap row (gridDim.x)
@@ -267,11 +367,15 @@ struct WgArgs {
   int* error;
 };
 
+// Two threads fill the stages with bulk copies (warp 0: the M operand,
+// warp 2: the N operand; per 8-channel group one strip of the run of pixels,
+// the shifted operand with its halo), warp 1 (one thread) issues the MMAs;
+// after the last block all warps read the three accumulators out.
 template <int NB>
 __global__ void __launch_bounds__(WG_THREADS, 1) k_wgrad(WgArgs g) {
   using C = WgCfg<NB>;
   extern __shared__ __align__(1024) unsigned char wsm[];
-  __shared__ uint64_t done[WG_STAGES];
+  __shared__ uint64_t full[WG_STAGES], empty[WG_STAGES];
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int dyi = blockIdx.y, chunk = blockIdx.x;
@@ -283,115 +387,107 @@ __global__ void __launch_bounds__(WG_THREADS, 1) k_wgrad(WgArgs g) {
   const uint32_t sbo_a = g.shift_a ? WG_SBO_H : WG_SBO_P;
   const uint32_t sbo_b = g.shift_a ? WG_SBO_P : WG_SBO_H;
   const uint32_t a_bytes = 16 * sbo_a;
+  const uint32_t rows_a = g.shift_a ? WG_KP + 2 : WG_KP, rows_b = g.shift_a ? WG_KP : WG_KP + 2;
   const uint32_t sbase = smem_u32(wsm);
 
   if (warp == 0) tc_alloc(&tmem_slot, C::TMEM_COLS);
   if (tid == 0) {
-    for (int s = 0; s < WG_STAGES; ++s) mbar_init(&done[s], 1);
+    for (int s = 0; s < WG_STAGES; ++s) {
+      mbar_init(&full[s], 2);
+      mbar_init(&empty[s], 1);
+    }
     fence_mbar_init();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
+  bool ok = true;
 
-  // one operand of one K block: `ch` channels of `nrows` pixels starting at
-  // z = zs (wrapped) of image row rr, into 8-channel strips of stride sbo
-  auto stage_operand = [&](uint32_t dst, const bf16* src, int ch, int rr, int zs, int nrows, uint32_t sbo) {
-    const int groups = ch / 8;
-    const size_t rbase = (size_t)rr * g.nz;
-    for (int e = tid; e < nrows * groups; e += WG_THREADS) {
-      const int r = e / groups, kg = e - r * groups;
-      int z = zs + r;
-      z += (z < 0) ? g.nz : 0;
-      z -= (z >= g.nz) ? g.nz : 0;
-      cp_async16(dst + (uint32_t)kg * sbo + (uint32_t)r * 16, src + (rbase + z) * ch + kg * 8);
-    }
-  };
-  auto load = [&](int i, int s) {
-    const int kb = kb0 + i;
-    const int rr = kb / per_row, zb = (kb - rr * per_row) * WG_KP;
-    const int bb = rr / g.ny, y = rr - bb * g.ny;
-    int ys = y + dyi - 1;
-    ys += (ys < 0) ? g.ny : 0;
-    ys -= (ys >= g.ny) ? g.ny : 0;
-    const int rs = bb * g.ny + ys;
-    const uint32_t sa = sbase + (uint32_t)s * C::STAGE;
-    const uint32_t sb = sa + a_bytes;
-    if (g.shift_a) {
-      stage_operand(sa, g.a, 128, rs, zb - 1, WG_KP + 2, sbo_a);
-      stage_operand(sb, g.b, NB, rr, zb, WG_KP, sbo_b);
-    } else {
-      stage_operand(sa, g.a, 128, rr, zb, WG_KP, sbo_a);
-      stage_operand(sb, g.b, NB, rs, zb - 1, WG_KP + 2, sbo_b);
-    }
-  };
-  constexpr uint32_t idesc = tc_idesc_bf16(128, NB, true, true);
-  auto issue = [&](int i, int s) {
-    const uint32_t sa = sbase + (uint32_t)s * C::STAGE;
-    const uint32_t sb = sa + a_bytes;
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      const uint32_t ao = g.shift_a ? (uint32_t)t * 16 : 0u;
-      const uint32_t bo = g.shift_a ? 0u : (uint32_t)t * 16;
-#pragma unroll
-      for (int kk = 0; kk < WG_KP / 16; ++kk) {
-        const uint64_t ad = tc_desc(sa + ao + (uint32_t)kk * 256, 128, sbo_a);
-        const uint64_t bd = tc_desc(sb + bo + (uint32_t)kk * 256, 128, sbo_b);
-        tc_mma_bf16(tmem + (uint32_t)(t * NB), ad, bd, idesc, (i == 0 && kk == 0) ? 0u : 1u);
+  if ((warp == 0 || warp == 2) && lane == 0) {
+    const bool is_a = warp == 0;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % WG_STAGES;
+      if (i >= WG_STAGES) ok = mbar_wait(&empty[s], (uint32_t)((i - WG_STAGES) / WG_STAGES) & 1u) && ok;
+      const int kb = kb0 + i;
+      const int rr = kb / per_row, zb = (kb - rr * per_row) * WG_KP;
+      const int bb = rr / g.ny, y = rr - bb * g.ny;
+      int ys = y + dyi - 1;
+      ys += (ys < 0) ? g.ny : 0;
+      ys -= (ys >= g.ny) ? g.ny : 0;
+      const int rs = bb * g.ny + ys;
+      const uint32_t sa = sbase + (uint32_t)s * C::STAGE;
+      if (is_a) {
+        mbar_arrive_expect_tx(&full[s], 16 * rows_a * 16);
+        const int ra = g.shift_a ? rs : rr, za = g.shift_a ? zb - 1 : zb;
+        for (int cg = 0; cg < 16; ++cg)
+          copy_strip(sa + (uint32_t)cg * sbo_a, g.a, granule(ra, cg, 0, 128, g.nz), g.nz, za, rows_a, &full[s]);
+      } else {
+        mbar_arrive_expect_tx(&full[s], (NB / 8) * rows_b * 16);
+        const int rb = g.shift_a ? rr : rs, zbb = g.shift_a ? zb : zb - 1;
+        for (int cg = 0; cg < NB / 8; ++cg)
+          copy_strip(sa + a_bytes + (uint32_t)cg * sbo_b, g.b, granule(rb, cg, 0, NB, g.nz), g.nz, zbb, rows_b,
+                     &full[s]);
       }
     }
-    tc_commit_to(&done[s]);
-  };
-
-  bool ok = true;
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc_bf16(128, NB, true, true);
+      for (int i = 0; i < nkb; ++i) {
+        const int s = i % WG_STAGES;
+        ok = mbar_wait(&full[s], (uint32_t)(i / WG_STAGES) & 1u) && ok;
+        tc_fence_after();
+        const uint32_t sa = sbase + (uint32_t)s * C::STAGE;
+        const uint32_t sb = sa + a_bytes;
 #pragma unroll
-  for (int i = 0; i < WG_STAGES - 1; ++i) {
-    if (i < nkb) load(i, i);
-    cp_async_commit();
-  }
-  for (int i = 0; i < nkb; ++i) {
-    const int s = i % WG_STAGES;
-    const int in = i + WG_STAGES - 1;
-    if (in < nkb) {
-      const int sn = in % WG_STAGES;
-      if (in >= WG_STAGES) ok = mbar_wait(&done[sn], (uint32_t)((in - WG_STAGES) / WG_STAGES) & 1u) && ok;
-      load(in, sn);
-    }
-    cp_async_commit();
-    cp_async_wait<WG_STAGES - 1>();
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      issue(i, s);
+        for (int t = 0; t < 3; ++t) {
+          const uint32_t ao = g.shift_a ? (uint32_t)t * 16 : 0u;
+          const uint32_t bo = g.shift_a ? 0u : (uint32_t)t * 16;
+#pragma unroll
+          for (int kk = 0; kk < WG_KP / 16; ++kk) {
+            const uint64_t ad = tc_desc(sa + ao + (uint32_t)kk * 256, 128, sbo_a);
+            const uint64_t bd = tc_desc(sb + bo + (uint32_t)kk * 256, 128, sbo_b);
+            tc_mma_bf16(tmem + (uint32_t)(t * NB), ad, bd, idesc, (i == 0 && kk == 0) ? 0u : 1u);
+          }
+        }
+        tc_commit_to(&empty[s]);
+      }
+      if (nkb > 0) ok = mbar_wait(&empty[(nkb - 1) % WG_STAGES], (uint32_t)((nkb - 1) / WG_STAGES) & 1u) && ok;
     }
   }
-  if (nkb > 0) ok = mbar_wait(&done[(nkb - 1) % WG_STAGES], (uint32_t)((nkb - 1) / WG_STAGES) & 1u) && ok;
-  cp_async_wait<0>();
   ok = __syncthreads_and(ok) != 0;
   tc_fence_after();
   if (!ok && tid == 0) atomicOr(g.error, ERR_TIMEOUT);
   if (ok) {
-    const int m = warp * 32 + lane;
+    const int quarter = warp & 3, part = warp >> 2;
     float* out = g.part + ((size_t)(dyi * g.chunks + chunk) * 3) * 128 * NB;
+    float* tr = reinterpret_cast<float*>(wsm) + warp * 32 * 33;   // the stages are free now
     constexpr int CW = NB < 32 ? NB : 32;
+    constexpr int SPLIT = NB >= 64 ? 2 : 1;
+    if (part < SPLIT) {
 #pragma unroll 1
-    for (int t = 0; t < 3; ++t)
+      for (int t = 0; t < 3; ++t)
 #pragma unroll 1
-      for (int c0 = 0; c0 < NB; c0 += CW) {
-        float v[CW];
-        if (nkb > 0) {
-          const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * NB + c0);
-          if constexpr (CW == 32) tc_ld_x32(ta, v); else tc_ld_x16(ta, v);
-        } else {
+        for (int c0 = part * (NB / SPLIT); c0 < (part + 1) * (NB / SPLIT); c0 += CW) {
+          float v[CW];
+          if (nkb > 0) {
+            const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * NB + c0);
+            if constexpr (CW == 32) tc_ld_x32(ta, v); else tc_ld_x16(ta, v);
+          } else {
 #pragma unroll
-          for (int q = 0; q < CW; ++q) v[q] = 0.f;
+            for (int q = 0; q < CW; ++q) v[q] = 0.f;
+          }
+          // transpose through the warp's tile: row j of the partial, lanes = columns
+#pragma unroll
+          for (int q = 0; q < CW; ++q) tr[lane * 33 + q] = v[q];
+          __syncwarp();
+          if (lane < CW)
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j)
+              out[((size_t)t * 128 + quarter * 32 + j) * NB + c0 + lane] = tr[j * 33 + lane];
+          __syncwarp();
         }
-        float* o = out + ((size_t)t * 128 + m) * NB + c0;
-#pragma unroll
-        for (int q = 0; q < CW; q += 4) *reinterpret_cast<float4*>(o + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-      }
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -412,17 +508,23 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, int chunks, int N
   grad[i] = s;
 }
 
-// bias gradients: per block, per lane of a stride S (a multiple of C) partial sums
-__global__ void k_colsum_part(const float* __restrict__ x, size_t n, int S, double* __restrict__ part) {
-  const int k = threadIdx.x;
-  if (k >= S) return;
-  const size_t per = (n + gridDim.x - 1) / gridDim.x;
+// bias gradients out[c] = sum_p x[p][c]: the flat array [pixels][C] is split
+// into equal runs, one per block; thread t of a block (blockDim a multiple of
+// C) sums the elements t, t + blockDim, ... of its run (channel t mod C), four
+// loads in flight; a second kernel adds the partials in a fixed order
+constexpr int COLSUM_BLOCKS = 608;   // 4 per SM
+__global__ void __launch_bounds__(256) k_colsum_part(const float* __restrict__ x, size_t n, double* __restrict__ part) {
+  const size_t per = ((n + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
   const size_t lo = (size_t)blockIdx.x * per, hi = min(n, lo + per);
-  double s = 0.0;
-  long long r = ((long long)k - (long long)(lo % S)) % S;   // first index >= lo with i % S == k
-  if (r < 0) r += S;
-  for (size_t i = lo + (size_t)r; i < hi; i += S) s += x[i];
-  part[(size_t)blockIdx.x * S + k] = s;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const size_t st = blockDim.x;
+  size_t i = lo + threadIdx.x;
+  for (; i + 3 * st < hi; i += 4 * st) {
+    const float a = x[i], b = x[i + st], c = x[i + 2 * st], d = x[i + 3 * st];
+    s0 += a; s1 += b; s2 += c; s3 += d;
+  }
+  for (; i < hi; i += st) s0 += x[i];
+  part[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = (s0 + s1) + (s2 + s3);
 }
 
 __global__ void k_colsum_final(const double* __restrict__ part, int blocks, int S, int Cc, float* __restrict__ out) {
@@ -438,10 +540,31 @@ struct TIdx {
   int t[64];
 };
 
+// SplitMix64 (Steele, Lea and Flood, 2014): state key + (counter + 1) times
+// the golden gamma, then the published finaliser
+__device__ inline uint64_t splitmix64(uint64_t key, uint64_t counter) {
+  uint64_t z = key + (counter + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// standard normal by the Box-Muller transform of the two 32-bit halves
+// (u1 in (0, 1], u2 in [0, 1))
+__device__ inline float normal_from(uint64_t r) {
+  const float u1 = ((float)(uint32_t)(r >> 32) + 1.0f) * 2.3283064365386963e-10f;
+  const float u2 = (float)(uint32_t)r * 2.3283064365386963e-10f;
+  return sqrtf(-2.f * logf(u1)) * cosf(6.2831853071795865f * u2);
+}
+
 // network input and target from raw planes [n][3][P]: x = (q_t, q_{t-1}, 0),
-// target = q_{t+1} - q_t, q = (plane - mean) / std
-__global__ void k_input_planes(const float* __restrict__ planes, int P, TIdx idx, int B, float3 mean, float3 istd,
-                               bf16* __restrict__ x, float* __restrict__ target) {
+// target = q_{t+1} - q_t, q = (plane - mean) / std. With noise_std > 0 the
+// inputs carry Gaussian noise (counter (b P + p) 6 + channel, key `key`) and
+// the target is taken from the noisy q_t (the network learns to return to
+// the data: q_t + eps + delta = q_{t+1})
+__global__ void k_input_planes(const float* __restrict__ planes, int P, int nz, TIdx idx, int B, float3 mean,
+                               float3 istd, float noise_std, uint64_t key, bf16* __restrict__ x,
+                               float* __restrict__ target) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * P) return;
   const int b = i / P, p = i - b * P;
@@ -453,6 +576,14 @@ __global__ void k_input_planes(const float* __restrict__ planes, int P, TIdx idx
     qt[c] = (planes[((size_t)t * 3 + c) * P + p] - mu[c]) * is[c];
     qp[c] = (planes[((size_t)(t - 1) * 3 + c) * P + p] - mu[c]) * is[c];
     qn[c] = (planes[((size_t)(t + 1) * 3 + c) * P + p] - mu[c]) * is[c];
+  }
+  if (noise_std > 0.f) {
+    const uint64_t base = (uint64_t)i * 6;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      qt[c] += noise_std * normal_from(splitmix64(key, base + c));
+      qp[c] += noise_std * normal_from(splitmix64(key, base + 3 + c));
+    }
   }
   uint4 r0, r1;
   bf16* e0 = reinterpret_cast<bf16*>(&r0);
@@ -468,12 +599,15 @@ __global__ void k_input_planes(const float* __restrict__ planes, int P, TIdx idx
     e0[3 + c] = __float2bfloat16_rn(qp[c]);
     target[(size_t)i * 3 + c] = qn[c] - qt[c];
   }
-  reinterpret_cast<uint4*>(x + (size_t)i * 16)[0] = r0;
-  reinterpret_cast<uint4*>(x + (size_t)i * 16)[1] = r1;
+  const size_t row = (size_t)i / nz;
+  const int z = i - (int)(row * nz);
+  *reinterpret_cast<uint4*>(x + granule(row, 0, z, 16, nz) * 8) = r0;
+  *reinterpret_cast<uint4*>(x + granule(row, 1, z, 16, nz) * 8) = r1;
 }
 
 // network input from normalised planes [B][P][3]
-__global__ void k_input_q(const float* __restrict__ qt, const float* __restrict__ qp, int n, bf16* __restrict__ x) {
+__global__ void k_input_q(const float* __restrict__ qt, const float* __restrict__ qp, int n, int nz,
+                          bf16* __restrict__ x) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint4 r0, r1;
@@ -489,15 +623,17 @@ __global__ void k_input_q(const float* __restrict__ qt, const float* __restrict_
     e0[c] = __float2bfloat16_rn(qt[(size_t)i * 3 + c]);
     e0[3 + c] = __float2bfloat16_rn(qp[(size_t)i * 3 + c]);
   }
-  reinterpret_cast<uint4*>(x + (size_t)i * 16)[0] = r0;
-  reinterpret_cast<uint4*>(x + (size_t)i * 16)[1] = r1;
+  const size_t row = (size_t)i / nz;
+  const int z = i - (int)(row * nz);
+  *reinterpret_cast<uint4*>(x + granule(row, 0, z, 16, nz) * 8) = r0;
+  *reinterpret_cast<uint4*>(x + granule(row, 1, z, 16, nz) * 8) = r1;
 }
 
 // gradient of the mean-square loss in delta (bf16, 16 channels, and FP32),
 // per-block sums of the squared error
 constexpr int LOSS_THREADS = 256;
 __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__ delta, const float* __restrict__ target,
-                                                       int n, float scale, bf16* __restrict__ gd16,
+                                                       int n, int nz, float scale, bf16* __restrict__ gd16,
                                                        float* __restrict__ gd32, double* __restrict__ part) {
   __shared__ double red[LOSS_THREADS];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -519,8 +655,10 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__
       gd32[(size_t)i * 3 + c] = gg;
       e0[c] = __float2bfloat16_rn(gg);
     }
-    reinterpret_cast<uint4*>(gd16 + (size_t)i * 16)[0] = r0;
-    reinterpret_cast<uint4*>(gd16 + (size_t)i * 16)[1] = r1;
+    const size_t row = (size_t)i / nz;
+    const int z = i - (int)(row * nz);
+    *reinterpret_cast<uint4*>(gd16 + granule(row, 0, z, 16, nz) * 8) = r0;
+    *reinterpret_cast<uint4*>(gd16 + granule(row, 1, z, 16, nz) * 8) = r1;
   }
   red[threadIdx.x] = se;
   __syncthreads();
@@ -555,17 +693,18 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ gr, floa
   w[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
 }
 
-// bf16 operand copies of one layer's weights: wf[tap][Op][Cp] (forward) and
-// wb[8 - tap][Cp][Op] (input gradient), zero in the padding
-__global__ void k_pack(const float* __restrict__ w, int O, int Cc, int Op, int Cp, bf16* __restrict__ wf,
-                       bf16* __restrict__ wb) {
+// bfloat16 B-operand images of one layer's weights (wimg_off): forward
+// (rows = padded outputs Op, K = padded inputs Cp) and input gradient (taps
+// flipped, rows = Cp, K = Op); zero in the padding
+__global__ void k_pack(const float* __restrict__ w, int O, int Cc, int Op, int Cp, unsigned char* __restrict__ wf,
+                       unsigned char* __restrict__ wb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 9 * Op * Cp) return;
   const int tap = i / (Op * Cp), o = (i / Cp) % Op, c = i % Cp;
   const float val = (o < O && c < Cc) ? w[((size_t)tap * O + o) * Cc + c] : 0.f;
   const bf16 hv = __float2bfloat16_rn(val);
-  wf[i] = hv;
-  if (wb) wb[((size_t)(8 - tap) * Cp + c) * Op + o] = hv;
+  *reinterpret_cast<bf16*>(wf + wimg_off(tap, o, c, Op, Cp)) = hv;
+  if (wb) *reinterpret_cast<bf16*>(wb + wimg_off(8 - tap, c, o, Cp, Op)) = hv;
 }
 
 // rollout: per-block sums of q = q_t + delta (pass 0) or of (q - mean)^2 (pass 1)
@@ -640,16 +779,38 @@ __global__ void k_normalise(const float* __restrict__ plane, int P, float3 mean,
 
 template <int N, int KC>
 void set_conv_attr() {
-  cudaFuncSetAttribute(k_conv<N, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ConvCfg<N, KC>::SMEM);
+  cudaFuncSetAttribute(k_conv<N, KC, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ConvCfg<N, KC, 128>::SMEM);
+  cudaFuncSetAttribute(k_conv<N, KC, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)ConvCfg<N, KC, 256>::SMEM);
 }
 template <int NB>
 void set_wgrad_attr() {
   cudaFuncSetAttribute(k_wgrad<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WgCfg<NB>::SMEM);
 }
 
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// tiles of 256 pixels when the row allows, else 128; one persistent CTA per SM
 template <int N, int KC>
-void launch_conv(const ConvArgs& a, int tiles, cudaStream_t s) {
-  k_conv<N, KC><<<tiles, CV_THREADS, ConvCfg<N, KC>::SMEM, s>>>(a);
+void launch_conv(const ConvArgs& a, cudaStream_t s) {
+  const int sms = num_sms();
+  if (a.nz % 256 == 0) {
+    const int tiles = a.rows * (a.nz / 256);
+    k_conv<N, KC, 256><<<std::min(tiles, sms), CV_THREADS, ConvCfg<N, KC, 256>::SMEM, s>>>(a);
+  } else {
+    const int tiles = a.rows * (a.nz / 128);
+    k_conv<N, KC, 128><<<std::min(tiles, sms), CV_THREADS, ConvCfg<N, KC, 128>::SMEM, s>>>(a);
+  }
 }
 
 template <int NB>
@@ -666,8 +827,8 @@ constexpr int SUM_BLOCKS = 152;
 struct Layer {
   int O, C, Op, Cp;        // real and padded output / input channels
   size_t woff, boff;       // offsets of W, b in the flat parameter array
-  bf16* wf = nullptr;      // [9][Op][Cp]
-  bf16* wb = nullptr;      // [9][Cp][Op]
+  unsigned char* wf = nullptr;   // forward B-operand image (wimg_off with Op rows, Cp inputs)
+  unsigned char* wb = nullptr;   // input-gradient image (flipped taps, Cp rows, Op inputs)
 };
 
 }  // namespace
@@ -683,7 +844,7 @@ struct ibm_gen {
   size_t np = 0;
   std::vector<ibm::Layer> layers;   // in, blocks..., out
   float *w = nullptr, *gw = nullptr, *m = nullptr, *v = nullptr;
-  __nv_bfloat16* wpack = nullptr;
+  unsigned char* wpack = nullptr;
   __nv_bfloat16* x = nullptr;       // [B P][16]
   __nv_bfloat16* act = nullptr;     // (L + 1) maps [B P][128]: phi(h_1) .. phi(h_{L+1})
   __nv_bfloat16* g16[2] = {nullptr, nullptr};
@@ -698,6 +859,8 @@ struct ibm_gen {
   int cur = 0;                      // hist[cur] = q_t, hist[cur ^ 1] = q_{t-1}
   float3 dmean = {0.f, 0.f, 0.f}, dstd = {1.f, 1.f, 1.f};
   double3 rms = {1.0, 1.0, 1.0};
+  float noise_std = 0.f;            // training-input noise (normalised units)
+  unsigned long long noise_seed = 0;
   int* error = nullptr;
   std::vector<void*> allocs;
 };
@@ -738,26 +901,25 @@ void pack_weights(ibm_gen* g) {
 void forward(ibm_gen* g, int B) {
   using namespace ibm;
   const int rows = B * g->ny;
-  const int tiles = rows * (g->nz / CV_M);
   ConvArgs a{};
   a.ny = g->ny; a.nz = g->nz; a.rows = rows; a.error = g->error;
   // h_1 = conv(W_in, x) + b_in; act_0 = phi(h_1)
   a.in = g->x; a.w = g->layers[0].wf; a.bias = g->w + g->layers[0].boff; a.nbias = WIDTH;
   a.out32 = g->h[0]; a.ld32 = WIDTH; a.n32 = WIDTH; a.out16 = act_map(g, 0); a.out16_phi = 1;
-  launch_conv<WIDTH, CIN_PAD>(a, tiles, g->stream);
+  launch_conv<WIDTH, CIN_PAD>(a, g->stream);
   for (int l = 1; l <= g->blocks; ++l) {
     const Layer& L = g->layers[l];
     ConvArgs c = a;
     c.in = act_map(g, l - 1); c.w = L.wf; c.bias = g->w + L.boff;
     c.res = g->h[(l - 1) & 1]; c.out32 = g->h[l & 1]; c.out16 = act_map(g, l);
-    launch_conv<WIDTH, WIDTH>(c, tiles, g->stream);
+    launch_conv<WIDTH, WIDTH>(c, g->stream);
   }
   const Layer& Lo = g->layers.back();
   ConvArgs o{};
   o.ny = g->ny; o.nz = g->nz; o.rows = rows; o.error = g->error;
   o.in = act_map(g, g->blocks); o.w = Lo.wf; o.bias = g->w + Lo.boff; o.nbias = 3;
   o.out32 = g->delta; o.ld32 = 3; o.n32 = 3;
-  launch_conv<COUT_PAD, WIDTH>(o, tiles, g->stream);
+  launch_conv<COUT_PAD, WIDTH>(o, g->stream);
 }
 
 void wgrad(ibm_gen* g, const bf16* a, const bf16* b, int nb, int shift_a, int trans, const ibm::Layer& L, int rows) {
@@ -771,9 +933,9 @@ void wgrad(ibm_gen* g, const bf16* a, const bf16* b, int nb, int shift_a, int tr
 }
 
 void colsum(ibm_gen* g, const float* x, size_t pixels, int C, float* out) {
-  const int S = (C == 3) ? 96 : C;
-  ibm::k_colsum_part<<<ibm::SUM_BLOCKS, 128, 0, g->stream>>>(x, pixels * C, S, g->dpart);
-  ibm::k_colsum_final<<<1, 128, 0, g->stream>>>(g->dpart, ibm::SUM_BLOCKS, S, C, out);
+  const int S = (C == 3) ? 192 : 256;   // threads per block, a multiple of C
+  ibm::k_colsum_part<<<ibm::COLSUM_BLOCKS, S, 0, g->stream>>>(x, pixels * C, g->dpart);
+  ibm::k_colsum_final<<<1, 128, 0, g->stream>>>(g->dpart, ibm::COLSUM_BLOCKS, S, C, out);
 }
 
 // loss gradients of B samples whose input x and target are in place
@@ -781,11 +943,10 @@ void backward(ibm_gen* g, int B) {
   using namespace ibm;
   const int rows = B * g->ny;
   const size_t n = (size_t)B * g->P;
-  const int tiles = rows * (g->nz / CV_M);
   forward(g, B);
   const int lb = (int)((n + LOSS_THREADS - 1) / LOSS_THREADS);
-  k_loss<<<lb, LOSS_THREADS, 0, g->stream>>>(g->delta, g->target, (int)n, (float)(2.0 / (3.0 * n)), g->gd16,
-                                             g->gd32, g->dpart);
+  k_loss<<<lb, LOSS_THREADS, 0, g->stream>>>(g->delta, g->target, (int)n, g->nz, (float)(2.0 / (3.0 * n)),
+                                             g->gd16, g->gd32, g->dpart);
   k_sum_double<<<1, 32, 0, g->stream>>>(g->dpart, lb, g->dscal);
   const Layer& Lo = g->layers.back();
   // output layer: dW_out^T = sum act_L[p + tap] gd[p]; db_out; g_{L+1} = phi' * conv(Wb_out, gd)
@@ -795,7 +956,7 @@ void backward(ibm_gen* g, int B) {
   a.ny = g->ny; a.nz = g->nz; a.rows = rows; a.error = g->error;
   a.in = g->gd16; a.w = Lo.wb; a.dact = act_map(g, g->blocks);
   a.out32 = g->g32[0]; a.ld32 = WIDTH; a.n32 = WIDTH; a.out16 = g->g16[0];
-  launch_conv<WIDTH, COUT_PAD>(a, tiles, g->stream);
+  launch_conv<WIDTH, COUT_PAD>(a, g->stream);
   int cur = 0;
   for (int l = g->blocks; l >= 1; --l) {
     const Layer& L = g->layers[l];
@@ -807,7 +968,7 @@ void backward(ibm_gen* g, int B) {
     c.ny = g->ny; c.nz = g->nz; c.rows = rows; c.error = g->error;
     c.in = g->g16[cur]; c.w = L.wb; c.dact = act_map(g, l - 1); c.res = g->g32[cur];
     c.out32 = g->g32[cur ^ 1]; c.ld32 = WIDTH; c.n32 = WIDTH; c.out16 = g->g16[cur ^ 1];
-    launch_conv<WIDTH, WIDTH>(c, tiles, g->stream);
+    launch_conv<WIDTH, WIDTH>(c, g->stream);
     cur ^= 1;
   }
   const Layer& Li = g->layers[0];
@@ -857,7 +1018,7 @@ int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out) {
   using namespace ibm;
   if (!cfg || !out) return IBM_EINVAL;
   *out = nullptr;
-  if (cfg->ny < 1 || cfg->nz < CV_M || cfg->nz % CV_M != 0 || cfg->width != WIDTH || cfg->blocks < 0 ||
+  if (cfg->ny < 1 || cfg->nz < 128 || cfg->nz % 128 != 0 || cfg->width != WIDTH || cfg->blocks < 0 ||
       cfg->blocks > 64 || cfg->in_channels < 1 || cfg->in_channels > 6 || cfg->batch < 1 || cfg->batch > 64)
     return IBM_EINVAL;
   if ((size_t)cfg->ny * cfg->nz > (size_t)1 << 24) return IBM_EINVAL;
@@ -884,7 +1045,7 @@ int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out) {
   add(3, WIDTH, COUT_PAD, WIDTH);
   g->np = off;
   size_t npack = 0;
-  for (auto& L : g->layers) npack += (size_t)2 * 9 * L.Op * L.Cp;
+  for (auto& L : g->layers) npack += wimg_bytes(L.Op, L.Cp) + wimg_bytes(L.Cp, L.Op);
   const size_t BP = (size_t)g->batch * g->P;
   bool ok = ready_attr();
   ok = ok && dalloc(g, &g->w, g->np) && dalloc(g, &g->gw, g->np) && dalloc(g, &g->m, g->np) &&
@@ -894,18 +1055,19 @@ int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out) {
        dalloc(g, &g->h[1], BP * WIDTH) && dalloc(g, &g->g32[0], BP * WIDTH) && dalloc(g, &g->g32[1], BP * WIDTH) &&
        dalloc(g, &g->delta, BP * 3) && dalloc(g, &g->target, BP * 3) && dalloc(g, &g->gd32, BP * 3) &&
        dalloc(g, &g->part, (size_t)3 * WG_CHUNKS * 3 * 128 * WIDTH) &&
-       dalloc(g, &g->dpart, (size_t)std::max<size_t>(SUM_BLOCKS * 128, BP / LOSS_THREADS + 1)) &&
+       dalloc(g, &g->dpart, (size_t)std::max<size_t>(COLSUM_BLOCKS * 256, BP / LOSS_THREADS + 1)) &&
        dalloc(g, &g->dscal, 8) && dalloc(g, &g->hist[0], g->P * 3) && dalloc(g, &g->hist[1], g->P * 3) &&
        dalloc(g, &g->error, 1);
   if (!ok) {
     ibm_gen_destroy(g);
     return IBM_ENOMEM;
   }
-  bf16* pk = g->wpack;
+  unsigned char* pk = g->wpack;
   for (auto& L : g->layers) {
-    L.wf = pk; pk += (size_t)9 * L.Op * L.Cp;
-    L.wb = pk; pk += (size_t)9 * L.Op * L.Cp;
+    L.wf = pk; pk += wimg_bytes(L.Op, L.Cp);
+    L.wb = pk; pk += wimg_bytes(L.Cp, L.Op);
   }
+  cudaMemsetAsync(g->wpack, 0, npack, g->stream);
   cudaMemsetAsync(g->w, 0, g->np * sizeof(float), g->stream);
   cudaMemsetAsync(g->gw, 0, g->np * sizeof(float), g->stream);
   cudaMemsetAsync(g->m, 0, g->np * sizeof(float), g->stream);
@@ -966,7 +1128,7 @@ int ibm_gen_set_norm(ibm_gen* g, const double* mean, const double* std, const do
 int ibm_gen_forward(ibm_gen* g, const float* q_t, const float* q_prev, float* delta, int batch) {
   if (!g || !q_t || !q_prev || !delta || batch < 1 || batch > g->batch) return IBM_EINVAL;
   const size_t n = (size_t)batch * g->P;
-  ibm::k_input_q<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(q_t, q_prev, (int)n, g->x);
+  ibm::k_input_q<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(q_t, q_prev, (int)n, g->nz, g->x);
   forward(g, batch);
   if (cudaMemcpyAsync(delta, g->delta, n * 3 * sizeof(float), cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
     return IBM_ECUDA;
@@ -977,7 +1139,7 @@ int ibm_gen_grad(ibm_gen* g, const float* q_t, const float* q_prev, const float*
                  double* loss) {
   if (!g || !q_t || !q_prev || !target || batch < 1 || batch > g->batch) return IBM_EINVAL;
   const size_t n = (size_t)batch * g->P;
-  ibm::k_input_q<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(q_t, q_prev, (int)n, g->x);
+  ibm::k_input_q<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(q_t, q_prev, (int)n, g->nz, g->x);
   if (cudaMemcpyAsync(g->target, target, n * 3 * sizeof(float), cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
     return IBM_ECUDA;
   backward(g, batch);
@@ -999,12 +1161,89 @@ int ibm_gen_train_step(ibm_gen* g, const float* planes, int n_planes, const int*
   }
   const size_t n = (size_t)batch * g->P;
   const float3 istd = make_float3(1.f / g->dstd.x, 1.f / g->dstd.y, 1.f / g->dstd.z);
-  ibm::k_input_planes<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(planes, (int)g->P, idx, batch, g->dmean,
-                                                                          istd, g->x, g->target);
+  ibm::k_input_planes<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(
+      planes, (int)g->P, g->nz, idx, batch, g->dmean, istd, g->noise_std, g->noise_seed + (unsigned long long)g->t, g->x,
+      g->target);
   backward(g, batch);
   adam(g);
   if (!loss) return cuda_status(cudaGetLastError());
   return read_loss(g, n, loss);
+}
+
+int ibm_gen_eval(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch, double* loss) {
+  if (!g || !planes || !t_idx || !loss || batch < 1 || batch > g->batch) return IBM_EINVAL;
+  ibm::TIdx idx{};
+  for (int b = 0; b < batch; ++b) {
+    if (t_idx[b] < 1 || t_idx[b] + 1 >= n_planes) return IBM_EINVAL;
+    idx.t[b] = t_idx[b];
+  }
+  const size_t n = (size_t)batch * g->P;
+  const float3 istd = make_float3(1.f / g->dstd.x, 1.f / g->dstd.y, 1.f / g->dstd.z);
+  ibm::k_input_planes<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(planes, (int)g->P, g->nz, idx, batch,
+                                                                          g->dmean, istd, 0.f, 0ull, g->x, g->target);
+  forward(g, batch);
+  const int lb = (int)((n + ibm::LOSS_THREADS - 1) / ibm::LOSS_THREADS);
+  ibm::k_loss<<<lb, ibm::LOSS_THREADS, 0, g->stream>>>(g->delta, g->target, (int)n, g->nz,
+                                                       (float)(2.0 / (3.0 * n)), g->gd16, g->gd32, g->dpart);
+  ibm::k_sum_double<<<1, 32, 0, g->stream>>>(g->dpart, lb, g->dscal);
+  return read_loss(g, n, loss);
+}
+
+int ibm_gen_set_noise(ibm_gen* g, double std, unsigned long long seed) {
+  if (!g || !(std >= 0.0) || !std::isfinite(std)) return IBM_EINVAL;
+  g->noise_std = (float)std;
+  g->noise_seed = seed;
+  return IBM_OK;
+}
+
+int ibm_gen_set_lr(ibm_gen* g, double lr) {
+  if (!g || !(lr > 0.0)) return IBM_EINVAL;
+  g->lr = lr;
+  return IBM_OK;
+}
+
+int ibm_gen_time(ibm_gen* g, int what, int nrep, double* ms) {
+  using namespace ibm;
+  if (!g || !ms || nrep < 1 || what < 0 || what > 4) return IBM_EINVAL;
+  if (what >= 2 && g->blocks < 1) return IBM_EINVAL;
+  const int B = g->batch, rows = B * g->ny;
+  auto run = [&]() {
+    switch (what) {
+      case 0: backward(g, B); adam(g); break;   // training step on the data in place
+      case 1: forward(g, B); break;
+      case 2: {                                  // one residual-block convolution, forward
+        ConvArgs c{};
+        c.ny = g->ny; c.nz = g->nz; c.rows = rows; c.error = g->error;
+        c.in = act_map(g, 0); c.w = g->layers[1].wf; c.bias = g->w + g->layers[1].boff; c.nbias = WIDTH;
+        c.res = g->h[0]; c.out32 = g->h[1]; c.ld32 = WIDTH; c.n32 = WIDTH; c.out16 = act_map(g, 1); c.out16_phi = 1;
+        launch_conv<WIDTH, WIDTH>(c, g->stream);
+        break;
+      }
+      case 3: {                                  // its input gradient
+        ConvArgs c{};
+        c.ny = g->ny; c.nz = g->nz; c.rows = rows; c.error = g->error;
+        c.in = g->g16[0]; c.w = g->layers[1].wb; c.dact = act_map(g, 0); c.res = g->g32[0];
+        c.out32 = g->g32[1]; c.ld32 = WIDTH; c.n32 = WIDTH; c.out16 = g->g16[1];
+        launch_conv<WIDTH, WIDTH>(c, g->stream);
+        break;
+      }
+      case 4: wgrad(g, g->g16[0], act_map(g, 0), WIDTH, 0, 0, g->layers[1], rows); break;
+    }
+  };
+  run();   // warm-up
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return IBM_ECUDA;
+  cudaEventRecord(e0, g->stream);
+  for (int r = 0; r < nrep; ++r) run();
+  cudaEventRecord(e1, g->stream);
+  const int st = check_error(g);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != IBM_OK) return st;
+  *ms = (double)t / nrep;
+  return IBM_OK;
 }
 
 int ibm_gen_rollout_init(ibm_gen* g, const float* plane_prev, const float* plane_cur) {
@@ -1024,7 +1263,7 @@ int ibm_gen_rollout(ibm_gen* g, void* u, void* v, void* w, int precision) {
   const int P = (int)g->P;
   float* qt = g->hist[g->cur];
   float* qp = g->hist[g->cur ^ 1];
-  k_input_q<<<(P + 255) / 256, 256, 0, g->stream>>>(qt, qp, P, g->x);
+  k_input_q<<<(P + 255) / 256, 256, 0, g->stream>>>(qt, qp, P, g->nz, g->x);
   forward(g, 1);
   const int nb = SUM_BLOCKS;
   double* mean = g->dscal + 1;

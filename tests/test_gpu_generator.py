@@ -143,6 +143,40 @@ def test_training_on_planes(lib):
     gen.close()
 
 
+def test_training_noise_matches_oracle(lib):
+    """With input noise the first step's loss is the oracle's loss of the
+    same SplitMix64 / Box-Muller draws (key = seed + Adam steps done)."""
+    from oracle import generator as og
+    from paper_2103_08246_gb300 import binding, inputs
+    planes = inputs.advected_planes(12, NY, NZ, seed=4, shift=1)
+    mean = planes.mean(axis=(0, 2, 3))
+    std = planes.std(axis=(0, 2, 3))
+    gen = binding.Generator(NY, NZ, blocks=BLOCKS, in_channels=CIN, batch=BATCH, lr=1e-3)
+    w = _params(15)
+    gen.set_params(w)
+    gen.set_norm(mean, std, [1.0, 1.0, 1.0])
+    gen.set_noise(0.05, seed=99)
+    dev = torch.as_tensor(planes.astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    idx = [3, 8]
+    pl32 = planes.astype(np.float32).astype(np.float64)
+    m32 = mean.astype(np.float32).astype(np.float64)
+    inv = (np.float32(1.0) / std.astype(np.float32)).astype(np.float64)
+
+    def q(t):
+        return np.moveaxis((pl32[t] - m32[:, None, None]) * inv[:, None, None], 0, -1)
+    p = og.unflatten(w.astype(np.float32).astype(np.float64), 128, BLOCKS, CIN)
+    xs, ts = [], []
+    for b, t in enumerate(idx):
+        qt, qp = og.noisy_inputs(q(t), q(t - 1), b, 0.05, 99)
+        xs.append(og.make_input(qt, qp, CIN))
+        ts.append(q(t + 1) - qt)
+    loss_ref, _ = og.loss_and_grads(p, xs, ts, bf16=True)
+    first = gen.train_step(dev, idx)
+    assert abs(first - loss_ref) <= 1e-3 * loss_ref, (first, loss_ref)
+    gen.close()
+
+
 def test_rollout_matches_oracle(lib):
     """One rollout step: q = q_t + delta, renormalised to the target rms,
     emitted as mean + std q into FP64 and FP32 planes; the history advances."""

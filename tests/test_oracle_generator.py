@@ -124,3 +124,26 @@ def test_renormalise():
     assert np.allclose(np.sqrt((out ** 2).mean(axis=(0, 1))), [0.3, 0.2, 0.1], rtol=1e-14)
     # a rescaling of the input does not change the result
     assert np.allclose(gen.renormalise(3.0 * q, [0.3, 0.2, 0.1]), out, atol=1e-14)
+
+
+def test_splitmix64_published_outputs():
+    # the reference generator seeded with 0 starts 0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F
+    r = gen.splitmix64(0, np.arange(3))
+    assert [int(x) for x in r] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_box_muller_normals():
+    z = gen.normal_from(gen.splitmix64(12345, np.arange(400000)))
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+    from scipy import stats
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+
+
+def test_noisy_inputs_shift_by_the_drawn_noise():
+    rng = np.random.default_rng(9)
+    qt, qp = rng.standard_normal((2, 3, 4, 3))
+    a, b = gen.noisy_inputs(qt, qp, 1, 0.0, 7)
+    assert np.array_equal(a, qt) and np.array_equal(b, qp)
+    a, b = gen.noisy_inputs(qt, qp, 1, 0.5, 7)
+    eps = gen.normal_from(gen.splitmix64(7, (12 + 0) * 6 + 4))     # sample 1, pixel 0, q_{t-1} channel 1
+    assert abs((b[0, 0, 1] - qp[0, 0, 1]) - 0.5 * eps) < 1e-15
