@@ -78,6 +78,10 @@ def parse():
     ap.add_argument("--profile-precision", choices=["fp32", "fp64", "mixed"], default="fp32")
     ap.add_argument("--profile-small", action="store_true",
                     help="profile the 256x256x256 half-length case (flag at x = 2)")
+    ap.add_argument("--profile-generator", type=int, default=0,
+                    help="only run this many launches of each generator kernel timing "
+                         "(residual-block convolution, input gradient, weight gradient; "
+                         "256x256 planes, batch 8) for ncu and exit")
     return ap.parse_args()
 
 
@@ -95,6 +99,18 @@ def run_profile(args):
     s.step(args.profile_steps)
     torch.cuda.synchronize()
     s.close()
+
+
+def run_profile_generator(args):
+    """Plain run for profilers: one residual block of the inflow generator at
+    the production plane; each kernel timed once warm plus n times."""
+    from paper_2103_08246_gb300 import binding, build, inputs
+    build.build()
+    g = binding.Generator(256, 256, blocks=1, in_channels=6, batch=8)
+    g.set_params(inputs.generator_params(0, 128, 1, 6))
+    for what in ("conv_fwd", "conv_dgrad", "conv_wgrad"):
+        print(what, "ms", g.time(what, args.profile_generator))
+    g.close()
 
 
 def measured_peaks():
@@ -532,6 +548,9 @@ def main():
     args = parse()
     if args.profile_steps > 0:
         run_profile(args)
+        return
+    if args.profile_generator > 0:
+        run_profile_generator(args)
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

@@ -315,17 +315,18 @@ void ibm_ensemble_destroy(ibm_ensemble* e);
 
 /* ---- Learned inflow generator ------------------------------------------
  * The synthetic-inflow alternative that Sec. V of the paper leaves open: an
- * autoregressive convolutional network that maps the two latest inflow
- * planes of velocity fluctuations (q_t, q_{t-1}, each 3 components on the
- * periodic ny x nz plane) to the next one, trained on planes recorded from
- * a grid-resolved (precursor) run, then rolled out as the prescribed inflow
- * of a state created with opts->inflow.
+ * autoregressive convolutional network that maps the two latest keyframes
+ * of inflow velocity fluctuations (q_t, q_{t-s}, each 3 components on the
+ * periodic ny x nz plane, s the keyframe stride in recorded planes) to the
+ * next one, trained on planes recorded from a grid-resolved (precursor) run,
+ * then rolled out as the prescribed inflow of a state created with
+ * opts->inflow (keyframes, and planes interpolated between them).
  *
  * Network (periodic 3 x 3 cross-correlations, phi(s) = s for s > 0, s / 8
  * otherwise, width 128, `blocks` residual blocks):
- *   h_1 = conv(W_in, x) + b_in,  x = (q_t, q_{t-1})[:in_channels]
+ *   h_1 = conv(W_in, x) + b_in,  x = (q_t, q_{t-s})[:in_channels]
  *   h_{l+1} = h_l + conv(W_l, phi(h_l)) + b_l
- *   delta = conv(W_out, phi(h_{L+1})) + b_out,   q_{t+1} = q_t + delta
+ *   delta = conv(W_out, phi(h_{L+1})) + b_out,   q_{t+s} = q_t + delta
  * Convolution operands are bfloat16 (tensor cores), accumulation, residual
  * streams and the Adam master weights FP32. Loss: mean of (delta - target)^2
  * over samples, pixels and the 3 components.
@@ -342,10 +343,12 @@ typedef struct {
   int ny, nz;         /* plane: ny >= 1, nz a multiple of 128, ny * nz <= 2^24 */
   int width;          /* 128 */
   int blocks;         /* residual blocks, 0 .. 64 */
-  int in_channels;    /* input components used, 1 .. 6 (6: q_t and q_{t-1}) */
+  int in_channels;    /* input components used, 1 .. 6 (6: q_t and q_{t-s}) */
   int batch;          /* most samples per training step, 1 .. 64 */
   double lr, beta1, beta2, eps;   /* Adam (<= 0: 1e-3, 0.9, 0.999, 1e-8) */
   void* stream;       /* cudaStream_t (NULL: the default stream) */
+  int stride;         /* planes between the generator's keyframes (<= 0: 1): it
+                         predicts plane t + stride from t and t - stride */
 } ibm_gen_config;
 int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out);
 size_t ibm_gen_param_count(const ibm_gen* g);
@@ -365,8 +368,9 @@ int ibm_gen_grad(ibm_gen* g, const float* q_t, const float* q_prev, const float*
 /* one Adam step with the stored gradients */
 int ibm_gen_adam_step(ibm_gen* g);
 /* one training step on raw planes [n_planes][3][ny][nz] (FP32, e.g. a
- * precursor record): sample b predicts plane t_idx[b] + 1 from t_idx[b] and
- * t_idx[b] - 1 (host ints, 1 <= t < n_planes - 1); gradients, then Adam.
+ * precursor record): sample b predicts plane t_idx[b] + stride from
+ * t_idx[b] and t_idx[b] - stride (host ints, stride <= t < n_planes - stride);
+ * gradients, then Adam.
  * loss (host, nullable): the batch loss before the step. */
 int ibm_gen_train_step(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch,
                        double* loss);
@@ -375,7 +379,7 @@ int ibm_gen_train_step(ibm_gen* g, const float* planes, int n_planes, const int*
 int ibm_gen_eval(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch,
                  double* loss);
 /* training-input noise: ibm_gen_train_step adds std * N(0, 1) to every
- * normalised input value (q_t and q_{t-1}) and takes the target from the
+ * normalised input value (q_t and q_{t-s}) and takes the target from the
  * noisy q_t, so that the network learns to pull perturbed planes back to
  * the data (a stable rollout). N(0, 1) is Box-Muller of SplitMix64 (Steele,
  * Lea and Flood 2014) with key seed + (Adam steps done) and counter
@@ -398,7 +402,12 @@ int ibm_gen_rollout_init(ibm_gen* g, const float* plane_prev, const float* plane
  * otherwise; any may be NULL), e.g. the pending planes of
  * ibm_inflow_planes. Asynchronous. */
 int ibm_gen_rollout(ibm_gen* g, void* u, void* v, void* w, int precision);
-/* copy the rollout history (normalised q_t, q_{t-1}, [ny][nz][3]) */
+/* planes between the last two keyframes of the rollout: writes
+ * mean + std ((1 - w) q_prev + w q_t) (0 <= w <= 1) like ibm_gen_rollout,
+ * so that a run can take one plane per step with keyframes every `stride`
+ * steps. Asynchronous. */
+int ibm_gen_emit(ibm_gen* g, double w, void* u, void* v, void* wv, int precision);
+/* copy the rollout history (normalised newest and previous keyframes, [ny][nz][3]) */
 int ibm_gen_history(ibm_gen* g, float* q_t, float* q_prev);
 int ibm_gen_sync(ibm_gen* g);
 void ibm_gen_destroy(ibm_gen* g);

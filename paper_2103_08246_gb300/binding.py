@@ -30,7 +30,7 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_gen_create", "ibm_gen_param_count", "ibm_gen_set_params", "ibm_gen_get_params",
            "ibm_gen_get_grads", "ibm_gen_set_norm", "ibm_gen_forward", "ibm_gen_grad", "ibm_gen_adam_step",
-           "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_history", "ibm_gen_sync",
+           "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_emit", "ibm_gen_history", "ibm_gen_sync",
            "ibm_gen_destroy", "ibm_destroy", "ibm_strerror")
 _VOID = ("ibm_destroy", "ibm_ensemble_destroy", "ibm_gen_destroy")
 
@@ -73,7 +73,7 @@ class ibm_gen_config(ctypes.Structure):
     _fields_ = [("ny", ctypes.c_int), ("nz", ctypes.c_int), ("width", ctypes.c_int),
                 ("blocks", ctypes.c_int), ("in_channels", ctypes.c_int), ("batch", ctypes.c_int),
                 ("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
-                ("eps", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("eps", ctypes.c_double), ("stream", ctypes.c_void_p), ("stride", ctypes.c_int)]
 
 
 class ibm_stats_t(ctypes.Structure):
@@ -154,6 +154,7 @@ def load(path: str = LIB_PATH):
     lib.ibm_gen_rollout_init.argtypes = [vp, vp, vp]
     lib.ibm_gen_rollout.argtypes = [vp, vp, vp, vp, ctypes.c_int]
     lib.ibm_gen_history.argtypes = [vp, vp, vp]
+    lib.ibm_gen_emit.argtypes = [vp, ctypes.c_double, vp, vp, vp, ctypes.c_int]
     lib.ibm_gen_sync.argtypes = [vp]
     lib.ibm_gen_destroy.argtypes = [vp]
     for name in SYMBOLS:
@@ -395,6 +396,10 @@ def ibm_gen_rollout(gen, u, v, w, precision):
     _check(load().ibm_gen_rollout(gen, u, v, w, int(precision)), "ibm_gen_rollout")
 
 
+def ibm_gen_emit(gen, w, u, v, wv, precision):
+    _check(load().ibm_gen_emit(gen, float(w), u, v, wv, int(precision)), "ibm_gen_emit")
+
+
 def ibm_gen_history(gen, q_t, q_prev):
     _check(load().ibm_gen_history(gen, q_t, q_prev), "ibm_gen_history")
 
@@ -534,15 +539,16 @@ class Generator:
     """Learned inflow generator (ibm_gen_*): device buffers are torch tensors
     on the current CUDA device, the stream is torch's unless one is given."""
 
-    def __init__(self, ny, nz, blocks=13, in_channels=6, batch=8, lr=1e-3, stream=None):
+    def __init__(self, ny, nz, blocks=13, in_channels=6, batch=8, lr=1e-3, stream=None, stride=1):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the generator needs a CUDA device")
         load()
         self.ny, self.nz, self.blocks, self.in_channels, self.batch = ny, nz, blocks, in_channels, batch
+        self.stride = stride
         self.stream = stream if stream is not None else torch.cuda.Stream()
         cfg = ibm_gen_config(ny, nz, 128, blocks, in_channels, batch, lr, 0.0, 0.0, 0.0,
-                             ctypes.c_void_p(self.stream.cuda_stream))
+                             ctypes.c_void_p(self.stream.cuda_stream), stride)
         torch.cuda.synchronize()
         self.handle = ibm_gen_create(cfg)
         self.n_params = ibm_gen_param_count(self.handle)
@@ -606,6 +612,9 @@ class Generator:
 
     def rollout(self, u, v, w, precision=IBM_FP32):
         ibm_gen_rollout(self.handle, u, v, w, precision)
+
+    def emit(self, w, u, v, wv, precision=IBM_FP32):
+        ibm_gen_emit(self.handle, w, u, v, wv, precision)
 
     def history(self):
         import torch

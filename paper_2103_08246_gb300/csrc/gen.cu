@@ -557,13 +557,13 @@ __device__ inline float normal_from(uint64_t r) {
   return sqrtf(-2.f * logf(u1)) * cosf(6.2831853071795865f * u2);
 }
 
-// network input and target from raw planes [n][3][P]: x = (q_t, q_{t-1}, 0),
-// target = q_{t+1} - q_t, q = (plane - mean) / std. With noise_std > 0 the
+// network input and target from raw planes [n][3][P]: x = (q_t, q_{t-s}, 0),
+// target = q_{t+s} - q_t (s the keyframe stride), q = (plane - mean) / std. With noise_std > 0 the
 // inputs carry Gaussian noise (counter (b P + p) 6 + channel, key `key`) and
 // the target is taken from the noisy q_t (the network learns to return to
 // the data: q_t + eps + delta = q_{t+1})
-__global__ void k_input_planes(const float* __restrict__ planes, int P, int nz, TIdx idx, int B, float3 mean,
-                               float3 istd, float noise_std, uint64_t key, bf16* __restrict__ x,
+__global__ void k_input_planes(const float* __restrict__ planes, int P, int nz, int stride, TIdx idx, int B,
+                               float3 mean, float3 istd, float noise_std, uint64_t key, bf16* __restrict__ x,
                                float* __restrict__ target) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B * P) return;
@@ -574,8 +574,8 @@ __global__ void k_input_planes(const float* __restrict__ planes, int P, int nz, 
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     qt[c] = (planes[((size_t)t * 3 + c) * P + p] - mu[c]) * is[c];
-    qp[c] = (planes[((size_t)(t - 1) * 3 + c) * P + p] - mu[c]) * is[c];
-    qn[c] = (planes[((size_t)(t + 1) * 3 + c) * P + p] - mu[c]) * is[c];
+    qp[c] = (planes[((size_t)(t - stride) * 3 + c) * P + p] - mu[c]) * is[c];
+    qn[c] = (planes[((size_t)(t + stride) * 3 + c) * P + p] - mu[c]) * is[c];
   }
   if (noise_std > 0.f) {
     const uint64_t base = (uint64_t)i * 6;
@@ -768,6 +768,21 @@ __global__ void k_roll_emit(const float* __restrict__ qt, const float* __restric
   }
 }
 
+// planes mean + std ((1 - w) a + w b) from normalised [P][3] a, b
+template <class T>
+__global__ void k_emit_interp(const float* __restrict__ a, const float* __restrict__ b, int P, float w,
+                              float3 dmean, float3 dstd, T* __restrict__ u, T* __restrict__ v, T* __restrict__ wv) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float mu[3] = {dmean.x, dmean.y, dmean.z}, sd[3] = {dstd.x, dstd.y, dstd.z};
+  T* outs[3] = {u, v, wv};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float q = (1.f - w) * a[(size_t)p * 3 + c] + w * b[(size_t)p * 3 + c];
+    if (outs[c]) outs[c][p] = (T)(mu[c] + sd[c] * q);
+  }
+}
+
 // raw planes [3][P] -> normalised [P][3]
 __global__ void k_normalise(const float* __restrict__ plane, int P, float3 mean, float3 istd, float* __restrict__ q) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -836,7 +851,7 @@ struct Layer {
 }  // namespace ibm
 
 struct ibm_gen {
-  int ny = 0, nz = 0, blocks = 0, cin = 0, batch = 0;
+  int ny = 0, nz = 0, blocks = 0, cin = 0, batch = 0, stride = 1;
   size_t P = 0;
   cudaStream_t stream = nullptr;
   double lr = 1e-3, b1 = 0.9, b2 = 0.999, eps = 1e-8;
@@ -1025,6 +1040,7 @@ int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out) {
   ibm_gen* g = new (std::nothrow) ibm_gen();
   if (!g) return IBM_ENOMEM;
   g->ny = cfg->ny; g->nz = cfg->nz; g->blocks = cfg->blocks; g->cin = cfg->in_channels; g->batch = cfg->batch;
+  g->stride = cfg->stride > 0 ? cfg->stride : 1;
   g->P = (size_t)cfg->ny * cfg->nz;
   g->stream = static_cast<cudaStream_t>(cfg->stream);
   if (cfg->lr > 0) g->lr = cfg->lr;
@@ -1156,13 +1172,13 @@ int ibm_gen_train_step(ibm_gen* g, const float* planes, int n_planes, const int*
   if (!g || !planes || !t_idx || batch < 1 || batch > g->batch) return IBM_EINVAL;
   ibm::TIdx idx{};
   for (int b = 0; b < batch; ++b) {
-    if (t_idx[b] < 1 || t_idx[b] + 1 >= n_planes) return IBM_EINVAL;
+    if (t_idx[b] < g->stride || t_idx[b] + g->stride >= n_planes) return IBM_EINVAL;
     idx.t[b] = t_idx[b];
   }
   const size_t n = (size_t)batch * g->P;
   const float3 istd = make_float3(1.f / g->dstd.x, 1.f / g->dstd.y, 1.f / g->dstd.z);
   ibm::k_input_planes<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(
-      planes, (int)g->P, g->nz, idx, batch, g->dmean, istd, g->noise_std, g->noise_seed + (unsigned long long)g->t, g->x,
+      planes, (int)g->P, g->nz, g->stride, idx, batch, g->dmean, istd, g->noise_std, g->noise_seed + (unsigned long long)g->t, g->x,
       g->target);
   backward(g, batch);
   adam(g);
@@ -1174,13 +1190,14 @@ int ibm_gen_eval(ibm_gen* g, const float* planes, int n_planes, const int* t_idx
   if (!g || !planes || !t_idx || !loss || batch < 1 || batch > g->batch) return IBM_EINVAL;
   ibm::TIdx idx{};
   for (int b = 0; b < batch; ++b) {
-    if (t_idx[b] < 1 || t_idx[b] + 1 >= n_planes) return IBM_EINVAL;
+    if (t_idx[b] < g->stride || t_idx[b] + g->stride >= n_planes) return IBM_EINVAL;
     idx.t[b] = t_idx[b];
   }
   const size_t n = (size_t)batch * g->P;
   const float3 istd = make_float3(1.f / g->dstd.x, 1.f / g->dstd.y, 1.f / g->dstd.z);
-  ibm::k_input_planes<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(planes, (int)g->P, g->nz, idx, batch,
-                                                                          g->dmean, istd, 0.f, 0ull, g->x, g->target);
+  ibm::k_input_planes<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(planes, (int)g->P, g->nz, g->stride,
+                                                                          idx, batch, g->dmean, istd, 0.f, 0ull, g->x,
+                                                                          g->target);
   forward(g, batch);
   const int lb = (int)((n + ibm::LOSS_THREADS - 1) / ibm::LOSS_THREADS);
   ibm::k_loss<<<lb, ibm::LOSS_THREADS, 0, g->stream>>>(g->delta, g->target, (int)n, g->nz,
@@ -1280,6 +1297,22 @@ int ibm_gen_rollout(ibm_gen* g, void* u, void* v, void* w, int precision) {
     k_roll_emit<float><<<(P + 255) / 256, 256, 0, g->stream>>>(qt, g->delta, P, mean, scale, g->dmean, g->dstd,
                                                                qp, (float*)u, (float*)v, (float*)w);
   g->cur ^= 1;
+  return cuda_status(cudaGetLastError());
+}
+
+int ibm_gen_emit(ibm_gen* g, double w, void* u, void* v, void* wv, int precision) {
+  using namespace ibm;
+  if (!g || !(w >= 0.0 && w <= 1.0)) return IBM_EINVAL;
+  if (precision != IBM_FP64 && precision != IBM_FP32 && precision != IBM_MIXED) return IBM_EINVAL;
+  const int P = (int)g->P;
+  const float* qt = g->hist[g->cur];
+  const float* qp = g->hist[g->cur ^ 1];
+  if (precision == IBM_FP64)
+    k_emit_interp<double><<<(P + 255) / 256, 256, 0, g->stream>>>(qp, qt, P, (float)w, g->dmean, g->dstd,
+                                                                  (double*)u, (double*)v, (double*)wv);
+  else
+    k_emit_interp<float><<<(P + 255) / 256, 256, 0, g->stream>>>(qp, qt, P, (float)w, g->dmean, g->dstd,
+                                                                 (float*)u, (float*)v, (float*)wv);
   return cuda_status(cudaGetLastError());
 }
 

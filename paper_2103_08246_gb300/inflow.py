@@ -11,15 +11,16 @@ learned generator of the C ABI (``ibm_gen_*``):
    about 1.5), that
    plane (u on the face, v, w on the cell centres) is recorded every step
    (device planes, FP32);
-2. training: the generator learns q_{t+1} - q_t from (q_t, q_{t-1}) on the
-   first 90% of the record (Adam, cosine learning-rate decay; Gaussian
+2. training: the generator learns keyframe steps q_{t+s} - q_t from
+   (q_t, q_{t-s}), s = 10 recorded planes, on the first 90% of the record (Adam, cosine learning-rate decay; Gaussian
    noise on the inputs with the target taken from the noisy q_t, so that
    the rollout is pulled back towards the data), the last 10% is held out;
 3. runs with the flag, each for the same number of steps:
    R  grid-resolved: the production workload (bars at 0.5, flag at 3);
    G  generated inflow: a 384 x 256 x 256 domain of length 6 without bars,
-      flag at 1, inflow planes from the generator rollout, one per step
-      (seeded with the last two recorded planes);
+      flag at 1, inflow planes from the generator rollout: a keyframe every
+      s steps (seeded with the last two recorded keyframes), the planes in
+      between interpolated linearly in time;
    U  uniform inflow on the same domain;
    W  white-noise inflow on the same domain: independent Gaussian planes
       with the record's per-component rms (matched turbulence intensity);
@@ -125,17 +126,19 @@ def data_norm(planes, sample=256, seed=0):
 
 
 def train(gen, planes, steps, lr0=5e-4, lr1=2e-5, train_frac=0.9, seed=0, log_every=100):
-    """Adam with cosine decay from lr0 to lr1; returns the loss history."""
+    """Adam with cosine decay from lr0 to lr1; returns the loss history.
+    Samples are keyframe triples (t - s, t, t + s), s = gen.stride."""
     n = planes.shape[0]
+    s_ = gen.stride
     n_train = int(n * train_frac)
     rng = np.random.default_rng(seed)
-    val_idx = np.arange(n_train + 1, n - 1)
+    val_idx = np.arange(n_train + s_, n - s_)
     hist = {"step": [], "train": [], "val": []}
     t0 = time.perf_counter()
     for s in range(steps):
         lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + np.cos(np.pi * s / max(steps - 1, 1)))
         gen.set_lr(lr)
-        idx = rng.integers(1, n_train - 1, size=gen.batch)
+        idx = rng.integers(s_, n_train - s_, size=gen.batch)
         log = (s % log_every == 0) or s == steps - 1
         loss = gen.train_step(planes, idx, with_loss=log)
         if log:
@@ -148,18 +151,18 @@ def train(gen, planes, steps, lr0=5e-4, lr1=2e-5, train_frac=0.9, seed=0, log_ev
     return hist
 
 
-def baselines(planes, mean, std, n_train, count=64, seed=1):
+def baselines(planes, mean, std, n_train, stride=1, count=64, seed=1):
     """Validation losses of two predictors without parameters, in the
     training loss's units: persistence (delta = 0) and linear extrapolation
-    (delta = q_t - q_{t-1})."""
+    (delta = q_t - q_{t-s})."""
     rng = np.random.default_rng(seed)
     n = planes.shape[0]
-    idx = rng.integers(n_train + 1, n - 1, size=count)
+    idx = rng.integers(n_train + stride, n - stride, size=count)
     s = std[:, None, None]
     m = mean[:, None, None]
     pers, lin = 0.0, 0.0
     for t in idx:
-        q = [(planes[k].double().cpu().numpy() - m) / s for k in (t - 1, t, t + 1)]
+        q = [(planes[k].double().cpu().numpy() - m) / s for k in (t - stride, t, t + stride)]
         d = q[2] - q[1]
         pers += float(np.mean(d * d))
         e = d - (q[1] - q[0])
@@ -167,13 +170,14 @@ def baselines(planes, mean, std, n_train, count=64, seed=1):
     return {"persistence": pers / count, "linear_extrapolation": lin / count}
 
 
-def rollout_diagnostics(gen, planes, checkpoints=(1, 10, 100, 1000, 3000)):
-    """Generator alone, seeded with the last two recorded planes: the u
+def rollout_diagnostics(gen, planes, checkpoints=(1, 10, 100, 300, 800)):
+    """Generator alone, seeded with the last two recorded keyframes: the u
     spectrum across z, the component rms and the correlation of u' with the
-    seed plane at the given rollout steps, and the record's mean u spectrum."""
+    seed plane after the given numbers of keyframes, and the record's mean u
+    spectrum."""
     import torch
     ny, nz = planes.shape[2], planes.shape[3]
-    gen.rollout_init(planes[-2].cpu().numpy(), planes[-1].cpu().numpy())
+    gen.rollout_init(planes[-1 - gen.stride].cpu().numpy(), planes[-1].cpu().numpy())
     out = [torch.zeros((ny, nz), dtype=torch.float32, device="cuda") for _ in range(3)]
     torch.cuda.synchronize()
     seed_u = planes[-1, 0].double().cpu().numpy()
@@ -328,10 +332,10 @@ def compare(res, x_st, x0):
 
 def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3000, blocks=13, batch=8,
              precision=binding.IBM_FP32, seed=0, log=print, base=inputs.PRODUCTION, sample_every=10,
-             re=None, noise=0.01):
+             re=None, noise=0.03, stride=10):
     import torch
     prod = base if re is None else base.replace(re=float(re))
-    out = {"bounds": BOUNDS, "workload": base.name, "re": prod.re, "train_noise": noise}
+    out = {"bounds": BOUNDS, "workload": base.name, "re": prod.re, "train_noise": noise, "stride": stride}
     h = prod.lx / prod.nx
     R_SHIFT = shift_cells(prod)
     i_rec = R_SHIFT
@@ -346,22 +350,22 @@ def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3
     out["data"] = {"mean": mean.tolist(), "std": std.tolist(), "rms_normalised": rms.tolist()}
     log(f"precursor: {out['precursor']}, data {out['data']}")
     # 2. training
-    gen = binding.Generator(prod.ny, prod.nz, blocks=blocks, in_channels=6, batch=batch)
+    gen = binding.Generator(prod.ny, prod.nz, blocks=blocks, in_channels=6, batch=batch, stride=stride)
     gen.set_params(inputs.generator_params(seed, 128, blocks, 6))
     gen.set_norm(mean, std, rms)
     gen.set_noise(noise, seed=seed + 17)
     out["train"] = train(gen, planes, train_steps, seed=seed)
     out["train"]["n_params"] = gen.n_params
-    out["train"]["baselines"] = baselines(planes, mean, std, int(planes.shape[0] * 0.9))
-    diag_gen = binding.Generator(prod.ny, prod.nz, blocks=blocks, in_channels=6, batch=1)
+    out["train"]["baselines"] = baselines(planes, mean, std, int(planes.shape[0] * 0.9), stride)
+    diag_gen = binding.Generator(prod.ny, prod.nz, blocks=blocks, in_channels=6, batch=1, stride=stride)
     diag_gen.set_params(gen.params())
     diag_gen.set_norm(mean, std, rms)
     out["rollout"] = rollout_diagnostics(diag_gen, planes,
-                                         tuple(k for k in (1, 10, 100, 1000, 3000) if k <= max(run_steps, 1)))
+                                         tuple(k for k in (1, 10, 100, 300, 800) if k * stride <= max(run_steps, 1)))
     diag_gen.close()
     log(f"training: final train {out['train']['train'][-1]:.4g} val {out['train']['val'][-1]:.4g} "
         f"in {out['train']['seconds']:.1f} s")
-    seed_prev = planes[-2].clone()
+    seed_prev = planes[-1 - stride].clone()
     seed_cur = planes[-1].clone()
     del planes
     torch.cuda.empty_cache()
@@ -376,15 +380,20 @@ def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3
     log(f"R: {res['R']['tu']} St {res['R']['strouhal']:.3f} Y {res['R']['y_rms']:.3f}")
     s = binding.Solver(drv, precision, noise=inputs.initial_noise(drv), inflow=True)
     # the generator shares the solver's stream: rollout k is ordered before step k
-    gen_run = binding.Generator(prod.ny, prod.nz, blocks=blocks, in_channels=6, batch=1, stream=s.stream)
+    gen_run = binding.Generator(prod.ny, prod.nz, blocks=blocks, in_channels=6, batch=1, stream=s.stream,
+                                stride=stride)
     gen_run.set_params(gen.params())
     gen_run.set_norm(mean, std, rms)
     gen.close()
     gen_run.rollout_init(seed_prev.cpu().numpy(), seed_cur.cpu().numpy())
     ptrs = binding.ibm_inflow_planes(s.state)
     fp64 = precision == binding.IBM_FP64
-    res["G"] = run_flag(s, run_steps, discard, st_d, sample_every,
-                        before_step=lambda k: gen_run.rollout(*ptrs, precision=precision))
+    def generated(k):
+        # a keyframe every `stride` steps, planes in between interpolated in time
+        if k % stride == 0:
+            gen_run.rollout(None, None, None, precision=precision)
+        gen_run.emit((k % stride) / stride, *ptrs, precision=precision)
+    res["G"] = run_flag(s, run_steps, discard, st_d, sample_every, before_step=generated)
     s.close()
     gen_run.close()
     log(f"G: {res['G']['tu']} St {res['G']['strouhal']:.3f} Y {res['G']['y_rms']:.3f}")
@@ -426,13 +435,14 @@ def main(argv=None):
     ap.add_argument("--blocks", type=int, default=13)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--re", type=float, default=None, help="Reynolds number of every run (default: the workload's)")
-    ap.add_argument("--noise", type=float, default=0.01, help="training-input noise, normalised units")
+    ap.add_argument("--noise", type=float, default=0.03, help="training-input noise, normalised units")
+    ap.add_argument("--stride", type=int, default=10, help="solver steps between generated keyframes")
     ap.add_argument("--out", default="inflow_campaign.json")
     a = ap.parse_args(argv)
     from . import build
     build.build()
     res = campaign(a.spin, a.record, a.train_steps, a.run_steps, a.discard, a.blocks, a.batch, re=a.re,
-                   noise=a.noise)
+                   noise=a.noise, stride=a.stride)
     with open(a.out, "w") as f:
         json.dump(res, f, indent=1, default=lambda o: o.tolist() if hasattr(o, "tolist") else str(o))
     print(json.dumps(res["comparison"], indent=1, default=str))

@@ -223,6 +223,49 @@ def test_rollout_matches_oracle(lib):
     gen.close()
 
 
+def test_keyframe_stride_and_interpolated_planes(lib):
+    """Stride s: the first training loss is the oracle's on (t - s, t, t + s);
+    rollout keyframes and the planes emitted between them are
+    mean + std ((1 - w) q_prev + w q_t)."""
+    from oracle import generator as og
+    from paper_2103_08246_gb300 import binding, inputs
+    s = 3
+    planes = inputs.advected_planes(16, NY, NZ, seed=6, shift=1)
+    mean = planes.mean(axis=(0, 2, 3))
+    std = planes.std(axis=(0, 2, 3))
+    gen = binding.Generator(NY, NZ, blocks=BLOCKS, in_channels=CIN, batch=BATCH, stride=s)
+    w = _params(16)
+    gen.set_params(w)
+    gen.set_norm(mean, std, [1.0, 1.0, 1.0])
+    dev = torch.as_tensor(planes.astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    idx = [3, 12]
+    pl32 = planes.astype(np.float32).astype(np.float64)
+    m32 = mean.astype(np.float32).astype(np.float64)
+    inv = (np.float32(1.0) / std.astype(np.float32)).astype(np.float64)
+
+    def q(t):
+        return np.moveaxis((pl32[t] - m32[:, None, None]) * inv[:, None, None], 0, -1)
+    p = og.unflatten(w.astype(np.float32).astype(np.float64), 128, BLOCKS, CIN)
+    xs = [og.make_input(q(t), q(t - s), CIN) for t in idx]
+    ts = [q(t + s) - q(t) for t in idx]
+    loss_ref, _ = og.loss_and_grads(p, xs, ts, bf16=True)
+    assert abs(gen.eval(dev, idx) - loss_ref) <= 1e-3 * loss_ref
+    with pytest.raises(binding.IBMError):
+        gen.eval(dev, [2, 5])            # t - s < 0
+    gen.rollout_init(planes[0], planes[3])
+    gen.rollout(None, None, None, precision=binding.IBM_FP32)
+    q_t, q_prev = gen.history()
+    out = [torch.zeros((NY, NZ), dtype=torch.float64, device="cuda") for _ in range(3)]
+    torch.cuda.synchronize()
+    gen.emit(0.25, *[o.data_ptr() for o in out], precision=binding.IBM_FP64)
+    gen.sync()
+    for c in range(3):
+        ref = m32[c] + std.astype(np.float32)[c] * (0.75 * q_prev[..., c] + 0.25 * q_t[..., c])
+        assert np.abs(out[c].cpu().numpy() - ref).max() <= 1e-5 * std[c]
+    gen.close()
+
+
 def test_bad_configurations_are_refused(lib):
     from paper_2103_08246_gb300 import binding
     for kw in ({"nz": 100}, {"nz": 64}, {"blocks": -1}, {"in_channels": 7}, {"batch": 0}, {"batch": 65}):

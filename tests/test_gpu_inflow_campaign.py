@@ -27,8 +27,8 @@ def test_small_campaign_runs(lib):
     base = inputs.PRODUCTION.replace(name="campaign-128x32x128", nx=128, ny=32, nz=128, lx=128 * h,
                                      ly=32 * h, lz=128 * h, flag_ns=17, flag_nt=17, flag_x_le=3.0)
     # 150 steps carry the bar wakes past x = 2 at this spacing
-    out = inflow.campaign(spin=150, record=40, train_steps=10, run_steps=200, discard=150, blocks=1, batch=2,
-                          base=base, sample_every=5, log=lambda *a: None)
+    out = inflow.campaign(spin=150, record=60, train_steps=10, run_steps=200, discard=150, blocks=1, batch=2,
+                          base=base, sample_every=5, log=lambda *a: None, stride=2)
     json.dumps(out, default=str)
     assert out["train"]["n_params"] == inputs.generator_param_count(128, 1, 6)
     assert all(np.isfinite(out["train"]["train"])) and all(np.isfinite(out["train"]["val"]))
