@@ -54,7 +54,7 @@ METHOD_PASSES = 57
 # (profiles/dram_traffic_production_fp32.md); valid for the kernels of that
 # capture and to be refreshed whenever one of them changes.
 TRAFFIC_BYTES = {"rhs": 1743.7e6, "project": 1199.9e6, "af_yz": 1156.7e6, "af_x": 755.0e6,
-                 "mass_div": 520.9e6, "poisson_x": 408.2e6}
+                 "mass_div": 520.9e6, "poisson_x": 408.2e6, "dht2d": 205.8e6}
 # FP64 path: the explicit stage's FP64 instructions per cell (DFMA + DMUL +
 # DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of
 # GB300 (2 per clock per SM): the FP64 step is bound by that pipe.
@@ -82,6 +82,9 @@ def parse():
                     help="only run this many launches of each generator kernel timing "
                          "(residual-block convolution, input gradient, weight gradient; "
                          "256x256 planes, batch 8) for ncu and exit")
+    ap.add_argument("--profile-generator-train", type=int, default=0,
+                    help="only run this many generator training steps (256x256 planes, "
+                         "batch 8, 13 blocks) after one warm step, for ncu, and exit")
     return ap.parse_args()
 
 
@@ -110,6 +113,16 @@ def run_profile_generator(args):
     g.set_params(inputs.generator_params(0, 128, 1, 6))
     for what in ("conv_fwd", "conv_dgrad", "conv_wgrad"):
         print(what, "ms", g.time(what, args.profile_generator))
+    g.close()
+
+
+def run_profile_generator_train(args):
+    """Plain run for profilers: training steps of the production-size generator."""
+    from paper_2103_08246_gb300 import binding, build, inputs
+    build.build()
+    g = binding.Generator(256, 256, blocks=13, in_channels=6, batch=8)
+    g.set_params(inputs.generator_params(0, 128, 13, 6))
+    print("train_step ms", g.time("train_step", args.profile_generator_train))
     g.close()
 
 
@@ -431,7 +444,15 @@ def generator_rate(bf16_peak, peak_kind, nrep=10):
     ms_roll = g1.time("forward", nrep)
     g1.close()
     conv_flops = 2.0 * batch * ny * nz * 9 * 128 * 128
+    # algorithmic bytes of the residual-block convolution: read the bf16
+    # activation and the FP32 residual, write the FP32 sum and its bf16
+    # activation (the weights and the halo rows come from L2)
+    conv_bytes = batch * ny * nz * 128 * (2 + 4 + 4 + 2)
     tf = lambda fl, ms: fl / (ms * 1e-3) / 1e12
+    hbm_peak, hbm_kind = measured_peaks()
+    gbs = conv_bytes / (ms_conv * 1e-3) / 1e9
+    # the binding roof: HBM (0.119 ms at the measured copy bandwidth) above
+    # the tensor pipe (0.082 ms at the measured bf16 burst)
     return {"plane": f"{ny}x{nz}", "blocks": blocks, "width": 128, "batch": batch,
             "params": inputs.generator_param_count(128, blocks, 6),
             "train_step_ms": ms_train, "train_samples_per_s": batch / ms_train * 1e3,
@@ -439,10 +460,13 @@ def generator_rate(bf16_peak, peak_kind, nrep=10):
             "forward_ms": ms_fwd, "forward_tflops": tf(batch * fwd, ms_fwd),
             "rollout_forward_ms": ms_roll,
             "conv_ms": {"fwd": ms_conv, "dgrad": ms_dgrad, "wgrad": ms_wgrad},
-            "roofline": {"kernel": "k_conv<128,128> (residual block, forward)", "bound": "tensor",
-                         "achieved": tf(conv_flops, ms_conv), "peak": bf16_peak, "peak_kind": peak_kind,
-                         "unit": "TFLOP/s", "frac": tf(conv_flops, ms_conv) / bf16_peak,
-                         "traffic": None, "flops_per_launch": conv_flops, "ms_per_launch": ms_conv},
+            "roofline": {"kernel": "k_conv<128,128,256> (residual block, forward)", "bound": "hbm",
+                         "achieved": gbs, "peak": hbm_peak, "peak_kind": hbm_kind, "unit": "GB/s",
+                         "frac": gbs / hbm_peak, "traffic": None, "bytes_per_launch": conv_bytes,
+                         "ms_per_launch": ms_conv},
+            "tensor": {"achieved": tf(conv_flops, ms_conv), "peak": bf16_peak, "peak_kind": peak_kind,
+                       "unit": "TFLOP/s", "frac": tf(conv_flops, ms_conv) / bf16_peak,
+                       "flops_per_launch": conv_flops},
             "wgrad_tflops": tf(conv_flops, ms_wgrad), "dgrad_tflops": tf(conv_flops, ms_dgrad)}
 
 
@@ -551,6 +575,9 @@ def main():
         return
     if args.profile_generator > 0:
         run_profile_generator(args)
+        return
+    if args.profile_generator_train > 0:
+        run_profile_generator_train(args)
         return
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

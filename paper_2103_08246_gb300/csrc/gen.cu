@@ -17,24 +17,25 @@
 // Kernels:
 //  * k_conv: implicit-GEMM convolution on tiles of 256 (or 128) pixels of
 //    one image row (nz a multiple of 128) and all N output channels,
-//    persistent (one CTA per SM) and warp-specialised. Per K block (one tap
-//    row dy, 32 input channels) four copy warps stage the haloed row segment
-//    and the three taps' weights with 16-byte cp.async copies into K-major
-//    core-matrix tiles whose pixel dimension is linear in 16-byte rows, so
-//    the three z taps (and the two 128-pixel halves) are start addresses of
-//    one tile; one thread issues 3 x 2 x 2 MMAs (M = 128, N, K = 16) per
-//    block into the tile's two tensor-memory accumulators. Four stages, two
-//    blocks of copies in flight ahead of the MMAs, hand-offs by mbarriers
-//    only. Four epilogue warps (bias, residual, activation, or the
-//    activation derivative of the backward pass; tcgen05.ld rows, one pixel
-//    per thread) drain one tile's accumulators while the MMAs fill the
-//    other buffer.
-//    Forward and input-gradient passes are the same kernel: the input
-//    gradient is a convolution with the flipped, transposed weights.
+//    persistent (one CTA per SM) and warp-specialised. Feature maps are
+//    bfloat16 in 16-byte granules of 8 channels, pixel-fastest within a
+//    channel group, so per K block (one tap row dy, 32 input channels) one
+//    thread fills a stage with bulk copies (cp.async.bulk): per 8-channel
+//    group the haloed run of pixels into a K-major core-matrix strip whose
+//    pixel dimension is linear in 16-byte rows (the three z taps and the two
+//    128-pixel halves are then start addresses of one tile), and the three
+//    taps' weights from a pre-packed image of the stage. One thread issues
+//    3 x 2 x 2 MMAs (M = 128, N, K = 16) per block into the tile's two
+//    tensor-memory accumulators. Four stages, hand-offs by mbarriers only.
+//    Eight epilogue warps (bias, residual, activation, or the activation
+//    derivative of the backward pass; tcgen05.ld rows, one pixel per
+//    thread) drain one tile's accumulators while the MMAs fill the other
+//    buffer. Forward and input-gradient passes are the same kernel: the
+//    input gradient is a convolution with the flipped, transposed weights.
 //  * k_wgrad: weight gradients dW[tap][o][c] = sum_p G[p][o] X[p + tap][c],
-//    K = pixels: MN-major operand tiles straight from the channels-last maps
-//    (a pixel's channels are one core-matrix row), the three z taps again as
-//    start-address shifts of the haloed tile, three accumulators (one per
+//    K = pixels: MN-major operand tiles bulk-copied from the granule maps
+//    (8 channels of a pixel are one core-matrix row), the three z taps again
+//    as start-address shifts of the haloed tile, three accumulators (one per
 //    tap) in tensor memory; blocks of 128 pixels filled by bulk copies from
 //    two threads (one per operand), three stages; CTAs split the pixels,
 //    their partials are summed in a fixed order (deterministic training).
@@ -63,7 +64,8 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int CV_THREADS = 256;
+constexpr int CV_THREADS = 384;                // copy warp, MMA warp, 2 idle, 8 epilogue warps
+constexpr int CV_EPI_THREADS = 256;
 constexpr int CV_STAGES = 4;
 
 template <int N, int KC, int TM>
@@ -219,8 +221,9 @@ __device__ inline void conv_epilogue(const ConvArgs& g, size_t row, int z, int c
 //    tile's tensor-memory buffer (two buffers, alternating by tile) and
 //    commits them to the stage's `empty` barrier, after the tile's last
 //    block also to the buffer's `tfull` barrier;
-//  * warps 4-7 run the epilogue of tile i from its buffer while the MMAs of
-//    tile i + 1 fill the other one, then arrive on the buffer's `tempty`.
+//  * warps 4-11 run the epilogue of tile i from its buffer (two warps per
+//    lane quarter, each half of the columns) while the MMAs of tile i + 1
+//    fill the other one, then arrive on the buffer's `tempty`.
 template <int N, int KC, int TM>
 __global__ void __launch_bounds__(CV_THREADS, 1) k_conv(ConvArgs g) {
   using C = ConvCfg<N, KC, TM>;
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(CV_THREADS, 1) k_conv(ConvArgs g) {
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 128);
+      mbar_init(&tempty[b], CV_EPI_THREADS);
     }
     fence_mbar_init();
   }
@@ -310,9 +313,11 @@ __global__ void __launch_bounds__(CV_THREADS, 1) k_conv(ConvArgs g) {
       }
     }
   } else if (warp >= 4) {
-    // epilogue warps: lane quarter warp - 4, all columns, both halves
-    const int quarter = warp - 4;
+    // epilogue warps 4 .. 11: lane quarter warp % 4; warps w and w + 4 split
+    // the columns (narrow outputs: warps 4 .. 7 take all of them)
+    const int quarter = warp & 3, part = (warp - 4) >> 2;
     constexpr int CW = N < 32 ? N : 32;
+    constexpr int SPLIT = N >= 64 ? 2 : 1;
     for (int lt = 0; lt < my_tiles; ++lt) {
       const int tile = blockIdx.x + lt * gridDim.x;
       const int row = tile / tiles_per_row, z0 = (tile - row * tiles_per_row) * TM;
@@ -323,7 +328,7 @@ __global__ void __launch_bounds__(CV_THREADS, 1) k_conv(ConvArgs g) {
       for (int h = 0; h < TM / 128; ++h) {
         const int z = z0 + h * 128 + quarter * 32 + lane;
 #pragma unroll 1
-        for (int c0 = 0; c0 < N; c0 += CW) {
+        for (int c0 = part * (N / SPLIT); c0 < (part + 1) * (N / SPLIT) && part < SPLIT; c0 += CW) {
           float v[CW];
           const uint32_t ta = dbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(h * N + c0);
           if constexpr (CW == 32) tc_ld_x32(ta, v); else tc_ld_x16(ta, v);
@@ -509,31 +514,70 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, int chunks, int N
 }
 
 // bias gradients out[c] = sum_p x[p][c]: the flat array [pixels][C] is split
-// into equal runs, one per block; thread t of a block (blockDim a multiple of
-// C) sums the elements t, t + blockDim, ... of its run (channel t mod C), four
-// loads in flight; a second kernel adds the partials in a fixed order
+// into equal runs, one per block (a multiple of the block's span); thread t
+// of a block sums the elements t, t + span, ... of its run (about a hundred
+// values, in FP32: the FP64 pipe of this part is far too narrow for per-
+// element double additions), four loads in flight, into entries of its
+// block's partial row whose index mod C is the channel; the partials are
+// added in FP64. Float4 variant (C a multiple of 4, 4 channels per thread,
+// span 4 blockDim) and scalar variant (span blockDim, a multiple of C).
 constexpr int COLSUM_BLOCKS = 608;   // 4 per SM
-__global__ void __launch_bounds__(256) k_colsum_part(const float* __restrict__ x, size_t n, double* __restrict__ part) {
-  const size_t per = ((n + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
-  const size_t lo = (size_t)blockIdx.x * per, hi = min(n, lo + per);
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+__global__ void __launch_bounds__(256) k_colsum_part4(const float4* __restrict__ x, size_t n4,
+                                                      double* __restrict__ part) {
+  const size_t per = ((n4 + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const size_t lo = (size_t)blockIdx.x * per, hi = min(n4, lo + per);
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
   const size_t st = blockDim.x;
   size_t i = lo + threadIdx.x;
   for (; i + 3 * st < hi; i += 4 * st) {
-    const float a = x[i], b = x[i + st], c = x[i + 2 * st], d = x[i + 3 * st];
-    s0 += a; s1 += b; s2 += c; s3 += d;
+    const float4 a = x[i], b = x[i + st], c = x[i + 2 * st], d = x[i + 3 * st];
+    s.x += (a.x + b.x) + (c.x + d.x);
+    s.y += (a.y + b.y) + (c.y + d.y);
+    s.z += (a.z + b.z) + (c.z + d.z);
+    s.w += (a.w + b.w) + (c.w + d.w);
   }
-  for (; i < hi; i += st) s0 += x[i];
-  part[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = (s0 + s1) + (s2 + s3);
+  for (; i < hi; i += st) {
+    const float4 a = x[i];
+    s.x += a.x; s.y += a.y; s.z += a.z; s.w += a.w;
+  }
+  double* o = part + ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  o[0] = s.x; o[1] = s.y; o[2] = s.z; o[3] = s.w;
 }
 
-__global__ void k_colsum_final(const double* __restrict__ part, int blocks, int S, int Cc, float* __restrict__ out) {
-  const int c = threadIdx.x;
-  if (c >= Cc) return;
+__global__ void __launch_bounds__(256) k_colsum_part(const float* __restrict__ x, size_t n, double* __restrict__ part) {
+  const size_t per = ((n + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
+  const size_t lo = (size_t)blockIdx.x * per, hi = min(n, lo + per);
+  float s0 = 0.f, s1 = 0.f;
+  const size_t st = blockDim.x;
+  size_t i = lo + threadIdx.x;
+  for (; i + st < hi; i += 2 * st) {
+    s0 += x[i];
+    s1 += x[i + st];
+  }
+  for (; i < hi; i += st) s0 += x[i];
+  part[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = (double)s0 + (double)s1;
+}
+
+// one block per channel: the entries e = c mod C of every block's partial
+// row (S entries), summed in a fixed order (deterministic)
+__global__ void __launch_bounds__(256) k_colsum_final(const double* __restrict__ part, int blocks, int S, int Cc,
+                                                      float* __restrict__ out) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  const int per_block = S / Cc;
+  const int total = blocks * per_block;
   double s = 0.0;
-  for (int bl = 0; bl < blocks; ++bl)
-    for (int k = c; k < S; k += Cc) s += part[(size_t)bl * S + k];
-  out[c] = (float)s;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int bl = i / per_block, k = c + (i - bl * per_block) * Cc;
+    s += part[(size_t)bl * S + k];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = (float)red[0];
 }
 
 struct TIdx {
@@ -669,12 +713,18 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-__global__ void k_sum_double(const double* __restrict__ part, int n, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *out = s;
+// sum of n partials in a fixed order: strided per thread, then a tree
+__global__ void __launch_bounds__(256) k_sum_double(const double* __restrict__ part, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *out = red[0];
 }
 
 // Adam; ob1 = 1 - b1, ob2 = 1 - b2 and the bias corrections c1 = 1 / (1 - b1^t),
@@ -948,9 +998,14 @@ void wgrad(ibm_gen* g, const bf16* a, const bf16* b, int nb, int shift_a, int tr
 }
 
 void colsum(ibm_gen* g, const float* x, size_t pixels, int C, float* out) {
-  const int S = (C == 3) ? 192 : 256;   // threads per block, a multiple of C
-  ibm::k_colsum_part<<<ibm::COLSUM_BLOCKS, S, 0, g->stream>>>(x, pixels * C, g->dpart);
-  ibm::k_colsum_final<<<1, 128, 0, g->stream>>>(g->dpart, ibm::COLSUM_BLOCKS, S, C, out);
+  if (C % 4 == 0) {   // 256 threads x 4 channels: a row of 1024 partials per block (1024 = 0 mod C)
+    ibm::k_colsum_part4<<<ibm::COLSUM_BLOCKS, 256, 0, g->stream>>>(reinterpret_cast<const float4*>(x),
+                                                                    pixels * C / 4, g->dpart);
+    ibm::k_colsum_final<<<C, 256, 0, g->stream>>>(g->dpart, ibm::COLSUM_BLOCKS, 1024, C, out);
+  } else {            // C = 3: 192 threads, one channel each
+    ibm::k_colsum_part<<<ibm::COLSUM_BLOCKS, 192, 0, g->stream>>>(x, pixels * C, g->dpart);
+    ibm::k_colsum_final<<<C, 256, 0, g->stream>>>(g->dpart, ibm::COLSUM_BLOCKS, 192, C, out);
+  }
 }
 
 // loss gradients of B samples whose input x and target are in place
@@ -962,7 +1017,7 @@ void backward(ibm_gen* g, int B) {
   const int lb = (int)((n + LOSS_THREADS - 1) / LOSS_THREADS);
   k_loss<<<lb, LOSS_THREADS, 0, g->stream>>>(g->delta, g->target, (int)n, g->nz, (float)(2.0 / (3.0 * n)),
                                              g->gd16, g->gd32, g->dpart);
-  k_sum_double<<<1, 32, 0, g->stream>>>(g->dpart, lb, g->dscal);
+  k_sum_double<<<1, 256, 0, g->stream>>>(g->dpart, lb, g->dscal);
   const Layer& Lo = g->layers.back();
   // output layer: dW_out^T = sum act_L[p + tap] gd[p]; db_out; g_{L+1} = phi' * conv(Wb_out, gd)
   wgrad(g, act_map(g, g->blocks), g->gd16, 16, 1, 1, Lo, rows);
@@ -1071,7 +1126,7 @@ int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out) {
        dalloc(g, &g->h[1], BP * WIDTH) && dalloc(g, &g->g32[0], BP * WIDTH) && dalloc(g, &g->g32[1], BP * WIDTH) &&
        dalloc(g, &g->delta, BP * 3) && dalloc(g, &g->target, BP * 3) && dalloc(g, &g->gd32, BP * 3) &&
        dalloc(g, &g->part, (size_t)3 * WG_CHUNKS * 3 * 128 * WIDTH) &&
-       dalloc(g, &g->dpart, (size_t)std::max<size_t>(COLSUM_BLOCKS * 256, BP / LOSS_THREADS + 1)) &&
+       dalloc(g, &g->dpart, (size_t)std::max<size_t>(COLSUM_BLOCKS * 1024, BP / LOSS_THREADS + 1)) &&
        dalloc(g, &g->dscal, 8) && dalloc(g, &g->hist[0], g->P * 3) && dalloc(g, &g->hist[1], g->P * 3) &&
        dalloc(g, &g->error, 1);
   if (!ok) {
@@ -1202,7 +1257,7 @@ int ibm_gen_eval(ibm_gen* g, const float* planes, int n_planes, const int* t_idx
   const int lb = (int)((n + ibm::LOSS_THREADS - 1) / ibm::LOSS_THREADS);
   ibm::k_loss<<<lb, ibm::LOSS_THREADS, 0, g->stream>>>(g->delta, g->target, (int)n, g->nz,
                                                        (float)(2.0 / (3.0 * n)), g->gd16, g->gd32, g->dpart);
-  ibm::k_sum_double<<<1, 32, 0, g->stream>>>(g->dpart, lb, g->dscal);
+  ibm::k_sum_double<<<1, 256, 0, g->stream>>>(g->dpart, lb, g->dscal);
   return read_loss(g, n, loss);
 }
 
