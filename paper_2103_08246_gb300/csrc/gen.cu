@@ -44,6 +44,8 @@
 // Every mbarrier wait is bounded; on expiry the kernel sets the error flag,
 // waits (bounded) for its own tensor-core work, frees its tensor memory and
 // returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -91,10 +93,20 @@ struct ConvCfg {
 __device__ inline float phi(float s) { return s > 0.f ? s : 0.125f * s; }
 
 // bfloat16 maps are stored in 16-byte granules of 8 channels, pixel-fastest
-// within a channel group: granule (row, group, z) at ((row C/8 + group) nz + z),
-// so that one channel group of a run of pixels is contiguous (one bulk copy)
+// within a channel group, with one periodic halo granule at each end of every
+// (row, group) run: slot z + 1 holds pixel z, slot 0 pixel nz - 1, slot
+// nz + 1 pixel 0. A channel group of a haloed run of pixels is then one
+// contiguous block (one bulk copy, one tensor-map box, no wrap).
 __host__ __device__ inline size_t granule(size_t row, int group, int z, int C, int nz) {
-  return (row * (size_t)(C / 8) + group) * nz + z;
+  return (row * (size_t)(C / 8) + group) * (size_t)(nz + 2) + (size_t)(z + 1);
+}
+__host__ __device__ inline size_t map_elems(size_t rows, int C, int nz) { return rows * (size_t)(C / 8) * (nz + 2) * 8; }
+
+// store granule (row, group, z) and its halo copy
+__device__ inline void store_granule(bf16* map, size_t row, int group, int z, int C, int nz, uint4 v) {
+  *reinterpret_cast<uint4*>(map + granule(row, group, z, C, nz) * 8) = v;
+  if (z == 0) *reinterpret_cast<uint4*>(map + granule(row, group, nz, C, nz) * 8) = v;
+  if (z == nz - 1) *reinterpret_cast<uint4*>(map + granule(row, group, -1, C, nz) * 8) = v;
 }
 
 // byte offset of weight (tap, row n, input channel k) in the shared-memory
@@ -117,21 +129,13 @@ __device__ inline void bulk_g2s_u32(uint32_t dst, const void* src, uint32_t byte
       : "memory");
 }
 
-// granules z = zs .. zs + n - 1 (periodic in nz, n <= nz + 2) of one channel
-// group of one image row, contiguous at dst: one to three bulk copies
-__device__ inline void copy_strip(uint32_t dst, const bf16* map, size_t first_granule, int nz, int zs, int n,
-                                  uint64_t* bar) {
-  const char* base = reinterpret_cast<const char*>(map) + first_granule * 16;
-  int done = 0, z = zs;
-  if (z < 0) {
-    bulk_g2s_u32(dst, base + (size_t)(nz + z) * 16, (uint32_t)(-z) * 16, bar);
-    done = -z;
-    z = 0;
-  }
-  const int m = min(n - done, nz - z);
-  bulk_g2s_u32(dst + (uint32_t)done * 16, base + (size_t)z * 16, (uint32_t)m * 16, bar);
-  done += m;
-  if (done < n) bulk_g2s_u32(dst + (uint32_t)done * 16, base, (uint32_t)(n - done) * 16, bar);
+// bulk copy of the tensor-map box at coordinates (x, y, z) of a 3-D map
+__device__ inline void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
 }
 
 struct ConvArgs {
@@ -204,7 +208,7 @@ __device__ inline void conv_epilogue(const ConvArgs& g, size_t row, int z, int c
         const float x = v[8 * q + j];
         e[j] = __float2bfloat16_rn(g.out16_phi ? phi(x) : x);
       }
-      *reinterpret_cast<uint4*>(g.out16 + granule(row, c0 / 8 + q, z, N, g.nz) * 8) = raw;
+      store_granule(g.out16, row, c0 / 8 + q, z, N, g.nz, raw);
     }
   }
 }
@@ -275,10 +279,14 @@ __global__ void __launch_bounds__(CV_THREADS, 1) k_conv(ConvArgs g) {
         const size_t rr = (size_t)(b * g.ny + yy);
         const uint32_t sa = sbase + (uint32_t)s * C::STAGE;
         mbar_arrive_expect_tx(&full[s], A_TX + B_TX);
+        const char* src = reinterpret_cast<const char*>(g.in) + granule(rr, cb * C::KG, z0 - 1, KC, g.nz) * 16;
+        if (C::ALBO == (uint32_t)(g.nz + 2) * 16) {   // the groups' runs are adjacent here too: one copy
+          bulk_g2s_u32(sa, src, A_TX, &full[s]);
+        } else {
 #pragma unroll
-        for (int kg = 0; kg < C::KG; ++kg)
-          copy_strip(sa + (uint32_t)kg * C::ALBO, g.in, granule(rr, cb * C::KG + kg, 0, KC, g.nz), g.nz, z0 - 1,
-                     C::AROWS, &full[s]);
+          for (int kg = 0; kg < C::KG; ++kg)
+            bulk_g2s_u32(sa + (uint32_t)kg * C::ALBO, src + (size_t)kg * (g.nz + 2) * 16, C::AROWS * 16, &full[s]);
+        }
         bulk_g2s_u32(sa + C::A_BYTES, g.w + (size_t)(dyi * C::CB + cb) * B_TX, B_TX, &full[s]);
       }
     }
@@ -351,8 +359,8 @@ __global__ void __launch_bounds__(CV_THREADS, 1) k_conv(ConvArgs g) {
 // ---- weight gradients
 constexpr int WG_THREADS = 256;
 constexpr int WG_KP = 128;                 // pixels per K block
-constexpr uint32_t WG_SBO_H = 131 * 16;    // 8-channel strip, 130 haloed rows (odd x 16: no bank conflicts)
-constexpr uint32_t WG_SBO_P = 129 * 16;    // 8-channel strip, 128 rows
+constexpr uint32_t WG_SBO_H = (WG_KP + 2) * 16;   // 8-channel strip of the haloed operand (a box row block)
+constexpr uint32_t WG_SBO_P = WG_KP * 16;         // 8-channel strip of the other operand
 constexpr int WG_STAGES = 3;
 
 template <int NB>
@@ -372,12 +380,16 @@ struct WgArgs {
   int* error;
 };
 
-// Two threads fill the stages with bulk copies (warp 0: the M operand,
-// warp 2: the N operand; per 8-channel group one strip of the run of pixels,
-// the shifted operand with its halo), warp 1 (one thread) issues the MMAs;
-// after the last block all warps read the three accumulators out.
+// Two threads fill the stages, one tensor-map box per operand and stage
+// (warp 0: the M operand, all 16 channel groups of the run of pixels; warp 2:
+// the N operand; the shifted one with its halo, which the maps store), warp 1
+// (one thread) issues the MMAs; after the last block all warps read the three
+// accumulators out. Maps: 3-D (8 channels, nz + 2 slots, rows x groups),
+// boxes (8, 128 or 130, groups): the box lands as [group][pixel][8], the
+// MN-major core-matrix strips.
 template <int NB>
-__global__ void __launch_bounds__(WG_THREADS, 1) k_wgrad(WgArgs g) {
+__global__ void __launch_bounds__(WG_THREADS, 1) k_wgrad(WgArgs g, const __grid_constant__ CUtensorMap map_a,
+                                                        const __grid_constant__ CUtensorMap map_b) {
   using C = WgCfg<NB>;
   extern __shared__ __align__(1024) unsigned char wsm[];
   __shared__ uint64_t full[WG_STAGES], empty[WG_STAGES];
@@ -425,14 +437,11 @@ __global__ void __launch_bounds__(WG_THREADS, 1) k_wgrad(WgArgs g) {
       if (is_a) {
         mbar_arrive_expect_tx(&full[s], 16 * rows_a * 16);
         const int ra = g.shift_a ? rs : rr, za = g.shift_a ? zb - 1 : zb;
-        for (int cg = 0; cg < 16; ++cg)
-          copy_strip(sa + (uint32_t)cg * sbo_a, g.a, granule(ra, cg, 0, 128, g.nz), g.nz, za, rows_a, &full[s]);
+        tma_load_3d(sa, &map_a, 0, za + 1, ra * 16, &full[s]);
       } else {
         mbar_arrive_expect_tx(&full[s], (NB / 8) * rows_b * 16);
         const int rb = g.shift_a ? rr : rs, zbb = g.shift_a ? zb : zb - 1;
-        for (int cg = 0; cg < NB / 8; ++cg)
-          copy_strip(sa + a_bytes + (uint32_t)cg * sbo_b, g.b, granule(rb, cg, 0, NB, g.nz), g.nz, zbb, rows_b,
-                     &full[s]);
+        tma_load_3d(sa + a_bytes, &map_b, 0, zbb + 1, rb * (NB / 8), &full[s]);
       }
     }
   } else if (warp == 1) {
@@ -645,8 +654,8 @@ __global__ void k_input_planes(const float* __restrict__ planes, int P, int nz, 
   }
   const size_t row = (size_t)i / nz;
   const int z = i - (int)(row * nz);
-  *reinterpret_cast<uint4*>(x + granule(row, 0, z, 16, nz) * 8) = r0;
-  *reinterpret_cast<uint4*>(x + granule(row, 1, z, 16, nz) * 8) = r1;
+  store_granule(x, row, 0, z, 16, nz, r0);
+  store_granule(x, row, 1, z, 16, nz, r1);
 }
 
 // network input from normalised planes [B][P][3]
@@ -669,8 +678,8 @@ __global__ void k_input_q(const float* __restrict__ qt, const float* __restrict_
   }
   const size_t row = (size_t)i / nz;
   const int z = i - (int)(row * nz);
-  *reinterpret_cast<uint4*>(x + granule(row, 0, z, 16, nz) * 8) = r0;
-  *reinterpret_cast<uint4*>(x + granule(row, 1, z, 16, nz) * 8) = r1;
+  store_granule(x, row, 0, z, 16, nz, r0);
+  store_granule(x, row, 1, z, 16, nz, r1);
 }
 
 // gradient of the mean-square loss in delta (bf16, 16 channels, and FP32),
@@ -701,8 +710,8 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss(const float* __restrict__
     }
     const size_t row = (size_t)i / nz;
     const int z = i - (int)(row * nz);
-    *reinterpret_cast<uint4*>(gd16 + granule(row, 0, z, 16, nz) * 8) = r0;
-    *reinterpret_cast<uint4*>(gd16 + granule(row, 1, z, 16, nz) * 8) = r1;
+    store_granule(gd16, row, 0, z, 16, nz, r0);
+    store_granule(gd16, row, 1, z, 16, nz, r1);
   }
   red[threadIdx.x] = se;
   __syncthreads();
@@ -879,8 +888,8 @@ void launch_conv(const ConvArgs& a, cudaStream_t s) {
 }
 
 template <int NB>
-void launch_wgrad(const WgArgs& a, cudaStream_t s) {
-  k_wgrad<NB><<<dim3(a.chunks, 3), WG_THREADS, WgCfg<NB>::SMEM, s>>>(a);
+void launch_wgrad(const WgArgs& a, const CUtensorMap& ma, const CUtensorMap& mb, cudaStream_t s) {
+  k_wgrad<NB><<<dim3(a.chunks, 3), WG_THREADS, WgCfg<NB>::SMEM, s>>>(a, ma, mb);
 }
 
 constexpr int WIDTH = 128;     // channels of the residual stream
@@ -928,6 +937,9 @@ struct ibm_gen {
   unsigned long long noise_seed = 0;
   int* error = nullptr;
   std::vector<void*> allocs;
+  // tensor maps of the bfloat16 maps: per base address, boxes of 128 and 130 pixels
+  std::vector<const void*> map_base;
+  std::vector<CUtensorMap> map_box;   // 2 per base: [128-pixel box, 130-pixel box]
 };
 
 namespace {
@@ -945,7 +957,44 @@ bool dalloc(ibm_gen* g, T** p, size_t n) {
   return true;
 }
 
-bf16* act_map(ibm_gen* g, int l) { return g->act + (size_t)l * g->batch * g->P * ibm::WIDTH; }
+bf16* act_map(ibm_gen* g, int l) {
+  return g->act + (size_t)l * ibm::map_elems((size_t)g->batch * g->ny, ibm::WIDTH, g->nz);
+}
+
+// 3-D tensor maps over a C-channel granule map: (8 channels, nz + 2 slots,
+// rows x C/8 groups), boxes (8, 128 or 130 pixels, C/8 groups)
+bool add_maps(ibm_gen* g, const bf16* base, int C) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t rows = (cuuint64_t)g->batch * g->ny;
+  const cuuint64_t dims[3] = {8, (cuuint64_t)g->nz + 2, rows * (C / 8)};
+  const cuuint64_t strides[2] = {16, ((cuuint64_t)g->nz + 2) * 16};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int halo = 0; halo < 2; ++halo) {
+    const cuuint32_t box[3] = {8, (cuuint32_t)(ibm::WG_KP + 2 * halo), (cuuint32_t)(C / 8)};
+    CUtensorMap m;
+    if (encode(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+    g->map_box.push_back(m);
+  }
+  g->map_base.push_back(base);
+  return true;
+}
+
+const CUtensorMap& tmap(const ibm_gen* g, const bf16* base, bool halo) {
+  size_t i = 0;
+  while (i + 1 < g->map_base.size() && g->map_base[i] != base) ++i;
+  return g->map_box[2 * i + (halo ? 1 : 0)];
+}
 
 int check_error(ibm_gen* g) {
   int e = 0;
@@ -992,7 +1041,9 @@ void wgrad(ibm_gen* g, const bf16* a, const bf16* b, int nb, int shift_a, int tr
   WgArgs w{};
   w.a = a; w.b = b; w.shift_a = shift_a; w.ny = g->ny; w.nz = g->nz; w.rows = rows;
   w.chunks = WG_CHUNKS; w.part = g->part; w.error = g->error;
-  if (nb == WIDTH) launch_wgrad<WIDTH>(w, g->stream); else launch_wgrad<16>(w, g->stream);
+  const CUtensorMap& ma = tmap(g, a, shift_a != 0);
+  const CUtensorMap& mb = tmap(g, b, shift_a == 0);
+  if (nb == WIDTH) launch_wgrad<WIDTH>(w, ma, mb, g->stream); else launch_wgrad<16>(w, ma, mb, g->stream);
   const int n = 9 * L.O * L.C;
   k_wgrad_reduce<<<(n + 255) / 256, 256, 0, g->stream>>>(g->part, WG_CHUNKS, nb, trans, L.O, L.C, g->gw + L.woff);
 }
@@ -1118,11 +1169,13 @@ int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out) {
   size_t npack = 0;
   for (auto& L : g->layers) npack += wimg_bytes(L.Op, L.Cp) + wimg_bytes(L.Cp, L.Op);
   const size_t BP = (size_t)g->batch * g->P;
+  const size_t rows = (size_t)g->batch * g->ny;
   bool ok = ready_attr();
   ok = ok && dalloc(g, &g->w, g->np) && dalloc(g, &g->gw, g->np) && dalloc(g, &g->m, g->np) &&
-       dalloc(g, &g->v, g->np) && dalloc(g, &g->wpack, npack) && dalloc(g, &g->x, BP * CIN_PAD) &&
-       dalloc(g, &g->act, (size_t)(g->blocks + 1) * BP * WIDTH) && dalloc(g, &g->g16[0], BP * WIDTH) &&
-       dalloc(g, &g->g16[1], BP * WIDTH) && dalloc(g, &g->gd16, BP * COUT_PAD) && dalloc(g, &g->h[0], BP * WIDTH) &&
+       dalloc(g, &g->v, g->np) && dalloc(g, &g->wpack, npack) && dalloc(g, &g->x, map_elems(rows, CIN_PAD, g->nz)) &&
+       dalloc(g, &g->act, (size_t)(g->blocks + 1) * map_elems(rows, WIDTH, g->nz)) &&
+       dalloc(g, &g->g16[0], map_elems(rows, WIDTH, g->nz)) && dalloc(g, &g->g16[1], map_elems(rows, WIDTH, g->nz)) &&
+       dalloc(g, &g->gd16, map_elems(rows, COUT_PAD, g->nz)) && dalloc(g, &g->h[0], BP * WIDTH) &&
        dalloc(g, &g->h[1], BP * WIDTH) && dalloc(g, &g->g32[0], BP * WIDTH) && dalloc(g, &g->g32[1], BP * WIDTH) &&
        dalloc(g, &g->delta, BP * 3) && dalloc(g, &g->target, BP * 3) && dalloc(g, &g->gd32, BP * 3) &&
        dalloc(g, &g->part, (size_t)3 * WG_CHUNKS * 3 * 128 * WIDTH) &&
@@ -1143,7 +1196,14 @@ int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out) {
   cudaMemsetAsync(g->gw, 0, g->np * sizeof(float), g->stream);
   cudaMemsetAsync(g->m, 0, g->np * sizeof(float), g->stream);
   cudaMemsetAsync(g->v, 0, g->np * sizeof(float), g->stream);
-  cudaMemsetAsync(g->x, 0, BP * CIN_PAD * sizeof(bf16), g->stream);
+  cudaMemsetAsync(g->x, 0, map_elems(rows, CIN_PAD, g->nz) * sizeof(bf16), g->stream);
+  bool maps = add_maps(g, g->x, CIN_PAD) && add_maps(g, g->gd16, COUT_PAD) && add_maps(g, g->g16[0], WIDTH) &&
+              add_maps(g, g->g16[1], WIDTH);
+  for (int l = 0; l <= g->blocks && maps; ++l) maps = add_maps(g, act_map(g, l), WIDTH);
+  if (!maps) {
+    ibm_gen_destroy(g);
+    return IBM_ECUDA;
+  }
   cudaMemsetAsync(g->hist[0], 0, g->P * 3 * sizeof(float), g->stream);
   cudaMemsetAsync(g->hist[1], 0, g->P * 3 * sizeof(float), g->stream);
   cudaMemsetAsync(g->error, 0, sizeof(int), g->stream);
