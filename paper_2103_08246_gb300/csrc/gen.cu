@@ -102,6 +102,14 @@ __host__ __device__ inline size_t granule(size_t row, int group, int z, int C, i
 }
 __host__ __device__ inline size_t map_elems(size_t rows, int C, int nz) { return rows * (size_t)(C / 8) * (nz + 2) * 8; }
 
+// FP32 streams (the residual h and the back-propagated gradient, N = 128
+// channels) in float4 granules, pixel-fastest within a 4-channel group:
+// granule (row, group, z) at (row N/4 + group) nz + z, so that the epilogue's
+// lanes (consecutive pixels) touch consecutive 16-byte granules
+__host__ __device__ inline size_t f32_granule(size_t row, int group, int z, int N, int nz) {
+  return (row * (size_t)(N / 4) + group) * (size_t)nz + (size_t)z;
+}
+
 // store granule (row, group, z) and its halo copy
 __device__ inline void store_granule(bf16* map, size_t row, int group, int z, int C, int nz, uint4 v) {
   *reinterpret_cast<uint4*>(map + granule(row, group, z, C, nz) * 8) = v;
@@ -146,8 +154,8 @@ struct ConvArgs {
   const bf16* dact;    // N-channel map (granule layout) or null
   const float* bias;   // [nbias] or null
   int nbias;
-  const float* res;    // [pixels][N] or null
-  float* out32;        // [pixels][ld32], channels < n32 (null: none)
+  const float* res;    // FP32 stream (f32_granule layout) or null
+  float* out32;        // ld32 == N: FP32 stream (f32_granule layout); else [pixels][ld32], channels < n32
   int ld32, n32;
   bf16* out16;         // N-channel map, granule layout (null: none)
   int out16_phi;       // out16 = phi(val) instead of val
@@ -178,9 +186,9 @@ __device__ inline void conv_epilogue(const ConvArgs& g, size_t row, int z, int c
   }
   if (g.res) {
     float4 t[CW / 4];
-    const float* rr = g.res + p * N + c0;
+    const float4* rr = reinterpret_cast<const float4*>(g.res);
 #pragma unroll
-    for (int q = 0; q < CW / 4; ++q) t[q] = *reinterpret_cast<const float4*>(rr + 4 * q);
+    for (int q = 0; q < CW / 4; ++q) t[q] = rr[f32_granule(row, c0 / 4 + q, z, N, g.nz)];
 #pragma unroll
     for (int q = 0; q < CW / 4; ++q) {
       v[4 * q] += t[q].x; v[4 * q + 1] += t[q].y; v[4 * q + 2] += t[q].z; v[4 * q + 3] += t[q].w;
@@ -188,10 +196,11 @@ __device__ inline void conv_epilogue(const ConvArgs& g, size_t row, int z, int c
   }
   if (g.out32) {
     float* o = g.out32 + p * g.ld32 + c0;
-    if (g.ld32 == N) {
+    if (g.ld32 == N) {   // an FP32 stream: granule layout
+      float4* o4 = reinterpret_cast<float4*>(g.out32);
 #pragma unroll
       for (int q = 0; q < CW; q += 4)
-        *reinterpret_cast<float4*>(o + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        o4[f32_granule(row, (c0 + q) / 4, z, N, g.nz)] = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
     } else {
 #pragma unroll
       for (int q = 0; q < CW; ++q)
@@ -522,37 +531,13 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, int chunks, int N
   grad[i] = s;
 }
 
-// bias gradients out[c] = sum_p x[p][c]: the flat array [pixels][C] is split
-// into equal runs, one per block (a multiple of the block's span); thread t
-// of a block sums the elements t, t + span, ... of its run (about a hundred
-// values, in FP32: the FP64 pipe of this part is far too narrow for per-
-// element double additions), four loads in flight, into entries of its
-// block's partial row whose index mod C is the channel; the partials are
-// added in FP64. Float4 variant (C a multiple of 4, 4 channels per thread,
-// span 4 blockDim) and scalar variant (span blockDim, a multiple of C).
+// bias gradient of the 3-channel output: the flat array [pixels][3] is split
+// into equal runs, one per block (a multiple of the block's span, blockDim, a
+// multiple of 3); thread t sums the elements t, t + span, ... of its run
+// (about a hundred values, in FP32: the FP64 pipe of this part is far too
+// narrow for per-element double additions) into entry t of its block's
+// partial row (channel t mod 3); the partials are added in FP64.
 constexpr int COLSUM_BLOCKS = 608;   // 4 per SM
-__global__ void __launch_bounds__(256) k_colsum_part4(const float4* __restrict__ x, size_t n4,
-                                                      double* __restrict__ part) {
-  const size_t per = ((n4 + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
-  const size_t lo = (size_t)blockIdx.x * per, hi = min(n4, lo + per);
-  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-  const size_t st = blockDim.x;
-  size_t i = lo + threadIdx.x;
-  for (; i + 3 * st < hi; i += 4 * st) {
-    const float4 a = x[i], b = x[i + st], c = x[i + 2 * st], d = x[i + 3 * st];
-    s.x += (a.x + b.x) + (c.x + d.x);
-    s.y += (a.y + b.y) + (c.y + d.y);
-    s.z += (a.z + b.z) + (c.z + d.z);
-    s.w += (a.w + b.w) + (c.w + d.w);
-  }
-  for (; i < hi; i += st) {
-    const float4 a = x[i];
-    s.x += a.x; s.y += a.y; s.z += a.z; s.w += a.w;
-  }
-  double* o = part + ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  o[0] = s.x; o[1] = s.y; o[2] = s.z; o[3] = s.w;
-}
-
 __global__ void __launch_bounds__(256) k_colsum_part(const float* __restrict__ x, size_t n, double* __restrict__ part) {
   const size_t per = ((n + gridDim.x - 1) / gridDim.x + blockDim.x - 1) / blockDim.x * blockDim.x;
   const size_t lo = (size_t)blockIdx.x * per, hi = min(n, lo + per);
@@ -565,6 +550,35 @@ __global__ void __launch_bounds__(256) k_colsum_part(const float* __restrict__ x
   }
   for (; i < hi; i += st) s0 += x[i];
   part[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = (double)s0 + (double)s1;
+}
+
+// bias gradients of an FP32 stream (f32_granule layout, N channels): one
+// block per (row, 4-channel group) sums its run of nz granules (FP32 per
+// thread), partial row per image row: part[row][N]
+__global__ void __launch_bounds__(64) k_colsum_stream(const float4* __restrict__ x, int nz, int N,
+                                                      double* __restrict__ part) {
+  __shared__ float4 red[64];
+  const size_t run = blockIdx.x;   // row * N/4 + group
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int z = threadIdx.x; z < nz; z += 64) {
+    const float4 a = x[run * nz + z];
+    s.x += a.x; s.y += a.y; s.z += a.z; s.w += a.w;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 32; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      red[threadIdx.x].x += red[threadIdx.x + w].x;
+      red[threadIdx.x].y += red[threadIdx.x + w].y;
+      red[threadIdx.x].z += red[threadIdx.x + w].z;
+      red[threadIdx.x].w += red[threadIdx.x + w].w;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double* o = part + run * 4;   // = row * N + 4 group
+    o[0] = red[0].x; o[1] = red[0].y; o[2] = red[0].z; o[3] = red[0].w;
+  }
 }
 
 // one block per channel: the entries e = c mod C of every block's partial
@@ -1049,10 +1063,11 @@ void wgrad(ibm_gen* g, const bf16* a, const bf16* b, int nb, int shift_a, int tr
 }
 
 void colsum(ibm_gen* g, const float* x, size_t pixels, int C, float* out) {
-  if (C % 4 == 0) {   // 256 threads x 4 channels: a row of 1024 partials per block (1024 = 0 mod C)
-    ibm::k_colsum_part4<<<ibm::COLSUM_BLOCKS, 256, 0, g->stream>>>(reinterpret_cast<const float4*>(x),
-                                                                    pixels * C / 4, g->dpart);
-    ibm::k_colsum_final<<<C, 256, 0, g->stream>>>(g->dpart, ibm::COLSUM_BLOCKS, 1024, C, out);
+  if (C % 4 == 0) {   // an FP32 stream: per-row partials, then per channel over the rows
+    const int rows = (int)(pixels / g->nz);
+    ibm::k_colsum_stream<<<rows * (C / 4), 64, 0, g->stream>>>(reinterpret_cast<const float4*>(x), g->nz, C,
+                                                                g->dpart);
+    ibm::k_colsum_final<<<C, 256, 0, g->stream>>>(g->dpart, rows, C, C, out);
   } else {            // C = 3: 192 threads, one channel each
     ibm::k_colsum_part<<<ibm::COLSUM_BLOCKS, 192, 0, g->stream>>>(x, pixels * C, g->dpart);
     ibm::k_colsum_final<<<C, 256, 0, g->stream>>>(g->dpart, ibm::COLSUM_BLOCKS, 192, C, out);
