@@ -59,6 +59,9 @@ TRAFFIC_BYTES = {"rhs": 1743.7e6, "project": 1199.9e6, "af_yz": 1156.7e6, "af_x"
 # DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of
 # GB300 (2 per clock per SM): the FP64 step is bound by that pipe.
 FP64_RHS_INST_PER_CELL = 86.2
+# DRAM bytes of one residual-block convolution of the generator (8 x 256 x 256
+# pixels, 128 -> 128 channels) from an ncu capture of the current kernel
+GEN_CONV_TRAFFIC_BYTES = 757.4e6
 FP64_INST_PER_CLK_SM = 2
 N_SMS = 152
 SAMPLE_NX = 64   # x planes of the CPU sample (the inflow end of the workload)
@@ -462,7 +465,7 @@ def generator_rate(bf16_peak, peak_kind, nrep=10):
             "conv_ms": {"fwd": ms_conv, "dgrad": ms_dgrad, "wgrad": ms_wgrad},
             "roofline": {"kernel": "k_conv<128,128,256> (residual block, forward)", "bound": "hbm",
                          "achieved": gbs, "peak": hbm_peak, "peak_kind": hbm_kind, "unit": "GB/s",
-                         "frac": gbs / hbm_peak, "traffic": None, "bytes_per_launch": conv_bytes,
+                         "frac": gbs / hbm_peak, "traffic": GEN_CONV_TRAFFIC_BYTES, "bytes_per_launch": conv_bytes,
                          "ms_per_launch": ms_conv},
             "tensor": {"achieved": tf(conv_flops, ms_conv), "peak": bf16_peak, "peak_kind": peak_kind,
                        "unit": "TFLOP/s", "frac": tf(conv_flops, ms_conv) / bf16_peak,
