@@ -394,9 +394,15 @@ int ibm_gen_set_lr(ibm_gen* g, double lr);
  * weight gradient of the first residual block (blocks >= 1). Changes the
  * parameters when what = 0. */
 int ibm_gen_time(ibm_gen* g, int what, int nrep, double* ms);
+/* rollout relaxation (after ibm_gen_set_norm): each keyframe step becomes
+ * q_t + delta - lambda (q_t - q_ref), q_ref the normalised host plane
+ * [3][ny][nz] of doubles (e.g. the data's time mean), before the
+ * renormalisation; it damps slow drifts of the rollout away from the data.
+ * 0 <= lambda <= 1 (0, the default, disables it; plane may then be NULL). */
+int ibm_gen_set_relax(ibm_gen* g, const double* plane, double lambda);
 /* rollout: start from two raw planes [3][ny][nz] (FP32) */
 int ibm_gen_rollout_init(ibm_gen* g, const float* plane_prev, const float* plane_cur);
-/* generate the next plane: q = q_t + delta, each component's plane mean
+/* generate the next plane: q = q_t + delta (relaxed, see above), each component's plane mean
  * removed and its rms set to the `rms` of ibm_gen_set_norm; writes
  * mean + std * q into u, v, w ([ny][nz], doubles for IBM_FP64, floats
  * otherwise; any may be NULL), e.g. the pending planes of

@@ -209,6 +209,16 @@ def noisy_inputs(q_t, q_prev, b, noise_std, key):
     return q_t + noise_std * eps[..., :3], q_prev + noise_std * eps[..., 3:]
 
 
+def rollout_step(q_t, delta, rms_target, q_ref=None, lam=0.0):
+    """One rollout keyframe: q_t + delta, relaxed towards q_ref at rate lam
+    (a stated reading: nudging towards the data's time-mean plane), then
+    renormalised."""
+    q = q_t + delta
+    if lam > 0.0:
+        q = q - lam * (q_t - q_ref)
+    return renormalise(q, rms_target)
+
+
 def renormalise(q, rms_target):
     """Rollout closure (a stated reading): each component of a generated plane
     has its plane mean removed and is rescaled to the target rms, so that the

@@ -856,6 +856,14 @@ __global__ void k_emit_interp(const float* __restrict__ a, const float* __restri
   }
 }
 
+// relaxation of the rollout towards a reference plane (the data's time mean):
+// delta -= lambda (q_t - q_ref)
+__global__ void k_relax(float* __restrict__ delta, const float* __restrict__ qt, const float* __restrict__ qref,
+                        int n, float lambda) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) delta[i] -= lambda * (qt[i] - qref[i]);
+}
+
 // raw planes [3][P] -> normalised [P][3]
 __global__ void k_normalise(const float* __restrict__ plane, int P, float3 mean, float3 istd, float* __restrict__ q) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -948,6 +956,8 @@ struct ibm_gen {
   float3 dmean = {0.f, 0.f, 0.f}, dstd = {1.f, 1.f, 1.f};
   double3 rms = {1.0, 1.0, 1.0};
   float noise_std = 0.f;            // training-input noise (normalised units)
+  float relax = 0.f;                // rollout relaxation rate towards qref, per keyframe
+  float* qref = nullptr;            // normalised reference plane [P][3]
   unsigned long long noise_seed = 0;
   int* error = nullptr;
   std::vector<void*> allocs;
@@ -1196,7 +1206,7 @@ int ibm_gen_create(const ibm_gen_config* cfg, ibm_gen** out) {
        dalloc(g, &g->part, (size_t)3 * WG_CHUNKS * 3 * 128 * WIDTH) &&
        dalloc(g, &g->dpart, (size_t)std::max<size_t>(COLSUM_BLOCKS * 1024, BP / LOSS_THREADS + 1)) &&
        dalloc(g, &g->dscal, 8) && dalloc(g, &g->hist[0], g->P * 3) && dalloc(g, &g->hist[1], g->P * 3) &&
-       dalloc(g, &g->error, 1);
+       dalloc(g, &g->qref, g->P * 3) && dalloc(g, &g->error, 1);
   if (!ok) {
     ibm_gen_destroy(g);
     return IBM_ENOMEM;
@@ -1343,6 +1353,20 @@ int ibm_gen_set_noise(ibm_gen* g, double std, unsigned long long seed) {
   return IBM_OK;
 }
 
+int ibm_gen_set_relax(ibm_gen* g, const double* plane, double lambda) {
+  if (!g || !(lambda >= 0.0 && lambda <= 1.0) || (lambda > 0.0 && !plane)) return IBM_EINVAL;
+  g->relax = (float)lambda;
+  if (lambda == 0.0) return IBM_OK;
+  const size_t P = g->P;
+  std::vector<float> q(P * 3);
+  const float mu[3] = {g->dmean.x, g->dmean.y, g->dmean.z}, sd[3] = {g->dstd.x, g->dstd.y, g->dstd.z};
+  for (int c = 0; c < 3; ++c)
+    for (size_t p = 0; p < P; ++p) q[p * 3 + c] = (float)((plane[c * P + p] - mu[c]) / sd[c]);
+  if (cudaMemcpyAsync(g->qref, q.data(), P * 3 * sizeof(float), cudaMemcpyHostToDevice, g->stream) != cudaSuccess)
+    return IBM_ECUDA;
+  return check_error(g);
+}
+
 int ibm_gen_set_lr(ibm_gen* g, double lr) {
   if (!g || !(lr > 0.0)) return IBM_EINVAL;
   g->lr = lr;
@@ -1412,6 +1436,7 @@ int ibm_gen_rollout(ibm_gen* g, void* u, void* v, void* w, int precision) {
   float* qp = g->hist[g->cur ^ 1];
   k_input_q<<<(P + 255) / 256, 256, 0, g->stream>>>(qt, qp, P, g->nz, g->x);
   forward(g, 1);
+  if (g->relax > 0.f) k_relax<<<(3 * P + 255) / 256, 256, 0, g->stream>>>(g->delta, qt, g->qref, 3 * P, g->relax);
   const int nb = SUM_BLOCKS;
   double* mean = g->dscal + 1;
   double* scale = g->dscal + 4;

@@ -19,7 +19,8 @@ learned generator of the C ABI (``ibm_gen_*``):
    R  grid-resolved: the production workload (bars at 0.5, flag at 3);
    G  generated inflow: a 384 x 256 x 256 domain of length 6 without bars,
       flag at 1, inflow planes from the generator rollout: a keyframe every
-      s steps (seeded with the last two recorded keyframes), the planes in
+      s steps (seeded with the last two recorded keyframes, relaxed towards
+      the record's time-mean plane at 5% per keyframe), the planes in
       between interpolated linearly in time;
    U  uniform inflow on the same domain;
    W  white-noise inflow on the same domain: independent Gaussian planes
@@ -112,8 +113,9 @@ def record_planes(solver, i_plane, n, spin=0):
 
 
 def data_norm(planes, sample=256, seed=0):
-    """Per-component mean and std of a record, and the rms of the normalised
-    planes with their plane mean removed (the rollout's target rms)."""
+    """Per-component mean and std of a record, the rms of the normalised
+    planes with their plane mean removed (the rollout's target rms), and the
+    time-mean plane [3, ny, nz] (the rollout's relaxation reference)."""
     rng = np.random.default_rng(seed)
     idx = np.sort(rng.choice(planes.shape[0], min(sample, planes.shape[0]), replace=False))
     a = planes[idx].double().cpu().numpy()
@@ -122,7 +124,7 @@ def data_norm(planes, sample=256, seed=0):
     q = (a - mean[None, :, None, None]) / std[None, :, None, None]
     q = q - q.mean(axis=(2, 3), keepdims=True)
     rms = np.sqrt((q ** 2).mean(axis=(0, 2, 3)))
-    return mean, std, rms
+    return mean, std, rms, a.mean(axis=0)
 
 
 def train(gen, planes, steps, lr0=5e-4, lr1=2e-5, train_frac=0.9, seed=0, log_every=100):
@@ -332,10 +334,11 @@ def compare(res, x_st, x0):
 
 def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3000, blocks=13, batch=8,
              precision=binding.IBM_FP32, seed=0, log=print, base=inputs.PRODUCTION, sample_every=10,
-             re=None, noise=0.03, stride=10):
+             re=None, noise=0.03, stride=10, relax=0.05):
     import torch
     prod = base if re is None else base.replace(re=float(re))
-    out = {"bounds": BOUNDS, "workload": base.name, "re": prod.re, "train_noise": noise, "stride": stride}
+    out = {"bounds": BOUNDS, "workload": base.name, "re": prod.re, "train_noise": noise, "stride": stride,
+           "relax": relax}
     h = prod.lx / prod.nx
     R_SHIFT = shift_cells(prod)
     i_rec = R_SHIFT
@@ -346,7 +349,7 @@ def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3
     out["precursor"] = {"spin": spin, "record": record, "plane_x": i_rec * h,
                         "seconds": time.perf_counter() - t0, "t_end": pre.stats()["t"]}
     pre.close()
-    mean, std, rms = data_norm(planes)
+    mean, std, rms, mean_plane = data_norm(planes)
     out["data"] = {"mean": mean.tolist(), "std": std.tolist(), "rms_normalised": rms.tolist()}
     log(f"precursor: {out['precursor']}, data {out['data']}")
     # 2. training
@@ -360,6 +363,7 @@ def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3
     diag_gen = binding.Generator(prod.ny, prod.nz, blocks=blocks, in_channels=6, batch=1, stride=stride)
     diag_gen.set_params(gen.params())
     diag_gen.set_norm(mean, std, rms)
+    diag_gen.set_relax(mean_plane, relax)
     out["rollout"] = rollout_diagnostics(diag_gen, planes,
                                          tuple(k for k in (1, 10, 100, 300, 800) if k * stride <= max(run_steps, 1)))
     diag_gen.close()
@@ -384,6 +388,7 @@ def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3
                                 stride=stride)
     gen_run.set_params(gen.params())
     gen_run.set_norm(mean, std, rms)
+    gen_run.set_relax(mean_plane, relax)
     gen.close()
     gen_run.rollout_init(seed_prev.cpu().numpy(), seed_cur.cpu().numpy())
     ptrs = binding.ibm_inflow_planes(s.state)
@@ -437,12 +442,14 @@ def main(argv=None):
     ap.add_argument("--re", type=float, default=None, help="Reynolds number of every run (default: the workload's)")
     ap.add_argument("--noise", type=float, default=0.03, help="training-input noise, normalised units")
     ap.add_argument("--stride", type=int, default=10, help="solver steps between generated keyframes")
+    ap.add_argument("--relax", type=float, default=0.05,
+                    help="rollout relaxation rate per keyframe towards the record's time-mean plane")
     ap.add_argument("--out", default="inflow_campaign.json")
     a = ap.parse_args(argv)
     from . import build
     build.build()
     res = campaign(a.spin, a.record, a.train_steps, a.run_steps, a.discard, a.blocks, a.batch, re=a.re,
-                   noise=a.noise, stride=a.stride)
+                   noise=a.noise, stride=a.stride, relax=a.relax)
     with open(a.out, "w") as f:
         json.dump(res, f, indent=1, default=lambda o: o.tolist() if hasattr(o, "tolist") else str(o))
     print(json.dumps(res["comparison"], indent=1, default=str))

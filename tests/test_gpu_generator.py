@@ -266,6 +266,39 @@ def test_keyframe_stride_and_interpolated_planes(lib):
     gen.close()
 
 
+def test_rollout_relaxation_matches_oracle(lib):
+    """With relaxation towards a reference plane the keyframe is
+    renormalise(q_t + delta - lambda (q_t - q_ref))."""
+    from oracle import generator as og
+    from paper_2103_08246_gb300 import binding, inputs
+    gen = binding.Generator(NY, NZ, blocks=BLOCKS, in_channels=CIN, batch=BATCH)
+    w = _params(17)
+    gen.set_params(w)
+    planes = inputs.advected_planes(3, NY, NZ, seed=7)
+    mean = np.array([1.0, 0.01, -0.02])
+    std = np.array([0.1, 0.05, 0.06])
+    rms = np.array([1.0, 0.9, 1.1])
+    gen.set_norm(mean, std, rms)
+    ref_plane = planes.mean(axis=0)
+    gen.set_relax(ref_plane, 0.2)
+    gen.rollout_init(planes[0], planes[1])
+    gen.rollout(None, None, None, precision=binding.IBM_FP32)
+    gen.sync()
+    h_t, _ = gen.history()
+    m32 = mean.astype(np.float32).astype(np.float64)
+    inv = (np.float32(1.0) / std.astype(np.float32)).astype(np.float64)
+
+    def q(pl):
+        return np.moveaxis((pl.astype(np.float32).astype(np.float64) - m32[:, None, None]) * inv[:, None, None], 0, -1)
+    qt, qp = q(planes[1]), q(planes[0])
+    q_ref = np.moveaxis((ref_plane - mean[:, None, None]) / std[:, None, None], 0, -1)
+    p = og.unflatten(w.astype(np.float32).astype(np.float64), 128, BLOCKS, CIN)
+    delta, _ = og.forward(p, og.make_input(qt, qp, CIN), bf16=True)
+    ref = og.rollout_step(qt, delta, rms, q_ref, 0.2)
+    assert np.abs(h_t - ref).max() <= 2e-3 * np.abs(ref).max()
+    gen.close()
+
+
 def test_bad_configurations_are_refused(lib):
     from paper_2103_08246_gb300 import binding
     for kw in ({"nz": 100}, {"nz": 64}, {"blocks": -1}, {"in_channels": 7}, {"batch": 0}, {"batch": 65}):

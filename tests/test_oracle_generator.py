@@ -147,3 +147,12 @@ def test_noisy_inputs_shift_by_the_drawn_noise():
     a, b = gen.noisy_inputs(qt, qp, 1, 0.5, 7)
     eps = gen.normal_from(gen.splitmix64(7, (12 + 0) * 6 + 4))     # sample 1, pixel 0, q_{t-1} channel 1
     assert abs((b[0, 0, 1] - qp[0, 0, 1]) - 0.5 * eps) < 1e-15
+
+
+def test_rollout_step_relaxation():
+    rng = np.random.default_rng(10)
+    qt, d, qr = rng.standard_normal((3, 6, 5, 3))
+    rms = [1.0, 2.0, 0.5]
+    assert np.allclose(gen.rollout_step(qt, d, rms), gen.renormalise(qt + d, rms), atol=1e-15)
+    # lambda = 1 replaces q_t by the reference: the step starts from q_ref
+    assert np.allclose(gen.rollout_step(qt, d, rms, qr, 1.0), gen.renormalise(qr + d, rms), atol=1e-14)
