@@ -7,9 +7,9 @@ path imports this module.
 The paper closes (Sec. V) by proposing that the costly grid-resolved inflow
 turbulence be replaced by a generated one. The generator here is a stated
 reading of that proposal: an autoregressive convolutional network that
-predicts the next inflow plane of velocity fluctuations from the two
-previous ones, on the periodic y-z plane of the domain (Sec. II.A: periodic
-in y and z).
+predicts the next keyframe of the inflow plane of velocity fluctuations
+from the two latest ones (keyframes s recorded planes apart), on the
+periodic y-z plane of the domain (Sec. II.A: periodic in y and z).
 
 Feature maps are channels-last arrays [ny, nz, C]. Definitions:
 
@@ -25,7 +25,7 @@ Feature maps are channels-last arrays [ny, nz, C]. Definitions:
 * Adam (Kingma & Ba): m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
   w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
 
-The input x holds the normalised planes q_t (channels 0-2) and q_{t-1}
+The input x holds the normalised planes q_t (channels 0-2) and q_{t-s}
 (channels 3-5); the remaining input channels are zero.
 
 ``bf16=True`` rounds every convolution operand (weights, activations,

@@ -816,7 +816,10 @@ k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
     __syncwarp();
   }
   if (!act) return;
+  // the recursions' loads (plane values, pivots) do not depend on the
+  // running value: unrolled, they issue ahead of the two-operation chain
   T y = 0;
+#pragma unroll 8
   for (int k = ks; k <= ke; ++k) {
     T e = s[(k - ks) * 32 + lane] * ir;
     if (k == m) e += ob;
@@ -825,6 +828,7 @@ k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
     s[(k - ks) * 32 + lane] = y;
   }
   T x = 0;
+#pragma unroll 8
   for (int k = ke; k >= k0; --k) {
     x = s[(k - ks) * 32 + lane] + x * ip[k];
     if (k < k1) out[(size_t)k * P] = x;
