@@ -218,13 +218,12 @@ static void gemm(const GemmArgs& g, int batch, cudaStream_t s) {
 }
 
 // 2-D Hartley transform of every x plane: out = H_y in H_z (tmp: scratch).
-// 256 x 256 planes run on the tcgen05 tensor cores as two passes
-// out = ((in H)^T H)^T; other shapes on the mma.sync kernel above.
+// Square planes of 32, 64, 128 or 256 run on the tcgen05 tensor cores as two
+// passes out = ((in H)^T H)^T; other shapes on the mma.sync kernel above.
 static void transform2d(const Consts& c, const float* Hy, const float* Hz, const float* in,
                         float* tmp, float* out, int* error, cudaStream_t s) {
-  if (c.ny == 256 && c.nz == 256) {
-    tc_rows_times_h_t(in, Hz, tmp, c.nx, error, s);
-    tc_rows_times_h_t(tmp, Hy, out, c.nx, error, s);
+  if (c.ny == c.nz && tc_rows_times_h_t(in, Hz, tmp, c.nx, c.nz, error, s)) {
+    tc_rows_times_h_t(tmp, Hy, out, c.nx, c.ny, error, s);
     return;
   }
   const long long P = (long long)c.ny * c.nz;

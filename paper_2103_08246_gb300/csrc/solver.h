@@ -89,7 +89,7 @@ template <class T>
 int partial_count(const Consts& c);
 size_t poisson_table_size(const Consts& c);
 // tensor-core (tcgen05) split-TF32 transform pass: out = (X H)^T per 256 x 256 plane
-void tc_rows_times_h_t(const float* X, const float* H, float* out, int planes, int* error,
+bool tc_rows_times_h_t(const float* X, const float* H, float* out, int planes, int n, int* error,
                        cudaStream_t s);
 void tc_gemm_set_attributes();
 int outflow_blocks(const Consts& c);

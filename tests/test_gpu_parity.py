@@ -228,6 +228,18 @@ def test_mixed_small_cases(lib, case):
     print(case, "mixed errors:", errs)
 
 
+@pytest.mark.parametrize("shape", [(7, 32, 32), (21, 64, 64), (13, 128, 128)])
+def test_mixed_tensor_core_plane_sizes(lib, shape):
+    """Square planes of 32, 64 and 128 take the tcgen05 transform GEMMs too;
+    7 x 32 and 21 x 64 rows leave the last 128-row tile partly empty."""
+    from paper_2103_08246_gb300 import binding
+    wl = _small(shape=shape, bars_on=True, bar_x=1.0)
+    gpu, ora = _run(wl, binding.IBM_MIXED, 5)
+    errs = _compare(gpu, ora, FP32_TOL, flag=False, floor=FP32_FLOOR)
+    gpu.close()
+    print(shape, "mixed errors:", errs)
+
+
 def test_mixed_tiny_workload(lib):
     from paper_2103_08246_gb300 import binding, inputs
     wl = inputs.TINY
