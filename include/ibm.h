@@ -415,6 +415,14 @@ int ibm_gen_rollout(ibm_gen* g, void* u, void* v, void* w, int precision);
 int ibm_gen_emit(ibm_gen* g, double w, void* u, void* v, void* wv, int precision);
 /* copy the rollout history (normalised newest and previous keyframes, [ny][nz][3]) */
 int ibm_gen_history(ibm_gen* g, float* q_t, float* q_prev);
+/* checkpoint of the trainable state: FP32 master weights, Adam moments and
+ * step count, normalisation (mean, std, rms). A file of another
+ * configuration (plane, blocks, input channels, stride) is refused with
+ * IBM_EINVAL; a missing, truncated, foreign or over-long file with IBM_EIO;
+ * a refused load leaves the generator as it was. The relaxation plane and
+ * the rollout history are not saved. Synchronise. */
+int ibm_gen_save(ibm_gen* g, const char* path);
+int ibm_gen_load(ibm_gen* g, const char* path);
 int ibm_gen_sync(ibm_gen* g);
 void ibm_gen_destroy(ibm_gen* g);
 

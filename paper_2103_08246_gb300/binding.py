@@ -30,7 +30,7 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_gen_create", "ibm_gen_param_count", "ibm_gen_set_params", "ibm_gen_get_params",
            "ibm_gen_get_grads", "ibm_gen_set_norm", "ibm_gen_forward", "ibm_gen_grad", "ibm_gen_adam_step",
-           "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_relax", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_emit", "ibm_gen_history", "ibm_gen_sync",
+           "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_relax", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_emit", "ibm_gen_history", "ibm_gen_save", "ibm_gen_load", "ibm_gen_sync",
            "ibm_gen_destroy", "ibm_destroy", "ibm_strerror")
 _VOID = ("ibm_destroy", "ibm_ensemble_destroy", "ibm_gen_destroy")
 
@@ -157,6 +157,8 @@ def load(path: str = LIB_PATH):
     lib.ibm_gen_history.argtypes = [vp, vp, vp]
     lib.ibm_gen_emit.argtypes = [vp, ctypes.c_double, vp, vp, vp, ctypes.c_int]
     lib.ibm_gen_sync.argtypes = [vp]
+    lib.ibm_gen_save.argtypes = [vp, ctypes.c_char_p]
+    lib.ibm_gen_load.argtypes = [vp, ctypes.c_char_p]
     lib.ibm_gen_destroy.argtypes = [vp]
     for name in SYMBOLS:
         if name in _VOID:
@@ -410,6 +412,14 @@ def ibm_gen_history(gen, q_t, q_prev):
     _check(load().ibm_gen_history(gen, q_t, q_prev), "ibm_gen_history")
 
 
+def ibm_gen_save(gen, path):
+    _check(load().ibm_gen_save(gen, os.fsencode(path)), "ibm_gen_save")
+
+
+def ibm_gen_load(gen, path):
+    _check(load().ibm_gen_load(gen, os.fsencode(path)), "ibm_gen_load")
+
+
 def ibm_gen_sync(gen):
     _check(load().ibm_gen_sync(gen), "ibm_gen_sync")
 
@@ -632,6 +642,12 @@ class Generator:
         qp = torch.empty_like(qt)
         ibm_gen_history(self.handle, qt.data_ptr(), qp.data_ptr())
         return qt.cpu().numpy().astype(np.float64), qp.cpu().numpy().astype(np.float64)
+
+    def save(self, path):
+        ibm_gen_save(self.handle, path)
+
+    def load(self, path):
+        ibm_gen_load(self.handle, path)
 
     def sync(self):
         ibm_gen_sync(self.handle)

@@ -52,6 +52,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -1477,6 +1478,78 @@ int ibm_gen_history(ibm_gen* g, float* q_t, float* q_prev) {
   if (cudaMemcpyAsync(q_t, g->hist[g->cur], bytes, cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess ||
       cudaMemcpyAsync(q_prev, g->hist[g->cur ^ 1], bytes, cudaMemcpyDeviceToDevice, g->stream) != cudaSuccess)
     return IBM_ECUDA;
+  return check_error(g);
+}
+
+// ---- checkpoints: header, then the FP32 masters, Adam moments and the
+// normalisation; the configuration must match on load
+struct GenCkptHeader {
+  char magic[8];
+  int version, ny, nz, blocks, cin, stride, pad;
+  long long np, t;
+  double dmean[3], dstd[3], rms[3];
+};
+
+int ibm_gen_save(ibm_gen* g, const char* path) {
+  if (!g || !path) return IBM_EINVAL;
+  GenCkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "IBMGEN01", 8);
+  h.version = 1;
+  h.ny = g->ny; h.nz = g->nz; h.blocks = g->blocks; h.cin = g->cin; h.stride = g->stride;
+  h.np = (long long)g->np;
+  h.t = g->t;
+  const float mu[3] = {g->dmean.x, g->dmean.y, g->dmean.z}, sd[3] = {g->dstd.x, g->dstd.y, g->dstd.z};
+  const double rm[3] = {g->rms.x, g->rms.y, g->rms.z};
+  for (int c = 0; c < 3; ++c) {
+    h.dmean[c] = mu[c];
+    h.dstd[c] = sd[c];
+    h.rms[c] = rm[c];
+  }
+  std::vector<float> buf(3 * g->np);
+  if (cudaMemcpyAsync(buf.data(), g->w, g->np * sizeof(float), cudaMemcpyDeviceToHost, g->stream) != cudaSuccess ||
+      cudaMemcpyAsync(buf.data() + g->np, g->m, g->np * sizeof(float), cudaMemcpyDeviceToHost, g->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(buf.data() + 2 * g->np, g->v, g->np * sizeof(float), cudaMemcpyDeviceToHost, g->stream) !=
+          cudaSuccess)
+    return IBM_ECUDA;
+  const int st = check_error(g);
+  if (st != IBM_OK) return st;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return IBM_EIO;
+  const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+                  std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  return (std::fclose(f) == 0 && ok) ? IBM_OK : IBM_EIO;
+}
+
+int ibm_gen_load(ibm_gen* g, const char* path) {
+  if (!g || !path) return IBM_EINVAL;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return IBM_EIO;
+  GenCkptHeader h;
+  std::vector<float> buf(3 * g->np);
+  bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, "IBMGEN01", 8) == 0 && h.version == 1;
+  if (ok && (h.ny != g->ny || h.nz != g->nz || h.blocks != g->blocks || h.cin != g->cin ||
+             h.stride != g->stride || h.np != (long long)g->np)) {
+    std::fclose(f);
+    return IBM_EINVAL;
+  }
+  ok = ok && std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  char extra;
+  ok = ok && std::fread(&extra, 1, 1, f) == 0;   // nothing may follow
+  std::fclose(f);
+  if (!ok) return IBM_EIO;
+  if (cudaMemcpyAsync(g->w, buf.data(), g->np * sizeof(float), cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+      cudaMemcpyAsync(g->m, buf.data() + g->np, g->np * sizeof(float), cudaMemcpyHostToDevice, g->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(g->v, buf.data() + 2 * g->np, g->np * sizeof(float), cudaMemcpyHostToDevice, g->stream) !=
+          cudaSuccess)
+    return IBM_ECUDA;
+  g->t = h.t;
+  g->dmean = make_float3((float)h.dmean[0], (float)h.dmean[1], (float)h.dmean[2]);
+  g->dstd = make_float3((float)h.dstd[0], (float)h.dstd[1], (float)h.dstd[2]);
+  g->rms = make_double3(h.rms[0], h.rms[1], h.rms[2]);
+  pack_weights(g);
   return check_error(g);
 }
 

@@ -299,6 +299,44 @@ def test_rollout_relaxation_matches_oracle(lib):
     gen.close()
 
 
+def test_checkpoint_restores_training(lib, tmp_path):
+    """save after two Adam steps, load into a fresh generator: the next step
+    gives the same loss and parameters as the uninterrupted run; a file of
+    another configuration or a truncated file is refused."""
+    from paper_2103_08246_gb300 import binding, inputs
+    planes = inputs.advected_planes(12, NY, NZ, seed=8, shift=1)
+    mean, std = planes.mean(axis=(0, 2, 3)), planes.std(axis=(0, 2, 3))
+    dev = torch.as_tensor(planes.astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    a = binding.Generator(NY, NZ, blocks=BLOCKS, in_channels=CIN, batch=BATCH)
+    a.set_params(_params(18))
+    a.set_norm(mean, std, [1.0, 1.0, 1.0])
+    a.train_step(dev, [2, 5])
+    a.train_step(dev, [3, 9])
+    path = str(tmp_path / "gen.ckpt")
+    a.save(path)
+    la = a.train_step(dev, [4, 7])
+    b = binding.Generator(NY, NZ, blocks=BLOCKS, in_channels=CIN, batch=BATCH)
+    b.load(path)
+    lb = b.train_step(dev, [4, 7])
+    assert lb == la
+    assert np.array_equal(a.params(), b.params())
+    other = binding.Generator(NY, NZ, blocks=BLOCKS + 1, in_channels=CIN, batch=BATCH)
+    with pytest.raises(binding.IBMError) as e:
+        other.load(path)
+    assert e.value.code == binding.IBM_EINVAL
+    blob = open(path, "rb").read()
+    short = str(tmp_path / "short.ckpt")
+    open(short, "wb").write(blob[: len(blob) // 2])
+    before = b.params()
+    with pytest.raises(binding.IBMError) as e:
+        b.load(short)
+    assert e.value.code == binding.IBM_EIO
+    assert np.array_equal(b.params(), before)
+    for g in (a, b, other):
+        g.close()
+
+
 def test_bad_configurations_are_refused(lib):
     from paper_2103_08246_gb300 import binding
     for kw in ({"nz": 100}, {"nz": 64}, {"blocks": -1}, {"in_channels": 7}, {"batch": 0}, {"batch": 65}):
