@@ -1,0 +1,26 @@
+"""Laminar flag validation helpers (CPU): the oscillation analysis against a
+synthetic trailing-edge signal and the workloads' geometry."""
+import numpy as np
+
+from paper_2103_08246_gb300 import inputs, validation
+
+
+def test_flag_oscillation_of_a_synthetic_signal():
+    t = np.linspace(0.0, 30.0, 6000)
+    te = np.stack([3.0 + 0.01 * np.sin(t), 2.0 + 0.01 * t * 0, 2.0 + 0.3 * np.sin(2 * np.pi * 0.25 * t)], axis=1)
+    out = validation.flag_oscillation(t, te)
+    assert out["component"] == 2
+    assert abs(out["strouhal"] - 0.25) < 0.003
+    assert abs(out["period"] - 4.0) < 0.05
+    assert abs(out["amplitude"] - 0.3) < 1e-3
+
+
+def test_laminar_workloads():
+    fine = validation.laminar_workload(64)
+    coarse = validation.laminar_workload(32)
+    p = inputs.PRODUCTION
+    assert (fine.nx, fine.ny, fine.nz) == (p.nx, p.ny, p.nz) and not fine.bars_on and fine.flag_on
+    assert (coarse.nx, coarse.ny, coarse.nz) == (256, 128, 128)
+    for wl, n in ((fine, 64), (coarse, 32)):
+        assert abs(wl.lx / wl.nx - 1.0 / n) < 1e-12 and abs(wl.ly / wl.ny - 1.0 / n) < 1e-12
+        assert wl.flag_ns == wl.flag_nt == n + 1
