@@ -155,6 +155,13 @@ typedef struct {
    * (ibm_set_inflow / ibm_inflow_planes) instead of the uniform (U, 0, 0).
    * Costs 8 planes of workspace and two small kernels per step. [0] */
   int inflow;
+  /* Forcing of the bar grid. 0: delta-kernel markers filling the bars,
+   * forced like the flag's. 1: Eulerian direct forcing (Sec. II.B forces the
+   * fixed grid on Eulerian nodes): every velocity node whose cell
+   * [x - h/2, x + h/2]^3 the bars cut is set to (1 - alpha) u*, alpha the
+   * cell's solid fraction (zero inside the solid); the bars then carry no
+   * markers. [0] */
+  int bar_forcing;
 } ibm_options;
 
 /* Diagnostics read by ibm_stats (all FP64). */

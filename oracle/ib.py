@@ -141,3 +141,47 @@ def bar_markers(wl, h):
     X = np.array(pts, dtype=float)
     volume = d * d * (ny_r * wl.lz + nz_r * wl.ly) - ny_r * nz_r * d ** 3
     return X, volume / X.shape[0]
+
+
+def bar_volume_fraction(wl, comp, h):
+    """Eulerian forcing of the bar grid (Sec. II.B: the fixed grid is forced
+    on Eulerian nodes, after Fadlun et al.), read as a volume-fraction direct
+    forcing: each velocity node of component `comp` carries the fraction
+    alpha of its cell [x - h/2, x + h/2]^3 that lies inside the bars, and the
+    forcing sets u** = (1 - alpha) u* (zero inside the solid).
+
+    The solid is the union of the rods of the bar_markers geometry: square
+    rods of side d in the slab |x - bar_x| <= d/2, along y centred at
+    z = (r + 1/2) M and along z centred at y = (r + 1/2) M (periodic in y, z).
+    With ox, oy, oz the overlaps of the cell with the slab and with the rods
+    across y and z, |cell and (Y-rods or Z-rods)| = ox (h oz + oy h - oy oz).
+
+    Returns alpha with the shape of the component's field, (nx + 1, ny, nz),
+    zero on the planes that are not unknowns (u faces 0 and nx, v/w plane nx).
+    """
+    nx, ny, nz = wl.nx, wl.ny, wl.nz
+    d, M = wl.bar_width, wl.bar_mesh
+
+    def overlap(c, lo, hi):
+        return np.clip(np.minimum(c + 0.5 * h, hi) - np.maximum(c - 0.5 * h, lo), 0.0, None)
+
+    def rods(c, centres, period):
+        o = np.zeros_like(c)
+        for c0 in centres:
+            for img in (-period, 0.0, period):
+                o += overlap(c, c0 + img - 0.5 * d, c0 + img + 0.5 * d)
+        return o
+
+    i = np.arange(nx + 1)
+    x = i * h if comp == 0 else (i + 0.5) * h
+    y = np.arange(ny) * h if comp == 1 else (np.arange(ny) + 0.5) * h
+    z = np.arange(nz) * h if comp == 2 else (np.arange(nz) + 0.5) * h
+    ox = overlap(x, wl.bar_x - 0.5 * d, wl.bar_x + 0.5 * d)
+    oy = rods(y, (np.arange(int(round(wl.ly / M))) + 0.5) * M, wl.ly)
+    oz = rods(z, (np.arange(int(round(wl.lz / M))) + 0.5) * M, wl.lz)
+    alpha = ox[:, None, None] * (h * oz[None, None, :] + oy[None, :, None] * h
+                                 - oy[None, :, None] * oz[None, None, :]) / h ** 3
+    lo, hi = _valid_x_range(comp, nx)
+    alpha[:lo] = 0.0
+    alpha[hi + 1:] = 0.0
+    return alpha

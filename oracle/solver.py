@@ -11,7 +11,9 @@ immersed-boundary forcing, then the Poisson equation and the projection.
   A3  (1 - aL_x)(1 - aL_y)(1 - aL_z) du = RHS, a = nu dt / 2; u* = u^n + du
   A4  U*_l = I u* at every marker (flag and bars)
   A5  F_l = (U_l - U*_l) / dt with U_l = V^n_l (flag), 0 (bars);
-      u** = u* + dt S F
+      u** = u* + dt S F. With Eulerian bar forcing (bar_forcing "eulerian")
+      the bars carry no markers: first u* <- (1 - alpha) u* at every velocity
+      node, alpha the node cell's solid fraction, then the flag markers.
   A6  flag: fluid force -F_l dV_l, velocity Verlet sub-steps -> X^{n+1}, V^{n+1}
   A7  mass fix: (Q_in - Q_out) / (Ly Lz) added to u on the outflow face;
       D = div(u**) / dt
@@ -85,7 +87,12 @@ class OracleSolver:
             self.nf = self.mesh.nv
             self.flag_dv = self.mesh.area * h
             self.F_flag = np.zeros_like(self.X)
-        if wl.bars_on:
+        self.bar_alpha = None
+        if wl.bars_on and wl.bar_forcing == "eulerian":
+            self.bar_alpha = [ib.bar_volume_fraction(wl, c, h) for c in range(3)]
+            self.Xb = np.zeros((0, 3))
+            self.bar_dv = np.zeros(0)
+        elif wl.bars_on:
             self.Xb, dvb = ib.bar_markers(wl, h)
             self.bar_dv = np.full(self.Xb.shape[0], dvb)
         else:
@@ -159,6 +166,10 @@ class OracleSolver:
             us[0] = u_new
             self.v_in, self.w_in = self.pending_inflow[1].copy(), self.pending_inflow[2].copy()
 
+        if self.bar_alpha is not None:                                   # A4-A5, Eulerian bars
+            us *= 1.0 - self.bar_alpha[0]
+            vs *= 1.0 - self.bar_alpha[1]
+            ws *= 1.0 - self.bar_alpha[2]
         Xm = self.markers()                                              # A4
         if Xm.shape[0]:
             Ustar = ib.interpolate((us, vs, ws), Xm, h, nx)

@@ -66,7 +66,7 @@ class ibm_options(ctypes.Structure):
                 ("init_u", _dp), ("init_v", _dp), ("init_w", _dp),
                 ("rhs_planes", ctypes.c_int), ("afx_planes", ctypes.c_int),
                 ("rhs_stages", ctypes.c_int), ("deterministic", ctypes.c_int),
-                ("inflow", ctypes.c_int)]
+                ("inflow", ctypes.c_int), ("bar_forcing", ctypes.c_int)]
 
 
 class ibm_gen_config(ctypes.Structure):
@@ -455,7 +455,7 @@ class Solver:
                            *([_ptr(a) for a in self._noise] if self._noise else [None] * 3),
                            int(tiles.get("rhs_planes", 0)), int(tiles.get("afx_planes", 0)),
                            int(tiles.get("rhs_stages", 0)), 1 if deterministic else 0,
-                           1 if inflow else 0)
+                           1 if inflow else 0, 1 if wl.bar_forcing == "eulerian" else 0)
         self.ws_bytes = ibm_workspace_bytes(self.grid, self.dom, self.bodies, opts)
         self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device="cuda")
         torch.cuda.synchronize()

@@ -254,7 +254,62 @@ struct Carver {
 
 struct Layout {
   int nf = 0, nb = 0, nsp = 0, ntri = 0, nslot = 0, ncsr = 0;
+  int nbm[3] = {0, 0, 0};   // Eulerian bar forcing: forced nodes per component
 };
+
+// Eulerian forcing of the bar grid: for every velocity node whose cell
+// [x - h/2, x + h/2]^3 the bars cut, its field index and the solid fraction
+// alpha of the cell. The solid is the union of the rods (side d, in the slab
+// |x - bar_x| <= d/2; along y centred at z = (r + 1/2) M, along z centred at
+// y = (r + 1/2) M, periodic); with ox, oy, oz the cell's overlaps with the
+// slab and with the rods across y and z,
+// alpha h^3 = ox (h oz + oy h - oy oz).
+struct BarMask {
+  std::vector<int> idx;
+  std::vector<double> alpha;
+  int n[3] = {0, 0, 0};
+};
+
+double cell_overlap(double c, double h, double lo, double hi) {
+  return std::max(0.0, std::min(c + 0.5 * h, hi) - std::max(c - 0.5 * h, lo));
+}
+
+double rod_overlap(double c, double h, double d, double M, int nrods, double period) {
+  double o = 0.0;
+  for (int r = 0; r < nrods; ++r)
+    for (int img = -1; img <= 1; ++img) {
+      const double c0 = (r + 0.5) * M + img * period;
+      o += cell_overlap(c, h, c0 - 0.5 * d, c0 + 0.5 * d);
+    }
+  return o;
+}
+
+void build_bar_mask(const ibm_bodies& b, const ibm_domain& dm, const ibm_grid& g, double h, BarMask& bm) {
+  const double d = b.bar_width, M = b.bar_mesh;
+  const int nry = (int)std::lround(dm.ly / M), nrz = (int)std::lround(dm.lz / M);
+  bm.idx.clear();
+  bm.alpha.clear();
+  for (int comp = 0; comp < 3; ++comp) {
+    const int ilo = comp == 0 ? 1 : 0, ihi = g.nx - 1;   // unknown planes of the component
+    std::vector<double> oy(g.ny), oz(g.nz);
+    for (int j = 0; j < g.ny; ++j) oy[j] = rod_overlap((j + (comp == 1 ? 0.0 : 0.5)) * h, h, d, M, nry, dm.ly);
+    for (int k = 0; k < g.nz; ++k) oz[k] = rod_overlap((k + (comp == 2 ? 0.0 : 0.5)) * h, h, d, M, nrz, dm.lz);
+    const size_t before = bm.idx.size();
+    for (int i = ilo; i <= ihi; ++i) {
+      const double x = (i + (comp == 0 ? 0.0 : 0.5)) * h;
+      const double ox = cell_overlap(x, h, b.bar_x - 0.5 * d, b.bar_x + 0.5 * d);
+      if (ox <= 0.0) continue;
+      for (int j = 0; j < g.ny; ++j)
+        for (int k = 0; k < g.nz; ++k) {
+          const double a = ox * (h * oz[k] + oy[j] * h - oy[j] * oz[k]) / (h * h * h);
+          if (a <= 0.0) continue;
+          bm.idx.push_back((int)(((size_t)i * g.ny + j) * g.nz + k));
+          bm.alpha.push_back(std::min(a, 1.0));
+        }
+    }
+    bm.n[comp] = (int)(bm.idx.size() - before);
+  }
+}
 
 }  // namespace
 
@@ -265,6 +320,7 @@ struct ibm_state {
   int precision = IBM_FP64;
   bool deterministic = false;
   bool inflow = false;
+  int bar_forcing = 0;   // 0: bar markers, 1: Eulerian volume-fraction forcing
   Consts c{};
   ibm_grid grid{};
   ibm_domain dom{};
@@ -328,6 +384,7 @@ int check_args(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, cons
     if (o->precision != IBM_FP64 && o->precision != IBM_FP32 && o->precision != IBM_MIXED)
       return IBM_EINVAL;
     if (o->cfl < 0 || o->cfl_limit < 0) return IBM_EINVAL;
+    if (o->bar_forcing != 0 && o->bar_forcing != 1) return IBM_EINVAL;
   }
   return IBM_OK;
 }
@@ -372,6 +429,9 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   m.coef = cv.take<double>(3 * (size_t)m.nm);
   m.nfield = NF;
   m.acc = s->deterministic ? cv.take<unsigned long long>(3 * NF) : nullptr;
+  for (int q = 0; q < 3; ++q) m.nbm[q] = L.nbm[q];
+  m.bm_idx = cv.take<int>((size_t)L.nbm[0] + L.nbm[1] + L.nbm[2]);
+  m.bm_alpha = cv.take<double>((size_t)L.nbm[0] + L.nbm[1] + L.nbm[2]);
   Flag& fl = s->fl;
   fl.nv = L.nf;
   fl.X = cv.take<double>(3 * (size_t)L.nf);
@@ -552,7 +612,7 @@ void record_graph(ibm_state* s, int kind, int cur) {
 
 template <class T>
 int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
-               const std::vector<double>& Xb, double bar_dv) {
+               const std::vector<double>& Xb, double bar_dv, const BarMask& bm) {
   Fields<T>& f = fields<T>(s);
   const Consts& c = s->c;
   cudaStream_t st = s->stream;
@@ -590,6 +650,10 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
   Markers& m = s->mk;
   m.bar_dv = bar_dv;
   if (m.nb) CK(cudaMemcpyAsync(m.Xb, Xb.data(), Xb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (!bm.idx.empty()) {
+    CK(cudaMemcpyAsync(m.bm_idx, bm.idx.data(), bm.idx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(m.bm_alpha, bm.alpha.data(), bm.alpha.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
   Flag& fl = s->fl;
   if (fl.nv) {
     fl.ns = fg.ns;
@@ -674,7 +738,7 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
 }
 
 int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const ibm_options* o,
-            ibm_state* s, FlagGeom& fg, std::vector<double>& Xb, double& bar_dv, Layout& L) {
+            ibm_state* s, FlagGeom& fg, std::vector<double>& Xb, double& bar_dv, Layout& L, BarMask& bm) {
   int rc = check_args(g, d, b, o);
   if (rc) return rc;
   s->grid = *g;
@@ -683,6 +747,7 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   s->precision = o ? o->precision : IBM_FP64;
   s->deterministic = o && o->deterministic;
   s->inflow = o && o->inflow;
+  s->bar_forcing = o ? o->bar_forcing : 0;
   s->cfl = (o && o->cfl > 0) ? o->cfl : 0.3;
   s->cfl_limit = (o && o->cfl_limit > 0) ? o->cfl_limit : 2.0;
   Consts& c = s->c;
@@ -702,7 +767,9 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   c.afx_planes = (o && o->afx_planes > 0) ? o->afx_planes : 64;
   bar_dv = 0.0;
   if (b->flag_on) fg = build_flag(*b, *d, c.h);
-  if (b->bars_on) build_bars(*b, *d, c.h, Xb, bar_dv);
+  if (b->bars_on && s->bar_forcing == 1) build_bar_mask(*b, *d, *g, c.h, bm);
+  else if (b->bars_on) build_bars(*b, *d, c.h, Xb, bar_dv);
+  for (int q = 0; q < 3; ++q) L.nbm[q] = bm.n[q];
   c.omega_max = fg.omega_max;
   L.nf = b->flag_on ? b->flag_ns * b->flag_nt : 0;
   L.nb = (int)(Xb.size() / 3);
@@ -799,7 +866,8 @@ int ibm_workspace_bytes(const ibm_grid* g, const ibm_domain* d, const ibm_bodies
   std::vector<double> Xb;
   double bdv;
   Layout L;
-  int rc = prepare(g, d, b, o, &tmp, fg, Xb, bdv, L);
+  BarMask bm;
+  int rc = prepare(g, d, b, o, &tmp, fg, Xb, bdv, L, bm);
   if (rc) return rc;
   *bytes = tmp.precision == IBM_FP64 ? carve<double>(&tmp, nullptr, L, tmp.fd)
                                      : carve<float>(&tmp, nullptr, L, tmp.ff);
@@ -816,7 +884,8 @@ int ibm_create(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodi
   std::vector<double> Xb;
   double bdv = 0;
   Layout L;
-  int rc = prepare(g, d, b, o, s.get(), fg, Xb, bdv, L);
+  BarMask bm;
+  int rc = prepare(g, d, b, o, s.get(), fg, Xb, bdv, L, bm);
   if (rc) return rc;
   s->c.nu = 1.0 / re;
   s->c.f_nu = (float)s->c.nu;
@@ -851,8 +920,8 @@ int ibm_create(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodi
     ibm_destroy(s.release());
     return IBM_ECUDA;
   }
-  rc = s->precision == IBM_FP64 ? init_state<double>(s.get(), o, fg, Xb, bdv)
-                                : init_state<float>(s.get(), o, fg, Xb, bdv);
+  rc = s->precision == IBM_FP64 ? init_state<double>(s.get(), o, fg, Xb, bdv, bm)
+                                : init_state<float>(s.get(), o, fg, Xb, bdv, bm);
   if (rc) {
     ibm_destroy(s.release());
     return rc;
@@ -1070,7 +1139,7 @@ int ibm_get_markers(ibm_state* s, double* X, size_t n) {
 namespace {
 struct CkptHeader {
   char magic[8];
-  int version, precision, nx, ny, nz, nf, nb, elem, inflow;
+  int version, precision, nx, ny, nz, nf, nb, elem, inflow, bar_forcing;
   double lx, ly, lz, nu;
   double body[12];
   long long params_bytes;
@@ -1088,6 +1157,7 @@ void fill_header(const ibm_state* s, CkptHeader& h) {
   h.nb = s->mk.nb;
   h.elem = s->precision == IBM_FP64 ? 8 : 4;
   h.inflow = s->inflow ? 1 : 0;
+  h.bar_forcing = s->bar_forcing;
   h.lx = s->c.lx;
   h.ly = s->c.ly;
   h.lz = s->c.lz;

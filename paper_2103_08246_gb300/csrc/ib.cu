@@ -4,7 +4,8 @@
 // Peskin and Berger), the direct-forcing amplitude
 //   coef_l = dV_l / h^3 (U_l - U*_l)   (= dt F_l dV_l / h^3),
 // the fluid force on each flag vertex -F_l dV_l, and spreading of coef_l
-// with the same weights (atomic scatter).
+// with the same weights (atomic scatter). Alternatively the bars are forced
+// on the Eulerian nodes (k_bar_mask) and only the flag carries markers.
 //
 // Markers 0 .. nf-1 are the flag vertices (target velocity V_l, position X_l
 // from the structure), the rest the bar-grid markers (target 0). Nodes
@@ -231,9 +232,23 @@ __global__ void k_ib_flush(Consts c, Markers m, Flag fl, T* __restrict__ u, T* _
   }
 }
 
+// Eulerian direct forcing of the bar grid (Sec. II.B, the fixed grid forced
+// on Eulerian nodes): u** = (1 - alpha) u* at every velocity node whose cell
+// the bars cut, alpha the cell's solid fraction (zero velocity inside)
+template <class T>
+__global__ void k_bar_mask(Markers m, T* __restrict__ u, T* __restrict__ v, T* __restrict__ w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n0 = m.nbm[0], n1 = n0 + m.nbm[1], n2 = n1 + m.nbm[2];
+  if (i >= n2) return;
+  T* q = i < n0 ? u : (i < n1 ? v : w);
+  q[m.bm_idx[i]] *= (T)(1.0 - m.bm_alpha[i]);
+}
+
 template <class T>
 void launch_ib(const Consts& c, const Fields<T>& f, const Markers& m, const Flag& fl, int cur,
                cudaStream_t s) {
+  const int nbm = m.nbm[0] + m.nbm[1] + m.nbm[2];
+  if (nbm) k_bar_mask<T><<<(nbm + 255) / 256, 256, 0, s>>>(m, f.u[cur], f.v[cur], f.w[cur]);
   if (m.nm == 0) return;
   const int nb = (m.nm + 127) / 128;
   k_ib_interp<T><<<nb, 128, 0, s>>>(c, f.prm, m, fl, f.u[cur], f.v[cur], f.w[cur]);

@@ -42,6 +42,11 @@ struct Markers {
   double* coef = nullptr;     // 3 per marker: dV / h^3 * (U - U*)
   unsigned long long* acc = nullptr;   // deterministic mode: fixed-point sums, 3 fields
   size_t nfield = 0;                   // cells of one velocity field (accumulator stride)
+  // Eulerian bar forcing: the velocity nodes whose cells the bars cut, u's
+  // then v's then w's, with the solid fraction of each cell
+  int nbm[3] = {0, 0, 0};
+  int* bm_idx = nullptr;
+  double* bm_alpha = nullptr;
 };
 
 struct Flag {

@@ -40,6 +40,10 @@ class Workload:
     bar_x: float = 0.5
     bar_mesh: float = 0.5
     bar_width: float = 0.1
+    # "markers": delta-kernel markers filling the bars (the benchmark's
+    # specification); "eulerian": volume-fraction direct forcing at the
+    # Eulerian velocity nodes (the paper's treatment of the fixed grid)
+    bar_forcing: str = "markers"
     # flexible flag hinged at its leading edge
     flag_on: bool = True
     flag_x_le: float = 2.0

@@ -142,3 +142,33 @@ def test_bar_markers_geometry():
     assert np.all(in_y_rod | in_z_rod)
     volume = d * d * n_rod * (wl.ly + wl.lz) - n_rod * n_rod * d ** 3
     assert abs(dv * X.shape[0] - volume) < 1e-12
+
+
+def test_bar_volume_fraction():
+    """Eulerian bar forcing: the fractions sum to the exact solid volume of
+    the bars (union of the rods), lie in [0, 1], are 1 at the rod centre
+    lines and 0 away from the grid, and respect the rods' symmetry."""
+    from oracle import ib as oib
+    from paper_2103_08246_gb300 import inputs
+    for h, d in ((0.125, 0.1), (0.0625, 0.1), (0.0625, 0.25)):
+        wl = inputs.small(32, 16, 16, bars_on=True, bar_x=1.0, bar_width=d).replace(
+            lx=32 * h, ly=16 * h, lz=16 * h)
+        M = wl.bar_mesh
+        nr_y, nr_z = int(round(wl.ly / M)), int(round(wl.lz / M))
+        exact = d * d * (nr_y * wl.lz + nr_z * wl.ly) - nr_y * nr_z * d ** 3
+        for comp in range(3):
+            a = oib.bar_volume_fraction(wl, comp, h)
+            assert a.shape == (wl.nx + 1, wl.ny, wl.nz)
+            assert a.min() >= 0.0 and a.max() <= 1.0 + 1e-12
+            assert abs(a.sum() * h ** 3 - exact) < 1e-12 * max(exact, 1.0)
+    # a node on a rod's centre line inside the slab is fully solid, one far away empty
+    h = 1.0 / 64
+    wl = inputs.small(128, 64, 64, bars_on=True, bar_x=1.0).replace(lx=2.0, ly=1.0, lz=1.0)
+    a = oib.bar_volume_fraction(wl, 1, h)      # v at ((i + 1/2) h, j h, (k + 1/2) h)
+    i = int(round(1.0 / h - 0.5))              # x = 1 - h/2 ... inside the slab of width 0.1
+    k = int(round(0.25 / h - 0.5))             # z = 0.25 - h/2 near the centre of a y-rod
+    assert a[i, 5, k] == 1.0
+    assert a[i - 20, 5, k] == 0.0
+    # z-rods and y-rods are the same solid turned by 90 degrees
+    au, av, aw = (oib.bar_volume_fraction(wl, c, h) for c in range(3))
+    assert np.allclose(av, np.transpose(aw, (0, 2, 1)), atol=0)
