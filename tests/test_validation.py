@@ -24,3 +24,16 @@ def test_laminar_workloads():
     for wl, n in ((fine, 64), (coarse, 32)):
         assert abs(wl.lx / wl.nx - 1.0 / n) < 1e-12 and abs(wl.ly / wl.ny - 1.0 / n) < 1e-12
         assert wl.flag_ns == wl.flag_nt == n + 1
+
+
+def test_inside_rods_mask():
+    wl = inputs.PRODUCTION
+    h = wl.lx / wl.nx
+    i = int(round(wl.bar_x / h))            # u face at x = bar_x, mid-slab
+    m = validation._inside_rods(wl, 0, i)
+    # rods of width 0.1 = 6.4 cells, centred at (r + 1/2) M between cell
+    # centres: 6 whole cells across each rod, 8 rods per direction
+    full = 6 * 8 / 256
+    assert abs(m.mean() - (2 * full - full * full)) < 1e-12
+    assert m[int(0.25 / h), :].all() and m[:, int(0.25 / h)].all()
+    assert not validation._inside_rods(wl, 0, i + 10).any()
