@@ -262,6 +262,17 @@ int ibm_plane_device(ibm_state* s, int i, void** u, void** v, void** w);
 int ibm_marker_count(const ibm_state* s, size_t* n);
 int ibm_get_markers(ibm_state* s, double* X, size_t n);
 
+/* Virtual probes (time histories for the statistics of Sec. III): set n
+ * probes at cells (i, j, k) (host ints, 3 per probe, 0 <= i < nx); each
+ * ibm_probe_sample then writes the cell-centred velocity (u averaged over
+ * the faces i, i + 1, v over j, j + 1, w over k, k + 1, periodic in y, z) of
+ * every probe, (u, v, w) per probe, into the DEVICE buffer dst (3 n values in
+ * the state's precision), asynchronously on the state's stream. The state
+ * owns the probe list; n = 0 clears it. IBM_EINVAL for cells out of range or
+ * a sample without probes. */
+int ibm_probes_set(ibm_state* s, const int* ijk, int n);
+int ibm_probe_sample(ibm_state* s, void* dst);
+
 /* Checkpoint / restart. ibm_save writes everything the next step reads --
  * the device parameter block (time, step count, previous dt, AB2 and
  * time-step mode), u, v, w, p and the previous advection term N^{n-1} in the

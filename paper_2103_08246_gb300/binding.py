@@ -26,7 +26,7 @@ IBM_FIELD_U, IBM_FIELD_V, IBM_FIELD_W, IBM_FIELD_P = 0, 1, 2, 3
 SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_flag_state",
            "ibm_stats", "ibm_get_field", "ibm_set_field", "ibm_marker_count", "ibm_get_markers",
            "ibm_save", "ibm_load", "ibm_set_inflow", "ibm_inflow_planes", "ibm_get_plane",
-           "ibm_plane_device",
+           "ibm_plane_device", "ibm_probes_set", "ibm_probe_sample",
            "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_gen_create", "ibm_gen_param_count", "ibm_gen_set_params", "ibm_gen_get_params",
            "ibm_gen_get_grads", "ibm_gen_set_norm", "ibm_gen_forward", "ibm_gen_grad", "ibm_gen_adam_step",
@@ -127,6 +127,8 @@ def load(path: str = LIB_PATH):
     lib.ibm_plane_device.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(vp)]
     lib.ibm_inflow_planes.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    lib.ibm_probes_set.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    lib.ibm_probe_sample.argtypes = [vp, vp]
     lib.ibm_save.argtypes = [vp, ctypes.c_char_p]
     lib.ibm_load.argtypes = [vp, ctypes.c_char_p]
     lib.ibm_time_stage.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
@@ -278,6 +280,16 @@ def ibm_inflow_planes(state):
     ptrs = [ctypes.c_void_p() for _ in range(3)]
     _check(load().ibm_inflow_planes(state, *[ctypes.byref(q) for q in ptrs]), "ibm_inflow_planes")
     return tuple(q.value for q in ptrs)
+
+
+def ibm_probes_set(state, ijk):
+    a = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
+    _check(load().ibm_probes_set(state, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), a.shape[0]),
+           "ibm_probes_set")
+
+
+def ibm_probe_sample(state, dst):
+    _check(load().ibm_probe_sample(state, dst), "ibm_probe_sample")
 
 
 def ibm_save(state, path):
@@ -504,6 +516,15 @@ class Solver:
         out = [np.empty((wl.ny, wl.nz)) for _ in range(3)]
         ibm_get_plane(self.state, i, *out)
         return tuple(out)
+
+    def set_probes(self, ijk):
+        """Probe cells (n, 3) of (i, j, k)."""
+        ibm_probes_set(self.state, ijk)
+
+    def probe_sample(self, dst):
+        """Cell-centred (u, v, w) of every probe into a device buffer (3 n values
+        in the state's precision), asynchronous on the solver's stream."""
+        ibm_probe_sample(self.state, dst)
 
     def save(self, path):
         ibm_save(self.state, path)

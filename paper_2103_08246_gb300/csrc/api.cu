@@ -321,6 +321,8 @@ struct ibm_state {
   bool deterministic = false;
   bool inflow = false;
   int bar_forcing = 0;   // 0: bar markers, 1: Eulerian volume-fraction forcing
+  int* probes = nullptr;  // virtual probes: cell (i, j, k) index triples (own allocation)
+  int nprobe = 0;
   Consts c{};
   ibm_grid grid{};
   ibm_domain dom{};
@@ -843,6 +845,25 @@ void launch_stage(ibm_state* s, int stage) {
 }  // namespace
 
 // ------------------------------------------------------------------ C ABI
+namespace {
+
+// cell-centred velocity at the probes: u from faces i, i + 1, v from j, j + 1,
+// w from k, k + 1 (periodic), written (u, v, w) per probe
+template <class T>
+__global__ void k_probe(const int* __restrict__ ijk, int n, int ny, int nz, const T* __restrict__ u,
+                        const T* __restrict__ v, const T* __restrict__ w, T* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int i = ijk[3 * q], j = ijk[3 * q + 1], k = ijk[3 * q + 2];
+  const int jp = j + 1 == ny ? 0 : j + 1, kp = k + 1 == nz ? 0 : k + 1;
+  const size_t P = (size_t)ny * nz, c = (size_t)i * P + (size_t)j * nz + k;
+  out[3 * q] = (T)0.5 * (u[c] + u[c + P]);
+  out[3 * q + 1] = (T)0.5 * (v[c] + v[(size_t)i * P + (size_t)jp * nz + k]);
+  out[3 * q + 2] = (T)0.5 * (w[c] + w[(size_t)i * P + (size_t)j * nz + kp]);
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* ibm_strerror(int code) {
@@ -1073,6 +1094,41 @@ int ibm_plane_device(ibm_state* s, int i, void** u, void** v, void** w) {
   return IBM_OK;
 }
 
+int ibm_probes_set(ibm_state* s, const int* ijk, int n) {
+  if (!s || n < 0 || n > (1 << 22) || (n > 0 && !ijk)) return IBM_EINVAL;
+  for (int q = 0; q < n; ++q)
+    if (ijk[3 * q] < 0 || ijk[3 * q] >= s->c.nx || ijk[3 * q + 1] < 0 || ijk[3 * q + 1] >= s->c.ny ||
+        ijk[3 * q + 2] < 0 || ijk[3 * q + 2] >= s->c.nz)
+      return IBM_EINVAL;
+  if (s->probes) {
+    cudaStreamSynchronize(s->stream);
+    cudaFree(s->probes);
+    s->probes = nullptr;
+    s->nprobe = 0;
+  }
+  if (n == 0) return IBM_OK;
+  if (cudaMalloc(&s->probes, (size_t)3 * n * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return IBM_ENOMEM;
+  }
+  if (cudaMemcpy(s->probes, ijk, (size_t)3 * n * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+    return IBM_ECUDA;
+  s->nprobe = n;
+  return IBM_OK;
+}
+
+int ibm_probe_sample(ibm_state* s, void* dst) {
+  if (!s || !dst || s->nprobe == 0) return IBM_EINVAL;
+  const int n = s->nprobe, nb = (n + 255) / 256;
+  if (s->precision == IBM_FP64)
+    k_probe<double><<<nb, 256, 0, s->stream>>>(s->probes, n, s->c.ny, s->c.nz, s->fd.u[s->cur],
+                                               s->fd.v[s->cur], s->fd.w[s->cur], (double*)dst);
+  else
+    k_probe<float><<<nb, 256, 0, s->stream>>>(s->probes, n, s->c.ny, s->c.nz, s->ff.u[s->cur],
+                                              s->ff.v[s->cur], s->ff.w[s->cur], (float*)dst);
+  return cudaGetLastError() == cudaSuccess ? IBM_OK : IBM_ECUDA;
+}
+
 int ibm_get_plane(ibm_state* s, int i, double* u, double* v, double* w) {
   if (!s || !u || !v || !w || i < 0 || i > s->c.nx) return IBM_EINVAL;
   void* p[3];
@@ -1262,6 +1318,7 @@ void ibm_destroy(ibm_state* s) {
       if (s->graph[k][q]) cudaGraphDestroy(s->graph[k][q]);
     }
   if (s->own_ws && s->ws) cudaFree(s->ws);
+  if (s->probes) cudaFree(s->probes);
   if (s->hprm) cudaFreeHost(s->hprm);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   if (s->side) cudaStreamDestroy(s->side);
