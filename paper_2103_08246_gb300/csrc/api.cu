@@ -347,6 +347,8 @@ struct ibm_state {
   int kernels_per_step = 0;
   float* hy = nullptr;                    // Hartley matrices (mixed precision)
   float* hz = nullptr;
+  unsigned char* hy_img = nullptr;        // their pre-split tensor-core images (square planes)
+  unsigned char* hz_img = nullptr;
   cudaStream_t side = nullptr;            // structural update, overlapped in the graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t side2 = nullptr;           // implicit-factor tables, overlapped with the RHS
@@ -458,6 +460,10 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   if (s->precision == IBM_MIXED) {
     s->hy = cv.take<float>((size_t)c.ny * c.ny);
     s->hz = cv.take<float>((size_t)c.nz * c.nz);
+    if (c.ny == c.nz && tc_supported(c.ny)) {
+      s->hy_img = cv.take<unsigned char>(tc_h_image_bytes(c.ny));
+      s->hz_img = cv.take<unsigned char>(tc_h_image_bytes(c.nz));
+    }
   }
   return cv.off + 256;
 }
@@ -548,7 +554,7 @@ void solve_poisson(ibm_state* s, cudaStream_t st) {
   Fields<T>& f = fields<T>(s);
   if constexpr (std::is_same<T, float>::value) {
     if (s->precision == IBM_MIXED) {
-      launch_poisson_mixed(s->c, f, s->hy, s->hz, st);
+      launch_poisson_mixed(s->c, f, s->hy, s->hz, s->hy_img, s->hz_img, st);
       return;
     }
   }
@@ -696,6 +702,12 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
     hartley_matrix(c.nz, H.data());
     CK(cudaMemcpyAsync(s->hz, H.data(), (size_t)c.nz * c.nz * sizeof(float), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
+    if (s->hy_img) {
+      tc_pack_h(s->hy, c.ny, s->hy_img, st);
+      tc_pack_h(s->hz, c.nz, s->hz_img, st);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(st));
+    }
   }
   launch_poisson_table(c, f, st);
   // initial projection of u0 (dt absorbed in phi), velocity only

@@ -93,8 +93,12 @@ template <class T> void launch_project(const Consts& c, const Fields<T>& f, int 
 template <class T>
 int partial_count(const Consts& c);
 size_t poisson_table_size(const Consts& c);
-// tensor-core (tcgen05) split-TF32 transform pass: out = (X H)^T per 256 x 256 plane
-bool tc_rows_times_h_t(const float* X, const float* H, float* out, int planes, int n, int* error,
+// tensor-core (tcgen05) split-TF32 transform pass: out = (X H)^T per n x n
+// plane (n = 32, 64, 128, 256), H given by its pre-split image
+bool tc_supported(int n);
+size_t tc_h_image_bytes(int n);
+void tc_pack_h(const float* H, int n, unsigned char* img, cudaStream_t s);
+bool tc_rows_times_h_t(const float* X, const unsigned char* himg, float* out, int planes, int n, int* error,
                        cudaStream_t s);
 void tc_gemm_set_attributes();
 int outflow_blocks(const Consts& c);
@@ -112,7 +116,8 @@ void poisson_set_attributes();
 
 // ---- mixed.cu
 void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* Hy,
-                          const float* Hz, cudaStream_t s);
+                          const float* Hz, const unsigned char* Hy_img, const unsigned char* Hz_img,
+                          cudaStream_t s);
 void mixed_set_attributes();
 void hartley_matrix(int n, float* host);
 

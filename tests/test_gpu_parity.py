@@ -230,7 +230,8 @@ def test_production_size_properties_fp32(lib):
 
 # ---------------------------------------------------------------- mixed precision
 # FP32 fields with the Poisson transforms as split-TF32 tensor-core GEMMs and
-# one FP64-residual refinement sweep: errors against the FP64 oracle are held
+# one refinement sweep on a double-single (FP64-class) residual: errors
+# against the FP64 oracle are held
 # to the FP32 bounds above (the split products keep ~FP32 accuracy and the
 # refinement removes the amplification of the transform rounding by the
 # Poisson conditioning).
