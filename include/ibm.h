@@ -58,7 +58,9 @@ extern "C" {
 #define IBM_FP64  0        /* everything in FP64                               */
 #define IBM_FP32  1        /* fluid fields and kernels in FP32; flag, sums FP64 */
 #define IBM_MIXED 2        /* FP32 fields; Poisson transforms as split-TF32 tensor-core
-                              GEMMs (FP32 accumulation) + FP64 residual refinement */
+                              GEMMs (FP32 accumulation) + one refinement sweep on a
+                              residual evaluated in double-single (FP64-class)
+                              arithmetic */
 
 /* stages for ibm_time_stage (Sec. II.B step order) */
 #define IBM_STAGE_STEP      -1  /* the whole captured step                   */
