@@ -58,4 +58,12 @@ __device__ inline bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// cp.async (non-bulk) groups: close the group of copies issued so far; wait
+// until at most N groups are pending
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ inline void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 }  // namespace ibm

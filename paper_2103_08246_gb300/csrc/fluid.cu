@@ -758,6 +758,12 @@ k_outflow(Consts c, const Params* __restrict__ prm, T* __restrict__ u,
   }
 }
 
+// asynchronous copy of one element (4 or 8 bytes) into shared memory
+template <class T>
+__device__ inline void cp_async_elem(uint32_t dst, const T* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(sizeof(T)) : "memory");
+}
+
 // x factor by the LU recursions on shared-memory-staged planes: one warp per
 // 32 consecutive (y, z) columns and XS planes (+ warm-up halos); lanes walk
 // their columns (bank-conflict free), loads and stores are 128-byte rows.
@@ -788,33 +794,19 @@ k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
   const T ob = act ? (comp == 0 ? o0 : comp == 1 ? o1 : o2)[col] : (T)0;
   // inflow-face increment (u) or twice the inflow-value increment (v, w ghost)
   const T ib = (act && inc) ? (comp == 0 ? (T)1 : (T)2) * inc[(size_t)comp * P + col] : (T)0;
-  if (P % 32 == 0) {
-    // every plane's 32-column row is one 16-byte-aligned bulk copy; all of
-    // them are in flight at once on one mbarrier (bounded wait)
-    __shared__ uint64_t bar;
-    if (lane == 0) {
-      mbar_init(&bar, 1);
-      fence_mbar_init();
-    }
-    __syncwarp();
-    if (lane == 0) {
-      const T* rows = d - lane;   // column col0 of plane k + ioff at rows + k P
-      mbar_arrive_expect_tx(&bar, (uint32_t)((ke - ks + 1) * 32 * sizeof(T)));
-      for (int k = ks; k <= ke; ++k)
-        bulk_g2s(s + (k - ks) * 32, rows + (size_t)k * P, 32 * sizeof(T), &bar);
-    }
-    if (!mbar_wait(&bar, 0)) {
-      if (lane == 0) {
-        atomicOr(&const_cast<Params*>(prm)->error, ERR_TIMEOUT);
-        (void)mbar_wait(&bar, 0);   // let the copies land before leaving
-      }
-      return;
-    }
-  } else {
-    if (act)
-      for (int k = ks; k <= ke; ++k) s[(k - ks) * 32 + lane] = d[(size_t)k * P];
-    __syncwarp();
+  // every lane copies its column of every plane with cp.async (each warp
+  // instruction one coalesced 128-byte row through the load/store path), all
+  // planes in flight at once; per-row bulk copies of 128 bytes were limited by
+  // the copy engine's issue rate
+  if (act) {
+    const uint32_t sb = smem_u32(s) + (uint32_t)(lane * sizeof(T));
+#pragma unroll 4
+    for (int k = ks; k <= ke; ++k)
+      cp_async_elem<T>(sb + (uint32_t)((k - ks) * 32 * sizeof(T)), d + (size_t)k * P);
+    cp_async_commit();
+    cp_async_wait<0>();
   }
+  __syncwarp();
   if (!act) return;
   // the recursions' loads (plane values, pivots) do not depend on the
   // running value: unrolled, they issue ahead of the two-operation chain

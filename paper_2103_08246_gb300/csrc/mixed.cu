@@ -201,23 +201,10 @@ __device__ inline DS two_sum(float a, float b) {
   return {s, e};
 }
 
-// ih2 = ih2_hi + ih2_lo: 1 / h^2 split on the host
-__global__ void k_residual_ds(int nx, int ny, int nz, float ih2_hi, float ih2_lo, const float* __restrict__ D,
-                              const float* __restrict__ phi, float* __restrict__ r) {
-  const int P = ny * nz;
-  const int jk = blockIdx.x * blockDim.x + threadIdx.x;
-  if (jk >= P) return;
-  const int i = blockIdx.y;
-  const int j = jk / nz, k = jk - j * nz;
-  const size_t b = (size_t)i * P;
-  const size_t id = b + jk;
-  const float pc = phi[id];
-  const float pxm = i > 0 ? phi[id - P] : pc;
-  const float pxp = i < nx - 1 ? phi[id + P] : pc;
-  const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
-  const int km = k == 0 ? nz - 1 : k - 1, kp = k == nz - 1 ? 0 : k + 1;
-  const float pym = phi[b + (size_t)jm * nz + k], pyp = phi[b + (size_t)jp * nz + k];
-  const float pzm = phi[b + (size_t)j * nz + km], pzp = phi[b + (size_t)j * nz + kp];
+// residual of one cell from its value, six neighbours and D, with
+// ih2 = ih2_hi + ih2_lo the host-split 1 / h^2
+__device__ inline float residual_ds(float pc, float pxm, float pxp, float pym, float pyp, float pzm, float pzp,
+                                    float D, float ih2_hi, float ih2_lo) {
   // S = sum of the six neighbours - 6 pc, as hi + lo
   const DS s1 = two_sum(pxm, pxp), s2 = two_sum(pym, pyp), s3 = two_sum(pzm, pzp);
   const DS s4 = two_sum(s1.hi, s2.hi), s5 = two_sum(s4.hi, s3.hi);
@@ -233,8 +220,37 @@ __global__ void k_residual_ds(int nx, int ny, int nz, float ih2_hi, float ih2_lo
                              __fadd_rn(__fmul_rn(S.hi, ih2_lo), __fmul_rn(S.lo, ih2_hi)));
   const DS lap = two_sum(ph, pe);
   // r = D - lap
-  const DS t = two_sum(D[id], -lap.hi);
-  r[id] = __fadd_rn(t.hi, __fsub_rn(t.lo, lap.lo));
+  const DS t = two_sum(D, -lap.hi);
+  return __fadd_rn(t.hi, __fsub_rn(t.lo, lap.lo));
+}
+
+// four consecutive z cells per thread (nz is a power of two >= 4): 16-byte loads of
+// the cell run and of its x and y neighbours, the two z neighbours past the
+// run's ends as single loads; grid (z runs, y rows, x planes)
+__global__ void k_residual_ds4(int nx, int ny, int nz, float ih2_hi, float ih2_lo, const float* __restrict__ D,
+                               const float* __restrict__ phi, float* __restrict__ r) {
+  const int k0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (k0 >= nz) return;
+  const int j = blockIdx.y, i = blockIdx.z;
+  const size_t P = (size_t)ny * nz;
+  const size_t row = (size_t)i * P + (size_t)j * nz;
+  const size_t id = row + k0;
+  const float4 c4 = *reinterpret_cast<const float4*>(phi + id);
+  const float4 xm = i > 0 ? *reinterpret_cast<const float4*>(phi + id - P) : c4;
+  const float4 xp = i < nx - 1 ? *reinterpret_cast<const float4*>(phi + id + P) : c4;
+  const size_t rm = (size_t)i * P + (size_t)(j == 0 ? ny - 1 : j - 1) * nz + k0;
+  const size_t rp = (size_t)i * P + (size_t)(j == ny - 1 ? 0 : j + 1) * nz + k0;
+  const float4 ym = *reinterpret_cast<const float4*>(phi + rm);
+  const float4 yp = *reinterpret_cast<const float4*>(phi + rp);
+  const float zl = phi[row + (k0 == 0 ? nz - 1 : k0 - 1)];
+  const float zr = phi[row + (k0 + 4 == nz ? 0 : k0 + 4)];
+  const float4 d4 = *reinterpret_cast<const float4*>(D + id);
+  float4 o;
+  o.x = residual_ds(c4.x, xm.x, xp.x, ym.x, yp.x, zl, c4.y, d4.x, ih2_hi, ih2_lo);
+  o.y = residual_ds(c4.y, xm.y, xp.y, ym.y, yp.y, c4.x, c4.z, d4.y, ih2_hi, ih2_lo);
+  o.z = residual_ds(c4.z, xm.z, xp.z, ym.z, yp.z, c4.y, c4.w, d4.z, ih2_hi, ih2_lo);
+  o.w = residual_ds(c4.w, xm.w, xp.w, ym.w, yp.w, c4.z, zr, d4.w, ih2_hi, ih2_lo);
+  *reinterpret_cast<float4*>(r + id) = o;
 }
 
 __global__ void k_add(size_t n, const float* __restrict__ a, const float* __restrict__ b,
@@ -294,7 +310,7 @@ void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* 
   const int nb = 152 * 8;
   const double ih2 = c.inv_h * c.inv_h;
   const float ih2_hi = (float)ih2, ih2_lo = (float)(ih2 - (double)ih2_hi);
-  k_residual_ds<<<dim3((c.ny * c.nz + 255) / 256, c.nx), 256, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, t1);
+  k_residual_ds4<<<dim3((c.nz / 4 + 63) / 64, c.ny, c.nx), 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, t1);
   transform2d(c, H, t1, t0, t1, err, s);
   launch_poisson_x_on(c, f, t1, s);
   transform2d(c, H, t1, t0, t1, err, s);

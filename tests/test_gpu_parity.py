@@ -237,6 +237,7 @@ def test_production_size_properties_fp32(lib):
 # Poisson conditioning).
 @pytest.mark.parametrize("case", ["plain", "ragged", "bars_flag"])
 def test_mixed_small_cases(lib, case):
+    """ragged: 8 x 16 planes (not square) take the mma.sync transform GEMMs."""
     from paper_2103_08246_gb300 import binding
     kw = {"plain": {}, "ragged": dict(shape=(20, 8, 16)),
           "bars_flag": dict(bars_on=True, bar_x=1.0, **FLAG)}[case]
