@@ -347,7 +347,7 @@ struct ibm_state {
   int kernels_per_step = 0;
   float* hy = nullptr;                    // Hartley matrices (mixed precision)
   float* hz = nullptr;
-  unsigned char* hy_img = nullptr;        // their pre-split tensor-core images (square planes)
+  unsigned char* hy_img = nullptr;        // pre-split cos / sin images for the tensor cores (square planes)
   unsigned char* hz_img = nullptr;
   cudaStream_t side = nullptr;            // structural update, overlapped in the graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -703,8 +703,8 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
     CK(cudaMemcpyAsync(s->hz, H.data(), (size_t)c.nz * c.nz * sizeof(float), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     if (s->hy_img) {
-      tc_pack_h(s->hy, c.ny, s->hy_img, st);
-      tc_pack_h(s->hz, c.nz, s->hz_img, st);
+      tc_pack_hartley(c.ny, s->hy_img, st);
+      tc_pack_hartley(c.nz, s->hz_img, st);
       CK(cudaGetLastError());
       CK(cudaStreamSynchronize(st));
     }

@@ -94,10 +94,11 @@ template <class T>
 int partial_count(const Consts& c);
 size_t poisson_table_size(const Consts& c);
 // tensor-core (tcgen05) split-TF32 transform pass: out = (X H)^T per n x n
-// plane (n = 32, 64, 128, 256), H given by its pre-split image
+// plane (n = 32, 64, 128, 256), H the Hartley matrix given by its pre-split
+// cos / sin image
 bool tc_supported(int n);
 size_t tc_h_image_bytes(int n);
-void tc_pack_h(const float* H, int n, unsigned char* img, cudaStream_t s);
+void tc_pack_hartley(int n, unsigned char* img, cudaStream_t s);
 bool tc_rows_times_h_t(const float* X, const unsigned char* himg, float* out, int planes, int n, int* error,
                        cudaStream_t s);
 void tc_gemm_set_attributes();

@@ -2,29 +2,39 @@
 // the Hartley transforms of the mixed-precision pressure solve: for every
 // n x n plane X (n = 32, 64, 128 or 256; rows of n contiguous values) it
 // computes
-//   out = (X H)^T,   H = H^T the n-point Hartley matrix,
-// with FP32 operands rounded as a ~ a_hi + a_lo, a_hi = tf32(a),
-// a_lo = tf32(a - a_hi) (round to nearest, ties away), and
-// a_hi b_hi + a_hi b_lo + a_lo b_hi accumulated in FP32 in tensor memory.
-// Applied twice, ((X H)^T H)^T = H X H: the 2-D transform of the plane, with
-// both GEMMs reading K-major rows.
+//   out = (X H)^T,   H[k][c] = cas(2 pi k c / n) = cos + sin,
+// applied twice, ((X H)^T H)^T = H X H: the 2-D transform of the plane.
+//
+// Even/odd split of each row x (m = n / 2): with e[0] = x[0], o[0] = 0 and
+//   e[k] = x[k] + x[n - k],  o[k] = x[k] - x[n - k]        k = 1 .. m - 1,
+//   C[c] = sum_{k<m} e[k] cos(2 pi k c / n),  S[c] = sum_{k<m} o[k] sin(2 pi k c / n),
+// the row's transform is
+//   y[c] = C[c] + S[c] + x[m] (-1)^c,  y[n - c] = C[c] - S[c] + x[m] (-1)^c   (c < m),
+//   y[m] = sum_k x[k] (-1)^k,
+// two m x m contractions instead of one n x n: half the tensor-core work and
+// half the bytes of the matrix operands. Operands are rounded as
+// a ~ a_hi + a_lo, a_hi = tf32(a), a_lo = tf32(a - a_hi) (round to nearest,
+// ties away), and a_hi b_hi + a_hi b_lo + a_lo b_hi is accumulated in FP32 in
+// tensor memory.
 //
 // Persistent and warp-specialised, one CTA per SM, tiles of 128 rows (of one
-// or several planes) x n columns, K in blocks of 16 through a four-stage
-// shared-memory ring:
-//  * warp 0 (one thread) fills a stage with one tensor-map copy of the A
-//    block, which lands directly in the K-major core-matrix layout (box of
-//    4 floats x 128 rows x 4 K-groups: [K-group][row][16 bytes]), and one
-//    bulk copy of the block's slice of the pre-split H image (hi and lo
-//    tiles in the same layout, built once by tc_pack_h);
-//  * warps 2-7 split the A block in place: a_hi over the raw values, a_lo
-//    into the stage's second A tile;
-//  * warp 1 (one thread) issues the 2 x 3 tcgen05.mma (M = 128, N = n,
-//    K = 8) of the block into one of two tensor-memory accumulators and
-//    commits them to the stage's "empty" barrier (and, after the tile's last
-//    block, to the accumulator's "full" barrier);
-//  * warps 8-15 read the other accumulator back with tcgen05.ld (warp w its
-//    lane quarter w % 4, half of the columns) and store it transposed into
+// or several planes); stage j of a tile holds the raw K blocks j and
+// n / 16 - 1 - j (16 values of every row each), so a row is read once:
+//  * warp 0 (one thread) fills a stage with two tensor-map copies of raw
+//    blocks, which land in the K-major core-matrix layout (box of 4 floats x
+//    128 rows x 4 K-groups: [K-group][row][16 bytes]), and one bulk copy of
+//    the stage's slice of the pre-split cos / sin image (tc_pack_hartley);
+//  * warps 2-5 (one thread per row) form e and o of the stage's 16 K values
+//    (the mirror of the block's first value is the previous stage's last
+//    block's first value), write e_hi / o_hi over the raw blocks and e_lo /
+//    o_lo beside them, and keep x[m] and the alternating sum of the row for
+//    the epilogue;
+//  * warp 1 (one thread) issues 2 x 2 x 3 tcgen05.mma (M = 128, N = m,
+//    K = 8) per stage into the tile's C and S accumulators (one of two
+//    tensor-memory buffers), commits them to the stage's "empty" barrier and,
+//    after the tile's last stage, to the buffer's "full" barrier;
+//  * warps 6-13 read the other buffer back with tcgen05.ld (warp w its lane
+//    quarter w % 4, half of the columns), form y and store it transposed into
 //    the plane: for every column the warp's 32 rows are 32 consecutive
 //    floats. Rows past the last plane load zeros (the tensor map's
 //    out-of-range fill) and store nothing.
@@ -43,19 +53,26 @@ namespace ibm {
 
 namespace {
 
-constexpr int TC_M = 128, TC_KB = 16, TC_STAGES = 4;
-constexpr int TC_THREADS = 512;                    // 16 warps
-constexpr int TC_CONV_WARPS = 6, TC_EPI_WARPS = 8;
-constexpr uint32_t A_TILE = TC_M * TC_KB * 4;      // bytes of one A part (hi or lo)
+constexpr int TC_M = 128, TC_KB = 16;
+constexpr int TC_THREADS = 448;                    // 14 warps
+constexpr int TC_CONV_WARPS = 4, TC_EPI_WARPS = 8;
+constexpr int TC_EPI0 = 2 + TC_CONV_WARPS;         // first epilogue warp
+constexpr uint32_t A_TILE = TC_M * TC_KB * 4;      // one raw block (or one e / o part): 8 KB
 constexpr uint32_t A_LBO = TC_M * 16;              // K-adjacent core matrices of A
+constexpr uint32_t SMEM_BUDGET = 192 * 1024;
 template <int N>
 struct TcCfg {
-  static constexpr uint32_t B_TILE = (uint32_t)N * TC_KB * 4;
-  static constexpr uint32_t B_LBO = (uint32_t)N * 16;
-  static constexpr uint32_t STAGE = 2 * A_TILE + 2 * B_TILE;   // A_hi, A_lo, B_hi, B_lo
-  static constexpr uint32_t SMEM = TC_STAGES * STAGE;
-  static constexpr uint32_t TMEM_COLS = 2 * N;                 // two accumulators
-  static constexpr int NKB = N / TC_KB;
+  static constexpr int MH = N / 2;                              // m: the contractions' K and N
+  static constexpr uint32_t B_PART = (uint32_t)MH * TC_KB * 4;  // one of cos_hi, cos_lo, sin_hi, sin_lo
+  static constexpr uint32_t B_LBO = (uint32_t)MH * 16;
+  static constexpr uint32_t B_TX = 4 * B_PART;
+  // e_hi (over raw block j), o_hi (over raw block n/16-1-j), e_lo, o_lo, then the B parts
+  static constexpr uint32_t STAGE = 4 * A_TILE + B_TX;
+  static constexpr int STAGES = SMEM_BUDGET / STAGE > 4 ? 4 : (int)(SMEM_BUDGET / STAGE);
+  static constexpr uint32_t SMEM = STAGES * STAGE;
+  static constexpr uint32_t TMEM_COLS = 4 * MH;                 // two buffers of C and S
+  static constexpr int NS = N / 32;                             // stages per tile
+  static constexpr int NB = N / 16;                             // raw K blocks per row
 };
 
 __device__ inline uint32_t tf32_bits(float x) {
@@ -98,8 +115,21 @@ __device__ inline void bulk_g2s_u32(uint32_t dst, const void* src, uint32_t byte
       : "memory");
 }
 
+__device__ inline uint4 split_hi(const float (&v)[4], uint4& lo) {
+  uint4 h;
+  h.x = tf32_bits(v[0]);
+  h.y = tf32_bits(v[1]);
+  h.z = tf32_bits(v[2]);
+  h.w = tf32_bits(v[3]);
+  lo.x = tf32_bits(v[0] - __uint_as_float(h.x));
+  lo.y = tf32_bits(v[1] - __uint_as_float(h.y));
+  lo.z = tf32_bits(v[2] - __uint_as_float(h.z));
+  lo.w = tf32_bits(v[3] - __uint_as_float(h.w));
+  return h;
+}
+
 struct TcArgs {
-  const unsigned char* himg;   // pre-split H (tc_pack_h)
+  const unsigned char* img;    // pre-split cos / sin image (tc_pack_hartley)
   float* out;                  // per plane: out[c][r] = sum_k X[r][k] H[k][c]
   int M;                       // rows of X (planes x n)
   int* error;
@@ -108,19 +138,20 @@ struct TcArgs {
 template <int N>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, const __grid_constant__ CUtensorMap xmap) {
   using C = TcCfg<N>;
-  constexpr uint32_t A_TX = A_TILE, B_TX = 2 * C::B_TILE;
+  constexpr int MH = C::MH, ST = C::STAGES;
   extern __shared__ __align__(1024) unsigned char tsm[];
-  __shared__ uint64_t full[TC_STAGES], conv[TC_STAGES], empty[TC_STAGES], tfull[2], tempty[2];
+  __shared__ uint64_t full[ST], conv[ST], empty[ST], tfull[2], tempty[2], xfull[2], xempty[2];
+  __shared__ float xm_s[2][TC_M], ym_s[2][TC_M];   // per row of a tile: x[m] and y[m]
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = (g.M + TC_M - 1) / TC_M;
   const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int total = my_tiles * C::NKB;
+  const int total = my_tiles * C::NS;
   const uint32_t sbase = smem_u32(tsm);
 
   if (warp == 0) tc_alloc(&tmem_slot, C::TMEM_COLS);
   if (tid == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < ST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&conv[s], TC_CONV_WARPS);
       mbar_init(&empty[s], 1);
@@ -128,6 +159,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, cons
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], TC_EPI_WARPS);
+      mbar_init(&xfull[b], TC_CONV_WARPS);
+      mbar_init(&xempty[b], TC_EPI_WARPS);
     }
     fence_mbar_init();
   }
@@ -140,95 +173,149 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, cons
   if (warp == 0) {
     if (lane == 0) {
       for (int j = 0; j < total; ++j) {
-        const int s = j % TC_STAGES;
-        if (j >= TC_STAGES) ok = mbar_wait(&empty[s], (uint32_t)(j / TC_STAGES - 1) & 1u) && ok;
-        const int lt = j / C::NKB, kb = j % C::NKB;
+        const int s = j % ST;
+        if (j >= ST) ok = mbar_wait(&empty[s], (uint32_t)(j / ST - 1) & 1u) && ok;
+        const int lt = j / C::NS, js = j % C::NS;
         const int m0 = ((int)blockIdx.x + lt * (int)gridDim.x) * TC_M;
         const uint32_t st = sbase + (uint32_t)s * C::STAGE;
-        mbar_arrive_expect_tx(&full[s], A_TX + B_TX);
-        tma_load_3d(st, &xmap, 0, m0, kb * (TC_KB / 4), &full[s]);
-        bulk_g2s_u32(st + 2 * A_TILE, g.himg + (size_t)kb * B_TX, B_TX, &full[s]);
+        mbar_arrive_expect_tx(&full[s], 2 * A_TILE + C::B_TX);
+        tma_load_3d(st, &xmap, 0, m0, js * (TC_KB / 4), &full[s]);
+        tma_load_3d(st + A_TILE, &xmap, 0, m0, (C::NB - 1 - js) * (TC_KB / 4), &full[s]);
+        bulk_g2s_u32(st + 4 * A_TILE, g.img + (size_t)js * C::B_TX, C::B_TX, &full[s]);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc_idesc(N);
+      constexpr uint32_t idesc = tc_idesc(MH);
       for (int j = 0; j < total; ++j) {
-        const int s = j % TC_STAGES;
-        const int lt = j / C::NKB, kb = j % C::NKB;
-        // the accumulator's previous tile (lt - 2) must have been read out
-        if (kb == 0 && lt >= 2) ok = mbar_wait(&tempty[lt & 1], (uint32_t)((lt - 2) / 2) & 1u) && ok;
-        ok = mbar_wait(&conv[s], (uint32_t)(j / TC_STAGES) & 1u) && ok;
+        const int s = j % ST;
+        const int lt = j / C::NS, js = j % C::NS;
+        // the buffer's previous tile (lt - 2) must have been read out
+        if (js == 0 && lt >= 2) ok = mbar_wait(&tempty[lt & 1], (uint32_t)((lt - 2) / 2) & 1u) && ok;
+        ok = mbar_wait(&conv[s], (uint32_t)(j / ST) & 1u) && ok;
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)((lt & 1) * N);
-        const uint32_t ah = sbase + (uint32_t)s * C::STAGE, al = ah + A_TILE;
-        const uint32_t bh = ah + 2 * A_TILE, bl = bh + C::B_TILE;
+        const uint32_t dc = tmem + (uint32_t)((lt & 1) * 2 * MH), ds = dc + (uint32_t)MH;
+        const uint32_t eh = sbase + (uint32_t)s * C::STAGE, oh = eh + A_TILE, el = eh + 2 * A_TILE,
+                       ol = eh + 3 * A_TILE;
+        const uint32_t ch = eh + 4 * A_TILE, cl = ch + C::B_PART, sh = cl + C::B_PART, sl = sh + C::B_PART;
 #pragma unroll
         for (int kk = 0; kk < TC_KB / 8; ++kk) {   // K = 8: two K-groups per instruction
           const uint32_t ka = (uint32_t)kk * 2 * A_LBO, kb2 = (uint32_t)kk * 2 * C::B_LBO;
-          tc_mma(d, tc_desc(ah + ka, A_LBO, 128), tc_desc(bh + kb2, C::B_LBO, 128), idesc,
-                 (kb == 0 && kk == 0) ? 0u : 1u);
-          tc_mma(d, tc_desc(ah + ka, A_LBO, 128), tc_desc(bl + kb2, C::B_LBO, 128), idesc, 1u);
-          tc_mma(d, tc_desc(al + ka, A_LBO, 128), tc_desc(bh + kb2, C::B_LBO, 128), idesc, 1u);
+          const uint32_t first = (js == 0 && kk == 0) ? 0u : 1u;
+          tc_mma(dc, tc_desc(eh + ka, A_LBO, 128), tc_desc(ch + kb2, C::B_LBO, 128), idesc, first);
+          tc_mma(dc, tc_desc(eh + ka, A_LBO, 128), tc_desc(cl + kb2, C::B_LBO, 128), idesc, 1u);
+          tc_mma(dc, tc_desc(el + ka, A_LBO, 128), tc_desc(ch + kb2, C::B_LBO, 128), idesc, 1u);
+          tc_mma(ds, tc_desc(oh + ka, A_LBO, 128), tc_desc(sh + kb2, C::B_LBO, 128), idesc, first);
+          tc_mma(ds, tc_desc(oh + ka, A_LBO, 128), tc_desc(sl + kb2, C::B_LBO, 128), idesc, 1u);
+          tc_mma(ds, tc_desc(ol + ka, A_LBO, 128), tc_desc(sh + kb2, C::B_LBO, 128), idesc, 1u);
         }
         tc_commit_to(&empty[s]);
-        if (kb == C::NKB - 1) tc_commit_to(&tfull[lt & 1]);
+        if (js == C::NS - 1) tc_commit_to(&tfull[lt & 1]);
       }
     }
-  } else if (warp < 2 + TC_CONV_WARPS) {
-    // split: 16-byte chunks of the A block, a_hi in place, a_lo to the second tile
-    const int ct = tid - 64;
-    constexpr int CHUNKS = A_TILE / 16;
+  } else if (warp < TC_EPI0) {
+    // one thread per row of the tile: e and o of the stage's 16 K values
+    const int t = tid - 64;
+    float carry = 0.f, alt = 0.f;
     for (int j = 0; j < total; ++j) {
-      const int s = j % TC_STAGES;
-      ok = mbar_wait(&full[s], (uint32_t)(j / TC_STAGES) & 1u) && ok;
-      uint4* hi = reinterpret_cast<uint4*>(tsm + (size_t)s * C::STAGE);
-      uint4* lo = reinterpret_cast<uint4*>(tsm + (size_t)s * C::STAGE + A_TILE);
-      for (int q = ct; q < CHUNKS; q += 32 * TC_CONV_WARPS) {
-        const uint4 v = hi[q];
-        uint4 h, l;
-        h.x = tf32_bits(__uint_as_float(v.x));
-        h.y = tf32_bits(__uint_as_float(v.y));
-        h.z = tf32_bits(__uint_as_float(v.z));
-        h.w = tf32_bits(__uint_as_float(v.w));
-        l.x = tf32_bits(__uint_as_float(v.x) - __uint_as_float(h.x));
-        l.y = tf32_bits(__uint_as_float(v.y) - __uint_as_float(h.y));
-        l.z = tf32_bits(__uint_as_float(v.z) - __uint_as_float(h.z));
-        l.w = tf32_bits(__uint_as_float(v.w) - __uint_as_float(h.w));
-        hi[q] = h;
-        lo[q] = l;
+      const int s = j % ST;
+      const int lt = j / C::NS, js = j % C::NS;
+      ok = mbar_wait(&full[s], (uint32_t)(j / ST) & 1u) && ok;
+      unsigned char* st = tsm + (size_t)s * C::STAGE;
+      float a[16], b[16];
+#pragma unroll
+      for (int kg = 0; kg < 4; ++kg) {
+        const float4 va = *reinterpret_cast<const float4*>(st + kg * A_LBO + t * 16);
+        const float4 vb = *reinterpret_cast<const float4*>(st + A_TILE + kg * A_LBO + t * 16);
+        a[4 * kg] = va.x, a[4 * kg + 1] = va.y, a[4 * kg + 2] = va.z, a[4 * kg + 3] = va.w;
+        b[4 * kg] = vb.x, b[4 * kg + 1] = vb.y, b[4 * kg + 2] = vb.z, b[4 * kg + 3] = vb.w;
+      }
+      if (js == 0) alt = 0.f;
+      float e[16], o[16];
+      // the mirror n - k of k = 16 js + q is b[16 - q] (q > 0); of k = 16 js it
+      // is the first value of the previous stage's second block (none for k = 0)
+      e[0] = js == 0 ? a[0] : a[0] + carry;
+      o[0] = js == 0 ? 0.f : a[0] - carry;
+#pragma unroll
+      for (int q = 1; q < 16; ++q) {
+        e[q] = a[q] + b[16 - q];
+        o[q] = a[q] - b[16 - q];
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) alt += (q & 1) ? -(a[q] + b[q]) : (a[q] + b[q]);
+      carry = b[0];
+#pragma unroll
+      for (int kg = 0; kg < 4; ++kg) {
+        const float ve[4] = {e[4 * kg], e[4 * kg + 1], e[4 * kg + 2], e[4 * kg + 3]};
+        const float vo[4] = {o[4 * kg], o[4 * kg + 1], o[4 * kg + 2], o[4 * kg + 3]};
+        uint4 lo;
+        const uint4 he = split_hi(ve, lo);
+        *reinterpret_cast<uint4*>(st + kg * A_LBO + t * 16) = he;
+        *reinterpret_cast<uint4*>(st + 2 * A_TILE + kg * A_LBO + t * 16) = lo;
+        const uint4 ho = split_hi(vo, lo);
+        *reinterpret_cast<uint4*>(st + A_TILE + kg * A_LBO + t * 16) = ho;
+        *reinterpret_cast<uint4*>(st + 3 * A_TILE + kg * A_LBO + t * 16) = lo;
       }
       fence_proxy_async_smem();   // generic-proxy writes -> visible to the tensor core
+      if (js == C::NS - 1) {
+        // x[m] is the first value of the last stage's second block
+        if (lt >= 2) ok = mbar_wait(&xempty[lt & 1], (uint32_t)((lt - 2) / 2) & 1u) && ok;
+        xm_s[lt & 1][t] = b[0];
+        ym_s[lt & 1][t] = alt;
+      }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&conv[s]);
+      if (lane == 0) {
+        mbar_arrive(&conv[s]);
+        if (js == C::NS - 1) mbar_arrive(&xfull[lt & 1]);
+      }
     }
   } else {
-    // epilogue warps 8 .. 15: lane quarter warp % 4, column half (warp - 8) / 4
-    const int quarter = warp & 3, part = (warp - 8) >> 2;
-    constexpr int SPLIT = N >= 64 ? 2 : 1;
+    // epilogue warps: lane quarter warp % 4, column half (warp - TC_EPI0) / 4
+    const int quarter = warp & 3, part = (warp - TC_EPI0) >> 2;
+    constexpr int SPLIT = MH >= 32 ? 2 : 1;
+    constexpr int CW = MH / SPLIT < 32 ? MH / SPLIT : 32;
     for (int lt = 0; lt < my_tiles; ++lt) {
-      const int m = ((int)blockIdx.x + lt * (int)gridDim.x) * TC_M + quarter * 32 + lane;
+      const int r = quarter * 32 + lane;
+      const int m = ((int)blockIdx.x + lt * (int)gridDim.x) * TC_M + r;
       ok = mbar_wait(&tfull[lt & 1], (uint32_t)(lt / 2) & 1u) && ok;
+      ok = mbar_wait(&xfull[lt & 1], (uint32_t)(lt / 2) & 1u) && ok;
       tc_fence_after();
-      const uint32_t d = tmem + (uint32_t)((lt & 1) * N) + ((uint32_t)(quarter * 32) << 16);
+      const float xm = xm_s[lt & 1][r];
+      const uint32_t dc = tmem + (uint32_t)((lt & 1) * 2 * MH) + ((uint32_t)(quarter * 32) << 16);
       float* plane = g.out + (size_t)(m / N) * N * N + (m % N);
+      const bool live = m < g.M;
+      if (part == 0 && live) plane[(size_t)MH * N] = ym_s[lt & 1][r];
       if (part < SPLIT) {
 #pragma unroll 1
-        for (int c0 = part * (N / SPLIT); c0 < (part + 1) * (N / SPLIT); c0 += 32) {
-          float v[32];
-          tc_ld_x32(d + (uint32_t)c0, v);
-          if (m < g.M) {
+        for (int c0 = part * (MH / SPLIT); c0 < (part + 1) * (MH / SPLIT); c0 += CW) {
+          float vc[CW], vs[CW];
+          if constexpr (CW == 32) {
+            tc_ld_x32(dc + (uint32_t)c0, vc);
+            tc_ld_x32(dc + (uint32_t)(MH + c0), vs);
+          } else {
+            tc_ld_x16(dc + (uint32_t)c0, vc);
+            tc_ld_x16(dc + (uint32_t)(MH + c0), vs);
+          }
+          if (live) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) plane[(size_t)(c0 + q) * N] = v[q];
+            for (int q = 0; q < CW; ++q) {
+              const int c = c0 + q;
+              const float base = vc[q] + ((c & 1) ? -xm : xm);
+              plane[(size_t)c * N] = base + vs[q];
+              if (c > 0) plane[(size_t)(N - c) * N] = base - vs[q];
+            }
           }
         }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[lt & 1]);
+      if (lane == 0) {
+        mbar_arrive(&tempty[lt & 1]);
+        mbar_arrive(&xempty[lt & 1]);
+      }
     }
   }
-  // every MMA has completed once the last tile's accumulator was committed
+  // every MMA has completed once the last tile's buffer was committed
   if (tid == 32 && my_tiles > 0)
     ok = mbar_wait(&tfull[(my_tiles - 1) & 1], (uint32_t)((my_tiles - 1) / 2) & 1u) && ok;
   ok = __syncthreads_and(ok) != 0;
@@ -237,21 +324,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, cons
   if (warp == 0) tc_dealloc(tmem, C::TMEM_COLS);
 }
 
-// pre-split H image: per K block kb, the hi tile then the lo tile, each
-// [K-group][n][4 floats] (element (c, k) = H[k][c]); one thread per value
-__global__ void k_pack_h(const float* __restrict__ H, int n, uint32_t* __restrict__ img) {
-  const int total = 2 * n * n;
+// pre-split cos / sin image: per stage js (K rows k = 16 js .. 16 js + 15),
+// the parts cos_hi, cos_lo, sin_hi, sin_lo, each [K-group][c][4 floats],
+// c < n / 2, element (c, k) = cos or sin of 2 pi (k c mod n) / n from FP64
+// sincospi; hi = tf32(v), lo = tf32(v - hi) with the remainder taken in FP64
+__global__ void k_pack_hartley(int n, uint32_t* __restrict__ img) {
+  const int m = n / 2, total = n * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const int e = i & 3;
-    const int c = (i >> 2) % n;
-    const int rest = (i >> 2) / n;              // (kb * 2 + part) * (TC_KB / 4) + kg
-    const int kg = rest % (TC_KB / 4);
-    const int part = (rest / (TC_KB / 4)) & 1;
-    const int kb = rest / (2 * (TC_KB / 4));
-    const int k = kb * TC_KB + kg * 4 + e;
-    const float x = H[(size_t)k * n + c];
-    const uint32_t h = tf32_bits(x);
-    img[i] = part == 0 ? h : tf32_bits(x - __uint_as_float(h));
+    const int c = (i >> 2) % m;
+    const int rest = (i >> 2) / m;   // (js * 4 + part) * 4 + kg
+    const int kg = rest & 3, part = (rest >> 2) & 3, js = rest >> 4;
+    const int k = js * TC_KB + kg * 4 + e;
+    const long long kc = ((long long)k * c) % n;
+    double sv, cv;
+    sincospi(2.0 * (double)kc / (double)n, &sv, &cv);
+    const double v = part < 2 ? cv : sv;
+    const uint32_t h = tf32_bits((float)v);
+    img[i] = (part & 1) == 0 ? h : tf32_bits((float)(v - (double)__uint_as_float(h)));
   }
 }
 
@@ -301,23 +391,24 @@ bool launch_tc(const float* X, const TcArgs& g, cudaStream_t s) {
 
 bool tc_supported(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
 
-size_t tc_h_image_bytes(int n) { return tc_supported(n) ? (size_t)2 * n * n * sizeof(float) : 0; }
+size_t tc_h_image_bytes(int n) { return tc_supported(n) ? (size_t)n * n * sizeof(float) : 0; }
 
-void tc_pack_h(const float* H, int n, unsigned char* img, cudaStream_t s) {
+void tc_pack_hartley(int n, unsigned char* img, cudaStream_t s) {
   if (!tc_supported(n)) return;
-  const int total = 2 * n * n;
-  k_pack_h<<<(total + 255) / 256, 256, 0, s>>>(H, n, reinterpret_cast<uint32_t*>(img));
+  const int total = n * n;
+  k_pack_hartley<<<(total + 255) / 256, 256, 0, s>>>(n, reinterpret_cast<uint32_t*>(img));
 }
 
 // out = (X H)^T for each of the `planes` n x n planes of X (rows of n
-// contiguous values), n = 32, 64, 128 or 256, H given by its pre-split image
-// (tc_pack_h); X, out 16-byte aligned, out distinct from X. error: device
-// flag that receives ERR_TIMEOUT if a bounded wait runs out. Returns false
-// (nothing launched) for other n or when the tensor map cannot be encoded.
-bool tc_rows_times_h_t(const float* X, const unsigned char* himg, float* out, int planes, int n, int* error,
+// contiguous values), n = 32, 64, 128 or 256, H the n-point Hartley matrix
+// given by its pre-split cos / sin image (tc_pack_hartley); X, out 16-byte
+// aligned, out distinct from X. error: device flag that receives
+// ERR_TIMEOUT if a bounded wait runs out. Returns false (nothing launched)
+// for other n or when the tensor map cannot be encoded.
+bool tc_rows_times_h_t(const float* X, const unsigned char* img, float* out, int planes, int n, int* error,
                        cudaStream_t s) {
   if (planes <= 0) return tc_supported(n);
-  TcArgs g{himg, out, planes * n, error};
+  TcArgs g{img, out, planes * n, error};
   switch (n) {
     case 32: return launch_tc<32>(X, g, s);
     case 64: return launch_tc<64>(X, g, s);
