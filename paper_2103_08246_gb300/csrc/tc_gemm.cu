@@ -5,6 +5,10 @@
 //   out = (X H)^T,   H[k][c] = cas(2 pi k c / n) = cos + sin,
 // applied twice, ((X H)^T H)^T = H X H: the 2-D transform of the plane.
 //
+// Planes of 256 (the production case) use the even/odd form below; planes
+// of 32, 64 and 128 (the ensemble's members) the direct form (namespace
+// direct), one n x n contraction per row with a lighter register footprint.
+//
 // Even/odd split of each row x (m = n / 2): with e[0] = x[0], o[0] = 0 and
 //   e[k] = x[k] + x[n - k],  o[k] = x[k] - x[n - k]        k = 1 .. m - 1,
 //   C[c] = sum_{k<m} e[k] cos(2 pi k c / n),  S[c] = sum_{k<m} o[k] sin(2 pi k c / n),
@@ -68,7 +72,7 @@ struct TcCfg {
   static constexpr uint32_t B_TX = 4 * B_PART;
   // e_hi (over raw block j), o_hi (over raw block n/16-1-j), e_lo, o_lo, then the B parts
   static constexpr uint32_t STAGE = 4 * A_TILE + B_TX;
-  static constexpr int STAGES = SMEM_BUDGET / STAGE > 4 ? 4 : (int)(SMEM_BUDGET / STAGE);
+  static constexpr int STAGES = SMEM_BUDGET / STAGE > 3 ? 3 : (int)(SMEM_BUDGET / STAGE);
   static constexpr uint32_t SMEM = STAGES * STAGE;
   static constexpr uint32_t TMEM_COLS = 4 * MH;                 // two buffers of C and S
   static constexpr int NS = N / 32;                             // stages per tile
@@ -324,6 +328,189 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, cons
   if (warp == 0) tc_dealloc(tmem, C::TMEM_COLS);
 }
 
+// ---- direct form for planes of 32, 64 and 128 (the ensemble's members): one
+// n x n contraction per row, K in blocks of 16 through a four-stage ring, the
+// A block split in place by six warps; 512 threads at about 53 registers
+// leave room on the SM for the concurrent kernels of other ensemble members
+// (the even/odd form above holds 448 threads at 128 registers)
+namespace direct {
+
+constexpr int D_STAGES = 4;
+constexpr int D_THREADS = 512;                     // 16 warps
+constexpr int D_CONV_WARPS = 6, D_EPI_WARPS = 8;
+template <int N>
+struct DCfg {
+  static constexpr uint32_t B_TILE = (uint32_t)N * TC_KB * 4;
+  static constexpr uint32_t B_LBO = (uint32_t)N * 16;
+  static constexpr uint32_t STAGE = 2 * A_TILE + 2 * B_TILE;   // A_hi, A_lo, B_hi, B_lo
+  static constexpr uint32_t SMEM = D_STAGES * STAGE;
+  static constexpr uint32_t TMEM_COLS = 2 * N;                 // two accumulators
+  static constexpr int NKB = N / TC_KB;
+};
+
+struct DArgs {
+  const unsigned char* himg;   // pre-split H (k_pack_direct)
+  float* out;                  // per plane: out[c][r] = sum_k X[r][k] H[k][c]
+  int M;                       // rows of X (planes x n)
+  int* error;
+};
+
+template <int N>
+__global__ void __launch_bounds__(D_THREADS, 1) k_gemm_tc_direct(DArgs g, const __grid_constant__ CUtensorMap xmap) {
+  using C = DCfg<N>;
+  constexpr uint32_t A_TX = A_TILE, B_TX = 2 * C::B_TILE;
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  __shared__ uint64_t full[D_STAGES], conv[D_STAGES], empty[D_STAGES], tfull[2], tempty[2];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = (g.M + TC_M - 1) / TC_M;
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int total = my_tiles * C::NKB;
+  const uint32_t sbase = smem_u32(tsm);
+
+  if (warp == 0) tc_alloc(&tmem_slot, C::TMEM_COLS);
+  if (tid == 0) {
+    for (int s = 0; s < D_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], D_CONV_WARPS);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], D_EPI_WARPS);
+    }
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int j = 0; j < total; ++j) {
+        const int s = j % D_STAGES;
+        if (j >= D_STAGES) ok = mbar_wait(&empty[s], (uint32_t)(j / D_STAGES - 1) & 1u) && ok;
+        const int lt = j / C::NKB, kb = j % C::NKB;
+        const int m0 = ((int)blockIdx.x + lt * (int)gridDim.x) * TC_M;
+        const uint32_t st = sbase + (uint32_t)s * C::STAGE;
+        mbar_arrive_expect_tx(&full[s], A_TX + B_TX);
+        tma_load_3d(st, &xmap, 0, m0, kb * (TC_KB / 4), &full[s]);
+        bulk_g2s_u32(st + 2 * A_TILE, g.himg + (size_t)kb * B_TX, B_TX, &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc(N);
+      for (int j = 0; j < total; ++j) {
+        const int s = j % D_STAGES;
+        const int lt = j / C::NKB, kb = j % C::NKB;
+        // the accumulator's previous tile (lt - 2) must have been read out
+        if (kb == 0 && lt >= 2) ok = mbar_wait(&tempty[lt & 1], (uint32_t)((lt - 2) / 2) & 1u) && ok;
+        ok = mbar_wait(&conv[s], (uint32_t)(j / D_STAGES) & 1u) && ok;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)((lt & 1) * N);
+        const uint32_t ah = sbase + (uint32_t)s * C::STAGE, al = ah + A_TILE;
+        const uint32_t bh = ah + 2 * A_TILE, bl = bh + C::B_TILE;
+#pragma unroll
+        for (int kk = 0; kk < TC_KB / 8; ++kk) {   // K = 8: two K-groups per instruction
+          const uint32_t ka = (uint32_t)kk * 2 * A_LBO, kb2 = (uint32_t)kk * 2 * C::B_LBO;
+          tc_mma(d, tc_desc(ah + ka, A_LBO, 128), tc_desc(bh + kb2, C::B_LBO, 128), idesc,
+                 (kb == 0 && kk == 0) ? 0u : 1u);
+          tc_mma(d, tc_desc(ah + ka, A_LBO, 128), tc_desc(bl + kb2, C::B_LBO, 128), idesc, 1u);
+          tc_mma(d, tc_desc(al + ka, A_LBO, 128), tc_desc(bh + kb2, C::B_LBO, 128), idesc, 1u);
+        }
+        tc_commit_to(&empty[s]);
+        if (kb == C::NKB - 1) tc_commit_to(&tfull[lt & 1]);
+      }
+    }
+  } else if (warp < 2 + D_CONV_WARPS) {
+    // split: 16-byte chunks of the A block, a_hi in place, a_lo to the second tile
+    const int ct = tid - 64;
+    constexpr int CHUNKS = A_TILE / 16;
+    for (int j = 0; j < total; ++j) {
+      const int s = j % D_STAGES;
+      ok = mbar_wait(&full[s], (uint32_t)(j / D_STAGES) & 1u) && ok;
+      uint4* hi = reinterpret_cast<uint4*>(tsm + (size_t)s * C::STAGE);
+      uint4* lo = reinterpret_cast<uint4*>(tsm + (size_t)s * C::STAGE + A_TILE);
+      for (int q = ct; q < CHUNKS; q += 32 * D_CONV_WARPS) {
+        const uint4 v = hi[q];
+        uint4 h, l;
+        h.x = tf32_bits(__uint_as_float(v.x));
+        h.y = tf32_bits(__uint_as_float(v.y));
+        h.z = tf32_bits(__uint_as_float(v.z));
+        h.w = tf32_bits(__uint_as_float(v.w));
+        l.x = tf32_bits(__uint_as_float(v.x) - __uint_as_float(h.x));
+        l.y = tf32_bits(__uint_as_float(v.y) - __uint_as_float(h.y));
+        l.z = tf32_bits(__uint_as_float(v.z) - __uint_as_float(h.z));
+        l.w = tf32_bits(__uint_as_float(v.w) - __uint_as_float(h.w));
+        hi[q] = h;
+        lo[q] = l;
+      }
+      fence_proxy_async_smem();   // generic-proxy writes -> visible to the tensor core
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&conv[s]);
+    }
+  } else {
+    // epilogue warps 8 .. 15: lane quarter warp % 4, column half (warp - 8) / 4
+    const int quarter = warp & 3, part = (warp - 8) >> 2;
+    constexpr int SPLIT = N >= 64 ? 2 : 1;
+    for (int lt = 0; lt < my_tiles; ++lt) {
+      const int m = ((int)blockIdx.x + lt * (int)gridDim.x) * TC_M + quarter * 32 + lane;
+      ok = mbar_wait(&tfull[lt & 1], (uint32_t)(lt / 2) & 1u) && ok;
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)((lt & 1) * N) + ((uint32_t)(quarter * 32) << 16);
+      float* plane = g.out + (size_t)(m / N) * N * N + (m % N);
+      if (part < SPLIT) {
+#pragma unroll 1
+        for (int c0 = part * (N / SPLIT); c0 < (part + 1) * (N / SPLIT); c0 += 32) {
+          float v[32];
+          tc_ld_x32(d + (uint32_t)c0, v);
+          if (m < g.M) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) plane[(size_t)(c0 + q) * N] = v[q];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[lt & 1]);
+    }
+  }
+  // every MMA has completed once the last tile's accumulator was committed
+  if (tid == 32 && my_tiles > 0)
+    ok = mbar_wait(&tfull[(my_tiles - 1) & 1], (uint32_t)((my_tiles - 1) / 2) & 1u) && ok;
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok && tid == 0) atomicOr(g.error, ERR_TIMEOUT);
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tmem, C::TMEM_COLS);
+}
+
+// pre-split H image: per K block kb, the hi tile then the lo tile, each
+// [K-group][n][4 floats], element (c, k) = cas(2 pi (k c mod n) / n) from
+// FP64 sincospi; hi = tf32(v), lo = tf32(v - hi) with the remainder in FP64
+__global__ void k_pack_direct(int n, uint32_t* __restrict__ img) {
+  const int total = 2 * n * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int e = i & 3;
+    const int c = (i >> 2) % n;
+    const int rest = (i >> 2) / n;              // (kb * 2 + part) * (TC_KB / 4) + kg
+    const int kg = rest % (TC_KB / 4);
+    const int part = (rest / (TC_KB / 4)) & 1;
+    const int kb = rest / (2 * (TC_KB / 4));
+    const int k = kb * TC_KB + kg * 4 + e;
+    const long long kc = ((long long)k * c) % n;
+    double sv, cv;
+    sincospi(2.0 * (double)kc / (double)n, &sv, &cv);
+    const double v = cv + sv;
+    const uint32_t h = tf32_bits((float)v);
+    img[i] = part == 0 ? h : tf32_bits((float)(v - (double)__uint_as_float(h)));
+  }
+}
+
+}  // namespace direct
+
 // pre-split cos / sin image: per stage js (K rows k = 16 js .. 16 js + 15),
 // the parts cos_hi, cos_lo, sin_hi, sin_lo, each [K-group][c][4 floats],
 // c < n / 2, element (c, k) = cos or sin of 2 pi (k c mod n) / n from FP64
@@ -378,6 +565,16 @@ bool encode_xmap(CUtensorMap* m, const float* X, int M, int n) {
 }
 
 template <int N>
+bool launch_direct(const float* X, const direct::DArgs& g, cudaStream_t s) {
+  CUtensorMap m;
+  if (!encode_xmap(&m, X, g.M, N)) return false;
+  const int ntiles = (g.M + TC_M - 1) / TC_M;
+  const int grid = ntiles < sm_count() ? ntiles : sm_count();
+  direct::k_gemm_tc_direct<N><<<grid, direct::D_THREADS, direct::DCfg<N>::SMEM, s>>>(g, m);
+  return true;
+}
+
+template <int N>
 bool launch_tc(const float* X, const TcArgs& g, cudaStream_t s) {
   CUtensorMap m;
   if (!encode_xmap(&m, X, g.M, N)) return false;
@@ -391,40 +588,54 @@ bool launch_tc(const float* X, const TcArgs& g, cudaStream_t s) {
 
 bool tc_supported(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
 
-size_t tc_h_image_bytes(int n) { return tc_supported(n) ? (size_t)n * n * sizeof(float) : 0; }
+// image bytes: the even/odd cos / sin image at 256 (4 n^2), the direct H
+// image below (8 n^2)
+size_t tc_h_image_bytes(int n) {
+  if (!tc_supported(n)) return 0;
+  return (size_t)(n == 256 ? 1 : 2) * n * n * sizeof(float);
+}
 
 void tc_pack_hartley(int n, unsigned char* img, cudaStream_t s) {
   if (!tc_supported(n)) return;
-  const int total = n * n;
-  k_pack_hartley<<<(total + 255) / 256, 256, 0, s>>>(n, reinterpret_cast<uint32_t*>(img));
+  if (n == 256) {
+    k_pack_hartley<<<(n * n + 255) / 256, 256, 0, s>>>(n, reinterpret_cast<uint32_t*>(img));
+  } else {
+    direct::k_pack_direct<<<(2 * n * n + 255) / 256, 256, 0, s>>>(n, reinterpret_cast<uint32_t*>(img));
+  }
 }
 
 // out = (X H)^T for each of the `planes` n x n planes of X (rows of n
 // contiguous values), n = 32, 64, 128 or 256, H the n-point Hartley matrix
-// given by its pre-split cos / sin image (tc_pack_hartley); X, out 16-byte
-// aligned, out distinct from X. error: device flag that receives
-// ERR_TIMEOUT if a bounded wait runs out. Returns false (nothing launched)
-// for other n or when the tensor map cannot be encoded.
+// given by its pre-split image (tc_pack_hartley): the even/odd form at 256,
+// the direct form below; X, out 16-byte aligned, out distinct from X. error:
+// device flag that receives ERR_TIMEOUT if a bounded wait runs out. Returns
+// false (nothing launched) for other n or when the tensor map cannot be
+// encoded.
 bool tc_rows_times_h_t(const float* X, const unsigned char* img, float* out, int planes, int n, int* error,
                        cudaStream_t s) {
   if (planes <= 0) return tc_supported(n);
-  TcArgs g{img, out, planes * n, error};
+  if (n == 256) {
+    TcArgs g{img, out, planes * n, error};
+    return launch_tc<256>(X, g, s);
+  }
+  direct::DArgs d{img, out, planes * n, error};
   switch (n) {
-    case 32: return launch_tc<32>(X, g, s);
-    case 64: return launch_tc<64>(X, g, s);
-    case 128: return launch_tc<128>(X, g, s);
-    case 256: return launch_tc<256>(X, g, s);
+    case 32: return launch_direct<32>(X, d, s);
+    case 64: return launch_direct<64>(X, d, s);
+    case 128: return launch_direct<128>(X, d, s);
     default: return false;
   }
 }
 
 void tc_gemm_set_attributes() {
-  cudaFuncSetAttribute(k_gemm_tc_tf32x3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<32>::SMEM);
-  cudaFuncSetAttribute(k_gemm_tc_tf32x3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcCfg<64>::SMEM);
-  cudaFuncSetAttribute(k_gemm_tc_tf32x3<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TcCfg<128>::SMEM);
   cudaFuncSetAttribute(k_gemm_tc_tf32x3<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)TcCfg<256>::SMEM);
+  cudaFuncSetAttribute(direct::k_gemm_tc_direct<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)direct::DCfg<32>::SMEM);
+  cudaFuncSetAttribute(direct::k_gemm_tc_direct<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)direct::DCfg<64>::SMEM);
+  cudaFuncSetAttribute(direct::k_gemm_tc_direct<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)direct::DCfg<128>::SMEM);
 }
 
 }  // namespace ibm
