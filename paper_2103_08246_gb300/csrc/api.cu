@@ -347,7 +347,7 @@ struct ibm_state {
   int kernels_per_step = 0;
   float* hy = nullptr;                    // Hartley matrices (mixed precision)
   float* hz = nullptr;
-  unsigned char* hy_img = nullptr;        // pre-split cos / sin images for the tensor cores (square planes)
+  unsigned char* hy_img = nullptr;        // pre-split tensor-core images of them (square planes)
   unsigned char* hz_img = nullptr;
   cudaStream_t side = nullptr;            // structural update, overlapped in the graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
