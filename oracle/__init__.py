@@ -29,9 +29,11 @@ to check by eye rather than for speed:
 
 Every function states the passage it follows. Parity of each function is
 pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``, with one
-exception: parity unpinned for the AB2 weights and the pressure update
-p += phi - (nu dt / 2) L_h phi inside ``solver.OracleSolver.step`` -- no
-closed-form solution on this inflow/outflow domain exercises them; they are
-covered only by the solver-level invariants (symmetries, mass
-compatibility, uniform flow) and are stated readings.
+exception: parity unpinned for the correction term -(nu dt / 2) L_h phi of
+the pressure update inside ``solver.OracleSolver.step`` -- omitting it
+changes the pressure by less than the temporal-order test resolves at these
+viscosities, and no closed-form solution on this inflow/outflow domain
+isolates it; it is a stated reading. The AB2 weights and the half-step time
+level of the pressure are pinned by the temporal order of the step
+(``tests/test_oracle_time_order.py``).
 """

@@ -20,9 +20,11 @@ immersed-boundary forcing, then the Poisson equation and the projection.
   A8  L_h phi = D (mean(phi) = 0)
   A9  u^{n+1} = u** - dt G phi;  p^{n+1} = p^n + phi - (nu dt / 2) L_h phi
 
-Parity unpinned: the AB2 weights (A0) and the pressure update of A9 are
-checked only through solver-level invariants (mirror symmetries, mass
-compatibility, preserved uniform flow), not against a closed form.
+The AB2 weights (A0) are pinned by the step's second-order temporal
+convergence on a non-uniform step sequence, and the pressure by its
+second-order convergence at the half step. Parity unpinned: the correction
+term -(nu dt / 2) L_h phi of the pressure update (A9), which that test does
+not resolve; it is checked only through solver-level invariants.
 
 Readings (the paper does not state them): nu = 1 / Re with U = L = 1;
 fluid density 1; the initial state is u = U plus the given perturbation,
