@@ -378,7 +378,6 @@ def e2e_rate(wl, precision, steps):
     reports the host link's copy bandwidth and the state transfer time it
     implies; the caller adds the rate these allow, K / (K x device step time +
     transfer time)."""
-    import numpy as np
     import torch
     from paper_2103_08246_gb300 import binding, inputs
     s = binding.Solver(wl, precision, noise=inputs.initial_noise(wl))
@@ -423,7 +422,7 @@ def ensemble_rate(steps):
     """The 16-case ensemble (uneven grids, mixed precision, tuned tiles):
     aggregate cell updates per second stepped together and one by one."""
     import torch
-    from paper_2103_08246_gb300 import binding, ensemble
+    from paper_2103_08246_gb300 import ensemble
     solvers, ens = ensemble.build()
     ens.step(3)
     torch.cuda.synchronize()

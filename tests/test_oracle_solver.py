@@ -14,7 +14,6 @@ conditions).
 import math
 
 import numpy as np
-import pytest
 
 from oracle import mac
 from oracle.solver import OracleSolver
