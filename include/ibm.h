@@ -446,6 +446,17 @@ int ibm_gen_load(ibm_gen* g, const char* path);
 int ibm_gen_sync(ibm_gen* g);
 void ibm_gen_destroy(ibm_gen* g);
 
+/* Self-test of the bounded device-side waits that every kernel waiting on
+ * bulk copies or tensor-core work uses (see IBM_ETIMEOUT): one thread waits
+ * on an mbarrier that nothing completes, for at most `spins` try-wait rounds
+ * (1 .. 2^24), records the time-out in a device flag the way the solver's
+ * kernels do, and returns. Result: IBM_ETIMEOUT when the wait ran out (the
+ * expected outcome; the CUDA context stays usable), IBM_EINVAL for `spins`
+ * outside the range (checked before any CUDA call), IBM_ECUDA if a runtime
+ * call fails. Uses the current device and its default stream; synchronises;
+ * allocates and frees 4 bytes of device memory. */
+int ibm_check_bounded_wait(unsigned int spins);
+
 /* Release the state (and the workspace if the library allocated it). */
 void ibm_destroy(ibm_state* s);
 

@@ -31,7 +31,7 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_gen_create", "ibm_gen_param_count", "ibm_gen_set_params", "ibm_gen_get_params",
            "ibm_gen_get_grads", "ibm_gen_set_norm", "ibm_gen_forward", "ibm_gen_grad", "ibm_gen_adam_step",
            "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_relax", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_emit", "ibm_gen_history", "ibm_gen_save", "ibm_gen_load", "ibm_gen_sync",
-           "ibm_gen_destroy", "ibm_destroy", "ibm_strerror")
+           "ibm_gen_destroy", "ibm_check_bounded_wait", "ibm_destroy", "ibm_strerror")
 _VOID = ("ibm_destroy", "ibm_ensemble_destroy", "ibm_gen_destroy")
 
 STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH):
                                ctypes.POINTER(vp)]
     lib.ibm_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.ibm_sync.argtypes = [vp]
+    lib.ibm_check_bounded_wait.argtypes = [ctypes.c_uint]
     lib.ibm_flag_state.argtypes = [vp, _dp, _dp, _dp, sz]
     lib.ibm_stats.argtypes = [vp, ctypes.POINTER(ibm_stats_t)]
     lib.ibm_stats_static.argtypes = [vp, ctypes.POINTER(ibm_stats_t)]
@@ -220,6 +221,11 @@ def ibm_step(state, dt, nsteps):
 
 def ibm_sync(state):
     _check(load().ibm_sync(state), "ibm_sync")
+
+
+def ibm_check_bounded_wait(spins):
+    """Status of the bounded-wait self-test (IBM_ETIMEOUT expected)."""
+    return load().ibm_check_bounded_wait(int(spins))
 
 
 def ibm_flag_state(state, X, V=None, F=None):

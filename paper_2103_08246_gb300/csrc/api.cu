@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/ibm.h"
+#include "async_copy.cuh"
 #include "solver.h"
 
 using namespace ibm;
@@ -874,9 +875,47 @@ __global__ void k_probe(const int* __restrict__ ijk, int n, int ny, int nz, cons
   out[3 * q + 2] = (T)0.5 * (w[c] + w[(size_t)i * P + (size_t)j * nz + kp]);
 }
 
+// bounded wait on an mbarrier that nothing completes: at most `spins`
+// try-wait rounds, then the time-out goes to the flag as in the solver's kernels
+__global__ void k_wait_selftest(uint32_t spins, int* flag) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool done = false;
+    for (uint32_t it = 0; it < spins && !done; ++it) done = mbar_try_wait(&bar, 0);
+    if (!done) atomicOr(flag, ERR_TIMEOUT);
+  }
+}
+
 }  // namespace
 
 extern "C" {
+
+int ibm_check_bounded_wait(unsigned int spins) {
+  if (spins < 1 || spins > (1u << 24)) return IBM_EINVAL;
+  int* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return IBM_ECUDA;
+  }
+  int h = 0;
+  cudaError_t e = cudaMemset(flag, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32>>>(spins, flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(flag);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return IBM_ECUDA;
+  }
+  return (h & ERR_TIMEOUT) ? IBM_ETIMEOUT : IBM_OK;
+}
 
 const char* ibm_strerror(int code) {
   switch (code) {

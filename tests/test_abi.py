@@ -68,3 +68,9 @@ def test_create_rejects_null_output_without_gpu(lib):
     g, d, b = binding.structs_from_workload(inputs.TINY)
     rc = lib.ibm_create(ctypes.byref(g), ctypes.byref(d), 100.0, ctypes.byref(b), None, None, 0, None)
     assert rc == binding.IBM_EINVAL
+
+
+def test_bounded_wait_selftest_checks_its_argument(lib):
+    # refused before any CUDA call, so this runs without a GPU
+    assert lib.ibm_check_bounded_wait(0) == -1
+    assert lib.ibm_check_bounded_wait((1 << 24) + 1) == -1
