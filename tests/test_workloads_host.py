@@ -57,3 +57,15 @@ def test_reference_workloads_are_accepted(lib):
     field = (inputs.PRODUCTION.nx + 1) * inputs.PRODUCTION.ny * inputs.PRODUCTION.nz * 4
     assert 16 * field < prod < 19 * field, prod / field
     assert _bytes(inputs.PRODUCTION, binding.IBM_FP64) > 1.8 * prod
+
+
+def test_deterministic_forcing_costs_24_bytes_per_cell(lib):
+    # three 64-bit fixed-point accumulators per velocity node
+    from paper_2103_08246_gb300 import binding
+    wl = inputs.small(64, 32, 32, bars_on=True, bar_x=1.0)
+    g, d, b = binding.structs_from_workload(wl)
+    plain = binding.ibm_options(binding.IBM_FP32, 0.3, 2.0)
+    det = binding.ibm_options(binding.IBM_FP32, 0.3, 2.0)
+    det.deterministic = 1
+    extra = binding.ibm_workspace_bytes(g, d, b, det) - binding.ibm_workspace_bytes(g, d, b, plain)
+    assert extra == 24 * (wl.nx + 1) * wl.ny * wl.nz
