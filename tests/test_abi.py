@@ -74,3 +74,11 @@ def test_bounded_wait_selftest_checks_its_argument(lib):
     # refused before any CUDA call, so this runs without a GPU
     assert lib.ibm_check_bounded_wait(0) == -1
     assert lib.ibm_check_bounded_wait((1 << 24) + 1) == -1
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    # no fallback: without the built library the binding refuses to work
+    from paper_2103_08246_gb300 import binding
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.load(str(tmp_path / "absent.so"))
