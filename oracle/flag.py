@@ -46,6 +46,8 @@ import torch
 
 
 def vid(a, b, nt):
+    """Vertex index of lattice point (a, b) (a along the chord from the hinged
+    leading edge, b along the span), nt vertices per spanwise row (Sec. II.A)."""
     return a * nt + b
 
 
@@ -132,6 +134,8 @@ class FlagMesh:
         return X.reshape(-1, 3)
 
     def rest_lengths(self, X0):
+        """Spring rest lengths l0 = |X_b - X_a| in the flat reference state X0
+        (the stretching springs of Sec. II.A hold the sheet near inextensible)."""
         d = X0[self.springs[:, 1]] - X0[self.springs[:, 0]]
         return np.sqrt((d * d).sum(axis=1))
 
@@ -147,6 +151,9 @@ class FlagMesh:
         return math.sqrt(float(np.max(w2[self.free])))
 
     def substeps(self, dt):
+        """Velocity-Verlet sub-steps per fluid step (Sec. II.B: the structure
+        advances in smaller steps): ceil(dt omega_max / 1.8), so every mode
+        runs at dt_s omega <= 1.8 below the stability limit 2."""
         return max(1, int(math.ceil(dt * self.omega_max() / 1.8)))
 
 

@@ -53,10 +53,13 @@ def bf16_round(a):
 
 
 def phi(s):
+    """Activation of the generator (a stated reading of the synthetic-inflow
+    perspective of Sec. V): s for s > 0, s / 8 otherwise."""
     return np.where(s > 0, s, s / 8.0)
 
 
 def dphi(s):
+    """Derivative of ``phi``: 1 for s > 0, 1 / 8 otherwise (1 / 8 at 0)."""
     return np.where(s > 0, 1.0, 1.0 / 8.0)
 
 
@@ -94,6 +97,8 @@ def conv_weight_grad(G, X):
 
 
 def flatten(p):
+    """Parameter dict -> flat vector in the interface order W_in, b_in,
+    (W_l, b_l) per block, W_out, b_out, every W in [dy][dz][o][c] order."""
     parts = [p["W_in"].ravel(), p["b_in"]]
     for W, b in zip(p["W"], p["b"]):
         parts += [W.ravel(), b]
@@ -102,6 +107,8 @@ def flatten(p):
 
 
 def unflatten(v, width, blocks, in_channels):
+    """Flat vector in the interface order -> parameter dict (inverse of
+    ``flatten``)."""
     v = np.asarray(v, dtype=np.float64)
     o = 0
 

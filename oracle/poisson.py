@@ -31,6 +31,9 @@ def dft_matrix(n, sign=-1):
 
 
 def eigenvalues(n, h):
+    """Eigenvalues (2 cos(2 pi m / n) - 2) / h^2, m = 0 .. n-1, of the periodic
+    second difference that the transverse transforms diagonalise (Sec. II.B:
+    transforms in the periodic directions, Sec. II.A: periodic y and z)."""
     m = np.arange(n)
     return (2.0 * np.cos(2.0 * np.pi * m / n) - 2.0) / (h * h)
 

@@ -48,6 +48,10 @@ from . import af, flag, ib, mac, poisson
 
 
 class OracleSolver:
+    """The full time step of Sec. II.B in FP64 (steps A0-A9 of the module
+    header) on the domain of Sec. II.A, with the bar grid and the flag;
+    state: u, v, w, p, the flag's X, V, and the AB2 history."""
+
     U_IN = 1.0
 
     def __init__(self, wl, noise=None):
@@ -114,6 +118,8 @@ class OracleSolver:
         self.w -= dt * gw
 
     def markers(self):
+        """Lagrangian points forced this step: flag vertices then bar markers
+        (Sec. II.B: both bodies are immersed boundaries)."""
         if self.nf:
             return np.concatenate([self.X, self.Xb], axis=0)
         return self.Xb
@@ -123,12 +129,14 @@ class OracleSolver:
         self.pending_inflow = tuple(np.array(a, dtype=np.float64) for a in (u_in, v_in, w_in))
 
     def next_dt(self):
+        """A0: the fixed step, or CFL h / max over cells of (|u|+|v|+|w|)."""
         if self.wl.dt > 0:
             return self.wl.dt
         return self.wl.cfl * self.h / mac.cfl_speed(self.u, self.v, self.w)
 
     # ------------------------------------------------------------------ step
     def step(self, dt=None):
+        """One time step A0-A9 (Sec. II.B order); returns the step size."""
         wl, h, nu = self.wl, self.h, self.nu
         nx = wl.nx
         u, v, w = self.u, self.v, self.w
@@ -209,8 +217,10 @@ class OracleSolver:
         return dt
 
     def run(self, nsteps, dt=None):
+        """nsteps calls of ``step``."""
         for _ in range(nsteps):
             self.step(dt)
 
     def fields(self):
+        """(u, v, w, p) in the array conventions of ``oracle.mac``."""
         return self.u, self.v, self.w, self.p
