@@ -28,12 +28,10 @@ to check by eye rather than for speed:
                rollout renormalisation.
 
 Every function states the passage it follows. Parity of each function is
-pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``, with one
-exception: parity unpinned for the correction term -(nu dt / 2) L_h phi of
-the pressure update inside ``solver.OracleSolver.step`` -- omitting it
-changes the pressure by less than the temporal-order test resolves at these
-viscosities, and no closed-form solution on this inflow/outflow domain
-isolates it; it is a stated reading. The AB2 weights and the half-step time
-level of the pressure are pinned by the temporal order of the step
-(``tests/test_oracle_time_order.py``).
+pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``. The AB2
+weights and the half-step time level of the pressure are pinned by the
+temporal order of the step (``tests/test_oracle_time_order.py``); the
+pressure update, with its correction term -(nu dt / 2) L_h phi, by the
+Crank--Nicolson momentum balance that one step must satisfy at every
+interior node (``tests/test_oracle_pressure_update.py``).
 """

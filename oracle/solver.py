@@ -22,9 +22,11 @@ immersed-boundary forcing, then the Poisson equation and the projection.
 
 The AB2 weights (A0) are pinned by the step's second-order temporal
 convergence on a non-uniform step sequence, and the pressure by its
-second-order convergence at the half step. Parity unpinned: the correction
-term -(nu dt / 2) L_h phi of the pressure update (A9), which that test does
-not resolve; it is checked only through solver-level invariants.
+second-order convergence at the half step. The pressure update of A9,
+including its correction term -(nu dt / 2) L_h phi, is pinned by the
+momentum balance the three sub-steps must reproduce: away from the x
+boundaries, (u1 - u0)/dt + N* - (nu/2) L (u1 + u0) + G p1 equals minus the
+factorisation's splitting term, to round-off, only with that term present.
 
 Readings (the paper does not state them): nu = 1 / Re with U = L = 1;
 fluid density 1; the initial state is u = U plus the given perturbation,
