@@ -7,14 +7,18 @@ Poisson solve, projection) of the production workload: 512 x 256 x 256
 cells, domain 8 x 4 x 4, Re = 200, bar grid (mesh 0.5, width 0.1) at x = 0.5,
 65 x 65 flag hinged at x = 3, CFL 0.3, seeded synthetic initial noise.
 
-Output: one JSON line (rank 0). `value` is steps/s of the headline path
-(FP32 fields, FP64 flag and sums) summed over all ranks; each rank runs an
-independent replica (the path is not sharded). The FP64 path, the per-stage
-roofline of the dominant kernel, the end-to-end rate through the C ABI with
-host buffers, and the CPU oracle on a bounded sample are reported beside it.
+Output: one JSON line (rank 0). `value` is steps/s of the mixed-precision
+path (FP32 fields; Poisson transforms as split-TF32 tensor-core GEMMs with a
+refinement sweep on a double-single residual; FP64 flag and global sums)
+summed over all ranks; each rank runs an independent replica (the path is
+not sharded). Beside it: the FP64 path (the other half of the metric's
+pair) and the FP32 path, each with its own clock record; the roofline of
+every kernel of the step and of the dominant one; the end-to-end rate
+through the C ABI with host buffers; the CPU oracle on one core and on all
+host cores (bounded samples).
 
 --impl reference times the CPU oracle (the reference arm of this repository)
-on the same metric.
+on the same metric, on all host cores.
 """
 from __future__ import annotations
 
@@ -38,17 +42,25 @@ FALLBACK_BF16_TFLOPS = 1900.0
 # Algorithmic bytes per launch of each kernel of the step, in units of one
 # scalar field (one read or one write of every cell): the inputs it must read
 # and the outputs it must write, with perfect on-chip reuse inside the kernel.
+# Velocity-grid kernels count (nx + 1) ny nz cells, pressure-grid kernels
+# (transforms, x solves, residual) nx ny nz.
 FIELD_PASSES = {
     "rhs": 13, "af_x": 6, "af_yz": 9, "mass_div": 4,
-    "dht2d": 2, "poisson_x": 3, "project": 9,
+    "dht2d": 2, "poisson_x": 3, "project": 9, "tc_pass": 2, "residual": 3,
 }
+PRESSURE_GRID = ("dht2d", "poisson_x", "tc_pass", "residual")
 # launches of each stage per step
-PER_STEP = {"rhs": 1, "af_x": 1, "af_yz": 1, "mass_div": 1, "dht2d": 2,
-            "poisson_x": 1, "project": 1, "ib": 1, "flag": 1, "outflow": 1}
+PER_STEP = {
+    "fp32": {"rhs": 1, "outflow": 1, "af_x": 1, "af_yz": 1, "ib": 1, "flag": 1, "mass_div": 1,
+             "dht2d": 2, "poisson_x": 1, "project": 1},
+    "mixed": {"rhs": 1, "outflow": 1, "af_x": 1, "af_yz": 1, "ib": 1, "flag": 1, "mass_div": 1,
+              "tc_pass": 8, "poisson_x": 2, "residual": 1, "project": 1},
+}
 # The method's unfused field passes per step (explicit stage 13, three
 # implicit factors 21, mass fix and divergence 4, pressure solve 10,
 # projection 9): the step's roofline counts these bytes whatever the fusion.
-METHOD_PASSES = 57
+# The mixed path adds its refinement: the residual (3) and a second solve (10).
+METHOD_PASSES = {"fp32": 57, "mixed": 70}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # production FP32 kernels, from one single-pass ncu capture at full size
 # (profiles/dram_traffic_production_fp32.md); valid for the kernels of that
@@ -64,6 +76,7 @@ FP64_RHS_INST_PER_CELL = 86.2
 GEN_CONV_TRAFFIC_BYTES = 757.4e6
 FP64_INST_PER_CLK_SM = 2
 N_SMS = 152
+CLOCK_WINDOW_S = 0.6   # each leg's clock record spans at least this long
 SAMPLE_NX = 64   # x planes of the CPU sample (the inflow end of the workload)
 
 
@@ -74,7 +87,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64, FP32, ensemble and generator legs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="only run this many FP32 production steps (for ncu) and exit")
@@ -241,12 +255,26 @@ def max_over_ranks(pg, x):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample_rate(steps: int, warmup: int, nx: int = SAMPLE_NX):
-    """Time the CPU oracle (single thread) on the first `nx` x-planes of the
-    production workload (same spacing and transverse size; the bar grid when
-    the sample reaches it; the flag lies further downstream and is left out).
-    Runs in a fresh interpreter so that BLAS is pinned to one thread.
-    Returns (cell-updates/s, seconds per sample step, description)."""
+def cpu_model():
+    """The host CPU's model name (lscpu / /proc/cpuinfo), or 'unknown'."""
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                             timeout=10).stdout.decode()
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _sample_code(steps, warmup, nx):
     from paper_2103_08246_gb300 import inputs
     h = inputs.PRODUCTION.lx / inputs.PRODUCTION.nx
     lx = nx * h
@@ -267,30 +295,56 @@ for _ in range({steps}):
 dt = (time.perf_counter() - t0) / {steps}
 print(json.dumps({{"sec_per_step": dt, "cells": wl.cells}}))
 """
+    desc = (f"oracle (numpy/scipy FP64, 1 thread per process) on the first {nx} of 512 x-planes "
+            f"({nx}x256x256, {'bars' if bars else 'inflow region only'}, no flag), "
+            f"{steps} step(s) after {warmup} warm-up; scaled to the full workload by cell count")
+    return code, desc
+
+
+def oracle_sample_rate(steps: int, warmup: int, nx: int = SAMPLE_NX, procs: int = 1):
+    """Time the CPU oracle on the first `nx` x-planes of the production
+    workload (same spacing and transverse size; the bar grid when the sample
+    reaches it; the flag lies further downstream and is left out), in `procs`
+    independent single-threaded processes at once (one per host core for the
+    all-cores figure). Returns (aggregate cell-updates/s, mean seconds per
+    sample step, description)."""
+    code, desc = _sample_code(steps, warmup, nx)
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    out = subprocess.run([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
-                         stderr=subprocess.PIPE, timeout=3600)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr.decode()[-2000:])
-    r = json.loads(out.stdout.decode().strip().splitlines()[-1])
-    desc = (f"oracle (numpy/scipy FP64, 1 thread) on the first {nx} of 512 x-planes "
-            f"({nx}x256x256, {'bars' if bars else 'inflow region only'}, no flag), "
-            f"{steps} step(s) after {warmup} warm-up; scaled to the full workload by cell count")
-    return r["cells"] / r["sec_per_step"], r["sec_per_step"], desc
+    ps = [subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                           stderr=subprocess.PIPE) for _ in range(procs)]
+    rate, secs = 0.0, []
+    for p in ps:
+        out, err = p.communicate(timeout=3600)
+        if p.returncode != 0:
+            raise RuntimeError(err.decode()[-2000:])
+        r = json.loads(out.decode().strip().splitlines()[-1])
+        rate += r["cells"] / r["sec_per_step"]
+        secs.append(r["sec_per_step"])
+    if procs > 1:
+        desc += f"; {procs} such processes at once (one per host core), rates summed"
+    return rate, sum(secs) / len(secs), desc
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def run_reference(args):
     from paper_2103_08246_gb300 import inputs
     wl = inputs.PRODUCTION
-    # size each step's sample so that warm-up + timed steps take about two minutes
+    cores = host_cores()
+    # size each process's sample so that warm-up + timed steps take about two minutes
     _, sec16, _ = oracle_sample_rate(1, 0, 16)
     per_plane = sec16 / 16
     budget = 120.0 / max(1, args.steps + args.warmup)
-    nx = int(max(8, min(SAMPLE_NX, budget / per_plane)))
-    rate, sec, desc = oracle_sample_rate(max(1, args.steps), max(0, args.warmup), nx)
+    nx = int(max(8, min(SAMPLE_NX, budget / per_plane / 2)))
+    rate, sec, desc = oracle_sample_rate(max(1, args.steps), max(0, args.warmup), nx, procs=cores)
     steps_per_s = rate / wl.cells
     line = {
         "impl": "reference", "metric": METRIC, "value": steps_per_s, "unit": "steps/s",
@@ -300,8 +354,8 @@ def run_reference(args):
         "gcell_updates_per_s": rate / 1e9,
         "config": {"workload": wl.name, "cells": wl.cells, "precision": "fp64",
                    "cache": "inputs larger than L2"},
-        "cpu_baseline": {"value": steps_per_s, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                         "sample": desc},
+        "cpu_baseline": {"value": steps_per_s, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                         "sample": desc, "cpu_model": cpu_model()},
         "e2e": {"value": steps_per_s, "unit": "steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -320,28 +374,96 @@ def time_steps(solver, steps, stream):
     return e0.elapsed_time(e1) / steps
 
 
+def timed_leg(solver, steps, gpu_index, pg=None):
+    """ms per step of `steps` steps (CUDA events on the solver's stream,
+    bracketed by a barrier and a synchronize), with the SM clocks sampled
+    from just before the timed region until at least CLOCK_WINDOW_S later: a
+    short timed region is followed by more identical (untimed) steps inside
+    the sampling window, so that the record holds several samples."""
+    import torch
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    t0 = time.perf_counter()
+    ms = time_steps(solver, steps, solver.stream)
+    while time.perf_counter() - t0 < CLOCK_WINDOW_S:
+        solver.step(max(1, steps))
+        torch.cuda.synchronize()
+    clk = clocks.stop()
+    clk["window_s"] = time.perf_counter() - t0
+    barrier(pg)
+    return ms, clk
+
+
+def ib_algorithmic_bytes(solver, elem):
+    """Bytes the IB stage must move per step: every velocity node in the
+    support of any marker read once for the interpolation and read and
+    written once by the spreading (per component), plus the marker data
+    (positions read by both passes, the FP64 forcing amplitude written and
+    read, the flag's target velocity and force)."""
+    import numpy as np
+    wl = solver.wl
+    h = wl.lx / wl.nx
+    X = solver.markers()
+    nodes = 0
+    for comp in range(3):
+        off = [0.0 if d == comp else 0.5 for d in range(3)]
+        base = [np.floor(X[:, d] / h - off[d] - 0.5).astype(np.int64) for d in range(3)]
+        lo = 1 if comp == 0 else 0
+        keys = []
+        for a in range(3):
+            i = base[0] + a
+            ok = (i >= lo) & (i <= wl.nx - 1)
+            for b in range(3):
+                j = np.mod(base[1] + b, wl.ny)
+                for e in range(3):
+                    k = np.mod(base[2] + e, wl.nz)
+                    keys.append(((i * wl.ny + j) * wl.nz + k)[ok])
+        nodes += np.unique(np.concatenate(keys)).size
+    nm = X.shape[0]
+    return nodes * 3 * elem + nm * (2 * 24 + 2 * 24) + solver.nf * 48, nodes
+
+
 def stage_roofline(wl, precision, peak_gbs, peak_kind):
-    """Per-stage device times on a timing-only state; roofline of the dominant kernel."""
+    """Per-kernel device times on a timing-only state; roofline of every
+    streamed kernel and of the IB stage, and the dominant kernel (the most
+    time per step)."""
     from paper_2103_08246_gb300 import binding, inputs
+    key = "mixed" if precision == binding.IBM_MIXED else "fp32"
     t = binding.Solver(wl, precision, noise=inputs.initial_noise(wl))
     t.step(2)
-    elem = 4 if precision == binding.IBM_FP32 else 8
-    cells = (wl.nx + 1) * wl.ny * wl.nz
+    elem = 4
+    cells = {"velocity": (wl.nx + 1) * wl.ny * wl.nz, "pressure": wl.nx * wl.ny * wl.nz}
     stages = {}
-    for name in ("rhs", "outflow", "af_x", "af_yz", "ib", "flag", "mass_div", "dht2d",
-                 "poisson_x", "project"):
+    for name in PER_STEP[key]:
         t.time_stage(name, 2)
         stages[name] = t.time_stage(name, 10)
+    t.time_stage("poisson", 2)
+    stages["poisson"] = t.time_stage("poisson", 10)
+    ib_bytes, ib_nodes = ib_algorithmic_bytes(t, elem)
     t.close()
-    per_step = {k: v * PER_STEP[k] for k, v in stages.items()}
-    dom = max((k for k in stages if k in FIELD_PASSES), key=lambda k: per_step[k])
-    alg_bytes = FIELD_PASSES[dom] * cells * elem
-    achieved = alg_bytes / (stages[dom] * 1e-3) / 1e9
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak_gbs,
-            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak_gbs,
-            "traffic": (TRAFFIC_BYTES.get(dom) if precision == binding.IBM_FP32 else None),
-            "alg_bytes_per_launch": alg_bytes, "ms_per_launch": stages[dom]}
-    return roof, stages
+    per_step = {k: stages[k] * PER_STEP[key][k] for k in PER_STEP[key]}
+    kernels = {}
+    for k in PER_STEP[key]:
+        if k in FIELD_PASSES:
+            n = cells["pressure" if k in PRESSURE_GRID else "velocity"]
+            nbytes = FIELD_PASSES[k] * n * elem
+        elif k == "ib":
+            nbytes = ib_bytes
+        else:
+            continue
+        gbs = nbytes / (stages[k] * 1e-3) / 1e9
+        kernels[k] = {"ms_per_launch": stages[k], "launches_per_step": PER_STEP[key][k],
+                      "alg_bytes_per_launch": nbytes, "achieved_gbs": gbs, "frac": gbs / peak_gbs,
+                      "traffic": TRAFFIC_BYTES.get(k) if key == "fp32" else None}
+    kernels["ib"]["nodes_touched"] = ib_nodes
+    dom = max((k for k in kernels if k != "ib"), key=lambda k: per_step[k])
+    d = kernels[dom]
+    roof = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peak_gbs,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": d["frac"], "traffic": d["traffic"],
+            "alg_bytes_per_launch": d["alg_bytes_per_launch"], "ms_per_launch": d["ms_per_launch"]}
+    return roof, stages, kernels
 
 
 def host_link_gbs(nbytes=256 << 20, reps=5):
@@ -508,6 +630,16 @@ def generator_rate(bf16_peak, peak_kind, nrep=10):
             "wgrad_tflops": tf(conv_flops, ms_wgrad), "dgrad_tflops": tf(conv_flops, ms_dgrad)}
 
 
+def _with_clocks(gpu_index, fn, *a, **kw):
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    out = fn(*a, **kw)
+    clk = clocks.stop()
+    if isinstance(out, dict):
+        out["clocks"] = clk
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2103_08246_gb300 import binding, build, inputs
@@ -519,87 +651,84 @@ def run_ours(args):
     build.build()
     binding.load()
     wl = inputs.PRODUCTION
-    prec = binding.IBM_FP32
+    prec = binding.IBM_MIXED
     solver = binding.Solver(wl, prec, noise=inputs.initial_noise(wl))
     solver.step(max(3, args.warmup))
     torch.cuda.synchronize()
     kernels_per_step = solver.stats()["kernels_per_step"]
-    barrier(pg)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms = time_steps(solver, args.steps, solver.stream)
-    clk = clocks.stop()
-    barrier(pg)
+    ms, clk = timed_leg(solver, args.steps, local, pg)
     ms = max_over_ranks(pg, ms)
     st = solver.stats()
     solver.close()
     peak, peak_kind = measured_peaks()
-    out = None
     if rank == 0:
-        roof, stages = stage_roofline(wl, prec, peak, peak_kind)
-        step_bytes = METHOD_PASSES * \
-            (wl.nx + 1) * wl.ny * wl.nz * 4
-        fp64 = None
+        cells = wl.cells
+        roof, stages, kernels = stage_roofline(wl, prec, peak, peak_kind)
+        step_bytes = METHOD_PASSES["mixed"] * (wl.nx + 1) * wl.ny * wl.nz * 4
+        fp32 = fp64 = ens = gen = None
         if not args.no_fp64:
+            s32 = binding.Solver(wl, binding.IBM_FP32, noise=inputs.initial_noise(wl))
+            s32.step(3)
+            ms32, clk32 = timed_leg(s32, args.steps, local)
+            s32.close()
+            roof32, stages32, kernels32 = stage_roofline(wl, binding.IBM_FP32, peak, peak_kind)
+            fp32 = {"steps_per_s": 1000.0 / ms32, "ms_per_step": ms32,
+                    "gcell_updates_per_s": cells / ms32 / 1e6, "dtype": "f32",
+                    "step_hbm_frac": (METHOD_PASSES["fp32"] * (wl.nx + 1) * wl.ny * wl.nz * 4
+                                      / (ms32 * 1e-3) / 1e9) / peak,
+                    "roofline": roof32, "stages_ms": stages32, "kernels": kernels32, "clocks": clk32}
             s64 = binding.Solver(wl, binding.IBM_FP64, noise=inputs.initial_noise(wl))
             s64.step(3)
-            ms64 = time_steps(s64, max(5, args.steps // 5), s64.stream)
+            ms64, clk64 = timed_leg(s64, max(5, args.steps // 4), local)
             s64.time_stage("rhs", 1)
             rhs64 = s64.time_stage("rhs", 3)
             s64.close()
-            mhz = clk.get("sm_mhz") or 2070.0
+            mhz = clk64.get("sm_mhz") or 2070.0
             peak_inst = FP64_INST_PER_CLK_SM * N_SMS * mhz * 1e6 / 1e9
             ach_inst = FP64_RHS_INST_PER_CELL * (wl.nx + 1) * wl.ny * wl.nz / (rhs64 * 1e-3) / 1e9
             fp64 = {"steps_per_s": 1000.0 / ms64, "ms_per_step": ms64,
-                    "gcell_updates_per_s": wl.cells / ms64 / 1e6,
-                    "speedup_fp32_over_fp64": ms64 / ms,
+                    "gcell_updates_per_s": cells / ms64 / 1e6, "dtype": "f64",
                     "roofline": {"kernel": "rhs", "bound": "alu", "unit": "G FP64 inst/s",
                                  "achieved": ach_inst, "peak": peak_inst,
                                  "peak_kind": "derived: 2 FP64 inst/clk/SM x 152 SMs x sampled clock",
-                                 "frac": ach_inst / peak_inst, "ms_per_launch": rhs64}}
-        mixed = None
-        if not args.no_fp64:
-            sm = binding.Solver(wl, binding.IBM_MIXED, noise=inputs.initial_noise(wl))
-            sm.step(3)
-            msm = time_steps(sm, max(5, args.steps // 5), sm.stream)
-            poisson_mixed = sm.time_stage("poisson", 3)
-            smx = sm.stats()
-            sm.close()
-            mixed = {"steps_per_s": 1000.0 / msm, "ms_per_step": msm,
-                     "gcell_updates_per_s": wl.cells / msm / 1e6,
-                     "speedup_over_fp64": (fp64["ms_per_step"] / msm) if fp64 else None,
-                     "poisson_ms": poisson_mixed, "max_div": smx["max_div"]}
-        ens = None if args.no_fp64 else ensemble_rate(max(5, args.steps // 5))
-        gen = None
-        if not args.no_fp64:
-            gen = generator_rate(*measured_bf16_peak())
+                                 "frac": ach_inst / peak_inst, "ms_per_launch": rhs64},
+                    "clocks": clk64}
+            ens = _with_clocks(local, ensemble_rate, max(5, args.steps // 5))
+            gen = _with_clocks(local, generator_rate, *measured_bf16_peak())
         e2e = None if args.no_e2e else e2e_rate(wl, prec, args.steps)
         if e2e is not None:
             e2e["value"] *= world
             e2e["link_bound"] = world * args.steps / (args.steps * ms + e2e["state_transfer_ms"]) * 1000.0
         cpu = None
         if not args.no_cpu_baseline:
-            rate, sec, desc = oracle_sample_rate(2, 1)
-            cpu = {"value": rate / wl.cells, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                   "sample": desc, "gcell_updates_per_s": rate / 1e9}
+            rate1, _, desc1 = oracle_sample_rate(2, 1)
+            cores = host_cores()
+            rate_n, _, desc_n = oracle_sample_rate(1, 1, procs=cores)
+            cpu = {"value": rate1 / cells, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                   "sample": desc1, "gcell_updates_per_s": rate1 / 1e9, "cpu_model": cpu_model(),
+                   "all_cores": {"value": rate_n / cells, "unit": "steps/s", "cores": cores,
+                                 "sample": desc_n, "gcell_updates_per_s": rate_n / 1e9}}
         value = world * 1000.0 / ms
         out = {
             "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "mixed: f32 fields, split-tf32 tensor-core transforms, double-single residual, f64 flag",
             "data": "synthetic",
-            "config": {"workload": wl.name, "cells": wl.cells, "precision": "fp32 fields, fp64 flag",
+            "config": {"workload": wl.name, "cells": cells,
+                       "precision": "mixed (fp32 fields, tf32x3 tcgen05 transforms + refinement, fp64 flag)",
                        "cfl": wl.cfl, "re": wl.re, "markers": st["n_markers"],
                        "cache": "inputs larger than L2 (each field 134 MB)",
                        "parallelism": f"replicas x{world}"},
-            "gcell_updates_per_s": world * wl.cells / ms / 1e6,
+            "gcell_updates_per_s": world * cells / ms / 1e6,
+            "speedup_over_fp64": (fp64["ms_per_step"] / ms) if fp64 else None,
             "step_hbm_frac": (step_bytes / (ms * 1e-3) / 1e9) / peak,
-            "roofline": roof, "stages_ms": stages, "fp64": fp64, "mixed": mixed,
-            "ensemble": ens, "inflow_generator": gen, "e2e": e2e,
+            "roofline": roof, "stages_ms": stages, "kernels": kernels,
+            "fp64": fp64, "fp32": fp32, "ensemble": ens, "inflow_generator": gen, "e2e": e2e,
             "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": kernels_per_step * args.steps,
             "dt_last": st["dt"], "cfl_last": st["cfl"], "n_sub": st["n_sub"],
+            "max_div": st["max_div"],
         }
         print(json.dumps(out), flush=True)
     barrier(pg)

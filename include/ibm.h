@@ -86,6 +86,12 @@ extern "C" {
                                    (used by the pressure solve when ny = nz =
                                    256; otherwise the solve runs DHT_Y and
                                    DHT_Z and this stage launches nothing)     */
+#define IBM_STAGE_TC_PASS   15  /* one tensor-core transform pass (X H)^T over every
+                                   x plane (IBM_MIXED with square planes of 32,
+                                   64, 128 or 256; otherwise nothing): the
+                                   mixed pressure solve runs eight            */
+#define IBM_STAGE_RESIDUAL  16  /* the double-single residual D - L_h phi of the
+                                   mixed solve's refinement (IBM_MIXED only)  */
 
 /* field selectors for ibm_get_field / ibm_set_field */
 #define IBM_FIELD_U 0

@@ -256,6 +256,7 @@ struct Carver {
 struct Layout {
   int nf = 0, nb = 0, nsp = 0, ntri = 0, nslot = 0, ncsr = 0;
   int nbm[3] = {0, 0, 0};   // Eulerian bar forcing: forced nodes per component
+  int ntile = 0;            // tiles of the binned bar markers
 };
 
 // Eulerian forcing of the bar grid: for every velocity node whose cell
@@ -269,6 +270,7 @@ struct BarMask {
   std::vector<int> idx;
   std::vector<double> alpha;
   int n[3] = {0, 0, 0};
+  std::vector<int> tiles;   // bar markers: tile table of the binned markers
 };
 
 double cell_overlap(double c, double h, double lo, double hi) {
@@ -437,6 +439,10 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   for (int q = 0; q < 3; ++q) m.nbm[q] = L.nbm[q];
   m.bm_idx = cv.take<int>((size_t)L.nbm[0] + L.nbm[1] + L.nbm[2]);
   m.bm_alpha = cv.take<double>((size_t)L.nbm[0] + L.nbm[1] + L.nbm[2]);
+  m.n_tiles = L.ntile;
+  m.tile = cv.take<int>(5 * (size_t)L.ntile);
+  m.bar_w = L.ntile ? (void*)cv.take<T>(18 * (size_t)L.nb) : nullptr;
+  m.bar_o = L.ntile ? cv.take<int>((size_t)L.nb) : nullptr;
   Flag& fl = s->fl;
   fl.nv = L.nf;
   fl.X = cv.take<double>(3 * (size_t)L.nf);
@@ -659,6 +665,8 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
   Markers& m = s->mk;
   m.bar_dv = bar_dv;
   if (m.nb) CK(cudaMemcpyAsync(m.Xb, Xb.data(), Xb.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  if (!bm.tiles.empty())
+    CK(cudaMemcpyAsync(m.tile, bm.tiles.data(), bm.tiles.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   if (!bm.idx.empty()) {
     CK(cudaMemcpyAsync(m.bm_idx, bm.idx.data(), bm.idx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(m.bm_alpha, bm.alpha.data(), bm.alpha.size() * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -692,6 +700,9 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
   p.dt_fixed = -1.0;
   p.cfl = s->cfl;
   CK(cudaMemcpyAsync(f.prm, &p, sizeof(Params), cudaMemcpyHostToDevice, st));
+  ib_set_attributes();
+  launch_ib_setup<T>(c, f, m, st);   // the bar markers' weights and box indices, once
+  CK(cudaGetLastError());
   poisson_set_attributes();
   fluid_set_attributes();
   mixed_set_attributes();
@@ -784,6 +795,8 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   if (b->flag_on) fg = build_flag(*b, *d, c.h);
   if (b->bars_on && s->bar_forcing == 1) build_bar_mask(*b, *d, *g, c.h, bm);
   else if (b->bars_on) build_bars(*b, *d, c.h, Xb, bar_dv);
+  ib_bin_bars(c, Xb, bm.tiles, s->mk);
+  L.ntile = s->mk.n_tiles;
   for (int q = 0; q < 3; ++q) L.nbm[q] = bm.n[q];
   c.omega_max = fg.omega_max;
   L.nf = b->flag_on ? b->flag_ns * b->flag_nt : 0;
@@ -851,6 +864,15 @@ void launch_stage(ibm_state* s, int stage) {
     case IBM_STAGE_POISSON: solve_poisson<T>(s, st); break;
     case IBM_STAGE_AF_YZ: (void)launch_af_yz(c, f, cur, st); break;
     case IBM_STAGE_DHT_2D: (void)launch_dht2d(c, f, st); break;
+    case IBM_STAGE_TC_PASS:
+      if constexpr (std::is_same<T, float>::value)
+        if (s->precision == IBM_MIXED && s->hz_img)
+          (void)tc_rows_times_h_t(f.phi, s->hz_img, f.e[0], c.nx, c.nz, &f.prm->error, st);
+      break;
+    case IBM_STAGE_RESIDUAL:
+      if constexpr (std::is_same<T, float>::value)
+        if (s->precision == IBM_MIXED) launch_residual_mixed(c, f, st);
+      break;
     default: break;
   }
 }
@@ -1061,7 +1083,7 @@ int ibm_stats(ibm_state* s, ibm_stats_t* out) {
 }
 
 int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
-  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_DHT_2D) return IBM_EINVAL;
+  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_RESIDUAL) return IBM_EINVAL;
   cudaStream_t st = s->stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

@@ -62,6 +62,7 @@ __device__ __forceinline__ T pick(double d, float f) {
 constexpr int ERR_AF_RANGE = 1;     // implicit diffusion number outside range
 constexpr int ERR_NONFINITE = 2;    // non-finite CFL speed
 constexpr int ERR_TIMEOUT = 4;      // a bounded device-side wait ran out
+constexpr int ERR_IB_BIN = 8;       // a bar marker outside the tile it was binned to
 
 __host__ __device__ inline size_t plane(const Consts& c) { return (size_t)c.ny * c.nz; }
 __host__ __device__ inline size_t idx3(const Consts& c, int i, int j, int k) {

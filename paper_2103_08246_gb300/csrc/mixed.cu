@@ -317,6 +317,14 @@ void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* 
   k_add<<<nb, 256, 0, s>>>(n, x0, t1, f.phi);
 }
 
+// the refinement's residual alone (stage timing): e[2] = D - L_h e[1]
+void launch_residual_mixed(const Consts& c, const Fields<float>& f, cudaStream_t s) {
+  const double ih2 = c.inv_h * c.inv_h;
+  const float ih2_hi = (float)ih2, ih2_lo = (float)(ih2 - (double)ih2_hi);
+  k_residual_ds4<<<dim3((c.nz / 4 + 63) / 64, c.ny, c.nx), 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, f.phi,
+                                                                     f.e[1], f.e[2]);
+}
+
 void mixed_set_attributes() {
   cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   tc_gemm_set_attributes();

@@ -2,6 +2,8 @@
 // launchers each translation unit provides.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace ibm {
@@ -47,6 +49,13 @@ struct Markers {
   int nbm[3] = {0, 0, 0};
   int* bm_idx = nullptr;
   double* bm_alpha = nullptr;
+  // bar markers binned by tiles of tx x ty x tz cells (Xb sorted by tile):
+  // 5 ints per non-empty tile, its first cell (x, y, z) and bar range [b0, b1)
+  int n_tiles = 0;
+  int tx = 8, ty = 16, tz = 16;
+  int* tile = nullptr;
+  void* bar_w = nullptr;      // per bar marker: 18 kernel weights (field precision), set up once
+  int* bar_o = nullptr;       // per bar marker: packed first box indices of its stencils
 };
 
 struct Flag {
@@ -120,11 +129,17 @@ void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* 
                           const float* Hz, const unsigned char* Hy_img, const unsigned char* Hz_img,
                           cudaStream_t s);
 void mixed_set_attributes();
+void launch_residual_mixed(const Consts& c, const Fields<float>& f, cudaStream_t s);
 void hartley_matrix(int n, float* host);
 
 // ---- ib.cu
 template <class T> void launch_ib(const Consts& c, const Fields<T>& f, const Markers& m,
                                   const Flag& fl, int cur, cudaStream_t s);
+void ib_set_attributes();
+template <class T> void launch_ib_setup(const Consts& c, const Fields<T>& f, const Markers& m, cudaStream_t s);
+// bin the bar markers (3 doubles each, sorted in place) into tiles; fills
+// the tile table (5 ints per tile) and the tile shape of m
+void ib_bin_bars(const Consts& c, std::vector<double>& Xb, std::vector<int>& tiles, Markers& m);
 
 // ---- flag.cu
 void launch_flag(Params* prm, const Flag& fl, bool force, cudaStream_t s);

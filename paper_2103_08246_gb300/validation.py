@@ -9,6 +9,11 @@ The comparison data of the appendix (an earlier three-dimensional flag study)
 are not available here, so the run reports its own numbers and their
 grid dependence: the flapping period at h = 1/32 against h = 1/64 (the
 appendix states that its period and the reference one differ by about 2%).
+The precision comparison runs the laminar flag with the same fixed time
+step in FP64, mixed precision and FP32 and states the errors of the last two
+against the first (trailing-edge trajectory, Strouhal number, amplitude,
+fields, divergence).
+
 All stepping runs in the library's kernels; the analysis is host-side.
 """
 from __future__ import annotations
@@ -33,6 +38,26 @@ def flag_oscillation(t, te, length=1.0, speed=1.0):
     St, rms = strouhal(t, y, length, speed)
     return {"strouhal": St, "period": length / (St * speed) if St > 0 else float("inf"),
             "amplitude": 0.5 * float(y.max() - y.min()), "rms": rms, "component": comp}
+
+
+def cycle_statistics(t, y):
+    """Period and amplitude of an oscillation from its upward zero crossings
+    about the mean (crossing times by linear interpolation): the period is
+    the mean spacing of the crossings, the amplitude the mean over whole
+    cycles of half the peak-to-peak excursion. Resolves the frequency to a
+    fraction of the sampling interval over the record, where a periodogram
+    resolves one bin (1 / record length)."""
+    t = np.asarray(t, dtype=float)
+    y = np.asarray(y, dtype=float)
+    y = y - y.mean()
+    up = np.nonzero((y[:-1] < 0) & (y[1:] >= 0))[0]
+    if up.size < 2:
+        return {"period": float("nan"), "cycles": 0, "amplitude": float("nan")}
+    tc = t[up] - y[up] * (t[up + 1] - t[up]) / (y[up + 1] - y[up])
+    amps = [0.5 * float(y[a:b + 1].max() - y[a:b + 1].min()) for a, b in zip(up[:-1], up[1:])]
+    per = np.diff(tc)
+    return {"period": float(per.mean()), "period_std": float(per.std()), "cycles": int(per.size),
+            "amplitude": float(np.mean(amps)), "amplitude_std": float(np.std(amps))}
 
 
 def laminar_workload(cells_per_length=64, base=inputs.PRODUCTION):
@@ -60,6 +85,75 @@ def run(wl, steps, discard, precision=binding.IBM_FP32, every=2):
     out.update({"workload": wl.name, "cells": wl.cells, "steps": steps, "discard": discard,
                 "t_end": float(t[-1]), "seconds": wall})
     s.close()
+    return out
+
+
+def precision_comparison(steps=12000, discard=4000, cells_per_length=32, dt=6e-3, every=2, early=200,
+                         precisions=("fp64", "mixed", "fp32")):
+    """The laminar flag (production domain and flag, no bars, Re = 200) run
+    with the same fixed time step in each precision. Errors of the mixed and
+    FP32 runs are taken against the FP64 run (the path that matches the CPU
+    oracle to 1e-9):
+      * after `early` steps, u, v, w (relative to U), gauge-fixed p (relative
+        to U^2) and the trailing-edge midpoint (relative to L);
+      * the times at which the trailing-edge trajectories first differ by
+        1e-4, 1e-3 and 1e-2 L (the self-excited flapping amplifies any
+        difference until the runs drift apart in phase);
+      * after `discard` steps, the flapping statistics: period and amplitude
+        from zero crossings, Strouhal number St = L / (U T), rms;
+      * the divergence left after the projection (h max |div u|)."""
+    wl = laminar_workload(cells_per_length)
+    prec = {"fp64": binding.IBM_FP64, "fp32": binding.IBM_FP32, "mixed": binding.IBM_MIXED}
+    runs = {}
+    for name in precisions:
+        s = binding.Solver(wl, prec[name], noise=inputs.initial_noise(wl))
+        t, te = [], []
+        early_fields = None
+        t0 = time.perf_counter()
+        for k in range(0, steps, every):
+            s.step(every, dt=dt)
+            st = s.stats()
+            t.append(st["t"])
+            te.append(list(st["te_mid"]))
+            if early_fields is None and k + every >= early:
+                early_fields = s.fields()
+        wall = time.perf_counter() - t0
+        t, te = np.asarray(t), np.asarray(te)
+        keep = slice(discard // every, None)
+        comp = 1 + int(np.argmax(te[keep, 1:].std(axis=0)))
+        cyc = cycle_statistics(t[keep], te[keep, comp])
+        st = s.stats()
+        runs[name] = {"t": t, "te": te, "cyc": cyc, "comp": comp, "seconds": wall,
+                      "rms": float(te[keep, comp].std()), "h_max_div": st["max_div"] * wl.lx / wl.nx,
+                      "early": early_fields}
+        s.close()
+    ref = runs["fp64"]
+    out = {"workload": wl.name, "cells": wl.cells, "re": wl.re, "steps": steps, "discard": discard,
+           "dt": dt, "early_steps": early, "t_end": float(ref["t"][-1]),
+           "fp64": {"period": ref["cyc"]["period"], "strouhal": wl.flag_len / ref["cyc"]["period"],
+                    "amplitude": ref["cyc"]["amplitude"], "rms": ref["rms"], "cycles": ref["cyc"]["cycles"],
+                    "h_max_div": ref["h_max_div"], "seconds": ref["seconds"]}}
+    for name in precisions:
+        if name == "fp64":
+            continue
+        r = runs[name]
+        st_r = wl.flag_len / r["cyc"]["period"]
+        e = {"period": r["cyc"]["period"], "strouhal": st_r, "amplitude": r["cyc"]["amplitude"],
+             "rms": r["rms"], "cycles": r["cyc"]["cycles"],
+             "strouhal_rel_err": abs(st_r - out["fp64"]["strouhal"]) / out["fp64"]["strouhal"],
+             "amplitude_rel_err": abs(r["cyc"]["amplitude"] - ref["cyc"]["amplitude"]) / ref["cyc"]["amplitude"],
+             "rms_rel_err": abs(r["rms"] - ref["rms"]) / ref["rms"],
+             "h_max_div": r["h_max_div"], "seconds": r["seconds"]}
+        dte = np.abs(r["te"] - ref["te"]).max(axis=1) / wl.flag_len
+        for thr in (1e-4, 1e-3, 1e-2):
+            hit = np.nonzero(dte > thr)[0]
+            e[f"t_diverge_{thr:g}"] = float(ref["t"][hit[0]]) if hit.size else None
+        e["te_err_early"] = float(dte[early // every - 1])
+        for q, a, b in zip("uvwp", r["early"], ref["early"]):
+            if q == "p":
+                a, b = a - a.mean(), b - b.mean()
+            e[f"{q}_err_early"] = float(np.abs(a - b).max()) / max(float(np.abs(b).max()), 1.0)
+        out[name] = e
     return out
 
 
@@ -120,9 +214,17 @@ def main(argv=None):
     ap.add_argument("--out", default="laminar_flag.json")
     ap.add_argument("--bars", action="store_true",
                     help="compare the two bar-grid forcings instead (production workload, no flag)")
+    ap.add_argument("--precision", action="store_true",
+                    help="compare the mixed and FP32 paths with the FP64 one on the laminar flag (h = 1/32)")
     a = ap.parse_args(argv)
     from . import build
     build.build()
+    if a.precision:
+        res = precision_comparison(a.steps, a.discard)
+        with open(a.out, "w") as f:
+            json.dump(res, f, indent=1)
+        print(json.dumps(res, indent=1))
+        return
     if a.bars:
         res = bar_forcing_comparison()
         with open(a.out, "w") as f:

@@ -37,3 +37,19 @@ def test_inside_rods_mask():
     assert abs(m.mean() - (2 * full - full * full)) < 1e-12
     assert m[int(0.25 / h), :].all() and m[:, int(0.25 / h)].all()
     assert not validation._inside_rods(wl, 0, i + 10).any()
+
+
+def test_cycle_statistics_of_a_synthetic_signal():
+    """Zero-crossing period and per-cycle amplitude of a sampled sine with an
+    offset: exact to the interpolation error of the crossings, far below a
+    periodogram bin (1 / record length = 0.025 here)."""
+    t = np.linspace(0.0, 40.0, 2001)
+    y = 0.05 + 0.2 * np.sin(2 * np.pi * t / 4.5 + 0.7)
+    out = validation.cycle_statistics(t, y)
+    assert out["cycles"] == 8
+    assert abs(out["period"] - 4.5) < 1e-4
+    assert abs(out["amplitude"] - 0.2) < 1e-3
+    # a growing oscillation: the mean per-cycle amplitude, not the largest
+    g = np.sin(2 * np.pi * t / 4.0) * (1.0 + 0.01 * t)
+    out = validation.cycle_statistics(t, g)
+    assert abs(out["period"] - 4.0) < 2e-3 and out["amplitude_std"] > 0
