@@ -40,17 +40,31 @@ def flag_oscillation(t, te, length=1.0, speed=1.0):
             "amplitude": 0.5 * float(y.max() - y.min()), "rms": rms, "component": comp}
 
 
-def cycle_statistics(t, y):
-    """Period and amplitude of an oscillation from its upward zero crossings
-    about the mean (crossing times by linear interpolation): the period is
-    the mean spacing of the crossings, the amplitude the mean over whole
-    cycles of half the peak-to-peak excursion. Resolves the frequency to a
-    fraction of the sampling interval over the record, where a periodogram
-    resolves one bin (1 / record length)."""
+def cycle_statistics(t, y, hysteresis=0.5):
+    """Period and amplitude of an oscillation from its upward crossings of
+    the mean, with hysteresis: a crossing counts only after the signal has
+    been below -hysteresis * rms since the last one and it is confirmed once
+    the signal reaches +hysteresis * rms, so that harmonics and small
+    wiggles near the mean add no crossings. Crossing times by linear
+    interpolation; the period is the mean spacing of the crossings, the
+    amplitude the mean over whole cycles of half the peak-to-peak
+    excursion. Resolves the frequency to a fraction of the sampling interval
+    over the record, where a periodogram resolves one bin (1 / record
+    length)."""
     t = np.asarray(t, dtype=float)
     y = np.asarray(y, dtype=float)
     y = y - y.mean()
-    up = np.nonzero((y[:-1] < 0) & (y[1:] >= 0))[0]
+    band = hysteresis * float(np.sqrt(np.mean(y * y)))
+    up, armed, cand = [], False, None
+    for q in range(len(y) - 1):
+        if y[q] < -band:
+            armed, cand = True, None
+        if armed and y[q] < 0 <= y[q + 1]:
+            cand = q
+        if armed and cand is not None and y[q + 1] > band:
+            up.append(cand)
+            armed, cand = False, None
+    up = np.asarray(up, dtype=int)
     if up.size < 2:
         return {"period": float("nan"), "cycles": 0, "amplitude": float("nan")}
     tc = t[up] - y[up] * (t[up + 1] - t[up]) / (y[up + 1] - y[up])
@@ -132,14 +146,24 @@ def precision_comparison(steps=12000, discard=4000, cells_per_length=32, dt=6e-3
            "dt": dt, "early_steps": early, "t_end": float(ref["t"][-1]),
            "fp64": {"period": ref["cyc"]["period"], "strouhal": wl.flag_len / ref["cyc"]["period"],
                     "amplitude": ref["cyc"]["amplitude"], "rms": ref["rms"], "cycles": ref["cyc"]["cycles"],
+                    "period_std": ref["cyc"].get("period_std"), "amplitude_std": ref["cyc"].get("amplitude_std"),
                     "h_max_div": ref["h_max_div"], "seconds": ref["seconds"]}}
+    # sampling error of the mean period and amplitude (cycle-to-cycle spread / sqrt(cycles))
+    for key in ("period", "amplitude"):
+        sd = ref["cyc"].get(key + "_std")
+        out["fp64"][key + "_sampling_err"] = (sd / np.sqrt(ref["cyc"]["cycles"])) if sd is not None else None
+    # the trailing-edge trajectories, every 10th sample (t, fp64, and each other precision)
+    sub = slice(None, None, 10)
+    out["te_series"] = {"t": ref["t"][sub].tolist(), "component": ref["comp"],
+                        **{name: runs[name]["te"][sub, ref["comp"]].tolist() for name in precisions}}
     for name in precisions:
         if name == "fp64":
             continue
         r = runs[name]
         st_r = wl.flag_len / r["cyc"]["period"]
         e = {"period": r["cyc"]["period"], "strouhal": st_r, "amplitude": r["cyc"]["amplitude"],
-             "rms": r["rms"], "cycles": r["cyc"]["cycles"],
+             "rms": r["rms"], "cycles": r["cyc"]["cycles"], "period_std": r["cyc"].get("period_std"),
+             "amplitude_std": r["cyc"].get("amplitude_std"),
              "strouhal_rel_err": abs(st_r - out["fp64"]["strouhal"]) / out["fp64"]["strouhal"],
              "amplitude_rel_err": abs(r["cyc"]["amplitude"] - ref["cyc"]["amplitude"]) / ref["cyc"]["amplitude"],
              "rms_rel_err": abs(r["rms"] - ref["rms"]) / ref["rms"],

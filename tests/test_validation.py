@@ -46,10 +46,21 @@ def test_cycle_statistics_of_a_synthetic_signal():
     t = np.linspace(0.0, 40.0, 2001)
     y = 0.05 + 0.2 * np.sin(2 * np.pi * t / 4.5 + 0.7)
     out = validation.cycle_statistics(t, y)
-    assert out["cycles"] == 8
+    assert out["cycles"] == 7
     assert abs(out["period"] - 4.5) < 1e-4
     assert abs(out["amplitude"] - 0.2) < 1e-3
     # a growing oscillation: the mean per-cycle amplitude, not the largest
     g = np.sin(2 * np.pi * t / 4.0) * (1.0 + 0.01 * t)
     out = validation.cycle_statistics(t, g)
     assert abs(out["period"] - 4.0) < 2e-3 and out["amplitude_std"] > 0
+
+
+def test_cycle_statistics_ignores_harmonics():
+    """A second harmonic strong enough to add zero crossings of its own
+    leaves the period and the cycle count unchanged."""
+    t = np.linspace(0.0, 45.0, 9001)
+    y = np.sin(2 * np.pi * t / 4.5) + 0.8 * np.sin(2 * np.pi * 2 * t / 4.5)
+    naive = np.count_nonzero((y[:-1] < 0) & (y[1:] >= 0))
+    out = validation.cycle_statistics(t, y)
+    assert naive >= 19
+    assert out["cycles"] == 8 and abs(out["period"] - 4.5) < 1e-3
