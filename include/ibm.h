@@ -92,6 +92,10 @@ extern "C" {
                                    mixed pressure solve runs eight            */
 #define IBM_STAGE_RESIDUAL  16  /* the double-single residual D - L_h phi of the
                                    mixed solve's refinement (IBM_MIXED only)  */
+#define IBM_STAGE_TC_PASS1  17  /* one single-product (TF32) transform pass, as the
+                                   mixed solve's predictor runs at 256 x 256
+                                   planes (IBM_MIXED; otherwise nothing): the
+                                   solve runs four, and four of TC_PASS       */
 
 /* field selectors for ibm_get_field / ibm_set_field */
 #define IBM_FIELD_U 0
@@ -334,6 +338,17 @@ int ibm_stats_static(ibm_state* s, ibm_stats_t* out);
  * the library creates). */
 typedef struct ibm_ensemble ibm_ensemble;
 int ibm_ensemble_create(ibm_state* const* members, int n, void* stream, ibm_ensemble** out);
+/* The same ensemble with the explicit stage (Sec. II.B: AB2 advection, the
+ * explicit Crank-Nicolson half, -G p) of every member batched into one
+ * persistent launch: a case table lists each member's constants, fields
+ * and block grid, and the launch's blocks walk the concatenated block lists
+ * of all members. Each member's step is recorded in pieces (start of step,
+ * rest of the head, tail with the structural update joined) around that
+ * launch, so the members meet at the explicit stage once per step. Same
+ * results as ibm_ensemble_create up to rounding order; the table (device
+ * memory) belongs to the ensemble. Errors as ibm_ensemble_create, plus
+ * IBM_ENOMEM if the table cannot be allocated. */
+int ibm_ensemble_create_batched(ibm_state* const* members, int n, void* stream, ibm_ensemble** out);
 /* Advance every member nsteps steps (dt as in ibm_step, for every member).
  * Checks every member for divergence at the end; returns the first error. */
 int ibm_ensemble_step(ibm_ensemble* e, double dt, int nsteps);

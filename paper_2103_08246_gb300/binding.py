@@ -27,7 +27,8 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_stats", "ibm_get_field", "ibm_set_field", "ibm_marker_count", "ibm_get_markers",
            "ibm_save", "ibm_load", "ibm_set_inflow", "ibm_inflow_planes", "ibm_get_plane",
            "ibm_plane_device", "ibm_probes_set", "ibm_probe_sample",
-           "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_step", "ibm_ensemble_destroy",
+           "ibm_time_stage", "ibm_stats_static", "ibm_ensemble_create", "ibm_ensemble_create_batched",
+           "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_gen_create", "ibm_gen_param_count", "ibm_gen_set_params", "ibm_gen_get_params",
            "ibm_gen_get_grads", "ibm_gen_set_norm", "ibm_gen_forward", "ibm_gen_grad", "ibm_gen_adam_step",
            "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_relax", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_emit", "ibm_gen_history", "ibm_gen_save", "ibm_gen_load", "ibm_gen_sync",
@@ -36,7 +37,7 @@ _VOID = ("ibm_destroy", "ibm_ensemble_destroy", "ibm_gen_destroy")
 
 STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
           "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11, "poisson": 12,
-          "af_yz": 13, "dht2d": 14, "tc_pass": 15, "residual": 16}
+          "af_yz": 13, "dht2d": 14, "tc_pass": 15, "residual": 16, "tc_pass1": 17}
 
 
 class ibm_grid(ctypes.Structure):
@@ -134,6 +135,7 @@ def load(path: str = LIB_PATH):
     lib.ibm_load.argtypes = [vp, ctypes.c_char_p]
     lib.ibm_time_stage.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.ibm_ensemble_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.ibm_ensemble_create_batched.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.ibm_ensemble_step.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     lib.ibm_ensemble_destroy.argtypes = [vp]
     lib.ibm_destroy.argtypes = [vp]
@@ -312,12 +314,12 @@ def ibm_time_stage(state, stage, nrep) -> float:
     return ms.value
 
 
-def ibm_ensemble_create(states, stream=None):
+def ibm_ensemble_create(states, stream=None, batched=False):
     arr = (ctypes.c_void_p * len(states))(*[st.value if isinstance(st, ctypes.c_void_p) else st
                                              for st in states])
     h = ctypes.c_void_p()
-    _check(load().ibm_ensemble_create(arr, len(states), stream, ctypes.byref(h)),
-           "ibm_ensemble_create")
+    name = "ibm_ensemble_create_batched" if batched else "ibm_ensemble_create"
+    _check(getattr(load(), name)(arr, len(states), stream, ctypes.byref(h)), name)
     return h
 
 
@@ -554,14 +556,15 @@ class Solver:
 
 
 class Ensemble:
-    """Several Solver members stepped together by one graph launch per step."""
+    """Several Solver members stepped together by one graph launch per step;
+    batched: the members' explicit stages in one persistent launch."""
 
-    def __init__(self, solvers, stream=None):
+    def __init__(self, solvers, stream=None, batched=False):
         import torch
         self.solvers = list(solvers)
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.handle = ibm_ensemble_create([s.state for s in self.solvers],
-                                          ctypes.c_void_p(self.stream.cuda_stream))
+                                          ctypes.c_void_p(self.stream.cuda_stream), batched)
 
     def step(self, nsteps=1, dt=-1.0):
         _check(ibm_ensemble_step(self.handle, dt, nsteps), "ibm_ensemble_step")

@@ -568,6 +568,17 @@ void solve_poisson(ibm_state* s, cudaStream_t st) {
   launch_poisson(s->c, f, st);
 }
 
+// projection after solve_poisson: the mixed solve leaves phi as predictor
+// (e[1]) plus correction (e[2]), which the projection sums as it reads them
+template <class T>
+void project_after_solve(ibm_state* s, int cur, bool initial, cudaStream_t st) {
+  Fields<T>& f = fields<T>(s);
+  if (std::is_same<T, float>::value && s->precision == IBM_MIXED)
+    launch_project(s->c, f, cur, initial, st, (const T*)f.e[1], (const T*)f.e[2]);
+  else
+    launch_project(s->c, f, cur, initial, st);
+}
+
 // A time step is split at the immersed-boundary forcing into a head (dt, RHS,
 // implicit factors) and a tail (forcing, structure, pressure, projection).
 // The structural update needs only the forcing's result and is needed only
@@ -610,7 +621,7 @@ bool record_tail_body(ibm_state* s, int cur) {
   }
   launch_mass_div(c, f, cur, false, st);
   solve_poisson<T>(s, st);
-  launch_project(c, f, cur, false, st);
+  project_after_solve<T>(s, cur, false, st);
   return flag;
 }
 
@@ -693,6 +704,9 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
     const int want = std::min((fl.n_tri + fl.n_spring + 1023) / 1024, flag_max_cluster());
     fl.cluster = 1;
     while (2 * fl.cluster <= want) fl.cluster *= 2;
+    // the structural update runs beside the pressure solve: persistent
+    // kernels there leave its SMs free instead of queueing behind it
+    s->c.sm_reserved = fl.cluster;
   }
   // parameters
   Params p{};
@@ -726,7 +740,7 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
   s->cur = 0;
   launch_mass_div(c, f, 0, true, st);
   solve_poisson<T>(s, st);
-  launch_project(c, f, 0, true, st);
+  project_after_solve<T>(s, 0, true, st);
   s->cur = 1;
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
@@ -869,6 +883,11 @@ void launch_stage(ibm_state* s, int stage) {
         if (s->precision == IBM_MIXED && s->hz_img)
           (void)tc_rows_times_h_t(f.phi, s->hz_img, f.e[0], c.nx, c.nz, &f.prm->error, st);
       break;
+    case IBM_STAGE_TC_PASS1:
+      if constexpr (std::is_same<T, float>::value)
+        if (s->precision == IBM_MIXED && s->hz_img && c.nz == 256)
+          (void)tc_rows_times_h_t(f.phi, s->hz_img, f.e[0], c.nx, c.nz, &f.prm->error, st, true);
+      break;
     case IBM_STAGE_RESIDUAL:
       if constexpr (std::is_same<T, float>::value)
         if (s->precision == IBM_MIXED) launch_residual_mixed(c, f, st);
@@ -913,6 +932,81 @@ __global__ void k_wait_selftest(uint32_t spins, int* flag) {
   }
 }
 
+}  // namespace
+
+namespace {
+// pieces of a member's step for the batched ensemble: the step's start
+// (dt, implicit-factor tables), its explicit stage (batched across the
+// members), the rest of its head (inflow, outflow, implicit factors), its
+// tail (forcing, structure joined, pressure, projection)
+template <class T>
+void record_pre(ibm_state* s, int cur) {
+  Fields<T>& f = fields<T>(s);
+  launch_begin_step(s->c, f, s->stream);
+  launch_af_tables(s->c, f, s->stream);
+  (void)cur;
+}
+template <class T>
+void record_post(ibm_state* s, int cur) {
+  Fields<T>& f = fields<T>(s);
+  launch_inflow(s->c, f, cur, s->stream);
+  launch_outflow(s->c, f, cur, s->stream);
+  launch_af(s->c, f, cur, s->stream);
+}
+template <class T>
+void record_tail_joined(ibm_state* s, int cur) {
+  if (record_tail_body<T>(s, cur)) cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+}
+
+// capture one piece of a member's step into a graph
+template <class T>
+cudaError_t capture_piece(ibm_state* s, int piece, int cur, cudaGraph_t* g) {
+  cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  if (piece == 0) record_pre<T>(s, cur);
+  else if (piece == 1) record_post<T>(s, cur);
+  else record_tail_joined<T>(s, cur);
+  return cudaStreamEndCapture(s->stream, g);
+}
+
+cudaError_t member_piece(ibm_state* s, int piece, int cur, cudaGraph_t* g) {
+  return s->precision == IBM_FP64 ? capture_piece<double>(s, piece, cur, g) : capture_piece<float>(s, piece, cur, g);
+}
+
+// the case table of the members of one field precision at offset `off`,
+// uploaded to device memory; returns the number of blocks in *total
+template <class T>
+cudaError_t build_cases(const std::vector<ibm_state*>& ms, int off, void** dtab, int* ncases, int* total) {
+  std::vector<RhsCase<T>> tab;
+  int first = 0;
+  for (ibm_state* m : ms) {
+    if ((m->precision == IBM_FP64) != std::is_same<T, double>::value) continue;
+    RhsCase<T> e = rhs_case<T>(m->c, fields<T>(m), (m->cur + off) & 1);
+    e.first = first;
+    first += e.gx * e.gy * e.gz;
+    tab.push_back(e);
+  }
+  *ncases = (int)tab.size();
+  *total = first;
+  *dtab = nullptr;
+  if (tab.empty()) return cudaSuccess;
+  cudaError_t err = cudaMalloc(dtab, tab.size() * sizeof(RhsCase<T>));
+  if (err != cudaSuccess) return err;
+  return cudaMemcpy(*dtab, tab.data(), tab.size() * sizeof(RhsCase<T>), cudaMemcpyHostToDevice);
+}
+
+// the persistent launch over a case table, captured on `st` into a graph
+template <class T>
+cudaError_t cases_graph(const void* dtab, int ncases, int total, cudaStream_t st, cudaGraph_t* g) {
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = std::max(1, std::min(total, 8 * std::max(sms, 1)));
+  launch_rhs_cases<T>((const RhsCase<T>*)dtab, ncases, total, blocks, st);
+  return cudaStreamEndCapture(st, g);
+}
 }  // namespace
 
 extern "C" {
@@ -1083,7 +1177,7 @@ int ibm_stats(ibm_state* s, ibm_stats_t* out) {
 }
 
 int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
-  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_RESIDUAL) return IBM_EINVAL;
+  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_TC_PASS1) return IBM_EINVAL;
   cudaStream_t st = s->stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1413,7 +1507,12 @@ struct ibm_ensemble {
   int par = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // batched explicit stage: case tables per offset (FP32-field and FP64
+  // members), device memory owned by the ensemble
+  void* table[2][2] = {};
 };
+
+
 
 static int ensemble_set_dt(ibm_state* s, double dt, cudaStream_t st) {
   const double mode = dt > 0 ? dt : -1.0;
@@ -1476,6 +1575,106 @@ int ibm_ensemble_create(ibm_state* const* members, int n, void* stream, ibm_ense
   return IBM_OK;
 }
 
+int ibm_ensemble_create_batched(ibm_state* const* members, int n, void* stream, ibm_ensemble** out) {
+  if (!members || n < 1 || !out) return IBM_EINVAL;
+  *out = nullptr;
+  std::unique_ptr<ibm_ensemble> e(new (std::nothrow) ibm_ensemble());
+  if (!e) return IBM_ENOMEM;
+  for (int q = 0; q < n; ++q) {
+    if (!members[q] || !members[q]->graph[GRAPH_MID][0]) return IBM_EINVAL;
+    for (int r = 0; r < q; ++r)
+      if (members[r] == members[q]) return IBM_EINVAL;
+    e->members.push_back(members[q]);
+    CK(cudaStreamSynchronize(members[q]->stream));
+  }
+  if (stream) {
+    e->stream = (cudaStream_t)stream;
+  } else {
+    CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+    e->own_stream = true;
+  }
+  // member pieces [member][piece][parity] and the batched explicit stage
+  // [offset][precision: 0 FP32 fields, 1 FP64]
+  std::vector<std::array<std::array<cudaGraph_t, 2>, 3>> pieces(n);
+  cudaGraph_t kg[2][2] = {};
+  int nc[2][2] = {}, tot[2][2] = {};
+  auto fail = [&](cudaError_t err) {
+    for (auto& m : pieces)
+      for (auto& pc : m)
+        for (cudaGraph_t g : pc)
+          if (g) cudaGraphDestroy(g);
+    for (auto& a : kg)
+      for (cudaGraph_t g : a)
+        if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    ibm_ensemble_destroy(e.release());
+    return err == cudaErrorMemoryAllocation ? IBM_ENOMEM : IBM_ECUDA;
+  };
+  for (int q = 0; q < n; ++q)
+    for (int pc = 0; pc < 3; ++pc)
+      for (int par = 0; par < 2; ++par) {
+        pieces[q][pc][par] = nullptr;
+        cudaError_t err = member_piece(e->members[q], pc, par, &pieces[q][pc][par]);
+        if (err != cudaSuccess) return fail(err);
+      }
+  for (int off = 0; off < 2; ++off) {
+    cudaError_t err = build_cases<float>(e->members, off, &e->table[off][0], &nc[off][0], &tot[off][0]);
+    if (err == cudaSuccess)
+      err = build_cases<double>(e->members, off, &e->table[off][1], &nc[off][1], &tot[off][1]);
+    if (err == cudaSuccess && nc[off][0])
+      err = cases_graph<float>(e->table[off][0], nc[off][0], tot[off][0], e->stream, &kg[off][0]);
+    if (err == cudaSuccess && nc[off][1])
+      err = cases_graph<double>(e->table[off][1], nc[off][1], tot[off][1], e->stream, &kg[off][1]);
+    if (err != cudaSuccess) return fail(err);
+  }
+  // parent graphs: head = pre -> batched explicit stage -> post;
+  // mid = tail -> pre (other parity) -> batched stage -> post; tail = tail
+  for (int kind = 0; kind < GRAPH_KINDS; ++kind)
+    for (int off = 0; off < 2; ++off) {
+      cudaGraph_t parent;
+      CK(cudaGraphCreate(&parent, 0));
+      cudaError_t err = cudaSuccess;
+      std::vector<cudaGraphNode_t> pre(n), tails(n);
+      const int hoff = kind == GRAPH_MID ? off ^ 1 : off;   // offset of the head part
+      for (int q = 0; q < n && err == cudaSuccess; ++q) {
+        ibm_state* m = e->members[q];
+        const int pt = (m->cur + off) & 1, ph = (m->cur + hoff) & 1;
+        if (kind != GRAPH_HEAD)
+          err = cudaGraphAddChildGraphNode(&tails[q], parent, nullptr, 0, pieces[q][2][pt]);
+        if (err == cudaSuccess && kind != GRAPH_TAIL)
+          err = cudaGraphAddChildGraphNode(&pre[q], parent, kind == GRAPH_MID ? &tails[q] : nullptr,
+                                           kind == GRAPH_MID ? 1 : 0, pieces[q][0][ph]);
+      }
+      if (kind != GRAPH_TAIL) {
+        cudaGraphNode_t kn[2] = {};
+        for (int t = 0; t < 2 && err == cudaSuccess; ++t) {
+          if (!kg[hoff][t]) continue;
+          std::vector<cudaGraphNode_t> deps;
+          for (int q = 0; q < n; ++q)
+            if ((e->members[q]->precision == IBM_FP64) == (t == 1)) deps.push_back(pre[q]);
+          err = cudaGraphAddChildGraphNode(&kn[t], parent, deps.data(), deps.size(), kg[hoff][t]);
+        }
+        for (int q = 0; q < n && err == cudaSuccess; ++q) {
+          ibm_state* m = e->members[q];
+          cudaGraphNode_t post;
+          const cudaGraphNode_t dep = kn[m->precision == IBM_FP64 ? 1 : 0];
+          err = cudaGraphAddChildGraphNode(&post, parent, &dep, 1, pieces[q][1][(m->cur + hoff) & 1]);
+        }
+      }
+      if (err == cudaSuccess) err = cudaGraphInstantiate(&e->exec[kind][off], parent, 0);
+      cudaGraphDestroy(parent);
+      if (err != cudaSuccess) return fail(err);
+    }
+  for (auto& m : pieces)
+    for (auto& pc : m)
+      for (cudaGraph_t g : pc) cudaGraphDestroy(g);
+  for (auto& a : kg)
+    for (cudaGraph_t g : a)
+      if (g) cudaGraphDestroy(g);
+  *out = e.release();
+  return IBM_OK;
+}
+
 int ibm_ensemble_step(ibm_ensemble* e, double dt, int nsteps) {
   if (!e || nsteps < 0) return IBM_EINVAL;
   cudaStream_t st = e->stream;
@@ -1516,6 +1715,9 @@ void ibm_ensemble_destroy(ibm_ensemble* e) {
   for (int k = 0; k < GRAPH_KINDS; ++k)
     for (int q = 0; q < 2; ++q)
       if (e->exec[k][q]) cudaGraphExecDestroy(e->exec[k][q]);
+  for (auto& a : e->table)
+    for (void* t : a)
+      if (t) cudaFree(t);
   if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
   cudaGetLastError();
   delete e;

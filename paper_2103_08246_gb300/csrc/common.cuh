@@ -49,6 +49,7 @@ struct Consts {
   int rhs_planes;     // tile: x planes per block of the streamed RHS
   int rhs_stages;     // tile: most x planes in the streamed RHS's ring
   int afx_planes;     // tile: x planes per block of the FP32 x factor
+  int sm_reserved;    // SMs the structural update holds while the pressure solve runs
   float f_inv_h, f_inv_h2, f_nu;   // FP32 copies
 };
 

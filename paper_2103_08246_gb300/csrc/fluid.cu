@@ -156,15 +156,16 @@ __global__ void k_end_step(Params* prm) {
 // ---------------------------------------------------------------- RHS (A2)
 // RHS = dt [ -(alpha N^n + beta N^{n-1}) - G p^n + nu L u^n ], N in flux form.
 // One thread per (y, z) column and XCHUNK x planes; neighbours through L1.
+// column (j, k), x planes i0 .. i1 - 1 (block (bx, by, bz) of the grid
+// grid3(c, nx + 1) with threads (TK, TJ))
 template <class T>
-__global__ void __launch_bounds__(TK* TJ)
-k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
-      const T* __restrict__ v, const T* __restrict__ w, const T* __restrict__ p,
-      T* __restrict__ n0, T* __restrict__ n1, T* __restrict__ n2, T* __restrict__ d0,
-      T* __restrict__ d1, T* __restrict__ d2, const T* __restrict__ vin,
-      const T* __restrict__ win) {
-  const int k = blockIdx.x * TK + threadIdx.x;
-  const int j = blockIdx.y * TJ + threadIdx.y;
+__device__ inline void rhs_block(const Consts& c, const Params* __restrict__ prm, const T* __restrict__ u,
+                                 const T* __restrict__ v, const T* __restrict__ w, const T* __restrict__ p,
+                                 T* __restrict__ n0, T* __restrict__ n1, T* __restrict__ n2,
+                                 T* __restrict__ d0, T* __restrict__ d1, T* __restrict__ d2,
+                                 const T* __restrict__ vin, const T* __restrict__ win, int bx, int by, int bz) {
+  const int k = bx * TK + threadIdx.x;
+  const int j = by * TJ + threadIdx.y;
   if (k >= c.nz || j >= c.ny) return;
   const int nx = c.nx, ny = c.ny, nz = c.nz;
   const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
@@ -175,7 +176,7 @@ k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
   const T ih2 = pick<T>(c.inv_h * c.inv_h, c.f_inv_h2), hf = (T)0.5;
   const size_t P = plane(c);
   auto at = [&](int i, int jj, int kk) { return ((size_t)i * ny + jj) * nz + kk; };
-  const int i0 = blockIdx.z * XCHUNK;
+  const int i0 = bz * XCHUNK;
   const int i1 = min(i0 + XCHUNK, nx + 1);
   for (int i = i0; i < i1; ++i) {
     const size_t id = at(i, j, k);
@@ -246,6 +247,33 @@ k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
         d2[id] = dt * (-(alpha * N + beta * Np) - Gp + nu * L);
       }
     }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TK* TJ)
+k_rhs(Consts c, const Params* __restrict__ prm, const T* __restrict__ u,
+      const T* __restrict__ v, const T* __restrict__ w, const T* __restrict__ p,
+      T* __restrict__ n0, T* __restrict__ n1, T* __restrict__ n2, T* __restrict__ d0,
+      T* __restrict__ d1, T* __restrict__ d2, const T* __restrict__ vin,
+      const T* __restrict__ win) {
+  rhs_block<T>(c, prm, u, v, w, p, n0, n1, n2, d0, d1, d2, vin, win, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// The explicit stage of several independent cases (an ensemble) in one
+// persistent launch: the case table lists per case its constants, fields
+// and block grid; the blocks of the launch walk the concatenated block
+// lists of all cases.
+template <class T>
+__global__ void __launch_bounds__(TK* TJ)
+k_rhs_cases(const RhsCase<T>* __restrict__ table, int ncases, int total) {
+  for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    int q = 0;
+    while (q + 1 < ncases && table[q + 1].first <= item) ++q;
+    const RhsCase<T>& e = table[q];
+    const int local = item - e.first;
+    const int bx = local % e.gx, by = (local / e.gx) % e.gy, bz = local / (e.gx * e.gy);
+    rhs_block<T>(e.c, e.prm, e.u, e.v, e.w, e.p, e.n0, e.n1, e.n2, e.d0, e.d1, e.d2, e.vin, e.win, bx, by, bz);
   }
 }
 
@@ -1413,8 +1441,10 @@ template <class T>
 __global__ void __launch_bounds__(TK* TJ)
 k_project(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
           const T* __restrict__ va, const T* __restrict__ wa, T* __restrict__ ub,
-          T* __restrict__ vb, T* __restrict__ wb, const T* __restrict__ phi, T* __restrict__ p,
-          double* __restrict__ partial, int initial) {
+          T* __restrict__ vb, T* __restrict__ wb, const T* __restrict__ phi_a, const T* __restrict__ phi_b,
+          T* __restrict__ p, double* __restrict__ partial, int initial) {
+  // phi = phi_a (+ phi_b: the mixed solve's predictor and correction, summed here)
+  auto phiv = [&](size_t q) { return phi_b ? phi_a[q] + phi_b[q] : phi_a[q]; };
   const int k = blockIdx.x * TK + threadIdx.x;
   const int j = blockIdx.y * TJ + threadIdx.y;
   const bool act = (k < c.nz && j < c.ny);
@@ -1429,7 +1459,7 @@ k_project(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
     auto at = [&](int i, int jj, int kk) { return ((size_t)i * ny + jj) * nz + kk; };
     auto unew = [&](int i) -> T {  // new u on face i at (j, k)
       const size_t id = at(i, j, k);
-      if (i >= 1 && i <= nx - 1) return ua[id] - gdt * (phi[id] - phi[id - P]);
+      if (i >= 1 && i <= nx - 1) return ua[id] - gdt * (phiv(id) - phiv(id - P));
       return ua[id];
     };
     const int i0 = blockIdx.z * XCHUNK, i1 = min(i0 + XCHUNK, nx + 1);
@@ -1442,21 +1472,21 @@ k_project(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
         wb[id] = wa[id];
         continue;
       }
-      const T ph = phi[id];
-      const T vn = va[id] - gdt * (ph - phi[at(i, jm, k)]);
-      const T wn = wa[id] - gdt * (ph - phi[at(i, j, km)]);
+      const T ph = phiv(id);
+      const T vn = va[id] - gdt * (ph - phiv(at(i, jm, k)));
+      const T wn = wa[id] - gdt * (ph - phiv(at(i, j, km)));
       vb[id] = vn;
       wb[id] = wn;
       if (!initial) {
-        const T pxm = i == 0 ? ph : phi[id - P];
-        const T pxp = i == nx - 1 ? ph : phi[id + P];
-        const T lap = pxm + pxp + phi[at(i, jm, k)] + phi[at(i, jp, k)] + phi[at(i, j, km)] +
-                      phi[at(i, j, kp)] - (T)6 * ph;
+        const T pxm = i == 0 ? ph : phiv(id - P);
+        const T pxp = i == nx - 1 ? ph : phiv(id + P);
+        const T lap = pxm + pxp + phiv(at(i, jm, k)) + phiv(at(i, jp, k)) + phiv(at(i, j, km)) +
+                      phiv(at(i, j, kp)) - (T)6 * ph;
         p[id] += ph - hnu * lap;
       }
       const T un1 = unew(i + 1);
-      const T vn1 = va[at(i, jp, k)] - gdt * (phi[at(i, jp, k)] - ph);
-      const T wn1 = wa[at(i, j, kp)] - gdt * (phi[at(i, j, kp)] - ph);
+      const T vn1 = va[at(i, jp, k)] - gdt * (phiv(at(i, jp, k)) - ph);
+      const T wn1 = wa[at(i, j, kp)] - gdt * (phiv(at(i, j, kp)) - ph);
       T sp = fabs((T)0.5 * (un + un1)) + fabs((T)0.5 * (vn + vn1)) + fabs((T)0.5 * (wn + wn1));
       if (!isfinite(sp)) sp = (T)INFINITY;
       smaxT = fmax(smaxT, sp);
@@ -1537,13 +1567,27 @@ k_div_vec(Consts c, const Params* __restrict__ prm, T* __restrict__ u, const T* 
   }
 }
 
-template <class T>
+template <class T, bool TWO>
 __global__ void __launch_bounds__(256, 3)
 k_project_vec(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
               const T* __restrict__ va, const T* __restrict__ wa, T* __restrict__ ub,
-              T* __restrict__ vb, T* __restrict__ wb, const T* __restrict__ phi, T* __restrict__ p,
-              double* __restrict__ partial, int initial) {
+              T* __restrict__ vb, T* __restrict__ wb, const T* __restrict__ phi, const T* __restrict__ phi_b,
+              T* __restrict__ p, double* __restrict__ partial, int initial) {
   constexpr int E = RunTile<T>::E;
+  // phi (+ phi_b when TWO: the mixed solve's predictor and correction, summed here)
+  auto ldg_phi = [&](size_t q, T (&v)[E]) {
+    ldg_run<T, E>(phi + q, v);
+    if constexpr (TWO) {
+      T t[E];
+      ldg_run<T, E>(phi_b + q, t);
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = v[e] + t[e];
+    }
+  };
+  auto phi1 = [&](size_t q) {
+    if constexpr (TWO) return phi[q] + phi_b[q];
+    else return phi[q];
+  };
   const int nx = c.nx, ny = c.ny, nz = c.nz;
   const int runs = nz / E;
   const int tj = RunTile<T>::THREADS / runs;
@@ -1560,8 +1604,8 @@ k_project_vec(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua
   T phm[E], ph[E], php[E], un[E], un1[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) phm[e] = ph[e] = (T)0;
-  if (i0 >= 1 && i0 - 1 <= nx - 1) ldg_run<T, E>(phi + at(i0 - 1, j, k0), phm);
-  if (i0 <= nx - 1) ldg_run<T, E>(phi + at(i0, j, k0), ph);
+  if (i0 >= 1 && i0 - 1 <= nx - 1) ldg_phi(at(i0 - 1, j, k0), phm);
+  if (i0 <= nx - 1) ldg_phi(at(i0, j, k0), ph);
   ldg_run<T, E>(ua + at(i0, j, k0), un);
   if (i0 >= 1 && i0 <= nx - 1) {
 #pragma unroll
@@ -1580,7 +1624,7 @@ k_project_vec(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua
     }
     // next plane: phi (Neumann image at the last plane) and the new u of face i+1
     if (i + 1 <= nx - 1) {
-      ldg_run<T, E>(phi + id + plane(c), php);
+      ldg_phi(id + plane(c), php);
     } else {
 #pragma unroll
       for (int e = 0; e < E; ++e) php[e] = ph[e];
@@ -1594,10 +1638,10 @@ k_project_vec(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua
     ldg_run<T, E>(va + id, vv);
     ldg_run<T, E>(va + at(i, jp, k0), vjp);
     ldg_run<T, E>(wa + id, ww);
-    ldg_run<T, E>(phi + at(i, jm, k0), pjm);
-    ldg_run<T, E>(phi + at(i, jp, k0), pjp);
+    ldg_phi(at(i, jm, k0), pjm);
+    ldg_phi(at(i, jp, k0), pjp);
     const T w_r = wa[at(i, j, kpE)];
-    const T ph_l = phi[at(i, j, km1)], ph_r = phi[at(i, j, kpE)];
+    const T ph_l = phi1(at(i, j, km1)), ph_r = phi1(at(i, j, kpE));
     if (!initial) ldg_run<T, E>(p + id, pp);
     stg_run<T, E>(ub + id, un);
     T vo[E], wo[E];
@@ -1793,6 +1837,36 @@ void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
 
 int outflow_blocks(const Consts& c) { return (c.ny * c.nz + OUT_THREADS - 1) / OUT_THREADS; }
 
+// one case of the ensemble's explicit stage (k_rhs_cases)
+template <class T>
+RhsCase<T> rhs_case(const Consts& c, const Fields<T>& f, int cur) {
+  RhsCase<T> e{};
+  e.c = c;
+  e.prm = f.prm;
+  e.u = f.u[cur];
+  e.v = f.v[cur];
+  e.w = f.w[cur];
+  e.p = f.p;
+  e.n0 = f.n[0];
+  e.n1 = f.n[1];
+  e.n2 = f.n[2];
+  e.d0 = f.d[0];
+  e.d1 = f.d[1];
+  e.d2 = f.d[2];
+  e.vin = inflow_cur_v(c, f);
+  e.win = inflow_cur_w(c, f);
+  const dim3 g = grid3(c, c.nx + 1);
+  e.gx = (int)g.x;
+  e.gy = (int)g.y;
+  e.gz = (int)g.z;
+  return e;
+}
+
+template <class T>
+void launch_rhs_cases(const RhsCase<T>* table, int ncases, int total, int blocks, cudaStream_t s) {
+  k_rhs_cases<T><<<blocks, dim3(TK, TJ), 0, s>>>(table, ncases, total);
+}
+
 template <class T>
 void launch_outflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s) {
   k_outflow<T><<<outflow_blocks(c), OUT_THREADS, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
@@ -1919,22 +1993,34 @@ void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial,
   launch_div(c, f, cur, initial, s);
 }
 
+// phi = phi_a + phi_b when phi_b is given (the mixed solve's predictor and
+// correction), phi_a = f.phi when not given
 template <class T>
-void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
+void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s,
+                         const T* phi_a, const T* phi_b) {
+  if (!phi_a) phi_a = f.phi;
   if (const int tj = run_rows<T>(c)) {
-    k_project_vec<T><<<dim3(c.ny / tj, (c.nx + 1 + RUN_XCH - 1) / RUN_XCH), RunTile<T>::THREADS, 0,
-                       s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.u[cur ^ 1], f.v[cur ^ 1],
-                            f.w[cur ^ 1], f.phi, f.p, f.partial, initial ? 1 : 0);
+    const dim3 grid(c.ny / tj, (c.nx + 1 + RUN_XCH - 1) / RUN_XCH);
+    if (phi_b)
+      k_project_vec<T, true><<<grid, RunTile<T>::THREADS, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
+                                                                 f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1],
+                                                                 phi_a, phi_b, f.p, f.partial, initial ? 1 : 0);
+    else
+      k_project_vec<T, false><<<grid, RunTile<T>::THREADS, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
+                                                                  f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1],
+                                                                  phi_a, nullptr, f.p, f.partial,
+                                                                  initial ? 1 : 0);
     return;
   }
   k_project<T><<<grid3(c, c.nx + 1), dim3(TK, TJ), 0, s>>>(
-      c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1], f.phi, f.p,
+      c, f.prm, f.u[cur], f.v[cur], f.w[cur], f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1], phi_a, phi_b, f.p,
       f.partial, initial ? 1 : 0);
 }
 
 template <class T>
-void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s) {
-  launch_project_only(c, f, cur, initial, s);
+void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s,
+                    const T* phi_a, const T* phi_b) {
+  launch_project_only(c, f, cur, initial, s, phi_a, phi_b);
   if (!initial) k_end_step<<<1, 1, 0, s>>>(f.prm);
 }
 
@@ -1967,6 +2053,8 @@ template int partial_count<double>(const Consts&);
 #define INST(T)                                                                                \
   template void launch_begin_step<T>(const Consts&, const Fields<T>&, cudaStream_t);           \
   template void launch_rhs<T>(const Consts&, const Fields<T>&, int, cudaStream_t);             \
+  template RhsCase<T> rhs_case<T>(const Consts&, const Fields<T>&, int);                       \
+  template void launch_rhs_cases<T>(const RhsCase<T>*, int, int, int, cudaStream_t);          \
   template void launch_af_tables<T>(const Consts&, const Fields<T>&, cudaStream_t);             \
   template void launch_inflow<T>(const Consts&, const Fields<T>&, int, cudaStream_t);           \
   template void launch_outflow<T>(const Consts&, const Fields<T>&, int, cudaStream_t);         \
@@ -1977,9 +2065,11 @@ template int partial_count<double>(const Consts&);
   template bool launch_af_yz<T>(const Consts&, const Fields<T>&, int, cudaStream_t);           \
   template void launch_mass<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
   template void launch_div<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t);       \
-  template void launch_project_only<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t); \
+  template void launch_project_only<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t, const T*, \
+                                       const T*);                                                  \
   template void launch_mass_div<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t);  \
-  template void launch_project<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t);   \
+  template void launch_project<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t, const T*, \
+                                  const T*);                                                       \
   template void launch_stats<T>(const Consts&, const Fields<T>&, int, double*, cudaStream_t);
 INST(double)
 INST(float)

@@ -365,24 +365,35 @@ __device__ inline int bar_stencil(const Markers& m, const TileBox& bx, const T* 
 }
 
 // rows (component, x, y) of the tile box, one warp per row, lanes along z;
-// f(box index, field index or -1, component)
+// f(box index, field index or -1, component). The row coordinates advance
+// by the warp count with carries (no divisions); a tile starts inside the
+// periodic range and spans at most its own length beyond it, so one
+// conditional wrap per coordinate suffices.
 template <class F>
 __device__ inline void for_box_rows(const Consts& c, const TileBox& bx, F f) {
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int rows = 3 * bx.bx * bx.by;
-  for (int row = threadIdx.x >> 5; row < rows; row += nw) {
-    const int comp = row / (bx.bx * bx.by);
-    const int rr = row - comp * bx.bx * bx.by;
-    const int a = rr / bx.by, bb = rr - a * bx.by;
+  int row = threadIdx.x >> 5;
+  int comp = 0, a = 0, bb = row;
+  while (bb >= bx.by) {
+    bb -= bx.by;
+    if (++a == bx.bx) a = 0, ++comp;
+  }
+  int k = bx.oz + lane;
+  if (k < 0) k += c.nz;
+  if (k >= c.nz) k -= c.nz;
+  const bool lane_on = lane < bx.bz;
+  for (; row < rows; row += nw) {
     const int i = bx.ox + a;
+    int j = bx.oy + bb;
+    if (j < 0) j += c.ny;
+    if (j >= c.ny) j -= c.ny;
     const bool xin = i >= (comp == 0 ? 1 : 0) && i <= c.nx - 1;
-    const int j = pos_mod(bx.oy + bb, c.ny);
-    const long long rowbase = xin ? (long long)idx3(c, i, j, 0) : -1;
-    for (int e = lane; e < bx.bz; e += 32) {
-      int k = bx.oz + e;
-      while (k < 0) k += c.nz;
-      while (k >= c.nz) k -= c.nz;
-      f(row * bx.bz + e, rowbase >= 0 ? rowbase + k : -1ll, comp);
+    if (lane_on) f(row * bx.bz + lane, xin ? (long long)idx3(c, i, j, k) : -1ll, comp);
+    bb += nw;
+    while (bb >= bx.by) {
+      bb -= bx.by;
+      if (++a == bx.bx) a = 0, ++comp;
     }
   }
 }

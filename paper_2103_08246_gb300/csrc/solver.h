@@ -82,11 +82,28 @@ struct Flag {
   int cluster = 1;            // CTAs cooperating in the structure kernel
 };
 
+// one case of a batched explicit stage: its constants, step parameters,
+// fields of the current buffer parity, its block grid (x, y, z) and the index
+// of its first block in the concatenated block list
+template <class T>
+struct RhsCase {
+  Consts c;
+  const Params* prm;
+  const T *u, *v, *w, *p;
+  T *n0, *n1, *n2, *d0, *d1, *d2;
+  const T *vin, *win;
+  int gx, gy, gz, first;
+};
+
 // ---- fluid.cu
 template <class T> void launch_begin_step(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_af_tables(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_inflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
+template <class T> RhsCase<T> rhs_case(const Consts& c, const Fields<T>& f, int cur);
+// the explicit stage of every case of `table` (device memory, ncases
+// entries, `first` set) in one persistent launch of `blocks` blocks
+template <class T> void launch_rhs_cases(const RhsCase<T>* table, int ncases, int total, int blocks, cudaStream_t s);
 template <class T> void launch_outflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_af(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_af_x(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
@@ -96,9 +113,11 @@ template <class T> bool launch_af_yz(const Consts& c, const Fields<T>& f, int cu
 template <class T> bool launch_dht2d(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_mass(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
-template <class T> void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
+template <class T> void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s,
+                                            const T* phi_a = nullptr, const T* phi_b = nullptr);
 template <class T> void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
-template <class T> void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
+template <class T> void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s,
+                                       const T* phi_a = nullptr, const T* phi_b = nullptr);
 template <class T>
 int partial_count(const Consts& c);
 size_t poisson_table_size(const Consts& c);
@@ -109,7 +128,7 @@ bool tc_supported(int n);
 size_t tc_h_image_bytes(int n);
 void tc_pack_hartley(int n, unsigned char* img, cudaStream_t s);
 bool tc_rows_times_h_t(const float* X, const unsigned char* himg, float* out, int planes, int n, int* error,
-                       cudaStream_t s);
+                       cudaStream_t s, bool single = false, int sm_reserved = 0);
 void tc_gemm_set_attributes();
 int outflow_blocks(const Consts& c);
 void fluid_set_attributes();
@@ -125,6 +144,7 @@ template <class T> void launch_poisson_table(const Consts& c, const Fields<T>& f
 void poisson_set_attributes();
 
 // ---- mixed.cu
+// leaves phi = e[1] + e[2] (predictor + correction; the projection sums them)
 void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* Hy,
                           const float* Hz, const unsigned char* Hy_img, const unsigned char* Hz_img,
                           cudaStream_t s);

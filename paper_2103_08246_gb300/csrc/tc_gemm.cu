@@ -64,15 +64,21 @@ constexpr int TC_EPI0 = 2 + TC_CONV_WARPS;         // first epilogue warp
 constexpr uint32_t A_TILE = TC_M * TC_KB * 4;      // one raw block (or one e / o part): 8 KB
 constexpr uint32_t A_LBO = TC_M * 16;              // K-adjacent core matrices of A
 constexpr uint32_t SMEM_BUDGET = 192 * 1024;
-template <int N>
+// SPLIT = 3: the three split products (FP32-class result); SPLIT = 1: the
+// single product a_hi b_hi (TF32-class, about 2^-11 relative), half the
+// shared-memory bytes per stage and so twice the stages in flight
+template <int N, int SPLIT = 3>
 struct TcCfg {
   static constexpr int MH = N / 2;                              // m: the contractions' K and N
   static constexpr uint32_t B_PART = (uint32_t)MH * TC_KB * 4;  // one of cos_hi, cos_lo, sin_hi, sin_lo
   static constexpr uint32_t B_LBO = (uint32_t)MH * 16;
-  static constexpr uint32_t B_TX = 4 * B_PART;
-  // e_hi (over raw block j), o_hi (over raw block n/16-1-j), e_lo, o_lo, then the B parts
-  static constexpr uint32_t STAGE = 4 * A_TILE + B_TX;
-  static constexpr int STAGES = SMEM_BUDGET / STAGE > 3 ? 3 : (int)(SMEM_BUDGET / STAGE);
+  static constexpr uint32_t B_TX = (SPLIT == 3 ? 4 : 2) * B_PART;
+  // e_hi (over raw block j), o_hi (over raw block n/16-1-j), [e_lo, o_lo,] then the B parts
+  static constexpr uint32_t A_PARTS = SPLIT == 3 ? 4 : 2;
+  static constexpr uint32_t STAGE = A_PARTS * A_TILE + B_TX;
+  static constexpr int MAX_STAGES = SPLIT == 3 ? 3 : 6;
+  static constexpr int STAGES =
+      SMEM_BUDGET / STAGE > MAX_STAGES ? MAX_STAGES : (int)(SMEM_BUDGET / STAGE);
   static constexpr uint32_t SMEM = STAGES * STAGE;
   static constexpr uint32_t TMEM_COLS = 4 * MH;                 // two buffers of C and S
   static constexpr int NS = N / 32;                             // stages per tile
@@ -139,9 +145,9 @@ struct TcArgs {
   int* error;
 };
 
-template <int N>
+template <int N, int SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, const __grid_constant__ CUtensorMap xmap) {
-  using C = TcCfg<N>;
+  using C = TcCfg<N, SPLIT>;
   constexpr int MH = C::MH, ST = C::STAGES;
   extern __shared__ __align__(1024) unsigned char tsm[];
   __shared__ uint64_t full[ST], conv[ST], empty[ST], tfull[2], tempty[2], xfull[2], xempty[2];
@@ -185,7 +191,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, cons
         mbar_arrive_expect_tx(&full[s], 2 * A_TILE + C::B_TX);
         tma_load_3d(st, &xmap, 0, m0, js * (TC_KB / 4), &full[s]);
         tma_load_3d(st + A_TILE, &xmap, 0, m0, (C::NB - 1 - js) * (TC_KB / 4), &full[s]);
-        bulk_g2s_u32(st + 4 * A_TILE, g.img + (size_t)js * C::B_TX, C::B_TX, &full[s]);
+        // the image holds cos_hi, cos_lo, sin_hi, sin_lo per stage slice
+        const unsigned char* slice = g.img + (size_t)js * 4 * C::B_PART;
+        if constexpr (SPLIT == 3) {
+          bulk_g2s_u32(st + C::A_PARTS * A_TILE, slice, C::B_TX, &full[s]);
+        } else {
+          bulk_g2s_u32(st + C::A_PARTS * A_TILE, slice, C::B_PART, &full[s]);
+          bulk_g2s_u32(st + C::A_PARTS * A_TILE + C::B_PART, slice + 2 * C::B_PART, C::B_PART, &full[s]);
+        }
       }
     }
   } else if (warp == 1) {
@@ -201,17 +214,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, cons
         const uint32_t dc = tmem + (uint32_t)((lt & 1) * 2 * MH), ds = dc + (uint32_t)MH;
         const uint32_t eh = sbase + (uint32_t)s * C::STAGE, oh = eh + A_TILE, el = eh + 2 * A_TILE,
                        ol = eh + 3 * A_TILE;
-        const uint32_t ch = eh + 4 * A_TILE, cl = ch + C::B_PART, sh = cl + C::B_PART, sl = sh + C::B_PART;
+        const uint32_t ch = eh + C::A_PARTS * A_TILE;
+        const uint32_t cl = ch + C::B_PART, sh = SPLIT == 3 ? cl + C::B_PART : ch + C::B_PART,
+                       sl = sh + C::B_PART;
 #pragma unroll
         for (int kk = 0; kk < TC_KB / 8; ++kk) {   // K = 8: two K-groups per instruction
           const uint32_t ka = (uint32_t)kk * 2 * A_LBO, kb2 = (uint32_t)kk * 2 * C::B_LBO;
           const uint32_t first = (js == 0 && kk == 0) ? 0u : 1u;
           tc_mma(dc, tc_desc(eh + ka, A_LBO, 128), tc_desc(ch + kb2, C::B_LBO, 128), idesc, first);
-          tc_mma(dc, tc_desc(eh + ka, A_LBO, 128), tc_desc(cl + kb2, C::B_LBO, 128), idesc, 1u);
-          tc_mma(dc, tc_desc(el + ka, A_LBO, 128), tc_desc(ch + kb2, C::B_LBO, 128), idesc, 1u);
+          if constexpr (SPLIT == 3) {
+            tc_mma(dc, tc_desc(eh + ka, A_LBO, 128), tc_desc(cl + kb2, C::B_LBO, 128), idesc, 1u);
+            tc_mma(dc, tc_desc(el + ka, A_LBO, 128), tc_desc(ch + kb2, C::B_LBO, 128), idesc, 1u);
+          }
           tc_mma(ds, tc_desc(oh + ka, A_LBO, 128), tc_desc(sh + kb2, C::B_LBO, 128), idesc, first);
-          tc_mma(ds, tc_desc(oh + ka, A_LBO, 128), tc_desc(sl + kb2, C::B_LBO, 128), idesc, 1u);
-          tc_mma(ds, tc_desc(ol + ka, A_LBO, 128), tc_desc(sh + kb2, C::B_LBO, 128), idesc, 1u);
+          if constexpr (SPLIT == 3) {
+            tc_mma(ds, tc_desc(oh + ka, A_LBO, 128), tc_desc(sl + kb2, C::B_LBO, 128), idesc, 1u);
+            tc_mma(ds, tc_desc(ol + ka, A_LBO, 128), tc_desc(sh + kb2, C::B_LBO, 128), idesc, 1u);
+          }
         }
         tc_commit_to(&empty[s]);
         if (js == C::NS - 1) tc_commit_to(&tfull[lt & 1]);
@@ -255,10 +274,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, cons
         uint4 lo;
         const uint4 he = split_hi(ve, lo);
         *reinterpret_cast<uint4*>(st + kg * A_LBO + t * 16) = he;
-        *reinterpret_cast<uint4*>(st + 2 * A_TILE + kg * A_LBO + t * 16) = lo;
+        if constexpr (SPLIT == 3) *reinterpret_cast<uint4*>(st + 2 * A_TILE + kg * A_LBO + t * 16) = lo;
         const uint4 ho = split_hi(vo, lo);
         *reinterpret_cast<uint4*>(st + A_TILE + kg * A_LBO + t * 16) = ho;
-        *reinterpret_cast<uint4*>(st + 3 * A_TILE + kg * A_LBO + t * 16) = lo;
+        if constexpr (SPLIT == 3) *reinterpret_cast<uint4*>(st + 3 * A_TILE + kg * A_LBO + t * 16) = lo;
       }
       fence_proxy_async_smem();   // generic-proxy writes -> visible to the tensor core
       if (js == C::NS - 1) {
@@ -564,23 +583,30 @@ bool encode_xmap(CUtensorMap* m, const float* X, int M, int n) {
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// persistent grids: one CTA per SM, leaving `reserved` SMs to a concurrent kernel
+int persistent_grid(int ntiles, int reserved) {
+  int n = sm_count() - reserved;
+  if (n < sm_count() / 2) n = sm_count() / 2;
+  return ntiles < n ? ntiles : n;
+}
+
 template <int N>
-bool launch_direct(const float* X, const direct::DArgs& g, cudaStream_t s) {
+bool launch_direct(const float* X, const direct::DArgs& g, cudaStream_t s, int reserved) {
   CUtensorMap m;
   if (!encode_xmap(&m, X, g.M, N)) return false;
   const int ntiles = (g.M + TC_M - 1) / TC_M;
-  const int grid = ntiles < sm_count() ? ntiles : sm_count();
+  const int grid = persistent_grid(ntiles, reserved);
   direct::k_gemm_tc_direct<N><<<grid, direct::D_THREADS, direct::DCfg<N>::SMEM, s>>>(g, m);
   return true;
 }
 
-template <int N>
-bool launch_tc(const float* X, const TcArgs& g, cudaStream_t s) {
+template <int N, int SPLIT>
+bool launch_tc(const float* X, const TcArgs& g, cudaStream_t s, int reserved) {
   CUtensorMap m;
   if (!encode_xmap(&m, X, g.M, N)) return false;
   const int ntiles = (g.M + TC_M - 1) / TC_M;
-  const int grid = ntiles < sm_count() ? ntiles : sm_count();
-  k_gemm_tc_tf32x3<N><<<grid, TC_THREADS, TcCfg<N>::SMEM, s>>>(g, m);
+  const int grid = persistent_grid(ntiles, reserved);
+  k_gemm_tc_tf32x3<N, SPLIT><<<grid, TC_THREADS, TcCfg<N, SPLIT>::SMEM, s>>>(g, m);
   return true;
 }
 
@@ -608,28 +634,32 @@ void tc_pack_hartley(int n, unsigned char* img, cudaStream_t s) {
 // contiguous values), n = 32, 64, 128 or 256, H the n-point Hartley matrix
 // given by its pre-split image (tc_pack_hartley): the even/odd form at 256,
 // the direct form below; X, out 16-byte aligned, out distinct from X. error:
-// device flag that receives ERR_TIMEOUT if a bounded wait runs out. Returns
-// false (nothing launched) for other n or when the tensor map cannot be
-// encoded.
+// device flag that receives ERR_TIMEOUT if a bounded wait runs out. single:
+// the single TF32 product at 256 (the refinement's predictor); the split
+// products otherwise. sm_reserved: SMs held by a concurrent kernel, which
+// the persistent grid leaves free. Returns false (nothing launched) for other
+// n or when the tensor map cannot be encoded.
 bool tc_rows_times_h_t(const float* X, const unsigned char* img, float* out, int planes, int n, int* error,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool single, int sm_reserved) {
   if (planes <= 0) return tc_supported(n);
   if (n == 256) {
     TcArgs g{img, out, planes * n, error};
-    return launch_tc<256>(X, g, s);
+    return single ? launch_tc<256, 1>(X, g, s, sm_reserved) : launch_tc<256, 3>(X, g, s, sm_reserved);
   }
   direct::DArgs d{img, out, planes * n, error};
   switch (n) {
-    case 32: return launch_direct<32>(X, d, s);
-    case 64: return launch_direct<64>(X, d, s);
-    case 128: return launch_direct<128>(X, d, s);
+    case 32: return launch_direct<32>(X, d, s, sm_reserved);
+    case 64: return launch_direct<64>(X, d, s, sm_reserved);
+    case 128: return launch_direct<128>(X, d, s, sm_reserved);
     default: return false;
   }
 }
 
 void tc_gemm_set_attributes() {
-  cudaFuncSetAttribute(k_gemm_tc_tf32x3<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)TcCfg<256>::SMEM);
+  cudaFuncSetAttribute(k_gemm_tc_tf32x3<256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TcCfg<256, 3>::SMEM);
+  cudaFuncSetAttribute(k_gemm_tc_tf32x3<256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)TcCfg<256, 1>::SMEM);
   cudaFuncSetAttribute(direct::k_gemm_tc_direct<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)direct::DCfg<32>::SMEM);
   cudaFuncSetAttribute(direct::k_gemm_tc_direct<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
