@@ -96,3 +96,42 @@ def test_autotuner_returns_candidates(lib, tmp_path):
     assert tiles["afx_planes"] in autotune.CANDIDATES["afx_planes"]
     again = autotune.tune(wl, binding.IBM_FP32, cache_path=str(tmp_path / "c.json"))
     assert again == tiles
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_batched_explicit_stage_equals_graph_ensemble(lib, precision):
+    """The ensemble with every member's explicit stage in one persistent
+    case-table launch steps like the graph-of-graphs ensemble (FP64 to
+    1e-12 relative: the generic explicit-stage kernel differs from the
+    specialised ones only in rounding order; FP32 and mixed to 1e-5), and an
+    FP64 member still matches the oracle to 1e-9."""
+    from oracle.solver import OracleSolver
+    from paper_2103_08246_gb300 import binding, inputs
+    prec = {"fp64": binding.IBM_FP64, "fp32": binding.IBM_FP32, "mixed": binding.IBM_MIXED}[precision]
+    cases = _cases() + [inputs.small(16, 32, 32, bars_on=True, bar_x=1.0, seed=7)]
+    mk = lambda: [binding.Solver(wl, prec, noise=inputs.initial_noise(wl, amp=0.05)) for wl in cases]  # noqa: E731
+    ref, bat = mk(), mk()
+    e_ref = binding.Ensemble(ref)
+    e_bat = binding.Ensemble(bat, batched=True)
+    e_ref.step(5, dt=2e-3)
+    e_bat.step(5, dt=2e-3)
+    tol = 1e-12 if prec == binding.IBM_FP64 else 1e-5
+    for a, b in zip(ref, bat):
+        for fa, fb in zip(a.fields(), b.fields()):
+            assert np.abs(fb - fa).max() <= tol * max(np.abs(fa).max(), 1.0)
+        if a.nf:
+            assert np.abs(a.flag()[0] - b.flag()[0]).max() < tol
+    if prec == binding.IBM_FP64:
+        ora = OracleSolver(cases[0], inputs.initial_noise(cases[0], amp=0.05))
+        ora.run(5, 2e-3)
+        for g, o in zip(bat[0].fields()[:3], ora.fields()[:3]):
+            assert _rel(g, o) < 1e-9
+    # an odd number of steps, then more: the parities of the two graphs stay in step
+    e_ref.step(3, dt=2e-3)
+    e_bat.step(3, dt=2e-3)
+    for a, b in zip(ref, bat):
+        assert np.abs(b.fields()[0] - a.fields()[0]).max() <= tol * 2.0
+    for e in (e_ref, e_bat):
+        e.close()
+    for s in ref + bat:
+        s.close()
