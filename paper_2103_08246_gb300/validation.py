@@ -152,10 +152,10 @@ def precision_comparison(steps=12000, discard=4000, cells_per_length=32, dt=6e-3
     for key in ("period", "amplitude"):
         sd = ref["cyc"].get(key + "_std")
         out["fp64"][key + "_sampling_err"] = (sd / np.sqrt(ref["cyc"]["cycles"])) if sd is not None else None
-    # the trailing-edge trajectories, every 10th sample (t, fp64, and each other precision)
-    sub = slice(None, None, 10)
-    out["te_series"] = {"t": ref["t"][sub].tolist(), "component": ref["comp"],
-                        **{name: runs[name]["te"][sub, ref["comp"]].tolist() for name in precisions}}
+    # the trailing-edge trajectories, every 30th sample (t, fp64, and each other precision)
+    sub = slice(None, None, 30)
+    out["te_series"] = {"t": np.round(ref["t"][sub], 6).tolist(), "component": ref["comp"],
+                        **{name: np.round(runs[name]["te"][sub, ref["comp"]], 6).tolist() for name in precisions}}
     for name in precisions:
         if name == "fp64":
             continue
