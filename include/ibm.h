@@ -324,7 +324,9 @@ int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms);
  * (ceil(nz/32) * ceil(ny/8) * ceil((nx+1)/8)) are rejected with IBM_EINVAL.
  * The first call on a device looks the array's device address up once
  * (with that device current); make that first call before any stream
- * capture. Every call shares the array and overwrites all of it that it
+ * capture. The looked-up address is kept for the life of the process: after
+ * cudaDeviceReset it is stale, and the library must not be used on that
+ * device again. Every call shares the array and overwrites all of it that it
  * reads, so no clearing is needed; calls that overlap on the GPU (from two
  * streams or threads) race on it. Synchronises the state's stream. */
 int ibm_stats_static(ibm_state* s, ibm_stats_t* out);

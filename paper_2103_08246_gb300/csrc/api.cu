@@ -1733,6 +1733,8 @@ constexpr int kStatsMaxBlocks = 1 << 16;
 constexpr int kStatsScratch = 2 * kStatsMaxBlocks + 16;
 __device__ __align__(256) double g_stats_scratch[kStatsScratch];
 constexpr int kMaxDevices = 64;
+// the array's device address per device, looked up on the first call there;
+// concurrent first calls store the same value; stale after cudaDeviceReset
 double* g_stats_dev_ptr[kMaxDevices] = {nullptr};
 
 constexpr int kSTK = 32, kSTJ = 8, kSX = 8;   // block tile of the first pass

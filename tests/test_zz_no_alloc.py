@@ -52,9 +52,15 @@ def test_static_stats_match_workspace_stats(lib, precision):
     s.step(4)
     ref = binding.ibm_stats(s.state)
     first = binding.ibm_stats_static(s.state)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
     second = binding.ibm_stats_static(s.state)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
     _same(ref, first)
     _same(ref, second)
+    # the second call allocates nothing on the device
+    assert free_after == free_before, (free_before, free_after)
     # and after further steps (the array keeps the last call's contents)
     s.step(3)
     ref2 = binding.ibm_stats(s.state)
