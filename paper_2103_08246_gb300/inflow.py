@@ -20,7 +20,7 @@ learned generator of the C ABI (``ibm_gen_*``):
    G  generated inflow: a 384 x 256 x 256 domain of length 6 without bars,
       flag at 1, inflow planes from the generator rollout: a keyframe every
       s steps (seeded with the last two recorded keyframes, relaxed towards
-      the record's time-mean plane at 5% per keyframe), the planes in
+      the record's time-mean plane at 1% per keyframe), the planes in
       between interpolated linearly in time;
    U  uniform inflow on the same domain;
    W  white-noise inflow on the same domain: independent Gaussian planes
@@ -334,7 +334,7 @@ def compare(res, x_st, x0):
 
 def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3000, blocks=13, batch=8,
              precision=binding.IBM_FP32, seed=0, log=print, base=inputs.PRODUCTION, sample_every=10,
-             re=None, noise=0.03, stride=10, relax=0.05):
+             re=None, noise=0.03, stride=10, relax=0.01):
     import torch
     prod = base if re is None else base.replace(re=float(re))
     out = {"bounds": BOUNDS, "workload": base.name, "re": prod.re, "train_noise": noise, "stride": stride,
@@ -442,7 +442,7 @@ def main(argv=None):
     ap.add_argument("--re", type=float, default=None, help="Reynolds number of every run (default: the workload's)")
     ap.add_argument("--noise", type=float, default=0.03, help="training-input noise, normalised units")
     ap.add_argument("--stride", type=int, default=10, help="solver steps between generated keyframes")
-    ap.add_argument("--relax", type=float, default=0.05,
+    ap.add_argument("--relax", type=float, default=0.01,
                     help="rollout relaxation rate per keyframe towards the record's time-mean plane")
     ap.add_argument("--out", default="inflow_campaign.json")
     a = ap.parse_args(argv)
