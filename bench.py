@@ -61,12 +61,18 @@ PER_STEP = {
 # projection 9): the step's roofline counts these bytes whatever the fusion.
 # The mixed path adds its refinement: the residual (3) and a second solve (10).
 METHOD_PASSES = {"fp32": 57, "mixed": 70}
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# production FP32 kernels, from one single-pass ncu capture at full size
-# (profiles/dram_traffic_production_fp32.md); valid for the kernels of that
-# capture and to be refreshed whenever one of them changes.
-TRAFFIC_BYTES = {"rhs": 1743.7e6, "project": 1199.9e6, "af_yz": 1156.7e6, "af_x": 755.0e6,
-                 "mass_div": 520.9e6, "poisson_x": 408.2e6, "dht2d": 205.8e6}
+# DRAM bytes per launch of a stage (dram__bytes_read.sum +
+# dram__bytes_write.sum, both launches for "ib") from single-pass ncu
+# captures of every launch of the production FP32 and mixed steps
+# (profiles/launches_production_fp32.md, launches_production_mixed.md);
+# valid for the kernels of those captures and to be refreshed whenever one
+# of them changes.
+_TRAFFIC_COMMON = {"rhs": 1742.9e6, "af_yz": 1156.4e6, "af_x": 753.6e6, "mass_div": 519.3e6,
+                   "poisson_x": 405.3e6, "ib": 57.9e6}
+TRAFFIC_BYTES = {
+    "fp32": dict(_TRAFFIC_COMMON, project=1200.9e6, dht2d=204.2e6),
+    "mixed": dict(_TRAFFIC_COMMON, project=1394.6e6, tc_pass=215.1e6, tc_pass1=214.2e6, residual=374.2e6),
+}
 # FP64 path: the explicit stage's FP64 instructions per cell (DFMA + DMUL +
 # DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of
 # GB300 (2 per clock per SM): the FP64 step is bound by that pipe.
@@ -456,7 +462,7 @@ def stage_roofline(wl, precision, peak_gbs, peak_kind):
         gbs = nbytes / (stages[k] * 1e-3) / 1e9
         kernels[k] = {"ms_per_launch": stages[k], "launches_per_step": PER_STEP[key][k],
                       "alg_bytes_per_launch": nbytes, "achieved_gbs": gbs, "frac": gbs / peak_gbs,
-                      "traffic": TRAFFIC_BYTES.get(k) if key == "fp32" else None}
+                      "traffic": TRAFFIC_BYTES[key].get(k)}
     kernels["ib"]["nodes_touched"] = ib_nodes
     dom = max((k for k in kernels if k != "ib"), key=lambda k: per_step[k])
     d = kernels[dom]
