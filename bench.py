@@ -54,7 +54,7 @@ PER_STEP = {
     "fp32": {"rhs": 1, "outflow": 1, "af_x": 1, "af_yz": 1, "ib": 1, "flag": 1, "mass_div": 1,
              "dht2d": 2, "poisson_x": 1, "project": 1},
     "mixed": {"rhs": 1, "outflow": 1, "af_x": 1, "af_yz": 1, "ib": 1, "flag": 1, "mass_div": 1,
-              "tc_pass": 4, "tc_pass1": 4, "poisson_x": 2, "residual": 1, "project": 1},
+              "dht2d": 2, "tc_pass1": 4, "poisson_x": 2, "residual": 1, "project": 1},
 }
 # The method's unfused field passes per step (explicit stage 13, three
 # implicit factors 21, mass fix and divergence 4, pressure solve 10,
@@ -70,8 +70,8 @@ METHOD_PASSES = {"fp32": 57, "mixed": 70}
 _TRAFFIC_COMMON = {"rhs": 1742.9e6, "af_yz": 1156.4e6, "af_x": 753.6e6, "mass_div": 519.3e6,
                    "poisson_x": 405.3e6, "ib": 57.9e6}
 TRAFFIC_BYTES = {
-    "fp32": dict(_TRAFFIC_COMMON, project=1200.9e6, dht2d=204.2e6),
-    "mixed": dict(_TRAFFIC_COMMON, project=1394.6e6, tc_pass=215.1e6, tc_pass1=214.2e6, residual=374.2e6),
+    "fp32": dict(_TRAFFIC_COMMON, project=1200.9e6),
+    "mixed": dict(_TRAFFIC_COMMON, project=1394.6e6, tc_pass1=214.2e6, residual=374.2e6),
 }
 # FP64 path: the explicit stage's FP64 instructions per cell (DFMA + DMUL +
 # DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of

@@ -174,6 +174,14 @@ typedef struct {
    * cell's solid fraction (zero inside the solid); the bars then carry no
    * markers. [0] */
   int bar_forcing;
+  /* IBM_MIXED with 256 x 256 transverse planes. 0: the refinement's
+   * predictor is the FP32 FFT solve and the correction's transforms run on
+   * the tensor cores with the single TF32 product. 1: both solves on the
+   * tensor cores, the predictor with the single and the correction with the
+   * split TF32 products. Both leave the FP32 rounding of the stored result
+   * as the error (the final error is the product of the two solves' relative
+   * errors); 0 is faster. Other plane sizes always take 1's scheme. [0] */
+  int mixed_tc_predictor;
 } ibm_options;
 
 /* Diagnostics read by ibm_stats (all FP64). */

@@ -67,7 +67,8 @@ class ibm_options(ctypes.Structure):
                 ("init_u", _dp), ("init_v", _dp), ("init_w", _dp),
                 ("rhs_planes", ctypes.c_int), ("afx_planes", ctypes.c_int),
                 ("rhs_stages", ctypes.c_int), ("deterministic", ctypes.c_int),
-                ("inflow", ctypes.c_int), ("bar_forcing", ctypes.c_int)]
+                ("inflow", ctypes.c_int), ("bar_forcing", ctypes.c_int),
+                ("mixed_tc_predictor", ctypes.c_int)]
 
 
 class ibm_gen_config(ctypes.Structure):
@@ -458,7 +459,7 @@ class Solver:
 
     def __init__(self, wl: Workload, precision: int = IBM_FP64, noise=None, stream=None,
                  cfl: float | None = None, cfl_limit: float = 2.0, tiles=None,
-                 deterministic: bool = False, inflow: bool = False):
+                 deterministic: bool = False, inflow: bool = False, tc_predictor: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("the solver needs a CUDA device")
@@ -475,7 +476,8 @@ class Solver:
                            *([_ptr(a) for a in self._noise] if self._noise else [None] * 3),
                            int(tiles.get("rhs_planes", 0)), int(tiles.get("afx_planes", 0)),
                            int(tiles.get("rhs_stages", 0)), 1 if deterministic else 0,
-                           1 if inflow else 0, 1 if wl.bar_forcing == "eulerian" else 0)
+                           1 if inflow else 0, 1 if wl.bar_forcing == "eulerian" else 0,
+                           1 if tc_predictor else 0)
         self.ws_bytes = ibm_workspace_bytes(self.grid, self.dom, self.bodies, opts)
         self.workspace = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device="cuda")
         torch.cuda.synchronize()

@@ -392,6 +392,7 @@ int check_args(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, cons
       return IBM_EINVAL;
     if (o->cfl < 0 || o->cfl_limit < 0) return IBM_EINVAL;
     if (o->bar_forcing != 0 && o->bar_forcing != 1) return IBM_EINVAL;
+    if (o->mixed_tc_predictor != 0 && o->mixed_tc_predictor != 1) return IBM_EINVAL;
   }
   return IBM_OK;
 }
@@ -805,6 +806,7 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   c.rhs_planes = (o && o->rhs_planes > 0) ? o->rhs_planes : 16;
   c.rhs_stages = (o && o->rhs_stages > 0) ? o->rhs_stages : 8;
   c.afx_planes = (o && o->afx_planes > 0) ? o->afx_planes : 64;
+  c.mixed_tc = o ? o->mixed_tc_predictor : 0;
   bar_dv = 0.0;
   if (b->flag_on) fg = build_flag(*b, *d, c.h);
   if (b->bars_on && s->bar_forcing == 1) build_bar_mask(*b, *d, *g, c.h, bm);

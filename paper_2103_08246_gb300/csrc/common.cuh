@@ -50,6 +50,7 @@ struct Consts {
   int rhs_stages;     // tile: most x planes in the streamed RHS's ring
   int afx_planes;     // tile: x planes per block of the FP32 x factor
   int sm_reserved;    // SMs the structural update holds while the pressure solve runs
+  int mixed_tc;       // mixed solve at 256 x 256: 1 = tensor-core predictor, 0 = FFT predictor
   float f_inv_h, f_inv_h2, f_nu;   // FP32 copies
 };
 

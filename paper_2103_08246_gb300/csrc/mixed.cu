@@ -1,11 +1,12 @@
-// Mixed-precision pressure solve (FP32 fields): the transverse transforms of
-// the Poisson solve (Sec. II.B projection step) are dense contractions with
-// the Hartley matrices H_n[j][k] = cas(2 pi j k / n), run on tensor cores as
-// split-TF32 GEMMs with FP32 accumulation,
-//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,  a_hi = tf32(a), a_lo = tf32(a - a_hi),
-// followed by an extended-precision (double-single, FP64-class) evaluation of
-// the residual r = D - L_h phi and one refinement sweep (the same solve
-// applied to r, phi += delta).
+// Mixed-precision pressure solve (FP32 fields): a predictor solve, an
+// extended-precision (double-single, FP64-class) evaluation of the residual
+// r = D - L_h phi and one refinement sweep (a correction solve applied to r,
+// phi += delta). The transverse transforms of the correction (and of the
+// predictor where no FFT serves the plane size) are dense contractions with
+// the Hartley matrices H_n[j][k] = cas(2 pi j k / n) (Sec. II.B projection
+// step), run on tensor cores as TF32 GEMMs with FP32 accumulation, single
+// (a_hi b_hi) or split,
+//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,  a_hi = tf32(a), a_lo = tf32(a - a_hi).
 //
 // 2-D transform of every x plane X (ny x nz, z contiguous): H_y X H_z, as
 // two GEMMs: rows (all planes at once) times H_z, then H_y times each plane.
@@ -286,13 +287,14 @@ static void transform2d(const Consts& c, const Hartley& H, const float* in, floa
 
 // e[1] + e[2] <- solution of L_h phi = D (D in f.phi on entry), mixed precision
 // with one refinement sweep on the extended-precision residual; the
-// projection sums the two parts as it reads them (no separate pass). The predictor
-// x0 only has to be close enough for the correction to absorb its error: at
-// 256 x 256 planes its transforms take the single TF32 product (relative
-// error about 2^-11); the correction solve, whose error is the result's,
-// takes the split products. x0 + t1 with t1 = L^-1 (D - L x0) leaves the
-// correction's error times the predictor's relative error. Scratch: e[0],
-// e[1], e[2].
+// projection sums the two parts as it reads them (no separate pass).
+// x0 + t1 with t1 = L^-1 (D - L x0) leaves the correction's relative error
+// times the predictor's, so one of the two solves may be coarse. At 256 x 256
+// planes the predictor is the FP32 FFT solve (one pass per 2-D transform)
+// and the correction's tensor-core transforms take the single TF32 product
+// (relative error about 2^-11); at other square sizes both solves run on the
+// tensor cores, the predictor with the single product where it exists, the
+// correction with the split products. Scratch: e[0], e[1], e[2].
 void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* Hy, const float* Hz,
                           const unsigned char* Hy_img, const unsigned char* Hz_img, cudaStream_t s) {
   const Hartley H{Hy, Hz, Hy_img, Hz_img};
@@ -302,16 +304,22 @@ void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* 
   float* t1 = f.e[2];
   int* err = &f.prm->error;
   // predictor: x0 = L^-1 D
-  transform2d(c, H, D, t0, x0, err, s, true);
-  launch_poisson_x_on(c, f, x0, s);
-  transform2d(c, H, x0, t0, x0, err, s, true);
+  const bool fft = !c.mixed_tc && launch_dht2d_on(c, f, D, x0, s);
+  if (fft) {
+    launch_poisson_x_on(c, f, x0, s);
+    launch_dht2d_on(c, f, x0, x0, s);
+  } else {
+    transform2d(c, H, D, t0, x0, err, s, true);
+    launch_poisson_x_on(c, f, x0, s);
+    transform2d(c, H, x0, t0, x0, err, s, true);
+  }
   // double-single residual and correction: t1 = L^-1 (D - L x0)
   const double ih2 = c.inv_h * c.inv_h;
   const float ih2_hi = (float)ih2, ih2_lo = (float)(ih2 - (double)ih2_hi);
   k_residual_ds4<<<dim3((c.nz / 4 + 63) / 64, c.ny, c.nx), 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, t1);
-  transform2d(c, H, t1, t0, t1, err, s);
+  transform2d(c, H, t1, t0, t1, err, s, fft);
   launch_poisson_x_on(c, f, t1, s);
-  transform2d(c, H, t1, t0, t1, err, s);
+  transform2d(c, H, t1, t0, t1, err, s, fft);
 }
 
 // the refinement's residual alone (stage timing): e[2] = D - L_h e[1]

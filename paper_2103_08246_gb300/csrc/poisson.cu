@@ -405,6 +405,190 @@ k_dht2d_256(T* __restrict__ data, const T* __restrict__ twy) {
   cl.sync();   // no tile is released while another CTA may still read it
 }
 
+// ---- FP32: both transforms of a 256 x 256 plane with thread-level radix-16
+// FFTs. Four-step form N = 16 x 16 with n = j0 + 16 m, k = k1 + 16 k2:
+//   Z(k1 + 16 k2) = sum_j0 W16^{j0 k2} W256^{j0 k1} sum_m z(j0 + 16 m) W16^{m k1}.
+// A thread holds the 16 values m of one j0 in registers, runs the inner
+// 16-point DFT there, applies W256^{j0 k1} and hands its outputs through one
+// shared-memory transpose to the thread that owns k1; that thread runs the
+// outer 16-point DFT over j0. No shuffles; every shared-memory access is a
+// warp-contiguous row. Two real lines travel as z = a + i b and are
+// separated with the Hartley identities of the file header, each thread
+// producing the outputs k and N - k from the same two values.
+//
+// A cluster of four CTAs owns a plane (input and output planes may be the
+// same or distinct). Phase y: CTA q transforms columns
+// 64 q .. 64 q + 63 (complex pairs (64 q + p, 64 q + 32 + p)) along y,
+// loading straight from global memory (lanes along z, coalesced), and
+// stores the result in a permuted order inside the plane,
+//   element (row r, column z) -> r/64 * 16384 + z/16 * 1024 + z%16 * 64 + (r/32)%2 * 32 + r%32,
+// so that phase z finds its inputs (the 16 values m of one j0, for 32 row
+// pairs across the lanes) as coalesced 128-byte rows. That region of the
+// plane is read back from L2 at once. The permuted stores of one CTA land in
+// every quarter of the plane, so in place the cluster waits until every CTA
+// has consumed its phase-y loads before anyone stores (split barrier, hidden
+// behind the transpose), and in every case again before phase z loads. Phase z: CTA q
+// transforms rows 64 q .. 64 q + 63 (pairs (64 q + p, 64 q + 32 + p)) along
+// z and stores them in natural order; the permuted block it reads is the
+// block it overwrites, so no barrier follows. Plane read and written once in
+// HBM; 64 bytes of shared-memory traffic per complex value.
+constexpr int R16_CLUSTER = 4;
+constexpr int R16_THREADS = 512;
+constexpr int R16_ROW = 257;   // complex stride of the separation buffer [32][257]
+constexpr size_t R16_SMEM = (size_t)32 * R16_ROW * sizeof(Cx<float>);   // >= the transpose's 16 x 16 x 32
+
+__device__ __forceinline__ void dft4_cx(Cx<float>& a0, Cx<float>& a1, Cx<float>& a2, Cx<float>& a3) {
+  const Cx<float> t0 = {a0.r + a2.r, a0.i + a2.i}, t1 = {a0.r - a2.r, a0.i - a2.i};
+  const Cx<float> t2 = {a1.r + a3.r, a1.i + a3.i}, t3 = {a1.r - a3.r, a1.i - a3.i};
+  a0 = {t0.r + t2.r, t0.i + t2.i};
+  a2 = {t0.r - t2.r, t0.i - t2.i};
+  a1 = {t1.r + t3.i, t1.i - t3.r};   // t1 - i t3
+  a3 = {t1.r - t3.i, t1.i + t3.r};   // t1 + i t3
+}
+
+// (a + i b) W16^e for the exponents e = n2 k1 of the 4 x 4 split
+__device__ __forceinline__ Cx<float> w16(Cx<float> a, int e) {
+  const float C = 0.92387953251128675613f, S = 0.38268343236508977173f, R = 0.70710678118654752440f;
+  switch (e) {
+    case 1: return {a.r * C + a.i * S, a.i * C - a.r * S};
+    case 2: return {(a.r + a.i) * R, (a.i - a.r) * R};
+    case 3: return {a.r * S + a.i * C, a.i * S - a.r * C};
+    case 4: return {a.i, -a.r};
+    case 6: return {(a.i - a.r) * R, -(a.r + a.i) * R};
+    case 9: return {-a.r * C - a.i * S, a.r * S - a.i * C};
+    default: return a;
+  }
+}
+
+// in-register 16-point DFT, natural order in and out: n = 4 n1 + n2,
+// k = k1 + 4 k2, a 4-point DFT over n1, twiddles W16^{n2 k1}, a 4-point DFT
+// over n2
+__device__ __forceinline__ void dft16(Cx<float> (&x)[16]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4_cx(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
+#pragma unroll
+  for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+    for (int n2 = 1; n2 < 4; ++n2) x[4 * k1 + n2] = w16(x[4 * k1 + n2], n2 * k1);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4_cx(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+  // slot 4 k1 + k2 holds Z(k1 + 4 k2): transpose the 4 x 4 index
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = a + 1; b < 4; ++b) {
+      const Cx<float> t = x[4 * a + b];
+      x[4 * a + b] = x[4 * b + a];
+      x[4 * b + a] = t;
+    }
+}
+
+__device__ __forceinline__ int r16_perm(int row, int z) {
+  return (row >> 6) * 16384 + (z >> 4) * 1024 + (z & 15) * 64 + ((row >> 5) & 1) * 32 + (row & 31);
+}
+
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Inner DFT of the thread's 16 values, the W256^{j0 k1} twiddles, the
+// transpose, and the outer DFT: on return x[k2] = Z(k1 + 16 k2) of the lane's
+// line pair, k1 = the warp index. `pre_wait` runs between the transpose's
+// stores and loads (the cluster arrive of phase y).
+template <class F>
+__device__ __forceinline__ void r16_fft(Cx<float> (&x)[16], const Cx<float>* tw, Cx<float>* buf, int w, int l,
+                                        F pre_wait) {
+  dft16(x);
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) buf[(k1 * 16 + w) * 32 + l] = k1 ? cmul(x[k1], tw[w * k1]) : x[0];   // w k1 <= 225
+  pre_wait();
+  __syncthreads();
+#pragma unroll
+  for (int j0 = 0; j0 < 16; ++j0) x[j0] = buf[(w * 16 + j0) * 32 + l];
+  dft16(x);
+  __syncthreads();   // the transpose buffer is free for the separation buffer
+}
+
+__global__ void __cluster_dims__(R16_CLUSTER, 1, 1) __launch_bounds__(R16_THREADS, 2)
+k_dht2d_r16(const float* in, float* out, const float* __restrict__ twy) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Cx<float> tw[256];
+  Cx<float>* buf = reinterpret_cast<Cx<float>*>(smem_raw);
+  const int q = (int)(blockIdx.x % R16_CLUSTER);   // rank in the cluster (clusters are consecutive blocks)
+  const size_t plane = (size_t)(blockIdx.x / R16_CLUSTER) * 65536;
+  float* P = out + plane;
+  const bool inplace = in == out;   // the same for the whole grid
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  Cx<float> x[16];
+  // ---- phase y: columns (64 q + l, 64 q + 32 + l), rows w + 16 m
+  {
+    const float* col = in + plane + 64 * q + l;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int r = w + 16 * m;
+      x[m] = {__ldcg(col + r * 256), __ldcg(col + r * 256 + 32)};
+    }
+  }
+  load_twiddles(tw, twy);   // includes __syncthreads
+  r16_fft(x, tw, buf, w, l, [inplace] {
+    if (inplace) cluster_arrive_release();   // every phase-y load consumed
+  });
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) buf[l * R16_ROW + w + 16 * k2] = x[k2];
+  __syncthreads();
+  if (inplace) cluster_wait_acquire();   // no CTA still needs an original value of this plane
+#pragma unroll
+  for (int pp = 0; pp < 2; ++pp) {
+    const int p = 2 * w + pp;
+    const Cx<float>* Zp = buf + p * R16_ROW;
+    const int za = 64 * q + p, zb = za + 32;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int k = l + 32 * v;
+      const int kr = k == 0 ? 128 : 256 - k;   // k = 0 and 128 are their own mirrors
+      const Cx<float> zk = Zp[k], zr = Zp[kr];
+      const Cx<float> mk = k == 0 ? zk : zr, mr = k == 0 ? zr : zk;
+      P[r16_perm(k, za)] = 0.5f * (zk.r - zk.i + mk.r + mk.i);
+      P[r16_perm(k, zb)] = 0.5f * (zk.r + zk.i - mk.r + mk.i);
+      P[r16_perm(kr, za)] = 0.5f * (zr.r - zr.i + mr.r + mr.i);
+      P[r16_perm(kr, zb)] = 0.5f * (zr.r + zr.i - mr.r + mr.i);
+    }
+  }
+  cluster_arrive_release();
+  cluster_wait_acquire();   // the whole plane holds the y transform (permuted)
+  // ---- phase z: rows (64 q + l, 64 q + 32 + l), columns w + 16 m
+  {
+    const float* blk = P + q * 16384 + w * 64 + l;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) x[m] = {__ldcg(blk + m * 1024), __ldcg(blk + m * 1024 + 32)};
+  }
+  r16_fft(x, tw, buf, w, l, [] {});
+#pragma unroll
+  for (int k2 = 0; k2 < 16; ++k2) buf[l * R16_ROW + w + 16 * k2] = x[k2];
+  __syncthreads();
+#pragma unroll
+  for (int pp = 0; pp < 2; ++pp) {
+    const int p = 2 * w + pp;
+    const Cx<float>* Zp = buf + p * R16_ROW;
+    float* ra = P + (size_t)(64 * q + p) * 256;
+    float* rb = ra + 32 * 256;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int k = l + 32 * v;
+      const int kr = k == 0 ? 128 : 256 - k;
+      const Cx<float> zk = Zp[k], zr = Zp[kr];
+      const Cx<float> mk = k == 0 ? zk : zr, mr = k == 0 ? zr : zk;
+      ra[k] = 0.5f * (zk.r - zk.i + mk.r + mk.i);
+      rb[k] = 0.5f * (zk.r + zk.i - mk.r + mk.i);
+      ra[kr] = 0.5f * (zr.r - zr.i + mr.r + mr.i);
+      rb[kr] = 0.5f * (zr.r + zr.i - mr.r + mr.i);
+    }
+  }
+}
+
 // Thomas solve along x per mode; rhs scaled by h^2 / (ny nz) (Hartley
 // normalisation). One thread per mode walks x (coalesced across modes) in
 // chunks of PF planes; the loads of the next chunk (right-hand side and
@@ -603,8 +787,18 @@ void launch_poisson_x(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 template <class T>
 bool launch_dht2d(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   if (c.ny != 256 || c.nz != 256) return false;
+  if constexpr (sizeof(T) == 4) {
+    k_dht2d_r16<<<c.nx * R16_CLUSTER, R16_THREADS, R16_SMEM, s>>>(f.phi, f.phi, f.tw_y);
+    return true;
+  }
   const size_t sh = (size_t)256 * 33 * sizeof(T) + (DHT2D_THREADS / 32) * WFFT_BUF * sizeof(Cx<T>);
   k_dht2d_256<T><<<c.nx * DHT2D_CLUSTER, DHT2D_THREADS, sh, s>>>(f.phi, f.tw_y);
+  return true;
+}
+
+bool launch_dht2d_on(const Consts& c, const Fields<float>& f, const float* in, float* out, cudaStream_t s) {
+  if (c.ny != 256 || c.nz != 256) return false;
+  k_dht2d_r16<<<c.nx * R16_CLUSTER, R16_THREADS, R16_SMEM, s>>>(in, out, f.tw_y);
   return true;
 }
 
@@ -649,6 +843,7 @@ template void launch_poisson_table<float>(const Consts&, const Fields<float>&, c
 void poisson_set_attributes() {
   cudaFuncSetAttribute(k_dht2d_256<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_dht2d_256<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_dht2d_r16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R16_SMEM);
   cudaFuncSetAttribute(k_dht_y256<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_dht_y256<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_dht<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -111,6 +111,8 @@ template <class T> void launch_af_y(const Consts& c, const Fields<T>& f, int cur
 template <class T> void launch_af_z(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> bool launch_af_yz(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> bool launch_dht2d(const Consts& c, const Fields<T>& f, cudaStream_t s);
+// FP32 2-D transform of every 256 x 256 plane from `in` to `out` (may alias); false for other shapes
+bool launch_dht2d_on(const Consts& c, const Fields<float>& f, const float* in, float* out, cudaStream_t s);
 template <class T> void launch_mass(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 template <class T> void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s,

@@ -635,8 +635,8 @@ void tc_pack_hartley(int n, unsigned char* img, cudaStream_t s) {
 // given by its pre-split image (tc_pack_hartley): the even/odd form at 256,
 // the direct form below; X, out 16-byte aligned, out distinct from X. error:
 // device flag that receives ERR_TIMEOUT if a bounded wait runs out. single:
-// the single TF32 product at 256 (the refinement's predictor); the split
-// products otherwise. sm_reserved: SMs held by a concurrent kernel, which
+// the single TF32 product at 256 (whichever solve of the refinement may be
+// coarse); the split products otherwise. sm_reserved: SMs held by a concurrent kernel, which
 // the persistent grid leaves free. Returns false (nothing launched) for other
 // n or when the tensor map cannot be encoded.
 bool tc_rows_times_h_t(const float* X, const unsigned char* img, float* out, int planes, int n, int* error,

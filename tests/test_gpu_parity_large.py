@@ -119,12 +119,15 @@ def production_oracle():
     return wl, noise, ora
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed", "mixed_tc"])
 def test_production_transverse_shape(lib, production_oracle, precision):
+    """mixed: FP32 FFT predictor + single-TF32 tensor-core correction (the
+    default at 256 x 256 planes); mixed_tc: both solves on the tensor cores."""
     from paper_2103_08246_gb300 import binding
     wl, noise, ora = production_oracle
-    prec = {"fp64": binding.IBM_FP64, "fp32": binding.IBM_FP32, "mixed": binding.IBM_MIXED}[precision]
-    gpu = binding.Solver(wl, prec, noise=noise)
+    prec = {"fp64": binding.IBM_FP64, "fp32": binding.IBM_FP32, "mixed": binding.IBM_MIXED,
+            "mixed_tc": binding.IBM_MIXED}[precision]
+    gpu = binding.Solver(wl, prec, noise=noise, tc_predictor=precision == "mixed_tc")
     gpu.step(wl.steps)
     st = gpu.stats()
     assert st["step"] == wl.steps and abs(st["t"] - ora.t) <= 1e-6 * ora.t
@@ -134,7 +137,7 @@ def test_production_transverse_shape(lib, production_oracle, precision):
     else:
         errs = _compare(gpu, ora, FP32_TOL, floor=FP32_FLOOR)
     gpu.close()
-    print(precision, "production-shape errors:", errs)
+    print(precision, "production-shape errors:", errs, "max_div", st["max_div"])
 
 
 def test_fp64_production_flag_65x65(lib):
