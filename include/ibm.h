@@ -88,14 +88,22 @@ extern "C" {
                                    DHT_Z and this stage launches nothing)     */
 #define IBM_STAGE_TC_PASS   15  /* one tensor-core transform pass (X H)^T over every
                                    x plane (IBM_MIXED with square planes of 32,
-                                   64, 128 or 256; otherwise nothing): the
-                                   mixed pressure solve runs eight            */
+                                   64, 128 or 256; otherwise nothing), split
+                                   products: the correction of the tensor-core
+                                   mixed solve runs four                      */
 #define IBM_STAGE_RESIDUAL  16  /* the double-single residual D - L_h phi of the
                                    mixed solve's refinement (IBM_MIXED only)  */
 #define IBM_STAGE_TC_PASS1  17  /* one single-product (TF32) transform pass, as the
-                                   mixed solve's predictor runs at 256 x 256
-                                   planes (IBM_MIXED; otherwise nothing): the
-                                   solve runs four, and four of TC_PASS       */
+                                   mixed solve's tensor-core predictor runs at
+                                   256 x 256 planes (IBM_MIXED with
+                                   mixed_tc_predictor; otherwise nothing)     */
+#define IBM_STAGE_TC_BF16   18  /* one bfloat16 transform pass, as the mixed
+                                   solve's correction runs at 256 x 256 planes
+                                   (IBM_MIXED without mixed_tc_predictor;
+                                   otherwise nothing): the solve runs four    */
+#define IBM_STAGE_POISSON_X16 19 /* the tridiagonal solves along x on bfloat16
+                                   storage, as the correction runs them (same
+                                   condition as TC_BF16)                      */
 
 /* field selectors for ibm_get_field / ibm_set_field */
 #define IBM_FIELD_U 0

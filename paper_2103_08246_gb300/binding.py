@@ -37,7 +37,8 @@ _VOID = ("ibm_destroy", "ibm_ensemble_destroy", "ibm_gen_destroy")
 
 STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
           "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11, "poisson": 12,
-          "af_yz": 13, "dht2d": 14, "tc_pass": 15, "residual": 16, "tc_pass1": 17}
+          "af_yz": 13, "dht2d": 14, "tc_pass": 15, "residual": 16, "tc_pass1": 17, "tc_bf16": 18,
+          "poisson_x16": 19}
 
 
 class ibm_grid(ctypes.Structure):

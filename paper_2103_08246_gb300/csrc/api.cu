@@ -352,6 +352,7 @@ struct ibm_state {
   float* hz = nullptr;
   unsigned char* hy_img = nullptr;        // pre-split tensor-core images of them (square planes)
   unsigned char* hz_img = nullptr;
+  unsigned char* h16_img = nullptr;       // bfloat16 cos / sin image (256 x 256 planes, bfloat16 correction)
   cudaStream_t side = nullptr;            // structural update, overlapped in the graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t side2 = nullptr;           // implicit-factor tables, overlapped with the RHS
@@ -471,6 +472,7 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
     if (c.ny == c.nz && tc_supported(c.ny)) {
       s->hy_img = cv.take<unsigned char>(tc_h_image_bytes(c.ny));
       s->hz_img = cv.take<unsigned char>(tc_h_image_bytes(c.nz));
+      if (c.ny == 256) s->h16_img = cv.take<unsigned char>(tc_bf16_image_bytes());
     }
   }
   return cv.off + 256;
@@ -562,7 +564,7 @@ void solve_poisson(ibm_state* s, cudaStream_t st) {
   Fields<T>& f = fields<T>(s);
   if constexpr (std::is_same<T, float>::value) {
     if (s->precision == IBM_MIXED) {
-      launch_poisson_mixed(s->c, f, s->hy, s->hz, s->hy_img, s->hz_img, st);
+      launch_poisson_mixed(s->c, f, s->hy, s->hz, s->hy_img, s->hz_img, s->h16_img, st);
       return;
     }
   }
@@ -574,7 +576,9 @@ void solve_poisson(ibm_state* s, cudaStream_t st) {
 template <class T>
 void project_after_solve(ibm_state* s, int cur, bool initial, cudaStream_t st) {
   Fields<T>& f = fields<T>(s);
-  if (std::is_same<T, float>::value && s->precision == IBM_MIXED)
+  if (std::is_same<T, float>::value && s->precision == IBM_MIXED && s->c.corr_bf16)
+    launch_project(s->c, f, cur, initial, st, (const T*)f.e[1], (const T*)nullptr, (const void*)f.e[2]);
+  else if (std::is_same<T, float>::value && s->precision == IBM_MIXED)
     launch_project(s->c, f, cur, initial, st, (const T*)f.e[1], (const T*)f.e[2]);
   else
     launch_project(s->c, f, cur, initial, st);
@@ -732,9 +736,11 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
     if (s->hy_img) {
       tc_pack_hartley(c.ny, s->hy_img, st);
       tc_pack_hartley(c.nz, s->hz_img, st);
+      if (s->h16_img) tc_pack_hartley_bf16(s->h16_img, st);
       CK(cudaGetLastError());
       CK(cudaStreamSynchronize(st));
     }
+    s->c.corr_bf16 = (s->h16_img && !s->c.mixed_tc && tc_bf16_available(fields<float>(s).e[2], c.nx)) ? 1 : 0;
   }
   launch_poisson_table(c, f, st);
   // initial projection of u0 (dt absorbed in phi), velocity only
@@ -893,6 +899,15 @@ void launch_stage(ibm_state* s, int stage) {
     case IBM_STAGE_RESIDUAL:
       if constexpr (std::is_same<T, float>::value)
         if (s->precision == IBM_MIXED) launch_residual_mixed(c, f, st);
+      break;
+    case IBM_STAGE_TC_BF16:
+      if constexpr (std::is_same<T, float>::value)
+        if (s->precision == IBM_MIXED && c.corr_bf16)
+          (void)tc_rows_times_h_bf16(f.e[2], s->h16_img, f.e[0], c.nx, &f.prm->error, st, c.sm_reserved);
+      break;
+    case IBM_STAGE_POISSON_X16:
+      if constexpr (std::is_same<T, float>::value)
+        if (s->precision == IBM_MIXED && c.corr_bf16) launch_poisson_x_bf16(c, f, f.e[2], st);
       break;
     default: break;
   }
@@ -1179,7 +1194,7 @@ int ibm_stats(ibm_state* s, ibm_stats_t* out) {
 }
 
 int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
-  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_TC_PASS1) return IBM_EINVAL;
+  if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_POISSON_X16) return IBM_EINVAL;
   cudaStream_t st = s->stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

@@ -51,6 +51,7 @@ struct Consts {
   int afx_planes;     // tile: x planes per block of the FP32 x factor
   int sm_reserved;    // SMs the structural update holds while the pressure solve runs
   int mixed_tc;       // mixed solve at 256 x 256: 1 = tensor-core predictor, 0 = FFT predictor
+  int corr_bf16;      // mixed solve: the correction is stored in bfloat16 (FFT predictor path)
   float f_inv_h, f_inv_h2, f_nu;   // FP32 copies
 };
 

@@ -6,6 +6,7 @@
 //
 // Layout: x slowest, z fastest; u, v, w have nx + 1 planes (u: faces
 // 0..nx; v, w: cells 0..nx-1 plus the outflow ghost plane nx), p and phi nx.
+#include <cuda_bf16.h>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -1567,25 +1568,36 @@ k_div_vec(Consts c, const Params* __restrict__ prm, T* __restrict__ u, const T* 
   }
 }
 
-template <class T, bool TWO>
+// TWO: 0 phi alone; 1 phi + phi_b (FP32); 2 phi + phi_b (bfloat16) -- the
+// mixed solve's predictor and correction, summed as they are read
+template <class T, int TWO>
 __global__ void __launch_bounds__(256, 3)
 k_project_vec(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
               const T* __restrict__ va, const T* __restrict__ wa, T* __restrict__ ub,
-              T* __restrict__ vb, T* __restrict__ wb, const T* __restrict__ phi, const T* __restrict__ phi_b,
+              T* __restrict__ vb, T* __restrict__ wb, const T* __restrict__ phi, const void* __restrict__ phi_b,
               T* __restrict__ p, double* __restrict__ partial, int initial) {
   constexpr int E = RunTile<T>::E;
-  // phi (+ phi_b when TWO: the mixed solve's predictor and correction, summed here)
+  const T* pb = static_cast<const T*>(phi_b);
+  const __nv_bfloat16* pb16 = static_cast<const __nv_bfloat16*>(phi_b);
   auto ldg_phi = [&](size_t q, T (&v)[E]) {
     ldg_run<T, E>(phi + q, v);
-    if constexpr (TWO) {
+    if constexpr (TWO == 1) {
       T t[E];
-      ldg_run<T, E>(phi_b + q, t);
+      ldg_run<T, E>(pb + q, t);
 #pragma unroll
       for (int e = 0; e < E; ++e) v[e] = v[e] + t[e];
+    } else if constexpr (TWO == 2) {
+      static_assert(E == 4 && sizeof(T) == 4, "bfloat16 correction with FP32 runs of four");
+      const uint2 r = *reinterpret_cast<const uint2*>(pb16 + q);
+      v[0] += __uint_as_float(r.x << 16);
+      v[1] += __uint_as_float(r.x & 0xFFFF0000u);
+      v[2] += __uint_as_float(r.y << 16);
+      v[3] += __uint_as_float(r.y & 0xFFFF0000u);
     }
   };
   auto phi1 = [&](size_t q) {
-    if constexpr (TWO) return phi[q] + phi_b[q];
+    if constexpr (TWO == 1) return phi[q] + pb[q];
+    else if constexpr (TWO == 2) return phi[q] + (T)__bfloat162float(pb16[q]);
     else return phi[q];
   };
   const int nx = c.nx, ny = c.ny, nz = c.nz;
@@ -1997,19 +2009,27 @@ void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial,
 // correction), phi_a = f.phi when not given
 template <class T>
 void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s,
-                         const T* phi_a, const T* phi_b) {
+                         const T* phi_a, const T* phi_b, const void* phi_b16) {
   if (!phi_a) phi_a = f.phi;
   if (const int tj = run_rows<T>(c)) {
     const dim3 grid(c.ny / tj, (c.nx + 1 + RUN_XCH - 1) / RUN_XCH);
+    const int ini = initial ? 1 : 0;
+    if constexpr (sizeof(T) == 4 && RunTile<T>::E == 4) {
+      if (phi_b16) {
+        k_project_vec<T, 2><<<grid, RunTile<T>::THREADS, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
+                                                                f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1],
+                                                                phi_a, phi_b16, f.p, f.partial, ini);
+        return;
+      }
+    }
     if (phi_b)
-      k_project_vec<T, true><<<grid, RunTile<T>::THREADS, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
-                                                                 f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1],
-                                                                 phi_a, phi_b, f.p, f.partial, initial ? 1 : 0);
+      k_project_vec<T, 1><<<grid, RunTile<T>::THREADS, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
+                                                              f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1],
+                                                              phi_a, phi_b, f.p, f.partial, ini);
     else
-      k_project_vec<T, false><<<grid, RunTile<T>::THREADS, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
-                                                                  f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1],
-                                                                  phi_a, nullptr, f.p, f.partial,
-                                                                  initial ? 1 : 0);
+      k_project_vec<T, 0><<<grid, RunTile<T>::THREADS, 0, s>>>(c, f.prm, f.u[cur], f.v[cur], f.w[cur],
+                                                              f.u[cur ^ 1], f.v[cur ^ 1], f.w[cur ^ 1],
+                                                              phi_a, nullptr, f.p, f.partial, ini);
     return;
   }
   k_project<T><<<grid3(c, c.nx + 1), dim3(TK, TJ), 0, s>>>(
@@ -2019,8 +2039,8 @@ void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool init
 
 template <class T>
 void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s,
-                    const T* phi_a, const T* phi_b) {
-  launch_project_only(c, f, cur, initial, s, phi_a, phi_b);
+                    const T* phi_a, const T* phi_b, const void* phi_b16) {
+  launch_project_only(c, f, cur, initial, s, phi_a, phi_b, phi_b16);
   if (!initial) k_end_step<<<1, 1, 0, s>>>(f.prm);
 }
 
@@ -2066,10 +2086,10 @@ template int partial_count<double>(const Consts&);
   template void launch_mass<T>(const Consts&, const Fields<T>&, int, cudaStream_t);            \
   template void launch_div<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t);       \
   template void launch_project_only<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t, const T*, \
-                                       const T*);                                                  \
+                                       const T*, const void*);                                     \
   template void launch_mass_div<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t);  \
   template void launch_project<T>(const Consts&, const Fields<T>&, int, bool, cudaStream_t, const T*, \
-                                  const T*);                                                       \
+                                  const T*, const void*);                                          \
   template void launch_stats<T>(const Consts&, const Fields<T>&, int, double*, cudaStream_t);
 INST(double)
 INST(float)

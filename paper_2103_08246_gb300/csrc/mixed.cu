@@ -10,6 +10,8 @@
 //
 // 2-D transform of every x plane X (ny x nz, z contiguous): H_y X H_z, as
 // two GEMMs: rows (all planes at once) times H_z, then H_y times each plane.
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <cstdint>
 
@@ -228,8 +230,9 @@ __device__ inline float residual_ds(float pc, float pxm, float pxp, float pym, f
 // four consecutive z cells per thread (nz is a power of two >= 4): 16-byte loads of
 // the cell run and of its x and y neighbours, the two z neighbours past the
 // run's ends as single loads; grid (z runs, y rows, x planes)
+template <class R>
 __global__ void k_residual_ds4(int nx, int ny, int nz, float ih2_hi, float ih2_lo, const float* __restrict__ D,
-                               const float* __restrict__ phi, float* __restrict__ r) {
+                               const float* __restrict__ phi, R* __restrict__ r) {
   const int k0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   if (k0 >= nz) return;
   const int j = blockIdx.y, i = blockIdx.z;
@@ -251,7 +254,13 @@ __global__ void k_residual_ds4(int nx, int ny, int nz, float ih2_hi, float ih2_l
   o.y = residual_ds(c4.y, xm.y, xp.y, ym.y, yp.y, c4.x, c4.z, d4.y, ih2_hi, ih2_lo);
   o.z = residual_ds(c4.z, xm.z, xp.z, ym.z, yp.z, c4.y, c4.w, d4.z, ih2_hi, ih2_lo);
   o.w = residual_ds(c4.w, xm.w, xp.w, ym.w, yp.w, c4.z, zr, d4.w, ih2_hi, ih2_lo);
-  *reinterpret_cast<float4*>(r + id) = o;
+  if constexpr (sizeof(R) == 4) {
+    *reinterpret_cast<float4*>(r + id) = o;
+  } else {   // bfloat16: the correction's input
+    const __nv_bfloat162 a = __floats2bfloat162_rn(o.x, o.y), b = __floats2bfloat162_rn(o.z, o.w);
+    *reinterpret_cast<uint2*>(r + id) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+  }
 }
 
 static void gemm(const GemmArgs& g, int batch, cudaStream_t s) {
@@ -290,44 +299,64 @@ static void transform2d(const Consts& c, const Hartley& H, const float* in, floa
 // projection sums the two parts as it reads them (no separate pass).
 // x0 + t1 with t1 = L^-1 (D - L x0) leaves the correction's relative error
 // times the predictor's, so one of the two solves may be coarse. At 256 x 256
-// planes the predictor is the FP32 FFT solve (one pass per 2-D transform)
-// and the correction's tensor-core transforms take the single TF32 product
-// (relative error about 2^-11); at other square sizes both solves run on the
-// tensor cores, the predictor with the single product where it exists, the
-// correction with the split products. Scratch: e[0], e[1], e[2].
+// planes (c.corr_bf16) the predictor is the FP32 FFT solve (relative error
+// near FP32 rounding) and the whole correction is held in bfloat16: the
+// residual rounded to bfloat16, the tensor-core transforms on bfloat16
+// operands with FP32 accumulation, the Thomas sweeps in FP32 arithmetic on
+// bfloat16 storage (relative error about 2^-8 altogether), half the bytes of
+// an FP32 correction. Otherwise both solves run on the tensor cores with FP32
+// storage, the predictor with the single TF32 product where it exists (256),
+// the correction with the split products. Scratch: e[0], e[1], e[2]
+// (bfloat16 correction: the first halves of e[0] and e[2]).
 void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* Hy, const float* Hz,
-                          const unsigned char* Hy_img, const unsigned char* Hz_img, cudaStream_t s) {
+                          const unsigned char* Hy_img, const unsigned char* Hz_img, const unsigned char* H16_img,
+                          cudaStream_t s) {
   const Hartley H{Hy, Hz, Hy_img, Hz_img};
   float* D = f.phi;
   float* t0 = f.e[0];
   float* x0 = f.e[1];
   float* t1 = f.e[2];
   int* err = &f.prm->error;
-  // predictor: x0 = L^-1 D
-  const bool fft = !c.mixed_tc && launch_dht2d_on(c, f, D, x0, s);
-  if (fft) {
-    launch_poisson_x_on(c, f, x0, s);
-    launch_dht2d_on(c, f, x0, x0, s);
-  } else {
-    transform2d(c, H, D, t0, x0, err, s, true);
-    launch_poisson_x_on(c, f, x0, s);
-    transform2d(c, H, x0, t0, x0, err, s, true);
-  }
-  // double-single residual and correction: t1 = L^-1 (D - L x0)
   const double ih2 = c.inv_h * c.inv_h;
   const float ih2_hi = (float)ih2, ih2_lo = (float)(ih2 - (double)ih2_hi);
-  k_residual_ds4<<<dim3((c.nz / 4 + 63) / 64, c.ny, c.nx), 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, t1);
-  transform2d(c, H, t1, t0, t1, err, s, fft);
+  const dim3 rgrid((c.nz / 4 + 63) / 64, c.ny, c.nx);
+  if (c.corr_bf16) {
+    // predictor: x0 = L^-1 D by the FP32 FFT solve
+    launch_dht2d_on(c, f, D, x0, s);
+    launch_poisson_x_on(c, f, x0, s);
+    launch_dht2d_on(c, f, x0, x0, s);
+    // residual (double-single) and correction, in bfloat16
+    __nv_bfloat16* r16 = reinterpret_cast<__nv_bfloat16*>(t1);
+    __nv_bfloat16* w16 = reinterpret_cast<__nv_bfloat16*>(t0);
+    k_residual_ds4<<<rgrid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, r16);
+    tc_rows_times_h_bf16(r16, H16_img, w16, c.nx, err, s, c.sm_reserved);
+    tc_rows_times_h_bf16(w16, H16_img, r16, c.nx, err, s, c.sm_reserved);
+    launch_poisson_x_bf16(c, f, r16, s);
+    tc_rows_times_h_bf16(r16, H16_img, w16, c.nx, err, s, c.sm_reserved);
+    tc_rows_times_h_bf16(w16, H16_img, r16, c.nx, err, s, c.sm_reserved);
+    return;
+  }
+  // predictor: x0 = L^-1 D
+  transform2d(c, H, D, t0, x0, err, s, true);
+  launch_poisson_x_on(c, f, x0, s);
+  transform2d(c, H, x0, t0, x0, err, s, true);
+  // double-single residual and correction: t1 = L^-1 (D - L x0)
+  k_residual_ds4<<<rgrid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, t1);
+  transform2d(c, H, t1, t0, t1, err, s);
   launch_poisson_x_on(c, f, t1, s);
-  transform2d(c, H, t1, t0, t1, err, s, fft);
+  transform2d(c, H, t1, t0, t1, err, s);
 }
 
 // the refinement's residual alone (stage timing): e[2] = D - L_h e[1]
 void launch_residual_mixed(const Consts& c, const Fields<float>& f, cudaStream_t s) {
   const double ih2 = c.inv_h * c.inv_h;
   const float ih2_hi = (float)ih2, ih2_lo = (float)(ih2 - (double)ih2_hi);
-  k_residual_ds4<<<dim3((c.nz / 4 + 63) / 64, c.ny, c.nx), 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, f.phi,
-                                                                     f.e[1], f.e[2]);
+  const dim3 rgrid((c.nz / 4 + 63) / 64, c.ny, c.nx);
+  if (c.corr_bf16)
+    k_residual_ds4<<<rgrid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, f.phi, f.e[1],
+                                        reinterpret_cast<__nv_bfloat16*>(f.e[2]));
+  else
+    k_residual_ds4<<<rgrid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, f.phi, f.e[1], f.e[2]);
 }
 
 void mixed_set_attributes() {

@@ -25,7 +25,10 @@
 // which sets mean(phi) = 0.
 #include <cooperative_groups.h>
 
+#include <cuda_bf16.h>
+
 #include <cmath>
+#include <type_traits>
 
 #include "async_copy.cuh"
 #include "solver.h"
@@ -604,14 +607,28 @@ __device__ inline size_t ptab_index(const Consts& c, int jk) {
   return (size_t)qy * (c.nz / 2 + 1) + qz;
 }
 
-template <class T>
-__global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict__ tab, T* __restrict__ phi, T scale,
+// storage conversions: FP32 / FP64 fields, or bfloat16 (the mixed solve's correction)
+template <class T, class S>
+__device__ inline T from_store(S v) {
+  if constexpr (std::is_same<S, __nv_bfloat16>::value) return __bfloat162float(v);
+  else return (T)v;
+}
+template <class S, class T>
+__device__ inline S to_store(T v) {
+  if constexpr (std::is_same<S, __nv_bfloat16>::value) return __float2bfloat16_rn(v);
+  else return (S)v;
+}
+
+template <class T, class S>
+__global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict__ tab, S* __restrict__ phi, T scale,
                                                    double* __restrict__ mean00) {
   const int P = c.ny * c.nz;
   const int jk = blockIdx.x * blockDim.x + threadIdx.x;
   if (jk >= P) return;
   const int nx = c.nx;
-  T* d = phi + jk;
+  S* d = phi + jk;
+  auto LD = [&](size_t o) { return from_store<T>(d[o]); };
+  auto ST = [&](size_t o, T v) { d[o] = to_store<S>(v); };
   const T* iv = tab + ptab_index(c, jk);
   const size_t PT = ptab_plane(c);
   const bool zero_mode = (jk == 0);
@@ -624,7 +641,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
     if (nfull > 0) {
 #pragma unroll
       for (int q = 0; q < PF; ++q) {
-        rd[q] = d[(size_t)q * P];
+        rd[q] = LD((size_t)q * P);
         rt[q] = iv[(size_t)q * PT];
       }
     }
@@ -634,7 +651,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
       if (ch + 1 < nfull) {
 #pragma unroll
         for (int q = 0; q < PF; ++q) {
-          nd[q] = d[(size_t)(i + PF + q) * P];
+          nd[q] = LD((size_t)(i + PF + q) * P);
           nt[q] = iv[(size_t)(i + PF + q) * PT];
         }
       }
@@ -642,7 +659,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
       for (int q = 0; q < PF; ++q) {
         const T rhs = (zero_mode && i + q == 0) ? (T)0 : rd[q] * scale;
         y = (rhs - y) * rt[q];
-        d[(size_t)(i + q) * P] = y;
+        ST((size_t)(i + q) * P, y);
       }
 #pragma unroll
       for (int q = 0; q < PF; ++q) {
@@ -653,9 +670,9 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
   }
   for (int i = nfull * PF; i < nx; ++i) {
     const size_t o = (size_t)i * P;
-    const T rhs = (zero_mode && i == 0) ? (T)0 : d[o] * scale;
+    const T rhs = (zero_mode && i == 0) ? (T)0 : LD(o) * scale;
     y = (rhs - y) * iv[(size_t)i * PT];
-    d[o] = y;
+    ST(o, y);
   }
   // back substitution from the top, the same chunking (the partial chunk first);
   // the line sum of mode (0, 0) is gathered on the way (in T: an FP64
@@ -667,8 +684,8 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
   for (; i > nx - 2 - rem; --i) {
     const size_t o = (size_t)i * P;
     const T cp = (zero_mode && i == 0) ? (T)0 : iv[(size_t)i * PT];
-    x = d[o] - cp * x;
-    d[o] = x;
+    x = LD(o) - cp * x;
+    ST(o, x);
     lsum += x;
   }
   {
@@ -677,7 +694,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
     if (nch > 0) {
 #pragma unroll
       for (int q = 0; q < PF; ++q) {
-        rd[q] = d[(size_t)(i - q) * P];
+        rd[q] = LD((size_t)(i - q) * P);
         rt[q] = iv[(size_t)(i - q) * PT];
       }
     }
@@ -686,7 +703,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
       if (ch + 1 < nch) {
 #pragma unroll
         for (int q = 0; q < PF; ++q) {
-          nd[q] = d[(size_t)(i - PF - q) * P];
+          nd[q] = LD((size_t)(i - PF - q) * P);
           nt[q] = iv[(size_t)(i - PF - q) * PT];
         }
       }
@@ -694,7 +711,7 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
       for (int q = 0; q < PF; ++q) {
         const T cp = (zero_mode && i - q == 0) ? (T)0 : rt[q];
         x = rd[q] - cp * x;
-        d[(size_t)(i - q) * P] = x;
+        ST((size_t)(i - q) * P, x);
         lsum += x;
       }
 #pragma unroll
@@ -709,10 +726,13 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
 }
 
 // gauge mean(phi) = 0: subtract the line mean of mode (0, 0) in every plane
-template <class T>
-__global__ void k_mode00_sub(Consts c, T* __restrict__ phi, const double* __restrict__ mean00) {
+template <class S>
+__global__ void k_mode00_sub(Consts c, S* __restrict__ phi, const double* __restrict__ mean00) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < c.nx) phi[(size_t)i * c.ny * c.nz] -= (T)*mean00;
+  if (i < c.nx) {
+    S& v = phi[(size_t)i * c.ny * c.nz];
+    v = to_store<S>(from_store<double>(v) - *mean00);
+  }
 }
 
 // inverse pivots 1 / (diag_i - c'_{i-1}) of every distinct mode, FP64 arithmetic
@@ -775,8 +795,17 @@ void launch_poisson_x_on(const Consts& c, const Fields<T>& f, T* buf, cudaStream
   const int P = c.ny * c.nz;
   const T scale = (T)(c.h * c.h / ((double)c.ny * c.nz));
 
-  k_poisson_x<T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, buf, scale, f.mean00);
+  k_poisson_x<T, T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, buf, scale, f.mean00);
   k_mode00_sub<T><<<(c.nx + 255) / 256, 256, 0, s>>>(c, buf, f.mean00);
+}
+
+// the same on bfloat16 storage (FP32 arithmetic)
+void launch_poisson_x_bf16(const Consts& c, const Fields<float>& f, void* buf, cudaStream_t s) {
+  const int P = c.ny * c.nz;
+  const float scale = (float)(c.h * c.h / ((double)c.ny * c.nz));
+  __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(buf);
+  k_poisson_x<float, __nv_bfloat16><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, b, scale, f.mean00);
+  k_mode00_sub<__nv_bfloat16><<<(c.nx + 255) / 256, 256, 0, s>>>(c, b, f.mean00);
 }
 
 template <class T>

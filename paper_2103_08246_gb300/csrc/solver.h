@@ -115,11 +115,14 @@ template <class T> bool launch_dht2d(const Consts& c, const Fields<T>& f, cudaSt
 bool launch_dht2d_on(const Consts& c, const Fields<float>& f, const float* in, float* out, cudaStream_t s);
 template <class T> void launch_mass(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
+// phi = phi_a (f.phi when null) + phi_b (FP32) or + phi_b16 (bfloat16, FP32 fields only)
 template <class T> void launch_project_only(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s,
-                                            const T* phi_a = nullptr, const T* phi_b = nullptr);
+                                            const T* phi_a = nullptr, const T* phi_b = nullptr,
+                                            const void* phi_b16 = nullptr);
 template <class T> void launch_mass_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 template <class T> void launch_project(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s,
-                                       const T* phi_a = nullptr, const T* phi_b = nullptr);
+                                       const T* phi_a = nullptr, const T* phi_b = nullptr,
+                                       const void* phi_b16 = nullptr);
 template <class T>
 int partial_count(const Consts& c);
 size_t poisson_table_size(const Consts& c);
@@ -129,6 +132,12 @@ size_t poisson_table_size(const Consts& c);
 bool tc_supported(int n);
 size_t tc_h_image_bytes(int n);
 void tc_pack_hartley(int n, unsigned char* img, cudaStream_t s);
+// BF16 storage, 256 x 256 planes only (tc_gemm.cu)
+size_t tc_bf16_image_bytes();
+bool tc_bf16_available(const void* X, int planes);   // the tensor map of X can be encoded
+void tc_pack_hartley_bf16(unsigned char* img, cudaStream_t s);
+bool tc_rows_times_h_bf16(const void* X, const unsigned char* img, void* out, int planes, int* error,
+                          cudaStream_t s, int sm_reserved);
 bool tc_rows_times_h_t(const float* X, const unsigned char* himg, float* out, int planes, int n, int* error,
                        cudaStream_t s, bool single = false, int sm_reserved = 0);
 void tc_gemm_set_attributes();
@@ -142,13 +151,14 @@ template <class T> void launch_dht_y(const Consts& c, const Fields<T>& f, cudaSt
 template <class T> void launch_dht_z(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_poisson_x(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_poisson_x_on(const Consts& c, const Fields<T>& f, T* buf, cudaStream_t s);
+void launch_poisson_x_bf16(const Consts& c, const Fields<float>& f, void* buf, cudaStream_t s);
 template <class T> void launch_poisson_table(const Consts& c, const Fields<T>& f, cudaStream_t s);
 void poisson_set_attributes();
 
 // ---- mixed.cu
 // leaves phi = e[1] + e[2] (predictor + correction; the projection sums them)
-void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* Hy,
-                          const float* Hz, const unsigned char* Hy_img, const unsigned char* Hz_img,
+void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* Hy, const float* Hz,
+                          const unsigned char* Hy_img, const unsigned char* Hz_img, const unsigned char* H16_img,
                           cudaStream_t s);
 void mixed_set_attributes();
 void launch_residual_mixed(const Consts& c, const Fields<float>& f, cudaStream_t s);

@@ -47,6 +47,7 @@
 // tensor-core work, releases its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 
 #include <cstdint>
 
@@ -347,6 +348,231 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_tf32x3(TcArgs g, cons
   if (warp == 0) tc_dealloc(tmem, C::TMEM_COLS);
 }
 
+// ---- BF16 storage at 256 x 256 planes (the refinement's correction when the
+// predictor is the FP32 FFT solve): the same even/odd form with X and out in
+// bfloat16, e and o rounded to bfloat16 (relative 2^-9), products
+// e cos + o sin by tcgen05.mma kind::f16 (M = 128, N = 128, K = 16) into FP32
+// accumulators. The whole cos / sin image (2 x 128 x 128 bfloat16, 64 KB)
+// stays in shared memory for the kernel's lifetime, so a stage carries only
+// the two raw K blocks (8 KB) and twelve stages are in flight. A raw block of
+// 16 values is two K-groups of 8 bfloat16 (16 bytes per row of a core
+// matrix); one MMA per accumulator consumes it.
+namespace b16 {
+
+constexpr int N = 256, MH = 128, NS = N / 32, NB = N / 16;
+constexpr uint32_t A_TILE = TC_M * TC_KB * 2;      // one raw block of 128 rows: 4 KB
+constexpr uint32_t STAGE = 2 * A_TILE;
+constexpr uint32_t IMG = 2u * MH * MH * 2;         // cos, sin: 64 KB
+constexpr uint32_t IMG_SLICE = 2u * TC_KB * MH * 2;   // one stage's cos + sin K-slice: 8 KB
+constexpr uint32_t B_LBO = MH * 16;                // K-adjacent core matrices of a cos / sin part
+constexpr int ST = 12;
+constexpr uint32_t SMEM = IMG + ST * STAGE;        // 160 KB
+constexpr uint32_t TMEM_COLS = 4 * MH;             // two buffers of C and S
+
+struct Args {
+  const unsigned char* img;   // tc_pack_hartley_bf16
+  __nv_bfloat16* out;         // per plane: out[c][r] = sum_k X[r][k] H[k][c]
+  int M;                      // rows of X (planes x 256)
+  int* error;
+};
+
+__device__ inline void unpack8(uint4 v, float* f) {
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    f[2 * q] = __uint_as_float(w[q] << 16);
+    f[2 * q + 1] = __uint_as_float(w[q] & 0xFFFF0000u);
+  }
+}
+
+__device__ inline uint4 pack8(const float* f) {
+  uint32_t w[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+    w[q] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+  return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_tc_bf16(Args g, const __grid_constant__ CUtensorMap xmap) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  __shared__ uint64_t full[ST], conv[ST], empty[ST], tfull[2], tempty[2], xfull[2], xempty[2], imgbar;
+  __shared__ float xm_s[2][TC_M], ym_s[2][TC_M];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = (g.M + TC_M - 1) / TC_M;
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int total = my_tiles * NS;
+  const uint32_t ibase = smem_u32(tsm), sbase = ibase + IMG;
+
+  if (warp == 0) tc_alloc(&tmem_slot, TMEM_COLS);
+  if (tid == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], TC_CONV_WARPS);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], TC_EPI_WARPS);
+      mbar_init(&xfull[b], TC_CONV_WARPS);
+      mbar_init(&xempty[b], TC_EPI_WARPS);
+    }
+    mbar_init(&imgbar, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  bool ok = true;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      if (total > 0) {
+        mbar_arrive_expect_tx(&imgbar, IMG);
+        for (uint32_t o = 0; o < IMG; o += 16384) bulk_g2s_u32(ibase + o, g.img + o, 16384, &imgbar);
+      }
+      for (int j = 0; j < total; ++j) {
+        const int s = j % ST;
+        if (j >= ST) ok = mbar_wait(&empty[s], (uint32_t)(j / ST - 1) & 1u) && ok;
+        const int lt = j / NS, js = j % NS;
+        const int m0 = ((int)blockIdx.x + lt * (int)gridDim.x) * TC_M;
+        const uint32_t st = sbase + (uint32_t)s * STAGE;
+        mbar_arrive_expect_tx(&full[s], 2 * A_TILE);
+        tma_load_3d(st, &xmap, 0, m0, js * (TC_KB / 8), &full[s]);
+        tma_load_3d(st + A_TILE, &xmap, 0, m0, (NB - 1 - js) * (TC_KB / 8), &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc_bf16(TC_M, MH, false, false);
+      if (total > 0) ok = mbar_wait(&imgbar, 0u) && ok;
+      for (int j = 0; j < total; ++j) {
+        const int s = j % ST;
+        const int lt = j / NS, js = j % NS;
+        if (js == 0 && lt >= 2) ok = mbar_wait(&tempty[lt & 1], (uint32_t)((lt - 2) / 2) & 1u) && ok;
+        ok = mbar_wait(&conv[s], (uint32_t)(j / ST) & 1u) && ok;
+        tc_fence_after();
+        const uint32_t dc = tmem + (uint32_t)((lt & 1) * 2 * MH), ds = dc + (uint32_t)MH;
+        const uint32_t e = sbase + (uint32_t)s * STAGE, o = e + A_TILE;
+        const uint32_t cs = ibase + (uint32_t)js * IMG_SLICE, sn = cs + IMG_SLICE / 2;
+        const uint32_t first = js == 0 ? 0u : 1u;
+        tc_mma_bf16(dc, tc_desc(e, A_LBO, 128), tc_desc(cs, B_LBO, 128), idesc, first);
+        tc_mma_bf16(ds, tc_desc(o, A_LBO, 128), tc_desc(sn, B_LBO, 128), idesc, first);
+        tc_commit_to(&empty[s]);
+        if (js == NS - 1) tc_commit_to(&tfull[lt & 1]);
+      }
+    }
+  } else if (warp < TC_EPI0) {
+    const int t = tid - 64;   // the tile row this thread converts
+    float carry = 0.f, alt = 0.f;
+    for (int j = 0; j < total; ++j) {
+      const int s = j % ST;
+      const int lt = j / NS, js = j % NS;
+      ok = mbar_wait(&full[s], (uint32_t)(j / ST) & 1u) && ok;
+      unsigned char* st = tsm + IMG + (size_t)s * STAGE;
+      float a[16], b[16];
+#pragma unroll
+      for (int kg = 0; kg < 2; ++kg) {
+        unpack8(*reinterpret_cast<const uint4*>(st + kg * A_LBO + t * 16), a + 8 * kg);
+        unpack8(*reinterpret_cast<const uint4*>(st + A_TILE + kg * A_LBO + t * 16), b + 8 * kg);
+      }
+      if (js == 0) alt = 0.f;
+      float ev[16], ov[16];
+      ev[0] = js == 0 ? a[0] : a[0] + carry;
+      ov[0] = js == 0 ? 0.f : a[0] - carry;
+#pragma unroll
+      for (int q = 1; q < 16; ++q) {
+        ev[q] = a[q] + b[16 - q];
+        ov[q] = a[q] - b[16 - q];
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) alt += (q & 1) ? -(a[q] + b[q]) : (a[q] + b[q]);
+      carry = b[0];
+#pragma unroll
+      for (int kg = 0; kg < 2; ++kg) {
+        *reinterpret_cast<uint4*>(st + kg * A_LBO + t * 16) = pack8(ev + 8 * kg);
+        *reinterpret_cast<uint4*>(st + A_TILE + kg * A_LBO + t * 16) = pack8(ov + 8 * kg);
+      }
+      fence_proxy_async_smem();
+      if (js == NS - 1) {
+        if (lt >= 2) ok = mbar_wait(&xempty[lt & 1], (uint32_t)((lt - 2) / 2) & 1u) && ok;
+        xm_s[lt & 1][t] = b[0];
+        ym_s[lt & 1][t] = alt;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&conv[s]);
+        if (js == NS - 1) mbar_arrive(&xfull[lt & 1]);
+      }
+    }
+  } else {
+    // epilogue: lane quarter warp % 4, column half (warp - TC_EPI0) / 4
+    const int quarter = warp & 3, part = (warp - TC_EPI0) >> 2;
+    for (int lt = 0; lt < my_tiles; ++lt) {
+      const int r = quarter * 32 + lane;
+      const int m = ((int)blockIdx.x + lt * (int)gridDim.x) * TC_M + r;
+      ok = mbar_wait(&tfull[lt & 1], (uint32_t)(lt / 2) & 1u) && ok;
+      ok = mbar_wait(&xfull[lt & 1], (uint32_t)(lt / 2) & 1u) && ok;
+      tc_fence_after();
+      const float xm = xm_s[lt & 1][r];
+      const uint32_t dc = tmem + (uint32_t)((lt & 1) * 2 * MH) + ((uint32_t)(quarter * 32) << 16);
+      __nv_bfloat16* plane = g.out + (size_t)(m / N) * N * N + (m % N);
+      const bool live = m < g.M;
+      if (part == 0 && live) plane[(size_t)MH * N] = __float2bfloat16_rn(ym_s[lt & 1][r]);
+#pragma unroll 1
+      for (int c0 = part * (MH / 2); c0 < (part + 1) * (MH / 2); c0 += 32) {
+        float vc[32], vs[32];
+        tc_ld_x32(dc + (uint32_t)c0, vc);
+        tc_ld_x32(dc + (uint32_t)(MH + c0), vs);
+        if (live) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int c = c0 + q;
+            const float base = vc[q] + ((c & 1) ? -xm : xm);
+            plane[(size_t)c * N] = __float2bfloat16_rn(base + vs[q]);
+            if (c > 0) plane[(size_t)(N - c) * N] = __float2bfloat16_rn(base - vs[q]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&tempty[lt & 1]);
+        mbar_arrive(&xempty[lt & 1]);
+      }
+    }
+  }
+  if (tid == 32 && my_tiles > 0)
+    ok = mbar_wait(&tfull[(my_tiles - 1) & 1], (uint32_t)((my_tiles - 1) / 2) & 1u) && ok;
+  ok = __syncthreads_and(ok) != 0;
+  if (!ok && tid == 0) atomicOr(g.error, ERR_TIMEOUT);
+  tc_fence_after();
+  if (warp == 0) tc_dealloc(tmem, TMEM_COLS);
+}
+
+// image: per stage slice js (K = 16 js .. 16 js + 15), cos then sin, each as
+// [K-group (2)][c (128)][8 bfloat16]
+__global__ void k_pack(uint16_t* __restrict__ img) {
+  const int total = 2 * MH * MH;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int e = i & 7;
+    const int c = (i >> 3) & (MH - 1);
+    const int rest = i >> 10;   // (js * 2 + part) * 2 + kg
+    const int kg = rest & 1, part = (rest >> 1) & 1, js = rest >> 2;
+    const int k = js * TC_KB + kg * 8 + e;
+    const int kc = (k * c) % N;
+    double sv, cv;
+    sincospi(2.0 * (double)kc / (double)N, &sv, &cv);
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)(part == 0 ? cv : sv));
+    img[i] = *reinterpret_cast<const uint16_t*>(&h);
+  }
+}
+
+}  // namespace b16
+
 // ---- direct form for planes of 32, 64 and 128 (the ensemble's members): one
 // n x n contraction per row, K in blocks of 16 through a four-stage ring, the
 // A block split in place by six warps; 512 threads at about 53 registers
@@ -564,21 +790,41 @@ int sm_count() {
 
 // 3-D map over the rows of X: (4 floats, M rows, n / 4 K-groups), strides
 // (n * 4, 16) bytes, box (4, 128, TC_KB / 4); rows past M read as zero
-bool encode_xmap(CUtensorMap* m, const float* X, int M, int n) {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
             cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-      return false;
+      return nullptr;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
+  return encode;
+}
+
+bool encode_xmap(CUtensorMap* m, const float* X, int M, int n) {
+  const auto encode = tensor_map_encoder();
+  if (!encode) return false;
   const cuuint64_t dims[3] = {4, (cuuint64_t)M, (cuuint64_t)(n / 4)};
   const cuuint64_t strides[2] = {(cuuint64_t)n * 4, 16};
   const cuuint32_t box[3] = {4, TC_M, TC_KB / 4};
   const cuuint32_t estr[3] = {1, 1, 1};
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(X), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the same over bfloat16 rows: (8 values, M rows, n / 8 K-groups), strides
+// (n * 2, 16) bytes, box (8, 128, TC_KB / 8)
+bool encode_xmap_bf16(CUtensorMap* m, const void* X, int M, int n) {
+  const auto encode = tensor_map_encoder();
+  if (!encode) return false;
+  const cuuint64_t dims[3] = {8, (cuuint64_t)M, (cuuint64_t)(n / 8)};
+  const cuuint64_t strides[2] = {(cuuint64_t)n * 2, 16};
+  const cuuint32_t box[3] = {8, TC_M, TC_KB / 8};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(X), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -610,7 +856,38 @@ bool launch_tc(const float* X, const TcArgs& g, cudaStream_t s, int reserved) {
   return true;
 }
 
+bool launch_tc_bf16(const void* X, const b16::Args& g, cudaStream_t s, int reserved) {
+  CUtensorMap m;
+  if (!encode_xmap_bf16(&m, X, g.M, b16::N)) return false;
+  const int ntiles = (g.M + TC_M - 1) / TC_M;
+  const int grid = persistent_grid(ntiles, reserved);
+  b16::k_gemm_tc_bf16<<<grid, TC_THREADS, b16::SMEM, s>>>(g, m);
+  return true;
+}
+
 }  // namespace
+
+size_t tc_bf16_image_bytes() { return b16::IMG; }
+
+bool tc_bf16_available(const void* X, int planes) {
+  CUtensorMap m;
+  return planes > 0 && encode_xmap_bf16(&m, X, planes * b16::N, b16::N);
+}
+
+void tc_pack_hartley_bf16(unsigned char* img, cudaStream_t s) {
+  b16::k_pack<<<(2 * b16::MH * b16::MH + 255) / 256, 256, 0, s>>>(reinterpret_cast<uint16_t*>(img));
+}
+
+// out = (X H)^T for each 256 x 256 plane of X, X and out bfloat16 (16-byte
+// aligned, distinct), H the 256-point Hartley matrix as the bfloat16 image of
+// tc_pack_hartley_bf16 (resident in shared memory), FP32 accumulation.
+// Returns false (nothing launched) when the tensor map cannot be encoded.
+bool tc_rows_times_h_bf16(const void* X, const unsigned char* img, void* out, int planes, int* error,
+                          cudaStream_t s, int sm_reserved) {
+  if (planes <= 0) return true;
+  const b16::Args g{img, reinterpret_cast<__nv_bfloat16*>(out), planes * b16::N, error};
+  return launch_tc_bf16(X, g, s, sm_reserved);
+}
 
 bool tc_supported(int n) { return n == 32 || n == 64 || n == 128 || n == 256; }
 
@@ -666,6 +943,7 @@ void tc_gemm_set_attributes() {
                        (int)direct::DCfg<64>::SMEM);
   cudaFuncSetAttribute(direct::k_gemm_tc_direct<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)direct::DCfg<128>::SMEM);
+  cudaFuncSetAttribute(b16::k_gemm_tc_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b16::SMEM);
 }
 
 }  // namespace ibm
