@@ -73,11 +73,11 @@ METHOD_PASSES = {"fp32": 57, "mixed": 65}
 # (profiles/launches_production_fp32.md, launches_production_mixed.md);
 # valid for the kernels of those captures and to be refreshed whenever one
 # of them changes.
-_TRAFFIC_COMMON = {"rhs": 1742.9e6, "af_yz": 1156.4e6, "af_x": 753.6e6, "mass_div": 519.3e6,
-                   "poisson_x": 405.3e6, "ib": 57.9e6}
+_TRAFFIC_COMMON = {"rhs": 1742.6e6, "af_yz": 1156.4e6, "af_x": 753.7e6, "mass_div": 519.2e6,
+                   "poisson_x": 405.0e6, "ib": 57.9e6, "project": 1201.0e6}
 TRAFFIC_BYTES = {
-    "fp32": dict(_TRAFFIC_COMMON, project=1200.9e6),
-    "mixed": dict(_TRAFFIC_COMMON),
+    "fp32": dict(_TRAFFIC_COMMON, dht2d=209.6e6),
+    "mixed": dict(_TRAFFIC_COMMON, dht2d=212.2e6, tc_bf16=84.5e6, residual=317.7e6, poisson_x16=150.4e6),
 }
 # FP64 path: the explicit stage's FP64 instructions per cell (DFMA + DMUL +
 # DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of
