@@ -27,6 +27,9 @@ constexpr int XCHUNK = 8;    // x planes per block in 3-D kernels
 // 1e-9 in FP32).
 constexpr int SEG = 32;      // outputs per thread in the implicit line solves
 constexpr int HMAX = 24;     // largest warm-up the segments carry
+// FP32 runs stop at the warm-up that covers the same diffusion numbers (the
+// FP32 tolerance needs about half the planes): smaller shared-memory segments
+template <class T> constexpr int hmax_of() { return sizeof(T) == 8 ? HMAX : 13; }
 
 __device__ inline double af_theta(double r) { return 2.0 * asinh(0.5 / sqrt(r)); }
 
@@ -36,7 +39,7 @@ __device__ inline double af_theta(double r) { return 2.0 * asinh(0.5 / sqrt(r));
 // pipe. Each kernel writes only the fields it owns: the structural update
 // runs concurrently and owns flag_pending.
 __global__ void k_begin_step(Consts c, Params* prm, const double* __restrict__ partial,
-                             int n_partial, double tol) {
+                             int n_partial, double tol, int hmax) {
   __shared__ unsigned long long wmax[32];
   unsigned long long mb = 0ull;
   for (int b = threadIdx.x; b < n_partial; b += blockDim.x)
@@ -68,9 +71,9 @@ __global__ void k_begin_step(Consts c, Params* prm, const double* __restrict__ p
     const double rho = exp(-th);
     int H = (int)ceil(log(tol) / log(rho));
     if (!(H >= 1)) H = 1;
-    if (H > HMAX) {
+    if (H > hmax) {
       err |= ERR_AF_RANGE;
-      H = HMAX;
+      H = hmax;
     }
     // velocity Verlet is stable for dt_s omega < 2; omega_max is a Gershgorin
     // upper bound, so dt_s = dt / n_sub <= 1.8 / omega_max keeps every mode stable
@@ -802,7 +805,7 @@ k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
         const T* __restrict__ d0, const T* __restrict__ d1, const T* __restrict__ d2,
         T* __restrict__ e0, T* __restrict__ e1, T* __restrict__ e2, const T* __restrict__ o0,
         const T* __restrict__ o1, const T* __restrict__ o2, const T* __restrict__ inc) {
-  __shared__ T s[(XS + 2 * HMAX) * 32];
+  __shared__ T s[(XS + 2 * hmax_of<T>()) * 32];
   const int P = c.ny * c.nz;
   const int lane = threadIdx.x;
   const int col0 = blockIdx.x * 32;
@@ -1802,7 +1805,7 @@ void launch_inflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s)
 template <class T>
 void launch_begin_step(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   const double tol = sizeof(T) == 8 ? 1e-17 : 1e-9;
-  k_begin_step<<<1, 1024, 0, s>>>(c, f.prm, f.partial, f.n_partial, tol);
+  k_begin_step<<<1, 1024, 0, s>>>(c, f.prm, f.partial, f.n_partial, tol, hmax_of<T>());
 }
 
 template <class T>
