@@ -459,6 +459,20 @@ int ibm_gen_time(ibm_gen* g, int what, int nrep, double* ms);
  * renormalisation; it damps slow drifts of the rollout away from the data.
  * 0 <= lambda <= 1 (0, the default, disables it; plane may then be NULL). */
 int ibm_gen_set_relax(ibm_gen* g, const double* plane, double lambda);
+/* spectral relaxation of the rollout (256 x 256 planes, after
+ * ibm_gen_set_relax with lambda > 0, whose plane is the reference q_ref):
+ * after each keyframe step the fluctuation f = q - q_ref of every component
+ * is taken to Fourier space (2-D, y and z periodic) and the amplitude of each
+ * wavenumber k scaled by (S(k) / P(k))^(lambda / 2), clamped to [1/2, 2],
+ * P(k) its current power and S(k) = power[c][ky][kz] the target, e.g. the
+ * recorded planes' mean |FFT2(f)|^2 (unnormalised transform, normalised
+ * units of ibm_gen_set_norm); the phases are kept. It keeps the rollout's
+ * spectrum on the data's where errors would otherwise accumulate in some
+ * wavenumbers. 0 <= lambda <= 1 (0, the default, disables it; power may
+ * then be NULL). IBM_EINVAL for other plane sizes or without the relaxation
+ * plane; IBM_ENOMEM if its buffers (four planes of 3 ny nz floats) cannot be
+ * allocated. */
+int ibm_gen_set_spectrum(ibm_gen* g, const double* power, double lambda);
 /* rollout: start from two raw planes [3][ny][nz] (FP32) */
 int ibm_gen_rollout_init(ibm_gen* g, const float* plane_prev, const float* plane_cur);
 /* generate the next plane: q = q_t + delta (relaxed, see above), each component's plane mean

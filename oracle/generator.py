@@ -226,6 +226,25 @@ def rollout_step(q_t, delta, rms_target, q_ref=None, lam=0.0):
     return renormalise(q, rms_target)
 
 
+def spectral_relax(q, q_ref, power, lam, lo=0.5, hi=2.0):
+    """Spectral relaxation of a keyframe (a stated reading, the rollout's
+    second closure): the fluctuation f = q - q_ref of every component is
+    taken to Fourier space (2-D, periodic y and z), the amplitude of each
+    wavenumber k multiplied by clip((S(k) / |F(k)|^2)^(lam / 2), lo, hi) with
+    S = power[c] the target power (unnormalised FFT), the phases kept, and
+    the plane transformed back. q, q_ref: [ny, nz, 3]; power: [3, ny, nz]."""
+    out = np.array(q, dtype=np.float64)
+    for c in range(3):
+        F = np.fft.fft2(out[:, :, c] - q_ref[:, :, c])
+        P = np.abs(F) ** 2
+        S = np.asarray(power[c], dtype=np.float64)
+        fac = np.ones_like(P)
+        ok = (P > 0) & (S > 0)
+        fac[ok] = np.clip((S[ok] / P[ok]) ** (0.5 * lam), lo, hi)
+        out[:, :, c] = q_ref[:, :, c] + np.real(np.fft.ifft2(F * fac))
+    return out
+
+
 def renormalise(q, rms_target):
     """Rollout closure (a stated reading): each component of a generated plane
     has its plane mean removed and is rescaled to the target rms, so that the

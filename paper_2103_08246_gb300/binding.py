@@ -31,7 +31,9 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_gen_create", "ibm_gen_param_count", "ibm_gen_set_params", "ibm_gen_get_params",
            "ibm_gen_get_grads", "ibm_gen_set_norm", "ibm_gen_forward", "ibm_gen_grad", "ibm_gen_adam_step",
-           "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_relax", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init", "ibm_gen_rollout", "ibm_gen_emit", "ibm_gen_history", "ibm_gen_save", "ibm_gen_load", "ibm_gen_sync",
+           "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_relax",
+           "ibm_gen_set_spectrum", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init",
+           "ibm_gen_rollout", "ibm_gen_emit", "ibm_gen_history", "ibm_gen_save", "ibm_gen_load", "ibm_gen_sync",
            "ibm_gen_destroy", "ibm_check_bounded_wait", "ibm_destroy", "ibm_strerror")
 _VOID = ("ibm_destroy", "ibm_ensemble_destroy", "ibm_gen_destroy")
 
@@ -158,6 +160,7 @@ def load(path: str = LIB_PATH):
     lib.ibm_gen_set_lr.argtypes = [vp, ctypes.c_double]
     lib.ibm_gen_set_noise.argtypes = [vp, ctypes.c_double, ctypes.c_ulonglong]
     lib.ibm_gen_set_relax.argtypes = [vp, _dp, ctypes.c_double]
+    lib.ibm_gen_set_spectrum.argtypes = [vp, _dp, ctypes.c_double]
     lib.ibm_gen_time.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp]
     lib.ibm_gen_rollout_init.argtypes = [vp, vp, vp]
     lib.ibm_gen_rollout.argtypes = [vp, vp, vp, vp, ctypes.c_int]
@@ -403,6 +406,11 @@ def ibm_gen_set_noise(gen, std, seed=0):
 def ibm_gen_set_relax(gen, plane, lam):
     a = None if plane is None else np.ascontiguousarray(plane, dtype=np.float64)
     _check(load().ibm_gen_set_relax(gen, _ptr(a), float(lam)), "ibm_gen_set_relax")
+
+
+def ibm_gen_set_spectrum(gen, power, lam):
+    a = None if power is None else np.ascontiguousarray(power, dtype=np.float64)
+    _check(load().ibm_gen_set_spectrum(gen, _ptr(a), float(lam)), "ibm_gen_set_spectrum")
 
 
 def ibm_gen_set_lr(gen, lr):
@@ -655,6 +663,11 @@ class Generator:
     def set_relax(self, plane, lam):
         """plane: host [3, ny, nz] raw plane (e.g. the data's time mean)."""
         ibm_gen_set_relax(self.handle, plane, lam)
+
+    def set_spectrum(self, power, lam):
+        """power: host [3, ny, nz] target Fourier power of the normalised
+        fluctuation about the relaxation plane (after set_relax)."""
+        ibm_gen_set_spectrum(self.handle, power, lam)
 
     def time(self, what, nrep=10):
         return ibm_gen_time(self.handle, GEN_TIMINGS[what] if isinstance(what, str) else what, nrep)

@@ -62,6 +62,12 @@
 #include "tcgen05.cuh"
 
 namespace ibm {
+// the FP32 2-D Hartley transform of 256 x 256 planes (poisson.cu)
+bool dht2d_planes_fp32(const float* in, float* out, int nplanes, const float* tw, cudaStream_t s);
+void poisson_set_attributes();
+}  // namespace ibm
+
+namespace ibm {
 
 namespace {
 
@@ -865,6 +871,62 @@ __global__ void k_relax(float* __restrict__ delta, const float* __restrict__ qt,
   if (i < n) delta[i] -= lambda * (qt[i] - qref[i]);
 }
 
+// Spectral relaxation of a new keyframe towards the data's power spectrum:
+// f = q - q_ref per component and its separable 2-D Hartley transform
+// H = H_y f H_z. With H1..H4 = H at (ky, kz), (ky, -kz), (-ky, kz), (-ky, -kz),
+// the Fourier coefficients of the real plane are
+//   F(ky, kz)  = (H2 + H3) / 2 - i (H1 - H4) / 2,
+//   F(ky, -kz) = (H1 + H4) / 2 - i (H2 - H3) / 2,
+// so each is multiplied by its factor (S(k) / |F(k)|^2)^(lambda / 2), clamped
+// to [1/2, 2] per keyframe, and H1 rebuilt as f2 Re F(ky, -kz) - f1 Im F(ky, kz);
+// the same transform / (ny nz) returns the relaxed plane. The phases (the
+// network's structure) are kept; only the amplitude of each wavenumber moves
+// towards the record's mean.
+__global__ void k_spec_gather(const float* __restrict__ q, const float* __restrict__ qref, int P,
+                              float* __restrict__ f) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) f[(size_t)c * P + p] = q[(size_t)p * 3 + c] - qref[(size_t)p * 3 + c];
+}
+
+__device__ inline float spec_factor(float target, float pw, float lambda) {
+  return (pw > 0.f && target > 0.f) ? fminf(2.f, fmaxf(0.5f, powf(target / pw, 0.5f * lambda))) : 1.f;
+}
+
+__global__ void k_spec_scale(const float* __restrict__ H, const float* __restrict__ S, int ny, int nz, float lambda,
+                             float* __restrict__ out) {
+  const int P = ny * nz;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * P) return;
+  const int c = i / P, p = i - c * P;
+  const int ky = p / nz, kz = p - ky * nz;
+  const int my = (ny - ky) % ny, mz = (nz - kz) % nz;
+  const float* Hc = H + (size_t)c * P;
+  const float h1 = Hc[p], h2 = Hc[ky * nz + mz], h3 = Hc[my * nz + kz], h4 = Hc[my * nz + mz];
+  const float re1 = 0.5f * (h2 + h3), im1 = -0.5f * (h1 - h4);
+  const float re2 = 0.5f * (h1 + h4), im2 = -0.5f * (h2 - h3);
+  const float f1 = spec_factor(S[i], re1 * re1 + im1 * im1, lambda);
+  const float f2 = spec_factor(S[(size_t)c * P + ky * nz + mz], re2 * re2 + im2 * im2, lambda);
+  out[i] = f2 * re2 - f1 * im1;
+}
+
+template <class T>
+__global__ void k_spec_scatter(const float* __restrict__ f, const float* __restrict__ qref, int P, float inv_n,
+                               float3 dmean, float3 dstd, float* __restrict__ q, T* __restrict__ u,
+                               T* __restrict__ v, T* __restrict__ w) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float mu[3] = {dmean.x, dmean.y, dmean.z}, sd[3] = {dstd.x, dstd.y, dstd.z};
+  T* outs[3] = {u, v, w};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float qn = qref[(size_t)p * 3 + c] + f[(size_t)c * P + p] * inv_n;
+    q[(size_t)p * 3 + c] = qn;
+    if (outs[c]) outs[c][p] = (T)(mu[c] + sd[c] * qn);
+  }
+}
+
 // raw planes [3][P] -> normalised [P][3]
 __global__ void k_normalise(const float* __restrict__ plane, int P, float3 mean, float3 istd, float* __restrict__ q) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -959,6 +1021,10 @@ struct ibm_gen {
   float noise_std = 0.f;            // training-input noise (normalised units)
   float relax = 0.f;                // rollout relaxation rate towards qref, per keyframe
   float* qref = nullptr;            // normalised reference plane [P][3]
+  float spec_lambda = 0.f;          // spectral relaxation exponent per keyframe
+  float* spec = nullptr;            // target power spectrum of q - q_ref, [3][ny][nz]
+  float* sbuf[2] = {nullptr, nullptr};   // [3][ny][nz] transform scratch
+  float* twz = nullptr;             // 256-point twiddles of the transform
   unsigned long long noise_seed = 0;
   int* error = nullptr;
   std::vector<void*> allocs;
@@ -1354,6 +1420,31 @@ int ibm_gen_set_noise(ibm_gen* g, double std, unsigned long long seed) {
   return IBM_OK;
 }
 
+int ibm_gen_set_spectrum(ibm_gen* g, const double* power, double lambda) {
+  if (!g || !(lambda >= 0.0 && lambda <= 1.0) || (lambda > 0.0 && !power)) return IBM_EINVAL;
+  if (lambda > 0.0 && (g->ny != 256 || g->nz != 256 || !(g->relax > 0.f))) return IBM_EINVAL;
+  g->spec_lambda = (float)lambda;
+  if (lambda == 0.0) return IBM_OK;
+  const size_t P = g->P;
+  if (!g->spec) {
+    if (!dalloc(g, &g->spec, 3 * P) || !dalloc(g, &g->sbuf[0], 3 * P) || !dalloc(g, &g->sbuf[1], 3 * P) ||
+        !dalloc(g, &g->twz, 256))
+      return IBM_ENOMEM;
+    ibm::poisson_set_attributes();
+  }
+  std::vector<float> sp(3 * P), tw(256);
+  for (size_t i = 0; i < 3 * P; ++i) sp[i] = (float)power[i];
+  for (int t = 0; t < 128; ++t) {
+    tw[2 * t] = (float)std::cos(2.0 * M_PI * t / 256.0);
+    tw[2 * t + 1] = (float)-std::sin(2.0 * M_PI * t / 256.0);
+  }
+  if (cudaMemcpyAsync(g->spec, sp.data(), 3 * P * sizeof(float), cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+      cudaMemcpyAsync(g->twz, tw.data(), 256 * sizeof(float), cudaMemcpyHostToDevice, g->stream) != cudaSuccess)
+    return IBM_ECUDA;
+  if (cudaStreamSynchronize(g->stream) != cudaSuccess) return IBM_ECUDA;
+  return check_error(g);
+}
+
 int ibm_gen_set_relax(ibm_gen* g, const double* plane, double lambda) {
   if (!g || !(lambda >= 0.0 && lambda <= 1.0) || (lambda > 0.0 && !plane)) return IBM_EINVAL;
   g->relax = (float)lambda;
@@ -1452,6 +1543,21 @@ int ibm_gen_rollout(ibm_gen* g, void* u, void* v, void* w, int precision) {
   else
     k_roll_emit<float><<<(P + 255) / 256, 256, 0, g->stream>>>(qt, g->delta, P, mean, scale, g->dmean, g->dstd,
                                                                qp, (float*)u, (float*)v, (float*)w);
+  if (g->spec_lambda > 0.f) {
+    const unsigned nb = (unsigned)((P + 255) / 256);
+    k_spec_gather<<<nb, 256, 0, g->stream>>>(qp, g->qref, P, g->sbuf[0]);
+    if (!dht2d_planes_fp32(g->sbuf[0], g->sbuf[1], 3, g->twz, g->stream)) return IBM_ECUDA;
+    k_spec_scale<<<(3 * P + 255) / 256, 256, 0, g->stream>>>(g->sbuf[1], g->spec, g->ny, g->nz, g->spec_lambda,
+                                                              g->sbuf[0]);
+    if (!dht2d_planes_fp32(g->sbuf[0], g->sbuf[1], 3, g->twz, g->stream)) return IBM_ECUDA;
+    const float inv_n = 1.f / (float)P;
+    if (precision == IBM_FP64)
+      k_spec_scatter<double><<<nb, 256, 0, g->stream>>>(g->sbuf[1], g->qref, P, inv_n, g->dmean, g->dstd, qp,
+                                                       (double*)u, (double*)v, (double*)w);
+    else
+      k_spec_scatter<float><<<nb, 256, 0, g->stream>>>(g->sbuf[1], g->qref, P, inv_n, g->dmean, g->dstd, qp,
+                                                      (float*)u, (float*)v, (float*)w);
+  }
   g->cur ^= 1;
   return cuda_status(cudaGetLastError());
 }

@@ -831,6 +831,14 @@ bool launch_dht2d_on(const Consts& c, const Fields<float>& f, const float* in, f
   return true;
 }
 
+// the same transform of `nplanes` 256 x 256 planes outside a solver state
+// (the generator's spectral relaxation); tw: the 256-point twiddles
+bool dht2d_planes_fp32(const float* in, float* out, int nplanes, const float* tw, cudaStream_t s) {
+  if (nplanes <= 0) return true;
+  k_dht2d_r16<<<nplanes * R16_CLUSTER, R16_THREADS, R16_SMEM, s>>>(in, out, tw);
+  return cudaGetLastError() == cudaSuccess;
+}
+
 template <class T>
 void launch_poisson(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   if (launch_dht2d(c, f, s)) {

@@ -113,6 +113,7 @@ template <class T> bool launch_af_yz(const Consts& c, const Fields<T>& f, int cu
 template <class T> bool launch_dht2d(const Consts& c, const Fields<T>& f, cudaStream_t s);
 // FP32 2-D transform of every 256 x 256 plane from `in` to `out` (may alias); false for other shapes
 bool launch_dht2d_on(const Consts& c, const Fields<float>& f, const float* in, float* out, cudaStream_t s);
+bool dht2d_planes_fp32(const float* in, float* out, int nplanes, const float* tw, cudaStream_t s);
 template <class T> void launch_mass(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_div(const Consts& c, const Fields<T>& f, int cur, bool initial, cudaStream_t s);
 // phi = phi_a (f.phi when null) + phi_b (FP32) or + phi_b16 (bfloat16, FP32 fields only)

@@ -127,6 +127,20 @@ def data_norm(planes, sample=256, seed=0):
     return mean, std, rms, a.mean(axis=0)
 
 
+def data_spectrum(planes, std, mean_plane, sample=512, seed=2):
+    """Mean 2-D Fourier power |FFT2(f)|^2 (unnormalised transform) of the
+    recorded planes' fluctuation about the time-mean plane, in the
+    generator's normalised units: the target of the rollout's spectral
+    relaxation, [3, ny, nz]."""
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(planes.shape[0], min(sample, planes.shape[0]), replace=False))
+    acc = np.zeros(mean_plane.shape)
+    for i in idx:
+        f = (planes[i].double().cpu().numpy() - mean_plane) / std[:, None, None]
+        acc += np.abs(np.fft.fft2(f, axes=(1, 2))) ** 2
+    return acc / len(idx)
+
+
 def train(gen, planes, steps, lr0=5e-4, lr1=2e-5, train_frac=0.9, seed=0, log_every=100):
     """Adam with cosine decay from lr0 to lr1; returns the loss history.
     Samples are keyframe triples (t - s, t, t + s), s = gen.stride."""
@@ -334,11 +348,11 @@ def compare(res, x_st, x0):
 
 def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3000, blocks=13, batch=8,
              precision=binding.IBM_FP32, seed=0, log=print, base=inputs.PRODUCTION, sample_every=10,
-             re=None, noise=0.03, stride=10, relax=0.01):
+             re=None, noise=0.03, stride=10, relax=0.01, spectral=0.0):
     import torch
     prod = base if re is None else base.replace(re=float(re))
     out = {"bounds": BOUNDS, "workload": base.name, "re": prod.re, "train_noise": noise, "stride": stride,
-           "relax": relax}
+           "relax": relax, "spectral": spectral}
     h = prod.lx / prod.nx
     R_SHIFT = shift_cells(prod)
     i_rec = R_SHIFT
@@ -360,10 +374,13 @@ def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3
     out["train"] = train(gen, planes, train_steps, seed=seed)
     out["train"]["n_params"] = gen.n_params
     out["train"]["baselines"] = baselines(planes, mean, std, int(planes.shape[0] * 0.9), stride)
+    power = data_spectrum(planes, std, mean_plane) if spectral > 0 else None
     diag_gen = binding.Generator(prod.ny, prod.nz, blocks=blocks, in_channels=6, batch=1, stride=stride)
     diag_gen.set_params(gen.params())
     diag_gen.set_norm(mean, std, rms)
     diag_gen.set_relax(mean_plane, relax)
+    if power is not None:
+        diag_gen.set_spectrum(power, spectral)
     out["rollout"] = rollout_diagnostics(diag_gen, planes,
                                          tuple(k for k in (1, 10, 100, 300, 800) if k * stride <= max(run_steps, 1)))
     diag_gen.close()
@@ -389,6 +406,8 @@ def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3
     gen_run.set_params(gen.params())
     gen_run.set_norm(mean, std, rms)
     gen_run.set_relax(mean_plane, relax)
+    if power is not None:
+        gen_run.set_spectrum(power, spectral)
     gen.close()
     gen_run.rollout_init(seed_prev.cpu().numpy(), seed_cur.cpu().numpy())
     ptrs = binding.ibm_inflow_planes(s.state)
@@ -444,12 +463,14 @@ def main(argv=None):
     ap.add_argument("--stride", type=int, default=10, help="solver steps between generated keyframes")
     ap.add_argument("--relax", type=float, default=0.01,
                     help="rollout relaxation rate per keyframe towards the record's time-mean plane")
+    ap.add_argument("--spectral", type=float, default=0.0,
+                    help="rollout spectral relaxation exponent per keyframe towards the record's power spectrum")
     ap.add_argument("--out", default="inflow_campaign.json")
     a = ap.parse_args(argv)
     from . import build
     build.build()
     res = campaign(a.spin, a.record, a.train_steps, a.run_steps, a.discard, a.blocks, a.batch, re=a.re,
-                   noise=a.noise, stride=a.stride, relax=a.relax)
+                   noise=a.noise, stride=a.stride, relax=a.relax, spectral=a.spectral)
     with open(a.out, "w") as f:
         json.dump(res, f, indent=1, default=lambda o: o.tolist() if hasattr(o, "tolist") else str(o))
     print(json.dumps(res["comparison"], indent=1, default=str))

@@ -346,3 +346,44 @@ def test_bad_configurations_are_refused(lib):
             binding.Generator(args["ny"], args["nz"], blocks=args["blocks"],
                               in_channels=args["in_channels"], batch=args["batch"])
         assert e.value.code == binding.IBM_EINVAL
+
+
+def test_rollout_spectral_relaxation_matches_oracle(lib):
+    """At 256 x 256 planes the keyframe's fluctuation about the reference
+    plane is moved towards a target power spectrum (the FP32 radix-16
+    transform on the GPU against numpy's FFT in the oracle): the same
+    generator state without the spectral step gives the input, the oracle's
+    spectral_relax the expected keyframe."""
+    from oracle import generator as og
+    from paper_2103_08246_gb300 import binding, inputs
+    ny = nz = 256
+    w = _params(23)
+    planes = inputs.advected_planes(3, ny, nz, seed=9)
+    mean = np.array([1.0, 0.01, -0.02])
+    std = np.array([0.1, 0.05, 0.06])
+    rms = np.array([1.0, 0.9, 1.1])
+    ref_plane = planes.mean(axis=0)
+    q_ref = np.moveaxis((ref_plane - mean[:, None, None]) / std[:, None, None], 0, -1)
+
+    def keyframe(power=None, lam=0.0):
+        gen = binding.Generator(ny, nz, blocks=BLOCKS, in_channels=CIN, batch=1)
+        gen.set_params(w)
+        gen.set_norm(mean, std, rms)
+        gen.set_relax(ref_plane, 0.2)
+        if power is not None:
+            gen.set_spectrum(power, lam)
+        gen.rollout_init(planes[0], planes[1])
+        gen.rollout(None, None, None, precision=binding.IBM_FP32)
+        gen.sync()
+        h_t, _ = gen.history()
+        gen.close()
+        return h_t
+    h_off = keyframe()
+    rng = np.random.default_rng(4)
+    P0 = np.abs(np.fft.fft2(np.moveaxis(h_off - q_ref, -1, 0), axes=(1, 2))) ** 2
+    power = P0 * np.exp(rng.uniform(np.log(0.2), np.log(5.0), size=P0.shape))
+    power = 0.5 * (power + power[:, (-np.arange(ny)) % ny][:, :, (-np.arange(nz)) % nz])
+    h_on = keyframe(power, 0.5)
+    ref = og.spectral_relax(h_off, q_ref, power, 0.5)
+    assert np.abs(h_on - ref).max() <= 1e-4 * np.abs(ref).max()
+    assert np.abs(h_on - h_off).max() > 1e-2 * np.abs(ref).max()   # the step did something

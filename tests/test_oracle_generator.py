@@ -156,3 +156,35 @@ def test_rollout_step_relaxation():
     assert np.allclose(gen.rollout_step(qt, d, rms), gen.renormalise(qt + d, rms), atol=1e-15)
     # lambda = 1 replaces q_t by the reference: the step starts from q_ref
     assert np.allclose(gen.rollout_step(qt, d, rms, qr, 1.0), gen.renormalise(qr + d, rms), atol=1e-14)
+
+
+def test_spectral_relaxation_pins():
+    """lam = 0 leaves the plane; lam = 1 with unclamped factors gives exactly
+    the target power at every wavenumber with the phases kept (checked
+    against a direct DFT sum on a small plane); clamped factors move the
+    power by at most 4x; the result stays real."""
+    from oracle import generator as gen
+    rng = np.random.default_rng(5)
+    ny, nz = 6, 8
+    q = rng.standard_normal((ny, nz, 3))
+    qr = 0.1 * rng.standard_normal((ny, nz, 3))
+    f = q - qr
+    # direct DFT, independent of numpy's FFT
+    y = np.arange(ny)[:, None, None, None]
+    z = np.arange(nz)[None, :, None, None]
+    ky = np.arange(ny)[None, None, :, None]
+    kz = np.arange(nz)[None, None, None, :]
+    E = np.exp(-2j * np.pi * (y * ky / ny + z * kz / nz))
+    F = np.einsum("yzc,yzab->cab", f, E)
+    P0 = np.abs(F) ** 2
+    assert np.allclose(gen.spectral_relax(q, qr, P0 * 3.0, 0.0), q, atol=1e-14)
+    target = P0 * rng.uniform(0.3, 3.0, size=P0.shape)
+    target = 0.5 * (target + target[:, (-np.arange(ny)) % ny][:, :, (-np.arange(nz)) % nz])   # real plane: S(k) = S(-k)
+    out = gen.spectral_relax(q, qr, target, 1.0, lo=0.0, hi=np.inf)
+    F1 = np.einsum("yzc,yzab->cab", out - qr, E)
+    assert np.allclose(np.abs(F1) ** 2, target, rtol=1e-10, atol=1e-12)
+    ph = np.abs(F) > 1e-9
+    assert np.allclose(F1[ph] / np.abs(F1[ph]), F[ph] / np.abs(F[ph]), atol=1e-10)
+    clamped = gen.spectral_relax(q, qr, P0 * 100.0, 1.0)
+    F2 = np.einsum("yzc,yzab->cab", clamped - qr, E)
+    assert np.allclose(np.abs(F2) ** 2, 4.0 * P0, rtol=1e-10, atol=1e-12)
