@@ -239,12 +239,14 @@ def main(argv=None):
     ap.add_argument("--bars", action="store_true",
                     help="compare the two bar-grid forcings instead (production workload, no flag)")
     ap.add_argument("--precision", action="store_true",
-                    help="compare the mixed and FP32 paths with the FP64 one on the laminar flag (h = 1/32)")
+                    help="compare the mixed and FP32 paths with the FP64 one on the laminar flag")
+    ap.add_argument("--cells", type=int, default=32, help="cells per unit length of the precision comparison")
+    ap.add_argument("--dt", type=float, default=6e-3, help="fixed time step of the precision comparison")
     a = ap.parse_args(argv)
     from . import build
     build.build()
     if a.precision:
-        res = precision_comparison(a.steps, a.discard)
+        res = precision_comparison(a.steps, a.discard, cells_per_length=a.cells, dt=a.dt)
         with open(a.out, "w") as f:
             json.dump(res, f, indent=1)
         print(json.dumps(res, indent=1))

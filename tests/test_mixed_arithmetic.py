@@ -9,7 +9,13 @@
   r = D - L_h phi, emulated in float32 with Knuth's TwoSum and the exact
   FMA product, against the FP64 evaluation rounded to FP32: identical where
   1/h^2 is a power of two, within one unit in the last place otherwise, on
-  fields whose residual is 1e-6 of the stencil's terms.
+  fields whose residual is 1e-6 of the stencil's terms;
+* the refinement with a bfloat16 correction: an FP32 predictor solve, the
+  residual in FP64 (which the double-single evaluation matches to an ulp),
+  the correction solve with every transform operand and pass output rounded
+  to bfloat16 (FP32 accumulation), summed: the predictor's error shrinks by
+  the correction's relative error (about 2^-7 here), far below FP32
+  rounding of the result.
 """
 import numpy as np
 import pytest
@@ -127,3 +133,64 @@ def test_double_single_residual_matches_fp64(h, exact):
     r32 = (D - ((pad[:-2] + pad[2:]).astype(F32) + np.roll(phi, 1, 1) + np.roll(phi, -1, 1)
                 + np.roll(phi, 1, 2) + np.roll(phi, -1, 2) - F32(6) * phi) * F32(ih2)).astype(F32)
     assert np.max(np.abs(r32.astype(np.float64) - ref)) > 100 * np.max(np.abs(r.astype(np.float64) - ref))
+
+
+def _bf16(a):
+    """Round to bfloat16 (nearest, ties to even), returned as float32."""
+    b = np.asarray(a, dtype=F32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(F32)
+
+
+def _x_solve(Dh, h):
+    """Per transverse mode the Neumann x solve of the Hartley-transformed
+    Poisson equation (mode (0, 0) pinned and its mean removed), in FP64."""
+    nx, ny, nz = Dh.shape
+    out = np.empty(Dh.shape)
+    for j in range(ny):
+        for k in range(nz):
+            lam = -4 * np.sin(np.pi * j / ny) ** 2 - 4 * np.sin(np.pi * k / nz) ** 2
+            A = np.diag(np.full(nx, -2.0 + lam)) + np.diag(np.ones(nx - 1), 1) + np.diag(np.ones(nx - 1), -1)
+            A[0, 0] += 1.0
+            A[-1, -1] += 1.0
+            b = h * h * Dh[:, j, k].astype(np.float64) / (ny * nz)
+            if j == 0 and k == 0:
+                A[0, :] = 0.0
+                A[0, 0] = 1.0
+                b[0] = 0.0
+                x = np.linalg.solve(A, b)
+                out[:, j, k] = x - x.mean()
+            else:
+                out[:, j, k] = np.linalg.solve(A, b)
+    return out
+
+
+def _transform2d(X, dtype, rnd=None):
+    n = X.shape[1]
+    r = rnd or (lambda a: a.astype(dtype))
+    H = r(_hartley(n))
+    T = r(np.einsum("iyz,zk->iyk", r(X), H, dtype=dtype))
+    return r(np.einsum("yj,ijk->iyk", H, T, dtype=dtype))
+
+
+def _laplacian(p, h):
+    pad = np.concatenate([p[:1], p, p[-1:]], 0)
+    return (pad[:-2] + pad[2:] + np.roll(p, 1, 1) + np.roll(p, -1, 1) + np.roll(p, 1, 2) + np.roll(p, -1, 2)
+            - 6.0 * p) / (h * h)
+
+
+def test_bfloat16_correction_refines_the_fp32_predictor():
+    rng = np.random.default_rng(0)
+    nx, n, h = 24, 16, 1.0 / 16
+    D = rng.standard_normal((nx, n, n))
+    D -= D.mean()
+    exact = _transform2d(_x_solve(_transform2d(D, np.float64), h), np.float64)
+    x0 = _transform2d(_x_solve(_transform2d(D.astype(F32), F32), h).astype(F32), F32).astype(np.float64)
+    r1 = D - _laplacian(x0, h)
+    t1 = _transform2d(_x_solve(_transform2d(_bf16(r1), F32, _bf16), h).astype(F32), F32, _bf16)
+    p = x0 + _bf16(t1).astype(np.float64)
+    scale = np.abs(exact).max()
+    e0 = np.abs(x0 - exact).max() / scale
+    e1 = np.abs(p - exact).max() / scale
+    assert 1e-8 < e0 < 1e-5          # an FP32 solve
+    assert e1 < e0 / 30 and e1 < 1e-8
