@@ -882,7 +882,15 @@ void launch_stage(ibm_state* s, int stage) {
     case IBM_STAGE_DHT_Y: launch_dht_y(c, f, st); break;
     case IBM_STAGE_DHT_Z: launch_dht_z(c, f, st); break;
     case IBM_STAGE_POISSON_X: launch_poisson_x(c, f, st); break;
-    case IBM_STAGE_PROJECT: launch_project_only(c, f, cur, false, st); break;
+    case IBM_STAGE_PROJECT:
+      // as the step runs it: the mixed solve's two parts summed as they are read
+      if (std::is_same<T, float>::value && s->precision == IBM_MIXED && c.corr_bf16)
+        launch_project_only(c, f, cur, false, st, (const T*)f.e[1], (const T*)nullptr, (const void*)f.e[2]);
+      else if (std::is_same<T, float>::value && s->precision == IBM_MIXED)
+        launch_project_only(c, f, cur, false, st, (const T*)f.e[1], (const T*)f.e[2]);
+      else
+        launch_project_only(c, f, cur, false, st);
+      break;
     case IBM_STAGE_POISSON: solve_poisson<T>(s, st); break;
     case IBM_STAGE_AF_YZ: (void)launch_af_yz(c, f, cur, st); break;
     case IBM_STAGE_DHT_2D: (void)launch_dht2d(c, f, st); break;

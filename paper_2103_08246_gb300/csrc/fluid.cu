@@ -1573,8 +1573,10 @@ k_div_vec(Consts c, const Params* __restrict__ prm, T* __restrict__ u, const T* 
 
 // TWO: 0 phi alone; 1 phi + phi_b (FP32); 2 phi + phi_b (bfloat16) -- the
 // mixed solve's predictor and correction, summed as they are read
+// two blocks per SM: the register budget of three made every variant spill
+// (0.262 against 0.207 ms for the mixed instance)
 template <class T, int TWO>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 2)
 k_project_vec(Consts c, const Params* __restrict__ prm, const T* __restrict__ ua,
               const T* __restrict__ va, const T* __restrict__ wa, T* __restrict__ ub,
               T* __restrict__ vb, T* __restrict__ wb, const T* __restrict__ phi, const void* __restrict__ phi_b,
