@@ -73,12 +73,16 @@ METHOD_PASSES = {"fp32": 57, "mixed": 65}
 # (profiles/launches_production_fp32.md, launches_production_mixed.md);
 # valid for the kernels of those captures and to be refreshed whenever one
 # of them changes.
-_TRAFFIC_COMMON = {"rhs": 1742.6e6, "af_yz": 1156.4e6, "af_x": 753.7e6, "mass_div": 519.2e6,
-                   "poisson_x": 405.0e6, "ib": 57.9e6, "project": 1201.0e6}
+_TRAFFIC_COMMON = {"rhs": 1742.7e6, "af_yz": 1156.4e6, "af_x": 752.4e6, "mass_div": 519.2e6,
+                   "poisson_x": 409.8e6, "ib": 57.9e6}
 TRAFFIC_BYTES = {
-    "fp32": dict(_TRAFFIC_COMMON, dht2d=209.6e6),
-    "mixed": dict(_TRAFFIC_COMMON, dht2d=212.2e6, tc_bf16=84.5e6, residual=317.7e6, poisson_x16=150.4e6),
+    "fp32": dict(_TRAFFIC_COMMON, dht2d=209.8e6, project=1181.2e6),
+    "mixed": dict(_TRAFFIC_COMMON, dht2d=212.2e6, tc_bf16=84.5e6, residual=317.7e6, poisson_x16=150.4e6,
+                  project=1258.1e6),
 }
+# the mixed path's projection reads the solve's two parts (FP32 predictor,
+# bfloat16 correction): half a pass more than FIELD_PASSES["project"]
+MIXED_PASSES = {"project": 9.5}
 # FP64 path: the explicit stage's FP64 instructions per cell (DFMA + DMUL +
 # DADD, from an ncu count of k_rhs_vec<double>) and the FP64 issue rate of
 # GB300 (2 per clock per SM): the FP64 step is bound by that pipe.
@@ -460,7 +464,8 @@ def stage_roofline(wl, precision, peak_gbs, peak_kind):
     for k in PER_STEP[key]:
         if k in FIELD_PASSES:
             n = cells["pressure" if k in PRESSURE_GRID else "velocity"]
-            nbytes = FIELD_PASSES[k] * n * elem
+            passes = MIXED_PASSES.get(k, FIELD_PASSES[k]) if key == "mixed" else FIELD_PASSES[k]
+            nbytes = passes * n * elem
         elif k == "ib":
             nbytes = ib_bytes
         else:
