@@ -112,14 +112,14 @@ def test_wide_transverse_grid(lib, precision):
     gpu.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
 def test_eulerian_bar_forcing(lib, precision):
     """The bars forced on the Eulerian nodes (solid volume fraction) instead of
     markers, with the flag's markers: FP64 to 1e-9, FP32 to its bounds; the
     Eulerian forcing costs a fraction of the markers' (no gathers, no
     atomics)."""
     from paper_2103_08246_gb300 import binding
-    prec = binding.IBM_FP64 if precision == "fp64" else binding.IBM_FP32
+    prec = {"fp64": binding.IBM_FP64, "fp32": binding.IBM_FP32, "mixed": binding.IBM_MIXED}[precision]
     wl = _small(shape=(24, 16, 16), bars_on=True, bar_x=1.5, bar_forcing="eulerian", **FLAG)
     gpu, ora = _run(wl, prec, 10)
     if prec == binding.IBM_FP64:
