@@ -433,6 +433,15 @@ int ibm_gen_adam_step(ibm_gen* g);
  * loss (host, nullable): the batch loss before the step. */
 int ibm_gen_train_step(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch,
                        double* loss);
+/* pushforward training step (rollout-aware): a first forward pass predicts
+ * q^_t = q_{t-s} + delta(q_{t-s}, q_{t-2s}) (with the training-input noise,
+ * no gradients), then the step of ibm_gen_train_step runs on the inputs
+ * (q^_t, q_{t-s}) with the target q_{t+s} - q^_t, so that the network learns
+ * to correct its own one-step errors, as in a rollout. 2 stride <= t_idx[b]
+ * < n_planes - stride; otherwise as ibm_gen_train_step (loss: the second
+ * pass's batch loss before the update). */
+int ibm_gen_train_step_pushforward(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch,
+                                   double* loss);
 /* loss (host double) of a batch of raw planes as in ibm_gen_train_step,
  * without gradients or update (validation) */
 int ibm_gen_eval(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch,

@@ -31,7 +31,8 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_ensemble_step", "ibm_ensemble_destroy",
            "ibm_gen_create", "ibm_gen_param_count", "ibm_gen_set_params", "ibm_gen_get_params",
            "ibm_gen_get_grads", "ibm_gen_set_norm", "ibm_gen_forward", "ibm_gen_grad", "ibm_gen_adam_step",
-           "ibm_gen_train_step", "ibm_gen_eval", "ibm_gen_set_noise", "ibm_gen_set_relax",
+           "ibm_gen_train_step", "ibm_gen_train_step_pushforward", "ibm_gen_eval", "ibm_gen_set_noise",
+           "ibm_gen_set_relax",
            "ibm_gen_set_spectrum", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init",
            "ibm_gen_rollout", "ibm_gen_emit", "ibm_gen_history", "ibm_gen_save", "ibm_gen_load", "ibm_gen_sync",
            "ibm_gen_destroy", "ibm_check_bounded_wait", "ibm_destroy", "ibm_strerror")
@@ -156,6 +157,7 @@ def load(path: str = LIB_PATH):
     lib.ibm_gen_grad.argtypes = [vp, vp, vp, vp, ctypes.c_int, _dp]
     lib.ibm_gen_adam_step.argtypes = [vp]
     lib.ibm_gen_train_step.argtypes = [vp, vp, ctypes.c_int, ip, ctypes.c_int, _dp]
+    lib.ibm_gen_train_step_pushforward.argtypes = [vp, vp, ctypes.c_int, ip, ctypes.c_int, _dp]
     lib.ibm_gen_eval.argtypes = [vp, vp, ctypes.c_int, ip, ctypes.c_int, _dp]
     lib.ibm_gen_set_lr.argtypes = [vp, ctypes.c_double]
     lib.ibm_gen_set_noise.argtypes = [vp, ctypes.c_double, ctypes.c_ulonglong]
@@ -388,6 +390,16 @@ def ibm_gen_train_step(gen, planes, n_planes, t_idx, with_loss=True):
     _check(load().ibm_gen_train_step(gen, planes, int(n_planes),
                                      idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), idx.size,
                                      ctypes.byref(loss) if with_loss else None), "ibm_gen_train_step")
+    return loss.value if with_loss else None
+
+
+def ibm_gen_train_step_pushforward(gen, planes, n_planes, t_idx, with_loss=True):
+    idx = np.ascontiguousarray(t_idx, dtype=np.int32)
+    loss = ctypes.c_double(0.0)
+    _check(load().ibm_gen_train_step_pushforward(gen, planes, int(n_planes),
+                                                 idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), idx.size,
+                                                 ctypes.byref(loss) if with_loss else None),
+           "ibm_gen_train_step_pushforward")
     return loss.value if with_loss else None
 
 
@@ -650,6 +662,10 @@ class Generator:
     def train_step(self, planes, t_idx, with_loss=True):
         """planes: CUDA float32 tensor [n, 3, ny, nz]."""
         return ibm_gen_train_step(self.handle, planes.data_ptr(), planes.shape[0], t_idx, with_loss)
+
+    def train_step_pushforward(self, planes, t_idx, with_loss=True):
+        """The pushforward step: inputs from the network's own prediction of q_t."""
+        return ibm_gen_train_step_pushforward(self.handle, planes.data_ptr(), planes.shape[0], t_idx, with_loss)
 
     def eval(self, planes, t_idx):
         return ibm_gen_eval(self.handle, planes.data_ptr(), planes.shape[0], t_idx)

@@ -679,6 +679,42 @@ __global__ void k_input_planes(const float* __restrict__ planes, int P, int nz, 
   store_granule(x, row, 1, z, 16, nz, r1);
 }
 
+// pushforward inputs (after a forward pass on (q_{t-s}, q_{t-2s}) whose
+// delta is in `delta`): the network's own prediction q^_t = q_{t-s} + delta
+// takes the place of q_t, the previous keyframe is q_{t-s}, and the target
+// is q_{t+s} - q^_t, so the network learns to correct its own one-step
+// errors (no gradient flows into the first pass)
+__global__ void k_pushforward_planes(const float* __restrict__ planes, int P, int nz, int stride, TIdx idx, int B,
+                                     float3 mean, float3 istd, const float* __restrict__ delta,
+                                     bf16* __restrict__ x, float* __restrict__ target) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= B * P) return;
+  const int b = i / P, p = i - b * P;
+  const int t = idx.t[b];
+  const float mu[3] = {mean.x, mean.y, mean.z}, is[3] = {istd.x, istd.y, istd.z};
+  uint4 r0, r1;
+  bf16* e0 = reinterpret_cast<bf16*>(&r0);
+  bf16* e1 = reinterpret_cast<bf16*>(&r1);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    e0[j] = __float2bfloat16_rn(0.f);
+    e1[j] = __float2bfloat16_rn(0.f);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float qp = (planes[((size_t)(t - stride) * 3 + c) * P + p] - mu[c]) * is[c];
+    const float qn = (planes[((size_t)(t + stride) * 3 + c) * P + p] - mu[c]) * is[c];
+    const float qh = qp + delta[(size_t)i * 3 + c];
+    e0[c] = __float2bfloat16_rn(qh);
+    e0[3 + c] = __float2bfloat16_rn(qp);
+    target[(size_t)i * 3 + c] = qn - qh;
+  }
+  const size_t row = (size_t)i / nz;
+  const int z = i - (int)(row * nz);
+  store_granule(x, row, 0, z, 16, nz, r0);
+  store_granule(x, row, 1, z, 16, nz, r1);
+}
+
 // network input from normalised planes [B][P][3]
 __global__ void k_input_q(const float* __restrict__ qt, const float* __restrict__ qp, int n, int nz,
                           bf16* __restrict__ x) {
@@ -1387,6 +1423,31 @@ int ibm_gen_train_step(ibm_gen* g, const float* planes, int n_planes, const int*
   ibm::k_input_planes<<<(unsigned)((n + 255) / 256), 256, 0, g->stream>>>(
       planes, (int)g->P, g->nz, g->stride, idx, batch, g->dmean, istd, g->noise_std, g->noise_seed + (unsigned long long)g->t, g->x,
       g->target);
+  backward(g, batch);
+  adam(g);
+  if (!loss) return cuda_status(cudaGetLastError());
+  return read_loss(g, n, loss);
+}
+
+int ibm_gen_train_step_pushforward(ibm_gen* g, const float* planes, int n_planes, const int* t_idx, int batch,
+                                   double* loss) {
+  if (!g || !planes || !t_idx || batch < 1 || batch > g->batch) return IBM_EINVAL;
+  ibm::TIdx idx{}, prev{};
+  for (int b = 0; b < batch; ++b) {
+    if (t_idx[b] < 2 * g->stride || t_idx[b] + g->stride >= n_planes) return IBM_EINVAL;
+    idx.t[b] = t_idx[b];
+    prev.t[b] = t_idx[b] - g->stride;
+  }
+  const size_t n = (size_t)batch * g->P;
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  const float3 istd = make_float3(1.f / g->dstd.x, 1.f / g->dstd.y, 1.f / g->dstd.z);
+  // the first pass predicts q_t from (q_{t-s}, q_{t-2s}), with the training-input noise
+  ibm::k_input_planes<<<nb, 256, 0, g->stream>>>(planes, (int)g->P, g->nz, g->stride, prev, batch, g->dmean, istd,
+                                                 g->noise_std, g->noise_seed + (unsigned long long)g->t, g->x,
+                                                 g->target);
+  forward(g, batch);
+  ibm::k_pushforward_planes<<<nb, 256, 0, g->stream>>>(planes, (int)g->P, g->nz, g->stride, idx, batch, g->dmean,
+                                                       istd, g->delta, g->x, g->target);
   backward(g, batch);
   adam(g);
   if (!loss) return cuda_status(cudaGetLastError());

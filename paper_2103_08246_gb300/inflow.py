@@ -141,9 +141,12 @@ def data_spectrum(planes, std, mean_plane, sample=512, seed=2):
     return acc / len(idx)
 
 
-def train(gen, planes, steps, lr0=5e-4, lr1=2e-5, train_frac=0.9, seed=0, log_every=100):
+def train(gen, planes, steps, lr0=5e-4, lr1=2e-5, train_frac=0.9, seed=0, log_every=100, pushforward=0.0):
     """Adam with cosine decay from lr0 to lr1; returns the loss history.
-    Samples are keyframe triples (t - s, t, t + s), s = gen.stride."""
+    Samples are keyframe triples (t - s, t, t + s), s = gen.stride. In the
+    second half of the steps a fraction `pushforward` of them are pushforward
+    steps (the input q_t replaced by the network's own prediction from
+    (q_{t-s}, q_{t-2s}))."""
     n = planes.shape[0]
     s_ = gen.stride
     n_train = int(n * train_frac)
@@ -154,9 +157,13 @@ def train(gen, planes, steps, lr0=5e-4, lr1=2e-5, train_frac=0.9, seed=0, log_ev
     for s in range(steps):
         lr = lr1 + 0.5 * (lr0 - lr1) * (1.0 + np.cos(np.pi * s / max(steps - 1, 1)))
         gen.set_lr(lr)
-        idx = rng.integers(s_, n_train - s_, size=gen.batch)
         log = (s % log_every == 0) or s == steps - 1
-        loss = gen.train_step(planes, idx, with_loss=log)
+        if pushforward > 0 and 2 * s >= steps and rng.random() < pushforward:
+            idx = rng.integers(2 * s_, n_train - s_, size=gen.batch)
+            loss = gen.train_step_pushforward(planes, idx, with_loss=log)
+        else:
+            idx = rng.integers(s_, n_train - s_, size=gen.batch)
+            loss = gen.train_step(planes, idx, with_loss=log)
         if log:
             vb = rng.choice(val_idx, size=gen.batch, replace=len(val_idx) < gen.batch)
             hist["step"].append(s)
@@ -348,11 +355,11 @@ def compare(res, x_st, x0):
 
 def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3000, blocks=13, batch=8,
              precision=binding.IBM_FP32, seed=0, log=print, base=inputs.PRODUCTION, sample_every=10,
-             re=None, noise=0.03, stride=10, relax=0.01, spectral=0.0):
+             re=None, noise=0.03, stride=10, relax=0.01, spectral=0.0, pushforward=0.0):
     import torch
     prod = base if re is None else base.replace(re=float(re))
     out = {"bounds": BOUNDS, "workload": base.name, "re": prod.re, "train_noise": noise, "stride": stride,
-           "relax": relax, "spectral": spectral}
+           "relax": relax, "spectral": spectral, "pushforward": pushforward}
     h = prod.lx / prod.nx
     R_SHIFT = shift_cells(prod)
     i_rec = R_SHIFT
@@ -371,7 +378,7 @@ def campaign(spin=3000, record=4000, train_steps=1500, run_steps=8000, discard=3
     gen.set_params(inputs.generator_params(seed, 128, blocks, 6))
     gen.set_norm(mean, std, rms)
     gen.set_noise(noise, seed=seed + 17)
-    out["train"] = train(gen, planes, train_steps, seed=seed)
+    out["train"] = train(gen, planes, train_steps, seed=seed, pushforward=pushforward)
     out["train"]["n_params"] = gen.n_params
     out["train"]["baselines"] = baselines(planes, mean, std, int(planes.shape[0] * 0.9), stride)
     power = data_spectrum(planes, std, mean_plane) if spectral > 0 else None
@@ -465,12 +472,15 @@ def main(argv=None):
                     help="rollout relaxation rate per keyframe towards the record's time-mean plane")
     ap.add_argument("--spectral", type=float, default=0.0,
                     help="rollout spectral relaxation exponent per keyframe towards the record's power spectrum")
+    ap.add_argument("--pushforward", type=float, default=0.0,
+                    help="fraction of pushforward steps in the second half of the training")
     ap.add_argument("--out", default="inflow_campaign.json")
     a = ap.parse_args(argv)
     from . import build
     build.build()
     res = campaign(a.spin, a.record, a.train_steps, a.run_steps, a.discard, a.blocks, a.batch, re=a.re,
-                   noise=a.noise, stride=a.stride, relax=a.relax, spectral=a.spectral)
+                   noise=a.noise, stride=a.stride, relax=a.relax, spectral=a.spectral,
+                   pushforward=a.pushforward)
     with open(a.out, "w") as f:
         json.dump(res, f, indent=1, default=lambda o: o.tolist() if hasattr(o, "tolist") else str(o))
     print(json.dumps(res["comparison"], indent=1, default=str))

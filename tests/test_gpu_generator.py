@@ -143,6 +143,45 @@ def test_training_on_planes(lib):
     gen.close()
 
 
+def test_pushforward_step_matches_oracle(lib):
+    """The pushforward step's loss is the oracle's loss of the inputs
+    (q^_t, q_{t-1}) with target q_{t+1} - q^_t, q^_t = q_{t-1} + delta the
+    network's own prediction from (q_{t-1}, q_{t-2}) (taken from the GPU's
+    forward pass, rounded as the kernel rounds it); the update follows (the
+    parameters move)."""
+    from oracle import generator as og
+    from paper_2103_08246_gb300 import binding, inputs
+    planes = inputs.advected_planes(12, NY, NZ, seed=5, shift=1)
+    mean = planes.mean(axis=(0, 2, 3))
+    std = planes.std(axis=(0, 2, 3))
+    gen = binding.Generator(NY, NZ, blocks=BLOCKS, in_channels=CIN, batch=BATCH, lr=1e-3)
+    w = _params(14)
+    gen.set_params(w)
+    gen.set_norm(mean, std, [1.0, 1.0, 1.0])
+    dev = torch.as_tensor(planes.astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    idx = [4, 8]
+    pl32 = planes.astype(np.float32).astype(np.float64)
+    m32 = mean.astype(np.float32).astype(np.float64)
+    inv = (np.float32(1.0) / std.astype(np.float32)).astype(np.float64)
+
+    def q(t):
+        return np.moveaxis((pl32[t] - m32[:, None, None]) * inv[:, None, None], 0, -1)
+    qprev = np.stack([q(t - 1) for t in idx])
+    delta = gen.forward(qprev, np.stack([q(t - 2) for t in idx]))
+    qhat = (qprev.astype(np.float32) + delta.astype(np.float32)).astype(np.float64)
+    p = og.unflatten(w.astype(np.float32).astype(np.float64), 128, BLOCKS, CIN)
+    xs = [og.make_input(qhat[b], qprev[b], CIN) for b in range(BATCH)]
+    ts = [q(t + 1) - qhat[b] for b, t in enumerate(idx)]
+    loss_ref, _ = og.loss_and_grads(p, xs, ts, bf16=True)
+    loss = gen.train_step_pushforward(dev, idx)
+    assert abs(loss - loss_ref) <= 1e-3 * loss_ref, (loss, loss_ref)
+    assert np.abs(gen.params() - w.astype(np.float32)).max() > 0
+    with pytest.raises(binding.IBMError):
+        gen.train_step_pushforward(dev, [1, 4])   # needs t >= 2 stride
+    gen.close()
+
+
 def test_training_noise_matches_oracle(lib):
     """With input noise the first step's loss is the oracle's loss of the
     same SplitMix64 / Box-Muller draws (key = seed + Adam steps done)."""
