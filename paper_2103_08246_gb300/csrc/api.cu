@@ -638,6 +638,7 @@ void record_graph(ibm_state* s, int kind, int cur) {
   }
   const bool join = record_tail_body<T>(s, cur);
   if (kind == GRAPH_MID) record_head<T>(s, cur ^ 1);
+  if (kind == GRAPH_TAIL) launch_speed_check(s->c, fields<T>(s), s->stream);
   if (join) cudaStreamWaitEvent(s->stream, s->ev_join, 0);
 }
 
@@ -980,7 +981,9 @@ void record_post(ibm_state* s, int cur) {
 }
 template <class T>
 void record_tail_joined(ibm_state* s, int cur) {
-  if (record_tail_body<T>(s, cur)) cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+  const bool join = record_tail_body<T>(s, cur);
+  launch_speed_check(s->c, fields<T>(s), s->stream);
+  if (join) cudaStreamWaitEvent(s->stream, s->ev_join, 0);
 }
 
 // capture one piece of a member's step into a graph

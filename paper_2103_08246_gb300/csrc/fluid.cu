@@ -101,6 +101,33 @@ __global__ void k_begin_step(Consts c, Params* prm, const double* __restrict__ p
   }
 }
 
+// After the last step of a call: the speed maximum of the velocity that step
+// left (the projection's block partials, reduced as in k_begin_step), so that
+// a non-finite or too fast field is reported by the call that produced it
+__global__ void k_speed_check(Params* prm, const double* __restrict__ partial, int n_partial) {
+  __shared__ unsigned long long wmax[32];
+  unsigned long long mb = 0ull;
+  for (int b = threadIdx.x; b < n_partial; b += blockDim.x)
+    mb = max(mb, (unsigned long long)__double_as_longlong(partial[b]));
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mb = max(mb, wmax[q]);
+    const double m = __longlong_as_double((long long)mb);
+    prm->speed_max = m;
+    if (!isfinite(m)) atomicOr(&prm->error, ERR_NONFINITE);
+  }
+}
+
+template <class T>
+void launch_speed_check(const Consts& c, const Fields<T>& f, cudaStream_t s) {
+  (void)c;
+  k_speed_check<<<1, 1024, 0, s>>>(f.prm, f.partial, f.n_partial);
+}
+template void launch_speed_check<float>(const Consts&, const Fields<float>&, cudaStream_t);
+template void launch_speed_check<double>(const Consts&, const Fields<double>&, cudaStream_t);
+
 // Tables of the implicit factors for this step's r, one entry per thread
 // (FP64 transcendental functions: spread over many blocks, and off the
 // critical path, concurrent with the explicit stage):

@@ -97,6 +97,7 @@ struct RhsCase {
 
 // ---- fluid.cu
 template <class T> void launch_begin_step(const Consts& c, const Fields<T>& f, cudaStream_t s);
+template <class T> void launch_speed_check(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_af_tables(const Consts& c, const Fields<T>& f, cudaStream_t s);
 template <class T> void launch_inflow(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);
 template <class T> void launch_rhs(const Consts& c, const Fields<T>& f, int cur, cudaStream_t s);

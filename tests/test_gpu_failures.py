@@ -6,7 +6,10 @@ status and the CUDA context stays usable.
   a fresh state steps normally;
 * the bounded-wait self-test waits on an mbarrier that nothing completes and
   returns IBM_ETIMEOUT after its iteration limit; work on the device runs
-  normally afterwards.
+  normally afterwards;
+* a non-finite value injected on the host (ibm_set_field uploads a velocity
+  field with one NaN) is reported as IBM_EDIVERGED by the next step, in every
+  precision, and the device stays usable.
 """
 import numpy as np
 import pytest
@@ -56,3 +59,22 @@ def test_bounded_wait_times_out_and_the_context_survives(lib):
     s.step(3)
     assert np.isfinite(s.stats()["ke"])
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_injected_nan_is_reported(lib, precision):
+    import torch
+    from paper_2103_08246_gb300 import binding, inputs
+    prec = {"fp64": binding.IBM_FP64, "fp32": binding.IBM_FP32, "mixed": binding.IBM_MIXED}[precision]
+    wl = inputs.small(16, 32, 32)
+    s = binding.Solver(wl, prec, noise=inputs.initial_noise(wl))
+    s.step(2)
+    u = s.fields()[0].copy()
+    u[5, 3, 7] = np.nan
+    binding.ibm_set_field(s.state, binding.IBM_FIELD_U, u)
+    with pytest.raises(binding.IBMError) as e:
+        s.step(1)
+    assert e.value.code == binding.IBM_EDIVERGED
+    s.close()
+    x = torch.ones(4096, device="cuda")
+    assert float(x.sum()) == 4096.0
