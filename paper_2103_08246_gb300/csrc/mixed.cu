@@ -205,7 +205,10 @@ __device__ inline DS two_sum(float a, float b) {
 }
 
 // residual of one cell from its value, six neighbours and D, with
-// ih2 = ih2_hi + ih2_lo the host-split 1 / h^2
+// ih2 = ih2_hi + ih2_lo the host-split 1 / h^2. POW2: 1 / h^2 is a power of
+// two (ih2_lo = 0), so S ih2 is exact as the pair (S.hi ih2, S.lo ih2) and
+// the product's error terms vanish (the same values with fewer operations)
+template <bool POW2>
 __device__ inline float residual_ds(float pc, float pxm, float pxp, float pym, float pyp, float pzm, float pzp,
                                     float D, float ih2_hi, float ih2_lo) {
   // S = sum of the six neighbours - 6 pc, as hi + lo
@@ -218,10 +221,15 @@ __device__ inline float residual_ds(float pc, float pxm, float pxp, float pym, f
       __fadd_rn(__fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(s3.lo, s4.lo)), __fadd_rn(s5.lo, s6.lo)), q6);
   const DS S = two_sum(s6.hi, lo);
   // lap = S ih2 (exact leading product plus the cross terms)
-  const float ph = __fmul_rn(S.hi, ih2_hi);
-  const float pe = __fadd_rn(__fmaf_rn(S.hi, ih2_hi, -ph),
-                             __fadd_rn(__fmul_rn(S.hi, ih2_lo), __fmul_rn(S.lo, ih2_hi)));
-  const DS lap = two_sum(ph, pe);
+  DS lap;
+  if constexpr (POW2) {
+    lap = {__fmul_rn(S.hi, ih2_hi), __fmul_rn(S.lo, ih2_hi)};
+  } else {
+    const float ph = __fmul_rn(S.hi, ih2_hi);
+    const float pe = __fadd_rn(__fmaf_rn(S.hi, ih2_hi, -ph),
+                               __fadd_rn(__fmul_rn(S.hi, ih2_lo), __fmul_rn(S.lo, ih2_hi)));
+    lap = two_sum(ph, pe);
+  }
   // r = D - lap
   const DS t = two_sum(D, -lap.hi);
   return __fadd_rn(t.hi, __fsub_rn(t.lo, lap.lo));
@@ -230,7 +238,7 @@ __device__ inline float residual_ds(float pc, float pxm, float pxp, float pym, f
 // four consecutive z cells per thread (nz is a power of two >= 4): 16-byte loads of
 // the cell run and of its x and y neighbours, the two z neighbours past the
 // run's ends as single loads; grid (z runs, y rows, x planes)
-template <class R>
+template <class R, bool POW2>
 __global__ void k_residual_ds4(int nx, int ny, int nz, float ih2_hi, float ih2_lo, const float* __restrict__ D,
                                const float* __restrict__ phi, R* __restrict__ r) {
   const int k0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -250,10 +258,10 @@ __global__ void k_residual_ds4(int nx, int ny, int nz, float ih2_hi, float ih2_l
   const float zr = phi[row + (k0 + 4 == nz ? 0 : k0 + 4)];
   const float4 d4 = *reinterpret_cast<const float4*>(D + id);
   float4 o;
-  o.x = residual_ds(c4.x, xm.x, xp.x, ym.x, yp.x, zl, c4.y, d4.x, ih2_hi, ih2_lo);
-  o.y = residual_ds(c4.y, xm.y, xp.y, ym.y, yp.y, c4.x, c4.z, d4.y, ih2_hi, ih2_lo);
-  o.z = residual_ds(c4.z, xm.z, xp.z, ym.z, yp.z, c4.y, c4.w, d4.z, ih2_hi, ih2_lo);
-  o.w = residual_ds(c4.w, xm.w, xp.w, ym.w, yp.w, c4.z, zr, d4.w, ih2_hi, ih2_lo);
+  o.x = residual_ds<POW2>(c4.x, xm.x, xp.x, ym.x, yp.x, zl, c4.y, d4.x, ih2_hi, ih2_lo);
+  o.y = residual_ds<POW2>(c4.y, xm.y, xp.y, ym.y, yp.y, c4.x, c4.z, d4.y, ih2_hi, ih2_lo);
+  o.z = residual_ds<POW2>(c4.z, xm.z, xp.z, ym.z, yp.z, c4.y, c4.w, d4.z, ih2_hi, ih2_lo);
+  o.w = residual_ds<POW2>(c4.w, xm.w, xp.w, ym.w, yp.w, c4.z, zr, d4.w, ih2_hi, ih2_lo);
   if constexpr (sizeof(R) == 4) {
     *reinterpret_cast<float4*>(r + id) = o;
   } else {   // bfloat16: the correction's input
@@ -261,6 +269,20 @@ __global__ void k_residual_ds4(int nx, int ny, int nz, float ih2_hi, float ih2_l
     *reinterpret_cast<uint2*>(r + id) =
         make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
   }
+}
+
+// the residual kernel for this 1 / h^2 (exact pair products when it is a power of two)
+template <class R>
+static void launch_residual(const Consts& c, const float* D, const float* x0, R* r, cudaStream_t s) {
+  const double ih2 = c.inv_h * c.inv_h;
+  const float ih2_hi = (float)ih2, ih2_lo = (float)(ih2 - (double)ih2_hi);
+  int e = 0;
+  const bool pow2 = ih2_lo == 0.f && std::frexp((double)ih2_hi, &e) == 0.5;
+  const dim3 grid((c.nz / 4 + 63) / 64, c.ny, c.nx);
+  if (pow2)
+    k_residual_ds4<R, true><<<grid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, r);
+  else
+    k_residual_ds4<R, false><<<grid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, r);
 }
 
 static void gemm(const GemmArgs& g, int batch, cudaStream_t s) {
@@ -317,9 +339,6 @@ void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* 
   float* x0 = f.e[1];
   float* t1 = f.e[2];
   int* err = &f.prm->error;
-  const double ih2 = c.inv_h * c.inv_h;
-  const float ih2_hi = (float)ih2, ih2_lo = (float)(ih2 - (double)ih2_hi);
-  const dim3 rgrid((c.nz / 4 + 63) / 64, c.ny, c.nx);
   if (c.corr_bf16) {
     // predictor: x0 = L^-1 D by the FP32 FFT solve
     launch_dht2d_on(c, f, D, x0, s);
@@ -328,7 +347,7 @@ void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* 
     // residual (double-single) and correction, in bfloat16
     __nv_bfloat16* r16 = reinterpret_cast<__nv_bfloat16*>(t1);
     __nv_bfloat16* w16 = reinterpret_cast<__nv_bfloat16*>(t0);
-    k_residual_ds4<<<rgrid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, r16);
+    launch_residual(c, D, x0, r16, s);
     tc_rows_times_h_bf16(r16, H16_img, w16, c.nx, err, s, c.sm_reserved);
     tc_rows_times_h_bf16(w16, H16_img, r16, c.nx, err, s, c.sm_reserved);
     launch_poisson_x_bf16(c, f, r16, s);
@@ -341,7 +360,7 @@ void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* 
   launch_poisson_x_on(c, f, x0, s);
   transform2d(c, H, x0, t0, x0, err, s, true);
   // double-single residual and correction: t1 = L^-1 (D - L x0)
-  k_residual_ds4<<<rgrid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, D, x0, t1);
+  launch_residual(c, D, x0, t1, s);
   transform2d(c, H, t1, t0, t1, err, s);
   launch_poisson_x_on(c, f, t1, s);
   transform2d(c, H, t1, t0, t1, err, s);
@@ -349,14 +368,10 @@ void launch_poisson_mixed(const Consts& c, const Fields<float>& f, const float* 
 
 // the refinement's residual alone (stage timing): e[2] = D - L_h e[1]
 void launch_residual_mixed(const Consts& c, const Fields<float>& f, cudaStream_t s) {
-  const double ih2 = c.inv_h * c.inv_h;
-  const float ih2_hi = (float)ih2, ih2_lo = (float)(ih2 - (double)ih2_hi);
-  const dim3 rgrid((c.nz / 4 + 63) / 64, c.ny, c.nx);
   if (c.corr_bf16)
-    k_residual_ds4<<<rgrid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, f.phi, f.e[1],
-                                        reinterpret_cast<__nv_bfloat16*>(f.e[2]));
+    launch_residual(c, f.phi, f.e[1], reinterpret_cast<__nv_bfloat16*>(f.e[2]), s);
   else
-    k_residual_ds4<<<rgrid, 64, 0, s>>>(c.nx, c.ny, c.nz, ih2_hi, ih2_lo, f.phi, f.e[1], f.e[2]);
+    launch_residual(c, f.phi, f.e[1], f.e[2], s);
 }
 
 void mixed_set_attributes() {
