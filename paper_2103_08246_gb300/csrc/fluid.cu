@@ -867,22 +867,42 @@ k_af_xr(Consts c, const Params* __restrict__ prm, const T* __restrict__ ipt,
   }
   __syncwarp();
   if (!act) return;
-  // the recursions' loads (plane values, pivots) do not depend on the
-  // running value: unrolled, they issue ahead of the two-operation chain
+  // The recursions' loads (plane values, pivots) do not depend on the
+  // running value: unrolled, they issue ahead of the two-operation chain.
+  // The boundary rows 1 and m are peeled off, so the loops carry no tests.
+  // Past the first rows the LU pivots have converged to rho to the last bit
+  // (they differ from it by rho^(2k) relative): a segment whose warm-up
+  // starts beyond row 32 takes one register for all of them.
+  T* sl = s + lane;   // row k at sl[(k - ks) * 32]
+  const bool pconst = ks > 32;
+  const T ipc = ip[ks];
+  auto piv = [&](int k) { return pconst ? ipc : ip[k]; };
   T y = 0;
+  int kf = ks;
+  if (ks == 1) {
+    y = (sl[0] * ir + ib) * ip[1];
+    sl[0] = y;
+    kf = 2;
+  }
+  const int kl = ke == m ? m - 1 : ke;   // the last row of the plain loop
 #pragma unroll 8
-  for (int k = ks; k <= ke; ++k) {
-    T e = s[(k - ks) * 32 + lane] * ir;
-    if (k == m) e += ob;
-    if (k == 1) e += ib;
-    y = (e + y) * ip[k];
-    s[(k - ks) * 32 + lane] = y;
+  for (int k = kf; k <= kl; ++k) {
+    y = (sl[(k - ks) * 32] * ir + y) * piv(k);
+    sl[(k - ks) * 32] = y;
+  }
+  if (ke == m) {
+    y = (sl[(m - ks) * 32] * ir + ob + y) * piv(m);
+    sl[(m - ks) * 32] = y;
   }
   T x = 0;
 #pragma unroll 8
-  for (int k = ke; k >= k0; --k) {
-    x = s[(k - ks) * 32 + lane] + x * ip[k];
-    if (k < k1) out[(size_t)k * P] = x;
+  for (int k = ke; k >= k1; --k) x = sl[(k - ks) * 32] + x * piv(k);   // warm-up rows
+  T* o = out + (size_t)(k1 - 1) * P;
+#pragma unroll 8
+  for (int k = k1 - 1; k >= k0; --k) {
+    x = sl[(k - ks) * 32] + x * piv(k);
+    *o = x;
+    o -= P;
   }
 }
 
