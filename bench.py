@@ -448,7 +448,8 @@ def stage_roofline(wl, precision, peak_gbs, peak_kind):
     from paper_2103_08246_gb300 import binding, inputs
     key = "mixed" if precision == binding.IBM_MIXED else "fp32"
     t = binding.Solver(wl, precision, noise=inputs.initial_noise(wl))
-    t.step(2)
+    t.step(5)
+    n_sub = t.stats()["n_sub"]
     elem = 4
     cells = {"velocity": (wl.nx + 1) * wl.ny * wl.nz, "pressure": wl.nx * wl.ny * wl.nz}
     stages = {}
@@ -475,7 +476,11 @@ def stage_roofline(wl, precision, peak_gbs, peak_kind):
                       "alg_bytes_per_launch": nbytes, "achieved_gbs": gbs, "frac": gbs / peak_gbs,
                       "traffic": TRAFFIC_BYTES[key].get(k)}
     kernels["ib"]["nodes_touched"] = ib_nodes
-    dom = max((k for k in kernels if k != "ib"), key=lambda k: per_step[k])
+    # the FP64 flag update (side stream, overlapped with the pressure solve);
+    # its cost scales with the sub-step count of this state's time step
+    kernels["flag"] = {"ms_per_launch": stages["flag"], "launches_per_step": 1, "sub_steps": n_sub,
+                       "bound": "fp64 pipe and cluster barriers", "overlapped": True}
+    dom = max((k for k in kernels if k not in ("ib", "flag")), key=lambda k: per_step[k])
     d = kernels[dom]
     roof = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peak_gbs,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": d["frac"], "traffic": d["traffic"],
@@ -745,7 +750,7 @@ def run_ours(args):
             "dtype": "mixed: f32 fields, f32 fft predictor, double-single residual, bf16 tensor-core correction, f64 flag",
             "data": "synthetic",
             "config": {"workload": wl.name, "cells": cells,
-                       "precision": "mixed (fp32 fields, tf32x3 tcgen05 transforms + refinement, fp64 flag)",
+                       "precision": "mixed (fp32 fields, fp32 fft predictor, double-single residual, bf16 tcgen05 correction, fp64 flag)",
                        "cfl": wl.cfl, "re": wl.re, "markers": st["n_markers"],
                        "cache": "inputs larger than L2 (each field 134 MB)",
                        "parallelism": f"replicas x{world}"},
