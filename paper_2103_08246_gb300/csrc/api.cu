@@ -419,6 +419,7 @@ size_t carve(ibm_state* s, void* base, const Layout& L, Fields<T>& f) {
   f.p = cv.take<T>(NP);
   f.phi = cv.take<T>(NP);
   f.ptab = cv.take<T>(poisson_table_size(c));
+  f.pconv = cv.take<int>(poisson_modes(c));
   for (int q = 0; q < 3; ++q) f.dout[q] = cv.take<T>(P);
   f.tw_y = cv.take<T>(c.ny);
   f.tw_z = cv.take<T>(c.nz);

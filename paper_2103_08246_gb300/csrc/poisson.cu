@@ -596,7 +596,10 @@ k_dht2d_r16(const float* in, float* out, const float* __restrict__ twy) {
 // normalisation). One thread per mode walks x (coalesced across modes) in
 // chunks of PF planes; the loads of the next chunk (right-hand side and
 // inverse pivots) are issued before the current chunk's recursion, so each
-// thread keeps up to 4 PF independent loads in flight.
+// thread keeps up to 4 PF independent loads in flight. Past the row from
+// which a mode's stored pivots equal their limit (a few rows for all but
+// the lowest modes) the limit stays in a register and the chunks carry
+// right-hand sides only, twice as many per chunk in FP32.
 constexpr int PF = 16;
 __host__ __device__ inline size_t ptab_plane(const Consts& c) {
   return (size_t)(c.ny / 2 + 1) * (c.nz / 2 + 1);
@@ -619,108 +622,147 @@ __device__ inline S to_store(T v) {
   else return (S)v;
 }
 
+// forward elimination over planes [i0, i1) in chunks of N planes, the next
+// chunk's loads issued before the current chunk's recursion (two chunks in
+// flight); TAB: inverse pivots from the table, else the converged limit
+template <int N, bool TAB, class T, class LDF, class STF>
+__device__ __forceinline__ void px_forward(LDF LD, STF ST, const T* iv, size_t PT, int P, T lim, T scale,
+                                           bool zero_mode, int i0, int i1, T& y) {
+  constexpr int NT = TAB ? N : 1;
+  const int nch = (i1 - i0) / N;
+  T rd[N], rt[NT];
+  if (nch > 0) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      rd[q] = LD((size_t)(i0 + q) * P);
+      if constexpr (TAB) rt[q] = iv[(size_t)(i0 + q) * PT];
+    }
+  }
+  int i = i0;
+  for (int ch = 0; ch < nch; ++ch, i += N) {
+    T nd[N], nt[NT];
+    if (ch + 1 < nch) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        nd[q] = LD((size_t)(i + N + q) * P);
+        if constexpr (TAB) nt[q] = iv[(size_t)(i + N + q) * PT];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      if constexpr (TAB) {
+        const T rhs = (zero_mode && i + q == 0) ? (T)0 : rd[q] * scale;
+        y = (rhs - y) * rt[q];
+      } else {
+        y = (rd[q] * scale - y) * lim;
+      }
+      ST((size_t)(i + q) * P, y);
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      rd[q] = nd[q];
+      if constexpr (TAB) rt[q] = nt[q];
+    }
+  }
+  for (; i < i1; ++i) {   // the partial chunk
+    const size_t o = (size_t)i * P;
+    if constexpr (TAB) {
+      const T rhs = (zero_mode && i == 0) ? (T)0 : LD(o) * scale;
+      y = (rhs - y) * iv[(size_t)i * PT];
+    } else {
+      y = (LD(o) * scale - y) * lim;
+    }
+    ST(o, y);
+  }
+}
+
+// back substitution over planes i1 - 1 down to i0 (x holds x_{i1} on entry),
+// the partial chunk first, then chunks of N as above; the line sum of mode
+// (0, 0) gathered on the way
+template <int N, bool TAB, class T, class LDF, class STF>
+__device__ __forceinline__ void px_backward(LDF LD, STF ST, const T* iv, size_t PT, int P, T lim, bool zero_mode,
+                                            int i0, int i1, T& x, T& lsum) {
+  constexpr int NT = TAB ? N : 1;
+  int i = i1 - 1;
+  const int rem = (i1 - i0) % N;
+  for (int r = 0; r < rem; ++r, --i) {
+    const size_t o = (size_t)i * P;
+    T cp = lim;
+    if constexpr (TAB) cp = (zero_mode && i == 0) ? (T)0 : iv[(size_t)i * PT];
+    x = LD(o) - cp * x;
+    ST(o, x);
+    lsum += x;
+  }
+  const int nch = (i1 - i0) / N;   // full chunks below: planes i, i - 1, ..., i0
+  T rd[N], rt[NT];
+  if (nch > 0) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      rd[q] = LD((size_t)(i - q) * P);
+      if constexpr (TAB) rt[q] = iv[(size_t)(i - q) * PT];
+    }
+  }
+  for (int ch = 0; ch < nch; ++ch, i -= N) {
+    T nd[N], nt[NT];
+    if (ch + 1 < nch) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        nd[q] = LD((size_t)(i - N - q) * P);
+        if constexpr (TAB) nt[q] = iv[(size_t)(i - N - q) * PT];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      T cp = lim;
+      if constexpr (TAB) cp = (zero_mode && i - q == 0) ? (T)0 : rt[q];
+      x = rd[q] - cp * x;
+      ST((size_t)(i - q) * P, x);
+      lsum += x;
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+      rd[q] = nd[q];
+      if constexpr (TAB) rt[q] = nt[q];
+    }
+  }
+}
+
 template <class T, class S>
-__global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict__ tab, S* __restrict__ phi, T scale,
-                                                   double* __restrict__ mean00) {
+__global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict__ tab, const int* __restrict__ conv,
+                                                   S* __restrict__ phi, T scale, double* __restrict__ mean00) {
   const int P = c.ny * c.nz;
   const int jk = blockIdx.x * blockDim.x + threadIdx.x;
   if (jk >= P) return;
   const int nx = c.nx;
   S* d = phi + jk;
-  auto LD = [&](size_t o) { return from_store<T>(d[o]); };
-  auto ST = [&](size_t o, T v) { d[o] = to_store<S>(v); };
-  const T* iv = tab + ptab_index(c, jk);
+  auto LD = [d](size_t o) { return from_store<T>(d[o]); };
+  auto ST = [d](size_t o, T v) { d[o] = to_store<S>(v); };
+  const size_t mi = ptab_index(c, jk);
+  const T* iv = tab + mi;
   const size_t PT = ptab_plane(c);
   const bool zero_mode = (jk == 0);
-  // forward elimination, PF planes per chunk; the next chunk's loads are
-  // issued before the current chunk's recursion (two chunks in flight)
+  // planes [0, ia) take the table's pivots, [ia, nx - 1) the converged
+  // limit held in a register (bitwise the table's values there), plane
+  // nx - 1 its own; ia is the largest convergence row of the warp's modes,
+  // so the split is warp-uniform and the converged range spends every load
+  // slot on the right-hand side (chunks of PB planes)
+  const int ia = min(max(__reduce_max_sync(__activemask(), conv[mi]), 1), nx - 1);
+  const T lim = iv[(size_t)(nx - 2) * PT];
+  constexpr int PB = sizeof(T) == 8 ? PF : 2 * PF;
   T y = 0;
-  const int nfull = nx / PF;
+  px_forward<PF, true>(LD, ST, iv, PT, P, lim, scale, zero_mode, 0, ia, y);
+  px_forward<PB, false>(LD, ST, iv, PT, P, lim, scale, zero_mode, ia, nx - 1, y);
   {
-    T rd[PF], rt[PF];
-    if (nfull > 0) {
-#pragma unroll
-      for (int q = 0; q < PF; ++q) {
-        rd[q] = LD((size_t)q * P);
-        rt[q] = iv[(size_t)q * PT];
-      }
-    }
-    for (int ch = 0; ch < nfull; ++ch) {
-      const int i = ch * PF;
-      T nd[PF], nt[PF];
-      if (ch + 1 < nfull) {
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-          nd[q] = LD((size_t)(i + PF + q) * P);
-          nt[q] = iv[(size_t)(i + PF + q) * PT];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < PF; ++q) {
-        const T rhs = (zero_mode && i + q == 0) ? (T)0 : rd[q] * scale;
-        y = (rhs - y) * rt[q];
-        ST((size_t)(i + q) * P, y);
-      }
-#pragma unroll
-      for (int q = 0; q < PF; ++q) {
-        rd[q] = nd[q];
-        rt[q] = nt[q];
-      }
-    }
-  }
-  for (int i = nfull * PF; i < nx; ++i) {
-    const size_t o = (size_t)i * P;
-    const T rhs = (zero_mode && i == 0) ? (T)0 : LD(o) * scale;
-    y = (rhs - y) * iv[(size_t)i * PT];
+    const size_t o = (size_t)(nx - 1) * P;
+    y = (LD(o) * scale - y) * iv[(size_t)(nx - 1) * PT];
     ST(o, y);
   }
-  // back substitution from the top, the same chunking (the partial chunk first);
-  // the line sum of mode (0, 0) is gathered on the way (in T: an FP64
-  // conversion per plane and mode would load the narrow FP64 pipe)
+  // back substitution from the top (in T: an FP64 conversion per plane and
+  // mode would load the narrow FP64 pipe)
   T x = y;  // x_{nx-1} = dp_{nx-1}
   T lsum = x;
-  int i = nx - 2;
-  const int rem = (nx - 1) % PF;
-  for (; i > nx - 2 - rem; --i) {
-    const size_t o = (size_t)i * P;
-    const T cp = (zero_mode && i == 0) ? (T)0 : iv[(size_t)i * PT];
-    x = LD(o) - cp * x;
-    ST(o, x);
-    lsum += x;
-  }
-  {
-    const int nch = (i + 1) / PF;   // full chunks below: planes i, i-1, ..., 0
-    T rd[PF], rt[PF];
-    if (nch > 0) {
-#pragma unroll
-      for (int q = 0; q < PF; ++q) {
-        rd[q] = LD((size_t)(i - q) * P);
-        rt[q] = iv[(size_t)(i - q) * PT];
-      }
-    }
-    for (int ch = 0; ch < nch; ++ch, i -= PF) {
-      T nd[PF], nt[PF];
-      if (ch + 1 < nch) {
-#pragma unroll
-        for (int q = 0; q < PF; ++q) {
-          nd[q] = LD((size_t)(i - PF - q) * P);
-          nt[q] = iv[(size_t)(i - PF - q) * PT];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < PF; ++q) {
-        const T cp = (zero_mode && i - q == 0) ? (T)0 : rt[q];
-        x = rd[q] - cp * x;
-        ST((size_t)(i - q) * P, x);
-        lsum += x;
-      }
-#pragma unroll
-      for (int q = 0; q < PF; ++q) {
-        rd[q] = nd[q];
-        rt[q] = nt[q];
-      }
-    }
-  }
+  px_backward<PB, false>(LD, ST, iv, PT, P, lim, zero_mode, ia, nx - 1, x, lsum);
+  px_backward<PF, true>(LD, ST, iv, PT, P, lim, zero_mode, 0, ia, x, lsum);
   // the mean is removed by k_mode00_sub, in parallel over the planes
   if (zero_mode) *mean00 = (double)lsum / nx;
 }
@@ -737,7 +779,7 @@ __global__ void k_mode00_sub(Consts c, S* __restrict__ phi, const double* __rest
 
 // inverse pivots 1 / (diag_i - c'_{i-1}) of every distinct mode, FP64 arithmetic
 template <class T>
-__global__ void k_poisson_table(Consts c, T* __restrict__ tab) {
+__global__ void k_poisson_table(Consts c, T* __restrict__ tab, int* __restrict__ conv) {
   const int qz_n = c.nz / 2 + 1;
   const int PT = (c.ny / 2 + 1) * qz_n;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -758,6 +800,12 @@ __global__ void k_poisson_table(Consts c, T* __restrict__ tab) {
     tab[(size_t)i * PT + m] = (T)inv;
     cp = inv;  // upper = 1
   }
+  // rows 1 .. nx - 2 share one recursion whose pivots converge to a limit;
+  // the first row from which the stored pivots equal the stored limit
+  const T lim = tab[(size_t)(nx - 2) * PT + m];
+  int ic = nx - 2;
+  while (ic > 0 && tab[(size_t)(ic - 1) * PT + m] == lim) --ic;
+  conv[m] = ic;
 }
 
 template <class T>
@@ -795,7 +843,7 @@ void launch_poisson_x_on(const Consts& c, const Fields<T>& f, T* buf, cudaStream
   const int P = c.ny * c.nz;
   const T scale = (T)(c.h * c.h / ((double)c.ny * c.nz));
 
-  k_poisson_x<T, T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, buf, scale, f.mean00);
+  k_poisson_x<T, T><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, f.pconv, buf, scale, f.mean00);
   k_mode00_sub<T><<<(c.nx + 255) / 256, 256, 0, s>>>(c, buf, f.mean00);
 }
 
@@ -804,7 +852,7 @@ void launch_poisson_x_bf16(const Consts& c, const Fields<float>& f, void* buf, c
   const int P = c.ny * c.nz;
   const float scale = (float)(c.h * c.h / ((double)c.ny * c.nz));
   __nv_bfloat16* b = reinterpret_cast<__nv_bfloat16*>(buf);
-  k_poisson_x<float, __nv_bfloat16><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, b, scale, f.mean00);
+  k_poisson_x<float, __nv_bfloat16><<<(P + 127) / 128, 128, 0, s>>>(c, f.ptab, f.pconv, b, scale, f.mean00);
   k_mode00_sub<__nv_bfloat16><<<(c.nx + 255) / 256, 256, 0, s>>>(c, b, f.mean00);
 }
 
@@ -854,11 +902,12 @@ void launch_poisson(const Consts& c, const Fields<T>& f, cudaStream_t s) {
 }
 
 size_t poisson_table_size(const Consts& c) { return (size_t)c.nx * ptab_plane(c); }
+size_t poisson_modes(const Consts& c) { return ptab_plane(c); }
 
 template <class T>
 void launch_poisson_table(const Consts& c, const Fields<T>& f, cudaStream_t s) {
   const int PT = (int)ptab_plane(c);
-  k_poisson_table<T><<<(PT + 127) / 128, 128, 0, s>>>(c, f.ptab);
+  k_poisson_table<T><<<(PT + 127) / 128, 128, 0, s>>>(c, f.ptab, f.pconv);
 }
 
 template void launch_poisson<double>(const Consts&, const Fields<double>&, cudaStream_t);

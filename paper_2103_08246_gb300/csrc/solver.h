@@ -21,6 +21,7 @@ struct Fields {
   float* tapsf;               // the same in FP32
   T* phi;                     // divergence -> transforms -> pressure correction
   T* ptab;                    // Poisson Thomas inverse pivots per distinct mode
+  int* pconv;                 // per distinct mode: first plane from which its pivots equal the limit
   T* dout[3];                 // outflow-plane increments (ny * nz each)
   T* tw_y; T* tw_z;           // FFT twiddles exp(-2 pi i t / N), t < N/2 (re, im)
   double* partial;            // per-block partial maxima of the CFL speed
@@ -128,6 +129,7 @@ template <class T> void launch_project(const Consts& c, const Fields<T>& f, int 
 template <class T>
 int partial_count(const Consts& c);
 size_t poisson_table_size(const Consts& c);
+size_t poisson_modes(const Consts& c);
 // tensor-core (tcgen05) split-TF32 transform pass: out = (X H)^T per n x n
 // plane (n = 32, 64, 128, 256), H the Hartley matrix given by its pre-split
 // cos / sin image
