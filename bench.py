@@ -74,10 +74,10 @@ METHOD_PASSES = {"fp32": 57, "mixed": 65}
 # valid for the kernels of those captures and to be refreshed whenever one
 # of them changes.
 _TRAFFIC_COMMON = {"rhs": 1742.7e6, "af_yz": 1156.4e6, "af_x": 752.4e6, "mass_div": 519.2e6,
-                   "poisson_x": 409.8e6, "ib": 57.9e6}
+                   "poisson_x": None, "ib": 57.9e6}
 TRAFFIC_BYTES = {
     "fp32": dict(_TRAFFIC_COMMON, dht2d=209.8e6, project=1181.2e6),
-    "mixed": dict(_TRAFFIC_COMMON, dht2d=212.2e6, tc_bf16=84.5e6, residual=317.7e6, poisson_x16=150.4e6,
+    "mixed": dict(_TRAFFIC_COMMON, dht2d=212.2e6, tc_bf16=84.5e6, residual=317.7e6, poisson_x16=None,
                   project=1258.1e6),
 }
 # the mixed path's projection reads the solve's two parts (FP32 predictor,
