@@ -372,6 +372,122 @@ int ibm_ensemble_create_batched(ibm_state* const* members, int n, void* stream, 
 int ibm_ensemble_step(ibm_ensemble* e, double dt, int nsteps);
 void ibm_ensemble_destroy(ibm_ensemble* e);
 
+/* ---- x-slab decomposition of one case ------------------------------------
+ * Sec. II.B runs one case on several GPUs by a one-dimensional domain
+ * decomposition: slabs of whole y-z planes along x. Here each rank (one
+ * process, one GPU) holds one slab state: its owned cell planes
+ * [x_begin, x_end) of the global grid plus `ghosts` overlap planes on each
+ * side that has a neighbour. A step is a fixed sequence of phases; between
+ * two phases the caller moves one buffer between the ranks with a plain
+ * collective (all-reduce, all-gather or a neighbour exchange, e.g. NCCL or
+ * gloo through torch.distributed), so the library itself never
+ * communicates and no kernel waits on another rank.
+ *   step:               FORCE, SOLVE, REDUCE, PROJECT, GHOSTS
+ *   initial projection: INIT, REDUCE, PROJECT, GHOSTS (once, before the
+ *                       first step; ibm_create_slab does not project)
+ * What couples the slabs (the rest is local to the window):
+ *   - the pressure equation's x solve per transverse mode, by the partition
+ *     method: local solves with the neighbours' values removed, a small
+ *     system for the values next to every cut assembled from all ranks' line
+ *     data (all-gather), and a corrected local solve (exact, not iterative);
+ *     the mode (0, 0) keeps the pinned first row and the gauge mean(phi) = 0
+ *     of the single-domain solve;
+ *   - the flag's fluid force (each vertex counted by the rank owning its x
+ *     position, all-reduce) and the inflow / outflow fluxes of the mass fix;
+ *   - the overlap planes of u, v, w, p and the advection history, refreshed
+ *     from the owning neighbours after every step. The implicit x factor's
+ *     dependence on the window's ends decays like rho^d over d planes
+ *     (rho < 1), so overlap planes wider than that decay plus the forcing
+ *     kernel's support leave the owned planes exact to round-off
+ *     (ibm_slab_ghosts).
+ * Every rank builds the same flag and advances it identically. Results equal
+ * the single-domain solver's up to rounding order. Limits: FP64 fields,
+ * fixed dt, uniform inflow, marker forcing of the bars, at most
+ * IBM_SLAB_MAX_RANKS ranks. */
+#define IBM_SLAB_MAX_RANKS 8
+
+typedef struct {
+  int nranks;    /* slabs along x, 1 .. IBM_SLAB_MAX_RANKS                     */
+  int rank;      /* this slab, 0 .. nranks - 1, in x order                      */
+  int x_begin;   /* first owned cell plane (0 on rank 0)                         */
+  int x_end;     /* one past the last owned cell plane (nx on the last rank)     */
+  int ghosts;    /* overlap planes on each side with a neighbour: at least
+                    ibm_slab_ghosts(), x_end - x_begin >= ghosts + 1, and the
+                    window [x_begin - ghosts, x_end + ghosts) inside [0, nx)     */
+} ibm_slab;
+
+/* phases (in step order) */
+#define IBM_SLAB_INIT    0  /* divergence of the initial velocity, transforms,
+                               local x solves                                   */
+#define IBM_SLAB_FORCE   1  /* dt, explicit terms, implicit factors, IB forcing */
+#define IBM_SLAB_SOLVE   2  /* structure, mass fix, divergence, transforms,
+                               local x solves                                   */
+#define IBM_SLAB_REDUCE  3  /* cut values, corrected x solves, inverse transforms */
+#define IBM_SLAB_PROJECT 4  /* projection (and pressure update after a step)    */
+#define IBM_SLAB_GHOSTS  5  /* overlap planes from the neighbours               */
+
+/* exchanges the caller performs on a phase's send buffer (doubles) */
+#define IBM_XCHG_NONE   0
+#define IBM_XCHG_SUM    1   /* element-wise sum over all ranks (all-reduce)     */
+#define IBM_XCHG_GATHER 2   /* every rank's buffer, concatenated in rank order
+                               (all-gather): nranks * send_count values         */
+#define IBM_XCHG_HALO   3   /* send = [to rank - 1 | to rank + 1], two halves of
+                               send_count / 2; recv = [from rank - 1 | from
+                               rank + 1] (a half without a neighbour is ignored
+                               on send and left as it is on receive)            */
+
+/* Smallest overlap (planes) for which the owned planes are exact to FP64
+ * round-off at viscosity 1/re, spacing h and fixed step dt: the decay length
+ * of the implicit x factor, ceil(log 1e-17 / log rho) with rho its decay
+ * factor at r = dt / (2 re h^2), plus 4 planes of forcing support and
+ * explicit stencil. Host only. */
+int ibm_slab_ghosts(double re, double h, double dt, int* ghosts);
+
+/* Even split of nx cell planes over nranks slabs with `ghosts` overlap
+ * planes (the first nx % nranks slabs one plane longer); IBM_EINVAL if a
+ * slab would be too short for its overlap. Host only. */
+int ibm_slab_split(int nx, int nranks, int rank, int ghosts, ibm_slab* out);
+
+/* Sizes of a phase's exchange: kind (IBM_XCHG_*), doubles the phase writes
+ * into `send`, and doubles the caller passes as `recv` to the next phase
+ * (the exchange's result). Depends only on the arguments (host only, no
+ * state needed): ny, nz of the global grid, the flag's vertex count
+ * (0 without flag) and the slab. */
+int ibm_slab_plan(const ibm_grid* grid, int n_flag_vertices, const ibm_slab* slab, int phase, int* xchg,
+                  size_t* send_count, size_t* recv_count);
+
+/* Build the slab state of `slab` for the global problem (grid, domain,
+ * bodies as for ibm_create; opts: FP64, no prescribed inflow, bar_forcing 0;
+ * init_u/v/w, if given, are the WINDOW's perturbations, (nx_w + 1) ny nz
+ * values with nx_w = x_end - x_begin + the overlap planes, window plane 0 =
+ * global plane x_begin - ghosts, or x_begin on rank 0). The state covers the
+ * window: ibm_get_field / ibm_set_field / ibm_get_plane work on window
+ * planes; ibm_flag_state reports the shared flag in global coordinates; bar
+ * markers are the global grid's within three cells of the window, shifted
+ * to window coordinates. No projection is applied: run the initial phase
+ * sequence before the first step. workspace: as ibm_create (window size);
+ * the slab's solve tables (pivots per mode and row, 6 values per mode, and a
+ * scratch of the owned planes) are allocated by the library. ibm_step
+ * refuses slab states (IBM_EINVAL). */
+int ibm_create_slab(const ibm_grid* grid, const ibm_domain* domain, double re,
+                    const ibm_bodies* bodies, const ibm_options* opts, const ibm_slab* slab,
+                    void* workspace, size_t workspace_bytes, ibm_state** out);
+/* Bytes of workspace ibm_create_slab needs. */
+int ibm_slab_workspace_bytes(const ibm_grid* grid, const ibm_domain* domain, const ibm_bodies* bodies,
+                             const ibm_options* opts, const ibm_slab* slab, size_t* bytes);
+
+/* Run one phase on the state's stream. recv: DEVICE buffer holding the
+ * previous phase's exchange result (ibm_slab_plan's recv_count doubles;
+ * NULL for IBM_SLAB_INIT and IBM_SLAB_FORCE); send: DEVICE buffer of
+ * send_count doubles that this phase fills for the next exchange (NULL when
+ * send_count is 0). dt > 0 (FORCE only; ignored otherwise). Phases must come
+ * in one of the two sequences above (IBM_EINVAL otherwise, state unchanged).
+ * Asynchronous, except GHOSTS, which synchronises and reports device-side
+ * errors of the step (IBM_EDIVERGED for a non-finite velocity, IBM_ETIMEOUT,
+ * IBM_EINVAL for a step size outside the implicit factor's range). Buffers
+ * belong to the caller; `send` may be reused once the exchange has read it. */
+int ibm_slab_phase(ibm_state* s, int phase, double dt, const double* recv, double* send);
+
 /* ---- Learned inflow generator ------------------------------------------
  * The synthetic-inflow alternative that Sec. V of the paper leaves open: an
  * autoregressive convolutional network that maps the two latest keyframes

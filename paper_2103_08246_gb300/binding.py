@@ -35,8 +35,14 @@ SYMBOLS = ("ibm_workspace_bytes", "ibm_create", "ibm_step", "ibm_sync", "ibm_fla
            "ibm_gen_set_relax",
            "ibm_gen_set_spectrum", "ibm_gen_set_lr", "ibm_gen_time", "ibm_gen_rollout_init",
            "ibm_gen_rollout", "ibm_gen_emit", "ibm_gen_history", "ibm_gen_save", "ibm_gen_load", "ibm_gen_sync",
-           "ibm_gen_destroy", "ibm_check_bounded_wait", "ibm_destroy", "ibm_strerror")
+           "ibm_gen_destroy", "ibm_check_bounded_wait", "ibm_destroy", "ibm_strerror",
+           "ibm_slab_ghosts", "ibm_slab_split", "ibm_slab_plan", "ibm_create_slab", "ibm_slab_workspace_bytes",
+           "ibm_slab_phase")
 _VOID = ("ibm_destroy", "ibm_ensemble_destroy", "ibm_gen_destroy")
+
+IBM_SLAB_INIT, IBM_SLAB_FORCE, IBM_SLAB_SOLVE, IBM_SLAB_REDUCE, IBM_SLAB_PROJECT, IBM_SLAB_GHOSTS = range(6)
+IBM_XCHG_NONE, IBM_XCHG_SUM, IBM_XCHG_GATHER, IBM_XCHG_HALO = range(4)
+IBM_SLAB_MAX_RANKS = 8
 
 STAGES = {"step": -1, "rhs": 0, "outflow": 1, "af_x": 2, "af_y": 3, "af_z": 4, "ib": 5, "flag": 6,
           "mass_div": 7, "dht_y": 8, "dht_z": 9, "poisson_x": 10, "project": 11, "poisson": 12,
@@ -73,6 +79,11 @@ class ibm_options(ctypes.Structure):
                 ("rhs_stages", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("inflow", ctypes.c_int), ("bar_forcing", ctypes.c_int),
                 ("mixed_tc_predictor", ctypes.c_int)]
+
+
+class ibm_slab(ctypes.Structure):
+    _fields_ = [("nranks", ctypes.c_int), ("rank", ctypes.c_int), ("x_begin", ctypes.c_int),
+                ("x_end", ctypes.c_int), ("ghosts", ctypes.c_int)]
 
 
 class ibm_gen_config(ctypes.Structure):
@@ -147,6 +158,18 @@ def load(path: str = LIB_PATH):
     lib.ibm_strerror.argtypes = [ctypes.c_int]
     lib.ibm_strerror.restype = ctypes.c_char_p
     ip = ctypes.POINTER(ctypes.c_int)
+    slp = ctypes.POINTER(ibm_slab)
+    lib.ibm_slab_ghosts.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, ip]
+    lib.ibm_slab_split.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, slp]
+    lib.ibm_slab_plan.argtypes = [ctypes.POINTER(ibm_grid), ctypes.c_int, slp, ctypes.c_int, ip,
+                                  ctypes.POINTER(sz), ctypes.POINTER(sz)]
+    lib.ibm_create_slab.argtypes = [ctypes.POINTER(ibm_grid), ctypes.POINTER(ibm_domain), ctypes.c_double,
+                                    ctypes.POINTER(ibm_bodies), ctypes.POINTER(ibm_options), slp, vp, sz,
+                                    ctypes.POINTER(vp)]
+    lib.ibm_slab_workspace_bytes.argtypes = [ctypes.POINTER(ibm_grid), ctypes.POINTER(ibm_domain),
+                                             ctypes.POINTER(ibm_bodies), ctypes.POINTER(ibm_options), slp,
+                                             ctypes.POINTER(sz)]
+    lib.ibm_slab_phase.argtypes = [vp, ctypes.c_int, ctypes.c_double, vp, vp]
     lib.ibm_gen_create.argtypes = [ctypes.POINTER(ibm_gen_config), ctypes.POINTER(vp)]
     lib.ibm_gen_param_count.argtypes = [vp]
     lib.ibm_gen_set_params.argtypes = [vp, _dp, sz]
@@ -222,6 +245,48 @@ def ibm_create(grid, dom, re, bodies, opts, workspace_ptr=None, workspace_bytes=
                              ctypes.byref(opts) if opts is not None else None,
                              workspace_ptr, workspace_bytes, ctypes.byref(h)), "ibm_create")
     return h
+
+
+def ibm_slab_ghosts(re, h, dt) -> int:
+    g = ctypes.c_int(0)
+    _check(load().ibm_slab_ghosts(float(re), float(h), float(dt), ctypes.byref(g)), "ibm_slab_ghosts")
+    return g.value
+
+
+def ibm_slab_split(nx, nranks, rank, ghosts) -> ibm_slab:
+    out = ibm_slab()
+    _check(load().ibm_slab_split(int(nx), int(nranks), int(rank), int(ghosts), ctypes.byref(out)),
+           "ibm_slab_split")
+    return out
+
+
+def ibm_slab_plan(grid, n_flag_vertices, slab, phase):
+    """(exchange kind, send count, recv count) of a phase."""
+    k = ctypes.c_int(0)
+    ns, nr = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(load().ibm_slab_plan(ctypes.byref(grid), int(n_flag_vertices), ctypes.byref(slab), int(phase),
+                                ctypes.byref(k), ctypes.byref(ns), ctypes.byref(nr)), "ibm_slab_plan")
+    return k.value, ns.value, nr.value
+
+
+def ibm_slab_workspace_bytes(grid, dom, bodies, opts, slab) -> int:
+    n = ctypes.c_size_t(0)
+    _check(load().ibm_slab_workspace_bytes(ctypes.byref(grid), ctypes.byref(dom), ctypes.byref(bodies),
+                                           ctypes.byref(opts) if opts is not None else None,
+                                           ctypes.byref(slab), ctypes.byref(n)), "ibm_slab_workspace_bytes")
+    return n.value
+
+
+def ibm_create_slab(grid, dom, re, bodies, opts, slab, workspace_ptr=None, workspace_bytes=0):
+    h = ctypes.c_void_p()
+    _check(load().ibm_create_slab(ctypes.byref(grid), ctypes.byref(dom), float(re), ctypes.byref(bodies),
+                                  ctypes.byref(opts) if opts is not None else None, ctypes.byref(slab),
+                                  workspace_ptr, workspace_bytes, ctypes.byref(h)), "ibm_create_slab")
+    return h
+
+
+def ibm_slab_phase(state, phase, dt, recv_ptr, send_ptr):
+    return load().ibm_slab_phase(state, int(phase), float(dt), recv_ptr, send_ptr)
 
 
 def ibm_step(state, dt, nsteps):

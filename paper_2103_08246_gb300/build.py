@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libibm_gb300.so")
-SOURCES = ["fluid.cu", "poisson.cu", "mixed.cu", "tc_gemm.cu", "ib.cu", "flag.cu", "api.cu", "gen.cu"]
+SOURCES = ["fluid.cu", "poisson.cu", "mixed.cu", "tc_gemm.cu", "ib.cu", "flag.cu", "api.cu", "gen.cu", "slab.cu"]
 HEADERS = ["common.cuh", "solver.h", "async_copy.cuh", "tcgen05.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -357,6 +357,13 @@ struct ibm_state {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaStream_t side2 = nullptr;           // implicit-factor tables, overlapped with the RHS
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
+  // slab of an x decomposition (ibm_create_slab): its geometry and solve
+  // tables, the phases allowed next (bit mask), and whether the pending
+  // projection is the initial one
+  bool slab_on = false;
+  SlabDev slab{};
+  int slab_allowed = 0;
+  bool slab_initial = false;
 };
 
 namespace {
@@ -745,6 +752,12 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
     s->c.corr_bf16 = (s->h16_img && !s->c.mixed_tc && tc_bf16_available(fields<float>(s).e[2], c.nx)) ? 1 : 0;
   }
   launch_poisson_table(c, f, st);
+  if (s->slab_on) {   // projected by the phase sequence; no captured step
+    s->cur = 0;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    return IBM_OK;
+  }
   // initial projection of u0 (dt absorbed in phi), velocity only
   s->cur = 0;
   launch_mass_div(c, f, 0, true, st);
@@ -786,10 +799,36 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
   return IBM_OK;
 }
 
+// the window of a slab: its first cell plane in the global grid and its planes
+int slab_window(const ibm_slab& sl, int* x0, int* nxw) {
+  const int gl = sl.rank > 0 ? sl.ghosts : 0, gr = sl.rank < sl.nranks - 1 ? sl.ghosts : 0;
+  *x0 = sl.x_begin - gl;
+  *nxw = sl.x_end - sl.x_begin + gl + gr;
+  return gl;
+}
+
+int check_slab(const ibm_grid* g, const ibm_options* o, const ibm_slab* sl) {
+  if (!sl || !g) return IBM_EINVAL;
+  if (sl->nranks < 1 || sl->nranks > IBM_SLAB_MAX_RANKS || sl->rank < 0 || sl->rank >= sl->nranks)
+    return IBM_EINVAL;
+  if (sl->x_begin < 0 || sl->x_end <= sl->x_begin || sl->x_end > g->nx) return IBM_EINVAL;
+  if ((sl->rank == 0) != (sl->x_begin == 0) || (sl->rank == sl->nranks - 1) != (sl->x_end == g->nx))
+    return IBM_EINVAL;
+  if (sl->nranks > 1 && (sl->ghosts < 1 || sl->x_end - sl->x_begin < sl->ghosts + 1)) return IBM_EINVAL;
+  if (sl->ghosts < 0) return IBM_EINVAL;
+  int x0, nxw;
+  slab_window(*sl, &x0, &nxw);
+  if (x0 < 0 || x0 + nxw > g->nx || nxw < 4) return IBM_EINVAL;
+  if (o && (o->precision != IBM_FP64 || o->inflow || o->bar_forcing != 0)) return IBM_EINVAL;
+  return IBM_OK;
+}
+
 int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const ibm_options* o,
-            ibm_state* s, FlagGeom& fg, std::vector<double>& Xb, double& bar_dv, Layout& L, BarMask& bm) {
+            ibm_state* s, FlagGeom& fg, std::vector<double>& Xb, double& bar_dv, Layout& L, BarMask& bm,
+            const ibm_slab* sl = nullptr) {
   int rc = check_args(g, d, b, o);
   if (rc) return rc;
+  if (sl && (rc = check_slab(g, o, sl))) return rc;
   s->grid = *g;
   s->dom = *d;
   s->bodies = *b;
@@ -819,6 +858,29 @@ int prepare(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const i
   if (b->flag_on) fg = build_flag(*b, *d, c.h);
   if (b->bars_on && s->bar_forcing == 1) build_bar_mask(*b, *d, *g, c.h, bm);
   else if (b->bars_on) build_bars(*b, *d, c.h, Xb, bar_dv);
+  if (sl) {
+    // the window: the global grid's bodies (flag in global coordinates,
+    // shifted by the forcing kernels), bar markers within three cells of the
+    // window shifted to window coordinates; the marker volume stays the
+    // global grid's
+    int x0, nxw;
+    slab_window(*sl, &x0, &nxw);
+    const double xs = x0 * c.h;
+    std::vector<double> keep;
+    for (size_t q = 0; q + 2 < Xb.size(); q += 3) {
+      const long long cx = (long long)std::floor(Xb[q] * c.inv_h);
+      if (cx < x0 - 3 || cx > x0 + nxw + 2) continue;
+      keep.push_back(Xb[q] - xs);
+      keep.push_back(Xb[q + 1]);
+      keep.push_back(Xb[q + 2]);
+    }
+    Xb.swap(keep);
+    c.nx = nxw;
+    c.lx = nxw * c.h;
+    s->grid.nx = nxw;
+    s->dom.lx = c.lx;
+    s->mk.x_shift = xs;
+  }
   ib_bin_bars(c, Xb, bm.tiles, s->mk);
   L.ntile = s->mk.n_tiles;
   for (int q = 0; q < 3; ++q) L.nbm[q] = bm.n[q];
@@ -1036,9 +1098,289 @@ cudaError_t cases_graph(const void* dtab, int ncases, int total, cudaStream_t st
   launch_rhs_cases<T>((const RhsCase<T>*)dtab, ncases, total, blocks, st);
   return cudaStreamEndCapture(st, g);
 }
+
+int create_impl(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodies* b,
+                const ibm_options* o, const ibm_slab* sl, void* workspace, size_t workspace_bytes,
+                ibm_state** out);
+
+// ------------------------------------------------------------------ x slabs
+// bit of a phase in the allowed-phase mask
+constexpr int slab_bit(int phase) { return 1 << phase; }
+
+// overlap planes needed at this viscosity, spacing and step (see ibm_slab_ghosts)
+int slab_min_ghosts(double nu, double h, double dt) {
+  const double r = nu * dt / (2.0 * h * h);
+  const double rho = std::exp(-2.0 * std::asinh(0.5 / std::sqrt(r)));
+  int H = (int)std::ceil(std::log(1e-17) / std::log(rho));
+  if (!(H >= 1)) H = 1;
+  return H + 4;
+}
+
+// doubles in one half of the overlap exchange: u, v, w and the three
+// advection components with ghosts + 1 planes, p with ghosts planes
+size_t slab_halo_half(size_t P, int g) { return (size_t)(7 * g + 6) * P; }
+
+int slab_setup(ibm_state* s, const ibm_slab& sl, int nx_global) {
+  SlabDev& sd = s->slab;
+  int x0, nxw;
+  sd.gL = slab_window(sl, &x0, &nxw);
+  sd.nranks = sl.nranks;
+  sd.rank = sl.rank;
+  sd.x_begin = sl.x_begin;
+  sd.x_end = sl.x_end;
+  sd.nx_global = nx_global;
+  sd.n = sl.x_end - sl.x_begin;
+  sd.g = sl.ghosts;
+  sd.gR = sl.rank < sl.nranks - 1 ? sl.ghosts : 0;
+  sd.first_phys = sl.rank == 0;
+  sd.last_phys = sl.rank == sl.nranks - 1;
+  const Consts& c = s->c;
+  const size_t P = plane(c), PT = poisson_modes(c);
+  if (cudaMalloc(&sd.tab, (size_t)sd.n * PT * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&sd.green, 6 * PT * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&sd.scr, (size_t)sd.n * P * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return IBM_ENOMEM;
+  }
+  slab_tables(c, sd, s->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s->stream));
+  s->slab_allowed = slab_bit(IBM_SLAB_INIT) | slab_bit(IBM_SLAB_FORCE);
+  return IBM_OK;
+}
+
+// forward (and, applied again, inverse) transforms of phi in y and z
+void slab_transforms(ibm_state* s, bool inverse) {
+  Fields<double>& f = s->fd;
+  if (launch_dht2d(s->c, f, s->stream)) return;
+  if (!inverse) {
+    launch_dht_y(s->c, f, s->stream);
+    launch_dht_z(s->c, f, s->stream);
+  } else {
+    launch_dht_z(s->c, f, s->stream);
+    launch_dht_y(s->c, f, s->stream);
+  }
+}
+
+// device-to-device copy of `planes` planes starting at plane i0 of a field
+cudaError_t copy_planes(double* dst, const double* src, int i0, int planes, size_t P, bool to_field,
+                        cudaStream_t st) {
+  if (planes <= 0) return cudaSuccess;
+  const size_t bytes = (size_t)planes * P * sizeof(double);
+  return to_field ? cudaMemcpyAsync(dst + (size_t)i0 * P, src, bytes, cudaMemcpyDeviceToDevice, st)
+                  : cudaMemcpyAsync(dst, src + (size_t)i0 * P, bytes, cudaMemcpyDeviceToDevice, st);
+}
+
+int slab_phase_impl(ibm_state* s, int phase, double dt, const double* recv, double* send) {
+  Fields<double>& f = s->fd;
+  const Consts& c = s->c;
+  const SlabDev& sd = s->slab;
+  cudaStream_t st = s->stream;
+  const size_t P = plane(c);
+  const int g = sd.g, n = sd.n, gL = sd.gL;
+  switch (phase) {
+    case IBM_SLAB_INIT:
+      launch_div<double>(c, f, s->cur, true, st);
+      slab_transforms(s, false);
+      slab_local_solve(c, sd, f.phi, send, st);
+      s->slab_initial = true;
+      s->slab_allowed = slab_bit(IBM_SLAB_REDUCE);
+      break;
+    case IBM_SLAB_FORCE: {
+      if (!(dt > 0) || sd.g < (sd.nranks > 1 ? slab_min_ghosts(c.nu, c.h, dt) : 0)) return IBM_EINVAL;
+      if (dt != s->last_dt_fixed) {
+        double two[2] = {dt, s->cfl};
+        CK(cudaMemcpyAsync(&f.prm->dt_fixed, two, sizeof(two), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        s->last_dt_fixed = dt;
+      }
+      launch_begin_step(c, f, st);
+      launch_af_tables(c, f, st);
+      launch_rhs(c, f, s->cur, st);
+      launch_outflow(c, f, s->cur, st);
+      launch_af(c, f, s->cur, st);
+      launch_ib(c, f, s->mk, s->fl, s->cur, st);
+      slab_pack_force(c, sd, s->fl, f.qpart, outflow_blocks(c), send, st);
+      s->slab_initial = false;
+      s->slab_allowed = slab_bit(IBM_SLAB_SOLVE);
+      break;
+    }
+    case IBM_SLAB_SOLVE:
+      slab_unpack_force(c, f.prm, s->fl, recv, st);
+      launch_flag(f.prm, s->fl, false, st);
+      launch_div<double>(c, f, s->cur, false, st);
+      slab_transforms(s, false);
+      slab_local_solve(c, sd, f.phi, send, st);
+      s->slab_allowed = slab_bit(IBM_SLAB_REDUCE);
+      break;
+    case IBM_SLAB_REDUCE:
+      slab_correct(c, sd, f.phi, recv, st);
+      slab_transforms(s, true);
+      CK(copy_planes(send, f.phi, gL, 1, P, false, st));
+      CK(copy_planes(send + P, f.phi, gL + n - 1, 1, P, false, st));
+      s->slab_allowed = slab_bit(IBM_SLAB_PROJECT);
+      break;
+    case IBM_SLAB_PROJECT: {
+      if (sd.gL > 0) CK(copy_planes(f.phi, recv, gL - 1, 1, P, true, st));
+      if (sd.gR > 0) CK(copy_planes(f.phi, recv + P, gL + n, 1, P, true, st));
+      launch_project<double>(c, f, s->cur, s->slab_initial, st);
+      s->cur ^= 1;
+      const int cur = s->cur;
+      double* arr[7] = {f.u[cur], f.v[cur], f.w[cur], f.n[0], f.n[1], f.n[2], f.p};
+      const size_t half = slab_halo_half(P, g);
+      if (sd.gL > 0) {   // to rank - 1: its right overlap, our planes [gL, gL + g] (p: g planes)
+        size_t off = 0;
+        for (int a = 0; a < 7; ++a) {
+          const int planes = a < 6 ? g + 1 : g;
+          CK(copy_planes(send + off, arr[a], gL, planes, P, false, st));
+          off += (size_t)planes * P;
+        }
+      }
+      if (sd.gR > 0) {   // to rank + 1: its left overlap, our last g owned planes
+        size_t off = half;
+        for (int a = 0; a < 7; ++a) {
+          CK(copy_planes(send + off, arr[a], gL + n - g, g, P, false, st));
+          off += (size_t)g * P;
+        }
+      }
+      s->slab_initial = false;
+      s->slab_allowed = slab_bit(IBM_SLAB_GHOSTS);
+      break;
+    }
+    case IBM_SLAB_GHOSTS: {
+      const int cur = s->cur;
+      double* arr[7] = {f.u[cur], f.v[cur], f.w[cur], f.n[0], f.n[1], f.n[2], f.p};
+      const size_t half = slab_halo_half(P, g);
+      if (sd.gL > 0) {   // from rank - 1: g planes per array into planes [0, g)
+        size_t off = 0;
+        for (int a = 0; a < 7; ++a) {
+          CK(copy_planes(arr[a], recv + off, 0, g, P, true, st));
+          off += (size_t)g * P;
+        }
+      }
+      if (sd.gR > 0) {   // from rank + 1: planes [nx - g, nx] (p: [nx - g, nx))
+        size_t off = half;
+        for (int a = 0; a < 7; ++a) {
+          const int planes = a < 6 ? g + 1 : g;
+          CK(copy_planes(arr[a], recv + off, c.nx - g, planes, P, true, st));
+          off += (size_t)planes * P;
+        }
+      }
+      s->slab_allowed = slab_bit(IBM_SLAB_INIT) | slab_bit(IBM_SLAB_FORCE);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(s->hprm, f.prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      const Params& p = *s->hprm;
+      if (p.error & ERR_TIMEOUT) return IBM_ETIMEOUT;
+      if (p.error & ERR_AF_RANGE) return IBM_EINVAL;
+      if (p.error) return IBM_EDIVERGED;
+      return IBM_OK;
+    }
+    default:
+      return IBM_EINVAL;
+  }
+  CK(cudaGetLastError());
+  return IBM_OK;
+}
+
+size_t slab_send_count(int phase, size_t P, int nv, int g) {
+  switch (phase) {
+    case IBM_SLAB_INIT:
+    case IBM_SLAB_SOLVE: return (size_t)SLAB_LINE * P;
+    case IBM_SLAB_FORCE: return 3 * (size_t)nv + 2;
+    case IBM_SLAB_REDUCE: return 2 * P;
+    case IBM_SLAB_PROJECT: return 2 * slab_halo_half(P, g);
+    default: return 0;
+  }
+}
 }  // namespace
 
 extern "C" {
+
+int ibm_slab_ghosts(double re, double h, double dt, int* ghosts) {
+  if (!ghosts || !(re > 0) || !(h > 0) || !(dt > 0) || !std::isfinite(re * h * dt)) return IBM_EINVAL;
+  *ghosts = slab_min_ghosts(1.0 / re, h, dt);
+  return IBM_OK;
+}
+
+int ibm_slab_split(int nx, int nranks, int rank, int ghosts, ibm_slab* out) {
+  if (!out || nx < 4 || nranks < 1 || nranks > IBM_SLAB_MAX_RANKS || rank < 0 || rank >= nranks || ghosts < 0)
+    return IBM_EINVAL;
+  const int base = nx / nranks, rem = nx % nranks;
+  ibm_slab sl;
+  sl.nranks = nranks;
+  sl.rank = rank;
+  sl.x_begin = rank * base + std::min(rank, rem);
+  sl.x_end = sl.x_begin + base + (rank < rem ? 1 : 0);
+  sl.ghosts = nranks > 1 ? ghosts : 0;
+  ibm_grid g{nx, 4, 4};
+  for (int q = 0; q < nranks; ++q) {   // every slab long enough for its overlap
+    ibm_slab t = sl;
+    t.rank = q;
+    t.x_begin = q * base + std::min(q, rem);
+    t.x_end = t.x_begin + base + (q < rem ? 1 : 0);
+    if (check_slab(&g, nullptr, &t)) return IBM_EINVAL;
+  }
+  *out = sl;
+  return IBM_OK;
+}
+
+int ibm_slab_plan(const ibm_grid* grid, int nv, const ibm_slab* sl, int phase, int* xchg, size_t* send_count,
+                  size_t* recv_count) {
+  if (!grid || !sl || !xchg || !send_count || !recv_count || nv < 0 || grid->ny < 1 || grid->nz < 1 ||
+      phase < IBM_SLAB_INIT || phase > IBM_SLAB_GHOSTS || sl->nranks < 1 || sl->nranks > IBM_SLAB_MAX_RANKS ||
+      sl->ghosts < 0)
+    return IBM_EINVAL;
+  const size_t P = (size_t)grid->ny * grid->nz;
+  const size_t n = slab_send_count(phase, P, nv, sl->ghosts);
+  *send_count = n;
+  switch (phase) {
+    case IBM_SLAB_INIT:
+    case IBM_SLAB_SOLVE:
+      *xchg = IBM_XCHG_GATHER;
+      *recv_count = n * sl->nranks;
+      break;
+    case IBM_SLAB_FORCE:
+      *xchg = IBM_XCHG_SUM;
+      *recv_count = n;
+      break;
+    case IBM_SLAB_REDUCE:
+    case IBM_SLAB_PROJECT:
+      *xchg = IBM_XCHG_HALO;
+      *recv_count = n;
+      break;
+    default:
+      *xchg = IBM_XCHG_NONE;
+      *recv_count = 0;
+      break;
+  }
+  return IBM_OK;
+}
+
+int ibm_slab_workspace_bytes(const ibm_grid* g, const ibm_domain* d, const ibm_bodies* b, const ibm_options* o,
+                             const ibm_slab* sl, size_t* bytes) {
+  if (!bytes || !sl) return IBM_EINVAL;
+  ibm_state tmp;
+  FlagGeom fg;
+  std::vector<double> Xb;
+  double bdv;
+  Layout L;
+  BarMask bm;
+  int rc = prepare(g, d, b, o, &tmp, fg, Xb, bdv, L, bm, sl);
+  if (rc) return rc;
+  *bytes = carve<double>(&tmp, nullptr, L, tmp.fd);
+  return IBM_OK;
+}
+
+int ibm_slab_phase(ibm_state* s, int phase, double dt, const double* recv, double* send) {
+  if (!s || !s->slab_on || phase < IBM_SLAB_INIT || phase > IBM_SLAB_GHOSTS) return IBM_EINVAL;
+  if (!(s->slab_allowed & slab_bit(phase))) return IBM_EINVAL;
+  const bool needs_recv = phase != IBM_SLAB_INIT && phase != IBM_SLAB_FORCE;
+  const bool needs_send = phase != IBM_SLAB_GHOSTS;
+  if ((needs_recv && !recv) || (needs_send && !send)) return IBM_EINVAL;
+  return slab_phase_impl(s, phase, dt, recv, send);
+}
+
 
 int ibm_check_bounded_wait(unsigned int spins) {
   if (spins < 1 || spins > (1u << 24)) return IBM_EINVAL;
@@ -1093,6 +1435,22 @@ int ibm_workspace_bytes(const ibm_grid* g, const ibm_domain* d, const ibm_bodies
 
 int ibm_create(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodies* b,
                const ibm_options* o, void* workspace, size_t workspace_bytes, ibm_state** out) {
+  return create_impl(g, d, re, b, o, nullptr, workspace, workspace_bytes, out);
+}
+
+int ibm_create_slab(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodies* b,
+                    const ibm_options* o, const ibm_slab* sl, void* workspace, size_t workspace_bytes,
+                    ibm_state** out) {
+  if (!sl) return IBM_EINVAL;
+  return create_impl(g, d, re, b, o, sl, workspace, workspace_bytes, out);
+}
+
+}  // extern "C"
+
+namespace {
+int create_impl(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodies* b,
+                const ibm_options* o, const ibm_slab* sl, void* workspace, size_t workspace_bytes,
+                ibm_state** out) {
   if (!out || !(re > 0)) return IBM_EINVAL;
   *out = nullptr;
   std::unique_ptr<ibm_state> s(new (std::nothrow) ibm_state());
@@ -1102,8 +1460,9 @@ int ibm_create(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodi
   double bdv = 0;
   Layout L;
   BarMask bm;
-  int rc = prepare(g, d, b, o, s.get(), fg, Xb, bdv, L, bm);
+  int rc = prepare(g, d, b, o, s.get(), fg, Xb, bdv, L, bm, sl);
   if (rc) return rc;
+  s->slab_on = sl != nullptr;
   s->c.nu = 1.0 / re;
   s->c.f_nu = (float)s->c.nu;
   const size_t need = s->precision == IBM_FP64 ? carve<double>(s.get(), nullptr, L, s->fd)
@@ -1139,6 +1498,7 @@ int ibm_create(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodi
   }
   rc = s->precision == IBM_FP64 ? init_state<double>(s.get(), o, fg, Xb, bdv, bm)
                                 : init_state<float>(s.get(), o, fg, Xb, bdv, bm);
+  if (!rc && sl) rc = slab_setup(s.get(), *sl, g->nx);
   if (rc) {
     ibm_destroy(s.release());
     return rc;
@@ -1146,9 +1506,12 @@ int ibm_create(const ibm_grid* g, const ibm_domain* d, double re, const ibm_bodi
   *out = s.release();
   return IBM_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int ibm_step(ibm_state* s, double dt, int nsteps) {
-  if (!s || nsteps < 0) return IBM_EINVAL;
+  if (!s || nsteps < 0 || s->slab_on) return IBM_EINVAL;
   return s->precision == IBM_FP64 ? step_impl<double>(s, dt, nsteps) : step_impl<float>(s, dt, nsteps);
 }
 
@@ -1515,6 +1878,9 @@ void ibm_destroy(ibm_state* s) {
     }
   if (s->own_ws && s->ws) cudaFree(s->ws);
   if (s->probes) cudaFree(s->probes);
+  if (s->slab.tab) cudaFree(s->slab.tab);
+  if (s->slab.green) cudaFree(s->slab.green);
+  if (s->slab.scr) cudaFree(s->slab.scr);
   if (s->hprm) cudaFreeHost(s->hprm);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   if (s->side) cudaStreamDestroy(s->side);

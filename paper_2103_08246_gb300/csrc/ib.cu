@@ -109,7 +109,7 @@ __device__ inline void stencil(const Consts& c, int comp, const Frac<T>& fx, con
 __device__ inline bool marker(const Markers& m, const Flag& fl, int l, double& X, double& Y,
                               double& Z, double U[3], double& dv) {
   if (l < m.nf) {
-    X = fl.X[3 * l];
+    X = fl.X[3 * l] - m.x_shift;
     Y = fl.X[3 * l + 1];
     Z = fl.X[3 * l + 2];
     U[0] = fl.V[3 * l];

@@ -42,6 +42,8 @@ struct Markers {
   int nb = 0;                 // bar markers
   double* Xb = nullptr;       // bar marker positions (3 per marker)
   double bar_dv = 0.0;        // volume carried by each bar marker
+  double x_shift = 0.0;       // slab of an x decomposition: x of its first local plane (flag vertices
+                              // are stored in global coordinates; bar markers are shifted once)
   double* coef = nullptr;     // 3 per marker: dV / h^3 * (U - U*)
   unsigned long long* acc = nullptr;   // deterministic mode: fixed-point sums, 3 fields
   size_t nfield = 0;                   // cells of one velocity field (accumulator stride)
@@ -94,6 +96,22 @@ struct RhsCase {
   T *n0, *n1, *n2, *d0, *d1, *d2;
   const T *vin, *win;
   int gx, gy, gz, first;
+};
+
+// one slab of the x decomposition of a case (slab.cu): owned cell planes
+// [x_begin, x_end) of the global grid at local planes [gL, gL + n); gL, gR
+// overlap planes on the sides with a neighbour; first_phys / last_phys: the
+// slab holds the inflow / outflow end. Device tables: inverse pivots of the
+// slab's rows per distinct mode (n x modes), six Green's-column values per
+// mode, and a scratch of n x ny x nz values.
+constexpr int SLAB_MAX_RANKS = 8;
+constexpr int SLAB_LINE = 9;   // values per line in the all-gather of the pressure solve
+struct SlabDev {
+  int nranks = 1, rank = 0, x_begin = 0, x_end = 0, nx_global = 0;
+  int n = 0, gL = 0, gR = 0, g = 0, first_phys = 1, last_phys = 1;
+  double* tab = nullptr;
+  double* green = nullptr;
+  double* scr = nullptr;
 };
 
 // ---- fluid.cu
@@ -176,6 +194,17 @@ template <class T> void launch_ib_setup(const Consts& c, const Fields<T>& f, con
 // bin the bar markers (3 doubles each, sorted in place) into tiles; fills
 // the tile table (5 ints per tile) and the tile shape of m
 void ib_bin_bars(const Consts& c, std::vector<double>& Xb, std::vector<int>& tiles, Markers& m);
+
+// ---- slab.cu
+void slab_tables(const Consts& c, const SlabDev& sd, cudaStream_t s);
+// local solves of the slab's rows (phi after the forward transforms); SLAB_LINE values per line to send
+void slab_local_solve(const Consts& c, const SlabDev& sd, const double* phi, double* send, cudaStream_t s);
+// reduced systems from every slab's line values (rank-major), corrected solution into phi
+void slab_correct(const Consts& c, const SlabDev& sd, double* phi, const double* gathered, cudaStream_t s);
+// owned flag forces (3 per vertex) and the two end fluxes; their sums back into the state
+void slab_pack_force(const Consts& c, const SlabDev& sd, const Flag& fl, const double* qpart, int nqb,
+                     double* send, cudaStream_t s);
+void slab_unpack_force(const Consts& c, Params* prm, const Flag& fl, const double* recv, cudaStream_t s);
 
 // ---- flag.cu
 void launch_flag(Params* prm, const Flag& fl, bool force, cudaStream_t s);
