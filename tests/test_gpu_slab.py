@@ -10,6 +10,8 @@ device copies between phases; no kernel waits on another rank).
 * the production transverse plane, 96x256x256 at h = 1/64 (the 2-D cluster
   transform of 256 x 256 planes): 3 slabs equal the single-domain GPU solver
   (itself oracle-checked) to 1e-9 after 3 steps;
+* the production workload in four slabs (the paper's own split), against the
+  single-domain solver;
 * phases out of order, a step too long for the overlap and ibm_step on a
   slab state are refused with IBM_EINVAL.
 """
@@ -85,6 +87,31 @@ def test_slabs_at_the_production_plane_match_single_domain():
     X, V = ranks[1].flag()
     X1, V1, _ = one.flag()
     assert np.abs(X - X1).max() < 1e-9 and np.abs(V - V1).max() < 1e-9
+    for r in ranks:
+        r.close()
+
+
+def test_four_slabs_of_the_production_workload_match_single_domain():
+    """The paper's own configuration (four x slabs, Sec. II.B) on the
+    production grid, 512x256x256 with the bar grid and the 65x65 flag, FP64
+    at a fixed step: four slabs equal the single-domain solver to 1e-9 after
+    the initial projection and 2 steps."""
+    from paper_2103_08246_gb300 import binding as B
+    from paper_2103_08246_gb300 import inputs
+    wl = inputs.PRODUCTION.replace(dt=2e-3)
+    noise = inputs.initial_noise(wl)
+    ranks, got = _run_slabs(wl, 4, 2, noise)
+    assert all(r.slab.x_end - r.slab.x_begin == 128 for r in ranks)
+    one = B.Solver(wl, B.IBM_FP64, noise=noise)
+    one.step(2)
+    for name, g, o in zip("uvwp", got, one.fields()):
+        if name == "p":
+            g, o = g - g.mean(), o - o.mean()
+        assert _rel(g, o) < 1e-9, (name, _rel(g, o))
+    X, V = ranks[3].flag()
+    X1, V1, _ = one.flag()
+    assert np.abs(X - X1).max() < 1e-9 and np.abs(V - V1).max() < 1e-9
+    one.close()
     for r in ranks:
         r.close()
 
