@@ -606,6 +606,44 @@ def ensemble_rate(steps):
             "precision": "mixed", "shapes": shapes}
 
 
+def slab_rate(steps, nranks=4):
+    """The production workload (fixed dt = 2e-3, FP64) decomposed into
+    `nranks` x slabs, the paper's own split of one case over four GPUs,
+    with every rank emulated on this one GPU: each phase runs on every rank
+    in turn and the exchanges are device copies (no collective, no kernel
+    waiting on another rank). Wall time per step with a synchronize on both
+    sides, against the single-domain FP64 step at the same dt; plus the bytes
+    each rank would exchange per step on several GPUs."""
+    import torch
+    from paper_2103_08246_gb300 import binding, inputs
+    from paper_2103_08246_gb300 import slab as S
+    wl = inputs.PRODUCTION.replace(dt=2e-3)
+    noise = inputs.initial_noise(wl)
+    ranks = S.make_ranks(wl, nranks, wl.dt, noise)
+    comm = S.LoopbackComm()
+    S.run_phases(ranks, comm, S.INIT_SEQUENCE)
+    for _ in range(2):
+        S.run_phases(ranks, comm, S.STEP_SEQUENCE, wl.dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        S.run_phases(ranks, comm, S.STEP_SEQUENCE, wl.dt)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    xbytes = max(8 * sum(r.plan(ph)[1] for ph in S.STEP_SEQUENCE) for r in ranks)
+    ghosts = ranks[0].slab.ghosts
+    for r in ranks:
+        r.close()
+    one = binding.Solver(wl, binding.IBM_FP64, noise=noise)
+    one.step(3)
+    ms1 = time_steps(one, steps, one.stream)
+    one.close()
+    return {"ranks": nranks, "precision": "fp64", "dt": wl.dt, "ghost_planes": ghosts,
+            "ms_per_step": ms, "steps_per_s": 1000.0 / ms, "single_domain_ms_per_step": ms1,
+            "exchange_mb_per_rank_per_step": xbytes / 1e6,
+            "emulated": "all ranks on one GPU in turn, exchanges as device copies"}
+
+
 def generator_flops(P, blocks, cin=6, width=128, cout=3):
     """Algorithmic FLOPs of the inflow generator per sample: forward, input
     gradients (every layer but the first) and weight gradients; 2 per
@@ -699,7 +737,7 @@ def run_ours(args):
         cells = wl.cells
         roof, stages, kernels = stage_roofline(wl, prec, peak, peak_kind)
         step_bytes = METHOD_PASSES["mixed"] * (wl.nx + 1) * wl.ny * wl.nz * 4
-        fp32 = fp64 = ens = gen = None
+        fp32 = fp64 = ens = gen = slab = None
         if not args.no_fp64:
             s32 = binding.Solver(wl, binding.IBM_FP32, noise=inputs.initial_noise(wl))
             s32.step(3)
@@ -728,6 +766,7 @@ def run_ours(args):
                                  "frac": ach_inst / peak_inst, "ms_per_launch": rhs64},
                     "clocks": clk64}
             ens = _with_clocks(local, ensemble_rate, max(5, args.steps // 5))
+            slab = _with_clocks(local, slab_rate, 3)
             gen = _with_clocks(local, generator_rate, *measured_bf16_peak())
         e2e = None if args.no_e2e else e2e_rate(wl, prec, args.steps)
         if e2e is not None:
@@ -759,6 +798,7 @@ def run_ours(args):
             "step_hbm_frac": (step_bytes / (ms * 1e-3) / 1e9) / peak,
             "roofline": roof, "stages_ms": stages, "kernels": kernels,
             "fp64": fp64, "fp32": fp32, "ensemble": ens, "inflow_generator": gen, "e2e": e2e,
+            "x_slabs": slab,
             "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": kernels_per_step * args.steps,
             "dt_last": st["dt"], "cfl_last": st["cfl"], "n_sub": st["n_sub"],
