@@ -727,6 +727,91 @@ __device__ __forceinline__ void px_backward(LDF LD, STF ST, const T* iv, size_t 
   }
 }
 
+// Single pass over the converged rows of modes whose converged inverse pivot
+// is at most 1/2 in magnitude (FP32 arithmetic): there the back substitution
+// x_j = y_j - lim x_{j+1} equals sum_k (-lim)^k y_{j+k}, and the sum after
+// PW terms is below lim^PW <= 2^-24 of x, the FP32 rounding. Each chunk of PW
+// rows is emitted once the next chunk's forward values exist: its last row
+// from the truncated sum, the others by the exact recursion downward. The
+// forward values of those rows never go to memory (read once, written once
+// instead of read, written, read, written). Rows below ia (table pivots) and
+// the last chunk with the remaining rows keep the stored forward values and
+// the exact back substitution.
+constexpr int PW = 24;
+template <class T, class LDF, class STF>
+__device__ __forceinline__ void px_single(LDF LD, STF ST, const T* iv, size_t PT, int P, T lim, T scale, int ia,
+                                          int nx) {
+  T y = 0;
+  for (int i = 0; i < ia; ++i) {   // head: table pivots, forward values stored
+    const size_t o = (size_t)i * P;
+    y = (LD(o) * scale - y) * iv[(size_t)i * PT];
+    ST(o, y);
+  }
+  const int nch = (nx - 1 - ia) / PW;   // >= 1 (checked by the caller)
+  T yc[PW], yp[PW], nd[PW];
+#pragma unroll
+  for (int q = 0; q < PW; ++q) nd[q] = LD((size_t)(ia + q) * P);
+  T x_ia = 0;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int i0 = ia + ch * PW;
+#pragma unroll
+    for (int q = 0; q < PW; ++q) yp[q] = yc[q];
+#pragma unroll
+    for (int q = 0; q < PW; ++q) yc[q] = nd[q];
+    if (ch + 1 < nch) {
+#pragma unroll
+      for (int q = 0; q < PW; ++q) nd[q] = LD((size_t)(i0 + PW + q) * P);
+    }
+#pragma unroll
+    for (int q = 0; q < PW; ++q) {
+      y = (yc[q] * scale - y) * lim;
+      yc[q] = y;
+    }
+    if (ch > 0) {   // emit the previous chunk
+      T acc = yc[PW - 2];
+#pragma unroll
+      for (int k = PW - 3; k >= 0; --k) acc = yc[k] - lim * acc;
+      T x = yp[PW - 1] - lim * acc;
+      const int j0 = i0 - PW;
+      ST((size_t)(j0 + PW - 1) * P, x);
+#pragma unroll
+      for (int q = PW - 2; q >= 0; --q) {
+        x = yp[q] - lim * x;
+        ST((size_t)(j0 + q) * P, x);
+      }
+      if (ch == 1) x_ia = x;
+    }
+  }
+  // tail: the last chunk's forward values, the remaining rows and the last
+  // row (its own pivot) stored; exact back substitution down to the last chunk
+  const int it = ia + (nch - 1) * PW;
+#pragma unroll
+  for (int q = 0; q < PW; ++q) ST((size_t)(it + q) * P, yc[q]);
+  for (int i = it + PW; i < nx - 1; ++i) {
+    const size_t o = (size_t)i * P;
+    y = (LD(o) * scale - y) * lim;
+    ST(o, y);
+  }
+  {
+    const size_t o = (size_t)(nx - 1) * P;
+    y = (LD(o) * scale - y) * iv[(size_t)(nx - 1) * PT];
+    ST(o, y);
+  }
+  T x = y;
+  for (int i = nx - 2; i >= it; --i) {
+    const size_t o = (size_t)i * P;
+    x = LD(o) - lim * x;
+    ST(o, x);
+  }
+  if (nch == 1) x_ia = x;
+  x = x_ia;   // head: exact back substitution with the table pivots
+  for (int i = ia - 1; i >= 0; --i) {
+    const size_t o = (size_t)i * P;
+    x = LD(o) - iv[(size_t)i * PT] * x;
+    ST(o, x);
+  }
+}
+
 template <class T, class S>
 __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict__ tab, const int* __restrict__ conv,
                                                    S* __restrict__ phi, T scale, double* __restrict__ mean00) {
@@ -748,6 +833,13 @@ __global__ void __launch_bounds__(128) k_poisson_x(Consts c, const T* __restrict
   // slot on the right-hand side (chunks of PB planes)
   const int ia = min(max(__reduce_max_sync(__activemask(), conv[mi]), 1), nx - 1);
   const T lim = iv[(size_t)(nx - 2) * PT];
+  if constexpr (sizeof(T) == 4) {
+    // every mode of the warp decays fast enough for the single pass (never mode (0, 0))
+    if (nx - 1 - ia >= PW && __all_sync(__activemask(), fabsf(lim) <= 0.5f) && !zero_mode) {
+      px_single<T>(LD, ST, iv, PT, P, lim, scale, ia, nx);
+      return;
+    }
+  }
   constexpr int PB = sizeof(T) == 8 ? PF : 2 * PF;
   T y = 0;
   px_forward<PF, true>(LD, ST, iv, PT, P, lim, scale, zero_mode, 0, ia, y);
