@@ -73,12 +73,12 @@ METHOD_PASSES = {"fp32": 57, "mixed": 65}
 # (profiles/launches_production_fp32.md, launches_production_mixed.md);
 # valid for the kernels of those captures and to be refreshed whenever one
 # of them changes.
-_TRAFFIC_COMMON = {"rhs": 1742.7e6, "af_yz": 1156.4e6, "af_x": 752.4e6, "mass_div": 519.2e6,
-                   "poisson_x": None, "ib": 57.9e6}
+_TRAFFIC_COMMON = {"rhs": 1743.1e6, "af_yz": 1156.6e6, "af_x": 752.3e6, "mass_div": 519.2e6,
+                   "poisson_x": 218.4e6, "ib": 57.9e6}
 TRAFFIC_BYTES = {
-    "fp32": dict(_TRAFFIC_COMMON, dht2d=209.8e6, project=1181.2e6),
-    "mixed": dict(_TRAFFIC_COMMON, dht2d=212.2e6, tc_bf16=84.5e6, residual=317.7e6, poisson_x16=None,
-                  project=1258.1e6),
+    "fp32": dict(_TRAFFIC_COMMON, dht2d=209.9e6, project=1181.3e6),
+    "mixed": dict(_TRAFFIC_COMMON, dht2d=212.3e6, tc_bf16=84.6e6, residual=317.6e6, poisson_x16=78.2e6,
+                  project=1258.4e6),
 }
 # the mixed path's projection reads the solve's two parts (FP32 predictor,
 # bfloat16 correction): half a pass more than FIELD_PASSES["project"]
