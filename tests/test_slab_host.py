@@ -2,6 +2,8 @@
 along x, one per GPU), host side.
 
 * the library's host-only partition, overlap and exchange-size rules;
+* the torch.distributed communicator on 3 gloo ranks delivers every exchange
+  kind (sum, gather, neighbour halo) exactly as the in-process loopback;
 * the phase protocol on real CPU ranks: 2 and 3 processes joined over gloo
   run the package's driver and torch.distributed communicator with each
   slab's phases carried out by the host model of tests/slab_oracle.py (the
@@ -168,3 +170,59 @@ def test_gloo_ranks_match_single_domain_oracle(lib, oracle_run, tmp_path, world)
     wl = workload()
     cuts = np.cumsum([q["p"].shape[0] for q in parts])[:-1] * wl.lx / wl.nx
     assert any(ora.X[:, 0].min() < c < ora.X[:, 0].max() for c in cuts)
+
+
+COMM_SCRIPT = r"""
+import json, os, sys
+sys.path.insert(0, {root!r})
+import torch
+import torch.distributed as dist
+from paper_2103_08246_gb300 import binding as B, slab as S
+rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
+dist.init_process_group("gloo", rank=rank, world_size=world,
+                        init_method="tcp://127.0.0.1:" + os.environ["MASTER_PORT"])
+comm = S.TorchComm()
+def buf(r, n):   # rank r's send buffer: distinct values per rank and element
+    return torch.arange(n, dtype=torch.float64) + 1000.0 * (r + 1)
+out = {{}}
+for kind, n in ((B.IBM_XCHG_SUM, 5), (B.IBM_XCHG_GATHER, 4), (B.IBM_XCHG_HALO, 6)):
+    recv_count = n * world if kind == B.IBM_XCHG_GATHER else n
+    (got,) = comm.exchange(kind, [buf(rank, n)], recv_count)
+    out[kind] = got.tolist()
+(none,) = comm.exchange(B.IBM_XCHG_NONE, [None], 0)
+out["none"] = none is None
+dist.destroy_process_group()
+print(json.dumps(out), flush=True)
+"""
+
+
+def test_torch_comm_matches_loopback_on_gloo_ranks():
+    """The torch.distributed communicator (3 gloo ranks) delivers every
+    exchange kind exactly as the in-process loopback does."""
+    import torch
+
+    from paper_2103_08246_gb300 import binding as B
+    from paper_2103_08246_gb300 import slab as S
+    world, port = 3, _free_port()
+    code = COMM_SCRIPT.format(root=ROOT)
+    env = dict(os.environ, WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port),
+               CUDA_VISIBLE_DEVICES="")
+    procs = [subprocess.Popen([sys.executable, "-c", code], env=dict(env, RANK=str(r)), cwd=ROOT,
+                              stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+             for r in range(world)]
+    outs = []
+    for p in procs:
+        out, err = p.communicate(timeout=300)
+        assert p.returncode == 0, err[-3000:]
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    loop = S.LoopbackComm()
+    for kind, n in ((B.IBM_XCHG_SUM, 5), (B.IBM_XCHG_GATHER, 4), (B.IBM_XCHG_HALO, 6)):
+        sends = [torch.arange(n, dtype=torch.float64) + 1000.0 * (r + 1) for r in range(world)]
+        recv_count = n * world if kind == B.IBM_XCHG_GATHER else n
+        ref = loop.exchange(kind, sends, recv_count)
+        for r in range(world):
+            assert outs[r][str(kind)] == ref[r].tolist(), (kind, r)
+    assert all(o["none"] for o in outs)
+    # halo: the first half comes from the left neighbour's second half, none on rank 0
+    assert outs[0][str(B.IBM_XCHG_HALO)][:3] == [0.0, 0.0, 0.0]
+    assert outs[1][str(B.IBM_XCHG_HALO)][:3] == [1003.0, 1004.0, 1005.0]
