@@ -630,6 +630,25 @@ def slab_rate(steps, nranks=4):
         S.run_phases(ranks, comm, S.STEP_SEQUENCE, wl.dt)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3 / steps
+    # each rank's own phases, timed one at a time with a synchronize after
+    # each (what that rank's GPU would spend per step), and the device-copy
+    # exchanges between them
+    per_rank = [0.0] * nranks
+    xch = 0.0
+    for _ in range(steps):
+        recv = [None] * nranks
+        for ph in S.STEP_SEQUENCE:
+            sends = []
+            for i, r in enumerate(ranks):
+                t1 = time.perf_counter()
+                sends.append(r.phase(ph, wl.dt, recv[i]))
+                torch.cuda.synchronize()
+                per_rank[i] += time.perf_counter() - t1
+            t1 = time.perf_counter()
+            kind, _, recv_count = ranks[0].plan(ph)
+            recv = comm.exchange(kind, sends, recv_count)
+            torch.cuda.synchronize()
+            xch += time.perf_counter() - t1
     xbytes = max(8 * sum(r.plan(ph)[1] for ph in S.STEP_SEQUENCE) for r in ranks)
     ghosts = ranks[0].slab.ghosts
     for r in ranks:
@@ -640,6 +659,8 @@ def slab_rate(steps, nranks=4):
     one.close()
     return {"ranks": nranks, "precision": "fp64", "dt": wl.dt, "ghost_planes": ghosts,
             "ms_per_step": ms, "steps_per_s": 1000.0 / ms, "single_domain_ms_per_step": ms1,
+            "rank_phases_ms_per_step": [1e3 * t / steps for t in per_rank],
+            "loopback_exchange_ms_per_step": 1e3 * xch / steps,
             "exchange_mb_per_rank_per_step": xbytes / 1e6,
             "emulated": "all ranks on one GPU in turn, exchanges as device copies"}
 
