@@ -485,7 +485,10 @@ int ibm_slab_workspace_bytes(const ibm_grid* grid, const ibm_domain* domain, con
  * Asynchronous, except GHOSTS, which synchronises and reports device-side
  * errors of the step (IBM_EDIVERGED for a non-finite velocity, IBM_ETIMEOUT,
  * IBM_EINVAL for a step size outside the implicit factor's range). Buffers
- * belong to the caller; `send` may be reused once the exchange has read it. */
+ * belong to the caller; `send` may be reused once the exchange has read it.
+ * The flag's structural update of SOLVE runs on a second stream of the
+ * state and is joined by GHOSTS: queries between FORCE and GHOSTS see a step
+ * in progress. */
 int ibm_slab_phase(ibm_state* s, int phase, double dt, const double* recv, double* send);
 
 /* ---- Learned inflow generator ------------------------------------------

@@ -756,6 +756,10 @@ int init_state(ibm_state* s, const ibm_options* o, const FlagGeom& fg,
     s->cur = 0;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
+    // the structural update runs beside the pressure phases
+    CK(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
     return IBM_OK;
   }
   // initial projection of u0 (dt absorbed in phi), velocity only
@@ -1207,7 +1211,12 @@ int slab_phase_impl(ibm_state* s, int phase, double dt, const double* recv, doub
     }
     case IBM_SLAB_SOLVE:
       slab_unpack_force(c, f.prm, s->fl, recv, st);
-      launch_flag(f.prm, s->fl, false, st);
+      if (s->fl.nv) {   // beside the divergence, transforms and solves; joined in GHOSTS
+        CK(cudaEventRecord(s->ev_fork, st));
+        CK(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+        launch_flag(f.prm, s->fl, false, s->side);
+        CK(cudaEventRecord(s->ev_join, s->side));
+      }
       launch_div<double>(c, f, s->cur, false, st);
       slab_transforms(s, false);
       slab_local_solve(c, sd, f.phi, send, st);
@@ -1267,6 +1276,7 @@ int slab_phase_impl(ibm_state* s, int phase, double dt, const double* recv, doub
         }
       }
       s->slab_allowed = slab_bit(IBM_SLAB_INIT) | slab_bit(IBM_SLAB_FORCE);
+      CK(cudaStreamWaitEvent(st, s->ev_join, 0));   // the step's structural update
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(s->hprm, f.prm, sizeof(Params), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
