@@ -467,8 +467,9 @@ int ibm_slab_plan(const ibm_grid* grid, int n_flag_vertices, const ibm_slab* sla
  * to window coordinates. No projection is applied: run the initial phase
  * sequence before the first step. workspace: as ibm_create (window size);
  * the slab's solve tables (pivots per mode and row, 6 values per mode, and a
- * scratch of the owned planes) are allocated by the library. ibm_step
- * refuses slab states (IBM_EINVAL). */
+ * scratch of the owned planes) are allocated by the library. ibm_step,
+ * ibm_time_stage(IBM_STAGE_STEP) and the ensembles refuse slab states
+ * (IBM_EINVAL). */
 int ibm_create_slab(const ibm_grid* grid, const ibm_domain* domain, double re,
                     const ibm_bodies* bodies, const ibm_options* opts, const ibm_slab* slab,
                     void* workspace, size_t workspace_bytes, ibm_state** out);

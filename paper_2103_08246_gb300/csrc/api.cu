@@ -1580,6 +1580,7 @@ int ibm_stats(ibm_state* s, ibm_stats_t* out) {
 
 int ibm_time_stage(ibm_state* s, int stage, int nrep, double* ms) {
   if (!s || !ms || nrep < 1 || stage < IBM_STAGE_STEP || stage > IBM_STAGE_POISSON_X16) return IBM_EINVAL;
+  if (stage == IBM_STAGE_STEP && s->slab_on) return IBM_EINVAL;   // a slab state captures no step
   cudaStream_t st = s->stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

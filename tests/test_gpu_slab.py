@@ -13,8 +13,8 @@ no kernel waits on another rank).
   (itself oracle-checked) to 1e-9 after 3 steps;
 * the production workload in four slabs (the paper's own split), against the
   single-domain solver;
-* phases out of order, a step too long for the overlap and ibm_step on a
-  slab state are refused with IBM_EINVAL.
+* phases out of order, a step too long for the overlap, and ibm_step, step
+  timing and ensembles on a slab state are refused with IBM_EINVAL.
 """
 import numpy as np
 import pytest
@@ -135,6 +135,10 @@ def test_phase_order_and_overlap_are_enforced():
     # a step whose implicit decay length exceeds the overlap
     assert B.ibm_slab_phase(st.state, B.IBM_SLAB_FORCE, 50 * wl.dt, None, p) == B.IBM_EINVAL
     assert B.ibm_step(st.state, wl.dt, 1) == B.IBM_EINVAL
+    with pytest.raises(B.IBMError):   # no captured step to time or to join an ensemble
+        B.ibm_time_stage(st.state, B.STAGES["step"], 1)
+    with pytest.raises(B.IBMError):
+        B.ibm_ensemble_create([st.state])
     # the full sequences still run afterwards
     S.run_phases(ranks, S.LoopbackComm(), S.INIT_SEQUENCE)
     S.run_phases(ranks, S.LoopbackComm(), S.STEP_SEQUENCE, wl.dt)
