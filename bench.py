@@ -518,7 +518,8 @@ def e2e_rate(wl, precision, steps):
     """Steps/s through the C ABI with host buffers: upload the state (FP64
     host arrays, converted on the device) from pinned host memory, K x
     (ibm_step + flag state read-back), read the fields back. One untimed pass
-    of the same sequence first (module loading, first graph uploads). Also
+    of the same sequence first (module loading, first graph uploads), then the
+    median of three timed passes. Also
     reports the host link's copy bandwidth and the state transfer time it
     implies; the caller adds the rate these allow, K / (K x device step time +
     transfer time)."""
@@ -548,16 +549,22 @@ def e2e_rate(wl, precision, steps):
         for q, a in zip(qs, host):
             binding.ibm_get_field(s.state, q, a)
     run(1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    run(steps)
-    el = time.perf_counter() - t0
+    # three timed repetitions, the median reported: the host's own scheduling
+    # between the per-step synchronisations moves single runs by up to ~20%
+    els = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(steps)
+        els.append(time.perf_counter() - t0)
+    el = statistics.median(els)
     s.close()
     field_bytes = sum(a.nbytes for a in host)          # FP64 host arrays: the bytes that cross the link
     h2d = field_bytes / steps + 16                     # + the time-step mode (two doubles) per step
     d2h = field_bytes / steps + 3 * X.nbytes + 8 * 64  # + flag X, V, F and the step parameters
     link_h2d, link_d2h = host_link_gbs()
     return {"value": steps / el, "unit": "steps/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "repeats_steps_per_s": [steps / e for e in els],
             "link_gbs": {"h2d": link_h2d, "d2h": link_d2h}, "state_transfer_ms":
             (field_bytes / (link_h2d * 1e6) + field_bytes / (link_d2h * 1e6))}
 
