@@ -11,7 +11,9 @@ along x, one per GPU), host side.
   pressure equation's x solve, owned flag forces and end fluxes); the
   assembled fields and the flag after the initial projection and 5 steps
   equal the single-domain oracle to 1e-9 (the FP64 parity bound), with bars
-  in the first slab and the flag across a cut.
+  in the first slab and the flag across a cut; with an overlap of 3 planes
+  instead of the library's the same run misses the oracle (the check sees
+  the overlap width).
 """
 import json
 import os
@@ -22,6 +24,8 @@ import sys
 
 import numpy as np
 import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 NSTEPS = 5
@@ -226,3 +230,28 @@ def test_torch_comm_matches_loopback_on_gloo_ranks():
     # halo: the first half comes from the left neighbour's second half, none on rank 0
     assert outs[0][str(B.IBM_XCHG_HALO)][:3] == [0.0, 0.0, 0.0]
     assert outs[1][str(B.IBM_XCHG_HALO)][:3] == [1003.0, 1004.0, 1005.0]
+
+
+def test_overlap_narrower_than_the_decay_length_is_detected(lib, oracle_run):
+    """The same decomposition in one process (loopback exchanges) equals the
+    oracle with the library's overlap and misses it with 3 planes: the
+    window's wrong ends reach the owned planes through the implicit x factor,
+    so the parity check above really tests the overlap width."""
+    from paper_2103_08246_gb300 import binding as B
+    from paper_2103_08246_gb300 import inputs
+    from paper_2103_08246_gb300 import slab as S
+    from slab_oracle import OracleSlab
+    wl = workload()
+    noise = inputs.initial_noise(wl, amp=0.05)
+
+    def run(g):
+        ranks = [OracleSlab(wl, B.ibm_slab_split(wl.nx, 2, r, g), noise) for r in range(2)]
+        S.run_phases(ranks, S.LoopbackComm(), S.INIT_SEQUENCE)
+        for _ in range(NSTEPS):
+            S.run_phases(ranks, S.LoopbackComm(), S.STEP_SEQUENCE, wl.dt)
+        got = np.concatenate([r.owned()[0] for r in ranks], axis=0)
+        ref = oracle_run.fields()[0]
+        return np.abs(got - ref).max() / np.abs(ref).max()
+
+    assert run(B.ibm_slab_ghosts(wl.re, wl.lx / wl.nx, wl.dt)) < 1e-12
+    assert run(3) > 1e-9
