@@ -118,6 +118,9 @@ def parse():
     ap.add_argument("--profile-generator-train", type=int, default=0,
                     help="only run this many generator training steps (256x256 planes, "
                          "batch 8, 13 blocks) after one warm step, for ncu, and exit")
+    ap.add_argument("--profile-slabs", type=int, default=0,
+                    help="only run this many FP64 steps of the 256x256x256 half-length case in four "
+                         "x slabs (all on this GPU, after the initial projection), for ncu, and exit")
     return ap.parse_args()
 
 
@@ -135,6 +138,24 @@ def run_profile(args):
     s.step(args.profile_steps)
     torch.cuda.synchronize()
     s.close()
+
+
+def run_profile_slabs(args):
+    """Plain run for profilers: the half-length production case (256 x-planes,
+    bars and flag, fixed dt 2e-3) decomposed into four x slabs on this GPU."""
+    import torch
+    from paper_2103_08246_gb300 import build, inputs
+    from paper_2103_08246_gb300 import slab as S
+    build.build()
+    wl = inputs.PRODUCTION.replace(name="half-256x256x256", nx=256, lx=4.0, flag_x_le=2.0, dt=2e-3)
+    ranks = S.make_ranks(wl, 4, wl.dt, inputs.initial_noise(wl))
+    comm = S.LoopbackComm()
+    S.run_phases(ranks, comm, S.INIT_SEQUENCE)
+    for _ in range(args.profile_slabs):
+        S.run_phases(ranks, comm, S.STEP_SEQUENCE, wl.dt)
+    torch.cuda.synchronize()
+    for r in ranks:
+        r.close()
 
 
 def run_profile_generator(args):
@@ -845,6 +866,9 @@ def main():
         return
     if args.profile_generator > 0:
         run_profile_generator(args)
+        return
+    if args.profile_slabs > 0:
+        run_profile_slabs(args)
         return
     if args.profile_generator_train > 0:
         run_profile_generator_train(args)
