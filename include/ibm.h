@@ -413,7 +413,8 @@ typedef struct {
   int x_end;     /* one past the last owned cell plane (nx on the last rank)     */
   int ghosts;    /* overlap planes on each side with a neighbour: at least
                     ibm_slab_ghosts(), x_end - x_begin >= ghosts + 1, and the
-                    window [x_begin - ghosts, x_end + ghosts) inside [0, nx)     */
+                    window [x_begin - ghosts, x_end + ghosts) inside [0, nx);
+                    the same on every rank (the exchange layouts depend on it) */
 } ibm_slab;
 
 /* phases (in step order) */
