@@ -394,8 +394,9 @@ void ibm_ensemble_destroy(ibm_ensemble* e);
  *     of the single-domain solve;
  *   - the flag's fluid force (each vertex counted by the rank owning its x
  *     position, all-reduce) and the inflow / outflow fluxes of the mass fix;
- *   - the overlap planes of u, v, w, p and the advection history, refreshed
- *     from the owning neighbours after every step. The implicit x factor's
+ *   - the overlap planes of u, v, w and p, refreshed from the owning
+ *     neighbours after every step (each rank recomputes the advection
+ *     history from the refreshed velocity). The implicit x factor's
  *     dependence on the window's ends decays like rho^d over d planes
  *     (rho < 1), so overlap planes wider than that decay plus the forcing
  *     kernel's support leave the owned planes exact to round-off

@@ -1120,9 +1120,13 @@ int slab_min_ghosts(double nu, double h, double dt) {
   return H + 4;
 }
 
-// doubles in one half of the overlap exchange: u, v, w and the three
-// advection components with ghosts + 1 planes, p with ghosts planes
-size_t slab_halo_half(size_t P, int g) { return (size_t)(7 * g + 6) * P; }
+// doubles in one half of the overlap exchange: u, v, w with ghosts + 1
+// planes, p with ghosts planes. The advection history N^{n-1} is not
+// exchanged: each rank computes it from the refreshed velocity, exact except
+// next to the window's ends, where it only disturbs planes that the implicit
+// x factor's decay keeps away from the owned ones (and that the next refresh
+// replaces)
+size_t slab_halo_half(size_t P, int g) { return (size_t)(4 * g + 3) * P; }
 
 int slab_setup(ibm_state* s, const ibm_slab& sl, int nx_global) {
   SlabDev& sd = s->slab;
@@ -1235,19 +1239,19 @@ int slab_phase_impl(ibm_state* s, int phase, double dt, const double* recv, doub
       launch_project<double>(c, f, s->cur, s->slab_initial, st);
       s->cur ^= 1;
       const int cur = s->cur;
-      double* arr[7] = {f.u[cur], f.v[cur], f.w[cur], f.n[0], f.n[1], f.n[2], f.p};
+      double* arr[4] = {f.u[cur], f.v[cur], f.w[cur], f.p};
       const size_t half = slab_halo_half(P, g);
       if (sd.gL > 0) {   // to rank - 1: its right overlap, our planes [gL, gL + g] (p: g planes)
         size_t off = 0;
-        for (int a = 0; a < 7; ++a) {
-          const int planes = a < 6 ? g + 1 : g;
+        for (int a = 0; a < 4; ++a) {
+          const int planes = a < 3 ? g + 1 : g;
           CK(copy_planes(send + off, arr[a], gL, planes, P, false, st));
           off += (size_t)planes * P;
         }
       }
       if (sd.gR > 0) {   // to rank + 1: its left overlap, our last g owned planes
         size_t off = half;
-        for (int a = 0; a < 7; ++a) {
+        for (int a = 0; a < 4; ++a) {
           CK(copy_planes(send + off, arr[a], gL + n - g, g, P, false, st));
           off += (size_t)g * P;
         }
@@ -1258,19 +1262,19 @@ int slab_phase_impl(ibm_state* s, int phase, double dt, const double* recv, doub
     }
     case IBM_SLAB_GHOSTS: {
       const int cur = s->cur;
-      double* arr[7] = {f.u[cur], f.v[cur], f.w[cur], f.n[0], f.n[1], f.n[2], f.p};
+      double* arr[4] = {f.u[cur], f.v[cur], f.w[cur], f.p};
       const size_t half = slab_halo_half(P, g);
       if (sd.gL > 0) {   // from rank - 1: g planes per array into planes [0, g)
         size_t off = 0;
-        for (int a = 0; a < 7; ++a) {
+        for (int a = 0; a < 4; ++a) {
           CK(copy_planes(arr[a], recv + off, 0, g, P, true, st));
           off += (size_t)g * P;
         }
       }
       if (sd.gR > 0) {   // from rank + 1: planes [nx - g, nx] (p: [nx - g, nx))
         size_t off = half;
-        for (int a = 0; a < 7; ++a) {
-          const int planes = a < 6 ? g + 1 : g;
+        for (int a = 0; a < 4; ++a) {
+          const int planes = a < 3 ? g + 1 : g;
           CK(copy_planes(arr[a], recv + off, c.nx - g, planes, P, true, st));
           off += (size_t)planes * P;
         }

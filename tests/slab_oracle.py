@@ -275,9 +275,9 @@ class OracleSlab:
             send = np.zeros(count)
             half = count // 2
             gg = self.slab.ghosts
-            arrs = [self.u, self.v, self.w] + self.N + [self.p]
+            arrs = [self.u, self.v, self.w, self.p]
             if self.gL > 0:
-                pieces = [a[g:g + gg + 1] for a in arrs[:6]] + [self.p[g:g + gg]]
+                pieces = [a[g:g + gg + 1] for a in arrs[:3]] + [self.p[g:g + gg]]
                 flat = np.concatenate([q.ravel() for q in pieces])
                 send[:flat.size] = flat
             if self.gR > 0:
@@ -288,7 +288,7 @@ class OracleSlab:
         elif phase == B.IBM_SLAB_GHOSTS:
             half = recv.size // 2
             gg = self.slab.ghosts
-            arrs = [self.u, self.v, self.w] + self.N + [self.p]
+            arrs = [self.u, self.v, self.w, self.p]
             if self.gL > 0:
                 off = 0
                 for a in arrs:
@@ -298,7 +298,7 @@ class OracleSlab:
             if self.gR > 0:
                 off = half
                 for i, a in enumerate(arrs):
-                    planes = gg + 1 if i < 6 else gg
+                    planes = gg + 1 if i < 3 else gg
                     m = planes * P
                     a[a.shape[0] - planes:] = recv[off:off + m].reshape((planes,) + a.shape[1:])
                     off += m

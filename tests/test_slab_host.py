@@ -90,7 +90,7 @@ def test_exchange_sizes(lib):
             B.IBM_SLAB_FORCE: (B.IBM_XCHG_SUM, 3 * 25 + 2, 3 * 25 + 2),
             B.IBM_SLAB_SOLVE: (B.IBM_XCHG_GATHER, 9 * P, 27 * P),
             B.IBM_SLAB_REDUCE: (B.IBM_XCHG_HALO, 2 * P, 2 * P),
-            B.IBM_SLAB_PROJECT: (B.IBM_XCHG_HALO, 2 * (7 * 11 + 6) * P, 2 * (7 * 11 + 6) * P),
+            B.IBM_SLAB_PROJECT: (B.IBM_XCHG_HALO, 2 * (4 * 11 + 3) * P, 2 * (4 * 11 + 3) * P),
             B.IBM_SLAB_GHOSTS: (B.IBM_XCHG_NONE, 0, 0)}
     for ph, w in want.items():
         assert B.ibm_slab_plan(grid, 25, sl, ph) == w
