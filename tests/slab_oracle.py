@@ -143,14 +143,12 @@ class OracleSlab:
         return out.ravel()
 
     def _reduce(self, gath):
-        import torch  # noqa: F401  (recv arrives as a torch tensor)
         R = self.slab.nranks
         ny, nz = self.wl.ny, self.wl.nz
         e = np.asarray(gath).reshape(R, ny, nz, 9)
         M = 2 * (R - 1)
         left = np.zeros((ny, nz))
         right = np.zeros((ny, nz))
-        mean = 0.0
         if M:
             A = np.zeros((ny, nz, M, M))
             b = np.zeros((ny, nz, M))
